@@ -1,0 +1,86 @@
+"""Small seeded or closed-form initial states for the tests (1-D problems run on
+an N x 1 x 1 periodic grid along any axis, 3-D random states), shared by the
+oracle pins and the GPU parity tests.  Nothing here computes a step of the
+update."""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2110_01792_gb300 import inputs as I
+
+
+def line_layout(N, axis=0, ng=4):
+    n = [1, 1, 1]
+    n[axis] = N
+    return I.make_layout([[0, 0, 0]], [n], tuple(n), ng)
+
+
+def set_line(lay, arr, values, axis):
+    """Write a length-N profile along ``axis`` into the interior of patch 0."""
+    v = lay.interior(arr, 0)
+    shape = [1, 1, 1]
+    shape[2 - axis] = len(values)
+    v[...] = np.asarray(values, dtype=arr.dtype).reshape(shape)
+
+
+def get_line(lay, arr, axis):
+    return lay.interior(arr, 0).reshape(-1).copy()
+
+
+def hydro_line(N, rho, u, p, gamma, axis=0, ng=4, vt=(0.0, 0.0)):
+    """1-D hydro state with normal velocity u along ``axis``; vt are the two
+    transverse velocities (axis+1, axis+2 mod 3)."""
+    lay = line_layout(N, axis, ng)
+    U = I.zeros(lay, 5)
+    rho = np.broadcast_to(np.asarray(rho, dtype=float), (N,))
+    u = np.broadcast_to(np.asarray(u, dtype=float), (N,))
+    p = np.broadcast_to(np.asarray(p, dtype=float), (N,))
+    vel = [None, None, None]
+    vel[axis] = u
+    vel[(axis + 1) % 3] = np.full(N, vt[0])
+    vel[(axis + 2) % 3] = np.full(N, vt[1])
+    set_line(lay, U[0], rho, axis)
+    for d in range(3):
+        set_line(lay, U[1 + d], rho * vel[d], axis)
+    ke = 0.5 * rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2)
+    set_line(lay, U[4], p / (gamma - 1.0) + ke, axis)
+    return lay, U
+
+
+def centres(N, L=1.0):
+    return (np.arange(N) + 0.5) * (L / N)
+
+
+def random_hydro_3d(n, seed=7, ng=4, lay=None, vamp=0.3):
+    """Random smooth-ish 3-D periodic hydro state (positive rho and P)."""
+    if lay is None:
+        lay = I.single_box(*n, ng=ng) if isinstance(n, (tuple, list)) else I.single_box(n, ng=ng)
+    rng = np.random.Generator(np.random.Philox(seed))
+    gamma = 5.0 / 3.0
+    U = I.zeros(lay, 5)
+    for b in range(lay.nbox):
+        shp = lay.interior(U[0], b).shape
+        rho = 1.0 + 0.3 * rng.random(shp)
+        v = vamp * rng.standard_normal((3,) + shp)
+        P = 1.0 + 0.3 * rng.random(shp)
+        lay.interior(U[0], b)[...] = rho
+        for d in range(3):
+            lay.interior(U[1 + d], b)[...] = rho * v[d]
+        lay.interior(U[4], b)[...] = P / (gamma - 1.0) + 0.5 * rho * (v ** 2).sum(0)
+    return lay, U, gamma
+
+
+def random_rad_3d(lay, seed=11, fmax=0.6):
+    """Random radiation state with |f| <= fmax."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    R = I.zeros(lay, 4)
+    c = 100.0
+    for b in range(lay.nbox):
+        shp = lay.interior(R[0], b).shape
+        Er = 0.5 + rng.random(shp)
+        f = rng.standard_normal((3,) + shp)
+        f *= fmax * rng.random(shp) / np.maximum(np.sqrt((f ** 2).sum(0)), 1e-12)
+        lay.interior(R[0], b)[...] = Er
+        for d in range(3):
+            lay.interior(R[1 + d], b)[...] = c * Er * f[d]
+    return R

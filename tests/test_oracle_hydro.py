@@ -1,0 +1,323 @@
+"""Pins of the oracle's hydro stage against what the paper and the mathematics
+fix (no GPU).  Each test names the passage or the textbook fact it checks."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_01792_gb300 import inputs as I
+from tests import exact_riemann as ER
+from tests import problems as P
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _grid(lay):
+    return O.Grid(lay.lo, lay.n, lay.off, lay.dom_n, lay.ng)
+
+
+def advance_to(lay, p, U, t_end, dt_fixed=None):
+    """RK2-SSP hydro steps with the oracle until t_end (last step shortened)."""
+    g = _grid(lay)
+    U1 = [np.zeros_like(a) for a in U]
+    t = 0.0
+    nstep = 0
+    while t < t_end * (1 - 1e-14):
+        dt = dt_fixed if dt_fixed else O.timestep(g, p, U)[0]
+        dt = min(dt, t_end - t)
+        O.hydro_stage(g, p, 1, U, None, U1, dt)
+        O.hydro_stage(g, p, 2, U, U1, U, dt)
+        t += dt
+        nstep += 1
+    return nstep
+
+
+# ---------------------------------------------------------------- PPM -----
+
+def test_ppm_constant_and_cubic_exactness():
+    """The 4-point interface stencil is exact for cell averages of a cubic
+    (textbook property of the PPM interface formula, Sec. 2.2.1); constants
+    are reproduced exactly."""
+    assert O.ppm_cell([2.5] * 5) == (2.5, 2.5)
+    # cell averages of x^3 on cells [i, i+1], i = 5..9 (monotone, no limiting)
+    avg = [((i + 1) ** 4 - i ** 4) / 4.0 for i in range(5, 10)]
+    qL, qR = O.ppm_cell(avg)
+    assert abs(qL - 7.0 ** 3) < 1e-11 * 343 and abs(qR - 8.0 ** 3) < 1e-11 * 512
+
+
+def test_ppm_extremum_goes_linear_with_mc_slope():
+    """At a cell-average extremum the reconstruction reverts to linear
+    (Balsara 2017); the MC slope is zero there, so the cell is flat."""
+    qL, qR = O.ppm_cell([0.0, 1.0, 3.0, 1.0, 0.0])
+    assert qL == 3.0 and qR == 3.0
+    # face values that form an extremum inside a monotone cell: linear, MC slope
+    s = [0.0, 0.0, 0.1, 10.0, 10.0]
+    qL, qR = O.ppm_cell(s)
+    assert qL <= s[2] <= qR and qL >= min(s[1:4]) - 1e-15 and qR <= max(s[1:4]) + 1e-15
+
+
+def test_ppm_mirror_symmetry():
+    """Reversing the stencil swaps and keeps the face states (the symmetric
+    grouping of Sec. 2.2.1 makes this exact in floating point)."""
+    rng = np.random.Generator(np.random.Philox(3))
+    for _ in range(2000):
+        s = rng.standard_normal(5)
+        qL, qR = O.ppm_cell(s)
+        rL, rR = O.ppm_cell(s[::-1])
+        assert (qL, qR) == (rR, rL)
+        lo, hi = min(s[1:4]), max(s[1:4])
+        # face states always lie within the 3-cell range or the CW84 reset range
+        assert np.isfinite(qL) and np.isfinite(qR)
+        assert min(qL, qR) <= s[2] <= max(qL, qR) or (qL == qR == s[2])
+        del lo, hi
+
+
+# --------------------------------------------------------------- HLLC -----
+
+def _phys_flux(w, d, g):
+    rho, p = w[0], w[4]
+    v = np.array(w[1:4])
+    E = p / (g - 1) + 0.5 * rho * (v ** 2).sum()
+    F = np.zeros(5)
+    F[0] = rho * v[d]
+    F[1:4] = rho * v[d] * v
+    F[1 + d] += p
+    F[4] = v[d] * (E + p)
+    return F
+
+
+def test_hllc_consistency_and_supersonic():
+    """F(w, w) equals the physical Euler flux; fully supersonic flow takes the
+    upwind flux (Toro 2009, ch. 10)."""
+    g = 1.4
+    rng = np.random.Generator(np.random.Philox(5))
+    for _ in range(200):
+        w = [0.5 + rng.random(), *rng.standard_normal(3), 0.5 + rng.random()]
+        for d in range(3):
+            np.testing.assert_allclose(O.hllc(w, w, d, g), _phys_flux(w, d, g), rtol=1e-13,
+                                       atol=1e-13)
+    wL = [1.0, 5.0, 0.1, -0.2, 1.0]
+    wR = [0.5, 4.0, 0.3, 0.1, 0.8]
+    np.testing.assert_allclose(O.hllc(wL, wR, 0, g), _phys_flux(wL, 0, g), rtol=1e-14)
+    wL2 = [1.0, -5.0, 0.1, -0.2, 1.0]
+    wR2 = [0.5, -4.0, 0.3, 0.1, 0.8]
+    np.testing.assert_allclose(O.hllc(wL2, wR2, 0, g), _phys_flux(wR2, 0, g), rtol=1e-14)
+
+
+def test_hllc_mirror_and_contact():
+    """Reflecting x -> -x swaps the states and flips the normal velocity; the
+    mass and energy fluxes change sign.  A stationary contact gives zero mass
+    and energy flux and momentum flux p exactly (Sec. 3.1.2)."""
+    g = 5.0 / 3.0
+    rng = np.random.Generator(np.random.Philox(9))
+    for _ in range(300):
+        wL = [0.3 + rng.random(), *rng.standard_normal(3), 0.3 + rng.random()]
+        wR = [0.3 + rng.random(), *rng.standard_normal(3), 0.3 + rng.random()]
+        F = O.hllc(wL, wR, 0, g)
+        mL = [wR[0], -wR[1], wR[2], wR[3], wR[4]]
+        mR = [wL[0], -wL[1], wL[2], wL[3], wL[4]]
+        Fm = O.hllc(mL, mR, 0, g)
+        np.testing.assert_allclose([-Fm[0], Fm[1], -Fm[2], -Fm[3], -Fm[4]], F, rtol=1e-12,
+                                   atol=1e-12)
+    F = O.hllc([1.4, 0, 0, 0, 1.0], [1.0, 0, 0, 0, 1.0], 0, 1.4)
+    assert F[0] == 0.0 and F[1] == 1.0 and F[2] == 0.0 and F[3] == 0.0 and F[4] == 0.0
+
+
+# ------------------------------------------------------- whole stages -----
+
+def test_uniform_state_unchanged_exactly():
+    """A uniform state (any uniform velocity) is a fixed point bit for bit."""
+    lay = I.single_box(8, 8, 8, ng=4)
+    U = I.zeros(lay, 5)
+    g = 5.0 / 3.0
+    rho, v, p = 1.3, np.array([0.2, -0.1, 0.05]), 0.7
+    for a, val in zip(U, [rho, *(rho * v), p / (g - 1) + 0.5 * rho * (v ** 2).sum()]):
+        lay.interior(a, 0)[...] = val
+    U0 = [a.copy() for a in U]
+    p_ = O.make_params(gamma=g, cfl=0.3, dx=1 / 8, hydro_only=1)
+    advance_to(lay, p_, U, 0.05)
+    for a, b in zip(U, U0):
+        assert np.array_equal(lay.interior(a, 0), lay.interior(b, 0))
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_stationary_contact_exactly_zero(axis):
+    """Sec. 3.1.2: rho_L = 1.4, rho_R = 1, p = 1, v = 0, gamma = 1.4, to t = 2:
+    the error is exactly zero."""
+    gold = json.load(open(os.path.join(GOLD, "paper_values.json")))["stationary_contact"]
+    N = 32
+    x = P.centres(N)
+    rho = np.where(x < 0.5, 1.4, 1.0)
+    lay, U = P.hydro_line(N, rho, 0.0, 1.0, 1.4, axis=axis)
+    U0 = [a.copy() for a in U]
+    p = O.make_params(gamma=1.4, cfl=0.3, dx=1.0 / N, hydro_only=1)
+    advance_to(lay, p, U, gold["t_end"])
+    err = max(np.abs(P.get_line(lay, a, axis) - P.get_line(lay, b, axis)).max() for a, b in zip(U, U0))
+    assert err == gold["error"] == 0.0
+
+
+def test_one_dimensional_problem_same_along_each_axis():
+    """A 1-D problem run along x, y or z gives identical results (the per
+    direction operators differ only by the axis permutation)."""
+    N = 48
+    x = P.centres(N)
+    rho = 1.0 + 0.5 * (x > 0.5) + 0.1 * np.sin(2 * np.pi * x)
+    u = 0.3 * np.cos(2 * np.pi * x)
+    pr = 1.0 + 0.2 * np.sin(4 * np.pi * x)
+    res = []
+    for axis in range(3):
+        lay, U = P.hydro_line(N, rho, u, pr, 5 / 3, axis=axis)
+        p = O.make_params(gamma=5 / 3, cfl=0.3, dx=1.0 / N, hydro_only=1)
+        advance_to(lay, p, U, 0.1)
+        res.append([P.get_line(lay, U[0], axis), P.get_line(lay, U[1 + axis], axis),
+                    P.get_line(lay, U[4], axis)])
+    for r in res[1:]:
+        for a, b in zip(res[0], r):
+            assert np.array_equal(a, b)
+
+
+def test_xy_transpose_symmetry_exact():
+    """Sec. 3.1.10 (Liska-Wendroff implosion): x<->y symmetry must hold
+    exactly; transposed initial data give the transposed result bit for bit."""
+    lay, U, g = P.random_hydro_3d((8, 8, 6), seed=21)
+    T = I.zeros(lay, 5)
+    for dst, src in zip([0, 2, 1, 3, 4], [0, 1, 2, 3, 4]):
+        lay.interior(T[dst], 0)[...] = np.swapaxes(lay.interior(U[src], 0), 1, 2)
+    p = O.make_params(gamma=g, cfl=0.3, dx=1.0 / 8, hydro_only=1)
+    for _ in range(3):
+        for S in (U, T):
+            gr = _grid(lay)
+            dt = 0.002
+            S1 = [np.zeros_like(a) for a in S]
+            O.hydro_stage(gr, p, 1, S, None, S1, dt)
+            O.hydro_stage(gr, p, 2, S, S1, S, dt)
+    for dst, src in zip([0, 2, 1, 3, 4], [0, 1, 2, 3, 4]):
+        assert np.array_equal(lay.interior(T[dst], 0), np.swapaxes(lay.interior(U[src], 0), 1, 2))
+
+
+def test_periodic_conservation_roundoff():
+    """Periodic boundaries: the flux form conserves mass, momentum and
+    energy to round-off (the design intent of Sec. 2.2 and Sec. 2.2.4)."""
+    lay, U, g = P.random_hydro_3d((12, 10, 8), seed=4)
+    p = O.make_params(gamma=g, cfl=0.3, dx=1.0 / 12, hydro_only=1)
+    gr = _grid(lay)
+    s0 = O.conserved_sums(gr, p, U)
+    for _ in range(3):
+        rc, _, _ = O.step(gr, p, U)
+        assert rc == 0
+    s1 = O.conserved_sums(gr, p, U)
+    for v in (0, 4):
+        assert abs(s1[v] - s0[v]) <= 1e-14 * abs(s0[v])
+    for v in (1, 2, 3):
+        assert abs(s1[v] - s0[v]) <= 1e-14 * abs(s0[4])
+
+
+def test_sound_wave_convergence_matches_paper():
+    """Sec. 3.1.1: linear sound wave, gamma = 5/3, A = 1e-6, R = (1,-1,1,1,1.5),
+    P0 = 1/gamma, CFL 0.1, one period.  Errors (eq. convergence_error, rms
+    over components) of order 1.0e-7 at N = 16 and 1.6e-9 at N = 128, slope
+    close to -2 (golden values printed in the paper)."""
+    gold = json.load(open(os.path.join(GOLD, "paper_values.json")))["sound_wave"]
+    g = 5.0 / 3.0
+    A = gold["amplitude"]
+    Rv = np.array(gold["eigenvector"])
+    errs = {}
+    for N in (16, 32, 64, 128):
+        x = P.centres(N)
+        lay = P.line_layout(N, 0)
+        U = I.zeros(lay, 5)
+        base = np.array([1.0, 0.0, 0.0, 0.0, (1.0 / g) / (g - 1.0)])
+        for k in range(5):
+            P.set_line(lay, U[k], base[k] + A * Rv[k] * np.sin(2 * np.pi * x), 0)
+        U0 = [a.copy() for a in U]
+        p = O.make_params(gamma=g, cfl=gold["cfl"], dx=1.0 / N, hydro_only=1)
+        advance_to(lay, p, U, 1.0)
+        dU = [np.abs(P.get_line(lay, a, 0) - P.get_line(lay, b, 0)).mean() for a, b in zip(U, U0)]
+        errs[N] = math.sqrt(np.mean(np.square(dU)))
+    slope = math.log(errs[128] / errs[16]) / math.log(8)
+    assert -2.4 < slope < -1.7, (errs, slope)
+    for N, ref in gold["errors"].items():
+        N = int(N)
+        if N in errs:
+            assert ref / 4 < errs[N] < ref * 4, (N, errs[N], ref)
+
+
+def test_exact_riemann_solver_textbook_values():
+    """Pin the exact Riemann solver itself on Toro (2009) Table 4.2."""
+    tab = json.load(open(os.path.join(GOLD, "toro_exact_riemann.json")))
+    for case in tab["cases"]:
+        p, u, rl, rr = ER.star_densities(case["WL"], case["WR"], tab["gamma"])
+        for got, ref in zip((p, u, rl, rr), (case["p"], case["u"], case["rhoL"], case["rhoR"])):
+            assert abs(got - ref) <= 6e-5 * max(1.0, abs(ref)), (case, got, ref)
+
+
+def _double_tube(N, WL, WR, L, x1, x2, g):
+    """Periodic [0, L): state WL on [x2-L.. x1) u (x2, L), WR on [x1, x2)."""
+    x = P.centres(N, L)
+    inside = (x >= x1) & (x < x2)
+    rho = np.where(inside, WR[0], WL[0])
+    u = np.where(inside, WR[1], WL[1])
+    pr = np.where(inside, WR[2], WL[2])
+    return x, P.hydro_line(N, rho, u, pr, g, axis=0)
+
+
+@pytest.mark.parametrize("case", ["sod", "stationary_tube"])
+def test_shock_tube_converges_to_exact_riemann(case):
+    """Sod (Toro test 1) and the stationary shock tube of Sec. 3.1.3
+    (rho/p = 10/100 | 1/1 at x0 = 2, gamma = 1.4, CFL 0.1, t = 0.4): the L1
+    error against the exact Riemann solution falls with resolution.  The
+    paper's 1.12e-3 uses shock flattening, which the plain method omits, so
+    it serves only as an order-of-magnitude bound."""
+    g = 1.4
+    if case == "sod":
+        WL, WR, L, x1, x2, t_end, cfl = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 2.0, 0.5, 1.5, 0.15, 0.3
+        window = (0.1, 0.9)
+        Ns = (100, 200, 400)
+    else:
+        WL, WR, L, x1, x2, t_end, cfl = (10.0, 0.0, 100.0), (1.0, 0.0, 1.0), 10.0, 2.0, 8.0, 0.4, 0.1
+        window = (0.5, 4.5)
+        Ns = (250, 500, 1000)
+    errs = []
+    for N in Ns:
+        x, (lay, U) = _double_tube(N, WL, WR, L, x1, x2, g)
+        p = O.make_params(gamma=g, cfl=cfl, dx=L / N, hydro_only=1)
+        advance_to(lay, p, U, t_end)
+        ex = ER.sample(WL, WR, g, (x - x1) / t_end)
+        sel = (x > window[0]) & (x < window[1])
+        rho = P.get_line(lay, U[0], 0)
+        mom = P.get_line(lay, U[1], 0)
+        E = P.get_line(lay, U[4], 0)
+        exU = [ex[:, 0], ex[:, 0] * ex[:, 1], ex[:, 2] / (g - 1) + 0.5 * ex[:, 0] * ex[:, 1] ** 2]
+        l1 = [np.abs(a[sel] - b[sel]).mean() for a, b in zip((rho, mom, E), exU)]
+        nrm = [np.abs(b[sel]).mean() for b in exU]
+        errs.append(math.sqrt(np.mean(np.square(l1))) / math.sqrt(np.mean(np.square(nrm))))
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[-1] < 3e-2, errs
+    assert math.log(errs[0] / errs[-1]) / math.log(Ns[-1] / Ns[0]) > 0.5, errs
+
+
+def test_timestep_rule():
+    """dt = CFL dx / max(|v| + c_s) (Sec. 2.2.1); the hydro step holds at most
+    N_sub,max radiation steps of CFL dx / chat (Sec. 2.2.4)."""
+    lay = I.single_box(4, 4, 4, ng=4)
+    U = I.zeros(lay, 5)
+    g = 5.0 / 3.0
+    rho, P0 = 2.0, 1.2
+    v = np.array([3.0, 0.0, 4.0])
+    for a, val in zip(U, [rho, *(rho * v), P0 / (g - 1) + 0.5 * rho * 25.0]):
+        lay.interior(a, 0)[...] = val
+    gr = _grid(lay)
+    smax = 5.0 + math.sqrt(g * P0 / rho)
+    p = O.make_params(gamma=g, cfl=0.3, dx=0.25, hydro_only=1)
+    assert abs(O.max_signal_speed(gr, p, U) - smax) < 1e-14 * smax
+    dt, nsub, _ = O.timestep(gr, p, U)
+    assert abs(dt - 0.3 * 0.25 / smax) < 1e-15 and nsub == 0
+    p = O.make_params(gamma=g, cfl=0.3, dx=0.25, chat=100.0, nsub_max=10, hydro_only=0)
+    dt, nsub, dtr = O.timestep(gr, p, U)
+    assert nsub == 10 and dt == 10 * (0.3 * 0.25 / 100.0) and dtr == dt / 10
+    p = O.make_params(gamma=g, cfl=0.3, dx=0.25, chat=3.5 * smax, nsub_max=10, hydro_only=0)
+    dt, nsub, dtr = O.timestep(gr, p, U)
+    assert nsub == 4 and abs(dt - 0.3 * 0.25 / smax) < 1e-16 and dtr == dt / 4
