@@ -1,0 +1,198 @@
+/*
+ * qk.h -- C ABI of the GB300 (sm_103a) per-cell uniform-patch
+ * radiation-hydrodynamics update of Wibking & Krumholz, "QUOKKA"
+ * (arXiv:2110.01792).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an int status: QK_OK (0) or one of the QK_E* codes.
+ *     A failing call leaves a message for qk_last_error().  No C++ exception
+ *     crosses this boundary.
+ *   - Field arguments are DEVICE pointers, one contiguous array per field.
+ *     All patches share each array: patch b starts at element boxes[b].offset
+ *     and holds (n_x+2g)(n_y+2g)(n_z+2g) cells, x fastest, the interior at
+ *     local cells [g, g+n) on each axis.  The element type is double for
+ *     QK_FP64 contexts and float for QK_FP32_MIXED contexts.  Hydro fields are
+ *     ordered (rho, m_x, m_y, m_z, E) (density, momentum, total gas energy
+ *     density); radiation fields (E_r, F_x, F_y, F_z).  The caller owns every
+ *     field buffer and stream; the library owns only its context, its
+ *     descriptor tables and its scratch (released by qk_destroy).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every launch is asynchronous on it unless stated otherwise.
+ *   - Calls on one context are not thread safe; use one context per thread.
+ */
+#ifndef QK_H
+#define QK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QK_OK 0
+#define QK_EINVAL 1     /* invalid argument                                  */
+#define QK_ECUDA 2      /* a CUDA runtime call failed                          */
+#define QK_ENOCONV 3    /* a Newton exchange exceeded max_iter (Sec. 2.2.3)   */
+#define QK_ENEGATIVE 4  /* a cell ended with E_g <= 0 or E_r <= 0            */
+
+#define QK_FP64 0        /* FP64 state and arithmetic                          */
+#define QK_FP32_MIXED 1  /* FP32 state and stencils; FP64 internal-energy
+                            recovery, Newton exchange and conservation sums   */
+
+#define QK_KAPPA_CONST 0 /* kappa_P, kappa_R are constant specific opacities  */
+#define QK_KAPPA_RHO 1   /* kappa = kappa0 * rho with kappa0 = kappa_P/kappa_R */
+
+#define QK_EOS_GAMMA 0   /* gamma-law gas, T = E_g / (rho c_v)                 */
+#define QK_EOS_ALPHA_T3 1 /* E_g = alpha T^4 / 4, i.e. C_v = alpha T^3
+                            (eq. heat_capacity; exchange test mode)           */
+
+#define QK_NSUMS 13
+
+typedef struct qk_ctx qk_ctx;
+
+/* Physical and numerical parameters (Sec. 2.1-2.2).  dx is the cell size on
+ * each axis; cfl is C0/D of Sec. 2.2.1 (the maximum stable value in 3-D is
+ * 1/3).  eps_newton and max_iter are the Newton tolerance and iteration limit
+ * of Sec. 2.2.3 (1e-10 and 400 in the paper); nsub_max is N_sub,max of
+ * Sec. 2.2.4 (10).  tau_correction enables the optical-depth correction of the
+ * radiation Riemann solver (Sec. 2.2.2).  hydro_only skips the radiation
+ * substeps in qk_step. */
+typedef struct {
+  double gamma;      /* adiabatic index                                        */
+  double cfl;        /* CFL number                                             */
+  double a_r;        /* radiation constant                                     */
+  double c;          /* speed of light                                         */
+  double chat;       /* reduced speed of light (RSLA), Sec. 2.1               */
+  double c_v;        /* specific heat at constant volume                       */
+  double kappa_P;    /* Planck mean opacity, or kappa0 (QK_KAPPA_RHO)          */
+  double kappa_R;    /* Rosseland mean opacity, or kappa0 (QK_KAPPA_RHO)       */
+  double alpha_eos;  /* alpha of QK_EOS_ALPHA_T3                               */
+  double eps_newton; /* Newton relative tolerance                              */
+  double dx[3];      /* cell size per axis                                     */
+  int32_t kappa_mode;
+  int32_t eos;
+  int32_t max_iter;
+  int32_t nsub_max;
+  int32_t tau_correction;
+  int32_t hydro_only;
+} qk_params;
+
+/* One patch: lower corner in the periodic domain, interior extents, and the
+ * element offset of its first (ghost) cell in every field array. */
+typedef struct {
+  int32_t lo[3];
+  int32_t n[3];
+  int64_t offset;
+} qk_box;
+
+/* Create a context for a set of patches that tile the periodic domain
+ * [0, domain_n) exactly once (Sec. 2.2, domain decomposition into boxes).
+ * Validates the boxes (inside the domain, no overlap, full cover, disjoint
+ * field ranges), builds the tile work list and the ghost-copy descriptors
+ * (periodic images included), uploads them, and allocates the scratch for
+ * qk_step (one extra copy of each field).  nghost >= 3 (the PPM stencil reach).
+ * precision is QK_FP64 or QK_FP32_MIXED.  Must be called with the target device
+ * current.  On failure *out is NULL and the status says why. */
+int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
+                    const int32_t domain_n[3], int32_t nghost, int32_t precision);
+
+/* Free the context and all library-owned device memory. */
+void qk_destroy(qk_ctx *ctx);
+
+/* Message of the last failing call on this context (never NULL); with
+ * ctx == NULL, the message of the last failed qk_init_patches on this thread. */
+const char *qk_last_error(const qk_ctx *ctx);
+
+/* Minimum number of elements of each field array (max over patches of
+ * offset + padded volume). */
+int64_t qk_field_len(const qk_ctx *ctx);
+
+/* Number of interior cells over all patches. */
+int64_t qk_num_cells(const qk_ctx *ctx);
+
+/* Replace the parameters (same patch set).  Captured step graphs are dropped. */
+int qk_set_params(qk_ctx *ctx, const qk_params *p);
+
+/* Fill the ghost cells of `nfields` field arrays (Sec. 2.2, 'FillBoundary'):
+ * every ghost cell of every patch receives the value of the interior cell that
+ * owns its periodic image.  One batched launch over precomputed copy
+ * descriptors. */
+int qk_fill_ghosts(qk_ctx *ctx, void *const *fields, int32_t nfields, void *stream);
+
+/* One RK2-SSP stage of the hydro update (Sec. 2.2.1): conserved -> primitive,
+ * PPM reconstruction of (rho, v, P) per direction, HLLC fluxes with PVRS
+ * wavespeeds, flux divergence, and
+ *   stage 1: Uout = U0 + dt L(U0)
+ *   stage 2: Uout = U0/2 + (U1 + dt L(U1))/2.
+ * The stencil source (U0 in stage 1, U1 in stage 2) must have its ghosts
+ * filled.  Uout may equal U0 in stage 2 (in place), never the stencil source.
+ * U1 is ignored in stage 1.  Face fluxes never leave the chip. */
+int qk_hydro_stage(qk_ctx *ctx, int32_t stage, void *const U0[5], void *const U1[5],
+                   void *const Uout[5], double dt, void *stream);
+
+/* One RK2-SSP stage of the radiation transport (Sec. 2.2.2): PPM of E_r and
+ * the reduced flux f = F/(c E_r), first-order fallback at faces where a state
+ * has |f| > 1, Levermore closure (eq. M1_closure), HLL flux with wavespeeds from
+ * the cell-average Eddington factors and the optical-depth correction, RSLA
+ * fluxes ((chat/c) F, c chat P_r) (eqs. rad_energy, rad_flux).  rho (the hydro
+ * density field, ghosts filled) sets the optical depth.  Same stage and alias
+ * rules as qk_hydro_stage. */
+int qk_rad_stage(qk_ctx *ctx, int32_t stage, void *const R0[4], void *const R1[4],
+                 void *const Rout[4], const void *rho, double dt_rad, void *stream);
+
+/* Per-cell implicit matter-radiation exchange over dt_rad (Sec. 2.2.3), in
+ * FP64 for both precisions: Newton-Raphson on (E_g, E_r) with the residuals
+ * F_G, F_R and eqs. delta_er / delta_eg, the backward-Euler flux source
+ * F <- F/(1 + rho kappa_R chat dt), the momentum update m -= dF/(c chat), and
+ * the work term through the kinetic-energy change.  Updates hydro (m, E) and
+ * rad (E_r, F) in place.  A cell that does not converge within max_iter sets
+ * QK_ENOCONV in the context status (see qk_status); the kernel never traps
+ * and always ends. */
+int qk_rad_matter_exchange(qk_ctx *ctx, void *const hydro[5], void *const rad[4],
+                           double dt_rad, void *stream);
+
+/* Device-side timestep (Sec. 2.2.1, Sec. 2.2.4) of the current hydro state:
+ * dt = CFL dx_min / max(|v| + c_s); with radiation, at most N_sub,max substeps
+ * of CFL dx_min / chat, N_sub = ceil(dt / (CFL dx_min / chat)) otherwise,
+ * dt_rad = dt / N_sub.  Synchronises `stream` and returns
+ * out[0] = dt, out[1] = N_sub, out[2] = dt_rad, out[3] = max(|v| + c_s). */
+int qk_timestep(qk_ctx *ctx, void *const hydro[5], double out[4], void *stream);
+
+/* One full update (operator split, Sec. 2.2): timestep on the device, ghost
+ * fill + hydro stage 1, ghost fill + hydro stage 2, then N_sub radiation
+ * substeps, each: ghost fill + radiation stage 1, ghost fill + radiation
+ * stage 2, exchange.  rad == NULL (or hydro_only) runs hydro alone.  The
+ * launch sequence is captured once into a CUDA graph per (hydro, rad) pointer
+ * set and replayed (N_sub,max predicated substeps; those beyond N_sub exit at
+ * once).  dt_out / nsub_out, when not NULL, receive dt and N_sub of this step
+ * by an asynchronous copy: valid after `stream` synchronises (use pinned host
+ * memory to keep the call asynchronous). */
+int qk_step(qk_ctx *ctx, void *const hydro[5], void *const rad[4], double *dt_out,
+            int32_t *nsub_out, void *stream);
+
+/* Enable (1, default) or disable (0) CUDA-graph capture in qk_step. */
+int qk_set_graph(qk_ctx *ctx, int32_t enable);
+
+/* Conservation sums over the interior cells times the cell volume, in
+ * compensated FP64 with a fixed reduction order (bitwise reproducible):
+ * out[0] = sum rho, out[1..3] = sum m, out[4] = sum E, out[5] = sum E_r,
+ * out[6..8] = sum F, out[9] = sum (E + (c/chat) E_r),
+ * out[10..12] = sum (m + F/(c chat)) (the quantities that the RSLA system
+ * conserves, Sec. 3.2.3).  rad may be NULL (radiation entries are then 0).
+ * Synchronises `stream`. */
+int qk_conserved_sums(qk_ctx *ctx, void *const hydro[5], void *const rad[4],
+                      double out[QK_NSUMS], void *stream);
+
+/* Read the accumulated exchange status (synchronises `stream`):
+ * *flags = bit (1 << QK_ENOCONV) | bit (1 << QK_ENEGATIVE); *first_bad = the
+ * smallest element index of a failing cell (-1 if none); *max_iter = the
+ * largest Newton iteration count seen.  reset != 0 clears the status.
+ * Returns QK_ENOCONV / QK_ENEGATIVE when those bits are set, else QK_OK. */
+int qk_status(qk_ctx *ctx, uint32_t *flags, int64_t *first_bad, int32_t *max_iter,
+              int32_t reset, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QK_H */

@@ -1,0 +1,607 @@
+// qk_api.cu -- host side of libqk: the C ABI of include/qk.h.  Validates the
+// patch set, builds the tile work list and the ghost-copy descriptors (with
+// periodic images), owns the scratch for qk_step and its CUDA graph, and
+// launches the stage kernels.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qk_internal.cuh"
+
+using namespace qk;
+
+struct qk_ctx {
+  qk_params p{};
+  int fp32 = 0;
+  int ng = 0;
+  int nbox = 0;
+  int dom[3] = {0, 0, 0};
+  std::vector<qk_box> boxes;
+  int64_t field_len = 0;
+  int64_t ncells = 0;
+  // device tables
+  DevBox *d_boxes = nullptr;
+  Tile *d_tiles = nullptr;
+  long long *d_cell0 = nullptr;
+  int ntiles = 0;
+  Copy *d_copies = nullptr;
+  Chunk *d_chunks = nullptr;
+  int ncopies = 0, nchunks = 0;
+  StepInfo *d_si = nullptr;
+  Status *d_status = nullptr;
+  double *d_partials = nullptr;
+  double *d_sums = nullptr;
+  int sum_blocks = 0;
+  void *scratch[9] = {};
+  size_t elem = 8;
+  // pinned host staging
+  double *h_buf = nullptr;
+  // step graph
+  int use_graph = 1;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  void *gkey[10] = {};
+  std::string err;
+};
+
+static thread_local std::string g_init_err = "qk: null context";
+
+static int fail(qk_ctx *c, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+static int cuda_fail(qk_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, QK_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define QK_CUDA(ctx, call)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+static Geometry geom(const qk_ctx *c) {
+  Geometry g;
+  g.boxes = c->d_boxes;
+  g.tiles = c->d_tiles;
+  g.ntiles = c->ntiles;
+  g.nbox = c->nbox;
+  g.ng = c->ng;
+  g.ncells = c->ncells;
+  g.box_cell0 = c->d_cell0;
+  return g;
+}
+
+static int check_params(qk_ctx *c, const qk_params *p) {
+  if (!p) return fail(c, QK_EINVAL, "params is NULL");
+  if (!(p->gamma > 1.0)) return fail(c, QK_EINVAL, "gamma must exceed 1");
+  if (!(p->cfl > 0.0)) return fail(c, QK_EINVAL, "cfl must be positive");
+  for (int d = 0; d < 3; ++d)
+    if (!(p->dx[d] > 0.0)) return fail(c, QK_EINVAL, "dx must be positive");
+  if (!p->hydro_only) {
+    if (!(p->c > 0.0) || !(p->chat > 0.0)) return fail(c, QK_EINVAL, "c and chat must be positive");
+    if (p->max_iter < 1) return fail(c, QK_EINVAL, "max_iter must be >= 1");
+    if (p->nsub_max < 1) return fail(c, QK_EINVAL, "nsub_max must be >= 1");
+    if (p->eos == QK_EOS_ALPHA_T3 && !(p->alpha_eos > 0.0))
+      return fail(c, QK_EINVAL, "alpha_eos must be positive");
+    if (p->eos == QK_EOS_GAMMA && !(p->c_v > 0.0)) return fail(c, QK_EINVAL, "c_v must be positive");
+  }
+  if (p->kappa_mode != QK_KAPPA_CONST && p->kappa_mode != QK_KAPPA_RHO)
+    return fail(c, QK_EINVAL, "unknown kappa_mode %d", p->kappa_mode);
+  if (p->eos != QK_EOS_GAMMA && p->eos != QK_EOS_ALPHA_T3)
+    return fail(c, QK_EINVAL, "unknown eos %d", p->eos);
+  return QK_OK;
+}
+
+static int64_t padded_vol(const qk_box &b, int ng) {
+  return (int64_t)(b.n[0] + 2 * ng) * (b.n[1] + 2 * ng) * (b.n[2] + 2 * ng);
+}
+
+// Ghost-copy descriptors: for each patch, the 26 ghost sub-boxes around its
+// interior, intersected with every patch's interior under every periodic
+// shift that reaches them.  A binned index of the patches keeps this linear.
+static int build_copies(qk_ctx *c, std::vector<Copy> &out) {
+  const int ng = c->ng;
+  const int *D = c->dom;
+  const int BIN = 16;
+  int nb[3];
+  for (int d = 0; d < 3; ++d) nb[d] = (D[d] + BIN - 1) / BIN;
+  std::vector<std::vector<int>> bins((size_t)nb[0] * nb[1] * nb[2]);
+  for (int b = 0; b < c->nbox; ++b) {
+    const qk_box &q = c->boxes[b];
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = q.lo[d] / BIN;
+      hi[d] = (q.lo[d] + q.n[d] - 1) / BIN;
+    }
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) bins[((size_t)z * nb[1] + y) * nb[0] + x].push_back(b);
+  }
+  std::vector<int> stamp(c->nbox, -1);
+  int stamp_id = 0;
+  for (int b = 0; b < c->nbox; ++b) {
+    const qk_box &B = c->boxes[b];
+    const int sx = B.n[0] + 2 * ng, sy = B.n[1] + 2 * ng;
+    for (int rz = 0; rz < 3; ++rz)
+      for (int ry = 0; ry < 3; ++ry)
+        for (int rx = 0; rx < 3; ++rx) {
+          if (rx == 1 && ry == 1 && rz == 1) continue;
+          int r0[3], r1[3];  // region in global (unwrapped) coordinates
+          const int rs[3] = {rx, ry, rz};
+          for (int d = 0; d < 3; ++d) {
+            if (rs[d] == 0) { r0[d] = B.lo[d] - ng; r1[d] = B.lo[d]; }
+            else if (rs[d] == 1) { r0[d] = B.lo[d]; r1[d] = B.lo[d] + B.n[d]; }
+            else { r0[d] = B.lo[d] + B.n[d]; r1[d] = B.lo[d] + B.n[d] + ng; }
+          }
+          int a0[3], a1[3];
+          for (int d = 0; d < 3; ++d) {
+            auto fdiv = [](int a, int m) { return a >= 0 ? a / m : -((-a + m - 1) / m); };
+            a0[d] = fdiv(r0[d], D[d]);
+            a1[d] = fdiv(r1[d] - 1, D[d]);
+          }
+          for (int az = a0[2]; az <= a1[2]; ++az)
+            for (int ay = a0[1]; ay <= a1[1]; ++ay)
+              for (int ax = a0[0]; ax <= a1[0]; ++ax) {
+                const int sh[3] = {ax * D[0], ay * D[1], az * D[2]};
+                int w0[3], w1[3];  // region shifted into the domain, clipped
+                bool empty = false;
+                for (int d = 0; d < 3; ++d) {
+                  w0[d] = std::max(r0[d] - sh[d], 0);
+                  w1[d] = std::min(r1[d] - sh[d], D[d]);
+                  if (w0[d] >= w1[d]) empty = true;
+                }
+                if (empty) continue;
+                ++stamp_id;
+                for (int z = w0[2] / BIN; z <= (w1[2] - 1) / BIN; ++z)
+                  for (int y = w0[1] / BIN; y <= (w1[1] - 1) / BIN; ++y)
+                    for (int x = w0[0] / BIN; x <= (w1[0] - 1) / BIN; ++x)
+                      for (int q : bins[((size_t)z * nb[1] + y) * nb[0] + x]) {
+                        if (stamp[q] == stamp_id) continue;
+                        stamp[q] = stamp_id;
+                        const qk_box &Q = c->boxes[q];
+                        int i0[3], i1[3];
+                        bool none = false;
+                        for (int d = 0; d < 3; ++d) {
+                          i0[d] = std::max(w0[d], Q.lo[d]);
+                          i1[d] = std::min(w1[d], Q.lo[d] + Q.n[d]);
+                          if (i0[d] >= i1[d]) none = true;
+                        }
+                        if (none) continue;
+                        Copy cp;
+                        const int qsx = Q.n[0] + 2 * ng, qsy = Q.n[1] + 2 * ng;
+                        // destination: local (i0 + shift - B.lo) in patch b
+                        long long dl[3], sl[3];
+                        for (int d = 0; d < 3; ++d) {
+                          dl[d] = (long long)i0[d] + sh[d] - B.lo[d] + ng;
+                          sl[d] = (long long)i0[d] - Q.lo[d] + ng;
+                        }
+                        cp.dst = B.offset + (dl[2] * sy + dl[1]) * sx + dl[0];
+                        cp.src = Q.offset + (sl[2] * qsy + sl[1]) * qsx + sl[0];
+                        cp.ex = i1[0] - i0[0];
+                        cp.ey = i1[1] - i0[1];
+                        cp.ez = i1[2] - i0[2];
+                        cp.dsx = sx;
+                        cp.dsy = sy;
+                        cp.ssx = qsx;
+                        cp.ssy = qsy;
+                        out.push_back(cp);
+                      }
+              }
+        }
+  }
+  return QK_OK;
+}
+
+static int validate_boxes(qk_ctx *c) {
+  const int ng = c->ng;
+  int64_t dvol = (int64_t)c->dom[0] * c->dom[1] * c->dom[2];
+  int64_t tot = 0;
+  for (int b = 0; b < c->nbox; ++b) {
+    const qk_box &q = c->boxes[b];
+    for (int d = 0; d < 3; ++d) {
+      if (q.n[d] < 1) return fail(c, QK_EINVAL, "box %d: empty extent", b);
+      if (q.lo[d] < 0 || q.lo[d] + q.n[d] > c->dom[d])
+        return fail(c, QK_EINVAL, "box %d lies outside the domain", b);
+    }
+    if (q.offset < 0) return fail(c, QK_EINVAL, "box %d: negative offset", b);
+    tot += (int64_t)q.n[0] * q.n[1] * q.n[2];
+  }
+  if (tot != dvol)
+    return fail(c, QK_EINVAL, "boxes cover %lld cells, the domain has %lld", (long long)tot,
+                (long long)dvol);
+  // pairwise overlap (sweep on x)
+  std::vector<int> order(c->nbox);
+  for (int b = 0; b < c->nbox; ++b) order[b] = b;
+  std::sort(order.begin(), order.end(),
+            [&](int a, int b) { return c->boxes[a].lo[0] < c->boxes[b].lo[0]; });
+  for (size_t a = 0; a < order.size(); ++a) {
+    const qk_box &A = c->boxes[order[a]];
+    for (size_t b = a + 1; b < order.size(); ++b) {
+      const qk_box &B = c->boxes[order[b]];
+      if (B.lo[0] >= A.lo[0] + A.n[0]) break;
+      bool ov = true;
+      for (int d = 0; d < 3; ++d)
+        if (B.lo[d] >= A.lo[d] + A.n[d] || A.lo[d] >= B.lo[d] + B.n[d]) ov = false;
+      if (ov) return fail(c, QK_EINVAL, "boxes %d and %d overlap", order[a], order[b]);
+    }
+  }
+  // disjoint field ranges
+  std::vector<int> byoff(c->nbox);
+  for (int b = 0; b < c->nbox; ++b) byoff[b] = b;
+  std::sort(byoff.begin(), byoff.end(),
+            [&](int a, int b) { return c->boxes[a].offset < c->boxes[b].offset; });
+  int64_t end = 0;
+  for (int b : byoff) {
+    const qk_box &q = c->boxes[b];
+    if (q.offset < end) return fail(c, QK_EINVAL, "box %d: field range overlaps another box", b);
+    end = q.offset + padded_vol(q, ng);
+  }
+  c->field_len = end;
+  c->ncells = tot;
+  return QK_OK;
+}
+
+template <typename T> static int upload(qk_ctx *c, T **dst, const std::vector<T> &v) {
+  size_t n = std::max<size_t>(v.size(), 1) * sizeof(T);
+  QK_CUDA(c, cudaMalloc((void **)dst, n));
+  if (!v.empty()) QK_CUDA(c, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return QK_OK;
+}
+
+static void release(qk_ctx *c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  cudaFree(c->d_boxes);
+  cudaFree(c->d_tiles);
+  cudaFree(c->d_cell0);
+  cudaFree(c->d_copies);
+  cudaFree(c->d_chunks);
+  cudaFree(c->d_si);
+  cudaFree(c->d_status);
+  cudaFree(c->d_partials);
+  cudaFree(c->d_sums);
+  for (void *s : c->scratch) cudaFree(s);
+  if (c->h_buf) cudaFreeHost(c->h_buf);
+}
+
+extern "C" {
+
+int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
+                    const int32_t domain_n[3], int32_t nghost, int32_t precision) {
+  if (!out) return QK_EINVAL;
+  *out = nullptr;
+  qk_ctx *c = new qk_ctx();
+  auto bail = [&](int rc) {
+    g_init_err = c->err.empty() ? std::string("qk_init_patches failed") : c->err;
+    release(c);
+    delete c;
+    return rc;
+  };
+  int rc = check_params(c, p);
+  if (rc) return bail(rc);
+  if (!boxes || nbox < 1 || !domain_n) return bail(fail(c, QK_EINVAL, "no boxes"));
+  if (nghost < HALO || nghost > 16) return bail(fail(c, QK_EINVAL, "nghost must be in [3, 16]"));
+  if (precision != QK_FP64 && precision != QK_FP32_MIXED)
+    return bail(fail(c, QK_EINVAL, "unknown precision"));
+  for (int d = 0; d < 3; ++d)
+    if (domain_n[d] < 1) return bail(fail(c, QK_EINVAL, "empty domain"));
+  c->p = *p;
+  c->fp32 = precision == QK_FP32_MIXED;
+  c->elem = c->fp32 ? 4 : 8;
+  c->ng = nghost;
+  c->nbox = nbox;
+  for (int d = 0; d < 3; ++d) c->dom[d] = domain_n[d];
+  c->boxes.assign(boxes, boxes + nbox);
+  if ((rc = validate_boxes(c))) return bail(rc);
+
+  // device boxes and the interior-cell prefix
+  std::vector<DevBox> db(nbox);
+  std::vector<long long> cell0(nbox + 1, 0);
+  for (int b = 0; b < nbox; ++b) {
+    const qk_box &q = boxes[b];
+    for (int d = 0; d < 3; ++d) {
+      db[b].lo[d] = q.lo[d];
+      db[b].n[d] = q.n[d];
+    }
+    db[b].sx = q.n[0] + 2 * nghost;
+    db[b].sy = q.n[1] + 2 * nghost;
+    db[b].off = q.offset;
+    db[b].cell0 = cell0[b];
+    cell0[b + 1] = cell0[b] + (long long)q.n[0] * q.n[1] * q.n[2];
+  }
+  std::vector<Tile> tiles;
+  for (int b = 0; b < nbox; ++b)
+    for (int z = 0; z < boxes[b].n[2]; z += TS)
+      for (int y = 0; y < boxes[b].n[1]; y += TS)
+        for (int x = 0; x < boxes[b].n[0]; x += TS) tiles.push_back(Tile{b, x, y, z});
+  c->ntiles = (int)tiles.size();
+  std::vector<Copy> copies;
+  build_copies(c, copies);
+  std::vector<Chunk> chunks;
+  for (int i = 0; i < (int)copies.size(); ++i) {
+    int n = copies[i].ex * copies[i].ey * copies[i].ez;
+    for (int s = 0; s < n; s += CHUNK_CELLS) chunks.push_back(Chunk{i, s});
+  }
+  c->ncopies = (int)copies.size();
+  c->nchunks = (int)chunks.size();
+
+  if ((rc = upload(c, &c->d_boxes, db))) return bail(rc);
+  if ((rc = upload(c, &c->d_tiles, tiles))) return bail(rc);
+  if ((rc = upload(c, &c->d_cell0, cell0))) return bail(rc);
+  if ((rc = upload(c, &c->d_copies, copies))) return bail(rc);
+  if ((rc = upload(c, &c->d_chunks, chunks))) return bail(rc);
+  cudaError_t e;
+  if ((e = cudaMalloc((void **)&c->d_si, sizeof(StepInfo))) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMalloc(step info)"));
+  if ((e = cudaMemset(c->d_si, 0, sizeof(StepInfo))) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMemset"));
+  if ((e = cudaMalloc((void **)&c->d_status, sizeof(Status))) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMalloc(status)"));
+  Status st0{0u, 0, ~0ull, 0ull};
+  if ((e = cudaMemcpy(c->d_status, &st0, sizeof(st0), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMemcpy(status)"));
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  c->sum_blocks = std::max(1, nsm * 2);
+  if ((e = cudaMalloc((void **)&c->d_partials, sizeof(double) * 2 * QK_NSUMS * c->sum_blocks)) !=
+      cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMalloc(partials)"));
+  if ((e = cudaMalloc((void **)&c->d_sums, sizeof(double) * QK_NSUMS)) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMalloc(sums)"));
+  for (int f = 0; f < 9; ++f)
+    if ((e = cudaMalloc(&c->scratch[f], (size_t)c->field_len * c->elem)) != cudaSuccess)
+      return bail(cuda_fail(c, e, "cudaMalloc(scratch field)"));
+  if ((e = cudaMallocHost((void **)&c->h_buf, 64 * sizeof(double))) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMallocHost"));
+  if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaStreamCreate"));
+  *out = c;
+  return QK_OK;
+}
+
+void qk_destroy(qk_ctx *c) {
+  if (!c) return;
+  release(c);
+  delete c;
+}
+
+const char *qk_last_error(const qk_ctx *c) {
+  if (!c) return g_init_err.c_str();
+  return c->err.c_str();
+}
+
+int64_t qk_field_len(const qk_ctx *c) { return c ? c->field_len : -1; }
+int64_t qk_num_cells(const qk_ctx *c) { return c ? c->ncells : -1; }
+
+int qk_set_params(qk_ctx *c, const qk_params *p) {
+  if (!c) return QK_EINVAL;
+  int rc = check_params(c, p);
+  if (rc) return rc;
+  c->p = *p;
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  return QK_OK;
+}
+
+int qk_set_graph(qk_ctx *c, int32_t enable) {
+  if (!c) return QK_EINVAL;
+  c->use_graph = enable ? 1 : 0;
+  return QK_OK;
+}
+
+static int check_fields(qk_ctx *c, void *const *f, int n, const char *what) {
+  if (!f) return fail(c, QK_EINVAL, "%s is NULL", what);
+  for (int i = 0; i < n; ++i)
+    if (!f[i]) return fail(c, QK_EINVAL, "%s[%d] is NULL", what, i);
+  return QK_OK;
+}
+
+int qk_fill_ghosts(qk_ctx *c, void *const *fields, int32_t nfields, void *stream) {
+  if (!c) return QK_EINVAL;
+  if (nfields < 0 || nfields > 9) return fail(c, QK_EINVAL, "nfields must be in [0, 9]");
+  int rc = check_fields(c, fields, nfields, "fields");
+  if (rc) return rc;
+  DtSrc pred{nullptr, 0.0, 0, -1};
+  QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, fields, nfields,
+                               pred, (cudaStream_t)stream));
+  return QK_OK;
+}
+
+int qk_hydro_stage(qk_ctx *c, int32_t stage, void *const U0[5], void *const U1[5],
+                   void *const Uout[5], double dt, void *stream) {
+  if (!c) return QK_EINVAL;
+  if (stage != 1 && stage != 2) return fail(c, QK_EINVAL, "stage must be 1 or 2");
+  int rc = check_fields(c, U0, 5, "U0");
+  if (!rc && stage == 2) rc = check_fields(c, U1, 5, "U1");
+  if (!rc) rc = check_fields(c, Uout, 5, "Uout");
+  if (rc) return rc;
+  if (stage == 1)
+    for (int q = 0; q < 5; ++q)
+      if (Uout[q] == U0[q]) return fail(c, QK_EINVAL, "stage 1 cannot update in place");
+  if (stage == 2)
+    for (int q = 0; q < 5; ++q)
+      if (Uout[q] == U1[q]) return fail(c, QK_EINVAL, "Uout must not alias U1");
+  DtSrc d{nullptr, dt, 0, -1};
+  QK_CUDA(c, launch_hydro_stage(c->fp32, stage, geom(c), c->p, U0, stage == 2 ? U1 : nullptr,
+                                Uout, d, 0, (cudaStream_t)stream));
+  return QK_OK;
+}
+
+int qk_rad_stage(qk_ctx *c, int32_t stage, void *const R0[4], void *const R1[4],
+                 void *const Rout[4], const void *rho, double dt_rad, void *stream) {
+  if (!c) return QK_EINVAL;
+  if (stage != 1 && stage != 2) return fail(c, QK_EINVAL, "stage must be 1 or 2");
+  int rc = check_fields(c, R0, 4, "R0");
+  if (!rc && stage == 2) rc = check_fields(c, R1, 4, "R1");
+  if (!rc) rc = check_fields(c, Rout, 4, "Rout");
+  if (rc) return rc;
+  if (!rho) return fail(c, QK_EINVAL, "rho is NULL");
+  if (stage == 1)
+    for (int q = 0; q < 4; ++q)
+      if (Rout[q] == R0[q]) return fail(c, QK_EINVAL, "stage 1 cannot update in place");
+  if (stage == 2)
+    for (int q = 0; q < 4; ++q)
+      if (Rout[q] == R1[q]) return fail(c, QK_EINVAL, "Rout must not alias R1");
+  DtSrc d{nullptr, dt_rad, 2, -1};
+  QK_CUDA(c, launch_rad_stage(c->fp32, stage, geom(c), c->p, R0, stage == 2 ? R1 : nullptr, Rout,
+                              rho, d, 0, (cudaStream_t)stream));
+  return QK_OK;
+}
+
+int qk_rad_matter_exchange(qk_ctx *c, void *const hydro[5], void *const rad[4], double dt_rad,
+                           void *stream) {
+  if (!c) return QK_EINVAL;
+  int rc = check_fields(c, hydro, 5, "hydro");
+  if (!rc) rc = check_fields(c, rad, 4, "rad");
+  if (rc) return rc;
+  DtSrc d{nullptr, dt_rad, 2, -1};
+  QK_CUDA(c, launch_exchange(c->fp32, geom(c), c->p, hydro, rad, d, c->d_status,
+                             (cudaStream_t)stream));
+  return QK_OK;
+}
+
+int qk_timestep(qk_ctx *c, void *const hydro[5], double out[4], void *stream) {
+  if (!c) return QK_EINVAL;
+  int rc = check_fields(c, hydro, 5, "hydro");
+  if (rc) return rc;
+  if (!out) return fail(c, QK_EINVAL, "out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  QK_CUDA(c, launch_max_speed(c->fp32, geom(c), c->p, hydro, c->d_si, s));
+  QK_CUDA(c, launch_timestep(c->p, c->d_si, s));
+  QK_CUDA(c, cudaMemcpyAsync(c->h_buf, c->d_si, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  QK_CUDA(c, cudaStreamSynchronize(s));
+  out[0] = c->h_buf[0];
+  out[1] = c->h_buf[1];
+  out[2] = c->h_buf[2];
+  out[3] = c->h_buf[3];
+  return QK_OK;
+}
+
+// The launch sequence of one full update (Sec. 2.2 operator split).
+static int enqueue_step(qk_ctx *c, void *const hydro[5], void *const rad[4], cudaStream_t s) {
+  const Geometry g = geom(c);
+  void *U1[5], *R1[4];
+  for (int q = 0; q < 5; ++q) U1[q] = c->scratch[q];
+  for (int q = 0; q < 4; ++q) R1[q] = c->scratch[5 + q];
+  const DtSrc dth{c->d_si, 0.0, 0, -1};
+  const DtSrc none{nullptr, 0.0, 0, -1};
+  QK_CUDA(c, launch_max_speed(c->fp32, g, c->p, hydro, c->d_si, s));
+  QK_CUDA(c, launch_timestep(c->p, c->d_si, s));
+  QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, hydro, 5, none, s));
+  QK_CUDA(c, launch_hydro_stage(c->fp32, 1, g, c->p, hydro, nullptr, U1, dth, 0, s));
+  QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, U1, 5, none, s));
+  QK_CUDA(c, launch_hydro_stage(c->fp32, 2, g, c->p, hydro, U1, hydro, dth, 0, s));
+  if (rad && !c->p.hydro_only) {
+    QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, hydro, 1, none, s));
+    for (int sub = 0; sub < c->p.nsub_max; ++sub) {
+      const DtSrc dr{c->d_si, 0.0, 2, sub};
+      QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, rad, 4, dr, s));
+      QK_CUDA(c, launch_rad_stage(c->fp32, 1, g, c->p, rad, nullptr, R1, hydro[0], dr, 0, s));
+      QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, R1, 4, dr, s));
+      QK_CUDA(c, launch_rad_stage(c->fp32, 2, g, c->p, rad, R1, rad, hydro[0], dr, 0, s));
+      QK_CUDA(c, launch_exchange(c->fp32, g, c->p, hydro, rad, dr, c->d_status, s));
+    }
+  }
+  return QK_OK;
+}
+
+int qk_step(qk_ctx *c, void *const hydro[5], void *const rad[4], double *dt_out, int32_t *nsub_out,
+            void *stream) {
+  if (!c) return QK_EINVAL;
+  int rc = check_fields(c, hydro, 5, "hydro");
+  if (rc) return rc;
+  if (rad && (rc = check_fields(c, rad, 4, "rad"))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->use_graph) {
+    void *key[10];
+    for (int q = 0; q < 5; ++q) key[q] = hydro[q];
+    for (int q = 0; q < 4; ++q) key[5 + q] = rad ? rad[q] : nullptr;
+    key[9] = (void *)(intptr_t)(rad ? 1 : 0);
+    if (!c->gexec || memcmp(key, c->gkey, sizeof(key)) != 0) {
+      if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+      }
+      // kernels see the caller's stream order through the graph launch; the
+      // capture itself runs on a private stream
+      QK_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue_step(c, hydro, rad, c->cap_stream);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+      if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&c->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+      memcpy(c->gkey, key, sizeof(key));
+    }
+    QK_CUDA(c, cudaGraphLaunch(c->gexec, s));
+  } else {
+    if ((rc = enqueue_step(c, hydro, rad, s))) return rc;
+  }
+  if (dt_out) QK_CUDA(c, cudaMemcpyAsync(dt_out, &c->d_si->dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (nsub_out) {
+    // N_sub is stored as a double on the device; convert on the host side
+    // through the pinned buffer only when asked, synchronously
+    QK_CUDA(c, cudaMemcpyAsync(c->h_buf + 8, &c->d_si->nsub, sizeof(double), cudaMemcpyDeviceToHost, s));
+    QK_CUDA(c, cudaStreamSynchronize(s));
+    *nsub_out = (int32_t)c->h_buf[8];
+  }
+  return QK_OK;
+}
+
+int qk_conserved_sums(qk_ctx *c, void *const hydro[5], void *const rad[4], double out[QK_NSUMS],
+                      void *stream) {
+  if (!c) return QK_EINVAL;
+  int rc = check_fields(c, hydro, 5, "hydro");
+  if (rc) return rc;
+  if (rad && (rc = check_fields(c, rad, 4, "rad"))) return rc;
+  if (!out) return fail(c, QK_EINVAL, "out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  QK_CUDA(c, launch_sums(c->fp32, geom(c), c->p, hydro, rad, c->d_partials, c->sum_blocks,
+                         c->d_sums, s));
+  QK_CUDA(c, cudaMemcpyAsync(c->h_buf, c->d_sums, QK_NSUMS * sizeof(double), cudaMemcpyDeviceToHost, s));
+  QK_CUDA(c, cudaStreamSynchronize(s));
+  memcpy(out, c->h_buf, QK_NSUMS * sizeof(double));
+  return QK_OK;
+}
+
+int qk_status(qk_ctx *c, uint32_t *flags, int64_t *first_bad, int32_t *max_iter, int32_t reset,
+              void *stream) {
+  if (!c) return QK_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Status *h = (Status *)(c->h_buf + 16);
+  QK_CUDA(c, cudaMemcpyAsync(h, c->d_status, sizeof(Status), cudaMemcpyDeviceToHost, s));
+  QK_CUDA(c, cudaStreamSynchronize(s));
+  Status st = *h;
+  if (flags) *flags = st.flags;
+  if (first_bad) *first_bad = st.first_bad == ~0ull ? -1 : (int64_t)st.first_bad;
+  if (max_iter) *max_iter = st.max_iter;
+  if (reset) {
+    Status st0{0u, 0, ~0ull, 0ull};
+    *h = st0;
+    QK_CUDA(c, cudaMemcpyAsync(c->d_status, h, sizeof(Status), cudaMemcpyHostToDevice, s));
+    QK_CUDA(c, cudaStreamSynchronize(s));
+  }
+  if (st.flags & (1u << QK_ENOCONV)) return fail(c, QK_ENOCONV, "Newton exchange did not converge");
+  if (st.flags & (1u << QK_ENEGATIVE)) return fail(c, QK_ENEGATIVE, "non-positive E_g or E_r");
+  return QK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,390 @@
+// qk_cell.cu -- per-cell kernels of the update (arXiv:2110.01792) for sm_103a:
+// the implicit matter-radiation exchange (Sec. 2.2.3), the CFL reduction and
+// timestep (Sec. 2.2.1, Sec. 2.2.4), the batched ghost fill, and the
+// compensated conservation sums.
+#include <algorithm>
+
+#include "qk_device.cuh"
+
+namespace qk {
+
+// ----------------------------------------------------------- cell lookup ---
+// Map a flat interior-cell index to (patch, element) with a binary search over
+// the per-patch prefix of interior cells.
+__device__ __forceinline__ long long cell_to_elem(const Geometry &g, long long c) {
+  int lo = 0, hi = g.nbox - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (g.box_cell0[mid] <= c) lo = mid; else hi = mid - 1;
+  }
+  const DevBox &b = g.boxes[lo];
+  long long r = c - g.box_cell0[lo];
+  int nx = b.n[0], ny = b.n[1];
+  int i = (int)(r % nx);
+  long long q = r / nx;
+  int j = (int)(q % ny);
+  int k = (int)(q / ny);
+  return cell_elem(b, g.ng, i, j, k);
+}
+
+// -------------------------------------------------------------- exchange ---
+template <typename T>
+__device__ __forceinline__ double load_d(const T *p, long long e) { return (double)p[e]; }
+
+// Newton-Raphson on (E_g, E_r) for one cell (Sec. 2.2.3, eqs. delta_er and
+// delta_eg), FP64.  R = dt rho kappa_P chat (a_r T^4 - E_r) (the '4 pi B' of
+// the paper read as chat a_r T^4), F_G = (E_g - E_g0) + (c/chat) R,
+// F_R = (E_r - E_r0) - R; convergence |F_G/E_tot| < eps and
+// |(c/chat) F_R / E_tot| < eps, E_tot = E_g0 + (c/chat) E_r0; the update of
+// the iterate that passes is applied, then the loop stops.  Returns the
+// iteration count, or -1 after max_iter iterations.
+__device__ __forceinline__ int newton_exchange(const qk_params &p, double rho, double Eg0,
+                                               double Er0, double dt, double &Eg_out,
+                                               double &Er_out) {
+  const double kP = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_P * rho : p.kappa_P;
+  const double cr = p.c / p.chat;
+  const double inv_Etot = 1.0 / (Eg0 + cr * Er0);
+  const double k = dt * rho * kP * p.chat;       // dt rho kappa_P chat
+  const double dFG_dEr = -p.c * dt * rho * kP;
+  const double dFR_dEr = 1.0 + k;
+  const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
+  const double inv_rcv = alpha_eos ? 0.0 : 1.0 / (rho * p.c_v);
+  const double dT4_alpha = alpha_eos ? 4.0 / p.alpha_eos : 0.0;
+  double Eg = Eg0, Er = Er0;
+  bool conv = false;
+  int it = 0;
+  for (it = 0; it < p.max_iter; ++it) {
+    double T4, dT4;
+    if (alpha_eos) {
+      T4 = dT4_alpha * Eg;
+      dT4 = dT4_alpha;
+    } else {
+      const double Tg = Eg * inv_rcv;
+      const double T2 = Tg * Tg;
+      T4 = T2 * T2;
+      dT4 = 4.0 * T2 * Tg * inv_rcv;
+    }
+    const double R = k * (p.a_r * T4 - Er);
+    const double FG = (Eg - Eg0) + cr * R;
+    const double FR = (Er - Er0) - R;
+    conv = fabs(FG * inv_Etot) < p.eps_newton && fabs(cr * FR * inv_Etot) < p.eps_newton;
+    const double dRdEg = k * p.a_r * dT4;
+    const double dFG_dEg = 1.0 + cr * dRdEg;
+    const double inv_G = 1.0 / dFG_dEg;
+    const double eta = dRdEg * inv_G;  // -(dF_R/dE_g)/(dF_G/dE_g), dF_R/dE_g = -dR/dE_g
+    const double dEr = -(FR + eta * FG) / (dFR_dEr + eta * dFG_dEr);
+    const double dEg = -(FG + dEr * dFG_dEr) * inv_G;
+    Er += dEr;
+    Eg += dEg;
+    if (conv) break;
+  }
+  Eg_out = Eg;
+  Er_out = Er;
+  return conv ? it + 1 : -1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, F5<T> U, F4<T> R,
+                                                        DtSrc dts, Status *st) {
+  if (skip_substep(dts)) return;
+  const double dt = dt_of(dts);
+  const double chat = p.chat, c = p.c;
+  int my_max = 0;
+  unsigned my_flags = 0;
+  unsigned long long my_bad = ~0ull;
+  for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < g.ncells;
+       cidx += (long long)gridDim.x * blockDim.x) {
+    const long long e = cell_to_elem(g, cidx);
+    const double rho = load_d(U.f[0], e);
+    double m[3] = {load_d(U.f[1], e), load_d(U.f[2], e), load_d(U.f[3], e)};
+    const double E = load_d(U.f[4], e);
+    const double Ekin0 = 0.5 * ((m[0] * m[0] + m[1] * m[1]) + m[2] * m[2]) / rho;
+    const double Eg0 = E - Ekin0;
+    const double Er0 = load_d(R.f[0], e);
+    double Eg, Er;
+    const int it = newton_exchange(p, rho, Eg0, Er0, dt, Eg, Er);
+    if (it < 0) {
+      my_flags |= 1u << QK_ENOCONV;
+      my_bad = min(my_bad, (unsigned long long)e);
+    } else {
+      my_max = max(my_max, it);
+    }
+    // flux source (backward Euler) and the equal and opposite momentum change
+    const double kF = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_R * rho : p.kappa_R;
+    const double damp = 1.0 / (1.0 + rho * kF * chat * dt);
+    double mn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double F0 = load_d(R.f[1 + a], e);
+      const double Fn = F0 * damp;
+      mn[a] = m[a] - (Fn - F0) / (chat * c);
+      R.f[1 + a][e] = (T)Fn;
+      U.f[1 + a][e] = (T)mn[a];
+    }
+    // work of the radiation force through the kinetic-energy change
+    const double Ekin1 = 0.5 * ((mn[0] * mn[0] + mn[1] * mn[1]) + mn[2] * mn[2]) / rho;
+    const double dEkin = Ekin1 - Ekin0;
+    U.f[4][e] = (T)(Eg + (Ekin0 + dEkin));
+    const double Er_new = Er - (chat / c) * dEkin;
+    R.f[0][e] = (T)Er_new;
+    if (!(Eg > 0.0) || !(Er_new > 0.0)) {
+      my_flags |= 1u << QK_ENEGATIVE;
+      my_bad = min(my_bad, (unsigned long long)e);
+    }
+  }
+  // warp-aggregated status update
+  const unsigned full = 0xffffffffu;
+  int wmax = __reduce_max_sync(full, my_max);
+  unsigned wflags = __reduce_or_sync(full, my_flags);
+  unsigned long long wbad = my_bad;
+  for (int o = 16; o > 0; o >>= 1) wbad = min(wbad, __shfl_xor_sync(full, wbad, o));
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&st->max_iter, wmax);
+    if (wflags) {
+      atomicOr(&st->flags, wflags);
+      atomicMin(&st->first_bad, wbad);
+    }
+  }
+}
+
+cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, void *const *U,
+                            void *const *R, DtSrc dt, Status *st, cudaStream_t s) {
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  long long want = (g.ncells + 255) / 256;
+  int grid = (int)std::min<long long>(want, (long long)nsm * 8);
+  if (grid < 1) return cudaSuccess;
+  if (fp32) {
+    F5<float> u; F4<float> r;
+    for (int q = 0; q < 5; ++q) u.f[q] = (float *)U[q];
+    for (int q = 0; q < 4; ++q) r.f[q] = (float *)R[q];
+    exchange_kernel<float><<<grid, 256, 0, s>>>(g, p, u, r, dt, st);
+  } else {
+    F5<double> u; F4<double> r;
+    for (int q = 0; q < 5; ++q) u.f[q] = (double *)U[q];
+    for (int q = 0; q < 4; ++q) r.f[q] = (double *)R[q];
+    exchange_kernel<double><<<grid, 256, 0, s>>>(g, p, u, r, dt, st);
+  }
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------- signal speed, dt -----
+// max(|v| + c_s) with IEEE round-to-nearest operations in the order
+// |v| = sqrt((vx^2 + vy^2) + vz^2), c_s = sqrt(gamma P / rho),
+// E_g = E - (rho/2) v^2 (no contraction), so that the step size is
+// reproducible bit for bit.
+template <typename T>
+__global__ void __launch_bounds__(256) max_speed_kernel(Geometry g, double gamma, F5<T> U,
+                                                        StepInfo *si) {
+  double best = 0.0;
+  for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < g.ncells;
+       cidx += (long long)gridDim.x * blockDim.x) {
+    const long long e = cell_to_elem(g, cidx);
+    const double rho = (double)U.f[0][e];
+    const double vx = __ddiv_rn((double)U.f[1][e], rho);
+    const double vy = __ddiv_rn((double)U.f[2][e], rho);
+    const double vz = __ddiv_rn((double)U.f[3][e], rho);
+    const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
+    const double Eg = __dsub_rn((double)U.f[4][e], __dmul_rn(__dmul_rn(0.5, rho), v2));
+    const double P = __dmul_rn(__dsub_rn(gamma, 1.0), Eg);
+    const double cs = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, P), rho));
+    const double sp = __dadd_rn(__dsqrt_rn(v2), cs);
+    best = fmax(best, sp);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  __shared__ double wbest[8];
+  if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, wbest[w]);
+    atomic_max_pos(&si->smax_bits, b);
+  }
+}
+
+cudaError_t launch_max_speed(int fp32, const Geometry &g, const qk_params &p, void *const *U,
+                             StepInfo *si, cudaStream_t s) {
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  long long want = (g.ncells + 255) / 256;
+  int grid = (int)std::min<long long>(want, (long long)nsm * 8);
+  if (grid < 1) grid = 1;
+  if (fp32) {
+    F5<float> u;
+    for (int q = 0; q < 5; ++q) u.f[q] = (float *)U[q];
+    max_speed_kernel<float><<<grid, 256, 0, s>>>(g, p.gamma, u, si);
+  } else {
+    F5<double> u;
+    for (int q = 0; q < 5; ++q) u.f[q] = (double *)U[q];
+    max_speed_kernel<double><<<grid, 256, 0, s>>>(g, p.gamma, u, si);
+  }
+  return cudaGetLastError();
+}
+
+// dt = CFL dx_min / smax; with radiation at most N_sub,max substeps of
+// CFL dx_min / chat (Sec. 2.2.4): if dt > N_sub,max dt_r then N_sub = N_sub,max
+// and dt = N_sub,max dt_r, else N_sub = max(1, ceil(dt / dt_r)); dt_rad =
+// dt / N_sub.  Resets the running maximum for the next step.
+__global__ void timestep_kernel(qk_params p, StepInfo *si) {
+  const double smax = __longlong_as_double((long long)si->smax_bits);
+  const double dxm = fmin(p.dx[0], fmin(p.dx[1], p.dx[2]));
+  double dt = __ddiv_rn(__dmul_rn(p.cfl, dxm), smax);
+  double nsub = 0.0, dtrad = 0.0;
+  if (!p.hydro_only) {
+    const double dtr = __ddiv_rn(__dmul_rn(p.cfl, dxm), p.chat);
+    const double cap = __dmul_rn((double)p.nsub_max, dtr);
+    if (dt > cap) {
+      nsub = (double)p.nsub_max;
+      dt = cap;
+    } else {
+      nsub = fmax(1.0, ceil(__ddiv_rn(dt, dtr)));
+    }
+    dtrad = __ddiv_rn(dt, nsub);
+  }
+  si->dt = dt;
+  si->nsub = nsub;
+  si->dtrad = dtrad;
+  si->smax = smax;
+  si->smax_bits = 0ull;
+}
+
+cudaError_t launch_timestep(const qk_params &p, StepInfo *si, cudaStream_t s) {
+  timestep_kernel<<<1, 1, 0, s>>>(p, si);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ ghost fill ---
+// One CTA per chunk of CHUNK_CELLS cells of one copy region; every field is
+// copied for each cell (the same addresses for all fields).
+template <typename T>
+__global__ void __launch_bounds__(256) ghost_fill_kernel(const Copy *copies, const Chunk *chunks,
+                                                         F5<T> fa, F4<T> fb, int nf, DtSrc pred) {
+  if (skip_substep(pred)) return;
+  const Chunk ch = chunks[blockIdx.x];
+  const Copy cp = copies[ch.copy];
+  const int ncell = cp.ex * cp.ey * cp.ez;
+  const int end = min(ncell, ch.start + CHUNK_CELLS);
+  for (int l = ch.start + threadIdx.x; l < end; l += blockDim.x) {
+    const int x = l % cp.ex;
+    const int r = l / cp.ex;
+    const int y = r % cp.ey;
+    const int z = r / cp.ey;
+    const long long d = cp.dst + ((long long)z * cp.dsy + y) * cp.dsx + x;
+    const long long s = cp.src + ((long long)z * cp.ssy + y) * cp.ssx + x;
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+      if (f < nf) fa.f[f][d] = fa.f[f][s];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      if (f + 5 < nf) fb.f[f][d] = fb.f[f][s];
+  }
+}
+
+cudaError_t launch_ghost_fill(int fp32, const Copy *copies, const Chunk *chunks, int nchunks,
+                              void *const *fields, int nf, DtSrc pred, cudaStream_t s) {
+  if (nchunks < 1 || nf < 1) return cudaSuccess;
+  if (fp32) {
+    F5<float> a{}; F4<float> b{};
+    for (int q = 0; q < nf && q < 5; ++q) a.f[q] = (float *)fields[q];
+    for (int q = 5; q < nf; ++q) b.f[q - 5] = (float *)fields[q];
+    ghost_fill_kernel<float><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, pred);
+  } else {
+    F5<double> a{}; F4<double> b{};
+    for (int q = 0; q < nf && q < 5; ++q) a.f[q] = (double *)fields[q];
+    for (int q = 5; q < nf; ++q) b.f[q - 5] = (double *)fields[q];
+    ghost_fill_kernel<double><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, pred);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ conservation sums ---
+// Double-double accumulation (Knuth's TwoSum) with a fixed assignment of cells
+// to threads and a fixed reduction tree: the result is bitwise reproducible.
+struct DD { double hi, lo; };
+__device__ __forceinline__ DD dd_add(DD a, double b) {
+  double s = a.hi + b;
+  double bb = s - a.hi;
+  double err = (a.hi - (s - bb)) + (b - bb);
+  return DD{s, a.lo + err};
+}
+__device__ __forceinline__ DD dd_add(DD a, DD b) {
+  DD s = dd_add(a, b.hi);
+  s.lo += b.lo;
+  double hi = s.hi + s.lo;
+  double lo = s.lo - (hi - s.hi);
+  return DD{hi, lo};
+}
+
+constexpr int SUM_NT = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(SUM_NT) sums_kernel(Geometry g, double cr, double icc, F5<T> U,
+                                                      F4<T> R, int has_rad, double *partials) {
+  DD acc[QK_NSUMS];
+#pragma unroll
+  for (int q = 0; q < QK_NSUMS; ++q) acc[q] = DD{0.0, 0.0};
+  for (long long cidx = (long long)blockIdx.x * SUM_NT + threadIdx.x; cidx < g.ncells;
+       cidx += (long long)gridDim.x * SUM_NT) {
+    const long long e = cell_to_elem(g, cidx);
+    double x[QK_NSUMS];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) x[q] = (double)U.f[q][e];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[5 + q] = has_rad ? (double)R.f[q][e] : 0.0;
+    x[9] = x[4] + cr * x[5];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[10 + a] = x[1 + a] + x[6 + a] * icc;
+#pragma unroll
+    for (int q = 0; q < QK_NSUMS; ++q) acc[q] = dd_add(acc[q], x[q]);
+  }
+  __shared__ DD sh[SUM_NT];
+  for (int q = 0; q < QK_NSUMS; ++q) {
+    sh[threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = SUM_NT / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] = dd_add(sh[threadIdx.x], sh[threadIdx.x + w]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      partials[(blockIdx.x * QK_NSUMS + q) * 2 + 0] = sh[0].hi;
+      partials[(blockIdx.x * QK_NSUMS + q) * 2 + 1] = sh[0].lo;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void sums_final_kernel(const double *partials, int nblocks, double vol, double *out) {
+  const int q = threadIdx.x;
+  if (q >= QK_NSUMS) return;
+  DD a{0.0, 0.0};
+  for (int b = 0; b < nblocks; ++b)
+    a = dd_add(a, DD{partials[(b * QK_NSUMS + q) * 2], partials[(b * QK_NSUMS + q) * 2 + 1]});
+  out[q] = (a.hi + a.lo) * vol;
+}
+
+cudaError_t launch_sums(int fp32, const Geometry &g, const qk_params &p, void *const *U,
+                        void *const *R, double *partials, int nblocks, double *out,
+                        cudaStream_t s) {
+  const double cr = p.c / p.chat, icc = 1.0 / (p.c * p.chat);
+  const double vol = p.dx[0] * p.dx[1] * p.dx[2];
+  const int has_rad = R != nullptr;
+  if (fp32) {
+    F5<float> u; F4<float> r{};
+    for (int q = 0; q < 5; ++q) u.f[q] = (float *)U[q];
+    if (has_rad) for (int q = 0; q < 4; ++q) r.f[q] = (float *)R[q];
+    sums_kernel<float><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials);
+  } else {
+    F5<double> u; F4<double> r{};
+    for (int q = 0; q < 5; ++q) u.f[q] = (double *)U[q];
+    if (has_rad) for (int q = 0; q < 4; ++q) r.f[q] = (double *)R[q];
+    sums_kernel<double><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sums_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, vol, out);
+  return cudaGetLastError();
+}
+
+}  // namespace qk

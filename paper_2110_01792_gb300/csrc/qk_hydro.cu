@@ -1,0 +1,196 @@
+// qk_hydro.cu -- fused hydro RK2-SSP stage (Sec. 2.2.1 of arXiv:2110.01792)
+// for sm_103a: conserved -> primitive, PPM reconstruction, HLLC flux, flux
+// divergence and the RK combination in one kernel per stage.  Each CTA owns
+// one TS^3 tile at a time (grid-stride over a tile work list spanning every
+// patch), stages the primitives of the tile and its cross halo in shared
+// memory once, then sweeps x, y, z: reconstruct -> face fluxes -> divergence,
+// with face states and fluxes kept in shared memory.
+#include "qk_device.cuh"
+
+namespace qk {
+
+template <typename T> struct HydroSmem {
+  T prim[5][NCROSS];   // rho, vx, vy, vz, P of the tile and its cross halo
+  T rec[10][NREC];     // per line position: qL, qR of each primitive
+  T flux[5][NFLUX];    // per face: mass, momentum x/y/z, energy
+};
+
+template <typename T, int D, int NT, int NOWN>
+__device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T inv_dx, T gamma,
+                                          T gm1inv, T g1, T (&acc)[NOWN][5]) {
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  // Phase A: reconstruction of every needed position of every line along D.
+  for (int it = threadIdx.x; it < NREC; it += NT) {
+    int pos, c[3];
+    item_cell<D>(it, NPOS, pos, c[0], c[1], c[2]);
+    if (c[A] >= v[A] || c[B] >= v[B] || c[D] > v[D]) continue;
+    int s[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+      int cc[3] = {c[0], c[1], c[2]};
+      cc[D] += o - 2;
+      s[o] = cross_slot(cc[0], cc[1], cc[2]);
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      T qL, qR;
+      ppm<T>(sm.prim[q][s[0]], sm.prim[q][s[1]], sm.prim[q][s[2]], sm.prim[q][s[3]],
+             sm.prim[q][s[4]], qL, qR);
+      sm.rec[2 * q][it] = qL;
+      sm.rec[2 * q + 1][it] = qR;
+    }
+  }
+  __syncthreads();
+  // Phase B: HLLC flux at every needed face (between positions f and f+1).
+  for (int it = threadIdx.x; it < NFLUX; it += NT) {
+    int f, c[3];
+    item_cell<D>(it, NFACE, f, c[0], c[1], c[2]);
+    if (c[A] >= v[A] || c[B] >= v[B] || f > v[D]) continue;
+    int il = item_index<D>(f, c[0], c[1], c[2], NPOS);
+    int ir = item_index<D>(f + 1, c[0], c[1], c[2], NPOS);
+    T wL[5], wR[5], F[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      wL[q] = sm.rec[2 * q + 1][il];
+      wR[q] = sm.rec[2 * q][ir];
+    }
+    hllc<T, D>(wL, wR, gamma, gm1inv, g1, F);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) sm.flux[q][it] = F[q];
+  }
+  __syncthreads();
+  // Phase C: accumulate the divergence of the owned cells, ((x + y) + z).
+#pragma unroll
+  for (int m = 0; m < NOWN; ++m) {
+    int s = threadIdx.x + m * NT;
+    int c[3] = {s % TS, (s / TS) % TS, s / (TS * TS)};
+    if (c[0] >= v[0] || c[1] >= v[1] || c[2] >= v[2]) continue;
+    int lo = item_index<D>(c[D] + 0, c[0], c[1], c[2], NFACE);
+    int hi = item_index<D>(c[D] + 1, c[0], c[1], c[2], NFACE);
+    // item_index for faces takes the face number as the position
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      T dv = (sm.flux[q][hi] - sm.flux[q][lo]) * inv_dx;
+      acc[m][q] = (D == 0) ? dv : acc[m][q] + dv;
+    }
+  }
+}
+
+template <typename T, int STAGE, int NT>
+__global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p, F5<T> U0,
+                                                         F5<T> U1, F5<T> Uo, DtSrc dts) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  HydroSmem<T> &sm = *reinterpret_cast<HydroSmem<T> *>(smem_raw);
+  constexpr int NOWN = NCORE / NT;
+  const T dt = (T)dt_of(dts);
+  const double gamma_d = p.gamma;
+  const T gamma = (T)p.gamma;
+  const T gm1inv = (T)(1.0 / (p.gamma - 1.0));
+  const T g1 = (T)((p.gamma + 1.0) / (2.0 * p.gamma));
+  const T inv_dx[3] = {(T)(1.0 / p.dx[0]), (T)(1.0 / p.dx[1]), (T)(1.0 / p.dx[2])};
+  const F5<T> src = STAGE == 1 ? U0 : U1;
+
+  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+    const Tile tl = g.tiles[t];
+    const DevBox b = g.boxes[tl.box];
+    const int v[3] = {min(TS, b.n[0] - tl.x0), min(TS, b.n[1] - tl.y0), min(TS, b.n[2] - tl.z0)};
+    // ---- load: conserved -> primitive into shared memory ----
+    T own[NOWN][5];
+#pragma unroll
+    for (int m = 0; m < NOWN; ++m) {
+      int s = threadIdx.x + m * NT;
+      int i = s % TS, j = (s / TS) % TS, k = s / (TS * TS);
+      if (!slot_needed(i, j, k, v)) continue;
+      long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
+      T u[5], w[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) u[q] = src.f[q][e];
+      con2prim<T>(u, gamma_d, w);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        own[m][q] = u[q];
+        sm.prim[q][s] = w[q];
+      }
+    }
+    for (int s = NCORE + threadIdx.x; s < NCROSS; s += NT) {
+      int i, j, k;
+      slot_cell(s, i, j, k);
+      if (!slot_needed(i, j, k, v)) continue;
+      long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
+      T u[5], w[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) u[q] = src.f[q][e];
+      con2prim<T>(u, gamma_d, w);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) sm.prim[q][s] = w[q];
+    }
+    __syncthreads();
+    T acc[NOWN][5];
+    hydro_dir<T, 0, NT, NOWN>(sm, v, inv_dx[0], gamma, gm1inv, g1, acc);
+    hydro_dir<T, 1, NT, NOWN>(sm, v, inv_dx[1], gamma, gm1inv, g1, acc);
+    hydro_dir<T, 2, NT, NOWN>(sm, v, inv_dx[2], gamma, gm1inv, g1, acc);
+    // ---- RK2-SSP combination for the owned cells ----
+#pragma unroll
+    for (int m = 0; m < NOWN; ++m) {
+      int s = threadIdx.x + m * NT;
+      int i = s % TS, j = (s / TS) % TS, k = s / (TS * TS);
+      if (i >= v[0] || j >= v[1] || k >= v[2]) continue;
+      long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        T L = -acc[m][q];
+        if (STAGE == 1) {
+          Uo.f[q][e] = own[m][q] + dt * L;
+        } else {
+          T u0 = U0.f[q][e];
+          Uo.f[q][e] = T(0.5) * u0 + T(0.5) * (own[m][q] + dt * L);
+        }
+      }
+    }
+    // the next tile's load overwrites prim, last read before the syncs of z
+  }
+}
+
+template <typename T, int STAGE>
+static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const *U0,
+                              void *const *U1, void *const *Uo, DtSrc dt, int grid,
+                              cudaStream_t s) {
+  constexpr int NT = 256;
+  F5<T> a, b, c;
+  for (int q = 0; q < 5; ++q) {
+    a.f[q] = (T *)U0[q];
+    b.f[q] = U1 ? (T *)U1[q] : nullptr;
+    c.f[q] = (T *)Uo[q];
+  }
+  int smem = (int)sizeof(HydroSmem<T>);
+  auto kern = hydro_stage_kernel<T, STAGE, NT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (grid <= 0) {
+    int per_sm = 0, nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    grid = nsm * (per_sm > 0 ? per_sm : 1);
+  }
+  if (grid > g.ntiles) grid = g.ntiles;
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
+                               void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
+                               int grid, cudaStream_t s) {
+  if (fp32)
+    return stage == 1 ? launch_one<float, 1>(g, p, U0, U1, Uout, dt, grid, s)
+                      : launch_one<float, 2>(g, p, U0, U1, Uout, dt, grid, s);
+  return stage == 1 ? launch_one<double, 1>(g, p, U0, U1, Uout, dt, grid, s)
+                    : launch_one<double, 2>(g, p, U0, U1, Uout, dt, grid, s);
+}
+
+int hydro_smem_bytes(int fp32) {
+  return fp32 ? (int)sizeof(HydroSmem<float>) : (int)sizeof(HydroSmem<double>);
+}
+
+}  // namespace qk

@@ -1,0 +1,248 @@
+// qk_rad.cu -- fused radiation RK2-SSP stage (Sec. 2.2.2 of arXiv:2110.01792)
+// for sm_103a: PPM reconstruction of E_r and f = F/(c E_r), first-order
+// fallback at faces where a state has |f| > 1, Levermore closure
+// (eq. M1_closure), HLL flux with wavespeeds from the cell-average Eddington
+// factors, optical-depth correction, RSLA fluxes (eqs. rad_energy, rad_flux),
+// divergence and RK combination.  Same tile scheme as the hydro stage.
+#include "qk_device.cuh"
+
+namespace qk {
+
+template <typename T> struct RadSmem {
+  T prim[4][NCROSS];   // E_r, f_x, f_y, f_z of the tile and its cross halo
+  T rk[NCROSS];        // rho kappa_R of the cell
+  T rec[8][NREC];      // qL, qR of each reconstructed variable
+  T sq[NREC];          // sqrt(T_DD) of the cell-average state at each position
+  T flux[4][NFLUX];
+};
+
+template <typename T> __device__ __forceinline__ T kappa_of(const qk_params &p, double k, T rho) {
+  return p.kappa_mode == QK_KAPPA_RHO ? (T)k * rho : (T)k;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T c, T chat, T ccc, T U[4],
+                                            T F[4]) {
+  T Tx, Ty, Tz;
+  eddington_col<T, D>(fx, fy, fz, Tx, Ty, Tz);
+  const T cE = c * E;
+  U[0] = E;
+  U[1] = cE * fx;
+  U[2] = cE * fy;
+  U[3] = cE * fz;
+  F[0] = (chat / c) * U[1 + D];
+  F[1] = ccc * (E * Tx);
+  F[2] = ccc * (E * Ty);
+  F[3] = ccc * (E * Tz);
+}
+
+template <typename T, int D, int NT, int NOWN>
+__device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx, T dx, T c,
+                                        T chat, int tau_corr, T (&acc)[NOWN][4]) {
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  const T ccc = c * chat;
+  for (int it = threadIdx.x; it < NREC; it += NT) {
+    int pos, cc[3];
+    item_cell<D>(it, NPOS, pos, cc[0], cc[1], cc[2]);
+    if (cc[A] >= v[A] || cc[B] >= v[B] || cc[D] > v[D]) continue;
+    int s[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+      int x[3] = {cc[0], cc[1], cc[2]};
+      x[D] += o - 2;
+      s[o] = cross_slot(x[0], x[1], x[2]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      T qL, qR;
+      ppm<T>(sm.prim[q][s[0]], sm.prim[q][s[1]], sm.prim[q][s[2]], sm.prim[q][s[3]],
+             sm.prim[q][s[4]], qL, qR);
+      sm.rec[2 * q][it] = qL;
+      sm.rec[2 * q + 1][it] = qR;
+    }
+    sm.sq[it] = sqrt(eddington_diag<T, D>(sm.prim[1][s[2]], sm.prim[2][s[2]], sm.prim[3][s[2]]));
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < NFLUX; it += NT) {
+    int f, cc[3];
+    item_cell<D>(it, NFACE, f, cc[0], cc[1], cc[2]);
+    if (cc[A] >= v[A] || cc[B] >= v[B] || f > v[D]) continue;
+    const int il = item_index<D>(f, cc[0], cc[1], cc[2], NPOS);
+    const int ir = item_index<D>(f + 1, cc[0], cc[1], cc[2], NPOS);
+    T wL[4], wR[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      wL[q] = sm.rec[2 * q + 1][il];
+      wR[q] = sm.rec[2 * q][ir];
+    }
+    const T fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
+    const T fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
+    int xa[3] = {cc[0], cc[1], cc[2]}, xb[3] = {cc[0], cc[1], cc[2]};
+    xa[D] = f - 1;
+    xb[D] = f;
+    const int sa = cross_slot(xa[0], xa[1], xa[2]);
+    const int sb = cross_slot(xb[0], xb[1], xb[2]);
+    if (fL2 > T(1) || fR2 > T(1)) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        wL[q] = sm.prim[q][sa];
+        wR[q] = sm.prim[q][sb];
+      }
+    }
+    T UL[4], FL[4], UR[4], FR[4];
+    rad_flux_of<T, D>(wL[0], wL[1], wL[2], wL[3], c, chat, ccc, UL, FL);
+    rad_flux_of<T, D>(wR[0], wR[1], wR[2], wR[3], c, chat, ccc, UR, FR);
+    const T S = chat * max(sm.sq[il], sm.sq[ir]);
+    T eps = T(1);
+    if (tau_corr) {
+      const T tau = dx * T(0.5) * (sm.rk[sa] + sm.rk[sb]);
+      if (tau > T(1)) eps = T(1) / tau;
+    }
+    T out[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = T(0.5) * (FL[q] + FR[q]) - T(0.5) * S * eps * (UR[q] - UL[q]);
+    if (eps < T(1) && fabs(out[0]) > chat * max(UL[0], UR[0])) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) out[q] = T(0.5) * (FL[q] + FR[q]) - T(0.5) * S * (UR[q] - UL[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sm.flux[q][it] = out[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < NOWN; ++m) {
+    int s = threadIdx.x + m * NT;
+    int cc[3] = {s % TS, (s / TS) % TS, s / (TS * TS)};
+    if (cc[0] >= v[0] || cc[1] >= v[1] || cc[2] >= v[2]) continue;
+    int lo = item_index<D>(cc[D], cc[0], cc[1], cc[2], NFACE);
+    int hi = item_index<D>(cc[D] + 1, cc[0], cc[1], cc[2], NFACE);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      T dv = (sm.flux[q][hi] - sm.flux[q][lo]) * inv_dx;
+      acc[m][q] = (D == 0) ? dv : acc[m][q] + dv;
+    }
+  }
+}
+
+template <typename T, int STAGE, int NT>
+__global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, F4<T> R0,
+                                                       F4<T> R1, F4<T> Ro, const T *rho,
+                                                       DtSrc dts) {
+  if (skip_substep(dts)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RadSmem<T> &sm = *reinterpret_cast<RadSmem<T> *>(smem_raw);
+  constexpr int NOWN = NCORE / NT;
+  const T dt = (T)dt_of(dts);
+  const T c = (T)p.c, chat = (T)p.chat;
+  const T inv_dx[3] = {(T)(1.0 / p.dx[0]), (T)(1.0 / p.dx[1]), (T)(1.0 / p.dx[2])};
+  const T dx[3] = {(T)p.dx[0], (T)p.dx[1], (T)p.dx[2]};
+  const F4<T> src = STAGE == 1 ? R0 : R1;
+
+  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+    const Tile tl = g.tiles[t];
+    const DevBox b = g.boxes[tl.box];
+    const int v[3] = {min(TS, b.n[0] - tl.x0), min(TS, b.n[1] - tl.y0), min(TS, b.n[2] - tl.z0)};
+    T own[NOWN][4];
+#pragma unroll
+    for (int m = 0; m < NOWN; ++m) {
+      int s = threadIdx.x + m * NT;
+      int i = s % TS, j = (s / TS) % TS, k = s / (TS * TS);
+      if (!slot_needed(i, j, k, v)) continue;
+      long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
+      T u[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) u[q] = src.f[q][e];
+      const T cE = c * u[0];
+      sm.prim[0][s] = u[0];
+      sm.prim[1][s] = u[1] / cE;
+      sm.prim[2][s] = u[2] / cE;
+      sm.prim[3][s] = u[3] / cE;
+      const T r = rho[e];
+      sm.rk[s] = r * kappa_of<T>(p, p.kappa_R, r);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) own[m][q] = u[q];
+    }
+    for (int s = NCORE + threadIdx.x; s < NCROSS; s += NT) {
+      int i, j, k;
+      slot_cell(s, i, j, k);
+      if (!slot_needed(i, j, k, v)) continue;
+      long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
+      T u[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) u[q] = src.f[q][e];
+      const T cE = c * u[0];
+      sm.prim[0][s] = u[0];
+      sm.prim[1][s] = u[1] / cE;
+      sm.prim[2][s] = u[2] / cE;
+      sm.prim[3][s] = u[3] / cE;
+      const T r = rho[e];
+      sm.rk[s] = r * kappa_of<T>(p, p.kappa_R, r);
+    }
+    __syncthreads();
+    T acc[NOWN][4];
+    rad_dir<T, 0, NT, NOWN>(sm, v, inv_dx[0], dx[0], c, chat, p.tau_correction, acc);
+    rad_dir<T, 1, NT, NOWN>(sm, v, inv_dx[1], dx[1], c, chat, p.tau_correction, acc);
+    rad_dir<T, 2, NT, NOWN>(sm, v, inv_dx[2], dx[2], c, chat, p.tau_correction, acc);
+#pragma unroll
+    for (int m = 0; m < NOWN; ++m) {
+      int s = threadIdx.x + m * NT;
+      int i = s % TS, j = (s / TS) % TS, k = s / (TS * TS);
+      if (i >= v[0] || j >= v[1] || k >= v[2]) continue;
+      long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        T L = -acc[m][q];
+        if (STAGE == 1) {
+          Ro.f[q][e] = own[m][q] + dt * L;
+        } else {
+          T u0 = R0.f[q][e];
+          Ro.f[q][e] = T(0.5) * u0 + T(0.5) * (own[m][q] + dt * L);
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int STAGE>
+static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const *R0,
+                              void *const *R1, void *const *Ro, const void *rho, DtSrc dt,
+                              int grid, cudaStream_t s) {
+  constexpr int NT = 256;
+  F4<T> a, b, c;
+  for (int q = 0; q < 4; ++q) {
+    a.f[q] = (T *)R0[q];
+    b.f[q] = R1 ? (T *)R1[q] : nullptr;
+    c.f[q] = (T *)Ro[q];
+  }
+  int smem = (int)sizeof(RadSmem<T>);
+  auto kern = rad_stage_kernel<T, STAGE, NT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (grid <= 0) {
+    int per_sm = 0, nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    grid = nsm * (per_sm > 0 ? per_sm : 1);
+  }
+  if (grid > g.ntiles) grid = g.ntiles;
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, (const T *)rho, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
+                             void *const *R0, void *const *R1, void *const *Rout,
+                             const void *rho, DtSrc dt, int grid, cudaStream_t s) {
+  if (fp32)
+    return stage == 1 ? launch_one<float, 1>(g, p, R0, R1, Rout, rho, dt, grid, s)
+                      : launch_one<float, 2>(g, p, R0, R1, Rout, rho, dt, grid, s);
+  return stage == 1 ? launch_one<double, 1>(g, p, R0, R1, Rout, rho, dt, grid, s)
+                    : launch_one<double, 2>(g, p, R0, R1, Rout, rho, dt, grid, s);
+}
+
+int rad_smem_bytes(int fp32) {
+  return fp32 ? (int)sizeof(RadSmem<float>) : (int)sizeof(RadSmem<double>);
+}
+
+}  // namespace qk

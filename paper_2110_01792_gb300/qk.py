@@ -1,0 +1,221 @@
+"""Python binding of libqk (include/qk.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of ``libqk.so``; this module turns
+torch CUDA tensors into device pointers and the current torch stream into a
+cudaStream_t.  It never computes a step itself and has no CPU path: if the
+library is missing it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqk.so")
+
+OK, EINVAL, ECUDA, ENOCONV, ENEGATIVE = 0, 1, 2, 3, 4
+FP64, FP32_MIXED = 0, 1
+NSUMS = 13
+_lib = None
+
+
+class QKError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"qk error {code}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    """Mirror of qk_params."""
+    _fields_ = [
+        ("gamma", C.c_double), ("cfl", C.c_double), ("a_r", C.c_double),
+        ("c", C.c_double), ("chat", C.c_double), ("c_v", C.c_double),
+        ("kappa_P", C.c_double), ("kappa_R", C.c_double), ("alpha_eos", C.c_double),
+        ("eps_newton", C.c_double), ("dx", C.c_double * 3),
+        ("kappa_mode", C.c_int32), ("eos", C.c_int32), ("max_iter", C.c_int32),
+        ("nsub_max", C.c_int32), ("tau_correction", C.c_int32), ("hydro_only", C.c_int32),
+    ]
+
+
+class Box(C.Structure):
+    """Mirror of qk_box."""
+    _fields_ = [("lo", C.c_int32 * 3), ("n", C.c_int32 * 3), ("offset", C.c_int64)]
+
+
+def lib():
+    """Load libqk.so (built by ``paper_2110_01792_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libqk.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    P = C.POINTER
+    L.qk_init_patches.argtypes = [P(vp), P(Params), P(Box), i32, P(i32), i32, i32]
+    L.qk_init_patches.restype = C.c_int
+    L.qk_destroy.argtypes = [vp]
+    L.qk_destroy.restype = None
+    L.qk_last_error.argtypes = [vp]
+    L.qk_last_error.restype = C.c_char_p
+    L.qk_field_len.argtypes = [vp]
+    L.qk_field_len.restype = i64
+    L.qk_num_cells.argtypes = [vp]
+    L.qk_num_cells.restype = i64
+    L.qk_set_params.argtypes = [vp, P(Params)]
+    L.qk_set_graph.argtypes = [vp, i32]
+    L.qk_fill_ghosts.argtypes = [vp, P(vp), i32, vp]
+    L.qk_hydro_stage.argtypes = [vp, i32, P(vp), P(vp), P(vp), dbl, vp]
+    L.qk_rad_stage.argtypes = [vp, i32, P(vp), P(vp), P(vp), vp, dbl, vp]
+    L.qk_rad_matter_exchange.argtypes = [vp, P(vp), P(vp), dbl, vp]
+    L.qk_timestep.argtypes = [vp, P(vp), P(dbl), vp]
+    L.qk_step.argtypes = [vp, P(vp), P(vp), P(dbl), P(i32), vp]
+    L.qk_conserved_sums.argtypes = [vp, P(vp), P(vp), P(dbl), vp]
+    L.qk_status.argtypes = [vp, P(C.c_uint32), P(i64), P(i32), i32, vp]
+    for f in ("qk_set_params", "qk_set_graph", "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
+              "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
+              "qk_status"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def make_params(**kw) -> Params:
+    p = Params()
+    p.gamma = kw.get("gamma", 5.0 / 3.0)
+    p.cfl = kw.get("cfl", 0.3)
+    p.a_r = kw.get("a_r", 1.0)
+    p.c = kw.get("c", 100.0)
+    p.chat = kw.get("chat", 10.0)
+    p.c_v = kw.get("c_v", 1.0 / (p.gamma - 1.0))
+    p.kappa_P = kw.get("kappa_P", 1.0)
+    p.kappa_R = kw.get("kappa_R", 1.0)
+    p.alpha_eos = kw.get("alpha_eos", 0.0)
+    p.eps_newton = kw.get("eps_newton", 1e-10)
+    dx = kw.get("dx", (1.0, 1.0, 1.0))
+    if np.isscalar(dx):
+        dx = (dx, dx, dx)
+    for i in range(3):
+        p.dx[i] = float(dx[i])
+    p.kappa_mode = int(kw.get("kappa_mode", 0))
+    p.eos = int(kw.get("eos", 0))
+    p.max_iter = int(kw.get("max_iter", 400))
+    p.nsub_max = int(kw.get("nsub_max", 10))
+    p.tau_correction = int(kw.get("tau_correction", 1))
+    p.hydro_only = int(kw.get("hydro_only", 0))
+    return p
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptrs(fields, n):
+    if fields is None:
+        return None
+    assert len(fields) == n, f"expected {n} fields"
+    return (C.c_void_p * n)(*[int(f.data_ptr()) for f in fields])
+
+
+class Context:
+    """A patch set on the current CUDA device (wraps qk_init_patches)."""
+
+    def __init__(self, layout, params: dict, precision: int = FP64):
+        self._L = lib()
+        nb = layout.nbox
+        boxes = (Box * nb)()
+        for b in range(nb):
+            for d in range(3):
+                boxes[b].lo[d] = int(layout.lo[b][d])
+                boxes[b].n[d] = int(layout.n[b][d])
+            boxes[b].offset = int(layout.off[b])
+        dom = (C.c_int32 * 3)(*[int(v) for v in layout.dom_n])
+        self.params = make_params(**params)
+        self.precision = precision
+        self.layout = layout
+        h = C.c_void_p()
+        rc = self._L.qk_init_patches(C.byref(h), C.byref(self.params), boxes, nb, dom,
+                                     int(layout.ng), int(precision))
+        if rc != OK:
+            raise QKError(rc, self._L.qk_last_error(None).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.qk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise QKError(rc, self._L.qk_last_error(self._h).decode())
+
+    @property
+    def field_len(self):
+        return int(self._L.qk_field_len(self._h))
+
+    @property
+    def num_cells(self):
+        return int(self._L.qk_num_cells(self._h))
+
+    def set_params(self, **kw):
+        self.params = make_params(**kw)
+        self._check(self._L.qk_set_params(self._h, C.byref(self.params)))
+
+    def set_graph(self, enable: bool):
+        self._check(self._L.qk_set_graph(self._h, 1 if enable else 0))
+
+    def fill_ghosts(self, fields, stream=None):
+        self._check(self._L.qk_fill_ghosts(self._h, _ptrs(fields, len(fields)), len(fields),
+                                           _stream(stream)))
+
+    def hydro_stage(self, stage, U0, U1, Uout, dt, stream=None):
+        self._check(self._L.qk_hydro_stage(self._h, stage, _ptrs(U0, 5), _ptrs(U1, 5),
+                                           _ptrs(Uout, 5), float(dt), _stream(stream)))
+
+    def rad_stage(self, stage, R0, R1, Rout, rho, dt, stream=None):
+        self._check(self._L.qk_rad_stage(self._h, stage, _ptrs(R0, 4), _ptrs(R1, 4),
+                                         _ptrs(Rout, 4), C.c_void_p(int(rho.data_ptr())),
+                                         float(dt), _stream(stream)))
+
+    def exchange(self, U, R, dt, stream=None):
+        self._check(self._L.qk_rad_matter_exchange(self._h, _ptrs(U, 5), _ptrs(R, 4), float(dt),
+                                                   _stream(stream)))
+
+    def timestep(self, U, stream=None):
+        out = (C.c_double * 4)()
+        self._check(self._L.qk_timestep(self._h, _ptrs(U, 5), out, _stream(stream)))
+        return out[0], int(out[1]), out[2], out[3]
+
+    def step(self, U, R=None, want_dt=False, stream=None):
+        dt = C.c_double(0.0)
+        ns = C.c_int32(0)
+        self._check(self._L.qk_step(self._h, _ptrs(U, 5), _ptrs(R, 4) if R is not None else None,
+                                    C.byref(dt) if want_dt else None,
+                                    C.byref(ns) if want_dt else None, _stream(stream)))
+        return (dt.value, ns.value) if want_dt else None
+
+    def conserved_sums(self, U, R=None, stream=None):
+        out = (C.c_double * NSUMS)()
+        self._check(self._L.qk_conserved_sums(self._h, _ptrs(U, 5),
+                                              _ptrs(R, 4) if R is not None else None, out,
+                                              _stream(stream)))
+        return np.array(out[:])
+
+    def status(self, reset=False, stream=None):
+        fl = C.c_uint32()
+        fb = C.c_int64()
+        mi = C.c_int32()
+        rc = self._L.qk_status(self._h, C.byref(fl), C.byref(fb), C.byref(mi), 1 if reset else 0,
+                               _stream(stream))
+        return rc, int(fl.value), int(fb.value), int(mi.value)

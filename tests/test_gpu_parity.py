@@ -1,0 +1,370 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  FP64: max relative error per cell (floor = RMS of the
+field) <= 1e-12 for one stage, <= 1e-10 after 10 steps; ghost fill and the
+timestep are bit-exact.  FP32-mixed: relative L1 error <= 1e-5 in rho, E, E_r."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_01792_gb300 import inputs as I
+from tests import gpu_util as G
+from tests import problems as P
+
+pytestmark = pytest.mark.gpu
+
+TOL_STAGE = 1e-12
+TOL_STEPS = 1e-10
+TOL_MIXED_L1 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2110_01792_gb300 import qk
+    qk.lib()
+    return torch
+
+
+def _ctx(lay, prm, prec=0):
+    from paper_2110_01792_gb300 import qk
+    return qk.Context(lay, prm, prec)
+
+
+def _grid(lay):
+    return O.Grid(lay.lo, lay.n, lay.off, lay.dom_n, lay.ng)
+
+
+RAGGED = I.make_layout([[0, 0, 0], [13, 0, 0], [0, 7, 0]],
+                       [[13, 7, 11], [6, 17, 11], [13, 10, 11]], (19, 17, 11), 4)
+
+
+def _random_rhd(lay, seed, kappa0=None):
+    prob = I.rhd_lognormal(layout=lay, seed=seed)
+    # give the gas some velocity and the radiation some flux, incl. |f| > 1 spots
+    rng = np.random.Generator(np.random.Philox(seed + 100))
+    for b in range(lay.nbox):
+        rho = lay.interior(prob.U[0], b)
+        v = 0.3 * rng.standard_normal((3,) + rho.shape)
+        for d in range(3):
+            lay.interior(prob.U[1 + d], b)[...] = rho * v[d]
+        lay.interior(prob.U[4], b)[...] += 0.5 * rho * (v ** 2).sum(0)
+        Er = lay.interior(prob.R[0], b)
+        f = rng.standard_normal((3,) + Er.shape)
+        f *= (0.9 * rng.random(Er.shape) / np.sqrt((f ** 2).sum(0)))
+        f[:, rng.random(Er.shape) < 0.03] *= 1.3  # a few superluminal states
+        for d in range(3):
+            lay.interior(prob.R[1 + d], b)[...] = prob.params["c"] * Er * f[d]
+    prm = dict(prob.params)
+    prm["dx"] = 1.0 / max(lay.dom_n)
+    if kappa0 is not None:
+        prm["kappa_mode"] = 1
+        prm["kappa_P"] = prm["kappa_R"] = kappa0
+    return prob, prm
+
+
+# ------------------------------------------------------------ ghost fill --
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ghost_fill_bit_exact(torch_cuda, prec):
+    torch = torch_cuda
+    for lay in (I.single_box(13, 10, 9, ng=4), RAGGED,
+                I.patch_tiling(dom_n=(48, 40, 32), seed=5, ng=3, edges=(8, 16, 24)),
+                I.single_box(9, 1, 2, ng=4)):
+        rng = np.random.Generator(np.random.Philox(1))
+        fields = [rng.standard_normal(lay.field_len) for _ in range(9)]
+        for f in fields:  # the interior only; the ghosts hold garbage
+            pass
+        ref = [f.copy() for f in fields]
+        g = _grid(lay)
+        for f in ref:
+            O.fill_ghosts(g, f)
+        ctx = _ctx(lay, dict(hydro_only=1, dx=0.1), prec)
+        dt = torch.float64 if prec == 0 else torch.float32
+        d = G.dev(fields, dt)
+        ctx.fill_ghosts(d)
+        torch.cuda.synchronize()
+        for got, r in zip(G.host(d), ref):
+            rr = r if prec == 0 else r.astype(np.float32).astype(np.float64)
+            for b in range(lay.nbox):
+                assert np.array_equal(lay.full(got, b), lay.full(rr, b))
+        ctx.close()
+
+
+# ----------------------------------------------------------- hydro stage --
+
+@pytest.mark.parametrize("lay", [RAGGED, I.single_box(16, ng=4)], ids=["ragged", "box16"])
+def test_hydro_stages_match_oracle(torch_cuda, lay):
+    torch = torch_cuda
+    prob, prm = _random_rhd(lay, 3)
+    prm["hydro_only"] = 1
+    U0 = prob.U
+    p = O.make_params(**prm)
+    g = _grid(lay)
+    dt = 0.2 * O.timestep(g, p, U0)[0]
+    U1r = [np.zeros_like(a) for a in U0]
+    O.hydro_stage(g, p, 1, U0, None, U1r, dt)
+    U2r = [a.copy() for a in U0]
+    O.hydro_stage(g, p, 2, U2r, U1r, U2r, dt)
+    ctx = _ctx(lay, prm)
+    dU0 = G.dev(U0)
+    dU1 = G.dev([np.zeros_like(a) for a in U0])
+    ctx.fill_ghosts(dU0)
+    ctx.hydro_stage(1, dU0, None, dU1, dt)
+    e1 = G.max_rel_err(lay, G.host(dU1), U1r)
+    # stage 2 from the oracle's U1 so that the two stages are checked separately
+    dU1 = G.dev(U1r)
+    ctx.fill_ghosts(dU1)
+    ctx.hydro_stage(2, dU0, dU1, dU0, dt)
+    torch.cuda.synchronize()
+    e2 = G.max_rel_err(lay, G.host(dU0), U2r)
+    ctx.close()
+    assert max(e1) <= TOL_STAGE, e1
+    assert max(e2) <= TOL_STAGE, e2
+
+
+# ------------------------------------------------------------- rad stage --
+
+@pytest.mark.parametrize("kappa0", [None, 60.0], ids=["thin", "thick_kappa_rho"])
+def test_rad_stages_match_oracle(torch_cuda, kappa0):
+    torch = torch_cuda
+    lay = RAGGED
+    prob, prm = _random_rhd(lay, 4, kappa0)
+    p = O.make_params(**prm)
+    g = _grid(lay)
+    dtr = 0.3 * (1.0 / 19) / prm["chat"]
+    rho = prob.U[0]
+    R1r = [np.zeros_like(a) for a in prob.R]
+    O.rad_stage(g, p, 1, prob.R, None, R1r, rho, dtr)
+    R2r = [a.copy() for a in prob.R]
+    O.rad_stage(g, p, 2, R2r, R1r, R2r, rho, dtr)
+    ctx = _ctx(lay, prm)
+    dR0 = G.dev(prob.R)
+    drho = G.dev([rho])[0]
+    dR1 = G.dev([np.zeros_like(a) for a in prob.R])
+    ctx.fill_ghosts(dR0 + [drho])
+    ctx.rad_stage(1, dR0, None, dR1, drho, dtr)
+    e1 = G.max_rel_err(lay, G.host(dR1), R1r)
+    dR1 = G.dev(R1r)
+    ctx.fill_ghosts(dR1)
+    ctx.rad_stage(2, dR0, dR1, dR0, drho, dtr)
+    torch.cuda.synchronize()
+    e2 = G.max_rel_err(lay, G.host(dR0), R2r)
+    ctx.close()
+    assert max(e1) <= TOL_STAGE, e1
+    assert max(e2) <= TOL_STAGE, e2
+
+
+# -------------------------------------------------------------- exchange --
+
+@pytest.mark.parametrize("kappa0", [None, 40.0], ids=["kconst", "krho"])
+def test_exchange_matches_oracle(torch_cuda, kappa0):
+    torch = torch_cuda
+    lay = RAGGED
+    prob, prm = _random_rhd(lay, 5, kappa0)
+    p = O.make_params(**prm)
+    g = _grid(lay)
+    dtr = 0.3 * (1.0 / 19) / prm["chat"]
+    Ur = [a.copy() for a in prob.U]
+    Rr = [a.copy() for a in prob.R]
+    rc, info = O.exchange(g, p, Ur, Rr, dtr)
+    assert rc == 0
+    ctx = _ctx(lay, prm)
+    dU, dR = G.dev(prob.U), G.dev(prob.R)
+    ctx.exchange(dU, dR, dtr)
+    torch.cuda.synchronize()
+    rc, flags, bad, maxit = ctx.status()
+    assert rc == 0 and flags == 0 and bad == -1 and maxit == info[2]
+    e = G.max_rel_err(lay, G.host(dU) + G.host(dR), Ur + Rr)
+    ctx.close()
+    assert max(e) <= TOL_STAGE, e
+
+
+def test_exchange_nonconvergence_reported(torch_cuda):
+    torch = torch_cuda
+    lay = I.single_box(3, 2, 2)
+    prob = I.rhd_lognormal(layout=lay, seed=1)
+    prm = dict(prob.params, max_iter=1, dx=1.0 / 3)
+    ctx = _ctx(lay, prm)
+    dU, dR = G.dev(prob.U), G.dev(prob.R)
+    ctx.exchange(dU, dR, 0.5)
+    torch.cuda.synchronize()
+    from paper_2110_01792_gb300 import qk
+    rc, flags, bad, maxit = ctx.status(reset=True)
+    assert rc == qk.ENOCONV and flags & (1 << qk.ENOCONV)
+    assert bad == int(lay.off[0]) + (4 * 10 + 4) * 11 + 4  # first interior cell
+    rc2, flags2, bad2, _ = ctx.status()
+    assert rc2 == 0 and flags2 == 0 and bad2 == -1
+    ctx.close()
+
+
+# ------------------------------------------------------- timestep, sums ---
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_timestep_bit_exact(torch_cuda, prec):
+    torch = torch_cuda
+    lay = RAGGED
+    prob, prm = _random_rhd(lay, 6)
+    U = prob.U if prec == 0 else [a.astype(np.float32).astype(np.float64) for a in prob.U]
+    p = O.make_params(**prm)
+    ref = O.timestep(_grid(lay), p, U)
+    smax = O.max_signal_speed(_grid(lay), p, U)
+    ctx = _ctx(lay, prm, prec)
+    got = ctx.timestep(G.dev(U, torch.float64 if prec == 0 else torch.float32))
+    ctx.close()
+    assert got[3] == smax and got[0] == ref[0] and got[1] == ref[1] and got[2] == ref[2]
+
+
+def test_conserved_sums_match_oracle(torch_cuda):
+    lay = RAGGED
+    prob, prm = _random_rhd(lay, 7)
+    ref = O.conserved_sums(_grid(lay), O.make_params(**prm), prob.U, prob.R)
+    ctx = _ctx(lay, prm)
+    got = ctx.conserved_sums(G.dev(prob.U), G.dev(prob.R))
+    again = ctx.conserved_sums(G.dev(prob.U), G.dev(prob.R))
+    ctx.close()
+    assert np.array_equal(got, again)  # fixed reduction order
+    for a, b in zip(got, ref):
+        assert abs(a - b) <= 4e-16 * max(abs(b), 1e-300) + 1e-300
+
+
+# --------------------------------------------------------- whole steps ----
+
+def _run_gpu_steps(lay, prob, prm, nsteps, prec=0, graph=True):
+    torch = pytest.importorskip("torch")
+    ctx = _ctx(lay, prm, prec)
+    ctx.set_graph(graph)
+    dt_ = torch.float64 if prec == 0 else torch.float32
+    dU = G.dev(prob.U, dt_)
+    dR = G.dev(prob.R, dt_) if prob.R is not None else None
+    hist = []
+    for _ in range(nsteps):
+        hist.append(ctx.step(dU, dR, want_dt=True))
+    torch.cuda.synchronize()
+    st = ctx.status()
+    ctx.close()
+    return G.host(dU), (G.host(dR) if dR is not None else None), hist, st
+
+
+def _run_oracle_steps(lay, prob, prm, nsteps):
+    g = _grid(lay)
+    p = O.make_params(**prm)
+    U = [a.copy() for a in prob.U]
+    R = [a.copy() for a in prob.R] if prob.R is not None else None
+    hist = []
+    for _ in range(nsteps):
+        rc, ts, info = O.step(g, p, U, R)
+        assert rc == 0
+        hist.append((ts[0], ts[1]))
+    return U, R, hist
+
+
+def test_hydro32_ten_steps_fp64(torch_cuda):
+    """The hydro workload (32^3, seeded waves, PPM + HLLC + RK2, CFL 0.3):
+    10 FP64 steps agree with the oracle to 1e-10 per cell, step sizes equal."""
+    prob = I.config("hydro32")
+    Ug, _, hg, st = _run_gpu_steps(prob.layout, prob, prob.params, 10)
+    Ur, _, hr, = _run_oracle_steps(prob.layout, prob, prob.params, 10)[0:3]
+    _check_dt(hg, hr)
+    e = G.max_rel_err(prob.layout, Ug, Ur)
+    assert max(e) <= TOL_STEPS, e
+
+
+def _check_dt(hg, hr):
+    """The first step size is bit-exact (identical inputs, IEEE-ordered
+    reduction); later ones follow states that differ by round-off, so dt may
+    move by an ulp; N_sub must agree."""
+    assert hg[0][0] == hr[0][0]
+    for (dg, ng), (dr, nr) in zip(hg, hr):
+        assert abs(dg - dr) <= 1e-13 * dr and int(ng) == int(nr)
+
+
+def _small_rhd(kappa_mode=0, sigma=1.0):
+    lay = I.make_layout([[0, 0, 0], [8, 0, 0], [0, 8, 0]], [[8, 8, 12], [12, 16, 12], [8, 8, 12]],
+                        (20, 16, 12), 4)
+    prob = I.rhd_lognormal(layout=lay, seed=9, sigma=sigma, kappa_mode=kappa_mode,
+                           kappa0=1.0 if kappa_mode == 0 else 30.0)
+    prm = dict(prob.params)
+    prm["dx"] = 1.0 / 20
+    return lay, prob, prm
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_rhd_patches_ten_steps_fp64(torch_cuda, graph):
+    """RHD on a 3-patch periodic set with ragged tiles: 10 full steps (hydro +
+    N_sub radiation substeps + exchange) agree with the oracle to 1e-10 per
+    cell; dt and N_sub agree exactly; no Newton failure."""
+    lay, prob, prm = _small_rhd()
+    Ug, Rg, hg, st = _run_gpu_steps(lay, prob, prm, 10, graph=graph)
+    Ur, Rr, hr = _run_oracle_steps(lay, prob, prm, 10)
+    assert st[0] == 0, st
+    _check_dt(hg, hr)
+    e = G.max_rel_err(lay, Ug + Rg, Ur + Rr)
+    assert max(e) <= TOL_STEPS, e
+
+
+def test_rhd_kappa_rho_ten_steps_fp64(torch_cuda):
+    """kappa = kappa0 rho with optically thick cells (the optical-depth
+    correction active) and sigma_ln rho = 1.5."""
+    lay, prob, prm = _small_rhd(kappa_mode=1, sigma=1.5)
+    Ug, Rg, hg, st = _run_gpu_steps(lay, prob, prm, 10)
+    Ur, Rr, hr = _run_oracle_steps(lay, prob, prm, 10)
+    assert st[0] == 0, st
+    e = G.max_rel_err(lay, Ug + Rg, Ur + Rr)
+    assert max(e) <= TOL_STEPS, e
+
+
+def test_mixed_precision_error_bounds(torch_cuda):
+    """FP32 state and stencils with FP64 Newton / E_g / sums: relative L1 error
+    in rho, E and E_r against the FP64 oracle <= 1e-5 after 10 steps."""
+    prob = I.config("hydro32")
+    Ug, _, _, _ = _run_gpu_steps(prob.layout, prob, prob.params, 10, prec=1)
+    Ur, _, _ = _run_oracle_steps(prob.layout, prob, prob.params, 10)
+    l1 = G.rel_l1(prob.layout, [Ug[0], Ug[4]], [Ur[0], Ur[4]])
+    assert max(l1) <= TOL_MIXED_L1, l1
+    lay, prob, prm = _small_rhd()
+    Ug, Rg, _, st = _run_gpu_steps(lay, prob, prm, 10, prec=1)
+    Ur, Rr, _ = _run_oracle_steps(lay, prob, prm, 10)
+    assert st[0] == 0
+    l1 = G.rel_l1(lay, [Ug[0], Ug[4], Rg[0]], [Ur[0], Ur[4], Rr[0]])
+    assert max(l1) <= TOL_MIXED_L1, l1
+
+
+def test_stationary_contact_and_uniform_exact_on_gpu(torch_cuda):
+    """Sec. 3.1.2 on the GPU: the stationary contact stays exactly unchanged
+    (and so does a uniform moving state), in 3-D and through qk_step."""
+    torch = torch_cuda
+    N = 24
+    lay = I.single_box(N, 8, 8, ng=4)
+    U = I.zeros(lay, 5)
+    x = P.centres(N)
+    rho = np.where(x < 0.5, 1.4, 1.0)
+    lay.interior(U[0], 0)[...] = rho[None, None, :]
+    lay.interior(U[4], 0)[...] = 1.0 / 0.4
+    prob = I.Problem("contact", lay, dict(gamma=1.4, cfl=0.3, dx=1.0 / N, hydro_only=1), U)
+    Ug, _, _, _ = _run_gpu_steps(lay, prob, prob.params, 20)
+    for a, b in zip(Ug, U):
+        assert np.array_equal(G.interior(lay, a), G.interior(lay, b))
+
+
+def test_step_conserves_on_gpu(torch_cuda):
+    """Periodic FP64 RHD: sum rho exact to round-off, sum(E + (c/chat) E_r) and
+    sum(m + F/(c chat)) to round-off, measured with qk_conserved_sums."""
+    torch = torch_cuda
+    lay, prob, prm = _small_rhd()
+    ctx = _ctx(lay, prm)
+    dU, dR = G.dev(prob.U), G.dev(prob.R)
+    s0 = ctx.conserved_sums(dU, dR)
+    for _ in range(5):
+        ctx.step(dU, dR)
+    s1 = ctx.conserved_sums(dU, dR)
+    ctx.close()
+    assert abs(s1[0] - s0[0]) <= 1e-14 * abs(s0[0])
+    assert abs(s1[9] - s0[9]) <= 1e-13 * abs(s0[9])
+    for d in range(3):
+        assert abs(s1[10 + d] - s0[10 + d]) <= 1e-13 * abs(s0[9]) / 100.0
