@@ -30,7 +30,24 @@ if ROOT not in sys.path:
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-FP64_NOMINAL_TFLOPS = 1.25  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal)
+# ALU peaks from the unit counts and the maximum SM clock (152 SMs, 2.07 GHz):
+# FP64 2 FMA/clk/SM -> 1.26 TFLOP/s; FP32 128 FMA/clk/SM -> 80.6 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# Algorithmic flops per interior cell of one launch (add, sub, mul, div, sqrt),
+# counted on the oracle's formulas by oracle/count_flops.cpp on a seeded
+# workload: con2prim 13, PPM 21.3 per call, HLLC 119.6 per face, radiation
+# face work 283.4 (closures, HLL, optical depth), f = F/(c E_r) 6, exchange
+# 256.4 (4.2 Newton iterations); divergence 2 per variable and direction,
+# RK combine 2 (stage 1) or 5 (stage 2) per variable.
+ALGO_FLOPS = {
+    "hydro1": 13 + 3 * (5 * 21.3 + 119.6) + 30 + 10 + 10,
+    "hydro2": 13 + 3 * (5 * 21.3 + 119.6) + 30 + 10 + 25,
+    "rad1": 6 + 3 * (4 * 21.1 + 283.4) + 24 + 8 + 8,
+    "rad2": 6 + 3 * (4 * 21.1 + 283.4) + 24 + 8 + 20,
+    "exchange": 256.4,
+}
 
 # kernels launched per step (captured in one CUDA graph; substeps beyond N_sub
 # are predicated off but still launched)
@@ -143,7 +160,7 @@ def algorithmic_bytes_per_cell(kernel: str, elem: int) -> float:
     return vals * elem
 
 
-def cpu_baseline(precision: str, budget_s: float = 20.0):
+def cpu_baseline(precision: str, budget_s: float = 12.0):
     """The oracle as it stands, single-threaded on the host, on a bounded sample
     of the same workload: one RHD update of a 32^3 periodic box drawn with the
     same generators and parameters (same N_sub,max, CFL, chat rule)."""
@@ -160,7 +177,7 @@ def cpu_baseline(precision: str, budget_s: float = 20.0):
         rc, ts, _ = O.step(g, p, U, R)
         steps += 1
         el = time.perf_counter() - t0
-        if el > budget_s or steps >= 3:
+        if el > budget_s or steps >= 12:
             break
     cells = prob.layout.ncells
     return {"value": cells * steps / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
@@ -214,6 +231,41 @@ def time_kernel(torch, fn, reps, stream):
     ev1.record(stream)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1) / 1e3 / reps
+
+
+def run_variants(args, steps=5, warmup=3):
+    """Cell-updates/s of the other precision / physics combinations on the same
+    GPU (device time over `steps` full updates after `warmup`)."""
+    import torch
+    from paper_2110_01792_gb300 import qk
+    out = {}
+    for name, prec in (("rhd128", "fp32"), ("hydro128", "fp64"), ("hydro128", "fp32"),
+                       ("rhd128", "fp64")):
+        if name == args.workload and prec == args.precision:
+            continue
+        prob = workload(name)
+        p = qk.FP64 if prec == "fp64" else qk.FP32_MIXED
+        tdt = torch.float64 if p == qk.FP64 else torch.float32
+        ctx = qk.Context(prob.layout, prob.params, p)
+        U = [torch.from_numpy(a).cuda().to(tdt) for a in prob.U]
+        R = None if prob.R is None else [torch.from_numpy(a).cuda().to(tdt) for a in prob.R]
+        for _ in range(warmup):
+            ctx.step(U, R)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            ctx.step(U, R)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        st = ctx.status()
+        ctx.close()
+        out[f"{name}_{prec}"] = {"value": prob.layout.ncells * steps / t, "unit": "cell-updates/s",
+                                 "ms_per_step": 1e3 * t / steps, "steps": steps,
+                                 "status_ok": st[0] == qk.OK}
+    return out
 
 
 def run_ours(args):
@@ -313,8 +365,6 @@ def run_ours(args):
     # ---- dominant kernel, timed alone through its entry point ----
     pk, pk_kind = peaks()
     reps = 20
-    for a in U + (R or []):
-        pass
     if hydro_only:
         U1 = [torch.empty_like(a) for a in U]
         ctx.fill_ghosts(U)
@@ -328,13 +378,23 @@ def run_ours(args):
         kname = "rad1"
         t_k = time_kernel(torch, lambda: ctx.rad_stage(1, R, None, R1, U[0], dtr), reps, stream)
     bytes_launch = algorithmic_bytes_per_cell(kname, elem) * cells
-    achieved = bytes_launch / t_k / 1e9
-    peak = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
-    roofline = {"bound": "hbm", "kernel": {"hydro1": "hydro_stage_kernel<1>",
-                                            "rad1": "rad_stage_kernel<1>"}[kname],
-                "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": pk_kind,
-                "launch_s": t_k, "algorithmic_bytes_per_launch": bytes_launch}
+    flops_launch = ALGO_FLOPS[kname] * cells
+    hbm_ach = bytes_launch / t_k / 1e9
+    hbm_peak = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
+    alu_peak = FP64_PEAK_TFLOPS if prec == qk.FP64 else FP32_PEAK_TFLOPS
+    alu_ach = flops_launch / t_k / 1e12
+    kern = {"hydro1": "hydro_stage_kernel<%s,1>", "rad1": "rad_stage_kernel<%s,1>"}[kname] % (
+        "double" if prec == qk.FP64 else "float")
+    hbm = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+           "frac": hbm_ach / hbm_peak, "peak_source": f"{pk_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
+           "frac": alu_ach / alu_peak,
+           "peak_source": ("FP64" if prec == qk.FP64 else "FP32") +
+                          " unit counts x 2.07 GHz (no measured FP64/FP32 peak in MEASURED_PEAKS.json)"}
+    main_, other = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
+    roofline = dict(main_, kernel=kern, traffic=None, launch_s=t_k,
+                    algorithmic_bytes_per_launch=bytes_launch,
+                    algorithmic_flops_per_launch=flops_launch, other=other)
 
     ctx.close()
     if rank != 0:
@@ -342,6 +402,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(args.precision)
+    variants = None if args.no_variants or world > 1 else run_variants(args)
     nl = launches_per_step(hydro_only, int(prob.params.get("nsub_max", 10)))
     line = {
         "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
@@ -357,6 +418,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": nl * args.steps,
         "clocks": clk,
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -372,6 +434,7 @@ def main():
     ap.add_argument("--workload", default="rhd128")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

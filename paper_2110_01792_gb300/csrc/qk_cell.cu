@@ -32,54 +32,54 @@ template <typename T>
 __device__ __forceinline__ double load_d(const T *p, long long e) { return (double)p[e]; }
 
 // Newton-Raphson on (E_g, E_r) for one cell (Sec. 2.2.3, eqs. delta_er and
-// delta_eg), FP64.  R = dt rho kappa_P chat (a_r T^4 - E_r) (the '4 pi B' of
-// the paper read as chat a_r T^4), F_G = (E_g - E_g0) + (c/chat) R,
+// delta_eg).  R = dt rho kappa_P chat (a_r T^4 - E_r) (the '4 pi B' of the
+// paper read as chat a_r T^4), F_G = (E_g - E_g0) + (c/chat) R,
 // F_R = (E_r - E_r0) - R; convergence |F_G/E_tot| < eps and
 // |(c/chat) F_R / E_tot| < eps, E_tot = E_g0 + (c/chat) E_r0; the update of
-// the iterate that passes is applied, then the loop stops.  Returns the
-// iteration count, or -1 after max_iter iterations.
-__device__ __forceinline__ int newton_exchange(const qk_params &p, double rho, double Eg0,
-                                               double Er0, double dt, double &Eg_out,
-                                               double &Er_out) {
-  const double kP = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_P * rho : p.kappa_P;
-  const double cr = p.c / p.chat;
-  const double inv_Etot = 1.0 / (Eg0 + cr * Er0);
-  const double k = dt * rho * kP * p.chat;       // dt rho kappa_P chat
-  const double dFG_dEr = -p.c * dt * rho * kP;
-  const double dFR_dEr = 1.0 + k;
+// the iterate that passes is applied, then the loop stops.  The 2x2
+// elimination of eqs. delta_er / delta_eg is evaluated with one division:
+// with G = dF_G/dE_g, eta = (dR/dE_g)/G,
+//   dE_r = -(F_R G + R' F_G) / D1,  D1 = (dF_R/dE_r) G + R' (dF_G/dE_r),
+//   dE_g = -(F_G + dE_r dF_G/dE_r) / G,
+// and 1/D1, 1/G taken from the single reciprocal of D1 G.  Starts from
+// (Eg, Er) (the cell state, or a warm start); returns the iteration count,
+// or -1 after max_iter iterations.
+template <typename R_>
+__device__ __forceinline__ int newton_exchange(const qk_params &p, R_ Eg0, R_ Er0, R_ k, R_ cr,
+                                               R_ inv_Etot, R_ inv_rcv, R_ eps, int max_iter,
+                                               R_ &Eg, R_ &Er) {
+  const R_ a_r = (R_)p.a_r;
+  const R_ dFG_dEr = -cr * k;     // -c dt rho kappa_P
+  const R_ dFR_dEr = R_(1) + k;
   const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
-  const double inv_rcv = alpha_eos ? 0.0 : 1.0 / (rho * p.c_v);
-  const double dT4_alpha = alpha_eos ? 4.0 / p.alpha_eos : 0.0;
-  double Eg = Eg0, Er = Er0;
+  const R_ dT4_alpha = alpha_eos ? (R_)(4.0 / p.alpha_eos) : R_(0);
   bool conv = false;
   int it = 0;
-  for (it = 0; it < p.max_iter; ++it) {
-    double T4, dT4;
+  for (it = 0; it < max_iter; ++it) {
+    R_ T4, dT4;
     if (alpha_eos) {
       T4 = dT4_alpha * Eg;
       dT4 = dT4_alpha;
     } else {
-      const double Tg = Eg * inv_rcv;
-      const double T2 = Tg * Tg;
+      const R_ Tg = Eg * inv_rcv;
+      const R_ T2 = Tg * Tg;
       T4 = T2 * T2;
-      dT4 = 4.0 * T2 * Tg * inv_rcv;
+      dT4 = R_(4) * T2 * Tg * inv_rcv;
     }
-    const double R = k * (p.a_r * T4 - Er);
-    const double FG = (Eg - Eg0) + cr * R;
-    const double FR = (Er - Er0) - R;
-    conv = fabs(FG * inv_Etot) < p.eps_newton && fabs(cr * FR * inv_Etot) < p.eps_newton;
-    const double dRdEg = k * p.a_r * dT4;
-    const double dFG_dEg = 1.0 + cr * dRdEg;
-    const double inv_G = 1.0 / dFG_dEg;
-    const double eta = dRdEg * inv_G;  // -(dF_R/dE_g)/(dF_G/dE_g), dF_R/dE_g = -dR/dE_g
-    const double dEr = -(FR + eta * FG) / (dFR_dEr + eta * dFG_dEr);
-    const double dEg = -(FG + dEr * dFG_dEr) * inv_G;
+    const R_ Rr = k * (a_r * T4 - Er);
+    const R_ FG = (Eg - Eg0) + cr * Rr;
+    const R_ FR = (Er - Er0) - Rr;
+    conv = fabs(FG * inv_Etot) < eps && fabs(cr * FR * inv_Etot) < eps;
+    const R_ dRdEg = k * a_r * dT4;
+    const R_ G = R_(1) + cr * dRdEg;
+    const R_ D1 = dFR_dEr * G + dRdEg * dFG_dEr;
+    const R_ inv = R_(1) / (D1 * G);
+    const R_ dEr = -(FR * G + dRdEg * FG) * (G * inv);
+    const R_ dEg = -(FG + dEr * dFG_dEr) * (D1 * inv);
     Er += dEr;
     Eg += dEg;
     if (conv) break;
   }
-  Eg_out = Eg;
-  Er_out = Er;
   return conv ? it + 1 : -1;
 }
 
@@ -89,6 +89,8 @@ __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, 
   if (skip_substep(dts)) return;
   const double dt = dt_of(dts);
   const double chat = p.chat, c = p.c;
+  const double cr = c / chat, icc = 1.0 / (chat * c), rc = chat / c;
+  const double inv_cv = p.eos == QK_EOS_ALPHA_T3 ? 0.0 : 1.0 / p.c_v;
   int my_max = 0;
   unsigned my_flags = 0;
   unsigned long long my_bad = ~0ull;
@@ -98,11 +100,34 @@ __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, 
     const double rho = load_d(U.f[0], e);
     double m[3] = {load_d(U.f[1], e), load_d(U.f[2], e), load_d(U.f[3], e)};
     const double E = load_d(U.f[4], e);
-    const double Ekin0 = 0.5 * ((m[0] * m[0] + m[1] * m[1]) + m[2] * m[2]) / rho;
-    const double Eg0 = E - Ekin0;
     const double Er0 = load_d(R.f[0], e);
-    double Eg, Er;
-    const int it = newton_exchange(p, rho, Eg0, Er0, dt, Eg, Er);
+    const double kP = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_P * rho : p.kappa_P;
+    const double kF = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_R * rho : p.kappa_R;
+    const double m2 = (m[0] * m[0] + m[1] * m[1]) + m[2] * m[2];
+    // one reciprocal serves 1/rho and the flux damping 1/(1 + rho kF chat dt)
+    const double Dm = 1.0 + rho * kF * chat * dt;
+    const double inv_rho_Dm = 1.0 / (rho * Dm);
+    const double inv_rho = Dm * inv_rho_Dm;
+    const double damp = rho * inv_rho_Dm;
+    const double Ekin0 = 0.5 * m2 * inv_rho;
+    const double Eg0 = E - Ekin0;
+    const double inv_Etot = 1.0 / (Eg0 + cr * Er0);
+    const double k = dt * rho * kP * chat;
+    const double inv_rcv = inv_rho * inv_cv;
+    double Eg = Eg0, Er = Er0;
+    int it;
+    if (sizeof(T) == 4) {
+      // mixed precision: FP32 Newton to ~1e-6, then the FP64 iterations
+      float Egf = (float)Eg0, Erf = (float)Er0;
+      int itf = newton_exchange<float>(p, (float)Eg0, (float)Er0, (float)k, (float)cr,
+                                       (float)inv_Etot, (float)inv_rcv, 1e-6f, 12, Egf, Erf);
+      if (itf > 0 && Egf > 0.0f && Erf > 0.0f && isfinite(Egf) && isfinite(Erf)) {
+        Eg = Egf;
+        Er = Erf;
+      }
+    }
+    it = newton_exchange<double>(p, Eg0, Er0, k, cr, inv_Etot, inv_rcv, p.eps_newton,
+                                 p.max_iter, Eg, Er);
     if (it < 0) {
       my_flags |= 1u << QK_ENOCONV;
       my_bad = min(my_bad, (unsigned long long)e);
@@ -110,22 +135,20 @@ __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, 
       my_max = max(my_max, it);
     }
     // flux source (backward Euler) and the equal and opposite momentum change
-    const double kF = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_R * rho : p.kappa_R;
-    const double damp = 1.0 / (1.0 + rho * kF * chat * dt);
     double mn[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const double F0 = load_d(R.f[1 + a], e);
       const double Fn = F0 * damp;
-      mn[a] = m[a] - (Fn - F0) / (chat * c);
+      mn[a] = m[a] - (Fn - F0) * icc;
       R.f[1 + a][e] = (T)Fn;
       U.f[1 + a][e] = (T)mn[a];
     }
     // work of the radiation force through the kinetic-energy change
-    const double Ekin1 = 0.5 * ((mn[0] * mn[0] + mn[1] * mn[1]) + mn[2] * mn[2]) / rho;
+    const double Ekin1 = 0.5 * ((mn[0] * mn[0] + mn[1] * mn[1]) + mn[2] * mn[2]) * inv_rho;
     const double dEkin = Ekin1 - Ekin0;
     U.f[4][e] = (T)(Eg + (Ekin0 + dEkin));
-    const double Er_new = Er - (chat / c) * dEkin;
+    const double Er_new = Er - rc * dEkin;
     R.f[0][e] = (T)Er_new;
     if (!(Eg > 0.0) || !(Er_new > 0.0)) {
       my_flags |= 1u << QK_ENEGATIVE;
@@ -170,27 +193,39 @@ cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, voi
 }
 
 // -------------------------------------------------- signal speed, dt -----
-// max(|v| + c_s) with IEEE round-to-nearest operations in the order
-// |v| = sqrt((vx^2 + vy^2) + vz^2), c_s = sqrt(gamma P / rho),
-// E_g = E - (rho/2) v^2 (no contraction), so that the step size is
-// reproducible bit for bit.
+// max(|v| + c_s) over the interior cells (Sec. 2.2.1, eq. signal), with
+// |v| = sqrt((vx^2 + vy^2) + vz^2) and c_s = sqrt(gamma P / rho); FP32 state
+// uses the FP32 con2prim (error-free internal-energy recovery).
+template <typename T>
+__device__ __forceinline__ double cell_speed(const F5<T> &U, long long e, double gamma);
+template <>
+__device__ __forceinline__ double cell_speed<double>(const F5<double> &U, long long e,
+                                                     double gamma) {
+  const double rho = U.f[0][e];
+  const double inv = 1.0 / rho;
+  const double vx = U.f[1][e] * inv, vy = U.f[2][e] * inv, vz = U.f[3][e] * inv;
+  const double v2 = (vx * vx + vy * vy) + vz * vz;
+  const double P = (gamma - 1.0) * (U.f[4][e] - 0.5 * rho * v2);
+  return sqrt(v2) + sqrt(gamma * P * inv);
+}
+template <>
+__device__ __forceinline__ double cell_speed<float>(const F5<float> &U, long long e,
+                                                    double gamma) {
+  float u[5], w[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
+  con2prim<float>(u, gamma, w);
+  const float v2 = (w[1] * w[1] + w[2] * w[2]) + w[3] * w[3];
+  return (double)(qsqrt(v2) + qsqrt((float)gamma * w[4] * qrcp(w[0])));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) max_speed_kernel(Geometry g, double gamma, F5<T> U,
                                                         StepInfo *si) {
   double best = 0.0;
   for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < g.ncells;
        cidx += (long long)gridDim.x * blockDim.x) {
-    const long long e = cell_to_elem(g, cidx);
-    const double rho = (double)U.f[0][e];
-    const double vx = __ddiv_rn((double)U.f[1][e], rho);
-    const double vy = __ddiv_rn((double)U.f[2][e], rho);
-    const double vz = __ddiv_rn((double)U.f[3][e], rho);
-    const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
-    const double Eg = __dsub_rn((double)U.f[4][e], __dmul_rn(__dmul_rn(0.5, rho), v2));
-    const double P = __dmul_rn(__dsub_rn(gamma, 1.0), Eg);
-    const double cs = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, P), rho));
-    const double sp = __dadd_rn(__dsqrt_rn(v2), cs);
-    best = fmax(best, sp);
+    best = fmax(best, cell_speed<T>(U, cell_to_elem(g, cidx), gamma));
   }
   for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
   __shared__ double wbest[8];

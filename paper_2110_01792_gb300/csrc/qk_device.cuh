@@ -9,8 +9,9 @@
 namespace qk {
 
 // Conserved -> primitive (Sec. 2.2.1): v = m / rho, E_g = E - rho v^2 / 2,
-// P = (gamma - 1) E_g.  In mixed precision the internal energy is recovered in
-// FP64 (cancellation of E against the kinetic energy), the rest in FP32.
+// P = (gamma - 1) E_g.  In mixed precision the internal energy is recovered
+// with ~48-bit error-free arithmetic (cancellation of E against the kinetic
+// energy), the rest in FP32.
 template <typename T>
 __device__ __forceinline__ void con2prim(const T u[5], double gamma, T w[5]);
 
@@ -27,18 +28,61 @@ __device__ __forceinline__ void con2prim<double>(const double u[5], double gamma
   w[4] = (gamma - 1.0) * Eg;
 }
 
+// Error-free transformations (Knuth's TwoSum, FMA TwoProduct) for the FP32
+// path: a value carried as hi + lo holds about 48 significant bits.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Division, reciprocal and square root: IEEE in FP64; in FP32 the hardware
+// approximations (a few ulp), which the FP32 path's error budget absorbs and
+// which avoid the ~60-instruction IEEE FP32 division sequence.
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qrcp(double b) { return 1.0 / b; }
+__device__ __forceinline__ float qrcp(float b) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+  return r;
+}
+__device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float qsqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Mixed precision: the internal energy E_g = E - |m|^2/(2 rho) is recovered
+// with error-free transformations on the FP32 pipe (|m|^2 by FMA TwoProduct
+// and TwoSum, the division and the subtraction in hi + lo form), which is as
+// accurate as an FP64 recovery relative to the FP32-stored E and costs no FP64
+// instruction (one FP64 instruction occupies ~64 FP32 issue slots on GB300).
 template <>
 __device__ __forceinline__ void con2prim<float>(const float u[5], double gamma, float w[5]) {
-  float rho = u[0];
-  float inv = 1.0f / rho;
+  const float rho = u[0];
+  float inv = qrcp(rho);
+  inv = inv * fmaf(-rho, inv, 2.0f);  // one Newton step: ~1 ulp
   w[0] = rho;
   w[1] = u[1] * inv;
   w[2] = u[2] * inv;
   w[3] = u[3] * inv;
-  double m2 = ((double)u[1] * (double)u[1] + (double)u[2] * (double)u[2]) +
-              (double)u[3] * (double)u[3];
-  double Eg = (double)u[4] - 0.5 * m2 / (double)rho;
-  w[4] = (float)((gamma - 1.0) * Eg);
+  float px = u[1] * u[1], py = u[2] * u[2], pz = u[3] * u[3];
+  float ex = fmaf(u[1], u[1], -px), ey = fmaf(u[2], u[2], -py), ez = fmaf(u[3], u[3], -pz);
+  float s1, t1, s2, t2;
+  two_sum(px, py, s1, t1);
+  two_sum(s1, pz, s2, t2);
+  const float lo = ((t1 + t2) + (ex + ey)) + ez;
+  // q = (s2 + lo) / rho as qh + ql
+  const float qh = s2 * inv;
+  const float r = fmaf(-qh, rho, s2) + lo;
+  const float ql = r * inv;
+  // E_g = E - (qh + ql)/2
+  float d, dl;
+  two_sum(u[4], -0.5f * qh, d, dl);
+  const float Eg = d + (dl - 0.5f * ql);
+  w[4] = (float)(gamma - 1.0) * Eg;
 }
 
 // PPM reconstruction of one cell from the stencil s0..s4 = q_{i-2..i+2}
@@ -89,15 +133,15 @@ __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm
   const T rR = wR[0], uR = wR[1 + D], aR_ = wR[1 + A], bR = wR[1 + B], pR = wR[4];
   const T EL = pL * gm1inv + T(0.5) * rL * (uL * uL + (aL_ * aL_ + bL * bL));
   const T ER = pR * gm1inv + T(0.5) * rR * (uR * uR + (aR_ * aR_ + bR * bR));
-  const T cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+  const T cL = qsqrt(qdiv(gamma * pL, rL)), cR = qsqrt(qdiv(gamma * pR, rR));
   const T abar = T(0.5) * (cL + cR), rbar = T(0.5) * (rL + rR);
   const T ppvrs = T(0.5) * (pL + pR) - T(0.5) * (uR - uL) * rbar * abar;
   const T ps = max(T(0), ppvrs);
-  const T qL = ps <= pL ? T(1) : sqrt(T(1) + g1 * (ps / pL - T(1)));
-  const T qR = ps <= pR ? T(1) : sqrt(T(1) + g1 * (ps / pR - T(1)));
+  const T qL = ps <= pL ? T(1) : qsqrt(T(1) + g1 * (qdiv(ps, pL) - T(1)));
+  const T qR = ps <= pR ? T(1) : qsqrt(T(1) + g1 * (qdiv(ps, pR) - T(1)));
   const T SL = uL - cL * qL, SR = uR + cR * qR;
   const T mL = rL * (SL - uL), mR = rR * (SR - uR);
-  const T Ss = (pR - pL + uL * mL - uR * mR) / (mL - mR);
+  const T Ss = qdiv(pR - pL + uL * mL - uR * mR, mL - mR);
   // upwind side K of the star region (tie S* = 0 -> left)
   const bool left = Ss >= T(0);
   const T rK = left ? rL : rR, uK = left ? uL : uR, aK = left ? aL_ : aR_;
@@ -106,9 +150,9 @@ __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm
   const T mK = rK * uK;
   // physical fluxes of K
   const T FK0 = mK, FKn = mK * uK + pK, FKa = mK * aK, FKb = mK * bK, FKe = uK * (EK + pK);
-  const T ratio = (SK - uK) / (SK - Ss);
+  const T ratio = qdiv(SK - uK, SK - Ss);
   const T fac = rK * ratio;
-  const T Ue = ratio * (EK + rK * (Ss - uK) * (Ss + pK / (rK * (SK - uK))));
+  const T Ue = ratio * (EK + rK * (Ss - uK) * (Ss + qdiv(pK, rK * (SK - uK))));
   T Fs0 = FK0 + SK * (fac - rK);
   T Fsn = FKn + SK * (fac * Ss - mK);
   T Fsa = FKa + SK * (fac * aK - rK * aK);
@@ -129,23 +173,39 @@ __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm
   F[4] = Fse;
 }
 
-// Levermore closure (eq. M1_closure): column D of the Eddington tensor
-// T = P_r / E_r for the reduced flux f, with |f| rescaled to 1 for the closure
-// when |f| > 1 and the n n term dropped when f = 0 (Sec. 2.2.2).  Written with
-// n_i n_D = f_i f_D / |f|^2, so the rescaling never needs |f| itself:
-//   T_iD = (1 - chi)/2 delta_iD + (3 chi - 1)/2 f_i f_D / |f|^2,
-//   chi = (3 + 4 fc^2) / (5 + 2 sqrt(4 - 3 fc^2)),  fc^2 = min(|f|^2, 1).
-template <typename T, int D>
-__device__ __forceinline__ void eddington_col(T fx, T fy, T fz, T &Tx, T &Ty, T &Tz) {
+// Levermore closure (eq. M1_closure) as the two coefficients of the Eddington
+// tensor T = P_r / E_r = a I + b f f for the reduced flux f, with |f| rescaled
+// to 1 for the closure when |f| > 1 and the n n term dropped when f = 0
+// (Sec. 2.2.2).  With fc^2 = min(|f|^2, 1), s = sqrt(4 - 3 fc^2),
+// D = 5 + 2 s, chi = (3 + 4 fc^2)/D:
+//   a = (1 - chi)/2 = (1 + s - 2 fc^2)/D,
+//   b = (3 chi - 1)/(2 |f|^2) = (2 + 6 fc^2 - s)/(D |f|^2),
+// so n_i n_j = f_i f_j / |f|^2 needs no |f| and one division serves both.
+template <typename T>
+__device__ __forceinline__ void levermore_ab(T fx, T fy, T fz, T &a, T &b) {
   const T f2 = (fx * fx + fy * fy) + fz * fz;
   const T fc2 = min(f2, T(1));
-  const T chi = (T(3) + T(4) * fc2) / (T(5) + T(2) * sqrt(T(4) - T(3) * fc2));
-  const T a = T(0.5) * (T(1) - chi);
-  const T bc = f2 > T(0) ? T(0.5) * (T(3) * chi - T(1)) / f2 : T(0);
+  const T s = qsqrt(T(4) - T(3) * fc2);
+  const T D = T(5) + T(2) * s;
+  if (f2 > T(0)) {
+    const T r = qrcp(D * f2);
+    a = (T(1) + s - T(2) * fc2) * (f2 * r);
+    b = (T(2) + T(6) * fc2 - s) * r;
+  } else {
+    a = qdiv(T(1) + s, D);
+    b = T(0);
+  }
+}
+
+// Column D of the Eddington tensor.
+template <typename T, int D>
+__device__ __forceinline__ void eddington_col(T fx, T fy, T fz, T &Tx, T &Ty, T &Tz) {
+  T a, b;
+  levermore_ab<T>(fx, fy, fz, a, b);
   const T fD = D == 0 ? fx : (D == 1 ? fy : fz);
-  Tx = bc * fx * fD + (D == 0 ? a : T(0));
-  Ty = bc * fy * fD + (D == 1 ? a : T(0));
-  Tz = bc * fz * fD + (D == 2 ? a : T(0));
+  Tx = b * fx * fD + (D == 0 ? a : T(0));
+  Ty = b * fy * fD + (D == 1 ? a : T(0));
+  Tz = b * fz * fD + (D == 2 ? a : T(0));
 }
 
 // Diagonal element T_DD only (for the HLL wavespeed).

@@ -8,11 +8,17 @@
 
 namespace qk {
 
+// FP64 keeps the cell-average closure coefficients (a, b) of every slot next
+// to a face (computed once per cell, shared by the three directions); FP32
+// recomputes sqrt(T_DD) per line position instead, which is cheap on the FP32
+// pipe and keeps three CTAs per SM.
 template <typename T> struct RadSmem {
-  T prim[4][NCROSS];   // E_r, f_x, f_y, f_z of the tile and its cross halo
-  T rk[NCROSS];        // rho kappa_R of the cell
-  T rec[8][NREC];      // qL, qR of each reconstructed variable
-  T sq[NREC];          // sqrt(T_DD) of the cell-average state at each position
+  static constexpr bool kAB = sizeof(T) == 8;
+  T prim[4][NCROSS];               // E_r, f_x, f_y, f_z of the tile and its cross halo
+  T rk[NCROSS];                    // rho kappa_R of the cell
+  T ab[2][kAB ? NCROSS : 1];       // FP64: Levermore a, b of the cell-average state
+  T rec[8][NREC];                  // qL, qR of each reconstructed variable
+  T sq[kAB ? 1 : NREC];            // FP32: sqrt(T_DD) of the cell average per position
   T flux[4][NFLUX];
 };
 
@@ -20,8 +26,33 @@ template <typename T> __device__ __forceinline__ T kappa_of(const qk_params &p, 
   return p.kappa_mode == QK_KAPPA_RHO ? (T)k * rho : (T)k;
 }
 
+// Stage one cross slot: E_r, f = F / (c E_r) (one reciprocal), rho kappa_R,
+// and in FP64 the closure coefficients of the cell average when the slot is
+// adjacent to a face of the tile (within one cell of the valid region).
+template <typename T>
+__device__ __forceinline__ void load_slot(RadSmem<T> &sm, int s, const T u[4], T c, T r,
+                                          const qk_params &p, int i, int j, int k,
+                                          const int v[3]) {
+  const T inv = qrcp(c * u[0]);
+  const T fx = u[1] * inv, fy = u[2] * inv, fz = u[3] * inv;
+  sm.prim[0][s] = u[0];
+  sm.prim[1][s] = fx;
+  sm.prim[2][s] = fy;
+  sm.prim[3][s] = fz;
+  sm.rk[s] = r * kappa_of<T>(p, p.kappa_R, r);
+  if constexpr (RadSmem<T>::kAB) {
+    const bool near = i >= -1 && j >= -1 && k >= -1 && i <= v[0] && j <= v[1] && k <= v[2];
+    if (near) {
+      T a, b;
+      levermore_ab<T>(fx, fy, fz, a, b);
+      sm.ab[0][s] = a;
+      sm.ab[1][s] = b;
+    }
+  }
+}
+
 template <typename T, int D>
-__device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T c, T chat, T ccc, T U[4],
+__device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T c, T chat_c, T ccc, T U[4],
                                             T F[4]) {
   T Tx, Ty, Tz;
   eddington_col<T, D>(fx, fy, fz, Tx, Ty, Tz);
@@ -30,7 +61,7 @@ __device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T c, T chat, 
   U[1] = cE * fx;
   U[2] = cE * fy;
   U[3] = cE * fz;
-  F[0] = (chat / c) * U[1 + D];
+  F[0] = chat_c * U[1 + D];
   F[1] = ccc * (E * Tx);
   F[2] = ccc * (E * Ty);
   F[3] = ccc * (E * Tz);
@@ -41,6 +72,7 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
                                         T chat, int tau_corr, T (&acc)[NOWN][4]) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
   const T ccc = c * chat;
+  const T chat_c = chat / c;
   for (int it = threadIdx.x; it < NREC; it += NT) {
     int pos, cc[3];
     item_cell<D>(it, NPOS, pos, cc[0], cc[1], cc[2]);
@@ -60,7 +92,8 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
       sm.rec[2 * q][it] = qL;
       sm.rec[2 * q + 1][it] = qR;
     }
-    sm.sq[it] = sqrt(eddington_diag<T, D>(sm.prim[1][s[2]], sm.prim[2][s[2]], sm.prim[3][s[2]]));
+    if constexpr (!RadSmem<T>::kAB)
+      sm.sq[it] = qsqrt(eddington_diag<T, D>(sm.prim[1][s[2]], sm.prim[2][s[2]], sm.prim[3][s[2]]));
   }
   __syncthreads();
   for (int it = threadIdx.x; it < NFLUX; it += NT) {
@@ -90,13 +123,22 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
       }
     }
     T UL[4], FL[4], UR[4], FR[4];
-    rad_flux_of<T, D>(wL[0], wL[1], wL[2], wL[3], c, chat, ccc, UL, FL);
-    rad_flux_of<T, D>(wR[0], wR[1], wR[2], wR[3], c, chat, ccc, UR, FR);
-    const T S = chat * max(sm.sq[il], sm.sq[ir]);
+    rad_flux_of<T, D>(wL[0], wL[1], wL[2], wL[3], c, chat_c, ccc, UL, FL);
+    rad_flux_of<T, D>(wR[0], wR[1], wR[2], wR[3], c, chat_c, ccc, UR, FR);
+    T S;
+    if constexpr (RadSmem<T>::kAB) {
+      // sqrt is monotone and correctly rounded: sqrt(max) == max(sqrt)
+      const T fa = sm.prim[1 + D][sa], fb = sm.prim[1 + D][sb];
+      const T Ta = sm.ab[0][sa] + sm.ab[1][sa] * fa * fa;
+      const T Tb = sm.ab[0][sb] + sm.ab[1][sb] * fb * fb;
+      S = chat * qsqrt(max(Ta, Tb));
+    } else {
+      S = chat * max(sm.sq[il], sm.sq[ir]);
+    }
     T eps = T(1);
     if (tau_corr) {
       const T tau = dx * T(0.5) * (sm.rk[sa] + sm.rk[sb]);
-      if (tau > T(1)) eps = T(1) / tau;
+      if (tau > T(1)) eps = qrcp(tau);
     }
     T out[4];
 #pragma unroll
@@ -152,13 +194,7 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
       T u[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) u[q] = src.f[q][e];
-      const T cE = c * u[0];
-      sm.prim[0][s] = u[0];
-      sm.prim[1][s] = u[1] / cE;
-      sm.prim[2][s] = u[2] / cE;
-      sm.prim[3][s] = u[3] / cE;
-      const T r = rho[e];
-      sm.rk[s] = r * kappa_of<T>(p, p.kappa_R, r);
+      load_slot<T>(sm, s, u, c, rho[e], p, i, j, k, v);
 #pragma unroll
       for (int q = 0; q < 4; ++q) own[m][q] = u[q];
     }
@@ -170,13 +206,7 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
       T u[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) u[q] = src.f[q][e];
-      const T cE = c * u[0];
-      sm.prim[0][s] = u[0];
-      sm.prim[1][s] = u[1] / cE;
-      sm.prim[2][s] = u[2] / cE;
-      sm.prim[3][s] = u[3] / cE;
-      const T r = rho[e];
-      sm.rk[s] = r * kappa_of<T>(p, p.kappa_R, r);
+      load_slot<T>(sm, s, u, c, rho[e], p, i, j, k, v);
     }
     __syncthreads();
     T acc[NOWN][4];
