@@ -183,6 +183,31 @@ int qk_set_graph(qk_ctx *ctx, int32_t enable);
 int qk_conserved_sums(qk_ctx *ctx, void *const hydro[5], void *const rad[4],
                       double out[QK_NSUMS], void *stream);
 
+/* Conservation sums without any GPU allocation.  There is no counterpart in the
+ * paper: this serves callers that cannot call cudaMalloc where they need the
+ * totals (a host callback or diagnostics hook, a process whose device memory
+ * is owned by an external allocator, or code that never creates a qk_ctx).
+ * It computes exactly what qk_conserved_sums computes (same kernels, same
+ * fixed reduction order, same output layout and units) for the patch set
+ * `boxes` (the layout of the field arrays, as given to qk_init_patches), and
+ * copies the QK_NSUMS results to the host array `out`.  All working memory
+ * (patch table, partial sums, result) lives in one static device array of
+ * QK_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads
+ * the library until the process exits; at most QK_NOALLOC_MAX_BOXES patches
+ * (QK_EINVAL beyond that).  On failure a message is written to `err` (a
+ * caller-owned buffer of `errlen` bytes; may be NULL).  The call
+ * allocates nothing and synchronises `stream`.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call outside any stream capture.  Every call
+ * overwrites the whole array, so nothing carries over between calls, but calls
+ * that overlap on the GPU (other streams, other host threads) race on it. */
+#define QK_NOALLOC_MAX_BOXES 4096
+#define QK_NOALLOC_SCRATCH_BYTES (576 * 1024)
+int qk_conserved_sums_noalloc(const qk_params *p, const qk_box *boxes, int32_t nbox,
+                              int32_t nghost, int32_t precision, void *const hydro[5],
+                              void *const rad[4], double out[QK_NSUMS], void *stream,
+                              char *err, int32_t errlen);
+
 /* Read the accumulated exchange status (synchronises `stream`):
  * *flags = bit (1 << QK_ENOCONV) | bit (1 << QK_ENEGATIVE); *first_bad = the
  * smallest element index of a failing cell (-1 if none); *max_iter = the

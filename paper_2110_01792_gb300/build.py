@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqk.so")
-SOURCES = ["qk_api.cu", "qk_hydro.cu", "qk_rad.cu", "qk_cell.cu"]
+SOURCES = ["qk_api.cu", "qk_hydro.cu", "qk_rad.cu", "qk_cell.cu", "qk_noalloc.cu"]
 HEADERS = ["qk_internal.cuh", "qk_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
