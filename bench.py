@@ -233,38 +233,109 @@ def time_kernel(torch, fn, reps, stream):
     return ev0.elapsed_time(ev1) / 1e3 / reps
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
+# (profiles/ncu_*_128.md), valid only while the kernel's sources hash to the
+# value recorded at capture time.
+NCU_TRAFFIC = {
+    ("rhd128", "rad_stage_kernel<double,1>"): (134.14e6, "rad", "f7000165b3bd"),
+    ("rhd128", "hydro_stage_kernel<double,1>"): (152.57e6, "hydro", "2332a5e22de0"),
+    ("rhd128", "rad_stage_kernel<float,1>"): (55.77e6, "rad", "f7000165b3bd"),
+    ("rhd128", "hydro_stage_kernel<float,1>"): (59.79e6, "hydro", "2332a5e22de0"),
+    ("rhd128", "exchange_kernel_mixed"): (95.42e6, "cell", "1f346e027e23"),
+}
+
+
+def _src_hash(kind: str) -> str:
+    import hashlib
+    cs = os.path.join(ROOT, "paper_2110_01792_gb300", "csrc")
+    files = {"rad": ["qk_rad.cu"], "hydro": ["qk_hydro.cu"], "cell": ["qk_cell.cu"]}[kind]
+    h = hashlib.sha1()
+    for f in files + ["qk_device.cuh", "qk_internal.cuh"]:
+        with open(os.path.join(cs, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(workload: str, kernel: str):
+    ent = NCU_TRAFFIC.get((workload, kernel))
+    if ent is None or _src_hash(ent[1]) != ent[2]:
+        return None
+    return ent[0]
+
+
+def run_kernel_only(args):
+    """Launch one stage kernel three times on the workload through the C ABI
+    (a small, self-contained case for ncu --set full)."""
+    import torch
+    import __graft_entry__
+    from paper_2110_01792_gb300 import qk
+    __graft_entry__.build()
+    prec = qk.FP64 if args.precision == "fp64" else qk.FP32_MIXED
+    tdt = torch.float64 if prec == qk.FP64 else torch.float32
+    prob = workload(args.workload)
+    ctx = qk.Context(prob.layout, prob.params, prec)
+    U = [torch.from_numpy(a).cuda().to(tdt) for a in prob.U]
+    R = None if prob.R is None else [torch.from_numpy(a).cuda().to(tdt) for a in prob.R]
+    ctx.fill_ghosts(U + (R or []))
+    dt, _, dtr, _ = ctx.timestep(U)
+    for _ in range(3):
+        if args.kernel_only == "hydro1":
+            ctx.hydro_stage(1, U, None, [torch.empty_like(a) for a in U], dt)
+        elif args.kernel_only == "rad1":
+            ctx.rad_stage(1, R, None, [torch.empty_like(a) for a in R], U[0], dtr)
+        else:
+            ctx.exchange(U, R, dtr)
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps({"kernel_only": args.kernel_only, "workload": args.workload,
+                      "precision": args.precision, "ok": True}))
+
+
 def run_variants(args, steps=5, warmup=3):
-    """Cell-updates/s of the other precision / physics combinations on the same
-    GPU (device time over `steps` full updates after `warmup`)."""
+    """Cell-updates/s of the other precision / physics / size combinations and
+    of the ~1700-patch set (batched persistent launches vs one launch per patch)
+    on the same GPU (device time over `steps` full updates after `warmup`)."""
     import torch
     from paper_2110_01792_gb300 import qk
     out = {}
-    for name, prec in (("rhd128", "fp32"), ("hydro128", "fp64"), ("hydro128", "fp32"),
-                       ("rhd128", "fp64")):
-        if name == args.workload and prec == args.precision:
+    specs = [("rhd128", "fp32", False, steps, warmup), ("hydro128", "fp64", False, steps, warmup),
+             ("hydro128", "fp32", False, steps, warmup), ("rhd128", "fp64", False, steps, warmup),
+             ("rhd256", "fp32", False, steps, warmup), ("hydro256", "fp32", False, steps, warmup),
+             ("patches", "fp32", False, 3, 2), ("patches", "fp32", True, 3, 2),
+             ("patches", "fp64", False, 2, 1)]
+    for name, prec, per_patch, st_, wu in specs:
+        if name == args.workload and prec == args.precision and not per_patch:
             continue
         prob = workload(name)
         p = qk.FP64 if prec == "fp64" else qk.FP32_MIXED
         tdt = torch.float64 if p == qk.FP64 else torch.float32
         ctx = qk.Context(prob.layout, prob.params, p)
+        ctx.set_launch_mode(per_patch)
         U = [torch.from_numpy(a).cuda().to(tdt) for a in prob.U]
         R = None if prob.R is None else [torch.from_numpy(a).cuda().to(tdt) for a in prob.R]
-        for _ in range(warmup):
+        del prob.U, prob.R
+        for _ in range(wu):
             ctx.step(U, R)
         torch.cuda.synchronize()
+        i0 = ctx.step_info()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(steps):
+        for _ in range(st_):
             ctx.step(U, R)
         e1.record()
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
-        st = ctx.status()
+        i1 = ctx.step_info()
+        stt = ctx.status()
         ctx.close()
-        out[f"{name}_{prec}"] = {"value": prob.layout.ncells * steps / t, "unit": "cell-updates/s",
-                                 "ms_per_step": 1e3 * t / steps, "steps": steps,
-                                 "status_ok": st[0] == qk.OK}
+        key = f"{name}_{prec}" + ("_per_patch_launches" if per_patch else "")
+        out[key] = {"value": prob.layout.ncells * st_ / t, "unit": "cell-updates/s",
+                    "ms_per_step": 1e3 * t / st_, "steps": st_,
+                    "nsub_mean": (i1[4] - i0[4]) / max(1.0, i1[5] - i0[5]),
+                    "patches": prob.layout.nbox, "status_ok": stt[0] == qk.OK}
+        del U, R
+        torch.cuda.empty_cache()
     return out
 
 
@@ -302,6 +373,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         ctx.step(U, R)
     torch.cuda.synchronize()
+    info_start = ctx.step_info()
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
@@ -327,23 +399,23 @@ def run_ours(args):
     cells = lay.ncells
     value = cells * args.steps * world / t_max
 
-    # ---- end to end through the public API with host buffers ----
-    hostU = [torch.from_numpy(a).to(tdt).pin_memory() for a in prob.U]
-    hostR = None if hydro_only else [torch.from_numpy(a).to(tdt).pin_memory() for a in prob.R]
-    outU = [torch.empty_like(h).pin_memory() for h in hostU]
-    outR = None if hydro_only else [torch.empty_like(h).pin_memory() for h in hostR]
-    fields_h = hostU + (hostR or [])
-    fields_o = outU + (outR or [])
+    info_end = ctx.step_info()
+    nsub_mean = (info_end[4] - info_start[4]) / max(1.0, info_end[5] - info_start[5])
+
+    # ---- end to end through the public API with a host-resident state ----
+    # the state lives in pinned host memory; every step copies it to the
+    # device, runs qk_step, and copies the updated state back (in place)
+    host = [d.cpu().pin_memory() for d in U + (R or [])]
     dfields = U + (R or [])
-    h2d = sum(h.numel() * h.element_size() for h in fields_h)
+    h2d = sum(h.numel() * h.element_size() for h in host)
     d2h = h2d
 
     def e2e_step():
-        for d, h in zip(dfields, fields_h):
+        for d, h in zip(dfields, host):
             d.copy_(h, non_blocking=True)
         ctx.step(U, R)
-        for o, d in zip(fields_o, dfields):
-            o.copy_(d, non_blocking=True)
+        for h, d in zip(host, dfields):
+            h.copy_(d, non_blocking=True)
 
     for _ in range(2):
         e2e_step()
@@ -362,39 +434,54 @@ def run_ours(args):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = cells * args.steps * world / float(te.item())
 
-    # ---- dominant kernel, timed alone through its entry point ----
+    # ---- dominant kernel: each stage kernel timed alone through its entry
+    # point (CUDA events on the launching stream), weighted by its launches
+    # per update; the largest share is reported against its roofline ----
     pk, pk_kind = peaks()
-    reps = 20
-    if hydro_only:
-        U1 = [torch.empty_like(a) for a in U]
-        ctx.fill_ghosts(U)
-        dt = ctx.timestep(U)[0]
-        kname = "hydro1"
-        t_k = time_kernel(torch, lambda: ctx.hydro_stage(1, U, None, U1, dt), reps, stream)
-    else:
+    reps = 10
+    times = {}
+    U1 = [torch.empty_like(a) for a in U]
+    ctx.fill_ghosts(U)
+    dt, _, dtr, _ = ctx.timestep(U)
+    times["hydro1"] = (time_kernel(torch, lambda: ctx.hydro_stage(1, U, None, U1, dt), reps,
+                                   stream), 1.0)
+    del U1
+    if not hydro_only:
         R1 = [torch.empty_like(a) for a in R]
         ctx.fill_ghosts(R + [U[0]])
-        dtr = ctx.timestep(U)[2]
-        kname = "rad1"
-        t_k = time_kernel(torch, lambda: ctx.rad_stage(1, R, None, R1, U[0], dtr), reps, stream)
+        times["rad1"] = (time_kernel(torch, lambda: ctx.rad_stage(1, R, None, R1, U[0], dtr),
+                                     reps, stream), nsub_mean)
+        del R1
+        Uc = [a.clone() for a in U]
+        Rc = [a.clone() for a in R]
+        times["exchange"] = (time_kernel(torch, lambda: ctx.exchange(Uc, Rc, dtr), reps, stream),
+                             nsub_mean)
+        ctx.status(reset=True)
+        del Uc, Rc
+    kname = max(times, key=lambda k: times[k][0] * times[k][1])
+    t_k = times[kname][0]
+    tname = "double" if prec == qk.FP64 else "float"
+    kern = {"hydro1": f"hydro_stage_kernel<{tname},1>", "rad1": f"rad_stage_kernel<{tname},1>",
+            "exchange": "exchange_kernel<double>" if prec == qk.FP64
+                        else "exchange_kernel_mixed"}[kname]
     bytes_launch = algorithmic_bytes_per_cell(kname, elem) * cells
     flops_launch = ALGO_FLOPS[kname] * cells
     hbm_ach = bytes_launch / t_k / 1e9
     hbm_peak = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
-    alu_peak = FP64_PEAK_TFLOPS if prec == qk.FP64 else FP32_PEAK_TFLOPS
+    fp64_unit = prec == qk.FP64 or kname == "exchange"  # the exchange is FP64 in both modes
+    alu_peak = FP64_PEAK_TFLOPS if fp64_unit else FP32_PEAK_TFLOPS
     alu_ach = flops_launch / t_k / 1e12
-    kern = {"hydro1": "hydro_stage_kernel<%s,1>", "rad1": "rad_stage_kernel<%s,1>"}[kname] % (
-        "double" if prec == qk.FP64 else "float")
     hbm = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
            "frac": hbm_ach / hbm_peak, "peak_source": f"{pk_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
            "frac": alu_ach / alu_peak,
-           "peak_source": ("FP64" if prec == qk.FP64 else "FP32") +
+           "peak_source": ("FP64" if fp64_unit else "FP32") +
                           " unit counts x 2.07 GHz (no measured FP64/FP32 peak in MEASURED_PEAKS.json)"}
     main_, other = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
-    roofline = dict(main_, kernel=kern, traffic=None, launch_s=t_k,
-                    algorithmic_bytes_per_launch=bytes_launch,
-                    algorithmic_flops_per_launch=flops_launch, other=other)
+    roofline = dict(main_, kernel=kern, traffic=ncu_traffic(args.workload, kern),
+                    launch_s=t_k, algorithmic_bytes_per_launch=bytes_launch,
+                    algorithmic_flops_per_launch=flops_launch, other=other,
+                    kernel_shares={k: v[0] * v[1] for k, v in times.items()})
 
     ctx.close()
     if rank != 0:
@@ -417,6 +504,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": nl * args.steps,
+        "nsub_mean": nsub_mean,
         "clocks": clk,
         "variants": variants,
     }
@@ -435,10 +523,14 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--kernel-only", choices=["hydro1", "rad1", "exchange"], default=None,
+                    help="launch one stage kernel 3 times and exit (for ncu captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.kernel_only:
+        run_kernel_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

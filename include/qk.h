@@ -170,6 +170,20 @@ int qk_timestep(qk_ctx *ctx, void *const hydro[5], double out[4], void *stream);
 int qk_step(qk_ctx *ctx, void *const hydro[5], void *const rad[4], double *dt_out,
             int32_t *nsub_out, void *stream);
 
+/* The device step record (synchronises `stream`): out[0] = dt, out[1] = N_sub,
+ * out[2] = dt_rad, out[3] = max(|v| + c_s) of the last timestep computed;
+ * out[4] = radiation substeps and out[5] = timesteps summed since the context
+ * was created. */
+int qk_step_info(qk_ctx *ctx, double out[6], void *stream);
+
+#define QK_LAUNCH_BATCHED 0   /* one persistent launch per stage over all patches */
+#define QK_LAUNCH_PER_PATCH 1 /* one launch per patch and stage (for comparison)  */
+
+/* Select how qk_step launches the hydro and radiation stage kernels (the
+ * default is QK_LAUNCH_BATCHED).  Results are identical; captured step graphs
+ * are dropped. */
+int qk_set_launch_mode(qk_ctx *ctx, int32_t mode);
+
 /* Enable (1, default) or disable (0) CUDA-graph capture in qk_step. */
 int qk_set_graph(qk_ctx *ctx, int32_t enable);
 

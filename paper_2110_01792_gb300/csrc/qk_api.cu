@@ -27,6 +27,8 @@ struct qk_ctx {
   Tile *d_tiles = nullptr;
   long long *d_cell0 = nullptr;
   int ntiles = 0;
+  std::vector<int> tile_start;  // first tile of each patch (tiles are grouped by patch)
+  int launch_mode = QK_LAUNCH_BATCHED;
   Copy *d_copies = nullptr;
   Chunk *d_chunks = nullptr;
   int ncopies = 0, nchunks = 0;
@@ -320,10 +322,14 @@ int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32
     cell0[b + 1] = cell0[b] + (long long)q.n[0] * q.n[1] * q.n[2];
   }
   std::vector<Tile> tiles;
-  for (int b = 0; b < nbox; ++b)
+  c->tile_start.assign(nbox + 1, 0);
+  for (int b = 0; b < nbox; ++b) {
+    c->tile_start[b] = (int)tiles.size();
     for (int z = 0; z < boxes[b].n[2]; z += TS)
       for (int y = 0; y < boxes[b].n[1]; y += TS)
         for (int x = 0; x < boxes[b].n[0]; x += TS) tiles.push_back(Tile{b, x, y, z});
+  }
+  c->tile_start[nbox] = (int)tiles.size();
   c->ntiles = (int)tiles.size();
   std::vector<Copy> copies;
   build_copies(c, copies);
@@ -389,6 +395,18 @@ int qk_set_params(qk_ctx *c, const qk_params *p) {
   int rc = check_params(c, p);
   if (rc) return rc;
   c->p = *p;
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  return QK_OK;
+}
+
+int qk_set_launch_mode(qk_ctx *c, int32_t mode) {
+  if (!c) return QK_EINVAL;
+  if (mode != QK_LAUNCH_BATCHED && mode != QK_LAUNCH_PER_PATCH)
+    return fail(c, QK_EINVAL, "unknown launch mode %d", mode);
+  c->launch_mode = mode;
   if (c->gexec) {
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
@@ -490,6 +508,39 @@ int qk_timestep(qk_ctx *c, void *const hydro[5], double out[4], void *stream) {
   return QK_OK;
 }
 
+// Stage launches: one persistent launch over the tiles of every patch
+// (QK_LAUNCH_BATCHED), or one launch per patch over its own tiles
+// (QK_LAUNCH_PER_PATCH, kept for comparison).
+static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *const *U1,
+                                  void *const *Uo, DtSrc dt, cudaStream_t s) {
+  const Geometry g = geom(c);
+  if (c->launch_mode == QK_LAUNCH_BATCHED)
+    return launch_hydro_stage(c->fp32, stage, g, c->p, U0, U1, Uo, dt, 0, s);
+  for (int b = 0; b < c->nbox; ++b) {
+    Geometry gb = g;
+    gb.tiles = c->d_tiles + c->tile_start[b];
+    gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
+    cudaError_t e = launch_hydro_stage(c->fp32, stage, gb, c->p, U0, U1, Uo, dt, 0, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t rad_launches(qk_ctx *c, int stage, void *const *R0, void *const *R1,
+                                void *const *Ro, const void *rho, DtSrc dt, cudaStream_t s) {
+  const Geometry g = geom(c);
+  if (c->launch_mode == QK_LAUNCH_BATCHED)
+    return launch_rad_stage(c->fp32, stage, g, c->p, R0, R1, Ro, rho, dt, 0, s);
+  for (int b = 0; b < c->nbox; ++b) {
+    Geometry gb = g;
+    gb.tiles = c->d_tiles + c->tile_start[b];
+    gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
+    cudaError_t e = launch_rad_stage(c->fp32, stage, gb, c->p, R0, R1, Ro, rho, dt, 0, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // The launch sequence of one full update (Sec. 2.2 operator split).
 static int enqueue_step(qk_ctx *c, void *const hydro[5], void *const rad[4], cudaStream_t s) {
   const Geometry g = geom(c);
@@ -501,17 +552,17 @@ static int enqueue_step(qk_ctx *c, void *const hydro[5], void *const rad[4], cud
   QK_CUDA(c, launch_max_speed(c->fp32, g, c->p, hydro, c->d_si, s));
   QK_CUDA(c, launch_timestep(c->p, c->d_si, s));
   QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, hydro, 5, none, s));
-  QK_CUDA(c, launch_hydro_stage(c->fp32, 1, g, c->p, hydro, nullptr, U1, dth, 0, s));
+  QK_CUDA(c, hydro_launches(c, 1, hydro, nullptr, U1, dth, s));
   QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, U1, 5, none, s));
-  QK_CUDA(c, launch_hydro_stage(c->fp32, 2, g, c->p, hydro, U1, hydro, dth, 0, s));
+  QK_CUDA(c, hydro_launches(c, 2, hydro, U1, hydro, dth, s));
   if (rad && !c->p.hydro_only) {
     QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, hydro, 1, none, s));
     for (int sub = 0; sub < c->p.nsub_max; ++sub) {
       const DtSrc dr{c->d_si, 0.0, 2, sub};
       QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, rad, 4, dr, s));
-      QK_CUDA(c, launch_rad_stage(c->fp32, 1, g, c->p, rad, nullptr, R1, hydro[0], dr, 0, s));
+      QK_CUDA(c, rad_launches(c, 1, rad, nullptr, R1, hydro[0], dr, s));
       QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, R1, 4, dr, s));
-      QK_CUDA(c, launch_rad_stage(c->fp32, 2, g, c->p, rad, R1, rad, hydro[0], dr, 0, s));
+      QK_CUDA(c, rad_launches(c, 2, rad, R1, rad, hydro[0], dr, s));
       QK_CUDA(c, launch_exchange(c->fp32, g, c->p, hydro, rad, dr, c->d_status, s));
     }
   }
@@ -563,6 +614,22 @@ int qk_step(qk_ctx *c, void *const hydro[5], void *const rad[4], double *dt_out,
     QK_CUDA(c, cudaStreamSynchronize(s));
     *nsub_out = (int32_t)c->h_buf[8];
   }
+  return QK_OK;
+}
+
+int qk_step_info(qk_ctx *c, double out[6], void *stream) {
+  if (!c) return QK_EINVAL;
+  if (!out) return fail(c, QK_EINVAL, "out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  QK_CUDA(c, cudaMemcpyAsync(c->h_buf + 24, c->d_si, sizeof(StepInfo), cudaMemcpyDeviceToHost, s));
+  QK_CUDA(c, cudaStreamSynchronize(s));
+  const StepInfo *h = (const StepInfo *)(c->h_buf + 24);
+  out[0] = h->dt;
+  out[1] = h->nsub;
+  out[2] = h->dtrad;
+  out[3] = h->smax;
+  out[4] = h->nsub_total;
+  out[5] = h->nsteps;
   return QK_OK;
 }
 

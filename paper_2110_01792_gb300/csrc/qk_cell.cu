@@ -83,6 +83,146 @@ __device__ __forceinline__ int newton_exchange(const qk_params &p, R_ Eg0, R_ Er
   return conv ? it + 1 : -1;
 }
 
+// Warp-aggregated status update of the exchange kernels.
+__device__ __forceinline__ void exchange_status(Status *st, int my_max, unsigned my_flags,
+                                                unsigned long long my_bad) {
+  const unsigned full = 0xffffffffu;
+  int wmax = __reduce_max_sync(full, my_max);
+  unsigned wflags = __reduce_or_sync(full, my_flags);
+  unsigned long long wbad = my_bad;
+  for (int o = 16; o > 0; o >>= 1) wbad = min(wbad, __shfl_xor_sync(full, wbad, o));
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&st->max_iter, wmax);
+    if (wflags) {
+      atomicOr(&st->flags, wflags);
+      atomicMin(&st->first_bad, wbad);
+    }
+  }
+}
+
+// Mixed-precision Newton for one cell: the residuals F_G, F_R and the
+// convergence test of Sec. 2.2.3 are evaluated in FP64 at the FP64 iterate,
+// the 2x2 correction (the same elimination as newton_exchange) is solved in
+// FP32 (iterative refinement: each iteration gains ~7 digits, so two
+// iterations from an FP32 warm start reach the 1e-10 tolerance).  Returns
+// the iteration count or -1.
+__device__ __forceinline__ int newton_refine(const qk_params &p, double Eg0, double Er0,
+                                             double k, double cr, double inv_Etot,
+                                             double inv_rcv, double &Eg, double &Er) {
+  const double a_r = p.a_r;
+  const float kf = (float)k, crf = (float)cr, arf = (float)p.a_r;
+  const float dFG_dEr = -crf * kf, dFR_dEr = 1.0f + kf;
+  const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
+  const double dT4_alpha = alpha_eos ? 4.0 / p.alpha_eos : 0.0;
+  bool conv = false;
+  int it = 0;
+  for (it = 0; it < p.max_iter; ++it) {
+    double T4;
+    float dT4;
+    if (alpha_eos) {
+      T4 = dT4_alpha * Eg;
+      dT4 = (float)dT4_alpha;
+    } else {
+      const double Tg = Eg * inv_rcv;
+      const double T2 = Tg * Tg;
+      T4 = T2 * T2;
+      const float Tf = (float)Tg;
+      dT4 = 4.0f * Tf * Tf * Tf * (float)inv_rcv;
+    }
+    const double Rr = k * (a_r * T4 - Er);
+    const double FG = (Eg - Eg0) + cr * Rr;
+    const double FR = (Er - Er0) - Rr;
+    conv = fabs(FG * inv_Etot) < p.eps_newton && fabs(cr * FR * inv_Etot) < p.eps_newton;
+    const float fg = (float)FG, fr = (float)FR;
+    const float dRdEg = kf * arf * dT4;
+    const float G = 1.0f + crf * dRdEg;
+    const float D1 = dFR_dEr * G + dRdEg * dFG_dEr;
+    const float inv = qrcp(D1 * G);
+    const float dEr = -(fr * G + dRdEg * fg) * (G * inv);
+    const float dEg = -(fg + dEr * dFG_dEr) * (D1 * inv);
+    Er += (double)dEr;
+    Eg += (double)dEg;
+    if (conv) break;
+  }
+  return conv ? it + 1 : -1;
+}
+
+// FP32-mixed exchange: FP32 state; the internal energy recovered with the
+// error-free FP32 transforms of con2prim; the Newton solve with FP64 residuals
+// and convergence test (FP32 warm start, then newton_refine); the flux
+// source, momentum and kinetic-energy work in FP32, the new total energy
+// accumulated in FP64 before the final rounding.
+__global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_params p,
+                                                              F5<float> U, F4<float> R,
+                                                              DtSrc dts, Status *st) {
+  if (skip_substep(dts)) return;
+  const double dt = dt_of(dts);
+  const double cr = p.c / p.chat;
+  const float icc = (float)(1.0 / (p.chat * p.c)), rc = (float)(p.chat / p.c);
+  const double inv_cv = p.eos == QK_EOS_ALPHA_T3 ? 0.0 : 1.0 / p.c_v;
+  int my_max = 0;
+  unsigned my_flags = 0;
+  unsigned long long my_bad = ~0ull;
+  for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < g.ncells;
+       cidx += (long long)gridDim.x * blockDim.x) {
+    const long long e = cell_to_elem(g, cidx);
+    float u[5], w[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
+    con2prim<float>(u, p.gamma, w);  // w[4] = (gamma-1) E_g with ~48-bit E_g
+    const float rho = u[0];
+    const float Er0f = R.f[0][e];
+    const double rho_d = (double)rho;
+    const double Eg0 = (double)w[4] * (1.0 / (p.gamma - 1.0));
+    const double Er0 = (double)Er0f;
+    const double kP = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_P * rho_d : p.kappa_P;
+    const double k = dt * rho_d * kP * p.chat;
+    const float rinv = qrcp(rho);
+    const double inv_rcv = (double)(rinv * (float)inv_cv);
+    const double inv_Etot = (double)qrcp((float)(Eg0 + cr * Er0));
+    // FP32 warm start
+    float Egf = (float)Eg0, Erf = Er0f;
+    const int itf = newton_exchange<float>(p, (float)Eg0, Er0f, (float)k, (float)cr,
+                                           (float)inv_Etot, (float)inv_rcv, 1e-6f, 12, Egf, Erf);
+    double Eg = Eg0, Er = Er0;
+    if (itf > 0 && Egf > 0.0f && Erf > 0.0f && isfinite(Egf) && isfinite(Erf)) {
+      Eg = Egf;
+      Er = Erf;
+    }
+    const int it = newton_refine(p, Eg0, Er0, k, cr, inv_Etot, inv_rcv, Eg, Er);
+    if (it < 0) {
+      my_flags |= 1u << QK_ENOCONV;
+      my_bad = min(my_bad, (unsigned long long)e);
+    } else {
+      my_max = max(my_max, it);
+    }
+    const float kF = p.kappa_mode == QK_KAPPA_RHO ? (float)p.kappa_R * rho : (float)p.kappa_R;
+    const float damp = qrcp(1.0f + rho * kF * (float)(p.chat * dt));
+    float mn[3];
+    float ke0 = 0.0f, ke1 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float F0 = R.f[1 + a][e];
+      const float Fn = F0 * damp;
+      mn[a] = u[1 + a] - (Fn - F0) * icc;
+      ke0 = fmaf(u[1 + a], u[1 + a], ke0);
+      ke1 = fmaf(mn[a], mn[a], ke1);
+      R.f[1 + a][e] = Fn;
+      U.f[1 + a][e] = mn[a];
+    }
+    const float Ekin1 = 0.5f * ke1 * rinv;
+    const float dEkin = 0.5f * (ke1 - ke0) * rinv;
+    U.f[4][e] = (float)(Eg + (double)Ekin1);
+    const double Er_new = Er - (double)(rc * dEkin);
+    R.f[0][e] = (float)Er_new;
+    if (!(Eg > 0.0) || !(Er_new > 0.0)) {
+      my_flags |= 1u << QK_ENEGATIVE;
+      my_bad = min(my_bad, (unsigned long long)e);
+    }
+  }
+  exchange_status(st, my_max, my_flags, my_bad);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, F5<T> U, F4<T> R,
                                                         DtSrc dts, Status *st) {
@@ -116,16 +256,6 @@ __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, 
     const double inv_rcv = inv_rho * inv_cv;
     double Eg = Eg0, Er = Er0;
     int it;
-    if (sizeof(T) == 4) {
-      // mixed precision: FP32 Newton to ~1e-6, then the FP64 iterations
-      float Egf = (float)Eg0, Erf = (float)Er0;
-      int itf = newton_exchange<float>(p, (float)Eg0, (float)Er0, (float)k, (float)cr,
-                                       (float)inv_Etot, (float)inv_rcv, 1e-6f, 12, Egf, Erf);
-      if (itf > 0 && Egf > 0.0f && Erf > 0.0f && isfinite(Egf) && isfinite(Erf)) {
-        Eg = Egf;
-        Er = Erf;
-      }
-    }
     it = newton_exchange<double>(p, Eg0, Er0, k, cr, inv_Etot, inv_rcv, p.eps_newton,
                                  p.max_iter, Eg, Er);
     if (it < 0) {
@@ -155,19 +285,7 @@ __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, 
       my_bad = min(my_bad, (unsigned long long)e);
     }
   }
-  // warp-aggregated status update
-  const unsigned full = 0xffffffffu;
-  int wmax = __reduce_max_sync(full, my_max);
-  unsigned wflags = __reduce_or_sync(full, my_flags);
-  unsigned long long wbad = my_bad;
-  for (int o = 16; o > 0; o >>= 1) wbad = min(wbad, __shfl_xor_sync(full, wbad, o));
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&st->max_iter, wmax);
-    if (wflags) {
-      atomicOr(&st->flags, wflags);
-      atomicMin(&st->first_bad, wbad);
-    }
-  }
+  exchange_status(st, my_max, my_flags, my_bad);
 }
 
 cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, void *const *U,
@@ -182,7 +300,7 @@ cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, voi
     F5<float> u; F4<float> r;
     for (int q = 0; q < 5; ++q) u.f[q] = (float *)U[q];
     for (int q = 0; q < 4; ++q) r.f[q] = (float *)R[q];
-    exchange_kernel<float><<<grid, 256, 0, s>>>(g, p, u, r, dt, st);
+    exchange_kernel_mixed<<<grid, 256, 0, s>>>(g, p, u, r, dt, st);
   } else {
     F5<double> u; F4<double> r;
     for (int q = 0; q < 5; ++q) u.f[q] = (double *)U[q];
@@ -283,6 +401,8 @@ __global__ void timestep_kernel(qk_params p, StepInfo *si) {
   si->dtrad = dtrad;
   si->smax = smax;
   si->smax_bits = 0ull;
+  si->nsub_total += nsub;
+  si->nsteps += 1.0;
 }
 
 cudaError_t launch_timestep(const qk_params &p, StepInfo *si, cudaStream_t s) {

@@ -120,6 +120,61 @@ __device__ __forceinline__ void ppm(T s0, T s1, T s2, T s3, T s4, T &qL, T &qR) 
   qR = r;
 }
 
+// Exact comparisons of finite doubles on the integer pipe.  On GB300 every
+// FP64 instruction, min/max and compare included, occupies a slot of the
+// 1/64-rate FP64 pipe; the map key(x) = bits(x) ^ ((bits(x) >> 63) & 0x7ff..f)
+// is strictly increasing in x (with -0 < +0) and its own inverse, so min, max
+// and order tests of doubles become 64-bit integer operations.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dunkey(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ bool dle0(double x) { return __double_as_longlong(x) <= 0; }
+__device__ __forceinline__ bool dgt0(double x) { return __double_as_longlong(x) > 0; }
+
+// FP64 PPM with the limiter's min/max and order tests on the integer pipe:
+// the same values as ppm<double> except possibly the sign of a zero.
+template <>
+__device__ __forceinline__ void ppm<double>(double s0, double s1, double s2, double s3,
+                                            double s4, double &qL, double &qR) {
+  const double c7 = 7.0 / 12.0, c1 = 1.0 / 12.0;
+  const double fL = c7 * (s1 + s2) - c1 * (s0 + s3);
+  const double fR = c7 * (s2 + s3) - c1 * (s1 + s4);
+  const long long k1 = dkey(s1), k2 = dkey(s2), k3 = dkey(s3);
+  const long long klo = min(k1, min(k2, k3)), khi = max(k1, max(k2, k3));
+  double l = dunkey(min(max(dkey(fL), klo), khi));
+  double r = dunkey(min(max(dkey(fR), klo), khi));
+  if (dle0((r - s2) * (s2 - l))) {
+    const double dm = s2 - s1, dp = s3 - s2;
+    double slope = 0.0;
+    if (dgt0(dm * dp)) {
+      // positive doubles order like their bit patterns
+      const long long a = __double_as_longlong(2.0 * fabs(dm));
+      const long long b = __double_as_longlong(2.0 * fabs(dp));
+      const long long c = __double_as_longlong(0.5 * fabs(dm + dp));
+      const long long m = min(a, min(b, c));
+      const long long sign = __double_as_longlong(dp) & (long long)0x8000000000000000ULL;
+      slope = __longlong_as_double(m | sign);
+    }
+    l = s2 - 0.5 * slope;
+    r = s2 + 0.5 * slope;
+  } else {
+    const double d = r - l;
+    const double q6 = 6.0 * (s2 - 0.5 * (l + r));
+    const long long kdq = dkey(d * q6), kdd = dkey(d * d);
+    if (kdq > kdd) {
+      l = 3.0 * s2 - 2.0 * r;
+    } else if (dkey(-(d * d)) > kdq) {
+      r = 3.0 * s2 - 2.0 * l;
+    }
+  }
+  qL = l;
+  qR = r;
+}
+
 // HLLC flux normal to axis D (Sec. 2.2.1; Toro 2009, ch. 10) from primitive
 // states wL, wR = (rho, vx, vy, vz, P): PVRS pressure estimate for the
 // wavespeeds S_L, S_R, contact speed S*, and the HLLC star state written with

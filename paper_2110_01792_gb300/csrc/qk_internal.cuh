@@ -66,6 +66,8 @@ struct StepInfo {
   double dtrad;        // radiation substep
   double smax;         // max(|v| + c_s)
   unsigned long long smax_bits;  // running max (bit pattern of a positive double)
+  double nsub_total;   // radiation substeps summed over all steps so far
+  double nsteps;       // timesteps computed so far
 };
 
 struct Status {

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqk.so")
 
 OK, EINVAL, ECUDA, ENOCONV, ENEGATIVE = 0, 1, 2, 3, 4
 FP64, FP32_MIXED = 0, 1
+LAUNCH_BATCHED, LAUNCH_PER_PATCH = 0, 1
 NSUMS = 13
 _lib = None
 
@@ -66,6 +67,7 @@ def lib():
     L.qk_num_cells.restype = i64
     L.qk_set_params.argtypes = [vp, P(Params)]
     L.qk_set_graph.argtypes = [vp, i32]
+    L.qk_set_launch_mode.argtypes = [vp, i32]
     L.qk_fill_ghosts.argtypes = [vp, P(vp), i32, vp]
     L.qk_hydro_stage.argtypes = [vp, i32, P(vp), P(vp), P(vp), dbl, vp]
     L.qk_rad_stage.argtypes = [vp, i32, P(vp), P(vp), P(vp), vp, dbl, vp]
@@ -73,10 +75,11 @@ def lib():
     L.qk_timestep.argtypes = [vp, P(vp), P(dbl), vp]
     L.qk_step.argtypes = [vp, P(vp), P(vp), P(dbl), P(i32), vp]
     L.qk_conserved_sums.argtypes = [vp, P(vp), P(vp), P(dbl), vp]
+    L.qk_step_info.argtypes = [vp, P(dbl), vp]
     L.qk_status.argtypes = [vp, P(C.c_uint32), P(i64), P(i32), i32, vp]
-    for f in ("qk_set_params", "qk_set_graph", "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
+    for f in ("qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
               "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
-              "qk_status"):
+              "qk_status", "qk_step_info"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -172,6 +175,10 @@ class Context:
         self.params = make_params(**kw)
         self._check(self._L.qk_set_params(self._h, C.byref(self.params)))
 
+    def set_launch_mode(self, per_patch: bool):
+        """Batched (one launch per stage over all patches) or one launch per patch."""
+        self._check(self._L.qk_set_launch_mode(self._h, 1 if per_patch else 0))
+
     def set_graph(self, enable: bool):
         self._check(self._L.qk_set_graph(self._h, 1 if enable else 0))
 
@@ -204,6 +211,12 @@ class Context:
                                     C.byref(dt) if want_dt else None,
                                     C.byref(ns) if want_dt else None, _stream(stream)))
         return (dt.value, ns.value) if want_dt else None
+
+    def step_info(self, stream=None):
+        """(dt, N_sub, dt_rad, smax) of the last timestep, total substeps, total steps."""
+        out = (C.c_double * 6)()
+        self._check(self._L.qk_step_info(self._h, out, _stream(stream)))
+        return tuple(out[:])
 
     def conserved_sums(self, U, R=None, stream=None):
         out = (C.c_double * NSUMS)()

@@ -370,3 +370,21 @@ def test_step_conserves_on_gpu(torch_cuda):
     assert abs(s1[9] - s0[9]) <= 1e-13 * abs(s0[9])
     for d in range(3):
         assert abs(s1[10 + d] - s0[10 + d]) <= 1e-13 * abs(s0[9]) / 100.0
+
+
+def test_per_patch_launches_match_batched(torch_cuda):
+    """One launch per patch and stage gives bit-identical results to the
+    batched persistent launch over all patches (each tile's arithmetic does not
+    depend on which CTA runs it)."""
+    lay, prob, prm = _small_rhd()
+    outs = []
+    for per_patch in (False, True):
+        ctx = _ctx(lay, prm)
+        ctx.set_launch_mode(per_patch)
+        dU, dR = G.dev(prob.U), G.dev(prob.R)
+        for _ in range(3):
+            ctx.step(dU, dR)
+        outs.append(G.host(dU) + G.host(dR))
+        ctx.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(G.interior(lay, a), G.interior(lay, b))
