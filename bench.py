@@ -237,11 +237,10 @@ def time_kernel(torch, fn, reps, stream):
 # (profiles/ncu_*_128.md), valid only while the kernel's sources hash to the
 # value recorded at capture time.
 NCU_TRAFFIC = {
-    ("rhd128", "rad_stage_kernel<double,1>"): (134.14e6, "rad", "f7000165b3bd"),
-    ("rhd128", "hydro_stage_kernel<double,1>"): (152.57e6, "hydro", "2332a5e22de0"),
-    ("rhd128", "rad_stage_kernel<float,1>"): (55.77e6, "rad", "f7000165b3bd"),
-    ("rhd128", "hydro_stage_kernel<float,1>"): (59.79e6, "hydro", "2332a5e22de0"),
-    ("rhd128", "exchange_kernel_mixed"): (95.42e6, "cell", "1f346e027e23"),
+    ("rhd128", "rad_stage_kernel<double,1>"): (134.25e6, "rad", "91c345f6a610"),
+    ("rhd128", "hydro_stage_kernel<double,1>"): (154.40e6, "hydro", "0c0a0be99950"),
+    ("rhd128", "hydro_stage_kernel<float,1>"): (105.51e6, "hydro", "0c0a0be99950"),
+    ("rhd128", "exchange_kernel_mixed"): (95.40e6, "cell", "dd4a3527ab00"),
 }
 
 
@@ -276,6 +275,7 @@ def run_kernel_only(args):
     ctx = qk.Context(prob.layout, prob.params, prec)
     U = [torch.from_numpy(a).cuda().to(tdt) for a in prob.U]
     R = None if prob.R is None else [torch.from_numpy(a).cuda().to(tdt) for a in prob.R]
+    tuned = None if args.no_autotune else ctx.autotune(U, R)
     ctx.fill_ghosts(U + (R or []))
     dt, _, dtr, _ = ctx.timestep(U)
     for _ in range(3):
@@ -288,7 +288,7 @@ def run_kernel_only(args):
     torch.cuda.synchronize()
     ctx.close()
     print(json.dumps({"kernel_only": args.kernel_only, "workload": args.workload,
-                      "precision": args.precision, "ok": True}))
+                      "precision": args.precision, "launch_config": tuned, "ok": True}))
 
 
 def run_variants(args, steps=5, warmup=3):
@@ -314,6 +314,7 @@ def run_variants(args, steps=5, warmup=3):
         U = [torch.from_numpy(a).cuda().to(tdt) for a in prob.U]
         R = None if prob.R is None else [torch.from_numpy(a).cuda().to(tdt) for a in prob.R]
         del prob.U, prob.R
+        tuned = None if args.no_autotune else ctx.autotune(U, R)
         for _ in range(wu):
             ctx.step(U, R)
         torch.cuda.synchronize()
@@ -333,7 +334,8 @@ def run_variants(args, steps=5, warmup=3):
         out[key] = {"value": prob.layout.ncells * st_ / t, "unit": "cell-updates/s",
                     "ms_per_step": 1e3 * t / st_, "steps": st_,
                     "nsub_mean": (i1[4] - i0[4]) / max(1.0, i1[5] - i0[5]),
-                    "patches": prob.layout.nbox, "status_ok": stt[0] == qk.OK}
+                    "patches": prob.layout.nbox, "status_ok": stt[0] == qk.OK,
+                    "launch_config": tuned}
         del U, R
         torch.cuda.empty_cache()
     return out
@@ -370,6 +372,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
+    tuned = None if args.no_autotune else ctx.autotune(U, R)
     for _ in range(args.warmup):
         ctx.step(U, R)
     torch.cuda.synchronize()
@@ -498,7 +501,8 @@ def run_ours(args):
         "dtype": "f64" if prec == qk.FP64 else "f32+f64", "data": "synthetic",
         "config": dict(describe(args.workload, prob, args.precision),
                        l2="inputs larger than L2 (state %.0f MB > 129 MB), no flush" %
-                          (h2d / 1e6), parallelism=f"{world} independent replica(s)"),
+                          (h2d / 1e6), parallelism=f"{world} independent replica(s)",
+                       launch_config=tuned or "default (256 threads, strided tiles)"),
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d,
@@ -523,6 +527,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--kernel-only", choices=["hydro1", "rad1", "exchange"], default=None,
                     help="launch one stage kernel 3 times and exit (for ncu captures)")
     args = ap.parse_args()

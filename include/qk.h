@@ -176,6 +176,18 @@ int qk_step(qk_ctx *ctx, void *const hydro[5], void *const rad[4], double *dt_ou
  * was created. */
 int qk_step_info(qk_ctx *ctx, double out[6], void *stream);
 
+/* Autotune the launch configuration of the four stage kernels (hydro stage
+ * 1/2, radiation stage 1/2): threads per CTA (128, 256, 512, the same 8^3
+ * shared-memory tile) and the tile schedule (strided over the grid, or one
+ * contiguous run of tiles per CTA), each timed with CUDA events on the
+ * caller's state; the fastest is kept for qk_step and the stage entry points
+ * of this context.  rad may be NULL (hydro only).  The state is not changed
+ * except that its ghost cells are refilled; allocates and frees one temporary
+ * copy of five fields; synchronises `stream`.  out_cfg (may be NULL) receives
+ * the choices as threads | schedule << 16. */
+int qk_autotune(qk_ctx *ctx, void *const hydro[5], void *const rad[4], int32_t out_cfg[4],
+                void *stream);
+
 #define QK_LAUNCH_BATCHED 0   /* one persistent launch per stage over all patches */
 #define QK_LAUNCH_PER_PATCH 1 /* one launch per patch and stage (for comparison)  */
 

@@ -74,7 +74,7 @@ def make_params(**kw) -> Params:
     p.a_r = kw.get("a_r", 1.0)
     p.c = kw.get("c", 100.0)
     p.chat = kw.get("chat", 10.0)
-    p.c_v = kw.get("c_v", 1.0 / (p.gamma - 1.0))
+    p.c_v = kw["c_v"] if "c_v" in kw else (1.0 / (p.gamma - 1.0) if p.gamma != 1.0 else 0.0)
     p.kappa_P = kw.get("kappa_P", 1.0)
     p.kappa_R = kw.get("kappa_R", 1.0)
     p.alpha_eos = kw.get("alpha_eos", 0.0)

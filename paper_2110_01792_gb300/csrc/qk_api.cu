@@ -29,6 +29,7 @@ struct qk_ctx {
   int ntiles = 0;
   std::vector<int> tile_start;  // first tile of each patch (tiles are grouped by patch)
   int launch_mode = QK_LAUNCH_BATCHED;
+  int cfg[4] = {kDefaultCfg, kDefaultCfg, kDefaultCfg, kDefaultCfg};  // hydro1/2, rad1/2
   Copy *d_copies = nullptr;
   Chunk *d_chunks = nullptr;
   int ncopies = 0, nchunks = 0;
@@ -402,6 +403,92 @@ int qk_set_params(qk_ctx *c, const qk_params *p) {
   return QK_OK;
 }
 
+static int check_fields(qk_ctx *c, void *const *f, int n, const char *what);
+
+// Autotuner: time every candidate launch configuration of each stage kernel
+// (threads per CTA x tile schedule) on the caller's state and keep the
+// fastest.  Timing launches write only library scratch (stage outputs go to
+// scratch buffers); the ghost cells of `hydro` and `rad` are refilled.
+int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out_cfg[4],
+                void *stream) {
+  if (!c) return QK_EINVAL;
+  int rc = check_fields(c, hydro, 5, "hydro");
+  if (rc) return rc;
+  if (rad && (rc = check_fields(c, rad, 4, "rad"))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geometry g = geom(c);
+  const int threads[3] = {128, 256, 512};
+  void *tmp[5] = {};
+  for (int q = 0; q < 5; ++q) {
+    cudaError_t e = cudaMalloc(&tmp[q], (size_t)c->field_len * c->elem);
+    if (e != cudaSuccess) {
+      for (void *t : tmp) cudaFree(t);
+      return cuda_fail(c, e, "cudaMalloc(autotune scratch)");
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  void *U1[5], *R1[4], *Rt[4];
+  for (int q = 0; q < 5; ++q) U1[q] = c->scratch[q];
+  for (int q = 0; q < 4; ++q) {
+    R1[q] = c->scratch[5 + q];
+    Rt[q] = tmp[q];
+  }
+  // timestep for realistic dt values; it does not change the state
+  cudaError_t err = launch_max_speed(c->fp32, g, c->p, hydro, c->d_si, s);
+  if (err == cudaSuccess) err = launch_timestep(c->p, c->d_si, s);
+  if (err == cudaSuccess)
+    err = launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, hydro, 5,
+                            DtSrc{nullptr, 0.0, 0, -1}, s);
+  if (err == cudaSuccess && rad)
+    err = launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, rad, 4,
+                            DtSrc{nullptr, 0.0, 0, -1}, s);
+  const DtSrc dth{c->d_si, 0.0, 0, -1}, dtr{c->d_si, 0.0, 2, -1};
+  for (int which = 0; which < 4 && err == cudaSuccess; ++which) {
+    const bool is_rad = which >= 2;
+    if (is_rad && !rad) continue;
+    const int stage = which % 2 + 1;
+    float best = 1e30f;
+    int best_cfg = c->cfg[which];
+    for (int ti = 0; ti < 3 && err == cudaSuccess; ++ti)
+      for (int sched = 0; sched < 2 && err == cudaSuccess; ++sched) {
+        const int cfg = cfg_make(threads[ti], sched);
+        auto launch = [&]() {
+          if (!is_rad)
+            return launch_hydro_stage(c->fp32, stage, g, c->p, hydro, stage == 2 ? U1 : nullptr,
+                                      stage == 1 ? U1 : tmp, dth, 0, cfg, s);
+          return launch_rad_stage(c->fp32, stage, g, c->p, rad, stage == 2 ? R1 : nullptr,
+                                  stage == 1 ? R1 : Rt, hydro[0], dtr, 0, cfg, s);
+        };
+        err = launch();
+        if (err != cudaSuccess) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = launch();
+        cudaEventRecord(e1, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && ms < best) {
+          best = ms;
+          best_cfg = cfg;
+        }
+      }
+    c->cfg[which] = best_cfg;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (void *t : tmp) cudaFree(t);
+  if (err != cudaSuccess) return cuda_fail(c, err, "autotune launch");
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  if (out_cfg)
+    for (int w = 0; w < 4; ++w) out_cfg[w] = c->cfg[w];
+  return QK_OK;
+}
+
 int qk_set_launch_mode(qk_ctx *c, int32_t mode) {
   if (!c) return QK_EINVAL;
   if (mode != QK_LAUNCH_BATCHED && mode != QK_LAUNCH_PER_PATCH)
@@ -454,7 +541,7 @@ int qk_hydro_stage(qk_ctx *c, int32_t stage, void *const U0[5], void *const U1[5
       if (Uout[q] == U1[q]) return fail(c, QK_EINVAL, "Uout must not alias U1");
   DtSrc d{nullptr, dt, 0, -1};
   QK_CUDA(c, launch_hydro_stage(c->fp32, stage, geom(c), c->p, U0, stage == 2 ? U1 : nullptr,
-                                Uout, d, 0, (cudaStream_t)stream));
+                                Uout, d, 0, c->cfg[stage - 1], (cudaStream_t)stream));
   return QK_OK;
 }
 
@@ -475,7 +562,7 @@ int qk_rad_stage(qk_ctx *c, int32_t stage, void *const R0[4], void *const R1[4],
       if (Rout[q] == R1[q]) return fail(c, QK_EINVAL, "Rout must not alias R1");
   DtSrc d{nullptr, dt_rad, 2, -1};
   QK_CUDA(c, launch_rad_stage(c->fp32, stage, geom(c), c->p, R0, stage == 2 ? R1 : nullptr, Rout,
-                              rho, d, 0, (cudaStream_t)stream));
+                              rho, d, 0, c->cfg[2 + stage - 1], (cudaStream_t)stream));
   return QK_OK;
 }
 
@@ -515,12 +602,13 @@ static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *c
                                   void *const *Uo, DtSrc dt, cudaStream_t s) {
   const Geometry g = geom(c);
   if (c->launch_mode == QK_LAUNCH_BATCHED)
-    return launch_hydro_stage(c->fp32, stage, g, c->p, U0, U1, Uo, dt, 0, s);
+    return launch_hydro_stage(c->fp32, stage, g, c->p, U0, U1, Uo, dt, 0, c->cfg[stage - 1], s);
   for (int b = 0; b < c->nbox; ++b) {
     Geometry gb = g;
     gb.tiles = c->d_tiles + c->tile_start[b];
     gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
-    cudaError_t e = launch_hydro_stage(c->fp32, stage, gb, c->p, U0, U1, Uo, dt, 0, s);
+    cudaError_t e =
+        launch_hydro_stage(c->fp32, stage, gb, c->p, U0, U1, Uo, dt, 0, c->cfg[stage - 1], s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -530,12 +618,13 @@ static cudaError_t rad_launches(qk_ctx *c, int stage, void *const *R0, void *con
                                 void *const *Ro, const void *rho, DtSrc dt, cudaStream_t s) {
   const Geometry g = geom(c);
   if (c->launch_mode == QK_LAUNCH_BATCHED)
-    return launch_rad_stage(c->fp32, stage, g, c->p, R0, R1, Ro, rho, dt, 0, s);
+    return launch_rad_stage(c->fp32, stage, g, c->p, R0, R1, Ro, rho, dt, 0, c->cfg[1 + stage], s);
   for (int b = 0; b < c->nbox; ++b) {
     Geometry gb = g;
     gb.tiles = c->d_tiles + c->tile_start[b];
     gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
-    cudaError_t e = launch_rad_stage(c->fp32, stage, gb, c->p, R0, R1, Ro, rho, dt, 0, s);
+    cudaError_t e =
+        launch_rad_stage(c->fp32, stage, gb, c->p, R0, R1, Ro, rho, dt, 0, c->cfg[1 + stage], s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

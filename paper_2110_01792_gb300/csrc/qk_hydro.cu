@@ -78,7 +78,7 @@ __device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T in
 
 template <typename T, int STAGE, int NT>
 __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p, F5<T> U0,
-                                                         F5<T> U1, F5<T> Uo, DtSrc dts) {
+                                                         F5<T> U1, F5<T> Uo, DtSrc dts, int sched) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   HydroSmem<T> &sm = *reinterpret_cast<HydroSmem<T> *>(smem_raw);
   constexpr int NOWN = NCORE / NT;
@@ -90,7 +90,16 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
   const T inv_dx[3] = {(T)(1.0 / p.dx[0]), (T)(1.0 / p.dx[1]), (T)(1.0 / p.dx[2])};
   const F5<T> src = STAGE == 1 ? U0 : U1;
 
-  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+  // tile schedule: strided over the grid (0) or one contiguous run of tiles
+  // per CTA (1, neighbouring tiles in sequence on one SM)
+  int t0 = blockIdx.x, t1 = g.ntiles, tstep = gridDim.x;
+  if (sched) {
+    const int per = (g.ntiles + gridDim.x - 1) / gridDim.x;
+    t0 = blockIdx.x * per;
+    t1 = min(g.ntiles, t0 + per);
+    tstep = 1;
+  }
+  for (int t = t0; t < t1; t += tstep) {
     const Tile tl = g.tiles[t];
     const DevBox b = g.boxes[tl.box];
     const int v[3] = {min(TS, b.n[0] - tl.x0), min(TS, b.n[1] - tl.y0), min(TS, b.n[2] - tl.z0)};
@@ -151,11 +160,10 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
   }
 }
 
-template <typename T, int STAGE>
+template <typename T, int STAGE, int NT>
 static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const *U0,
-                              void *const *U1, void *const *Uo, DtSrc dt, int grid,
+                              void *const *U1, void *const *Uo, DtSrc dt, int grid, int sched,
                               cudaStream_t s) {
-  constexpr int NT = 256;
   F5<T> a, b, c;
   for (int q = 0; q < 5; ++q) {
     a.f[q] = (T *)U0[q];
@@ -175,18 +183,30 @@ static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const
   }
   if (grid > g.ntiles) grid = g.ntiles;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, dt);
+  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, dt, sched);
   return cudaGetLastError();
+}
+
+template <typename T, int STAGE>
+static cudaError_t launch_nt(const Geometry &g, const qk_params &p, void *const *U0,
+                             void *const *U1, void *const *Uo, DtSrc dt, int grid, int cfg,
+                             cudaStream_t s) {
+  const int sched = cfg_sched(cfg);
+  switch (cfg_threads(cfg)) {
+    case 128: return launch_one<T, STAGE, 128>(g, p, U0, U1, Uo, dt, grid, sched, s);
+    case 512: return launch_one<T, STAGE, 512>(g, p, U0, U1, Uo, dt, grid, sched, s);
+    default: return launch_one<T, STAGE, 256>(g, p, U0, U1, Uo, dt, grid, sched, s);
+  }
 }
 
 cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                                void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
-                               int grid, cudaStream_t s) {
+                               int grid, int cfg, cudaStream_t s) {
   if (fp32)
-    return stage == 1 ? launch_one<float, 1>(g, p, U0, U1, Uout, dt, grid, s)
-                      : launch_one<float, 2>(g, p, U0, U1, Uout, dt, grid, s);
-  return stage == 1 ? launch_one<double, 1>(g, p, U0, U1, Uout, dt, grid, s)
-                    : launch_one<double, 2>(g, p, U0, U1, Uout, dt, grid, s);
+    return stage == 1 ? launch_nt<float, 1>(g, p, U0, U1, Uout, dt, grid, cfg, s)
+                      : launch_nt<float, 2>(g, p, U0, U1, Uout, dt, grid, cfg, s);
+  return stage == 1 ? launch_nt<double, 1>(g, p, U0, U1, Uout, dt, grid, cfg, s)
+                    : launch_nt<double, 2>(g, p, U0, U1, Uout, dt, grid, cfg, s);
 }
 
 int hydro_smem_bytes(int fp32) {

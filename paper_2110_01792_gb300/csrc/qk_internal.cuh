@@ -194,12 +194,20 @@ struct Geometry {
   const long long *box_cell0;  // nbox+1 prefix of interior cells
 };
 
+// Launch configuration of a stage kernel: threads per CTA (128, 256 or 512 on
+// the same shared-memory tile) and the tile schedule (0: strided over the
+// grid, 1: one contiguous run of tiles per CTA), packed as threads | sched<<16.
+constexpr int cfg_make(int threads, int sched) { return threads | (sched << 16); }
+constexpr int cfg_threads(int cfg) { return cfg & 0xffff; }
+constexpr int cfg_sched(int cfg) { return (cfg >> 16) & 1; }
+constexpr int kDefaultCfg = cfg_make(256, 0);
+
 cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                                void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
-                               int grid, cudaStream_t s);
+                               int grid, int cfg, cudaStream_t s);
 cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                              void *const *R0, void *const *R1, void *const *Rout,
-                             const void *rho, DtSrc dt, int grid, cudaStream_t s);
+                             const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s);
 cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                             void *const *R, DtSrc dt, Status *st, cudaStream_t s);
 cudaError_t launch_max_speed(int fp32, const Geometry &g, const qk_params &p,

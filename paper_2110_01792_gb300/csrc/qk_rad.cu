@@ -169,7 +169,7 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
 template <typename T, int STAGE, int NT>
 __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, F4<T> R0,
                                                        F4<T> R1, F4<T> Ro, const T *rho,
-                                                       DtSrc dts) {
+                                                       DtSrc dts, int sched) {
   if (skip_substep(dts)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RadSmem<T> &sm = *reinterpret_cast<RadSmem<T> *>(smem_raw);
@@ -180,7 +180,16 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
   const T dx[3] = {(T)p.dx[0], (T)p.dx[1], (T)p.dx[2]};
   const F4<T> src = STAGE == 1 ? R0 : R1;
 
-  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+  // tile schedule: strided over the grid (0) or one contiguous run of tiles
+  // per CTA (1, neighbouring tiles in sequence on one SM)
+  int t0 = blockIdx.x, t1 = g.ntiles, tstep = gridDim.x;
+  if (sched) {
+    const int per = (g.ntiles + gridDim.x - 1) / gridDim.x;
+    t0 = blockIdx.x * per;
+    t1 = min(g.ntiles, t0 + per);
+    tstep = 1;
+  }
+  for (int t = t0; t < t1; t += tstep) {
     const Tile tl = g.tiles[t];
     const DevBox b = g.boxes[tl.box];
     const int v[3] = {min(TS, b.n[0] - tl.x0), min(TS, b.n[1] - tl.y0), min(TS, b.n[2] - tl.z0)};
@@ -233,11 +242,10 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
   }
 }
 
-template <typename T, int STAGE>
+template <typename T, int STAGE, int NT>
 static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const *R0,
                               void *const *R1, void *const *Ro, const void *rho, DtSrc dt,
-                              int grid, cudaStream_t s) {
-  constexpr int NT = 256;
+                              int grid, int sched, cudaStream_t s) {
   F4<T> a, b, c;
   for (int q = 0; q < 4; ++q) {
     a.f[q] = (T *)R0[q];
@@ -257,18 +265,30 @@ static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const
   }
   if (grid > g.ntiles) grid = g.ntiles;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, (const T *)rho, dt);
+  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, (const T *)rho, dt, sched);
   return cudaGetLastError();
+}
+
+template <typename T, int STAGE>
+static cudaError_t launch_nt(const Geometry &g, const qk_params &p, void *const *R0,
+                             void *const *R1, void *const *Ro, const void *rho, DtSrc dt,
+                             int grid, int cfg, cudaStream_t s) {
+  const int sched = cfg_sched(cfg);
+  switch (cfg_threads(cfg)) {
+    case 128: return launch_one<T, STAGE, 128>(g, p, R0, R1, Ro, rho, dt, grid, sched, s);
+    case 512: return launch_one<T, STAGE, 512>(g, p, R0, R1, Ro, rho, dt, grid, sched, s);
+    default: return launch_one<T, STAGE, 256>(g, p, R0, R1, Ro, rho, dt, grid, sched, s);
+  }
 }
 
 cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                              void *const *R0, void *const *R1, void *const *Rout,
-                             const void *rho, DtSrc dt, int grid, cudaStream_t s) {
+                             const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s) {
   if (fp32)
-    return stage == 1 ? launch_one<float, 1>(g, p, R0, R1, Rout, rho, dt, grid, s)
-                      : launch_one<float, 2>(g, p, R0, R1, Rout, rho, dt, grid, s);
-  return stage == 1 ? launch_one<double, 1>(g, p, R0, R1, Rout, rho, dt, grid, s)
-                    : launch_one<double, 2>(g, p, R0, R1, Rout, rho, dt, grid, s);
+    return stage == 1 ? launch_nt<float, 1>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s)
+                      : launch_nt<float, 2>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s);
+  return stage == 1 ? launch_nt<double, 1>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s)
+                    : launch_nt<double, 2>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s);
 }
 
 int rad_smem_bytes(int fp32) {

@@ -68,6 +68,7 @@ def lib():
     L.qk_set_params.argtypes = [vp, P(Params)]
     L.qk_set_graph.argtypes = [vp, i32]
     L.qk_set_launch_mode.argtypes = [vp, i32]
+    L.qk_autotune.argtypes = [vp, P(vp), P(vp), P(i32), vp]
     L.qk_fill_ghosts.argtypes = [vp, P(vp), i32, vp]
     L.qk_hydro_stage.argtypes = [vp, i32, P(vp), P(vp), P(vp), dbl, vp]
     L.qk_rad_stage.argtypes = [vp, i32, P(vp), P(vp), P(vp), vp, dbl, vp]
@@ -77,7 +78,8 @@ def lib():
     L.qk_conserved_sums.argtypes = [vp, P(vp), P(vp), P(dbl), vp]
     L.qk_step_info.argtypes = [vp, P(dbl), vp]
     L.qk_status.argtypes = [vp, P(C.c_uint32), P(i64), P(i32), i32, vp]
-    for f in ("qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
+    for f in ("qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_autotune",
+              "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
               "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
               "qk_status", "qk_step_info"):
         getattr(L, f).restype = C.c_int
@@ -92,7 +94,7 @@ def make_params(**kw) -> Params:
     p.a_r = kw.get("a_r", 1.0)
     p.c = kw.get("c", 100.0)
     p.chat = kw.get("chat", 10.0)
-    p.c_v = kw.get("c_v", 1.0 / (p.gamma - 1.0))
+    p.c_v = kw["c_v"] if "c_v" in kw else (1.0 / (p.gamma - 1.0) if p.gamma != 1.0 else 0.0)
     p.kappa_P = kw.get("kappa_P", 1.0)
     p.kappa_R = kw.get("kappa_R", 1.0)
     p.alpha_eos = kw.get("alpha_eos", 0.0)
@@ -178,6 +180,16 @@ class Context:
     def set_launch_mode(self, per_patch: bool):
         """Batched (one launch per stage over all patches) or one launch per patch."""
         self._check(self._L.qk_set_launch_mode(self._h, 1 if per_patch else 0))
+
+    def autotune(self, U, R=None, stream=None):
+        """Pick the fastest launch configuration of each stage kernel on this
+        state; returns {kernel: (threads per CTA, schedule)}."""
+        out = (C.c_int32 * 4)()
+        self._check(self._L.qk_autotune(self._h, _ptrs(U, 5), _ptrs(R, 4) if R is not None else None,
+                                        out, _stream(stream)))
+        names = ("hydro1", "hydro2", "rad1", "rad2")
+        return {n: (int(v) & 0xffff, "contiguous" if (int(v) >> 16) & 1 else "strided")
+                for n, v in zip(names, out[:])}
 
     def set_graph(self, enable: bool):
         self._check(self._L.qk_set_graph(self._h, 1 if enable else 0))

@@ -35,3 +35,59 @@ def test_library_exports_every_declared_symbol():
     lib = ctypes.CDLL(path)
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def _qk():
+    from paper_2110_01792_gb300 import build as B
+    try:
+        B.build()
+    except (RuntimeError, FileNotFoundError) as e:
+        pytest.skip(f"cannot build libqk: {e}")
+    from paper_2110_01792_gb300 import qk
+    return qk
+
+
+def _init(qk, boxes, dom, ng=4, prec=0, **prm):
+    arr = (qk.Box * max(1, len(boxes)))()
+    for i, (lo, n, off) in enumerate(boxes):
+        for d in range(3):
+            arr[i].lo[d] = lo[d]
+            arr[i].n[d] = n[d]
+        arr[i].offset = off
+    p = qk.make_params(**dict(dict(hydro_only=1, dx=0.1), **prm))
+    h = ctypes.c_void_p()
+    dn = (ctypes.c_int32 * 3)(*dom)
+    rc = qk.lib().qk_init_patches(ctypes.byref(h), ctypes.byref(p), arr, len(boxes), dn, ng, prec)
+    msg = qk.lib().qk_last_error(None).decode()
+    if rc == 0:
+        qk.lib().qk_destroy(h)
+    return rc, msg
+
+
+def test_init_rejects_invalid_patch_sets():
+    """qk_init_patches validates before touching the GPU: empty sets, gaps,
+    overlaps, boxes outside the domain, shared field ranges, too few ghost
+    cells, unknown precision and invalid parameters are QK_EINVAL with a
+    message (runs on CPU)."""
+    qk = _qk()
+    vol = lambda n, g=4: (n[0] + 2 * g) * (n[1] + 2 * g) * (n[2] + 2 * g)
+    a = ((0, 0, 0), (8, 8, 8), 0)
+    b = ((8, 0, 0), (8, 8, 8), vol((8, 8, 8)))
+    cases = [
+        ([], (16, 8, 8), {}, "no boxes"),
+        ([a], (16, 8, 8), {}, "cover"),                      # gap
+        ([a, ((4, 0, 0), (8, 8, 8), vol((8, 8, 8)))], (16, 8, 8), {}, "overlap"),
+        ([a, ((8, 0, 0), (16, 8, 8), vol((8, 8, 8)))], (16, 8, 8), {}, "outside"),
+        ([a, ((8, 0, 0), (8, 8, 8), 10)], (16, 8, 8), {}, "field range"),
+        ([a, b], (16, 8, 8), {"ng": 2}, "nghost"),
+        ([a, b], (16, 8, 8), {"prec": 7}, "precision"),
+        ([a, b], (16, 8, 8), {"gamma": 1.0, "c_v": 1.0}, "gamma"),
+        ([a, b], (16, 8, 8), {"hydro_only": 0, "chat": 0.0}, "chat"),
+        ([((0, 0, 0), (0, 8, 8), 0)], (16, 8, 8), {}, "empty extent"),
+    ]
+    for boxes, dom, kw, word in cases:
+        ng = kw.pop("ng", 4)
+        prec = kw.pop("prec", 0)
+        rc, msg = _init(qk, boxes, dom, ng, prec, **kw)
+        assert rc == qk.EINVAL, (word, rc, msg)
+        assert word.split()[0] in msg.lower() or word in msg.lower(), (word, msg)
