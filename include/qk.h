@@ -56,7 +56,9 @@ typedef struct qk_ctx qk_ctx;
  * of Sec. 2.2.3 (1e-10 and 400 in the paper); nsub_max is N_sub,max of
  * Sec. 2.2.4 (10).  tau_correction enables the optical-depth correction of the
  * radiation Riemann solver (Sec. 2.2.2).  hydro_only skips the radiation
- * substeps in qk_step. */
+ * substeps in qk_step.  recon selects PPM or PLM for both subsystems;
+ * flattening enables the shock flattening of Miller & Colella (2002) on the
+ * hydro reconstruction (Sec. 2.2.1; the radiation is never flattened). */
 typedef struct {
   double gamma;      /* adiabatic index                                        */
   double cfl;        /* CFL number                                             */
@@ -75,7 +77,12 @@ typedef struct {
   int32_t nsub_max;
   int32_t tau_correction;
   int32_t hydro_only;
+  int32_t recon;       /* QK_RECON_PPM (default) or QK_RECON_PLM, hydro and radiation */
+  int32_t flattening;  /* 1: multidimensional shock flattening of the hydro states    */
 } qk_params;
+
+#define QK_RECON_PPM 0 /* piecewise parabolic with the paper's limiter (Sec. 2.2.1)  */
+#define QK_RECON_PLM 1 /* piecewise linear, monotonized-central slope (Sec. 2.2.1)  */
 
 /* One patch: lower corner in the periodic domain, interior extents, and the
  * element offset of its first (ghost) cell in every field array. */
@@ -126,7 +133,9 @@ int qk_fill_ghosts(qk_ctx *ctx, void *const *fields, int32_t nfields, void *stre
  *   stage 2: Uout = U0/2 + (U1 + dt L(U1))/2.
  * The stencil source (U0 in stage 1, U1 in stage 2) must have its ghosts
  * filled.  Uout may equal U0 in stage 2 (in place), never the stencil source.
- * U1 is ignored in stage 1.  Face fluxes never leave the chip. */
+ * U1 is ignored in stage 1.  Face fluxes never leave the chip.  With
+ * flattening, the coefficient is computed from the stencil source first (one
+ * extra launch into library scratch). */
 int qk_hydro_stage(qk_ctx *ctx, int32_t stage, void *const U0[5], void *const U1[5],
                    void *const Uout[5], double dt, void *stream);
 

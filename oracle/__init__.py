@@ -63,6 +63,7 @@ class Params(C.Structure):
         ("eps_newton", C.c_double), ("dx", C.c_double * 3),
         ("kappa_mode", C.c_int32), ("eos", C.c_int32), ("max_iter", C.c_int32),
         ("nsub_max", C.c_int32), ("tau_correction", C.c_int32), ("hydro_only", C.c_int32),
+        ("recon", C.c_int32), ("flattening", C.c_int32),
     ]
 
 
@@ -90,6 +91,8 @@ def make_params(**kw) -> Params:
     p.nsub_max = int(kw.get("nsub_max", 10))
     p.tau_correction = int(kw.get("tau_correction", 1))
     p.hydro_only = int(kw.get("hydro_only", 0))
+    p.recon = int(kw.get("recon", 0))
+    p.flattening = int(kw.get("flattening", 0))
     return p
 
 
@@ -106,6 +109,7 @@ def lib():
             L.or_grid_destroy.argtypes = [vp]
             L.or_fill_ghosts.argtypes = [vp, vp]
             L.or_ppm_cell.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double)]
+            L.or_plm_cell.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double)]
             L.or_hllc.argtypes = [P(C.c_double), P(C.c_double), C.c_int, C.c_double, P(C.c_double)]
             L.or_hydro_stage.argtypes = [vp, P(Params), C.c_int, vp, vp, vp, C.c_double,
                                          C.c_int64, vp]
@@ -182,6 +186,13 @@ def ppm_cell(stencil):
     s = (C.c_double * 5)(*[float(x) for x in stencil])
     qL, qR = C.c_double(), C.c_double()
     lib().or_ppm_cell(s, C.byref(qL), C.byref(qR))
+    return qL.value, qR.value
+
+
+def plm_cell(stencil):
+    s = (C.c_double * 5)(*[float(x) for x in stencil])
+    qL, qR = C.c_double(), C.c_double()
+    lib().or_plm_cell(s, C.byref(qL), C.byref(qR))
     return qL.value, qR.value
 
 

@@ -41,6 +41,7 @@ static inline bool operator>(Num a, Num b) { g_t.cmp++; return a.v > b.v; }
 static inline bool operator<=(Num a, Num b) { g_t.cmp++; return a.v <= b.v; }
 static inline bool operator>=(Num a, Num b) { g_t.cmp++; return a.v >= b.v; }
 static inline bool operator==(Num a, Num b) { g_t.cmp++; return a.v == b.v; }
+static inline bool operator!=(Num a, Num b) { g_t.cmp++; return a.v != b.v; }
 static inline bool operator!(Num a) { g_t.cmp++; return !a.v; }
 static inline Num sqrt(Num a) { g_t.sqrt_++; return Num(std::sqrt(a.v)); }
 static inline Num fabs(Num a) { return Num(std::fabs(a.v)); }
@@ -131,7 +132,7 @@ int main(int argc, char **argv) {
           Tally b = g_t;
           for (int v = 0; v < 5; ++v) or_ppm_cell(&w[v][1], &wR[v], &dum);
           Tally cc = g_t;
-          or_hllc(wL, wR, d, p.gamma, F);
+          or_hllc(wL, wR, d, p.gamma, F);  // (no flattening in the benchmark workloads)
           Tally dd = g_t;
           Tally x = diff(b, a);
           ppm_t.add += x.add; ppm_t.mul += x.mul; ppm_t.div += x.div; ppm_t.sqrt_ += x.sqrt_; ppm_t.cmp += x.cmp;

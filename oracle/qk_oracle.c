@@ -66,6 +66,8 @@ typedef struct {
   int32_t nsub_max;       /* N_sub,max (10 in the paper)                           */
   int32_t tau_correction; /* 1: optical-depth correction of the radiation flux     */
   int32_t hydro_only;     /* 1: skip radiation substeps                            */
+  int32_t recon;          /* 0: PPM; 1: PLM with the MC limiter (Sec. 2.2.1)       */
+  int32_t flattening;     /* 1: multidimensional shock flattening (Sec. 2.2.1)     */
 } or_params;
 
 typedef struct {
@@ -229,6 +231,29 @@ void or_ppm_cell(const double s[5], double *qL_out, double *qR_out) {
   *qR_out = qR;
 }
 
+/* PLM reconstruction of one cell with the monotonized-central limiter
+ * (van Leer 1977), the paper's compile-time alternative to PPM (Sec. 2.2.1):
+ * slope = 0 at a local extremum of the cell averages, else
+ * sign(dq+) min(2|dq-|, 2|dq+|, |dq- + dq+|/2); qL,R = q -/+ slope/2. */
+void or_plm_cell(const double s[5], double *qL_out, double *qR_out) {
+  double qm = s[1], q0 = s[2], qp = s[3];
+  double dm = q0 - qm, dp = qp - q0, slope = 0.0;
+  if (dm * dp > 0.0) {
+    double a = fabs(dm), b = fabs(dp), cc = fabs(dm + dp);
+    double m = dmin(2.0 * a, dmin(2.0 * b, 0.5 * cc));
+    slope = dp > 0.0 ? m : -m;
+  }
+  *qL_out = q0 - 0.5 * slope;
+  *qR_out = q0 + 0.5 * slope;
+}
+
+static void recon_cell(const or_params *p, const double s[5], double *qL, double *qR) {
+  if (p->recon == 1)
+    or_plm_cell(s, qL, qR);
+  else
+    or_ppm_cell(s, qL, qR);
+}
+
 /* Euler flux normal to direction d of primitive state w = (rho, vx, vy, vz, P)
  * and the matching conserved state.  The kinetic energy is summed as
  * un^2 + (ut1^2 + ut2^2), symmetric in the two transverse components. */
@@ -317,28 +342,98 @@ static void gather_prims(const or_grid *g, const or_params *p, double *const *U,
   }
 }
 
+/* Shock flattening (Sec. 2.2.1): the one-dimensional coefficient of Colella &
+ * Woodward (1984, appendix) along direction d at cell c,
+ *   ftilde = min(1, max(0, w2 (|p_{c+1} - p_{c-1}| / |p_{c+2} - p_{c-2}| - w1)))
+ * where the cell sits in a compressive jump (u_{c-1} > u_{c+1} along d and
+ * |p_{c+1} - p_{c-1}| > eps min(p_{c+1}, p_{c-1})), else 0; CW84's constants
+ * eps = 0.33, w1 = 0.75, w2 = 10. */
+static double flat_ftilde(const or_grid *g, const or_params *p, double *const *U, int b,
+                          const int c[3], int d) {
+  double pr[5], un[5];
+  for (int o = -2; o <= 2; ++o) {
+    int cc[3] = {c[0], c[1], c[2]};
+    cc[d] += o;
+    int64_t e = owner_index(g, b, cc[0], cc[1], cc[2]);
+    double Uc[NHYD], q[NHYD];
+    for (int v = 0; v < NHYD; ++v) Uc[v] = U[v][e];
+    con2prim(Uc, p->gamma, q);
+    pr[o + 2] = q[4];
+    un[o + 2] = q[1 + d];
+  }
+  double dp1 = pr[3] - pr[1], dp2 = pr[4] - pr[0];
+  int shock = fabs(dp1) > 0.33 * dmin(pr[3], pr[1]) && un[1] - un[3] > 0.0;
+  if (!shock) return 0.0;
+  if (!(fabs(dp2) > 0.0)) return 1.0;
+  return dmin(1.0, dmax(0.0, 10.0 * (fabs(dp1) / fabs(dp2) - 0.75)));
+}
+
+/* Multidimensional flattening coefficient of Miller & Colella (2002) at cell c:
+ * chi = min over directions of (1 - f_d), with f_d = max(ftilde_d(c),
+ * ftilde_d(c - sign(p_{c+1} - p_{c-1}))) (CW84's extension by one cell on the
+ * low-pressure side).  chi = 1 leaves the reconstruction unchanged. */
+static double flat_chi(const or_grid *g, const or_params *p, double *const *U, int b,
+                       const int c[3]) {
+  double chi = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    double f = flat_ftilde(g, p, U, b, c, d);
+    double pr[2];
+    for (int s = 0; s < 2; ++s) {
+      int cc[3] = {c[0], c[1], c[2]};
+      cc[d] += s == 0 ? -1 : 1;
+      int64_t e = owner_index(g, b, cc[0], cc[1], cc[2]);
+      double Uc[NHYD], q[NHYD];
+      for (int v = 0; v < NHYD; ++v) Uc[v] = U[v][e];
+      con2prim(Uc, p->gamma, q);
+      pr[s] = q[4];
+    }
+    double dp1 = pr[1] - pr[0];
+    if (dp1 != 0.0) {
+      int cc[3] = {c[0], c[1], c[2]};
+      cc[d] += dp1 > 0.0 ? -1 : 1;
+      f = dmax(f, flat_ftilde(g, p, U, b, cc, d));
+    }
+    chi = dmin(chi, 1.0 - f);
+  }
+  return chi;
+}
+
 /* hydro flux at the face between cell c+first+2 and c+first+3 along d,
  * computed from the six cells c+first .. c+first+5 */
-static void hydro_face_flux(const or_grid *g, const or_params *p, double *const *U, int b,
-                            const int c[3], int d, int first, double F[NHYD]) {
+static void hydro_face_flux(const or_grid *g, const or_params *p, double *const *U,
+                            const double *chi, int b, const int c[3], int d, int first,
+                            double F[NHYD]) {
   double w[NHYD][6], wL[NHYD], wR[NHYD], dummy;
   gather_prims(g, p, U, b, c, d, first, w);
   for (int v = 0; v < NHYD; ++v) {
-    or_ppm_cell(&w[v][0], &dummy, &wL[v]); /* right face of the left cell  */
-    or_ppm_cell(&w[v][1], &wR[v], &dummy); /* left face of the right cell  */
+    recon_cell(p, &w[v][0], &dummy, &wL[v]); /* right face of the left cell  */
+    recon_cell(p, &w[v][1], &wR[v], &dummy); /* left face of the right cell  */
+  }
+  if (chi) {
+    /* reading: the face states are blended with the cell average after the
+     * limiter, q <- chi q + (1 - chi) q_cell */
+    int cA[3] = {c[0], c[1], c[2]}, cB[3] = {c[0], c[1], c[2]};
+    cA[d] += first + 2;
+    cB[d] += first + 3;
+    double chiA = chi[owner_index(g, b, cA[0], cA[1], cA[2])];
+    double chiB = chi[owner_index(g, b, cB[0], cB[1], cB[2])];
+    for (int v = 0; v < NHYD; ++v) {
+      wL[v] = chiA * wL[v] + (1.0 - chiA) * w[v][2];
+      wR[v] = chiB * wR[v] + (1.0 - chiB) * w[v][3];
+    }
   }
   or_hllc(wL, wR, d, p->gamma, F);
 }
 
 /* L(U) at interior cell (b,i,j,k): minus the divergence of the face fluxes,
  * summed as ((x + y) + z) (Sec. 2.2.1, exact x<->y symmetry, Sec. 3.1). */
-static void hydro_rhs_cell(const or_grid *g, const or_params *p, double *const *U, int b,
-                           const int c[3], double L[NHYD]) {
+static void hydro_rhs_cell(const or_grid *g, const or_params *p, double *const *U,
+                           const double *chi, int b, const int c[3], double L[NHYD]) {
   double div[3][NHYD];
   for (int d = 0; d < 3; ++d) {
     double Flo[NHYD], Fhi[NHYD];
-    hydro_face_flux(g, p, U, b, c, d, -3, Flo); /* face c-1/2 */
-    hydro_face_flux(g, p, U, b, c, d, -2, Fhi); /* face c+1/2 */
+    hydro_face_flux(g, p, U, chi, b, c, d, -3, Flo); /* face c-1/2 */
+    hydro_face_flux(g, p, U, chi, b, c, d, -2, Fhi); /* face c+1/2 */
     for (int v = 0; v < NHYD; ++v) div[d][v] = (Fhi[v] - Flo[v]) / p->dx[d];
   }
   for (int v = 0; v < NHYD; ++v) L[v] = -((div[0][v] + div[1][v]) + div[2][v]);
@@ -376,6 +471,7 @@ typedef struct {
   double dt;
   const double *rho; /* radiation stages only */
   int nvar;
+  const double *chi; /* flattening coefficient per cell (hydro, or NULL) */
 } stage_ctx;
 
 /* RK2-SSP (Shu & Osher 1988), Sec. 2.2.1:
@@ -387,10 +483,10 @@ static void hydro_stage_cell(const or_grid *g, const or_params *p, int b, const 
   double L[NHYD];
   int64_t e = cell_index(g, b, c[0], c[1], c[2]);
   if (s->stage == 1) {
-    hydro_rhs_cell(g, p, s->U0, b, c, L);
+    hydro_rhs_cell(g, p, s->U0, s->chi, b, c, L);
     for (int v = 0; v < NHYD; ++v) s->Uout[v][e] = s->U0[v][e] + s->dt * L[v];
   } else {
-    hydro_rhs_cell(g, p, s->U1, b, c, L);
+    hydro_rhs_cell(g, p, s->U1, s->chi, b, c, L);
     for (int v = 0; v < NHYD; ++v)
       s->Uout[v][e] = 0.5 * s->U0[v][e] + 0.5 * (s->U1[v][e] + s->dt * L[v]);
   }
@@ -403,8 +499,32 @@ static void hydro_stage_cell(const or_grid *g, const or_params *p, int b, const 
 int or_hydro_stage(const or_grid *g, const or_params *p, int stage, double *const *U0,
                    double *const *U1, double *const *Uout, double dt, int64_t ncell,
                    const int32_t *cells) {
-  stage_ctx s = {stage, U0, U1, Uout, dt, NULL, NHYD};
+  stage_ctx s = {stage, U0, U1, Uout, dt, NULL, NHYD, NULL};
+  double *chi = NULL;
+  if (p->flattening) {
+    /* the flattening coefficient of every interior cell of the stencil source,
+     * computed once per stage (neighbours outside a patch read their owner's) */
+    double *const *src = stage == 1 ? U0 : U1;
+    int64_t len = 0;
+    for (int b = 0; b < g->nbox; ++b) {
+      int64_t end = cell_index(g, b, g->n[3 * b] + g->ng - 1, g->n[3 * b + 1] + g->ng - 1,
+                               g->n[3 * b + 2] + g->ng - 1) + 1;
+      if (end > len) len = end;
+    }
+    chi = (double *)calloc((size_t)len, sizeof(double));
+    for (int b = 0; b < g->nbox; ++b) {
+      const int32_t *n = g->n + 3 * b;
+      for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+          for (int i = 0; i < n[0]; ++i) {
+            int c[3] = {i, j, k};
+            chi[cell_index(g, b, i, j, k)] = flat_chi(g, p, src, b, c);
+          }
+    }
+    s.chi = chi;
+  }
   for_cells(g, p, ncell, cells, hydro_stage_cell, &s);
+  free(chi);
   return OR_OK;
 }
 
@@ -537,8 +657,8 @@ static void rad_face_flux(const or_grid *g, const or_params *p, double *const *R
   double w[NRAD][6], wL[NRAD], wR[NRAD], dummy;
   gather_rad(g, p, R, b, c, d, first, w);
   for (int v = 0; v < NRAD; ++v) {
-    or_ppm_cell(&w[v][0], &dummy, &wL[v]);
-    or_ppm_cell(&w[v][1], &wR[v], &dummy);
+    recon_cell(p, &w[v][0], &dummy, &wL[v]);
+    recon_cell(p, &w[v][1], &wR[v], &dummy);
   }
   double fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
   double fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
@@ -604,7 +724,7 @@ static void rad_stage_cell(const or_grid *g, const or_params *p, int b, const in
 int or_rad_stage(const or_grid *g, const or_params *p, int stage, double *const *R0,
                  double *const *R1, double *const *Rout, const double *rho, double dt,
                  int64_t ncell, const int32_t *cells) {
-  stage_ctx s = {stage, R0, R1, Rout, dt, rho, NRAD};
+  stage_ctx s = {stage, R0, R1, Rout, dt, rho, NRAD, NULL};
   for_cells(g, p, ncell, cells, rad_stage_cell, &s);
   return OR_OK;
 }

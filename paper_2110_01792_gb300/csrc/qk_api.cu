@@ -39,6 +39,7 @@ struct qk_ctx {
   double *d_sums = nullptr;
   int sum_blocks = 0;
   void *scratch[9] = {};
+  void *chi = nullptr;   // shock-flattening coefficient (one field)
   size_t elem = 8;
   // pinned host staging
   double *h_buf = nullptr;
@@ -102,6 +103,12 @@ static int check_params(qk_ctx *c, const qk_params *p) {
     return fail(c, QK_EINVAL, "unknown kappa_mode %d", p->kappa_mode);
   if (p->eos != QK_EOS_GAMMA && p->eos != QK_EOS_ALPHA_T3)
     return fail(c, QK_EINVAL, "unknown eos %d", p->eos);
+  if (p->recon != QK_RECON_PPM && p->recon != QK_RECON_PLM)
+    return fail(c, QK_EINVAL, "unknown recon %d", p->recon);
+  if (p->flattening != 0 && p->flattening != 1)
+    return fail(c, QK_EINVAL, "flattening must be 0 or 1");
+  if (p->flattening && c && c->ng && c->ng < 4)
+    return fail(c, QK_EINVAL, "flattening needs nghost >= 4 (its stencil reaches 4 cells)");
   return QK_OK;
 }
 
@@ -274,6 +281,7 @@ static void release(qk_ctx *c) {
   cudaFree(c->d_partials);
   cudaFree(c->d_sums);
   for (void *s : c->scratch) cudaFree(s);
+  cudaFree(c->chi);
   if (c->h_buf) cudaFreeHost(c->h_buf);
 }
 
@@ -294,6 +302,8 @@ int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32
   if (rc) return bail(rc);
   if (!boxes || nbox < 1 || !domain_n) return bail(fail(c, QK_EINVAL, "no boxes"));
   if (nghost < HALO || nghost > 16) return bail(fail(c, QK_EINVAL, "nghost must be in [3, 16]"));
+  if (p->flattening && nghost < 4)
+    return bail(fail(c, QK_EINVAL, "flattening needs nghost >= 4 (its stencil reaches 4 cells)"));
   if (precision != QK_FP64 && precision != QK_FP32_MIXED)
     return bail(fail(c, QK_EINVAL, "unknown precision"));
   for (int d = 0; d < 3; ++d)
@@ -369,6 +379,8 @@ int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32
   for (int f = 0; f < 9; ++f)
     if ((e = cudaMalloc(&c->scratch[f], (size_t)c->field_len * c->elem)) != cudaSuccess)
       return bail(cuda_fail(c, e, "cudaMalloc(scratch field)"));
+  if ((e = cudaMalloc(&c->chi, (size_t)c->field_len * c->elem)) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMalloc(flattening field)"));
   if ((e = cudaMallocHost((void **)&c->h_buf, 64 * sizeof(double))) != cudaSuccess)
     return bail(cuda_fail(c, e, "cudaMallocHost"));
   if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -444,6 +456,7 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
   if (err == cudaSuccess && rad)
     err = launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, rad, 4,
                             DtSrc{nullptr, 0.0, 0, -1}, s);
+  if (err == cudaSuccess && c->p.flattening) err = launch_flatten(c->fp32, g, c->p, hydro, c->chi, s);
   const DtSrc dth{c->d_si, 0.0, 0, -1}, dtr{c->d_si, 0.0, 2, -1};
   for (int which = 0; which < 4 && err == cudaSuccess; ++which) {
     const bool is_rad = which >= 2;
@@ -457,7 +470,8 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
         auto launch = [&]() {
           if (!is_rad)
             return launch_hydro_stage(c->fp32, stage, g, c->p, hydro, stage == 2 ? U1 : nullptr,
-                                      stage == 1 ? U1 : tmp, dth, 0, cfg, s);
+                                      stage == 1 ? U1 : tmp, dth, 0, cfg,
+                                      c->p.flattening ? c->chi : nullptr, s);
           return launch_rad_stage(c->fp32, stage, g, c->p, rad, stage == 2 ? R1 : nullptr,
                                   stage == 1 ? R1 : Rt, hydro[0], dtr, 0, cfg, s);
         };
@@ -540,8 +554,12 @@ int qk_hydro_stage(qk_ctx *c, int32_t stage, void *const U0[5], void *const U1[5
     for (int q = 0; q < 5; ++q)
       if (Uout[q] == U1[q]) return fail(c, QK_EINVAL, "Uout must not alias U1");
   DtSrc d{nullptr, dt, 0, -1};
+  if (c->p.flattening)
+    QK_CUDA(c, launch_flatten(c->fp32, geom(c), c->p, stage == 1 ? U0 : U1, c->chi,
+                              (cudaStream_t)stream));
   QK_CUDA(c, launch_hydro_stage(c->fp32, stage, geom(c), c->p, U0, stage == 2 ? U1 : nullptr,
-                                Uout, d, 0, c->cfg[stage - 1], (cudaStream_t)stream));
+                                Uout, d, 0, c->cfg[stage - 1], c->p.flattening ? c->chi : nullptr,
+                                (cudaStream_t)stream));
   return QK_OK;
 }
 
@@ -601,14 +619,20 @@ int qk_timestep(qk_ctx *c, void *const hydro[5], double out[4], void *stream) {
 static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *const *U1,
                                   void *const *Uo, DtSrc dt, cudaStream_t s) {
   const Geometry g = geom(c);
+  const void *chi = c->p.flattening ? c->chi : nullptr;
+  if (chi) {
+    cudaError_t e = launch_flatten(c->fp32, g, c->p, stage == 1 ? U0 : U1, c->chi, s);
+    if (e != cudaSuccess) return e;
+  }
   if (c->launch_mode == QK_LAUNCH_BATCHED)
-    return launch_hydro_stage(c->fp32, stage, g, c->p, U0, U1, Uo, dt, 0, c->cfg[stage - 1], s);
+    return launch_hydro_stage(c->fp32, stage, g, c->p, U0, U1, Uo, dt, 0, c->cfg[stage - 1], chi,
+                              s);
   for (int b = 0; b < c->nbox; ++b) {
     Geometry gb = g;
     gb.tiles = c->d_tiles + c->tile_start[b];
     gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
-    cudaError_t e =
-        launch_hydro_stage(c->fp32, stage, gb, c->p, U0, U1, Uo, dt, 0, c->cfg[stage - 1], s);
+    cudaError_t e = launch_hydro_stage(c->fp32, stage, gb, c->p, U0, U1, Uo, dt, 0,
+                                       c->cfg[stage - 1], chi, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

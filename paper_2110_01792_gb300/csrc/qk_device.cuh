@@ -135,6 +135,17 @@ __device__ __forceinline__ double dunkey(long long k) {
 __device__ __forceinline__ bool dle0(double x) { return __double_as_longlong(x) <= 0; }
 __device__ __forceinline__ bool dgt0(double x) { return __double_as_longlong(x) > 0; }
 
+// Order of non-negative values (+0 included): doubles compare as their bit
+// patterns on the integer pipe; floats use the FP32 comparisons.
+__device__ __forceinline__ bool nn_gt(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b);
+}
+__device__ __forceinline__ bool nn_gt(float a, float b) { return a > b; }
+__device__ __forceinline__ double nn_max(double a, double b) { return nn_gt(a, b) ? a : b; }
+__device__ __forceinline__ float nn_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double nn_min(double a, double b) { return nn_gt(a, b) ? b : a; }
+__device__ __forceinline__ float nn_min(float a, float b) { return fminf(a, b); }
+
 // FP64 PPM with the limiter's min/max and order tests on the integer pipe:
 // the same values as ppm<double> except possibly the sign of a zero.
 template <>
@@ -173,6 +184,29 @@ __device__ __forceinline__ void ppm<double>(double s0, double s1, double s2, dou
   }
   qL = l;
   qR = r;
+}
+
+// PLM with the monotonized-central limiter (van Leer 1977), the paper's
+// alternative reconstruction (Sec. 2.2.1): zero slope at an extremum of the
+// cell averages, else sign(dq+) min(2|dq-|, 2|dq+|, |dq- + dq+|/2).
+template <typename T>
+__device__ __forceinline__ void plm(T s1, T s2, T s3, T &qL, T &qR) {
+  const T dm = s2 - s1, dp = s3 - s2;
+  T slope = T(0);
+  if (dm * dp > T(0)) {
+    const T m = min(T(2) * fabs(dm), min(T(2) * fabs(dp), T(0.5) * fabs(dm + dp)));
+    slope = dp > T(0) ? m : -m;
+  }
+  qL = s2 - T(0.5) * slope;
+  qR = s2 + T(0.5) * slope;
+}
+
+template <typename T>
+__device__ __forceinline__ void recon(int kind, T s0, T s1, T s2, T s3, T s4, T &qL, T &qR) {
+  if (kind == QK_RECON_PLM)
+    plm<T>(s1, s2, s3, qL, qR);
+  else
+    ppm<T>(s0, s1, s2, s3, s4, qL, qR);
 }
 
 // HLLC flux normal to axis D (Sec. 2.2.1; Toro 2009, ch. 10) from primitive
@@ -237,12 +271,11 @@ __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm
 //   b = (3 chi - 1)/(2 |f|^2) = (2 + 6 fc^2 - s)/(D |f|^2),
 // so n_i n_j = f_i f_j / |f|^2 needs no |f| and one division serves both.
 template <typename T>
-__device__ __forceinline__ void levermore_ab(T fx, T fy, T fz, T &a, T &b) {
-  const T f2 = (fx * fx + fy * fy) + fz * fz;
-  const T fc2 = min(f2, T(1));
+__device__ __forceinline__ void levermore_ab_f2(T f2, T &a, T &b) {
+  const T fc2 = nn_min(f2, T(1));
   const T s = qsqrt(T(4) - T(3) * fc2);
   const T D = T(5) + T(2) * s;
-  if (f2 > T(0)) {
+  if (nn_gt(f2, T(0))) {
     const T r = qrcp(D * f2);
     a = (T(1) + s - T(2) * fc2) * (f2 * r);
     b = (T(2) + T(6) * fc2 - s) * r;
@@ -250,6 +283,11 @@ __device__ __forceinline__ void levermore_ab(T fx, T fy, T fz, T &a, T &b) {
     a = qdiv(T(1) + s, D);
     b = T(0);
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void levermore_ab(T fx, T fy, T fz, T &a, T &b) {
+  levermore_ab_f2<T>((fx * fx + fy * fy) + fz * fz, a, b);
 }
 
 // Column D of the Eddington tensor.

@@ -17,7 +17,9 @@ template <typename T> struct HydroSmem {
 
 template <typename T, int D, int NT, int NOWN>
 __device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T inv_dx, T gamma,
-                                          T gm1inv, T g1, T (&acc)[NOWN][5]) {
+                                          T gm1inv, T g1, int rk, const T *chi,
+                                          const DevBox &bx, int ng, int x0, int y0, int z0,
+                                          T (&acc)[NOWN][5]) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
   // Phase A: reconstruction of every needed position of every line along D.
   for (int it = threadIdx.x; it < NREC; it += NT) {
@@ -31,11 +33,19 @@ __device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T in
       cc[D] += o - 2;
       s[o] = cross_slot(cc[0], cc[1], cc[2]);
     }
+    // shock flattening: blend the face states with the cell average,
+    // q <- chi q + (1 - chi) q_cell (chi from the flattening pre-pass)
+    const T ch = chi ? chi[cell_elem(bx, ng, x0 + c[0], y0 + c[1], z0 + c[2])] : T(1);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       T qL, qR;
-      ppm<T>(sm.prim[q][s[0]], sm.prim[q][s[1]], sm.prim[q][s[2]], sm.prim[q][s[3]],
-             sm.prim[q][s[4]], qL, qR);
+      recon<T>(rk, sm.prim[q][s[0]], sm.prim[q][s[1]], sm.prim[q][s[2]], sm.prim[q][s[3]],
+               sm.prim[q][s[4]], qL, qR);
+      if (chi) {
+        const T qc = sm.prim[q][s[2]];
+        qL = ch * qL + (T(1) - ch) * qc;
+        qR = ch * qR + (T(1) - ch) * qc;
+      }
       sm.rec[2 * q][it] = qL;
       sm.rec[2 * q + 1][it] = qR;
     }
@@ -78,7 +88,8 @@ __device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T in
 
 template <typename T, int STAGE, int NT>
 __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p, F5<T> U0,
-                                                         F5<T> U1, F5<T> Uo, DtSrc dts, int sched) {
+                                                         F5<T> U1, F5<T> Uo, DtSrc dts, int sched,
+                                                         const T *chi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   HydroSmem<T> &sm = *reinterpret_cast<HydroSmem<T> *>(smem_raw);
   constexpr int NOWN = NCORE / NT;
@@ -135,9 +146,12 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
     }
     __syncthreads();
     T acc[NOWN][5];
-    hydro_dir<T, 0, NT, NOWN>(sm, v, inv_dx[0], gamma, gm1inv, g1, acc);
-    hydro_dir<T, 1, NT, NOWN>(sm, v, inv_dx[1], gamma, gm1inv, g1, acc);
-    hydro_dir<T, 2, NT, NOWN>(sm, v, inv_dx[2], gamma, gm1inv, g1, acc);
+    hydro_dir<T, 0, NT, NOWN>(sm, v, inv_dx[0], gamma, gm1inv, g1, p.recon, chi, b, g.ng,
+                                tl.x0, tl.y0, tl.z0, acc);
+    hydro_dir<T, 1, NT, NOWN>(sm, v, inv_dx[1], gamma, gm1inv, g1, p.recon, chi, b, g.ng,
+                                tl.x0, tl.y0, tl.z0, acc);
+    hydro_dir<T, 2, NT, NOWN>(sm, v, inv_dx[2], gamma, gm1inv, g1, p.recon, chi, b, g.ng,
+                                tl.x0, tl.y0, tl.z0, acc);
     // ---- RK2-SSP combination for the owned cells ----
 #pragma unroll
     for (int m = 0; m < NOWN; ++m) {
@@ -163,7 +177,7 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
 template <typename T, int STAGE, int NT>
 static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const *U0,
                               void *const *U1, void *const *Uo, DtSrc dt, int grid, int sched,
-                              cudaStream_t s) {
+                              const void *chi, cudaStream_t s) {
   F5<T> a, b, c;
   for (int q = 0; q < 5; ++q) {
     a.f[q] = (T *)U0[q];
@@ -183,30 +197,109 @@ static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const
   }
   if (grid > g.ntiles) grid = g.ntiles;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, dt, sched);
+  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, dt, sched, (const T *)chi);
   return cudaGetLastError();
 }
 
 template <typename T, int STAGE>
 static cudaError_t launch_nt(const Geometry &g, const qk_params &p, void *const *U0,
                              void *const *U1, void *const *Uo, DtSrc dt, int grid, int cfg,
-                             cudaStream_t s) {
+                             const void *chi, cudaStream_t s) {
   const int sched = cfg_sched(cfg);
   switch (cfg_threads(cfg)) {
-    case 128: return launch_one<T, STAGE, 128>(g, p, U0, U1, Uo, dt, grid, sched, s);
-    case 512: return launch_one<T, STAGE, 512>(g, p, U0, U1, Uo, dt, grid, sched, s);
-    default: return launch_one<T, STAGE, 256>(g, p, U0, U1, Uo, dt, grid, sched, s);
+    case 128: return launch_one<T, STAGE, 128>(g, p, U0, U1, Uo, dt, grid, sched, chi, s);
+    case 512: return launch_one<T, STAGE, 512>(g, p, U0, U1, Uo, dt, grid, sched, chi, s);
+    default: return launch_one<T, STAGE, 256>(g, p, U0, U1, Uo, dt, grid, sched, chi, s);
   }
 }
 
 cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                                void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
-                               int grid, int cfg, cudaStream_t s) {
+                               int grid, int cfg, const void *chi, cudaStream_t s) {
   if (fp32)
-    return stage == 1 ? launch_nt<float, 1>(g, p, U0, U1, Uout, dt, grid, cfg, s)
-                      : launch_nt<float, 2>(g, p, U0, U1, Uout, dt, grid, cfg, s);
-  return stage == 1 ? launch_nt<double, 1>(g, p, U0, U1, Uout, dt, grid, cfg, s)
-                    : launch_nt<double, 2>(g, p, U0, U1, Uout, dt, grid, cfg, s);
+    return stage == 1 ? launch_nt<float, 1>(g, p, U0, U1, Uout, dt, grid, cfg, chi, s)
+                      : launch_nt<float, 2>(g, p, U0, U1, Uout, dt, grid, cfg, chi, s);
+  return stage == 1 ? launch_nt<double, 1>(g, p, U0, U1, Uout, dt, grid, cfg, chi, s)
+                    : launch_nt<double, 2>(g, p, U0, U1, Uout, dt, grid, cfg, chi, s);
+}
+
+// ------------------------------------------------------------- flattening ---
+// Shock flattening coefficient chi (Sec. 2.2.1; Colella & Woodward 1984,
+// appendix, and its multidimensional form by Miller & Colella 2002) of every
+// cell within one cell of a patch interior, written into `chi` (same layout as
+// the fields).  Per direction d: ftilde = min(1, max(0, 10 (|dp1|/|dp2| -
+// 0.75))) in a compressive jump (u_{c-1} > u_{c+1}, |dp1| > 0.33 min(p_{c+1},
+// p_{c-1})), else 0, with dp1 = p_{c+1} - p_{c-1}, dp2 = p_{c+2} - p_{c-2};
+// f_d = max(ftilde(c), ftilde(c - sign(dp1))); chi = min_d (1 - f_d).
+template <typename T>
+__device__ __forceinline__ void flat_prim(const F5<T> &U, long long e, double gamma, int d,
+                                          T &pr, T &un) {
+  T u[5], w[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
+  con2prim<T>(u, gamma, w);
+  pr = w[4];
+  un = w[1 + d];
+}
+
+template <typename T>
+__device__ __forceinline__ T flat_ftilde(const T pr[7], const T un[7], int c) {
+  // c indexes the 7-point window -3..3 (c in 2..4)
+  const T dp1 = pr[c + 1] - pr[c - 1], dp2 = pr[c + 2] - pr[c - 2];
+  const bool shock = fabs(dp1) > T(0.33) * min(pr[c + 1], pr[c - 1]) && un[c - 1] - un[c + 1] > T(0);
+  if (!shock) return T(0);
+  if (!(fabs(dp2) > T(0))) return T(1);
+  return min(T(1), max(T(0), T(10) * (qdiv(fabs(dp1), fabs(dp2)) - T(0.75))));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) flatten_kernel(Geometry g, double gamma, F5<T> U, T *chi) {
+  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+    const Tile tl = g.tiles[t];
+    const DevBox b = g.boxes[tl.box];
+    const int v[3] = {min(TS, b.n[0] - tl.x0), min(TS, b.n[1] - tl.y0), min(TS, b.n[2] - tl.z0)};
+    // the tile extended by one cell on every side: (v+2)^3 cells
+    const int ex = v[0] + 2, ey = v[1] + 2, ez = v[2] + 2;
+    for (int l = threadIdx.x; l < ex * ey * ez; l += blockDim.x) {
+      const int c[3] = {l % ex - 1, (l / ex) % ey - 1, l / (ex * ey) - 1};
+      T x = T(1);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T pr[7], un[7];
+#pragma unroll
+        for (int o = -3; o <= 3; ++o) {
+          int cc[3] = {tl.x0 + c[0], tl.y0 + c[1], tl.z0 + c[2]};
+          cc[d] += o;
+          flat_prim<T>(U, cell_elem(b, g.ng, cc[0], cc[1], cc[2]), gamma, d, pr[o + 3], un[o + 3]);
+        }
+        T f = flat_ftilde<T>(pr, un, 3);
+        const T dp1 = pr[4] - pr[2];
+        if (dp1 > T(0)) f = max(f, flat_ftilde<T>(pr, un, 2));
+        else if (dp1 < T(0)) f = max(f, flat_ftilde<T>(pr, un, 4));
+        x = min(x, T(1) - f);
+      }
+      chi[cell_elem(b, g.ng, tl.x0 + c[0], tl.y0 + c[1], tl.z0 + c[2])] = x;
+    }
+  }
+}
+
+cudaError_t launch_flatten(int fp32, const Geometry &g, const qk_params &p, void *const *U,
+                           void *chi, cudaStream_t s) {
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = g.ntiles < nsm * 4 ? g.ntiles : nsm * 4;
+  if (grid < 1) return cudaSuccess;
+  if (fp32) {
+    F5<float> u;
+    for (int q = 0; q < 5; ++q) u.f[q] = (float *)U[q];
+    flatten_kernel<float><<<grid, 512, 0, s>>>(g, p.gamma, u, (float *)chi);
+  } else {
+    F5<double> u;
+    for (int q = 0; q < 5; ++q) u.f[q] = (double *)U[q];
+    flatten_kernel<double><<<grid, 512, 0, s>>>(g, p.gamma, u, (double *)chi);
+  }
+  return cudaGetLastError();
 }
 
 int hydro_smem_bytes(int fp32) {

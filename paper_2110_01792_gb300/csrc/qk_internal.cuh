@@ -204,7 +204,9 @@ constexpr int kDefaultCfg = cfg_make(256, 0);
 
 cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                                void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
-                               int grid, int cfg, cudaStream_t s);
+                               int grid, int cfg, const void *chi, cudaStream_t s);
+cudaError_t launch_flatten(int fp32, const Geometry &g, const qk_params &p, void *const *U,
+                           void *chi, cudaStream_t s);
 cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                              void *const *R0, void *const *R1, void *const *Rout,
                              const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s);

@@ -51,25 +51,31 @@ __device__ __forceinline__ void load_slot(RadSmem<T> &sm, int s, const T u[4], T
   }
 }
 
+// State vector (E, F) and flux along D of a radiation state (E_r, f) with
+// |f|^2 = f2 already known: flux_D = ((chat/c) F_D, c chat E T_xD, c chat E
+// T_yD, c chat E T_zD) (eqs. rad_energy, rad_flux; T from the Levermore closure).
 template <typename T, int D>
-__device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T c, T chat_c, T ccc, T U[4],
-                                            T F[4]) {
-  T Tx, Ty, Tz;
-  eddington_col<T, D>(fx, fy, fz, Tx, Ty, Tz);
+__device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T f2, T c, T chat_c, T ccc,
+                                            T U[4], T F[4]) {
+  T a, b;
+  levermore_ab_f2<T>(f2, a, b);
+  const T fD = D == 0 ? fx : (D == 1 ? fy : fz);
   const T cE = c * E;
   U[0] = E;
   U[1] = cE * fx;
   U[2] = cE * fy;
   U[3] = cE * fz;
   F[0] = chat_c * U[1 + D];
-  F[1] = ccc * (E * Tx);
-  F[2] = ccc * (E * Ty);
-  F[3] = ccc * (E * Tz);
+  const T cEb = ccc * E;                 // c chat E
+  const T bfD = b * fD;
+  F[1] = cEb * (bfD * fx + (D == 0 ? a : T(0)));
+  F[2] = cEb * (bfD * fy + (D == 1 ? a : T(0)));
+  F[3] = cEb * (bfD * fz + (D == 2 ? a : T(0)));
 }
 
 template <typename T, int D, int NT, int NOWN>
 __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx, T dx, T c,
-                                        T chat, int tau_corr, T (&acc)[NOWN][4]) {
+                                        T chat, int tau_corr, int rk, T (&acc)[NOWN][4]) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
   const T ccc = c * chat;
   const T chat_c = chat / c;
@@ -87,8 +93,8 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       T qL, qR;
-      ppm<T>(sm.prim[q][s[0]], sm.prim[q][s[1]], sm.prim[q][s[2]], sm.prim[q][s[3]],
-             sm.prim[q][s[4]], qL, qR);
+      recon<T>(rk, sm.prim[q][s[0]], sm.prim[q][s[1]], sm.prim[q][s[2]], sm.prim[q][s[3]],
+               sm.prim[q][s[4]], qL, qR);
       sm.rec[2 * q][it] = qL;
       sm.rec[2 * q + 1][it] = qR;
     }
@@ -108,42 +114,44 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
       wL[q] = sm.rec[2 * q + 1][il];
       wR[q] = sm.rec[2 * q][ir];
     }
-    const T fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
-    const T fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
+    T fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
+    T fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
     int xa[3] = {cc[0], cc[1], cc[2]}, xb[3] = {cc[0], cc[1], cc[2]};
     xa[D] = f - 1;
     xb[D] = f;
     const int sa = cross_slot(xa[0], xa[1], xa[2]);
     const int sb = cross_slot(xb[0], xb[1], xb[2]);
-    if (fL2 > T(1) || fR2 > T(1)) {
+    if (nn_gt(fL2, T(1)) || nn_gt(fR2, T(1))) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         wL[q] = sm.prim[q][sa];
         wR[q] = sm.prim[q][sb];
       }
+      fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
+      fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
     }
     T UL[4], FL[4], UR[4], FR[4];
-    rad_flux_of<T, D>(wL[0], wL[1], wL[2], wL[3], c, chat_c, ccc, UL, FL);
-    rad_flux_of<T, D>(wR[0], wR[1], wR[2], wR[3], c, chat_c, ccc, UR, FR);
+    rad_flux_of<T, D>(wL[0], wL[1], wL[2], wL[3], fL2, c, chat_c, ccc, UL, FL);
+    rad_flux_of<T, D>(wR[0], wR[1], wR[2], wR[3], fR2, c, chat_c, ccc, UR, FR);
     T S;
     if constexpr (RadSmem<T>::kAB) {
       // sqrt is monotone and correctly rounded: sqrt(max) == max(sqrt)
       const T fa = sm.prim[1 + D][sa], fb = sm.prim[1 + D][sb];
       const T Ta = sm.ab[0][sa] + sm.ab[1][sa] * fa * fa;
       const T Tb = sm.ab[0][sb] + sm.ab[1][sb] * fb * fb;
-      S = chat * qsqrt(max(Ta, Tb));
+      S = chat * qsqrt(nn_max(Ta, Tb));
     } else {
       S = chat * max(sm.sq[il], sm.sq[ir]);
     }
     T eps = T(1);
     if (tau_corr) {
       const T tau = dx * T(0.5) * (sm.rk[sa] + sm.rk[sb]);
-      if (tau > T(1)) eps = qrcp(tau);
+      if (nn_gt(tau, T(1))) eps = qrcp(tau);
     }
     T out[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) out[q] = T(0.5) * (FL[q] + FR[q]) - T(0.5) * S * eps * (UR[q] - UL[q]);
-    if (eps < T(1) && fabs(out[0]) > chat * max(UL[0], UR[0])) {
+    if (nn_gt(T(1), eps) && nn_gt(fabs(out[0]), chat * nn_max(UL[0], UR[0]))) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) out[q] = T(0.5) * (FL[q] + FR[q]) - T(0.5) * S * (UR[q] - UL[q]);
     }
@@ -219,9 +227,9 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
     }
     __syncthreads();
     T acc[NOWN][4];
-    rad_dir<T, 0, NT, NOWN>(sm, v, inv_dx[0], dx[0], c, chat, p.tau_correction, acc);
-    rad_dir<T, 1, NT, NOWN>(sm, v, inv_dx[1], dx[1], c, chat, p.tau_correction, acc);
-    rad_dir<T, 2, NT, NOWN>(sm, v, inv_dx[2], dx[2], c, chat, p.tau_correction, acc);
+    rad_dir<T, 0, NT, NOWN>(sm, v, inv_dx[0], dx[0], c, chat, p.tau_correction, p.recon, acc);
+    rad_dir<T, 1, NT, NOWN>(sm, v, inv_dx[1], dx[1], c, chat, p.tau_correction, p.recon, acc);
+    rad_dir<T, 2, NT, NOWN>(sm, v, inv_dx[2], dx[2], c, chat, p.tau_correction, p.recon, acc);
 #pragma unroll
     for (int m = 0; m < NOWN; ++m) {
       int s = threadIdx.x + m * NT;

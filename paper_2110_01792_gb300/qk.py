@@ -37,6 +37,7 @@ class Params(C.Structure):
         ("eps_newton", C.c_double), ("dx", C.c_double * 3),
         ("kappa_mode", C.c_int32), ("eos", C.c_int32), ("max_iter", C.c_int32),
         ("nsub_max", C.c_int32), ("tau_correction", C.c_int32), ("hydro_only", C.c_int32),
+        ("recon", C.c_int32), ("flattening", C.c_int32),
     ]
 
 
@@ -110,6 +111,8 @@ def make_params(**kw) -> Params:
     p.nsub_max = int(kw.get("nsub_max", 10))
     p.tau_correction = int(kw.get("tau_correction", 1))
     p.hydro_only = int(kw.get("hydro_only", 0))
+    p.recon = int(kw.get("recon", 0))
+    p.flattening = int(kw.get("flattening", 0))
     return p
 
 

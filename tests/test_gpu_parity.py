@@ -435,3 +435,57 @@ def test_shock_tube_thin_axes_gpu(torch_cuda, axis):
     _check_dt(hg, hr)
     e = G.max_rel_err(lay, Ug, Ur)
     assert max(e) <= TOL_STEPS, e
+
+
+@pytest.mark.parametrize("recon,flat", [(1, 0), (0, 1), (1, 1)], ids=["plm", "ppm_flat", "plm_flat"])
+def test_stages_with_plm_and_flattening(torch_cuda, recon, flat):
+    """PLM-MC reconstruction and Miller & Colella shock flattening (Sec. 2.2.1)
+    on random data with strong compressive jumps: one hydro stage and one
+    radiation stage (PLM for radiation too, never flattened) agree with the
+    oracle to 1e-12."""
+    torch = torch_cuda
+    lay = RAGGED
+    prob, prm = _random_rhd(lay, 8)
+    rng = np.random.Generator(np.random.Philox(31))
+    for b in range(lay.nbox):  # pressure jumps of a factor 2-10 with converging flow
+        E = lay.interior(prob.U[4], b)
+        E *= np.where(rng.random(E.shape) < 0.15, rng.uniform(2, 10, E.shape), 1.0)
+    prm = dict(prm, recon=recon, flattening=flat)
+    p = O.make_params(**prm)
+    g = _grid(lay)
+    dt = 0.2 * O.timestep(g, p, prob.U)[0]
+    U1r = [np.zeros_like(a) for a in prob.U]
+    O.hydro_stage(g, p, 1, prob.U, None, U1r, dt)
+    dtr = 0.3 * (1.0 / 19) / prm["chat"]
+    R1r = [np.zeros_like(a) for a in prob.R]
+    O.rad_stage(g, p, 1, prob.R, None, R1r, prob.U[0], dtr)
+    ctx = _ctx(lay, prm)
+    dU, dR = G.dev(prob.U), G.dev(prob.R)
+    dU1 = [torch.zeros_like(a) for a in dU]
+    dR1 = [torch.zeros_like(a) for a in dR]
+    ctx.fill_ghosts(dU + dR)
+    ctx.hydro_stage(1, dU, None, dU1, dt)
+    ctx.rad_stage(1, dR, None, dR1, dU[0], dtr)
+    torch.cuda.synchronize()
+    eh = G.max_rel_err(lay, G.host(dU1), U1r)
+    er = G.max_rel_err(lay, G.host(dR1), R1r)
+    ctx.close()
+    assert max(eh) <= TOL_STAGE, eh
+    assert max(er) <= TOL_STAGE, er
+
+
+def test_shock_tube_with_flattening_ten_steps_gpu(torch_cuda):
+    """The stationary shock tube of Sec. 3.1.3 (x0 = 2, rho/p = 10/100 | 1/1,
+    CFL 0.1) with flattening: 40 steps on the GPU agree with the oracle to
+    1e-10."""
+    N = 200
+    x = P.centres(N, 10.0)
+    inside = (x >= 2.0) & (x < 8.0)
+    lay, U = P.hydro_line(N, np.where(inside, 1.0, 10.0), 0.0, np.where(inside, 1.0, 100.0), 1.4)
+    prm = dict(gamma=1.4, cfl=0.1, dx=[10.0 / N, 1.0, 1.0], hydro_only=1, flattening=1)
+    prob = I.Problem("tube", lay, prm, U)
+    Ug, _, hg, _ = _run_gpu_steps(lay, prob, prm, 40)
+    Ur, _, hr = _run_oracle_steps(lay, prob, prm, 40)
+    _check_dt(hg, hr)
+    e = G.max_rel_err(lay, Ug, Ur)
+    assert max(e) <= TOL_STEPS, e
