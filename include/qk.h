@@ -103,6 +103,24 @@ typedef struct {
 int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
                     const int32_t domain_n[3], int32_t nghost, int32_t precision);
 
+/* A shard of a patch set for one rank of a multi-GPU run (Sec. 4: the
+ * update is distributed by patches and the ghost exchange between them is
+ * the only data-path communication).  `boxes`, `nbox`, `domain_n` describe the
+ * WHOLE patch set, identically on every rank; owner[b] in [0, nranks) names
+ * the rank that holds patch b (caller-owned host array of nbox entries).  This
+ * context advances only the patches with owner[b] == rank: their offsets
+ * place them in this rank's field arrays (offsets of other ranks' patches are
+ * not read) and every per-cell entry point works on them alone.
+ * qk_fill_ghosts then fills only the ghost regions whose source is also owned
+ * here; the rest travel through qk_halo_pack / qk_halo_unpack.  With
+ * nranks > 1, qk_step and qk_timestep return QK_EINVAL (they would need the
+ * other ranks' cells): a sharded step is composed from the stage entry points,
+ * qk_signal_speed and qk_set_timestep.  Returns QK_EINVAL
+ * when owner is NULL, an owner is out of range, or the rank owns no patch. */
+int qk_init_shard(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
+                  const int32_t domain_n[3], int32_t nghost, int32_t precision,
+                  const int32_t *owner, int32_t nranks, int32_t rank);
+
 /* Free the context and all library-owned device memory. */
 void qk_destroy(qk_ctx *ctx);
 
@@ -242,6 +260,41 @@ int qk_conserved_sums_noalloc(const qk_params *p, const qk_box *boxes, int32_t n
                               int32_t nghost, int32_t precision, void *const hydro[5],
                               void *const rad[4], double out[QK_NSUMS], void *stream,
                               char *err, int32_t errlen);
+
+/* Halo sizes of a sharded context: *send_cells = cells per field this rank
+ * sends to `peer`, *recv_cells = cells per field it receives from `peer`,
+ * *owned_boxes = patches this rank holds (any pointer may be NULL).  For a
+ * context from qk_init_patches there is one rank (peer 0, no halo). */
+int qk_halo_info(const qk_ctx *ctx, int32_t peer, int64_t *send_cells, int64_t *recv_cells,
+                 int32_t *owned_boxes);
+
+/* Cross-rank ghost exchange (Sec. 4, FillBoundary across GPUs).  Pack gathers,
+ * from this rank's `nfields` field arrays, the interior cells that `peer`'s
+ * ghost regions need, into the device buffer `buf` of nfields x send_cells
+ * elements (the context's precision; field-major, regions in one order agreed
+ * by both ranks, x fastest).  Unpack scatters a buffer received from `peer`
+ * (nfields x recv_cells elements, same layout) into this rank's ghost cells.
+ * The caller moves the buffer between the ranks (NCCL send/recv, a peer copy,
+ * or a plain device copy when both ranks share one GPU); the library never
+ * waits on another rank.  A full ghost fill of a sharded context is
+ * qk_fill_ghosts plus, for every peer, pack -> transfer -> unpack.  QK_EINVAL
+ * for peer == this rank or out of range; nothing is launched when the halo to
+ * that peer is empty. */
+int qk_halo_pack(qk_ctx *ctx, int32_t peer, void *const *fields, int32_t nfields, void *buf,
+                 void *stream);
+int qk_halo_unpack(qk_ctx *ctx, int32_t peer, void *const *fields, int32_t nfields,
+                   const void *buf, void *stream);
+
+/* Global timestep of a sharded step, in two halves around the caller's
+ * max-reduction over ranks (Sec. 2.2: one dt from the CFL condition on the
+ * whole domain).  qk_signal_speed writes the maximum of |v| + c_s over this
+ * context's cells to *smax (host); qk_set_timestep takes the global maximum
+ * and computes dt, N_sub and dt_rad on the device exactly as qk_step does,
+ * writing (dt, N_sub, dt_rad, smax) to out (may be NULL).  Both synchronise
+ * `stream`.  qk_set_timestep returns QK_EINVAL unless smax is positive and
+ * finite. */
+int qk_signal_speed(qk_ctx *ctx, void *const hydro[5], double *smax, void *stream);
+int qk_set_timestep(qk_ctx *ctx, double smax, double out[4], void *stream);
 
 /* Read the accumulated exchange status (synchronises `stream`):
  * *flags = bit (1 << QK_ENOCONV) | bit (1 << QK_ENEGATIVE); *first_bad = the

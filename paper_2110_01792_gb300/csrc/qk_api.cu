@@ -27,7 +27,18 @@ struct qk_ctx {
   Tile *d_tiles = nullptr;
   long long *d_cell0 = nullptr;
   int ntiles = 0;
-  std::vector<int> tile_start;  // first tile of each patch (tiles are grouped by patch)
+  int nbox_dev = 0;            // patches in the device table (the owned ones)
+  std::vector<int> tile_start;  // first tile of each owned patch (tiles grouped by patch)
+  // sharded contexts: owner rank of every patch, this rank, and the halo
+  // descriptors exchanged with each peer (send: owned source -> buffer;
+  // recv: buffer -> owned ghost region), in one global order on every rank
+  std::vector<int> owner;
+  int rank = 0, nranks = 1;
+  std::vector<int> own;          // owned patch indices (global numbering)
+  Copy *d_send = nullptr, *d_recv = nullptr;
+  Chunk *d_send_chunks = nullptr, *d_recv_chunks = nullptr;
+  std::vector<int> send_chunk0, recv_chunk0;  // per peer: chunk range [p], [p+1)
+  std::vector<long long> send_cells, recv_cells;
   int launch_mode = QK_LAUNCH_BATCHED;
   int cfg[4] = {kDefaultCfg, kDefaultCfg, kDefaultCfg, kDefaultCfg};  // hydro1/2, rad1/2
   Copy *d_copies = nullptr;
@@ -78,7 +89,7 @@ static Geometry geom(const qk_ctx *c) {
   g.boxes = c->d_boxes;
   g.tiles = c->d_tiles;
   g.ntiles = c->ntiles;
-  g.nbox = c->nbox;
+  g.nbox = c->nbox_dev;
   g.ng = c->ng;
   g.ncells = c->ncells;
   g.box_cell0 = c->d_cell0;
@@ -119,7 +130,9 @@ static int64_t padded_vol(const qk_box &b, int ng) {
 // Ghost-copy descriptors: for each patch, the 26 ghost sub-boxes around its
 // interior, intersected with every patch's interior under every periodic
 // shift that reaches them.  A binned index of the patches keeps this linear.
-static int build_copies(qk_ctx *c, std::vector<Copy> &out) {
+static int build_copies(qk_ctx *c, std::vector<Copy> &out,
+                        std::vector<std::vector<Copy>> *send = nullptr,
+                        std::vector<std::vector<Copy>> *recv = nullptr) {
   const int ng = c->ng;
   const int *D = c->dom;
   const int BIN = 16;
@@ -139,9 +152,12 @@ static int build_copies(qk_ctx *c, std::vector<Copy> &out) {
   }
   std::vector<int> stamp(c->nbox, -1);
   int stamp_id = 0;
+  const bool sharded = !c->owner.empty();
   for (int b = 0; b < c->nbox; ++b) {
     const qk_box &B = c->boxes[b];
     const int sx = B.n[0] + 2 * ng, sy = B.n[1] + 2 * ng;
+    // a sharded rank visits every destination patch: remote destinations
+    // can still need this rank's patches as sources (send lists)
     for (int rz = 0; rz < 3; ++rz)
       for (int ry = 0; ry < 3; ++ry)
         for (int rx = 0; rx < 3; ++rx) {
@@ -204,7 +220,14 @@ static int build_copies(qk_ctx *c, std::vector<Copy> &out) {
                         cp.dsy = sy;
                         cp.ssx = qsx;
                         cp.ssy = qsy;
-                        out.push_back(cp);
+                        if (!sharded) {
+                          out.push_back(cp);
+                        } else {
+                          const int rb = c->owner[b], rq = c->owner[q];
+                          if (rb == c->rank && rq == c->rank) out.push_back(cp);
+                          else if (rb == c->rank) (*recv)[rq].push_back(cp);
+                          else if (rq == c->rank) (*send)[rb].push_back(cp);
+                        }
                       }
               }
         }
@@ -245,9 +268,10 @@ static int validate_boxes(qk_ctx *c) {
       if (ov) return fail(c, QK_EINVAL, "boxes %d and %d overlap", order[a], order[b]);
     }
   }
-  // disjoint field ranges
-  std::vector<int> byoff(c->nbox);
-  for (int b = 0; b < c->nbox; ++b) byoff[b] = b;
+  // disjoint field ranges (of the owned patches in a sharded context)
+  std::vector<int> byoff;
+  for (int b = 0; b < c->nbox; ++b)
+    if (c->owner.empty() || c->owner[b] == c->rank) byoff.push_back(b);
   std::sort(byoff.begin(), byoff.end(),
             [&](int a, int b) { return c->boxes[a].offset < c->boxes[b].offset; });
   int64_t end = 0;
@@ -257,7 +281,8 @@ static int validate_boxes(qk_ctx *c) {
     end = q.offset + padded_vol(q, ng);
   }
   c->field_len = end;
-  c->ncells = tot;
+  c->ncells = 0;
+  for (int b : byoff) c->ncells += (int64_t)c->boxes[b].n[0] * c->boxes[b].n[1] * c->boxes[b].n[2];
   return QK_OK;
 }
 
@@ -276,6 +301,10 @@ static void release(qk_ctx *c) {
   cudaFree(c->d_cell0);
   cudaFree(c->d_copies);
   cudaFree(c->d_chunks);
+  cudaFree(c->d_send);
+  cudaFree(c->d_recv);
+  cudaFree(c->d_send_chunks);
+  cudaFree(c->d_recv_chunks);
   cudaFree(c->d_si);
   cudaFree(c->d_status);
   cudaFree(c->d_partials);
@@ -287,8 +316,9 @@ static void release(qk_ctx *c) {
 
 extern "C" {
 
-int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
-                    const int32_t domain_n[3], int32_t nghost, int32_t precision) {
+static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
+                       const int32_t domain_n[3], int32_t nghost, int32_t precision,
+                       const int32_t *owner, int32_t nranks, int32_t rank) {
   if (!out) return QK_EINVAL;
   *out = nullptr;
   qk_ctx *c = new qk_ctx();
@@ -315,35 +345,84 @@ int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32
   c->nbox = nbox;
   for (int d = 0; d < 3; ++d) c->dom[d] = domain_n[d];
   c->boxes.assign(boxes, boxes + nbox);
+  if (owner) {
+    if (nranks < 1 || rank < 0 || rank >= nranks)
+      return bail(fail(c, QK_EINVAL, "rank %d of %d ranks", rank, nranks));
+    c->owner.assign(owner, owner + nbox);
+    for (int b = 0; b < nbox; ++b)
+      if (owner[b] < 0 || owner[b] >= nranks)
+        return bail(fail(c, QK_EINVAL, "patch %d: owner %d outside [0, %d)", b, owner[b], nranks));
+    c->rank = rank;
+    c->nranks = nranks;
+  }
   if ((rc = validate_boxes(c))) return bail(rc);
+  for (int b = 0; b < nbox; ++b)
+    if (c->owner.empty() || c->owner[b] == c->rank) c->own.push_back(b);
+  if (c->own.empty()) return bail(fail(c, QK_EINVAL, "rank %d owns no patch", rank));
 
-  // device boxes and the interior-cell prefix
-  std::vector<DevBox> db(nbox);
-  std::vector<long long> cell0(nbox + 1, 0);
-  for (int b = 0; b < nbox; ++b) {
-    const qk_box &q = boxes[b];
+  // device table of the owned patches and their interior-cell prefix
+  const int nown = (int)c->own.size();
+  std::vector<DevBox> db(nown);
+  std::vector<long long> cell0(nown + 1, 0);
+  for (int l = 0; l < nown; ++l) {
+    const qk_box &q = boxes[c->own[l]];
     for (int d = 0; d < 3; ++d) {
-      db[b].lo[d] = q.lo[d];
-      db[b].n[d] = q.n[d];
+      db[l].lo[d] = q.lo[d];
+      db[l].n[d] = q.n[d];
     }
-    db[b].sx = q.n[0] + 2 * nghost;
-    db[b].sy = q.n[1] + 2 * nghost;
-    db[b].off = q.offset;
-    db[b].cell0 = cell0[b];
-    cell0[b + 1] = cell0[b] + (long long)q.n[0] * q.n[1] * q.n[2];
+    db[l].sx = q.n[0] + 2 * nghost;
+    db[l].sy = q.n[1] + 2 * nghost;
+    db[l].off = q.offset;
+    db[l].cell0 = cell0[l];
+    cell0[l + 1] = cell0[l] + (long long)q.n[0] * q.n[1] * q.n[2];
   }
   std::vector<Tile> tiles;
-  c->tile_start.assign(nbox + 1, 0);
-  for (int b = 0; b < nbox; ++b) {
-    c->tile_start[b] = (int)tiles.size();
-    for (int z = 0; z < boxes[b].n[2]; z += TS)
-      for (int y = 0; y < boxes[b].n[1]; y += TS)
-        for (int x = 0; x < boxes[b].n[0]; x += TS) tiles.push_back(Tile{b, x, y, z});
+  c->tile_start.assign(nown + 1, 0);
+  for (int l = 0; l < nown; ++l) {
+    const qk_box &q = boxes[c->own[l]];
+    c->tile_start[l] = (int)tiles.size();
+    for (int z = 0; z < q.n[2]; z += TS)
+      for (int y = 0; y < q.n[1]; y += TS)
+        for (int x = 0; x < q.n[0]; x += TS) tiles.push_back(Tile{l, x, y, z});
   }
-  c->tile_start[nbox] = (int)tiles.size();
+  c->tile_start[nown] = (int)tiles.size();
   c->ntiles = (int)tiles.size();
   std::vector<Copy> copies;
-  build_copies(c, copies);
+  std::vector<std::vector<Copy>> send(c->nranks), recv(c->nranks);
+  build_copies(c, copies, &send, &recv);
+  // halo descriptors: the send side packs each region contiguously (x fastest)
+  // into the peer's buffer; the receive side unpacks in the same order
+  std::vector<Copy> sd, rv;
+  std::vector<Chunk> sch, rch;
+  c->send_chunk0.assign(c->nranks + 1, 0);
+  c->recv_chunk0.assign(c->nranks + 1, 0);
+  c->send_cells.assign(c->nranks, 0);
+  c->recv_cells.assign(c->nranks, 0);
+  for (int pr = 0; pr < c->nranks; ++pr) {
+    c->send_chunk0[pr] = (int)sch.size();
+    for (Copy cp : send[pr]) {
+      cp.dst = c->send_cells[pr];  // position in the peer's buffer
+      sd.push_back(cp);
+      const int n = cp.ex * cp.ey * cp.ez;
+      for (int s0 = 0; s0 < n; s0 += CHUNK_CELLS) sch.push_back(Chunk{(int)sd.size() - 1, s0});
+      c->send_cells[pr] += n;
+    }
+    c->recv_chunk0[pr] = (int)rch.size();
+    for (Copy cp : recv[pr]) {
+      cp.src = c->recv_cells[pr];
+      rv.push_back(cp);
+      const int n = cp.ex * cp.ey * cp.ez;
+      for (int s0 = 0; s0 < n; s0 += CHUNK_CELLS) rch.push_back(Chunk{(int)rv.size() - 1, s0});
+      c->recv_cells[pr] += n;
+    }
+  }
+  c->send_chunk0[c->nranks] = (int)sch.size();
+  c->recv_chunk0[c->nranks] = (int)rch.size();
+  if ((rc = upload(c, &c->d_send, sd))) return bail(rc);
+  if ((rc = upload(c, &c->d_recv, rv))) return bail(rc);
+  if ((rc = upload(c, &c->d_send_chunks, sch))) return bail(rc);
+  if ((rc = upload(c, &c->d_recv_chunks, rch))) return bail(rc);
+  c->nbox_dev = nown;
   std::vector<Chunk> chunks;
   for (int i = 0; i < (int)copies.size(); ++i) {
     int n = copies[i].ex * copies[i].ey * copies[i].ez;
@@ -387,6 +466,21 @@ int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32
     return bail(cuda_fail(c, e, "cudaStreamCreate"));
   *out = c;
   return QK_OK;
+}
+
+int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
+                    const int32_t domain_n[3], int32_t nghost, int32_t precision) {
+  return init_common(out, p, boxes, nbox, domain_n, nghost, precision, nullptr, 1, 0);
+}
+
+int qk_init_shard(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
+                  const int32_t domain_n[3], int32_t nghost, int32_t precision,
+                  const int32_t *owner, int32_t nranks, int32_t rank) {
+  if (!owner) {
+    g_init_err = "qk_init_shard: owner is NULL";
+    return QK_EINVAL;
+  }
+  return init_common(out, p, boxes, nbox, domain_n, nghost, precision, owner, nranks, rank);
 }
 
 void qk_destroy(qk_ctx *c) {
@@ -601,6 +695,8 @@ int qk_timestep(qk_ctx *c, void *const hydro[5], double out[4], void *stream) {
   int rc = check_fields(c, hydro, 5, "hydro");
   if (rc) return rc;
   if (!out) return fail(c, QK_EINVAL, "out is NULL");
+  if (c->nranks > 1)
+    return fail(c, QK_EINVAL, "sharded context: use qk_signal_speed and qk_set_timestep");
   cudaStream_t s = (cudaStream_t)stream;
   QK_CUDA(c, launch_max_speed(c->fp32, geom(c), c->p, hydro, c->d_si, s));
   QK_CUDA(c, launch_timestep(c->p, c->d_si, s));
@@ -627,7 +723,7 @@ static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *c
   if (c->launch_mode == QK_LAUNCH_BATCHED)
     return launch_hydro_stage(c->fp32, stage, g, c->p, U0, U1, Uo, dt, 0, c->cfg[stage - 1], chi,
                               s);
-  for (int b = 0; b < c->nbox; ++b) {
+  for (int b = 0; b < c->nbox_dev; ++b) {
     Geometry gb = g;
     gb.tiles = c->d_tiles + c->tile_start[b];
     gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
@@ -643,7 +739,7 @@ static cudaError_t rad_launches(qk_ctx *c, int stage, void *const *R0, void *con
   const Geometry g = geom(c);
   if (c->launch_mode == QK_LAUNCH_BATCHED)
     return launch_rad_stage(c->fp32, stage, g, c->p, R0, R1, Ro, rho, dt, 0, c->cfg[1 + stage], s);
-  for (int b = 0; b < c->nbox; ++b) {
+  for (int b = 0; b < c->nbox_dev; ++b) {
     Geometry gb = g;
     gb.tiles = c->d_tiles + c->tile_start[b];
     gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
@@ -688,6 +784,8 @@ int qk_step(qk_ctx *c, void *const hydro[5], void *const rad[4], double *dt_out,
   int rc = check_fields(c, hydro, 5, "hydro");
   if (rc) return rc;
   if (rad && (rc = check_fields(c, rad, 4, "rad"))) return rc;
+  if (c->nranks > 1)
+    return fail(c, QK_EINVAL, "sharded context: compose the step from the stage entry points");
   cudaStream_t s = (cudaStream_t)stream;
   if (c->use_graph) {
     void *key[10];
@@ -759,6 +857,76 @@ int qk_conserved_sums(qk_ctx *c, void *const hydro[5], void *const rad[4], doubl
   QK_CUDA(c, cudaMemcpyAsync(c->h_buf, c->d_sums, QK_NSUMS * sizeof(double), cudaMemcpyDeviceToHost, s));
   QK_CUDA(c, cudaStreamSynchronize(s));
   memcpy(out, c->h_buf, QK_NSUMS * sizeof(double));
+  return QK_OK;
+}
+
+int qk_halo_info(const qk_ctx *c, int32_t peer, int64_t *send_cells, int64_t *recv_cells,
+                 int32_t *owned_boxes) {
+  if (!c) return QK_EINVAL;
+  if (peer < 0 || peer >= c->nranks) return QK_EINVAL;
+  if (send_cells) *send_cells = c->send_cells[peer];
+  if (recv_cells) *recv_cells = c->recv_cells[peer];
+  if (owned_boxes) *owned_boxes = (int32_t)c->own.size();
+  return QK_OK;
+}
+
+static int halo(qk_ctx *c, int pack, int32_t peer, void *const *fields, int32_t nfields,
+                void *buf, void *stream) {
+  if (!c) return QK_EINVAL;
+  if (peer < 0 || peer >= c->nranks) return fail(c, QK_EINVAL, "peer %d outside [0, %d)", peer, c->nranks);
+  if (peer == c->rank) return fail(c, QK_EINVAL, "peer %d is this rank", peer);
+  if (nfields < 1 || nfields > 9) return fail(c, QK_EINVAL, "nfields must be in [1, 9]");
+  int rc = check_fields(c, fields, nfields, "fields");
+  if (rc) return rc;
+  const int *ch0 = pack ? c->send_chunk0.data() : c->recv_chunk0.data();
+  const long long n = pack ? c->send_cells[peer] : c->recv_cells[peer];
+  if (n == 0) return QK_OK;
+  if (!buf) return fail(c, QK_EINVAL, "buf is NULL");
+  QK_CUDA(c, launch_halo(c->fp32, pack, pack ? c->d_send : c->d_recv,
+                         (pack ? c->d_send_chunks : c->d_recv_chunks) + ch0[peer],
+                         ch0[peer + 1] - ch0[peer], fields, nfields, buf, n,
+                         (cudaStream_t)stream));
+  return QK_OK;
+}
+
+int qk_halo_pack(qk_ctx *c, int32_t peer, void *const *fields, int32_t nfields, void *buf,
+                 void *stream) {
+  return halo(c, 1, peer, fields, nfields, buf, stream);
+}
+
+int qk_halo_unpack(qk_ctx *c, int32_t peer, void *const *fields, int32_t nfields,
+                   const void *buf, void *stream) {
+  return halo(c, 0, peer, fields, nfields, const_cast<void *>(buf), stream);
+}
+
+int qk_signal_speed(qk_ctx *c, void *const hydro[5], double *smax, void *stream) {
+  if (!c) return QK_EINVAL;
+  int rc = check_fields(c, hydro, 5, "hydro");
+  if (rc) return rc;
+  if (!smax) return fail(c, QK_EINVAL, "smax is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  QK_CUDA(c, launch_max_speed(c->fp32, geom(c), c->p, hydro, c->d_si, s));
+  unsigned long long *hb = (unsigned long long *)(c->h_buf + 40);
+  QK_CUDA(c, cudaMemcpyAsync(hb, &c->d_si->smax_bits, sizeof(*hb), cudaMemcpyDeviceToHost, s));
+  // the running maximum starts from zero at every step
+  QK_CUDA(c, cudaMemsetAsync(&c->d_si->smax_bits, 0, sizeof(*hb), s));
+  QK_CUDA(c, cudaStreamSynchronize(s));
+  memcpy(smax, hb, sizeof(double));
+  return QK_OK;
+}
+
+int qk_set_timestep(qk_ctx *c, double smax, double out[4], void *stream) {
+  if (!c) return QK_EINVAL;
+  if (!(smax > 0.0) || smax != smax || smax > 1.7976931348623157e308)
+    return fail(c, QK_EINVAL, "smax must be positive and finite");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *hv = c->h_buf + 41;
+  *hv = smax;
+  QK_CUDA(c, cudaMemcpyAsync(&c->d_si->smax_bits, hv, sizeof(double), cudaMemcpyHostToDevice, s));
+  QK_CUDA(c, launch_timestep(c->p, c->d_si, s));
+  QK_CUDA(c, cudaMemcpyAsync(c->h_buf + 42, c->d_si, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  QK_CUDA(c, cudaStreamSynchronize(s));
+  if (out) memcpy(out, c->h_buf + 42, 4 * sizeof(double));
   return QK_OK;
 }
 

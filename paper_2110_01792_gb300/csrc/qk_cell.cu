@@ -454,6 +454,64 @@ cudaError_t launch_ghost_fill(int fp32, const Copy *copies, const Chunk *chunks,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------- halo pack ---
+// Cross-rank part of the ghost fill.  The sending rank gathers, for each
+// region a peer needs, the interior cells of its own patch into a contiguous
+// buffer (x fastest, regions in the agreed order, one block of `npeer` cells
+// per field); the receiving rank scatters the same buffer into the ghost
+// regions.  A descriptor's strided side is (src, ssx, ssy) when packing and
+// (dst, dsx, dsy) when unpacking; its other side is the buffer position.
+template <typename T, bool PACK>
+__global__ void __launch_bounds__(256) halo_kernel(const Copy *copies, const Chunk *chunks,
+                                                   F5<T> fa, F4<T> fb, int nf, T *buf,
+                                                   long long npeer) {
+  const Chunk ch = chunks[blockIdx.x];
+  const Copy cp = copies[ch.copy];
+  const int ncell = cp.ex * cp.ey * cp.ez;
+  const int end = min(ncell, ch.start + CHUNK_CELLS);
+  for (int l = ch.start + threadIdx.x; l < end; l += blockDim.x) {
+    const int x = l % cp.ex;
+    const int r = l / cp.ex;
+    const int y = r % cp.ey;
+    const int z = r / cp.ey;
+    long long e, q;  // field element, buffer position
+    if (PACK) {
+      e = cp.src + ((long long)z * cp.ssy + y) * cp.ssx + x;
+      q = cp.dst + l;
+    } else {
+      e = cp.dst + ((long long)z * cp.dsy + y) * cp.dsx + x;
+      q = cp.src + l;
+    }
+#pragma unroll
+    for (int f = 0; f < 9; ++f) {
+      if (f >= nf) break;
+      T *fld = f < 5 ? fa.f[f] : fb.f[f - 5];
+      if (PACK) buf[f * npeer + q] = fld[e];
+      else fld[e] = buf[f * npeer + q];
+    }
+  }
+}
+
+cudaError_t launch_halo(int fp32, int pack, const Copy *copies, const Chunk *chunks, int nchunks,
+                        void *const *fields, int nf, void *buf, long long npeer,
+                        cudaStream_t s) {
+  if (nchunks < 1 || nf < 1) return cudaSuccess;
+  if (fp32) {
+    F5<float> a{}; F4<float> b{};
+    for (int q = 0; q < nf && q < 5; ++q) a.f[q] = (float *)fields[q];
+    for (int q = 5; q < nf; ++q) b.f[q - 5] = (float *)fields[q];
+    if (pack) halo_kernel<float, true><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, (float *)buf, npeer);
+    else halo_kernel<float, false><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, (float *)buf, npeer);
+  } else {
+    F5<double> a{}; F4<double> b{};
+    for (int q = 0; q < nf && q < 5; ++q) a.f[q] = (double *)fields[q];
+    for (int q = 5; q < nf; ++q) b.f[q - 5] = (double *)fields[q];
+    if (pack) halo_kernel<double, true><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, (double *)buf, npeer);
+    else halo_kernel<double, false><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, (double *)buf, npeer);
+  }
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------ conservation sums ---
 // Double-double accumulation (Knuth's TwoSum) with a fixed assignment of cells
 // to threads and a fixed reduction tree: the result is bitwise reproducible.

@@ -214,6 +214,9 @@ cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, voi
                             void *const *R, DtSrc dt, Status *st, cudaStream_t s);
 cudaError_t launch_max_speed(int fp32, const Geometry &g, const qk_params &p,
                              void *const *U, StepInfo *si, cudaStream_t s);
+cudaError_t launch_halo(int fp32, int pack, const Copy *copies, const Chunk *chunks, int nchunks,
+                        void *const *fields, int nf, void *buf, long long npeer,
+                        cudaStream_t s);
 cudaError_t launch_timestep(const qk_params &p, StepInfo *si, cudaStream_t s);
 cudaError_t launch_ghost_fill(int fp32, const Copy *copies, const Chunk *chunks, int nchunks,
                               void *const *fields, int nf, DtSrc pred, cudaStream_t s);

@@ -79,7 +79,14 @@ def lib():
     L.qk_conserved_sums.argtypes = [vp, P(vp), P(vp), P(dbl), vp]
     L.qk_step_info.argtypes = [vp, P(dbl), vp]
     L.qk_status.argtypes = [vp, P(C.c_uint32), P(i64), P(i32), i32, vp]
-    for f in ("qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_autotune",
+    L.qk_init_shard.argtypes = [P(vp), P(Params), P(Box), i32, P(i32), i32, i32, P(i32), i32, i32]
+    L.qk_halo_info.argtypes = [vp, i32, P(i64), P(i64), P(i32)]
+    L.qk_halo_pack.argtypes = [vp, i32, P(vp), i32, vp, vp]
+    L.qk_halo_unpack.argtypes = [vp, i32, P(vp), i32, vp, vp]
+    L.qk_signal_speed.argtypes = [vp, P(vp), P(dbl), vp]
+    L.qk_set_timestep.argtypes = [vp, dbl, P(dbl), vp]
+    for f in ("qk_init_shard", "qk_halo_info", "qk_halo_pack", "qk_halo_unpack",
+              "qk_signal_speed", "qk_set_timestep", "qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_autotune",
               "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
               "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
               "qk_status", "qk_step_info"):
@@ -131,9 +138,14 @@ def _ptrs(fields, n):
 
 
 class Context:
-    """A patch set on the current CUDA device (wraps qk_init_patches)."""
+    """A patch set on the current CUDA device (wraps qk_init_patches).
 
-    def __init__(self, layout, params: dict, precision: int = FP64):
+    With ``owner`` (owner rank of every patch) and ``rank``, the context is
+    this rank's shard of the patch set (qk_init_shard): ``layout`` then holds
+    the whole patch set with this rank's patches placed in its own field
+    arrays (see ``shard.rank_layout``)."""
+
+    def __init__(self, layout, params: dict, precision: int = FP64, owner=None, rank: int = 0):
         self._L = lib()
         nb = layout.nbox
         boxes = (Box * nb)()
@@ -147,8 +159,18 @@ class Context:
         self.precision = precision
         self.layout = layout
         h = C.c_void_p()
-        rc = self._L.qk_init_patches(C.byref(h), C.byref(self.params), boxes, nb, dom,
-                                     int(layout.ng), int(precision))
+        self.rank, self.nranks = 0, 1
+        if owner is None:
+            rc = self._L.qk_init_patches(C.byref(h), C.byref(self.params), boxes, nb, dom,
+                                         int(layout.ng), int(precision))
+        else:
+            own = np.ascontiguousarray(owner, dtype=np.int32)
+            assert own.shape == (nb,)
+            self.rank, self.nranks = int(rank), int(own.max()) + 1
+            rc = self._L.qk_init_shard(C.byref(h), C.byref(self.params), boxes, nb, dom,
+                                       int(layout.ng), int(precision),
+                                       own.ctypes.data_as(C.POINTER(C.c_int32)),
+                                       self.nranks, self.rank)
         if rc != OK:
             raise QKError(rc, self._L.qk_last_error(None).decode())
         self._h = h
@@ -247,3 +269,32 @@ class Context:
         rc = self._L.qk_status(self._h, C.byref(fl), C.byref(fb), C.byref(mi), 1 if reset else 0,
                                _stream(stream))
         return rc, int(fl.value), int(fb.value), int(mi.value)
+
+    # ---- sharded contexts (one rank of a multi-GPU run) ----
+    def halo_cells(self, peer):
+        """(cells per field sent to peer, cells per field received from peer)."""
+        s, r = C.c_int64(), C.c_int64()
+        self._check(self._L.qk_halo_info(self._h, int(peer), C.byref(s), C.byref(r), None))
+        return int(s.value), int(r.value)
+
+    def halo_pack(self, peer, fields, buf, stream=None):
+        self._check(self._L.qk_halo_pack(self._h, int(peer), _ptrs(fields, len(fields)),
+                                         len(fields), C.c_void_p(int(buf.data_ptr())),
+                                         _stream(stream)))
+
+    def halo_unpack(self, peer, fields, buf, stream=None):
+        self._check(self._L.qk_halo_unpack(self._h, int(peer), _ptrs(fields, len(fields)),
+                                           len(fields), C.c_void_p(int(buf.data_ptr())),
+                                           _stream(stream)))
+
+    def signal_speed(self, U, stream=None):
+        """max(|v| + c_s) over this context's cells."""
+        out = C.c_double(0.0)
+        self._check(self._L.qk_signal_speed(self._h, _ptrs(U, 5), C.byref(out), _stream(stream)))
+        return out.value
+
+    def set_timestep(self, smax, stream=None):
+        """(dt, N_sub, dt_rad, smax) from the global signal speed."""
+        out = (C.c_double * 4)()
+        self._check(self._L.qk_set_timestep(self._h, float(smax), out, _stream(stream)))
+        return out[0], int(out[1]), out[2], out[3]

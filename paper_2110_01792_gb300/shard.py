@@ -18,6 +18,16 @@ reductions per step (the minimum timestep and the conservation sums).
   both sides, so a packed buffer needs no headers).
 * ``exchange`` packs, sends / receives with ``torch.distributed`` point-to-point
   operations (gloo for host arrays, NCCL for device arrays) and unpacks.
+
+Device side: ``rank_layout`` places one rank's patches in that rank's own
+field arrays; ``RankStepper`` advances a rank's shard (a library context made
+by qk_init_shard) through one full update, as a generator that stops at the
+two kinds of global synchronisation point (the signal-speed max and every
+ghost exchange).  ``run_local`` drives several ranks in one process (each
+halo buffer copied to the peer's receive buffer); ``run_distributed`` drives
+one rank per process with ``torch.distributed`` (NCCL send / receive of the
+packed device buffers, all-reduce for the max).  No kernel of one rank ever
+waits on another rank: every synchronisation is between launches, on the host.
 """
 from __future__ import annotations
 
@@ -180,3 +190,129 @@ def global_max(value: float) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+# ------------------------------------------------------------ device shards ---
+def rank_layout(layout, owner: np.ndarray, rank: int, pad: int = 64):
+    """The whole patch set, with this rank's patches packed into this rank's
+    field arrays (others get offset 0: the library does not read them)."""
+    from .inputs import Layout
+    off = np.zeros(layout.nbox, dtype=np.int64)
+    pos = 0
+    for b in range(layout.nbox):
+        if owner[b] == rank:
+            off[b] = pos
+            vol = int(np.prod(layout.n[b].astype(np.int64) + 2 * layout.ng))
+            pos += (vol + pad - 1) // pad * pad
+    return Layout(layout.lo.copy(), layout.n.copy(), off, layout.ng, tuple(layout.dom_n), int(pos))
+
+
+class RankStepper:
+    """One rank's part of a sharded update (Sec. 2.2 operator split, Sec. 4
+    distribution by patches).  ``ctx`` is this rank's shard context; U / R its
+    conserved hydro and radiation fields (torch CUDA tensors in the rank's
+    layout).  ``step`` is a generator: it yields ("max", value) and expects the
+    global max back, and yields ("halo", {peer: send buffer}, {peer: receive
+    buffer}) after packing, expecting the receive buffers filled on resume."""
+
+    def __init__(self, ctx, U, R=None):
+        import torch
+        self.ctx, self.U, self.R = ctx, list(U), (list(R) if R is not None else None)
+        dt = U[0].dtype
+        self.U1 = [torch.empty_like(u) for u in U]
+        self.R1 = [torch.empty_like(r) for r in R] if R is not None else None
+        self.peers = [p for p in range(ctx.nranks) if p != ctx.rank]
+        self.cells = {p: ctx.halo_cells(p) for p in self.peers}
+        # one send and one receive buffer per peer, sized for the widest fill (5 fields)
+        nf = 5
+        dev = U[0].device
+        self.sbuf = {p: torch.empty(nf * max(1, s), dtype=dt, device=dev) for p, (s, _) in self.cells.items()}
+        self.rbuf = {p: torch.empty(nf * max(1, r), dtype=dt, device=dev) for p, (_, r) in self.cells.items()}
+
+    def _fill(self, fields):
+        """Full ghost fill of ``fields``: rank-local copies, then the halo."""
+        self.ctx.fill_ghosts(fields)
+        nf = len(fields)
+        sends, recvs = {}, {}
+        for p in self.peers:
+            s, r = self.cells[p]
+            if s:
+                sends[p] = self.sbuf[p][:nf * s]
+                self.ctx.halo_pack(p, fields, sends[p])
+            if r:
+                recvs[p] = self.rbuf[p][:nf * r]
+        yield ("halo", sends, recvs)
+        for p, buf in recvs.items():
+            self.ctx.halo_unpack(p, fields, buf)
+
+    def step(self):
+        ctx, U, R = self.ctx, self.U, self.R
+        smax = yield ("max", ctx.signal_speed(U))
+        dt, nsub, dtr, _ = ctx.set_timestep(smax)
+        yield from self._fill(U)
+        ctx.hydro_stage(1, U, None, self.U1, dt)
+        yield from self._fill(self.U1)
+        ctx.hydro_stage(2, U, self.U1, U, dt)
+        if R is not None and not ctx.params.hydro_only:
+            yield from self._fill(U[:1])
+            for _ in range(nsub):
+                yield from self._fill(R)
+                ctx.rad_stage(1, R, None, self.R1, U[0], dtr)
+                yield from self._fill(self.R1)
+                ctx.rad_stage(2, R, self.R1, R, U[0], dtr)
+                ctx.exchange(U, R, dtr)
+        return dt, nsub
+
+
+def run_local(steppers):
+    """Advance every rank of one process by one step, in lock-step: at each
+    synchronisation point all ranks have issued their launches up to it, the
+    host takes the max or copies each send buffer to the peer's receive
+    buffer (device copies on the current stream), then all ranks resume."""
+    gens = [s.step() for s in steppers]
+    msgs = [next(g) for g in gens]
+    result = [None] * len(gens)
+    while True:
+        kinds = {m[0] if m is not None else None for m in msgs}
+        assert len(kinds) == 1, f"ranks out of step: {kinds}"
+        kind = kinds.pop()
+        if kind is None:
+            return result
+        if kind == "max":
+            reply = [max(m[1] for m in msgs)] * len(gens)
+        else:
+            for r, m in enumerate(msgs):
+                for p, buf in m[2].items():
+                    buf.copy_(msgs[p][1][r])
+            reply = [None] * len(gens)
+        for r, g in enumerate(gens):
+            try:
+                msgs[r] = g.send(reply[r])
+            except StopIteration as e:
+                result[r] = e.value
+                msgs[r] = None
+
+
+def run_distributed(stepper):
+    """Advance this process's rank by one step with torch.distributed: an
+    all-reduce (MAX) for the signal speed and one isend / irecv pair per peer
+    for every ghost exchange (device buffers: NCCL; host buffers: gloo)."""
+    import torch
+    import torch.distributed as dist
+    g = stepper.step()
+    msg = next(g)
+    while True:
+        if msg[0] == "max":
+            t = torch.tensor([msg[1]], dtype=torch.float64, device=stepper.U[0].device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            reply = float(t.item())
+        else:
+            reqs = [dist.isend(buf, p) for p, buf in sorted(msg[1].items())]
+            reqs += [dist.irecv(buf, p) for p, buf in sorted(msg[2].items())]
+            for q in reqs:
+                q.wait()
+            reply = None
+        try:
+            msg = g.send(reply)
+        except StopIteration as e:
+            return e.value

@@ -91,3 +91,45 @@ def test_init_rejects_invalid_patch_sets():
         rc, msg = _init(qk, boxes, dom, ng, prec, **kw)
         assert rc == qk.EINVAL, (word, rc, msg)
         assert word.split()[0] in msg.lower() or word in msg.lower(), (word, msg)
+
+
+def test_init_shard_rejects_invalid_ownership():
+    """qk_init_shard checks the owner array and the rank before touching the
+    GPU: NULL owner, owners outside [0, nranks), a rank outside the range, a
+    rank that owns no patch, and overlapping field ranges among the patches
+    this rank owns are QK_EINVAL with a message (runs on CPU)."""
+    qk = _qk()
+    vol = (8 + 8) * (8 + 8) * (8 + 8)
+    boxes = [((0, 0, 0), (8, 8, 8), 0), ((8, 0, 0), (8, 8, 8), vol)]
+    arr = (qk.Box * 2)()
+    for i, (lo, n, off) in enumerate(boxes):
+        for d in range(3):
+            arr[i].lo[d] = lo[d]
+            arr[i].n[d] = n[d]
+        arr[i].offset = off
+    p = qk.make_params(hydro_only=1, dx=0.1)
+    dn = (ctypes.c_int32 * 3)(16, 8, 8)
+    L = qk.lib()
+
+    def init(owner, nranks, rank, offsets=None):
+        if offsets is not None:
+            for i, o in enumerate(offsets):
+                arr[i].offset = o
+        h = ctypes.c_void_p()
+        own = None if owner is None else (ctypes.c_int32 * 2)(*owner)
+        rc = L.qk_init_shard(ctypes.byref(h), ctypes.byref(p), arr, 2, dn, 4, 0, own, nranks, rank)
+        if rc == 0:
+            L.qk_destroy(h)
+        return rc, L.qk_last_error(None).decode()
+
+    cases = [
+        ((None, 2, 0, None), "owner is null"),
+        (([0, 2], 2, 0, None), "outside"),
+        (([0, 1], 2, 2, None), "rank 2 of 2"),
+        (([0, 0], 2, 1, None), "owns no patch"),
+        (([0, 0], 1, 0, [0, 10]), "field range"),
+    ]
+    for (owner, nranks, rank, offs), word in cases:
+        rc, msg = init(owner, nranks, rank, offs)
+        assert rc == qk.EINVAL, (word, rc, msg)
+        assert word in msg.lower(), (word, msg)

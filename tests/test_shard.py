@@ -102,3 +102,151 @@ def test_two_rank_exchange_gloo():
     for r in range(world):
         ok, gmax, nsend = results[r]
         assert ok and gmax == world + 0.5 and nsend > 0
+
+
+# ------------------------------------- step composer over torch.distributed ---
+class _Params:
+    hydro_only = 0
+
+
+class FakeShardCtx:
+    """Stand-in for one rank's library context with the same methods, in numpy
+    on the host: ghost fills and halos follow ``exchange_plan``; the stages are
+    simple neighbour stencils that read the ghost cells (so a missing or wrong
+    halo changes the result); the timestep is a fixed function of the speed."""
+
+    def __init__(self, lay, owner, rank):
+        self.lay, self.owner, self.rank = lay, owner, rank
+        self.nranks = int(owner.max()) + 1
+        self.plan = S.exchange_plan(lay, owner)[rank]
+        self.own = np.nonzero(owner == rank)[0]
+        self.params = _Params()
+
+    @staticmethod
+    def _np(fields):
+        return [f.numpy() for f in fields]
+
+    def halo_cells(self, p):
+        vol = lambda regs: sum(r[4][0] * r[4][1] * r[4][2] for r in regs)
+        return vol(self.plan["send"].get(p, [])), vol(self.plan["recv"].get(p, []))
+
+    def fill_ghosts(self, fields):
+        S.apply_local(self.lay, self._np(fields), self.plan["local"])
+
+    def halo_pack(self, p, fields, buf):
+        buf.numpy()[...] = S.pack(self.lay, self._np(fields), self.plan["send"][p])
+
+    def halo_unpack(self, p, fields, buf):
+        S.unpack(self.lay, self._np(fields), self.plan["recv"][p], buf.numpy())
+
+    def signal_speed(self, U):
+        return float(max(np.abs(self.lay.interior(U[1].numpy(), b)).max() for b in self.own))
+
+    def set_timestep(self, smax):
+        return 0.01 / smax, 3, 0.004 / smax, smax
+
+    def _lap(self, a, b, rho=None):
+        g = self.lay.ng
+        v = self.lay.full(a, b)
+        n = self.lay.n[b]
+        c = lambda dz, dy, dx: v[g + dz:g + dz + n[2], g + dy:g + dy + n[1], g + dx:g + dx + n[0]]
+        out = c(0, 0, 1) + c(0, 0, -1) + c(0, 1, 0) + c(0, -1, 0) + c(1, 0, 0) + c(-1, 0, 0) - 6 * c(0, 0, 0)
+        if rho is not None:
+            w = self.lay.full(rho, b)
+            out = out + 0.1 * (w[g:g + n[2], g:g + n[1], g + 2:g + 2 + n[0]] - w[g:g + n[2], g:g + n[1], g - 2:g - 2 + n[0]])
+        return out
+
+    def _stage(self, stage, A0, A1, Aout, dt, rho=None):
+        src = A0 if stage == 1 else A1
+        for f in range(len(A0)):
+            a0, s, o = A0[f].numpy(), src[f].numpy(), Aout[f].numpy()
+            for b in self.own:
+                upd = self.lay.interior(s, b) + dt * self._lap(s, b, rho)
+                self.lay.interior(o, b)[...] = upd if stage == 1 else 0.5 * self.lay.interior(a0, b) + 0.5 * upd
+
+    def hydro_stage(self, stage, U0, U1, Uout, dt):
+        self._stage(stage, U0, U1, Uout, dt)
+
+    def rad_stage(self, stage, R0, R1, Rout, rho, dt):
+        self._stage(stage, R0, R1, Rout, dt, rho.numpy())
+
+    def exchange(self, U, R, dt):
+        for b in self.own:
+            e, er = self.lay.interior(U[4].numpy(), b), self.lay.interior(R[0].numpy(), b)
+            d = dt * (er - e)
+            e += d
+            er -= d
+
+
+def _composer_layout():
+    return I.patch_tiling(dom_n=(32, 24, 16), seed=8, ng=3, edges=(8, 16))
+
+
+def _composer_fields(lay, owner, rank):
+    import torch
+    rng = np.random.Generator(np.random.Philox(31))
+    full = [rng.standard_normal(lay.field_len) for _ in range(9)]
+    rlay = S.rank_layout(lay, owner, rank)
+    out = []
+    for f in full:
+        r = np.full(rlay.field_len, np.nan)
+        for b in np.nonzero(owner == rank)[0]:
+            rlay.interior(r, b)[...] = lay.interior(f, b)
+        out.append(torch.from_numpy(r))
+    return rlay, out[:5], out[5:]
+
+
+def _composer_run(lay, owner, rank, steps, driver):
+    rlay, U, R = _composer_fields(lay, owner, rank)
+    st = S.RankStepper(FakeShardCtx(rlay, owner, rank), U, R)
+    hist = [driver(st) for _ in range(steps)]
+    res = {}
+    for b in np.nonzero(owner == rank)[0]:
+        res[int(b)] = np.stack([rlay.interior(f.numpy(), b) for f in st.U + st.R])
+    return res, hist
+
+
+def _composer_worker(rank, world, port, results):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        lay = _composer_layout()
+        owner = S.partition(lay, world)
+        res, hist = _composer_run(lay, owner, rank, 2, S.run_distributed)
+        results[rank] = (res, hist)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_step_composer_over_gloo_matches_one_rank():
+    """The per-rank step generator driven by ``run_distributed`` on 2 gloo ranks
+    (all-reduce for the speed, isend / irecv of packed halos, ghosts NaN
+    until filled) gives bit-for-bit the one-rank result of ``run_local`` with
+    the same stencil stages: every ghost fill of every stage and substep saw
+    the right neighbour data and the global timestep."""
+    import torch.multiprocessing as mp
+    lay = _composer_layout()
+    one = np.zeros(lay.nbox, dtype=np.int32)
+    ref, href = _composer_run(lay, one, 0, 2, lambda st: S.run_local([st])[0])
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    results = mgr.dict()
+    world = 2
+    port = _free_port()
+    procs = [ctx.Process(target=_composer_worker, args=(r, world, port, results)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=180)
+        assert p.exitcode == 0
+    got = {}
+    for r in range(world):
+        res, hist = results[r]
+        assert hist == href
+        got.update(res)
+    assert sorted(got) == sorted(ref)
+    for b in ref:
+        assert np.all(np.isfinite(got[b]))
+        assert np.array_equal(got[b], ref[b])
