@@ -237,10 +237,10 @@ def time_kernel(torch, fn, reps, stream):
 # (profiles/ncu_*_128.md), valid only while the kernel's sources hash to the
 # value recorded at capture time.
 NCU_TRAFFIC = {
-    ("rhd128", "rad_stage_kernel<double,1>"): (134.25e6, "rad", "91c345f6a610"),
-    ("rhd128", "hydro_stage_kernel<double,1>"): (154.40e6, "hydro", "0c0a0be99950"),
-    ("rhd128", "hydro_stage_kernel<float,1>"): (105.51e6, "hydro", "0c0a0be99950"),
-    ("rhd128", "exchange_kernel_mixed"): (95.40e6, "cell", "dd4a3527ab00"),
+    ("rhd128", "rad_stage_kernel<double,1>"): (136.33e6, "rad", "a4001c8e823b"),
+    ("rhd128", "hydro_stage_kernel<double,1>"): (152.35e6, "hydro", "735146949d70"),
+    ("rhd128", "hydro_stage_kernel<float,1>"): (105.66e6, "hydro", "735146949d70"),
+    ("rhd128", "exchange_kernel_mixed"): (95.45e6, "cell", "071a2ba2f58e"),
 }
 
 
