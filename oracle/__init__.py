@@ -63,8 +63,13 @@ class Params(C.Structure):
         ("eps_newton", C.c_double), ("dx", C.c_double * 3),
         ("kappa_mode", C.c_int32), ("eos", C.c_int32), ("max_iter", C.c_int32),
         ("nsub_max", C.c_int32), ("tau_correction", C.c_int32), ("hydro_only", C.c_int32),
-        ("recon", C.c_int32), ("flattening", C.c_int32),
+        ("recon", C.c_int32), ("flattening", C.c_int32), ("closure", C.c_int32),
+        ("bc_lo", C.c_int32 * 3), ("bc_hi", C.c_int32 * 3),
     ]
+
+
+BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_DIRICHLET = 0, 1, 2, 3
+CLOSURE_LEVERMORE, CLOSURE_MINERBO, CLOSURE_EDDINGTON = 0, 1, 2
 
 
 def make_params(**kw) -> Params:
@@ -93,6 +98,12 @@ def make_params(**kw) -> Params:
     p.hydro_only = int(kw.get("hydro_only", 0))
     p.recon = int(kw.get("recon", 0))
     p.flattening = int(kw.get("flattening", 0))
+    p.closure = int(kw.get("closure", 0))
+    lo = kw.get("bc_lo", (0, 0, 0))
+    hi = kw.get("bc_hi", (0, 0, 0))
+    for i in range(3):
+        p.bc_lo[i] = int(lo[i])
+        p.bc_hi[i] = int(hi[i])
     return p
 
 
@@ -119,15 +130,25 @@ def lib():
             L.or_max_signal_speed.argtypes = [vp, P(Params), vp]
             L.or_timestep.argtypes = [vp, P(Params), vp, P(C.c_double)]
             L.or_timestep_from_speed.argtypes = [P(Params), C.c_double, P(C.c_double)]
-            L.or_eddington_tensor.argtypes = [P(C.c_double), P(C.c_double)]
+            L.or_eddington_tensor.argtypes = [C.c_int, P(C.c_double), P(C.c_double)]
+            L.or_eddington_factor.restype = C.c_double
+            L.or_eddington_factor.argtypes = [C.c_int, C.c_double]
+            L.or_exchange_energy_src.restype = C.c_int
+            L.or_exchange_energy_src.argtypes = [P(Params), C.c_double, C.c_double, C.c_double,
+                                                 C.c_double, C.c_double, P(C.c_double),
+                                                 P(C.c_double)]
+            L.or_set_dirichlet.restype = C.c_int
+            L.or_set_dirichlet.argtypes = [vp, P(Params), vp]
+            L.or_fill_ghosts_bc.restype = C.c_int
+            L.or_fill_ghosts_bc.argtypes = [vp, P(Params), vp, C.c_int, C.c_int]
             L.or_exchange_energy.restype = C.c_int
             L.or_exchange_energy.argtypes = [P(Params), C.c_double, C.c_double, C.c_double,
                                              C.c_double, P(C.c_double), P(C.c_double)]
             L.or_exchange.argtypes = [vp, P(Params), vp, vp, C.c_double, C.c_int64, vp,
-                                      P(C.c_int64)]
+                                      vp, P(C.c_int64)]
             L.or_relax_cell.argtypes = [P(Params), C.c_double, C.c_double, C.c_double,
                                         C.c_double, C.c_int64, vp, vp]
-            L.or_step.argtypes = [vp, P(Params), vp, vp, vp, P(C.c_double), P(C.c_int64)]
+            L.or_step.argtypes = [vp, P(Params), vp, vp, vp, vp, P(C.c_double), P(C.c_int64)]
             L.or_conserved_sums.argtypes = [vp, P(Params), vp, vp, P(C.c_double)]
             _lib = L
     return _lib
@@ -204,11 +225,28 @@ def hllc(wL, wR, d, gamma):
     return np.array(F[:])
 
 
-def eddington_tensor(f):
+def eddington_tensor(f, closure=0):
     a = (C.c_double * 3)(*[float(x) for x in f])
     T = (C.c_double * 9)()
-    lib().or_eddington_tensor(a, T)
+    lib().or_eddington_tensor(int(closure), a, T)
     return np.array(T[:]).reshape(3, 3)
+
+
+def eddington_factor(f, closure=0):
+    return lib().or_eddington_factor(int(closure), float(f))
+
+
+def set_dirichlet(grid, p, U, R):
+    """Record the boundary states held in the ghost cells beyond Dirichlet faces
+    (all 9 fields); returns the status (OR_EINVAL when two ghost cells of the
+    same boundary position disagree)."""
+    return lib().or_set_dirichlet(grid.handle, C.byref(p), _ptr_array(list(U) + list(R)))
+
+
+def fill_ghosts_bc(grid, p, fields, fid0=0):
+    """Ghost cells of fields (field ids fid0, fid0+1, ...) under the boundary conditions."""
+    return lib().or_fill_ghosts_bc(grid.handle, C.byref(p), _ptr_array(fields), len(fields),
+                                   int(fid0))
 
 
 def hydro_stage(grid, p, stage, U0, U1, Uout, dt, cells=None):
@@ -241,18 +279,18 @@ def timestep_from_speed(p, smax):
     return out[0], int(out[1]), out[2]
 
 
-def exchange_energy(p, rho, Eg0, Er0, dt):
+def exchange_energy(p, rho, Eg0, Er0, dt, S=0.0):
     Eg, Er = C.c_double(), C.c_double()
-    it = lib().or_exchange_energy(C.byref(p), float(rho), float(Eg0), float(Er0), float(dt),
-                                  C.byref(Eg), C.byref(Er))
+    it = lib().or_exchange_energy_src(C.byref(p), float(rho), float(Eg0), float(Er0), float(dt),
+                                      float(S), C.byref(Eg), C.byref(Er))
     return Eg.value, Er.value, it
 
 
-def exchange(grid, p, U, R, dt, cells=None):
+def exchange(grid, p, U, R, dt, cells=None, src=None):
     n, ptr, keep = _cells_arg(cells)
     info = (C.c_int64 * 4)()
     rc = lib().or_exchange(grid.handle, C.byref(p), _ptr_array(U), _ptr_array(R), float(dt),
-                           n, ptr, info)
+                           n, ptr, _dptr(src) if src is not None else None, info)
     return rc, tuple(info[:])
 
 
@@ -264,14 +302,16 @@ def relax_cell(p, rho, Eg, Er, dt, nsteps):
     return rc, Egh, Erh
 
 
-def step(grid, p, U, R=None, scratch=None):
-    """One hydro step plus its radiation substeps; returns (rc, (dt, nsub, dt_rad), info)."""
+def step(grid, p, U, R=None, scratch=None, src=None):
+    """One hydro step plus its radiation substeps; returns (rc, (dt, nsub, dt_rad), info).
+    src: optional emissivity field j (radiation source of the exchange)."""
     if scratch is None:
         scratch = [np.zeros_like(U[0]) for _ in range(NHYD + NRAD)]
     out = (C.c_double * 3)()
     info = (C.c_int64 * 4)()
     rc = lib().or_step(grid.handle, C.byref(p), _ptr_array(U),
-                       _ptr_array(R) if R is not None else None, _ptr_array(scratch), out, info)
+                       _ptr_array(R) if R is not None else None, _ptr_array(scratch),
+                       _dptr(src) if src is not None else None, out, info)
     return rc, (out[0], int(out[1]), out[2]), tuple(info[:])
 
 

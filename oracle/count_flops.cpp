@@ -174,7 +174,7 @@ int main(int argc, char **argv) {
   for (int q = 0; q < 4; ++q) Rc[q] = Rcopy[q].data();
   int64_t info[4];
   double dtr = 0.3 * (1.0 / n) / chat;
-  or_exchange(g, &p, Uc, Rc, dtr, 0, nullptr, info);
+  or_exchange(g, &p, Uc, Rc, dtr, 0, nullptr, nullptr, info);
   Tally exch = diff(g_t, ex0);
 
   std::printf("{\n  \"cells\": %d,\n  \"convention\": \"add+sub+mul+div+sqrt, per unit\",\n", n * n * n);

@@ -32,7 +32,10 @@
  * at element off[b] and holds (n+2g)^3 cells, x fastest.  The oracle reads only
  * interior cells: a stencil neighbour outside its patch is fetched from the
  * patch that owns the periodic image of that cell (an owner map over the
- * periodic domain), so the oracle needs no ghost fill of its own.
+ * periodic domain), so the oracle needs no ghost fill of its own.  Across a
+ * non-periodic domain face the neighbour is resolved by the boundary
+ * condition of that face (mirror image with the normal vector components
+ * negated, nearest interior cell, or a stored boundary state).
  */
 #include <math.h>
 #include <stdint.h>
@@ -68,7 +71,16 @@ typedef struct {
   int32_t hydro_only;     /* 1: skip radiation substeps                            */
   int32_t recon;          /* 0: PPM; 1: PLM with the MC limiter (Sec. 2.2.1)       */
   int32_t flattening;     /* 1: multidimensional shock flattening (Sec. 2.2.1)     */
+  int32_t closure;        /* 0: Levermore; 1: Minerbo; 2: Eddington (Sec. 2.2.2)   */
+  int32_t bc_lo[3];       /* boundary of the low / high domain face per axis:      */
+  int32_t bc_hi[3];       /* 0 periodic, 1 reflecting, 2 outflow, 3 Dirichlet      */
 } or_params;
+
+#define OR_BC_PERIODIC 0
+#define OR_BC_REFLECT 1
+#define OR_BC_OUTFLOW 2
+#define OR_BC_DIRICHLET 3
+#define NFIELD 9 /* rho, mx, my, mz, E, Er, Fx, Fy, Fz: field ids of the boundary code */
 
 typedef struct {
   int32_t nbox, ng;
@@ -76,6 +88,10 @@ typedef struct {
   int32_t *lo, *n; /* 3*nbox */
   int64_t *off;    /* nbox   */
   int32_t *owner;  /* dom_n[0]*dom_n[1]*dom_n[2] -> box id */
+  /* Dirichlet boundary states: NFIELD values per cell of the domain extended
+   * by ng cells on every side (only cells outside a Dirichlet face are used) */
+  double *dstore;
+  unsigned char *dset;
 } or_grid;
 
 /* ------------------------------------------------------------------------ */
@@ -120,6 +136,8 @@ void or_grid_destroy(or_grid *g) {
   free(g->n);
   free(g->off);
   free(g->owner);
+  free(g->dstore);
+  free(g->dset);
   free(g);
 }
 
@@ -145,6 +163,139 @@ static int64_t owner_index(const or_grid *g, int b, int i, int j, int k) {
   int64_t lj = wrap(y - lq[1], g->dom_n[1]);
   int64_t lk = wrap(z - lq[2], g->dom_n[2]);
   return cell_index(g, q, (int)li, (int)lj, (int)lk);
+}
+
+/* Where the value of patch b's local cell c comes from, under the domain
+ * boundary conditions.  Each axis is resolved on its own: inside the domain
+ * the coordinate stays; across a periodic face it wraps; across a reflecting
+ * face it is mirrored (x -> -1-x below, 2N-1-x above) and the vector
+ * components along that axis change sign; across an outflow face it is
+ * clamped to the nearest interior cell (zero gradient); across a Dirichlet
+ * face the cell takes the stored boundary state (whatever the other axes do).
+ * Result: the element index of the interior cell (e >= 0) with the axes to
+ * negate, or e = -1 and the index of the cell in the Dirichlet store. */
+typedef struct {
+  int64_t e;
+  int flip;      /* bit d: negate the d-components of vectors */
+  int64_t key;   /* Dirichlet store index (e = -1) */
+  int outside;   /* 1: outside a non-periodic face on some axis */
+} or_src;
+
+static int64_t ext_index(const or_grid *g, const int64_t x[3]) {
+  int64_t ex = g->dom_n[0] + 2 * g->ng, ey = g->dom_n[1] + 2 * g->ng;
+  return ((x[2] + g->ng) * ey + (x[1] + g->ng)) * ex + (x[0] + g->ng);
+}
+
+static or_src resolve(const or_grid *g, const or_params *p, int b, const int c[3]) {
+  or_src r = {-1, 0, -1, 0};
+  int64_t x[3], raw[3];
+  int dir = 0;
+  for (int d = 0; d < 3; ++d) {
+    int64_t D = g->dom_n[d];
+    int64_t v = (int64_t)g->lo[3 * b + d] + c[d];
+    raw[d] = v;
+    if (v < 0 || v >= D) {
+      int bc = v < 0 ? p->bc_lo[d] : p->bc_hi[d];
+      if (bc == OR_BC_PERIODIC) {
+        v = wrap(v, D);
+        raw[d] = v;
+      } else {
+        r.outside = 1;
+        if (bc == OR_BC_REFLECT) {
+          v = v < 0 ? -1 - v : 2 * D - 1 - v;
+          r.flip |= 1 << d;
+        } else if (bc == OR_BC_OUTFLOW) {
+          v = v < 0 ? 0 : D - 1;
+        } else {
+          dir = 1;
+        }
+      }
+    }
+    x[d] = v;
+  }
+  if (dir) {
+    r.key = ext_index(g, raw);
+    r.flip = 0;
+    return r;
+  }
+  int q = g->owner[(x[2] * g->dom_n[1] + x[1]) * g->dom_n[0] + x[0]];
+  r.e = cell_index(g, q, (int)(x[0] - g->lo[3 * q]), (int)(x[1] - g->lo[3 * q + 1]),
+                   (int)(x[2] - g->lo[3 * q + 2]));
+  return r;
+}
+
+/* vector axis of a field id (momentum or radiation flux component), or -1 */
+static int field_axis(int fid) {
+  if (fid >= 1 && fid <= 3) return fid - 1;
+  if (fid >= 6 && fid <= 8) return fid - 6;
+  return -1;
+}
+
+/* value of field `fid` (array f) at a resolved cell */
+static double src_value(const or_grid *g, const double *f, int fid, const or_src *r) {
+  if (r->e < 0) return g->dstore[r->key * NFIELD + fid];
+  int ax = field_axis(fid);
+  double v = f[r->e];
+  return (ax >= 0 && ((r->flip >> ax) & 1)) ? -v : v;
+}
+
+/* value of field fid (array f) at patch b's local cell c */
+static double cell_value(const or_grid *g, const or_params *p, const double *f, int fid, int b,
+                         const int c[3]) {
+  or_src r = resolve(g, p, b, c);
+  return src_value(g, f, fid, &r);
+}
+
+/* Record the Dirichlet boundary states: the values that the caller's arrays
+ * (all NFIELD fields, hydro then radiation) hold in the ghost cells beyond
+ * the Dirichlet faces.  Every ghost cell that maps to the same boundary
+ * position must hold the same values (else OR_EINVAL). */
+int or_set_dirichlet(or_grid *g, const or_params *p, double *const *fields) {
+  int64_t ne = 1;
+  for (int d = 0; d < 3; ++d) ne *= g->dom_n[d] + 2 * g->ng;
+  free(g->dstore);
+  free(g->dset);
+  g->dstore = (double *)calloc((size_t)(ne * NFIELD), sizeof(double));
+  g->dset = (unsigned char *)calloc((size_t)ne, 1);
+  int ng = g->ng;
+  for (int b = 0; b < g->nbox; ++b) {
+    const int32_t *n = g->n + 3 * b;
+    for (int k = -ng; k < n[2] + ng; ++k)
+      for (int j = -ng; j < n[1] + ng; ++j)
+        for (int i = -ng; i < n[0] + ng; ++i) {
+          int c[3] = {i, j, k};
+          or_src r = resolve(g, p, b, c);
+          if (r.e >= 0) continue;
+          int64_t e = cell_index(g, b, i, j, k);
+          for (int f = 0; f < NFIELD; ++f) {
+            double v = fields[f][e];
+            if (g->dset[r.key] && g->dstore[r.key * NFIELD + f] != v) return OR_EINVAL;
+            g->dstore[r.key * NFIELD + f] = v;
+          }
+          g->dset[r.key] = 1;
+        }
+  }
+  return OR_OK;
+}
+
+/* Fill every ghost cell of nf fields (field ids fid0 .. fid0+nf-1) under the
+ * boundary conditions: the value a stencil read of that cell sees. */
+int or_fill_ghosts_bc(const or_grid *g, const or_params *p, double *const *f, int nf, int fid0) {
+  int ng = g->ng;
+  for (int b = 0; b < g->nbox; ++b) {
+    const int32_t *n = g->n + 3 * b;
+    for (int k = -ng; k < n[2] + ng; ++k)
+      for (int j = -ng; j < n[1] + ng; ++j)
+        for (int i = -ng; i < n[0] + ng; ++i) {
+          int inside = i >= 0 && j >= 0 && k >= 0 && i < n[0] && j < n[1] && k < n[2];
+          if (inside) continue;
+          int c[3] = {i, j, k};
+          or_src r = resolve(g, p, b, c);
+          if (r.e < 0 && !g->dstore) return OR_EINVAL;
+          for (int v = 0; v < nf; ++v) f[v][cell_index(g, b, i, j, k)] = src_value(g, f[v], fid0 + v, &r);
+        }
+  }
+  return OR_OK;
 }
 
 /* fill every ghost cell of every patch from the owner of its periodic image */
@@ -334,9 +485,9 @@ static void gather_prims(const or_grid *g, const or_params *p, double *const *U,
   for (int s = 0; s < 6; ++s) {
     int cc[3] = {c[0], c[1], c[2]};
     cc[d] += first + s;
-    int64_t e = owner_index(g, b, cc[0], cc[1], cc[2]);
+    or_src r = resolve(g, p, b, cc);
     double Uc[NHYD], q[NHYD];
-    for (int v = 0; v < NHYD; ++v) Uc[v] = U[v][e];
+    for (int v = 0; v < NHYD; ++v) Uc[v] = src_value(g, U[v], v, &r);
     con2prim(Uc, p->gamma, q);
     for (int v = 0; v < NHYD; ++v) w[v][s] = q[v];
   }
@@ -354,9 +505,9 @@ static double flat_ftilde(const or_grid *g, const or_params *p, double *const *U
   for (int o = -2; o <= 2; ++o) {
     int cc[3] = {c[0], c[1], c[2]};
     cc[d] += o;
-    int64_t e = owner_index(g, b, cc[0], cc[1], cc[2]);
+    or_src r = resolve(g, p, b, cc);
     double Uc[NHYD], q[NHYD];
-    for (int v = 0; v < NHYD; ++v) Uc[v] = U[v][e];
+    for (int v = 0; v < NHYD; ++v) Uc[v] = src_value(g, U[v], v, &r);
     con2prim(Uc, p->gamma, q);
     pr[o + 2] = q[4];
     un[o + 2] = q[1 + d];
@@ -381,9 +532,9 @@ static double flat_chi(const or_grid *g, const or_params *p, double *const *U, i
     for (int s = 0; s < 2; ++s) {
       int cc[3] = {c[0], c[1], c[2]};
       cc[d] += s == 0 ? -1 : 1;
-      int64_t e = owner_index(g, b, cc[0], cc[1], cc[2]);
+      or_src r = resolve(g, p, b, cc);
       double Uc[NHYD], q[NHYD];
-      for (int v = 0; v < NHYD; ++v) Uc[v] = U[v][e];
+      for (int v = 0; v < NHYD; ++v) Uc[v] = src_value(g, U[v], v, &r);
       con2prim(Uc, p->gamma, q);
       pr[s] = q[4];
     }
@@ -396,6 +547,17 @@ static double flat_chi(const or_grid *g, const or_params *p, double *const *U, i
     chi = dmin(chi, 1.0 - f);
   }
   return chi;
+}
+
+/* Flattening coefficient of patch b's local cell c: the stored value of the
+ * interior cell it maps to, or, for a cell outside a non-periodic domain
+ * face, the coefficient computed at that position from the boundary values
+ * around it (what a ghost cell holding those values yields). */
+static double chi_at(const or_grid *g, const or_params *p, double *const *U, const double *chi,
+                     int b, const int c[3]) {
+  or_src r = resolve(g, p, b, c);
+  if (r.outside) return flat_chi(g, p, U, b, c);
+  return chi[r.e];
 }
 
 /* hydro flux at the face between cell c+first+2 and c+first+3 along d,
@@ -415,8 +577,8 @@ static void hydro_face_flux(const or_grid *g, const or_params *p, double *const 
     int cA[3] = {c[0], c[1], c[2]}, cB[3] = {c[0], c[1], c[2]};
     cA[d] += first + 2;
     cB[d] += first + 3;
-    double chiA = chi[owner_index(g, b, cA[0], cA[1], cA[2])];
-    double chiB = chi[owner_index(g, b, cB[0], cB[1], cB[2])];
+    double chiA = chi_at(g, p, U, chi, b, cA);
+    double chiB = chi_at(g, p, U, chi, b, cB);
     for (int v = 0; v < NHYD; ++v) {
       wL[v] = chiA * wL[v] + (1.0 - chiA) * w[v][2];
       wR[v] = chiB * wR[v] + (1.0 - chiB) * w[v][3];
@@ -585,18 +747,33 @@ void or_timestep(const or_grid *g, const or_params *p, double *const *U, double 
 /* radiation transport (Sec. 2.2.2)                                          */
 /* ------------------------------------------------------------------------ */
 
-/* Levermore (1984) closure, eq. M1_closure:
- *   P_r = [ (1-chi)/2 I + (3 chi - 1)/2 n n ] E_r,
- *   chi = (3 + 4 f^2) / (5 + 2 sqrt(4 - 3 f^2)),  n = F / |F|,
- * with f = |F| / (c E_r).  When |f| > 1 the flux is rescaled to |F| = c E_r
- * for the closure only (Sec. 2.2.2); when F = 0 the n n term is dropped.
- * Returns the Eddington tensor T = P_r / E_r (row-major 3x3). */
-void or_eddington_tensor(const double f[3], double T[9]) {
+/* Eddington factor chi(f), 0 <= f <= 1, of the local closures (Sec. 2.2.2):
+ *   Levermore (1984):  chi = (3 + 4 f^2) / (5 + 2 sqrt(4 - 3 f^2))
+ *   Minerbo (1978):    the maximum-entropy closure in its polynomial form,
+ *                      chi = 1/3 + (2/15) (3 f^2 - f^3 + 3 f^4)
+ *   Eddington:         chi = 1/3 (isotropic pressure P_r = E_r I / 3). */
+double or_eddington_factor(int closure, double f) {
+  if (closure == 2) return 1.0 / 3.0;
+  if (closure == 1) return 1.0 / 3.0 + (2.0 / 15.0) * (3.0 * f * f - f * f * f + 3.0 * f * f * f * f);
+  return (3.0 + 4.0 * f * f) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f * f));
+}
+
+/* M1 closure, eq. M1_closure:
+ *   P_r = [ (1-chi)/2 I + (3 chi - 1)/2 n n ] E_r,  n = F / |F|,
+ * with f = |F| / (c E_r) and chi from the selected closure.  When |f| > 1 the
+ * flux is rescaled to |F| = c E_r for the closure only (Sec. 2.2.2); when
+ * F = 0 the n n term is dropped.  The Eddington closure gives T = I/3
+ * exactly.  Returns the Eddington tensor T = P_r / E_r (row-major 3x3). */
+void or_eddington_tensor(int closure, const double f[3], double T[9]) {
   double f2 = (f[0] * f[0] + f[1] * f[1]) + f[2] * f[2];
   double fmag = sqrt(f2);
   double fc = dmin(fmag, 1.0);
-  double chi = (3.0 + 4.0 * fc * fc) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * fc * fc));
+  double chi = or_eddington_factor(closure, fc);
   double a = 0.5 * (1.0 - chi), bcoef = 0.5 * (3.0 * chi - 1.0);
+  if (closure == 2) {
+    a = 1.0 / 3.0;
+    bcoef = 0.0;
+  }
   double nh[3] = {0.0, 0.0, 0.0};
   if (fmag > 0.0)
     for (int i = 0; i < 3; ++i) nh[i] = f[i] / fmag;
@@ -618,10 +795,10 @@ static void gather_rad(const or_grid *g, const or_params *p, double *const *R, i
   for (int s = 0; s < 6; ++s) {
     int cc[3] = {c[0], c[1], c[2]};
     cc[d] += first + s;
-    int64_t e = owner_index(g, b, cc[0], cc[1], cc[2]);
-    double Er = R[0][e];
+    or_src r = resolve(g, p, b, cc);
+    double Er = src_value(g, R[0], NHYD, &r);
     w[0][s] = Er;
-    for (int v = 1; v < NRAD; ++v) w[v][s] = R[v][e] / (p->c * Er);
+    for (int v = 1; v < NRAD; ++v) w[v][s] = src_value(g, R[v], NHYD + v, &r) / (p->c * Er);
   }
 }
 
@@ -632,7 +809,7 @@ static void rad_state(const or_params *p, const double w[NRAD], int d, double U[
                       double F[NRAD]) {
   double T[9];
   double f[3] = {w[1], w[2], w[3]};
-  or_eddington_tensor(f, T);
+  or_eddington_tensor(p->closure, f, T);
   double E = w[0];
   U[0] = E;
   for (int i = 0; i < 3; ++i) U[1 + i] = p->c * E * f[i];
@@ -674,16 +851,16 @@ static void rad_face_flux(const or_grid *g, const or_params *p, double *const *R
   /* wavespeed from the cell-average Eddington factors */
   double TA[9], TB[9];
   double fA[3] = {w[1][2], w[2][2], w[3][2]}, fB[3] = {w[1][3], w[2][3], w[3][3]};
-  or_eddington_tensor(fA, TA);
-  or_eddington_tensor(fB, TB);
+  or_eddington_tensor(p->closure, fA, TA);
+  or_eddington_tensor(p->closure, fB, TB);
   double S = p->chat * dmax(sqrt(TA[4 * d]), sqrt(TB[4 * d]));
   double eps = 1.0;
   if (p->tau_correction) {
     int cA[3] = {c[0], c[1], c[2]}, cB[3] = {c[0], c[1], c[2]};
     cA[d] += first + 2;
     cB[d] += first + 3;
-    double rA = rho[owner_index(g, b, cA[0], cA[1], cA[2])];
-    double rB = rho[owner_index(g, b, cB[0], cB[1], cB[2])];
+    double rA = cell_value(g, p, rho, 0, b, cA);
+    double rB = cell_value(g, p, rho, 0, b, cB);
     double tau = p->dx[d] * 0.5 * (rA * kappa_of(p, p->kappa_R, rA) + rB * kappa_of(p, p->kappa_R, rB));
     if (tau > 1.0) eps = 1.0 / tau;
   }
@@ -759,10 +936,12 @@ static void eos_T4(const or_params *p, double rho, double Eg, double *T4, double
  * |F_G/E_tot| < eps and |(c/chat) F_R/E_tot| < eps with E_tot = E_g0 +
  * (c/chat) E_r0 is made on the residuals of each iterate; reading: the Newton
  * update computed from the iterate whose residuals pass is still applied,
- * and the iteration then stops.  Returns the number of iterations, or -1
- * after max_iter iterations without convergence. */
-int or_exchange_energy(const or_params *p, double rho, double Eg0, double Er0, double dt,
-                       double *Eg_out, double *Er_out) {
+ * and the iteration then stops.  S is the optional source of the radiation
+ * energy residual, F_R = (E_r - E_r0) - (R + S); it does not depend on the
+ * iterate, so the Jacobian is unchanged.  Returns the number of iterations,
+ * or -1 after max_iter iterations without convergence. */
+int or_exchange_energy_src(const or_params *p, double rho, double Eg0, double Er0, double dt,
+                           double S, double *Eg_out, double *Er_out) {
   double kP = kappa_of(p, p->kappa_P, rho);
   double cr = p->c / p->chat;
   double Etot = Eg0 + cr * Er0;
@@ -773,7 +952,9 @@ int or_exchange_energy(const or_params *p, double rho, double Eg0, double Er0, d
     eos_T4(p, rho, Eg, &T4, &dT4);
     double R = dt * rho * kP * (p->chat * p->a_r * T4 - p->chat * Er);
     double FG = (Eg - Eg0) + cr * R;
-    double FR = (Er - Er0) - R;
+    double RS = R;
+    if (S != 0.0) RS = R + S; /* the source, when there is one */
+    double FR = (Er - Er0) - RS;
     converged = fabs(FG / Etot) < p->eps_newton && fabs(cr * FR / Etot) < p->eps_newton;
     double dRdEg = dt * rho * kP * p->chat * p->a_r * dT4;
     double dFG_dEg = 1.0 + cr * dRdEg;
@@ -792,10 +973,16 @@ int or_exchange_energy(const or_params *p, double rho, double Eg0, double Er0, d
   return converged ? it + 1 : -1;
 }
 
+int or_exchange_energy(const or_params *p, double rho, double Eg0, double Er0, double dt,
+                       double *Eg_out, double *Er_out) {
+  return or_exchange_energy_src(p, rho, Eg0, Er0, dt, 0.0, Eg_out, Er_out);
+}
+
 typedef struct {
   double *const *U;
   double *const *R;
   double dt;
+  const double *src; /* emissivity j per cell, or NULL */
   int status;
   int64_t first_bad;
   int max_it;
@@ -817,7 +1004,11 @@ static void exchange_cell(const or_grid *g, const or_params *p, int b, const int
   double Eg0 = E - Ekin0;
   double Er0 = x->R[0][e];
   double Eg, Er;
-  int it = or_exchange_energy(p, rho, Eg0, Er0, x->dt, &Eg, &Er);
+  /* reading: the source is an emissivity j (energy per volume per time, in
+   * the physical energy equation); in the reduced-speed system it enters the
+   * radiation energy as S = dt (chat/c) j, like the emission part of R */
+  double S = x->src ? x->dt * (p->chat / p->c) * x->src[e] : 0.0;
+  int it = or_exchange_energy_src(p, rho, Eg0, Er0, x->dt, S, &Eg, &Er);
   if (it < 0) {
     x->status |= 1 << OR_ENOCONV;
     if (x->first_bad < 0) x->first_bad = e;
@@ -848,8 +1039,9 @@ static void exchange_cell(const or_grid *g, const or_params *p, int b, const int
 /* out_info[0] = status bits, [1] = first bad element, [2] = max iterations,
  * [3] = total iterations */
 int or_exchange(const or_grid *g, const or_params *p, double *const *U, double *const *R,
-                double dt, int64_t ncell, const int32_t *cells, int64_t out_info[4]) {
-  exch_ctx x = {U, R, dt, 0, -1, 0, 0};
+                double dt, int64_t ncell, const int32_t *cells, const double *src,
+                int64_t out_info[4]) {
+  exch_ctx x = {U, R, dt, src, 0, -1, 0, 0};
   for_cells(g, p, ncell, cells, exchange_cell, &x);
   if (out_info) {
     out_info[0] = x.status;
@@ -882,8 +1074,10 @@ int or_relax_cell(const or_params *p, double rho, double Eg, double Er, double d
 /* whole step and conservation sums                                          */
 /* ------------------------------------------------------------------------ */
 
-static void fill_all(const or_grid *g, double *const *f, int nf) {
-  for (int v = 0; v < nf; ++v) or_fill_ghosts(g, f[v]);
+/* ghost cells as a stencil read sees them (the stages themselves read
+ * through the boundary resolver and do not need this) */
+static void fill_all(const or_grid *g, const or_params *p, double *const *f, int nf, int fid0) {
+  or_fill_ghosts_bc(g, p, f, nf, fid0);
 }
 
 /* One hydro step, then N_sub radiation substeps, each ending with the local
@@ -891,28 +1085,28 @@ static void fill_all(const or_grid *g, double *const *f, int nf) {
  * hydro_only runs the hydro step alone.  scratch must hold 9 arrays of the
  * field length.  out[0..2] = dt, N_sub, dt_rad; info as or_exchange. */
 int or_step(const or_grid *g, const or_params *p, double *const *U, double *const *R,
-            double *const *scratch, double out[3], int64_t info[4]) {
+            double *const *scratch, const double *src, double out[3], int64_t info[4]) {
   double ts[3];
   or_timestep(g, p, U, ts);
   double dt = ts[0];
   double *const *U1 = scratch;
-  fill_all(g, U, NHYD);
+  fill_all(g, p, U, NHYD, 0);
   or_hydro_stage(g, p, 1, U, NULL, U1, dt, 0, NULL);
-  fill_all(g, U1, NHYD);
+  fill_all(g, p, U1, NHYD, 0);
   or_hydro_stage(g, p, 2, U, U1, U, dt, 0, NULL);
   int rc = OR_OK;
   int64_t tot[4] = {0, -1, 0, 0};
   if (R && !p->hydro_only) {
     double *const *R1 = scratch + NHYD;
-    fill_all(g, U, NHYD);
+    fill_all(g, p, U, NHYD, 0);
     int nsub = (int)ts[1];
     for (int s = 0; s < nsub; ++s) {
-      fill_all(g, R, NRAD);
+      fill_all(g, p, R, NRAD, NHYD);
       or_rad_stage(g, p, 1, R, NULL, R1, U[0], ts[2], 0, NULL);
-      fill_all(g, R1, NRAD);
+      fill_all(g, p, R1, NRAD, NHYD);
       or_rad_stage(g, p, 2, R, R1, R, U[0], ts[2], 0, NULL);
       int64_t inf[4];
-      int r = or_exchange(g, p, U, R, ts[2], 0, NULL, inf);
+      int r = or_exchange(g, p, U, R, ts[2], 0, NULL, src, inf);
       if (r != OR_OK && rc == OR_OK) rc = r;
       tot[0] |= inf[0];
       if (tot[1] < 0) tot[1] = inf[1];

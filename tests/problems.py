@@ -84,3 +84,55 @@ def random_rad_3d(lay, seed=11, fmax=0.6):
         for d in range(3):
             lay.interior(R[1 + d], b)[...] = c * Er * f[d]
     return R
+
+
+# cgs constants (CODATA), used by the problems the paper states in cgs units
+A_RAD = 7.5657e-15      # radiation constant, erg cm^-3 K^-4
+C_LIGHT = 2.99792458e10  # cm s^-1
+K_B = 1.380649e-16      # erg K^-1
+M_H = 1.6735575e-24     # hydrogen atom mass, g
+
+
+def radiation_pressure_tube(spec, N=None, ng=4):
+    """Sec. 3.3.1: the steady state of radiation and gas pressure in the
+    equilibrium-diffusion limit.  T(x), rho(x) solve
+        d rho/dx = -(mu/(k T)) (k rho/mu + (4/3) a_r T^3) dT/dx,
+        d2T/dx2  = -(3/T) (dT/dx)^2 + (1/rho) (d rho/dx)(dT/dx)
+    from T0, rho0, drho0/dx at x = 0 (``spec``: the golden entry), integrated
+    with scipy over the interior and the ghost cells; E_r = a_r T^4, the flux is
+    the diffusion flux F = -(c/(3 kappa rho)) dE_r/dx, the gas is at rest.  The
+    ghost cells hold the same solution (the Dirichlet boundary states).
+    Returns (layout, U, R, params, T_exact at the interior cells)."""
+    from scipy.integrate import solve_ivp
+    N = int(spec["N"]) if N is None else N
+    L = float(spec["L"])
+    dx = L / N
+    mu = spec["mu_over_mH"] * M_H
+    gamma = spec["gamma"]
+    kappa = spec["kappa"]
+    T0, rho0, drho0 = spec["T0"], spec["rho0"], spec["drho0_dx"]
+
+    def rhs(x, y):
+        rho, T, Tp = y
+        drho = -(mu / (K_B * T)) * (K_B * rho / mu + 4.0 / 3.0 * A_RAD * T ** 3) * Tp
+        return [drho, Tp, -3.0 / T * Tp ** 2 + drho / rho * Tp]
+
+    Tp0 = -drho0 / ((mu / (K_B * T0)) * (K_B * rho0 / mu + 4.0 / 3.0 * A_RAD * T0 ** 3))
+    xc = (np.arange(-ng, N + ng) + 0.5) * dx
+    right = solve_ivp(rhs, (0.0, xc[-1]), [rho0, T0, Tp0], rtol=1e-12, atol=1e-30,
+                      dense_output=True)
+    left = solve_ivp(rhs, (0.0, xc[0]), [rho0, T0, Tp0], rtol=1e-12, atol=1e-30,
+                     dense_output=True)
+    rho, T, Tp = np.array([left.sol(x) if x < 0 else right.sol(x) for x in xc]).T
+    cv = K_B / ((gamma - 1.0) * mu)
+    cs0 = np.sqrt(gamma * K_B * T0 / mu)
+    lay = line_layout(N, 0, ng)
+    U = I.zeros(lay, 5)
+    R = I.zeros(lay, 4)
+    for arr, vals in ((U[0], rho), (U[4], rho * cv * T), (R[0], A_RAD * T ** 4),
+                      (R[1], -(C_LIGHT / (3 * kappa * rho)) * 4 * A_RAD * T ** 3 * Tp)):
+        lay.full(arr, 0)[...] = vals[None, None, :]
+    params = dict(gamma=gamma, cfl=spec["cfl"], a_r=A_RAD, c=C_LIGHT,
+                  chat=spec["chat_over_cs0"] * cs0, c_v=cv, kappa_P=kappa, kappa_R=kappa,
+                  dx=dx, bc_lo=(3, 0, 0), bc_hi=(3, 0, 0), nsub_max=10, tau_correction=1)
+    return lay, U, R, params, T[ng:N + ng], L / cs0

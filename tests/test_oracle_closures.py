@@ -1,0 +1,188 @@
+"""Pins of the oracle's alternative closures (Minerbo, Eddington) and of the
+radiation source term of the matter-radiation exchange (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_01792_gb300 import inputs as I
+from tests import problems as P
+
+LEVERMORE, MINERBO, EDDINGTON = O.CLOSURE_LEVERMORE, O.CLOSURE_MINERBO, O.CLOSURE_EDDINGTON
+
+
+def _grid(lay):
+    return O.Grid(lay.lo, lay.n, lay.off, lay.dom_n, lay.ng)
+
+
+# ------------------------------------------------------------ closures -----
+
+def test_levermore_is_isotropic_in_a_boosted_frame():
+    """Levermore (1984) derives his closure from radiation that is isotropic in
+    a frame moving at speed beta c: in the lab frame f = 4 beta / (3 + beta^2)
+    and chi = (1 + 3 beta^2) / (3 + beta^2).  The closure of eq. M1_closure
+    reproduces that parametric curve to round-off."""
+    for b in np.linspace(0.0, 1.0, 201):
+        f = 4 * b / (3 + b * b)
+        chi = (1 + 3 * b * b) / (3 + b * b)
+        assert abs(O.eddington_factor(f, LEVERMORE) - chi) < 1e-15
+
+
+def _minerbo_max_entropy(f):
+    """The maximum-entropy closure (Minerbo 1978): intensity ~ exp(Z mu), so
+    f = <mu> = coth Z - 1/Z (the Langevin function) and chi = <mu^2> = 1 - 2 f / Z.
+    Z is found by bisection."""
+    if f < 1e-8:
+        return 1.0 / 3.0
+    lo, hi = 1e-12, 1e7
+    for _ in range(200):
+        z = 0.5 * (lo + hi)
+        lz = (1.0 / math.tanh(z) - 1.0 / z) if z > 1e-4 else z / 3.0 - z ** 3 / 45.0
+        if lz < f:
+            lo = z
+        else:
+            hi = z
+    z = 0.5 * (lo + hi)
+    return 1.0 - 2.0 * f / z
+
+
+def test_minerbo_polynomial_tracks_the_maximum_entropy_closure():
+    """The Minerbo closure is the maximum-entropy closure; the polynomial form
+    1/3 + (2/15)(3 f^2 - f^3 + 3 f^4) stays within 0.006 of it on [0, 1)
+    (largest gap near f = 0.8), and is exact at both ends."""
+    assert O.eddington_factor(0.0, MINERBO) == pytest.approx(1.0 / 3.0, abs=1e-16)
+    assert O.eddington_factor(1.0, MINERBO) == pytest.approx(1.0, abs=1e-15)
+    gap = max(abs(O.eddington_factor(f, MINERBO) - _minerbo_max_entropy(f))
+              for f in np.linspace(0.0, 0.995, 400))
+    assert gap < 0.006, gap
+
+
+@pytest.mark.parametrize("closure", [LEVERMORE, MINERBO])
+def test_closures_are_realizable_and_monotone(closure):
+    """A local closure must satisfy f^2 <= chi <= 1 (a non-negative intensity
+    exists) and grow monotonically from 1/3 to 1."""
+    prev = 1.0 / 3.0 - 1e-16
+    for f in np.linspace(0.0, 1.0, 1001):
+        chi = O.eddington_factor(f, closure)
+        assert f * f - 1e-15 <= chi <= 1.0 + 1e-15
+        assert chi >= prev - 1e-15
+        prev = chi
+
+
+@pytest.mark.parametrize("closure", [MINERBO, EDDINGTON])
+def test_tensor_structure_of_the_other_closures(closure):
+    """T = (1-chi)/2 I + (3 chi - 1)/2 n n for every closure: trace 1,
+    eigenvalue chi along n, (1-chi)/2 across; the Eddington closure gives
+    T = I/3 exactly for every flux, including |f| > 1."""
+    rng = np.random.Generator(np.random.Philox(5))
+    for fm in (0.0, 0.2, 0.7, 1.0, 1.6):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        T = O.eddington_tensor(fm * d, closure)
+        assert abs(np.trace(T) - 1.0) < 1e-14
+        if closure == EDDINGTON:
+            assert np.array_equal(T, np.eye(3) / 3.0)
+            continue
+        chi = O.eddington_factor(min(fm, 1.0), closure)
+        if fm > 0:
+            assert abs(d @ T @ d - chi) < 1e-14
+            e = np.cross(d, [0.3, -0.1, 0.9])
+            e /= np.linalg.norm(e)
+            assert abs(e @ T @ e - 0.5 * (1 - chi)) < 1e-14
+
+
+def _eddington_wave_error(N, axis):
+    """kappa = 0, Eddington closure: eqs. rad_energy and rad_flux become the
+    linear system dE/dt + (chat/c) dF/dx = 0, dF/dt + (c chat/3) dE/dx = 0,
+    whose right-going wave E = E0 + g(x - v t), F = (c/sqrt 3) g(x - v t)
+    travels at v = chat/sqrt(3).  Run one crossing of the periodic line and
+    return the L1 error against the initial state."""
+    c, chat, E0, A = 50.0, 2.0, 1.0, 0.1
+    lay = P.line_layout(N, axis)
+    x = P.centres(N)
+    g = A * np.sin(2 * math.pi * x)
+    R = I.zeros(lay, 4)
+    P.set_line(lay, R[0], E0 + g, axis)
+    P.set_line(lay, R[1 + axis], c / math.sqrt(3.0) * g, axis)
+    rho = np.ones(lay.field_len)
+    dx = [1.0, 1.0, 1.0]
+    dx[axis] = 1.0 / N
+    p = O.make_params(c=c, chat=chat, kappa_P=0.0, kappa_R=0.0, cfl=0.3, dx=dx,
+                      closure=EDDINGTON)
+    grid = _grid(lay)
+    R1 = [np.zeros_like(a) for a in R]
+    t_end = math.sqrt(3.0) / chat
+    nsteps = int(math.ceil(t_end / (0.3 / N / chat)))
+    dt = t_end / nsteps
+    for _ in range(nsteps):
+        O.rad_stage(grid, p, 1, R, None, R1, rho, dt)
+        O.rad_stage(grid, p, 2, R, R1, R, rho, dt)
+    E = P.get_line(lay, R[0], axis)
+    F = P.get_line(lay, R[1 + axis], axis)
+    return (np.abs(E - E0 - g).mean() / A, np.abs(F - c / math.sqrt(3.0) * g).mean()
+            / (c / math.sqrt(3.0) * A))
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_eddington_closure_wave_speed(axis):
+    """The Eddington-closure radiation wave returns to its initial profile after
+    one crossing time sqrt(3)/chat (a wrong 1/3 or chat factor shifts it by a
+    large fraction of the wavelength), converging at second order."""
+    e1 = _eddington_wave_error(32, axis)
+    e2 = _eddington_wave_error(64, axis)
+    assert max(e2) < 5e-3, e2
+    assert e1[0] / e2[0] > 3.0 and e1[1] / e2[1] > 3.0, (e1, e2)
+
+
+# -------------------------------------------------------------- source -----
+
+def test_source_without_coupling_adds_S():
+    """kappa_P = 0: R vanishes, so F_G = 0 keeps E_g and F_R = 0 gives
+    E_r = E_r0 + S exactly."""
+    p = O.make_params(kappa_P=0.0, kappa_R=0.0, c=30.0, chat=3.0, c_v=1.0, a_r=1.0)
+    for S in (0.0, 0.25, 3.0):
+        Eg, Er, it = O.exchange_energy(p, 2.0, 1.5, 0.7, 0.1, S)
+        assert it >= 1 and Eg == 1.5 and Er == 0.7 + S
+
+
+@pytest.mark.parametrize("eos", [0, 1])
+def test_source_energy_budget(eos):
+    """Eqs. F_G and F_R with the source: F_G + (c/chat) F_R = 0 at the
+    solution means E_g + (c/chat) E_r grows by exactly (c/chat) S (the
+    injected energy dt j), to the Newton tolerance and round-off, for strong
+    and weak coupling."""
+    p = O.make_params(kappa_P=50.0, kappa_R=1.0, c=30.0, chat=3.0, c_v=1.3, a_r=0.8,
+                      eos=eos, alpha_eos=2.0, eps_newton=1e-13)
+    cr = p.c / p.chat
+    for rho, Eg0, Er0, S in ((1.0, 2.0, 0.1, 0.3), (3.0, 0.5, 4.0, 1.0), (0.01, 1.0, 1.0, 2.0)):
+        Eg, Er, it = O.exchange_energy(p, rho, Eg0, Er0, 0.05, S)
+        assert it > 0
+        tot0, tot1 = Eg0 + cr * Er0, Eg + cr * Er
+        assert abs((tot1 - tot0) - cr * S) <= 1e-11 * (tot0 + cr * S)
+
+
+def test_source_field_in_the_cell_exchange():
+    """or_exchange takes the source as an emissivity j per cell:
+    S = dt (chat/c) j.  With kappa = 0 the radiation energy of each cell rises
+    by that amount, the gas is untouched, and no source leaves the cell
+    unchanged."""
+    lay = I.single_box(4, 3, 2)
+    U = I.zeros(lay, 5)
+    R = I.zeros(lay, 4)
+    for b in range(lay.nbox):
+        lay.interior(U[0], b)[...] = 1.0
+        lay.interior(U[4], b)[...] = 2.0
+        lay.interior(R[0], b)[...] = 0.5
+    j = np.zeros(lay.field_len)
+    rng = np.random.Generator(np.random.Philox(4))
+    lay.interior(j, 0)[...] = rng.random(lay.interior(j, 0).shape)
+    p = O.make_params(kappa_P=0.0, kappa_R=0.0, c=40.0, chat=4.0)
+    Er0 = lay.interior(R[0], 0).copy()
+    E0 = lay.interior(U[4], 0).copy()
+    dt = 0.2
+    rc, _ = O.exchange(_grid(lay), p, U, R, dt, src=j)
+    assert rc == 0
+    np.testing.assert_array_equal(lay.interior(U[4], 0), E0)
+    np.testing.assert_allclose(lay.interior(R[0], 0), Er0 + dt * (p.chat / p.c) * lay.interior(j, 0),
+                               rtol=1e-15, atol=0)
