@@ -247,7 +247,7 @@ NCU_TRAFFIC = {
 def _src_hash(kind: str) -> str:
     import hashlib
     cs = os.path.join(ROOT, "paper_2110_01792_gb300", "csrc")
-    files = {"rad": ["qk_rad.cu"], "hydro": ["qk_hydro.cu"], "cell": ["qk_cell.cu"]}[kind]
+    files = {"rad": ["qk_rad.cu", "qk_rad.cuh"], "hydro": ["qk_hydro.cu"], "cell": ["qk_cell.cu"]}[kind]
     h = hashlib.sha1()
     for f in files + ["qk_device.cuh", "qk_internal.cuh"]:
         with open(os.path.join(cs, f), "rb") as fh:

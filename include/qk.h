@@ -58,7 +58,12 @@ typedef struct qk_ctx qk_ctx;
  * radiation Riemann solver (Sec. 2.2.2).  hydro_only skips the radiation
  * substeps in qk_step.  recon selects PPM or PLM for both subsystems;
  * flattening enables the shock flattening of Miller & Colella (2002) on the
- * hydro reconstruction (Sec. 2.2.1; the radiation is never flattened). */
+ * hydro reconstruction (Sec. 2.2.1; the radiation is never flattened).
+ * closure selects the local M1 closure chi(f) of the radiation pressure
+ * tensor (Sec. 2.2.2).  bc_lo / bc_hi give the boundary of the low / high
+ * domain face on each axis (QK_BC_*); periodic faces come in pairs.  The
+ * boundary types are fixed when the context is created (qk_set_params
+ * rejects a change). */
 typedef struct {
   double gamma;      /* adiabatic index                                        */
   double cfl;        /* CFL number                                             */
@@ -79,7 +84,31 @@ typedef struct {
   int32_t hydro_only;
   int32_t recon;       /* QK_RECON_PPM (default) or QK_RECON_PLM, hydro and radiation */
   int32_t flattening;  /* 1: multidimensional shock flattening of the hydro states    */
+  int32_t closure;     /* QK_CLOSURE_LEVERMORE (default), _MINERBO or _EDDINGTON       */
+  int32_t bc_lo[3];    /* QK_BC_* of the low face of x, y, z                            */
+  int32_t bc_hi[3];    /* QK_BC_* of the high face of x, y, z                           */
 } qk_params;
+
+/* Closures (Sec. 2.2.2): P_r = [(1-chi)/2 I + (3 chi - 1)/2 n n] E_r with
+ * f = |F|/(c E_r) clamped to 1 for the closure. */
+#define QK_CLOSURE_LEVERMORE 0 /* chi = (3 + 4 f^2)/(5 + 2 sqrt(4 - 3 f^2))              */
+#define QK_CLOSURE_MINERBO 1   /* maximum entropy, polynomial form:
+                                  chi = 1/3 + (2/15)(3 f^2 - f^3 + 3 f^4)              */
+#define QK_CLOSURE_EDDINGTON 2 /* chi = 1/3: P_r = E_r I / 3                           */
+
+/* Domain boundaries.  Ghost cells beyond a face hold:
+ *   PERIODIC  the interior cell of the periodic image;
+ *   REFLECT   the mirror image across the face (x -> -1-x), with the vector
+ *             components along that axis (m and F) negated;
+ *   OUTFLOW   the nearest interior cell (zero gradient);
+ *   DIRICHLET the boundary state recorded by qk_set_dirichlet.
+ * Each axis is mapped on its own (edges and corners combine them); a ghost
+ * cell beyond any Dirichlet face takes its recorded state.  A reflecting
+ * axis needs at least nghost cells across the domain. */
+#define QK_BC_PERIODIC 0
+#define QK_BC_REFLECT 1
+#define QK_BC_OUTFLOW 2
+#define QK_BC_DIRICHLET 3
 
 #define QK_RECON_PPM 0 /* piecewise parabolic with the paper's limiter (Sec. 2.2.1)  */
 #define QK_RECON_PLM 1 /* piecewise linear, monotonized-central slope (Sec. 2.2.1)  */
@@ -121,6 +150,23 @@ int qk_init_shard(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t
                   const int32_t domain_n[3], int32_t nghost, int32_t precision,
                   const int32_t *owner, int32_t nranks, int32_t rank);
 
+/* Host-only view of the ghost-fill plan that qk_init_patches would build
+ * for this patch set (no GPU call; for inspection and CPU-side checks of the
+ * boundary handling).  Writes at most `cap` records of 12 int64 each to
+ * `out`, copies first, then Dirichlet regions:
+ *   copy:      dst, src, ex, ey, ez, dsx, dsy, flip, sx, sy, sz, 0
+ *              (destination cell (x, y, z) of the region is element
+ *               dst + (z dsy + y) dsx + x; its source is src + x sx + y sy +
+ *               z sz; flip bit d negates the d-components of vectors)
+ *   Dirichlet: dst, 0, ex, ey, ez, dsx, dsy, 0, 0, 0, 0, 1
+ *              (a region whose cells take the recorded boundary state).
+ * *ncopies and *ndirichlet receive the full counts (records beyond cap are
+ * not written).  Validation as qk_init_patches; failures are reported through
+ * qk_last_error(NULL). */
+int qk_fill_plan(const qk_params *p, const qk_box *boxes, int32_t nbox,
+                 const int32_t domain_n[3], int32_t nghost, int64_t *out, int64_t cap,
+                 int64_t *ncopies, int64_t *ndirichlet);
+
 /* Free the context and all library-owned device memory. */
 void qk_destroy(qk_ctx *ctx);
 
@@ -140,9 +186,38 @@ int qk_set_params(qk_ctx *ctx, const qk_params *p);
 
 /* Fill the ghost cells of `nfields` field arrays (Sec. 2.2, 'FillBoundary'):
  * every ghost cell of every patch receives the value of the interior cell that
- * owns its periodic image.  One batched launch over precomputed copy
- * descriptors. */
+ * owns its periodic image (or, at non-periodic faces, its QK_BC_* value).  One
+ * batched launch over precomputed copy descriptors (plus one for Dirichlet
+ * states).  fields[i] holds state field i of (rho, m_x, m_y, m_z, E, E_r,
+ * F_x, F_y, F_z). */
 int qk_fill_ghosts(qk_ctx *ctx, void *const *fields, int32_t nfields, void *stream);
+
+/* The same fill for fields that hold the state fields first .. first+nfields-1
+ * of the list (rho, m_x, m_y, m_z, E, E_r, F_x, F_y, F_z): their identity
+ * decides which values change sign at a reflecting face and which Dirichlet
+ * states they take (qk_fill_ghosts is first = 0).  Under non-periodic
+ * boundaries every ghost cell follows the QK_BC_* rule of its faces. */
+int qk_fill_ghosts_range(qk_ctx *ctx, void *const *fields, int32_t first, int32_t nfields,
+                         void *stream);
+
+/* Record the Dirichlet boundary states: the values the caller's hydro and
+ * radiation arrays (rad may be NULL: zero radiation) hold in the ghost cells
+ * beyond the QK_BC_DIRICHLET faces are copied into library storage (9 values
+ * per such ghost cell, on the device); every later ghost fill restores them.
+ * Must precede any fill or step of a context with Dirichlet faces (those
+ * calls return QK_EINVAL until it has been made); call again to change the
+ * states.  Asynchronous on `stream`. */
+int qk_set_dirichlet(qk_ctx *ctx, void *const hydro[5], void *const rad[4], void *stream);
+
+/* Radiation source of the matter-radiation exchange (Sec. 2.2.3, the S of
+ * eq. F_R): `j` is a device field (the context's element type and layout)
+ * holding an emissivity per cell, energy per unit volume per unit time in
+ * the physical energy equation; each exchange of duration dt_rad adds
+ * S = dt_rad (chat/c) j to the radiation-energy residual (the reduced-speed
+ * form of that equation).  NULL removes it.  The caller keeps the array alive
+ * while it is set; qk_step and qk_rad_matter_exchange read it.  Captured step
+ * graphs are dropped. */
+int qk_set_source(qk_ctx *ctx, const void *j);
 
 /* One RK2-SSP stage of the hydro update (Sec. 2.2.1): conserved -> primitive,
  * PPM reconstruction of (rho, v, P) per direction, HLLC fluxes with PVRS
@@ -269,7 +344,9 @@ int qk_halo_info(const qk_ctx *ctx, int32_t peer, int64_t *send_cells, int64_t *
                  int32_t *owned_boxes);
 
 /* Cross-rank ghost exchange (Sec. 4, FillBoundary across GPUs).  Pack gathers,
- * from this rank's `nfields` field arrays, the interior cells that `peer`'s
+ * from this rank's `nfields` field arrays (state fields first ..
+ * first+nfields-1, as in qk_fill_ghosts_range: the sign flips of reflecting
+ * faces are applied while packing), the interior cells that `peer`'s
  * ghost regions need, into the device buffer `buf` of nfields x send_cells
  * elements (the context's precision; field-major, regions in one order agreed
  * by both ranks, x fastest).  Unpack scatters a buffer received from `peer`
@@ -280,10 +357,10 @@ int qk_halo_info(const qk_ctx *ctx, int32_t peer, int64_t *send_cells, int64_t *
  * qk_fill_ghosts plus, for every peer, pack -> transfer -> unpack.  QK_EINVAL
  * for peer == this rank or out of range; nothing is launched when the halo to
  * that peer is empty. */
-int qk_halo_pack(qk_ctx *ctx, int32_t peer, void *const *fields, int32_t nfields, void *buf,
-                 void *stream);
-int qk_halo_unpack(qk_ctx *ctx, int32_t peer, void *const *fields, int32_t nfields,
-                   const void *buf, void *stream);
+int qk_halo_pack(qk_ctx *ctx, int32_t peer, void *const *fields, int32_t first, int32_t nfields,
+                 void *buf, void *stream);
+int qk_halo_unpack(qk_ctx *ctx, int32_t peer, void *const *fields, int32_t first,
+                   int32_t nfields, const void *buf, void *stream);
 
 /* Global timestep of a sharded step, in two halves around the caller's
  * max-reduction over ranks (Sec. 2.2: one dt from the CFL condition on the

@@ -44,6 +44,14 @@ struct qk_ctx {
   Copy *d_copies = nullptr;
   Chunk *d_chunks = nullptr;
   int ncopies = 0, nchunks = 0;
+  // Dirichlet boundary store: 9 fields x ndir cells, recorded by
+  // qk_set_dirichlet from the caller's ghost cells, restored by every fill
+  Copy *d_dpack = nullptr, *d_dunpack = nullptr;
+  Chunk *d_dchunks = nullptr;
+  int ndchunks = 0;
+  long long ndir = 0;
+  void *dstore = nullptr;
+  int dir_set = 0;
   StepInfo *d_si = nullptr;
   Status *d_status = nullptr;
   double *d_partials = nullptr;
@@ -51,6 +59,7 @@ struct qk_ctx {
   int sum_blocks = 0;
   void *scratch[9] = {};
   void *chi = nullptr;   // shock-flattening coefficient (one field)
+  const void *src = nullptr;  // caller's emissivity field j of the exchange, or none
   size_t elem = 8;
   // pinned host staging
   double *h_buf = nullptr;
@@ -98,6 +107,15 @@ static Geometry geom(const qk_ctx *c) {
 
 static int check_params(qk_ctx *c, const qk_params *p) {
   if (!p) return fail(c, QK_EINVAL, "params is NULL");
+  if (p->closure < QK_CLOSURE_LEVERMORE || p->closure > QK_CLOSURE_EDDINGTON)
+    return fail(c, QK_EINVAL, "unknown closure %d", p->closure);
+  for (int d = 0; d < 3; ++d) {
+    if (p->bc_lo[d] < QK_BC_PERIODIC || p->bc_lo[d] > QK_BC_DIRICHLET || p->bc_hi[d] < QK_BC_PERIODIC ||
+        p->bc_hi[d] > QK_BC_DIRICHLET)
+      return fail(c, QK_EINVAL, "unknown boundary type on axis %d", d);
+    if ((p->bc_lo[d] == QK_BC_PERIODIC) != (p->bc_hi[d] == QK_BC_PERIODIC))
+      return fail(c, QK_EINVAL, "axis %d: a periodic boundary needs both faces periodic", d);
+  }
   if (!(p->gamma > 1.0)) return fail(c, QK_EINVAL, "gamma must exceed 1");
   if (!(p->cfl > 0.0)) return fail(c, QK_EINVAL, "cfl must be positive");
   for (int d = 0; d < 3; ++d)
@@ -127,12 +145,55 @@ static int64_t padded_vol(const qk_box &b, int ng) {
   return (int64_t)(b.n[0] + 2 * ng) * (b.n[1] + 2 * ng) * (b.n[2] + 2 * ng);
 }
 
+// One axis of a ghost sub-region: destination cells [a0, a1) in global
+// (unwrapped) coordinates and the rule that gives their source coordinate.
+struct Piece {
+  int a0, a1;
+  int kind;   // 0: x - shift (inside, or a periodic image); 1: mirror, m - x;
+              // 2: clamp to c (outflow); 3: Dirichlet store
+  int shift, m, c;
+};
+
+static int fdiv(int a, int m) { return a >= 0 ? a / m : -((-a + m - 1) / m); }
+
+// Split [r0, r1) on one axis of length D by the domain faces and their
+// boundary types.
+static void axis_pieces(int r0, int r1, int D, int bclo, int bchi, std::vector<Piece> &out) {
+  out.clear();
+  if (bclo == QK_BC_PERIODIC) {
+    for (int k = fdiv(r0, D); k <= fdiv(r1 - 1, D); ++k) {
+      const int a0 = std::max(r0, k * D), a1 = std::min(r1, (k + 1) * D);
+      if (a0 < a1) out.push_back(Piece{a0, a1, 0, k * D, 0, 0});
+    }
+    return;
+  }
+  auto outside = [&](int a0, int a1, int bc, bool low) {
+    if (a0 >= a1) return;
+    if (bc == QK_BC_REFLECT) out.push_back(Piece{a0, a1, 1, 0, low ? -1 : 2 * D - 1, 0});
+    else if (bc == QK_BC_OUTFLOW) out.push_back(Piece{a0, a1, 2, 0, 0, low ? 0 : D - 1});
+    else out.push_back(Piece{a0, a1, 3, 0, 0, 0});
+  };
+  outside(r0, std::min(r1, 0), bclo, true);
+  if (std::max(r0, 0) < std::min(r1, D)) out.push_back(Piece{std::max(r0, 0), std::min(r1, D), 0, 0, 0, 0});
+  outside(std::max(r0, D), r1, bchi, false);
+}
+
 // Ghost-copy descriptors: for each patch, the 26 ghost sub-boxes around its
-// interior, intersected with every patch's interior under every periodic
-// shift that reaches them.  A binned index of the patches keeps this linear.
+// interior, split per axis by the domain faces (periodic images, mirror
+// images, clamped cells, Dirichlet cells), and each copyable piece
+// intersected with every patch's interior that supplies its sources.  A
+// binned index of the patches keeps this linear.  Dirichlet pieces become
+// store regions (destination boxes in patch-local coordinates).  In a
+// sharded context, copies with both ends owned go to `out`, the others to the
+// per-peer send / receive lists; Dirichlet regions of owned patches only.
+struct DirRegion {
+  long long dst;      // first element
+  int ex, ey, ez, dsx, dsy;
+};
+
 static int build_copies(qk_ctx *c, std::vector<Copy> &out,
-                        std::vector<std::vector<Copy>> *send = nullptr,
-                        std::vector<std::vector<Copy>> *recv = nullptr) {
+                        std::vector<std::vector<Copy>> *send,
+                        std::vector<std::vector<Copy>> *recv, std::vector<DirRegion> *dir) {
   const int ng = c->ng;
   const int *D = c->dom;
   const int BIN = 16;
@@ -153,77 +214,104 @@ static int build_copies(qk_ctx *c, std::vector<Copy> &out,
   std::vector<int> stamp(c->nbox, -1);
   int stamp_id = 0;
   const bool sharded = !c->owner.empty();
+  std::vector<Piece> pc[3];
   for (int b = 0; b < c->nbox; ++b) {
     const qk_box &B = c->boxes[b];
     const int sx = B.n[0] + 2 * ng, sy = B.n[1] + 2 * ng;
+    const bool own_b = !sharded || c->owner[b] == c->rank;
     // a sharded rank visits every destination patch: remote destinations
     // can still need this rank's patches as sources (send lists)
     for (int rz = 0; rz < 3; ++rz)
       for (int ry = 0; ry < 3; ++ry)
         for (int rx = 0; rx < 3; ++rx) {
           if (rx == 1 && ry == 1 && rz == 1) continue;
-          int r0[3], r1[3];  // region in global (unwrapped) coordinates
           const int rs[3] = {rx, ry, rz};
           for (int d = 0; d < 3; ++d) {
-            if (rs[d] == 0) { r0[d] = B.lo[d] - ng; r1[d] = B.lo[d]; }
-            else if (rs[d] == 1) { r0[d] = B.lo[d]; r1[d] = B.lo[d] + B.n[d]; }
-            else { r0[d] = B.lo[d] + B.n[d]; r1[d] = B.lo[d] + B.n[d] + ng; }
+            int r0, r1;  // region in global (unwrapped) coordinates
+            if (rs[d] == 0) { r0 = B.lo[d] - ng; r1 = B.lo[d]; }
+            else if (rs[d] == 1) { r0 = B.lo[d]; r1 = B.lo[d] + B.n[d]; }
+            else { r0 = B.lo[d] + B.n[d]; r1 = B.lo[d] + B.n[d] + ng; }
+            axis_pieces(r0, r1, D[d], c->p.bc_lo[d], c->p.bc_hi[d], pc[d]);
           }
-          int a0[3], a1[3];
-          for (int d = 0; d < 3; ++d) {
-            auto fdiv = [](int a, int m) { return a >= 0 ? a / m : -((-a + m - 1) / m); };
-            a0[d] = fdiv(r0[d], D[d]);
-            a1[d] = fdiv(r1[d] - 1, D[d]);
-          }
-          for (int az = a0[2]; az <= a1[2]; ++az)
-            for (int ay = a0[1]; ay <= a1[1]; ++ay)
-              for (int ax = a0[0]; ax <= a1[0]; ++ax) {
-                const int sh[3] = {ax * D[0], ay * D[1], az * D[2]};
-                int w0[3], w1[3];  // region shifted into the domain, clipped
-                bool empty = false;
-                for (int d = 0; d < 3; ++d) {
-                  w0[d] = std::max(r0[d] - sh[d], 0);
-                  w1[d] = std::min(r1[d] - sh[d], D[d]);
-                  if (w0[d] >= w1[d]) empty = true;
+          for (const Piece &pz : pc[2])
+            for (const Piece &py : pc[1])
+              for (const Piece &px : pc[0]) {
+                const Piece *P[3] = {&px, &py, &pz};
+                long long dl0[3];
+                for (int d = 0; d < 3; ++d) dl0[d] = (long long)P[d]->a0 - B.lo[d] + ng;
+                if (px.kind == 3 || py.kind == 3 || pz.kind == 3) {
+                  if (own_b && dir)
+                    dir->push_back(DirRegion{B.offset + (dl0[2] * sy + dl0[1]) * sx + dl0[0],
+                                             px.a1 - px.a0, py.a1 - py.a0, pz.a1 - pz.a0, sx, sy});
+                  continue;
                 }
-                if (empty) continue;
+                int s0[3], s1[3];  // source range in the domain
+                for (int d = 0; d < 3; ++d) {
+                  const Piece &q = *P[d];
+                  if (q.kind == 0) { s0[d] = q.a0 - q.shift; s1[d] = q.a1 - q.shift; }
+                  else if (q.kind == 1) { s0[d] = q.m - q.a1 + 1; s1[d] = q.m - q.a0 + 1; }
+                  else { s0[d] = q.c; s1[d] = q.c + 1; }
+                }
                 ++stamp_id;
-                for (int z = w0[2] / BIN; z <= (w1[2] - 1) / BIN; ++z)
-                  for (int y = w0[1] / BIN; y <= (w1[1] - 1) / BIN; ++y)
-                    for (int x = w0[0] / BIN; x <= (w1[0] - 1) / BIN; ++x)
-                      for (int q : bins[((size_t)z * nb[1] + y) * nb[0] + x]) {
-                        if (stamp[q] == stamp_id) continue;
-                        stamp[q] = stamp_id;
-                        const qk_box &Q = c->boxes[q];
+                for (int z = s0[2] / BIN; z <= (s1[2] - 1) / BIN; ++z)
+                  for (int y = s0[1] / BIN; y <= (s1[1] - 1) / BIN; ++y)
+                    for (int x = s0[0] / BIN; x <= (s1[0] - 1) / BIN; ++x)
+                      for (int qb : bins[((size_t)z * nb[1] + y) * nb[0] + x]) {
+                        if (stamp[qb] == stamp_id) continue;
+                        stamp[qb] = stamp_id;
+                        const qk_box &Q = c->boxes[qb];
                         int i0[3], i1[3];
                         bool none = false;
                         for (int d = 0; d < 3; ++d) {
-                          i0[d] = std::max(w0[d], Q.lo[d]);
-                          i1[d] = std::min(w1[d], Q.lo[d] + Q.n[d]);
+                          i0[d] = std::max(s0[d], Q.lo[d]);
+                          i1[d] = std::min(s1[d], Q.lo[d] + Q.n[d]);
                           if (i0[d] >= i1[d]) none = true;
                         }
                         if (none) continue;
-                        Copy cp;
-                        const int qsx = Q.n[0] + 2 * ng, qsy = Q.n[1] + 2 * ng;
-                        // destination: local (i0 + shift - B.lo) in patch b
+                        // destination range and the source of its first cell, per axis
+                        int e0[3], ext[3], sfirst[3], step[3], flip = 0;
+                        for (int d = 0; d < 3; ++d) {
+                          const Piece &q = *P[d];
+                          if (q.kind == 0) {
+                            e0[d] = i0[d] + q.shift;
+                            ext[d] = i1[d] - i0[d];
+                            sfirst[d] = i0[d];
+                            step[d] = 1;
+                          } else if (q.kind == 1) {
+                            e0[d] = q.m - i1[d] + 1;
+                            ext[d] = i1[d] - i0[d];
+                            sfirst[d] = i1[d] - 1;
+                            step[d] = -1;
+                            flip |= 1 << d;
+                          } else {
+                            e0[d] = q.a0;
+                            ext[d] = q.a1 - q.a0;
+                            sfirst[d] = q.c;
+                            step[d] = 0;
+                          }
+                        }
+                        const long long qsx = Q.n[0] + 2 * ng, qsy = Q.n[1] + 2 * ng;
                         long long dl[3], sl[3];
                         for (int d = 0; d < 3; ++d) {
-                          dl[d] = (long long)i0[d] + sh[d] - B.lo[d] + ng;
-                          sl[d] = (long long)i0[d] - Q.lo[d] + ng;
+                          dl[d] = (long long)e0[d] - B.lo[d] + ng;
+                          sl[d] = (long long)sfirst[d] - Q.lo[d] + ng;
                         }
+                        Copy cp;
                         cp.dst = B.offset + (dl[2] * sy + dl[1]) * sx + dl[0];
                         cp.src = Q.offset + (sl[2] * qsy + sl[1]) * qsx + sl[0];
-                        cp.ex = i1[0] - i0[0];
-                        cp.ey = i1[1] - i0[1];
-                        cp.ez = i1[2] - i0[2];
+                        cp.ex = ext[0];
+                        cp.ey = ext[1];
+                        cp.ez = ext[2];
                         cp.dsx = sx;
                         cp.dsy = sy;
-                        cp.ssx = qsx;
-                        cp.ssy = qsy;
+                        cp.flip = flip;
+                        cp.sx = step[0];
+                        cp.sy = step[1] * qsx;
+                        cp.sz = step[2] * qsx * qsy;
                         if (!sharded) {
                           out.push_back(cp);
                         } else {
-                          const int rb = c->owner[b], rq = c->owner[q];
+                          const int rb = c->owner[b], rq = c->owner[qb];
                           if (rb == c->rank && rq == c->rank) out.push_back(cp);
                           else if (rb == c->rank) (*recv)[rq].push_back(cp);
                           else if (rq == c->rank) (*send)[rb].push_back(cp);
@@ -305,6 +393,10 @@ static void release(qk_ctx *c) {
   cudaFree(c->d_recv);
   cudaFree(c->d_send_chunks);
   cudaFree(c->d_recv_chunks);
+  cudaFree(c->d_dpack);
+  cudaFree(c->d_dunpack);
+  cudaFree(c->d_dchunks);
+  cudaFree(c->dstore);
   cudaFree(c->d_si);
   cudaFree(c->d_status);
   cudaFree(c->d_partials);
@@ -344,6 +436,9 @@ static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, in
   c->ng = nghost;
   c->nbox = nbox;
   for (int d = 0; d < 3; ++d) c->dom[d] = domain_n[d];
+  for (int d = 0; d < 3; ++d)
+    if ((p->bc_lo[d] == QK_BC_REFLECT || p->bc_hi[d] == QK_BC_REFLECT) && domain_n[d] < nghost)
+      return bail(fail(c, QK_EINVAL, "axis %d: a reflecting boundary needs at least nghost cells", d));
   c->boxes.assign(boxes, boxes + nbox);
   if (owner) {
     if (nranks < 1 || rank < 0 || rank >= nranks)
@@ -389,7 +484,46 @@ static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, in
   c->ntiles = (int)tiles.size();
   std::vector<Copy> copies;
   std::vector<std::vector<Copy>> send(c->nranks), recv(c->nranks);
-  build_copies(c, copies, &send, &recv);
+  std::vector<DirRegion> dir;
+  build_copies(c, copies, &send, &recv, &dir);
+  // Dirichlet store descriptors: packing reads the region (strided) into the
+  // store, unpacking writes it back; store positions in region order
+  {
+    std::vector<Copy> dp, du;
+    std::vector<Chunk> dch;
+    long long pos = 0;
+    for (const DirRegion &r : dir) {
+      Copy cp{};
+      cp.ex = r.ex;
+      cp.ey = r.ey;
+      cp.ez = r.ez;
+      cp.dsx = r.dsx;
+      cp.dsy = r.dsy;
+      cp.sx = 1;
+      cp.sy = r.dsx;
+      cp.sz = (long long)r.dsx * r.dsy;
+      Copy pk = cp, up = cp;
+      pk.src = r.dst;
+      pk.dst = pos;
+      up.dst = r.dst;
+      up.src = pos;
+      dp.push_back(pk);
+      du.push_back(up);
+      const int n = r.ex * r.ey * r.ez;
+      for (int s0 = 0; s0 < n; s0 += CHUNK_CELLS) dch.push_back(Chunk{(int)dp.size() - 1, s0});
+      pos += n;
+    }
+    c->ndir = pos;
+    c->ndchunks = (int)dch.size();
+    if ((rc = upload(c, &c->d_dpack, dp))) return bail(rc);
+    if ((rc = upload(c, &c->d_dunpack, du))) return bail(rc);
+    if ((rc = upload(c, &c->d_dchunks, dch))) return bail(rc);
+    if (pos > 0) {
+      cudaError_t e2 = cudaMalloc(&c->dstore, (size_t)(9 * pos) * c->elem);
+      if (e2 == cudaSuccess) e2 = cudaMemset(c->dstore, 0, (size_t)(9 * pos) * c->elem);
+      if (e2 != cudaSuccess) return bail(cuda_fail(c, e2, "cudaMalloc(Dirichlet store)"));
+    }
+  }
   // halo descriptors: the send side packs each region contiguously (x fastest)
   // into the peer's buffer; the receive side unpacks in the same order
   std::vector<Copy> sd, rv;
@@ -468,6 +602,53 @@ static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, in
   return QK_OK;
 }
 
+int qk_fill_plan(const qk_params *p, const qk_box *boxes, int32_t nbox,
+                 const int32_t domain_n[3], int32_t nghost, int64_t *out, int64_t cap,
+                 int64_t *ncopies, int64_t *ndirichlet) {
+  qk_ctx c;
+  int rc = check_params(&c, p);
+  if (!rc && (!boxes || nbox < 1 || !domain_n)) rc = fail(&c, QK_EINVAL, "no boxes");
+  if (!rc && (nghost < HALO || nghost > 16)) rc = fail(&c, QK_EINVAL, "nghost must be in [3, 16]");
+  if (rc) {
+    g_init_err = c.err;
+    return rc;
+  }
+  c.p = *p;
+  c.ng = nghost;
+  c.nbox = nbox;
+  for (int d = 0; d < 3; ++d) c.dom[d] = domain_n[d];
+  for (int d = 0; d < 3; ++d)
+    if ((p->bc_lo[d] == QK_BC_REFLECT || p->bc_hi[d] == QK_BC_REFLECT) && domain_n[d] < nghost) {
+      g_init_err = "a reflecting boundary needs at least nghost cells";
+      return QK_EINVAL;
+    }
+  c.boxes.assign(boxes, boxes + nbox);
+  if ((rc = validate_boxes(&c))) {
+    g_init_err = c.err;
+    return rc;
+  }
+  std::vector<Copy> copies;
+  std::vector<DirRegion> dir;
+  build_copies(&c, copies, nullptr, nullptr, &dir);
+  if (ncopies) *ncopies = (int64_t)copies.size();
+  if (ndirichlet) *ndirichlet = (int64_t)dir.size();
+  int64_t k = 0;
+  for (const Copy &cp : copies) {
+    if (k >= cap) break;
+    int64_t *o = out + 12 * k++;
+    const int64_t v[12] = {cp.dst, cp.src, cp.ex, cp.ey, cp.ez, cp.dsx, cp.dsy, cp.flip,
+                           cp.sx, cp.sy, cp.sz, 0};
+    memcpy(o, v, sizeof(v));
+  }
+  for (const DirRegion &r : dir) {
+    if (k >= cap) break;
+    int64_t *o = out + 12 * k++;
+    const int64_t v[12] = {r.dst, 0, r.ex, r.ey, r.ez, r.dsx, r.dsy, 0, 0, 0, 0, 1};
+    memcpy(o, v, sizeof(v));
+  }
+  return QK_OK;
+}
+
 int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
                     const int32_t domain_n[3], int32_t nghost, int32_t precision) {
   return init_common(out, p, boxes, nbox, domain_n, nghost, precision, nullptr, 1, 0);
@@ -501,6 +682,9 @@ int qk_set_params(qk_ctx *c, const qk_params *p) {
   if (!c) return QK_EINVAL;
   int rc = check_params(c, p);
   if (rc) return rc;
+  if (memcmp(p->bc_lo, c->p.bc_lo, sizeof(p->bc_lo)) != 0 ||
+      memcmp(p->bc_hi, c->p.bc_hi, sizeof(p->bc_hi)) != 0)
+    return fail(c, QK_EINVAL, "boundary types are fixed when the context is created");
   c->p = *p;
   if (c->gexec) {
     cudaGraphExecDestroy(c->gexec);
@@ -510,6 +694,24 @@ int qk_set_params(qk_ctx *c, const qk_params *p) {
 }
 
 static int check_fields(qk_ctx *c, void *const *f, int n, const char *what);
+
+// Full ghost fill of nf fields holding state fields first .. first+nf-1:
+// descriptor copies (periodic, mirror, clamped), then the Dirichlet states.
+static cudaError_t fill(qk_ctx *c, void *const *fields, int nf, int first, DtSrc pred,
+                        cudaStream_t s) {
+  cudaError_t e =
+      launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, fields, nf, first, pred, s);
+  if (e == cudaSuccess && c->ndir > 0)
+    e = launch_halo(c->fp32, 0, c->d_dunpack, c->d_dchunks, c->ndchunks, fields, nf, first,
+                    (char *)c->dstore + (size_t)first * c->ndir * c->elem, c->ndir, pred, s);
+  return e;
+}
+
+static int need_dirichlet(qk_ctx *c) {
+  if (c->ndir > 0 && !c->dir_set)
+    return fail(c, QK_EINVAL, "Dirichlet faces: record the boundary states with qk_set_dirichlet first");
+  return QK_OK;
+}
 
 // Autotuner: time every candidate launch configuration of each stage kernel
 // (threads per CTA x tile schedule) on the caller's state and keep the
@@ -521,6 +723,7 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
   int rc = check_fields(c, hydro, 5, "hydro");
   if (rc) return rc;
   if (rad && (rc = check_fields(c, rad, 4, "rad"))) return rc;
+  if ((rc = need_dirichlet(c))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const Geometry g = geom(c);
   const int threads[3] = {128, 256, 512};
@@ -544,12 +747,8 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
   // timestep for realistic dt values; it does not change the state
   cudaError_t err = launch_max_speed(c->fp32, g, c->p, hydro, c->d_si, s);
   if (err == cudaSuccess) err = launch_timestep(c->p, c->d_si, s);
-  if (err == cudaSuccess)
-    err = launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, hydro, 5,
-                            DtSrc{nullptr, 0.0, 0, -1}, s);
-  if (err == cudaSuccess && rad)
-    err = launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, rad, 4,
-                            DtSrc{nullptr, 0.0, 0, -1}, s);
+  if (err == cudaSuccess) err = fill(c, hydro, 5, 0, DtSrc{nullptr, 0.0, 0, -1}, s);
+  if (err == cudaSuccess && rad) err = fill(c, rad, 4, 5, DtSrc{nullptr, 0.0, 0, -1}, s);
   if (err == cudaSuccess && c->p.flattening) err = launch_flatten(c->fp32, g, c->p, hydro, c->chi, s);
   const DtSrc dth{c->d_si, 0.0, 0, -1}, dtr{c->d_si, 0.0, 2, -1};
   for (int which = 0; which < 4 && err == cudaSuccess; ++which) {
@@ -609,6 +808,16 @@ int qk_set_launch_mode(qk_ctx *c, int32_t mode) {
   return QK_OK;
 }
 
+int qk_set_source(qk_ctx *c, const void *j) {
+  if (!c) return QK_EINVAL;
+  c->src = j;
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  return QK_OK;
+}
+
 int qk_set_graph(qk_ctx *c, int32_t enable) {
   if (!c) return QK_EINVAL;
   c->use_graph = enable ? 1 : 0;
@@ -622,14 +831,41 @@ static int check_fields(qk_ctx *c, void *const *f, int n, const char *what) {
   return QK_OK;
 }
 
-int qk_fill_ghosts(qk_ctx *c, void *const *fields, int32_t nfields, void *stream) {
+int qk_fill_ghosts_range(qk_ctx *c, void *const *fields, int32_t first, int32_t nfields,
+                         void *stream) {
   if (!c) return QK_EINVAL;
-  if (nfields < 0 || nfields > 9) return fail(c, QK_EINVAL, "nfields must be in [0, 9]");
+  if (first < 0 || nfields < 0 || first + nfields > 9)
+    return fail(c, QK_EINVAL, "fields first .. first+nfields-1 must lie in [0, 9)");
   int rc = check_fields(c, fields, nfields, "fields");
   if (rc) return rc;
+  if ((rc = need_dirichlet(c))) return rc;
   DtSrc pred{nullptr, 0.0, 0, -1};
-  QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, fields, nfields,
-                               pred, (cudaStream_t)stream));
+  QK_CUDA(c, fill(c, fields, nfields, first, pred, (cudaStream_t)stream));
+  return QK_OK;
+}
+
+int qk_fill_ghosts(qk_ctx *c, void *const *fields, int32_t nfields, void *stream) {
+  return qk_fill_ghosts_range(c, fields, 0, nfields, stream);
+}
+
+int qk_set_dirichlet(qk_ctx *c, void *const hydro[5], void *const rad[4], void *stream) {
+  if (!c) return QK_EINVAL;
+  int rc = check_fields(c, hydro, 5, "hydro");
+  if (rc) return rc;
+  if (rad && (rc = check_fields(c, rad, 4, "rad"))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->ndir > 0) {
+    const DtSrc none{nullptr, 0.0, 0, -1};
+    QK_CUDA(c, launch_halo(c->fp32, 1, c->d_dpack, c->d_dchunks, c->ndchunks, hydro, 5, 0,
+                           c->dstore, c->ndir, none, s));
+    char *rbuf = (char *)c->dstore + (size_t)5 * c->ndir * c->elem;
+    if (rad)
+      QK_CUDA(c, launch_halo(c->fp32, 1, c->d_dpack, c->d_dchunks, c->ndchunks, rad, 4, 5, rbuf,
+                             c->ndir, none, s));
+    else
+      QK_CUDA(c, cudaMemsetAsync(rbuf, 0, (size_t)4 * c->ndir * c->elem, s));
+  }
+  c->dir_set = 1;
   return QK_OK;
 }
 
@@ -685,7 +921,7 @@ int qk_rad_matter_exchange(qk_ctx *c, void *const hydro[5], void *const rad[4], 
   if (!rc) rc = check_fields(c, rad, 4, "rad");
   if (rc) return rc;
   DtSrc d{nullptr, dt_rad, 2, -1};
-  QK_CUDA(c, launch_exchange(c->fp32, geom(c), c->p, hydro, rad, d, c->d_status,
+  QK_CUDA(c, launch_exchange(c->fp32, geom(c), c->p, hydro, rad, c->src, d, c->d_status,
                              (cudaStream_t)stream));
   return QK_OK;
 }
@@ -760,19 +996,19 @@ static int enqueue_step(qk_ctx *c, void *const hydro[5], void *const rad[4], cud
   const DtSrc none{nullptr, 0.0, 0, -1};
   QK_CUDA(c, launch_max_speed(c->fp32, g, c->p, hydro, c->d_si, s));
   QK_CUDA(c, launch_timestep(c->p, c->d_si, s));
-  QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, hydro, 5, none, s));
+  QK_CUDA(c, fill(c, hydro, 5, 0, none, s));
   QK_CUDA(c, hydro_launches(c, 1, hydro, nullptr, U1, dth, s));
-  QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, U1, 5, none, s));
+  QK_CUDA(c, fill(c, U1, 5, 0, none, s));
   QK_CUDA(c, hydro_launches(c, 2, hydro, U1, hydro, dth, s));
   if (rad && !c->p.hydro_only) {
-    QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, hydro, 1, none, s));
+    QK_CUDA(c, fill(c, hydro, 1, 0, none, s));
     for (int sub = 0; sub < c->p.nsub_max; ++sub) {
       const DtSrc dr{c->d_si, 0.0, 2, sub};
-      QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, rad, 4, dr, s));
+      QK_CUDA(c, fill(c, rad, 4, 5, dr, s));
       QK_CUDA(c, rad_launches(c, 1, rad, nullptr, R1, hydro[0], dr, s));
-      QK_CUDA(c, launch_ghost_fill(c->fp32, c->d_copies, c->d_chunks, c->nchunks, R1, 4, dr, s));
+      QK_CUDA(c, fill(c, R1, 4, 5, dr, s));
       QK_CUDA(c, rad_launches(c, 2, rad, R1, rad, hydro[0], dr, s));
-      QK_CUDA(c, launch_exchange(c->fp32, g, c->p, hydro, rad, dr, c->d_status, s));
+      QK_CUDA(c, launch_exchange(c->fp32, g, c->p, hydro, rad, c->src, dr, c->d_status, s));
     }
   }
   return QK_OK;
@@ -786,6 +1022,7 @@ int qk_step(qk_ctx *c, void *const hydro[5], void *const rad[4], double *dt_out,
   if (rad && (rc = check_fields(c, rad, 4, "rad"))) return rc;
   if (c->nranks > 1)
     return fail(c, QK_EINVAL, "sharded context: compose the step from the stage entry points");
+  if ((rc = need_dirichlet(c))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   if (c->use_graph) {
     void *key[10];
@@ -870,12 +1107,13 @@ int qk_halo_info(const qk_ctx *c, int32_t peer, int64_t *send_cells, int64_t *re
   return QK_OK;
 }
 
-static int halo(qk_ctx *c, int pack, int32_t peer, void *const *fields, int32_t nfields,
-                void *buf, void *stream) {
+static int halo(qk_ctx *c, int pack, int32_t peer, void *const *fields, int32_t first,
+                int32_t nfields, void *buf, void *stream) {
   if (!c) return QK_EINVAL;
   if (peer < 0 || peer >= c->nranks) return fail(c, QK_EINVAL, "peer %d outside [0, %d)", peer, c->nranks);
   if (peer == c->rank) return fail(c, QK_EINVAL, "peer %d is this rank", peer);
-  if (nfields < 1 || nfields > 9) return fail(c, QK_EINVAL, "nfields must be in [1, 9]");
+  if (first < 0 || nfields < 1 || first + nfields > 9)
+    return fail(c, QK_EINVAL, "fields first .. first+nfields-1 must lie in [0, 9)");
   int rc = check_fields(c, fields, nfields, "fields");
   if (rc) return rc;
   const int *ch0 = pack ? c->send_chunk0.data() : c->recv_chunk0.data();
@@ -884,19 +1122,19 @@ static int halo(qk_ctx *c, int pack, int32_t peer, void *const *fields, int32_t 
   if (!buf) return fail(c, QK_EINVAL, "buf is NULL");
   QK_CUDA(c, launch_halo(c->fp32, pack, pack ? c->d_send : c->d_recv,
                          (pack ? c->d_send_chunks : c->d_recv_chunks) + ch0[peer],
-                         ch0[peer + 1] - ch0[peer], fields, nfields, buf, n,
-                         (cudaStream_t)stream));
+                         ch0[peer + 1] - ch0[peer], fields, nfields, first, buf, n,
+                         DtSrc{nullptr, 0.0, 0, -1}, (cudaStream_t)stream));
   return QK_OK;
 }
 
-int qk_halo_pack(qk_ctx *c, int32_t peer, void *const *fields, int32_t nfields, void *buf,
-                 void *stream) {
-  return halo(c, 1, peer, fields, nfields, buf, stream);
+int qk_halo_pack(qk_ctx *c, int32_t peer, void *const *fields, int32_t first, int32_t nfields,
+                 void *buf, void *stream) {
+  return halo(c, 1, peer, fields, first, nfields, buf, stream);
 }
 
-int qk_halo_unpack(qk_ctx *c, int32_t peer, void *const *fields, int32_t nfields,
+int qk_halo_unpack(qk_ctx *c, int32_t peer, void *const *fields, int32_t first, int32_t nfields,
                    const void *buf, void *stream) {
-  return halo(c, 0, peer, fields, nfields, const_cast<void *>(buf), stream);
+  return halo(c, 0, peer, fields, first, nfields, const_cast<void *>(buf), stream);
 }
 
 int qk_signal_speed(qk_ctx *c, void *const hydro[5], double *smax, void *stream) {

@@ -34,7 +34,9 @@ __device__ __forceinline__ double load_d(const T *p, long long e) { return (doub
 // Newton-Raphson on (E_g, E_r) for one cell (Sec. 2.2.3, eqs. delta_er and
 // delta_eg).  R = dt rho kappa_P chat (a_r T^4 - E_r) (the '4 pi B' of the
 // paper read as chat a_r T^4), F_G = (E_g - E_g0) + (c/chat) R,
-// F_R = (E_r - E_r0) - R; convergence |F_G/E_tot| < eps and
+// F_R = (E_r - E_r0) - R; with a radiation source S the callers pass
+// E_r0 + S for E_r0 (F_R = (E_r - E_r0) - (R + S); the Jacobian does not
+// change); convergence |F_G/E_tot| < eps and
 // |(c/chat) F_R / E_tot| < eps, E_tot = E_g0 + (c/chat) E_r0; the update of
 // the iterate that passes is applied, then the loop stops.  The 2x2
 // elimination of eqs. delta_er / delta_eg is evaluated with one division:
@@ -154,7 +156,8 @@ __device__ __forceinline__ int newton_refine(const qk_params &p, double Eg0, dou
 // accumulated in FP64 before the final rounding.
 __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_params p,
                                                               F5<float> U, F4<float> R,
-                                                              DtSrc dts, Status *st) {
+                                                              const float *src, DtSrc dts,
+                                                              Status *st) {
   if (skip_substep(dts)) return;
   const double dt = dt_of(dts);
   const double cr = p.c / p.chat;
@@ -180,16 +183,18 @@ __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_para
     const float rinv = qrcp(rho);
     const double inv_rcv = (double)(rinv * (float)inv_cv);
     const double inv_Etot = (double)qrcp((float)(Eg0 + cr * Er0));
+    // radiation source S = dt (chat/c) j, carried in the residual's E_r0
+    const double Er0S = src ? Er0 + dt * (p.chat / p.c) * (double)src[e] : Er0;
     // FP32 warm start
-    float Egf = (float)Eg0, Erf = Er0f;
-    const int itf = newton_exchange<float>(p, (float)Eg0, Er0f, (float)k, (float)cr,
+    float Egf = (float)Eg0, Erf = (float)Er0S;
+    const int itf = newton_exchange<float>(p, (float)Eg0, (float)Er0S, (float)k, (float)cr,
                                            (float)inv_Etot, (float)inv_rcv, 1e-6f, 12, Egf, Erf);
     double Eg = Eg0, Er = Er0;
     if (itf > 0 && Egf > 0.0f && Erf > 0.0f && isfinite(Egf) && isfinite(Erf)) {
       Eg = Egf;
       Er = Erf;
     }
-    const int it = newton_refine(p, Eg0, Er0, k, cr, inv_Etot, inv_rcv, Eg, Er);
+    const int it = newton_refine(p, Eg0, Er0S, k, cr, inv_Etot, inv_rcv, Eg, Er);
     if (it < 0) {
       my_flags |= 1u << QK_ENOCONV;
       my_bad = min(my_bad, (unsigned long long)e);
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_para
 
 template <typename T>
 __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, F5<T> U, F4<T> R,
-                                                        DtSrc dts, Status *st) {
+                                                        const T *src, DtSrc dts, Status *st) {
   if (skip_substep(dts)) return;
   const double dt = dt_of(dts);
   const double chat = p.chat, c = p.c;
@@ -254,9 +259,11 @@ __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, 
     const double inv_Etot = 1.0 / (Eg0 + cr * Er0);
     const double k = dt * rho * kP * chat;
     const double inv_rcv = inv_rho * inv_cv;
+    // radiation source S = dt (chat/c) j, carried in the residual's E_r0
+    const double Er0S = src ? Er0 + dt * rc * load_d(src, e) : Er0;
     double Eg = Eg0, Er = Er0;
     int it;
-    it = newton_exchange<double>(p, Eg0, Er0, k, cr, inv_Etot, inv_rcv, p.eps_newton,
+    it = newton_exchange<double>(p, Eg0, Er0S, k, cr, inv_Etot, inv_rcv, p.eps_newton,
                                  p.max_iter, Eg, Er);
     if (it < 0) {
       my_flags |= 1u << QK_ENOCONV;
@@ -289,7 +296,8 @@ __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, 
 }
 
 cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, void *const *U,
-                            void *const *R, DtSrc dt, Status *st, cudaStream_t s) {
+                            void *const *R, const void *src, DtSrc dt, Status *st,
+                            cudaStream_t s) {
   int nsm = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -300,12 +308,12 @@ cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, voi
     F5<float> u; F4<float> r;
     for (int q = 0; q < 5; ++q) u.f[q] = (float *)U[q];
     for (int q = 0; q < 4; ++q) r.f[q] = (float *)R[q];
-    exchange_kernel_mixed<<<grid, 256, 0, s>>>(g, p, u, r, dt, st);
+    exchange_kernel_mixed<<<grid, 256, 0, s>>>(g, p, u, r, (const float *)src, dt, st);
   } else {
     F5<double> u; F4<double> r;
     for (int q = 0; q < 5; ++q) u.f[q] = (double *)U[q];
     for (int q = 0; q < 4; ++q) r.f[q] = (double *)R[q];
-    exchange_kernel<double><<<grid, 256, 0, s>>>(g, p, u, r, dt, st);
+    exchange_kernel<double><<<grid, 256, 0, s>>>(g, p, u, r, (const double *)src, dt, st);
   }
   return cudaGetLastError();
 }
@@ -411,11 +419,21 @@ cudaError_t launch_timestep(const qk_params &p, StepInfo *si, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ ghost fill ---
-// One CTA per chunk of CHUNK_CELLS cells of one copy region; every field is
-// copied for each cell (the same addresses for all fields).
+// Every ghost cell of every patch receives the value of the cell
+// its copy descriptor names (periodic image, mirror image or nearest interior
+// cell), with the vector components along reflecting axes negated.  One CTA
+// per chunk of at most CHUNK_CELLS destination cells of one descriptor; the
+// same source addresses serve all fields.  Fields are the state fields
+// first .. first+nf-1 (their identity decides the sign flips).
+template <typename T>
+__device__ __forceinline__ T *field_ptr(const F5<T> &fa, const F4<T> &fb, int f) {
+  return f < 5 ? fa.f[f] : fb.f[f - 5];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) ghost_fill_kernel(const Copy *copies, const Chunk *chunks,
-                                                         F5<T> fa, F4<T> fb, int nf, DtSrc pred) {
+                                                         F5<T> fa, F4<T> fb, int nf, int first,
+                                                         DtSrc pred) {
   if (skip_substep(pred)) return;
   const Chunk ch = chunks[blockIdx.x];
   const Copy cp = copies[ch.copy];
@@ -427,44 +445,48 @@ __global__ void __launch_bounds__(256) ghost_fill_kernel(const Copy *copies, con
     const int y = r % cp.ey;
     const int z = r / cp.ey;
     const long long d = cp.dst + ((long long)z * cp.dsy + y) * cp.dsx + x;
-    const long long s = cp.src + ((long long)z * cp.ssy + y) * cp.ssx + x;
+    const long long s = cp.src + z * cp.sz + y * cp.sy + x * cp.sx;
 #pragma unroll
-    for (int f = 0; f < 5; ++f)
-      if (f < nf) fa.f[f][d] = fa.f[f][s];
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-      if (f + 5 < nf) fb.f[f][d] = fb.f[f][s];
+    for (int f = 0; f < 9; ++f) {
+      if (f >= nf) break;
+      T *fld = field_ptr(fa, fb, f);
+      const int ax = field_axis(first + f);
+      const T v = fld[s];
+      fld[d] = (ax >= 0 && ((cp.flip >> ax) & 1)) ? -v : v;
+    }
   }
 }
 
 cudaError_t launch_ghost_fill(int fp32, const Copy *copies, const Chunk *chunks, int nchunks,
-                              void *const *fields, int nf, DtSrc pred, cudaStream_t s) {
+                              void *const *fields, int nf, int first, DtSrc pred, cudaStream_t s) {
   if (nchunks < 1 || nf < 1) return cudaSuccess;
   if (fp32) {
     F5<float> a{}; F4<float> b{};
     for (int q = 0; q < nf && q < 5; ++q) a.f[q] = (float *)fields[q];
     for (int q = 5; q < nf; ++q) b.f[q - 5] = (float *)fields[q];
-    ghost_fill_kernel<float><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, pred);
+    ghost_fill_kernel<float><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, first, pred);
   } else {
     F5<double> a{}; F4<double> b{};
     for (int q = 0; q < nf && q < 5; ++q) a.f[q] = (double *)fields[q];
     for (int q = 5; q < nf; ++q) b.f[q - 5] = (double *)fields[q];
-    ghost_fill_kernel<double><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, pred);
+    ghost_fill_kernel<double><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, first, pred);
   }
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------- halo pack ---
-// Cross-rank part of the ghost fill.  The sending rank gathers, for each
-// region a peer needs, the interior cells of its own patch into a contiguous
-// buffer (x fastest, regions in the agreed order, one block of `npeer` cells
-// per field); the receiving rank scatters the same buffer into the ghost
-// regions.  A descriptor's strided side is (src, ssx, ssy) when packing and
-// (dst, dsx, dsy) when unpacking; its other side is the buffer position.
+// Cross-rank part of the ghost fill, and the Dirichlet boundary store.  The
+// packing side gathers, for each region, the source cells (the descriptor's
+// strided source, sign flips applied) into a contiguous buffer (x fastest,
+// regions in the agreed order, one block of `nbuf` cells per field); the
+// unpacking side scatters the same buffer into the destination regions.  A
+// descriptor's other side is its position in the buffer (`dst` when packing,
+// `src` when unpacking).
 template <typename T, bool PACK>
 __global__ void __launch_bounds__(256) halo_kernel(const Copy *copies, const Chunk *chunks,
-                                                   F5<T> fa, F4<T> fb, int nf, T *buf,
-                                                   long long npeer) {
+                                                   F5<T> fa, F4<T> fb, int nf, int first, T *buf,
+                                                   long long nbuf, DtSrc pred) {
+  if (skip_substep(pred)) return;
   const Chunk ch = chunks[blockIdx.x];
   const Copy cp = copies[ch.copy];
   const int ncell = cp.ex * cp.ey * cp.ez;
@@ -476,7 +498,7 @@ __global__ void __launch_bounds__(256) halo_kernel(const Copy *copies, const Chu
     const int z = r / cp.ey;
     long long e, q;  // field element, buffer position
     if (PACK) {
-      e = cp.src + ((long long)z * cp.ssy + y) * cp.ssx + x;
+      e = cp.src + z * cp.sz + y * cp.sy + x * cp.sx;
       q = cp.dst + l;
     } else {
       e = cp.dst + ((long long)z * cp.dsy + y) * cp.dsx + x;
@@ -485,29 +507,38 @@ __global__ void __launch_bounds__(256) halo_kernel(const Copy *copies, const Chu
 #pragma unroll
     for (int f = 0; f < 9; ++f) {
       if (f >= nf) break;
-      T *fld = f < 5 ? fa.f[f] : fb.f[f - 5];
-      if (PACK) buf[f * npeer + q] = fld[e];
-      else fld[e] = buf[f * npeer + q];
+      T *fld = field_ptr(fa, fb, f);
+      if (PACK) {
+        const int ax = field_axis(first + f);
+        const T v = fld[e];
+        buf[f * nbuf + q] = (ax >= 0 && ((cp.flip >> ax) & 1)) ? -v : v;
+      } else {
+        fld[e] = buf[f * nbuf + q];
+      }
     }
   }
 }
 
 cudaError_t launch_halo(int fp32, int pack, const Copy *copies, const Chunk *chunks, int nchunks,
-                        void *const *fields, int nf, void *buf, long long npeer,
-                        cudaStream_t s) {
+                        void *const *fields, int nf, int first, void *buf, long long nbuf,
+                        DtSrc pred, cudaStream_t s) {
   if (nchunks < 1 || nf < 1) return cudaSuccess;
   if (fp32) {
     F5<float> a{}; F4<float> b{};
     for (int q = 0; q < nf && q < 5; ++q) a.f[q] = (float *)fields[q];
     for (int q = 5; q < nf; ++q) b.f[q - 5] = (float *)fields[q];
-    if (pack) halo_kernel<float, true><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, (float *)buf, npeer);
-    else halo_kernel<float, false><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, (float *)buf, npeer);
+    if (pack)
+      halo_kernel<float, true><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, first, (float *)buf, nbuf, pred);
+    else
+      halo_kernel<float, false><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, first, (float *)buf, nbuf, pred);
   } else {
     F5<double> a{}; F4<double> b{};
     for (int q = 0; q < nf && q < 5; ++q) a.f[q] = (double *)fields[q];
     for (int q = 5; q < nf; ++q) b.f[q - 5] = (double *)fields[q];
-    if (pack) halo_kernel<double, true><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, (double *)buf, npeer);
-    else halo_kernel<double, false><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, (double *)buf, npeer);
+    if (pack)
+      halo_kernel<double, true><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, first, (double *)buf, nbuf, pred);
+    else
+      halo_kernel<double, false><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, first, (double *)buf, nbuf, pred);
   }
   return cudaGetLastError();
 }

@@ -285,16 +285,42 @@ __device__ __forceinline__ void levermore_ab_f2(T f2, T &a, T &b) {
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void levermore_ab(T fx, T fy, T fz, T &a, T &b) {
-  levermore_ab_f2<T>((fx * fx + fy * fy) + fz * fz, a, b);
+// The same coefficients for every closure of Sec. 2.2.2, selected at compile
+// time (CL = QK_CLOSURE_*):
+//   Minerbo, chi = 1/3 + (2/15) g, g = 3 fc^2 - fc^3 + 3 fc^4 = fc^2 (3 - fc + 3 fc^2):
+//     a = 1/3 - g/15,  b = (3 chi - 1)/(2 |f|^2) = g / (5 |f|^2) = (3 - fc + 3 fc^2)/5
+//     for |f| <= 1 (fc^2 = |f|^2); chi = 1 beyond: a = 0, b = 1/|f|^2;
+//   Eddington, chi = 1/3: a = 1/3, b = 0 (T = I/3 for every flux).
+template <typename T, int CL>
+__device__ __forceinline__ void closure_ab_f2(T f2, T &a, T &b) {
+  if constexpr (CL == QK_CLOSURE_EDDINGTON) {
+    a = T(1) / T(3);
+    b = T(0);
+  } else if constexpr (CL == QK_CLOSURE_MINERBO) {
+    if (nn_gt(f2, T(1))) {
+      a = T(0);
+      b = qrcp(f2);
+    } else {
+      const T fc = qsqrt(f2);
+      const T h = (T(3) - fc) + T(3) * f2;
+      a = T(1) / T(3) - (f2 * h) * (T(1) / T(15));
+      b = h * T(0.2);
+    }
+  } else {
+    levermore_ab_f2<T>(f2, a, b);
+  }
+}
+
+template <typename T, int CL>
+__device__ __forceinline__ void closure_ab(T fx, T fy, T fz, T &a, T &b) {
+  closure_ab_f2<T, CL>((fx * fx + fy * fy) + fz * fz, a, b);
 }
 
 // Column D of the Eddington tensor.
-template <typename T, int D>
+template <typename T, int D, int CL>
 __device__ __forceinline__ void eddington_col(T fx, T fy, T fz, T &Tx, T &Ty, T &Tz) {
   T a, b;
-  levermore_ab<T>(fx, fy, fz, a, b);
+  closure_ab<T, CL>(fx, fy, fz, a, b);
   const T fD = D == 0 ? fx : (D == 1 ? fy : fz);
   Tx = b * fx * fD + (D == 0 ? a : T(0));
   Ty = b * fy * fD + (D == 1 ? a : T(0));
@@ -302,10 +328,10 @@ __device__ __forceinline__ void eddington_col(T fx, T fy, T fz, T &Tx, T &Ty, T 
 }
 
 // Diagonal element T_DD only (for the HLL wavespeed).
-template <typename T, int D>
+template <typename T, int D, int CL>
 __device__ __forceinline__ T eddington_diag(T fx, T fy, T fz) {
   T Tx, Ty, Tz;
-  eddington_col<T, D>(fx, fy, fz, Tx, Ty, Tz);
+  eddington_col<T, D, CL>(fx, fy, fz, Tx, Ty, Tz);
   return D == 0 ? Tx : (D == 1 ? Ty : Tz);
 }
 

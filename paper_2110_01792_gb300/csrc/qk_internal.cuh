@@ -47,11 +47,19 @@ struct Tile {
 // One rectangular ghost region copied from an interior region (possibly of
 // another patch, possibly a periodic image).  Element offsets are absolute.
 struct Copy {
-  long long dst, src;
+  long long dst, src;  // first destination / source element
   int ex, ey, ez;      // extents
   int dsx, dsy;        // destination row / plane strides (elements / rows)
-  int ssx, ssy;        // source row / plane strides
+  int flip;            // bit d: negate the d-components of vectors (reflecting face)
+  long long sx, sy, sz;  // source element step per x, y, z step: +-1 / +-row / +-plane,
+                         // negative across a reflecting face, 0 across an outflow face
 };
+
+// Vector axis of state field `fid` (0-4 rho, m_x, m_y, m_z, E; 5-8 E_r, F_x,
+// F_y, F_z), -1 for scalars.
+__host__ __device__ __forceinline__ int field_axis(int fid) {
+  return (fid >= 1 && fid <= 3) ? fid - 1 : ((fid >= 6 && fid <= 8) ? fid - 6 : -1);
+}
 
 struct Chunk {
   int copy;            // index into the copy list
@@ -211,15 +219,16 @@ cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_pa
                              void *const *R0, void *const *R1, void *const *Rout,
                              const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s);
 cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, void *const *U,
-                            void *const *R, DtSrc dt, Status *st, cudaStream_t s);
+                            void *const *R, const void *src, DtSrc dt, Status *st,
+                            cudaStream_t s);
 cudaError_t launch_max_speed(int fp32, const Geometry &g, const qk_params &p,
                              void *const *U, StepInfo *si, cudaStream_t s);
 cudaError_t launch_halo(int fp32, int pack, const Copy *copies, const Chunk *chunks, int nchunks,
-                        void *const *fields, int nf, void *buf, long long npeer,
-                        cudaStream_t s);
+                        void *const *fields, int nf, int first, void *buf, long long nbuf,
+                        DtSrc pred, cudaStream_t s);
 cudaError_t launch_timestep(const qk_params &p, StepInfo *si, cudaStream_t s);
 cudaError_t launch_ghost_fill(int fp32, const Copy *copies, const Chunk *chunks, int nchunks,
-                              void *const *fields, int nf, DtSrc pred, cudaStream_t s);
+                              void *const *fields, int nf, int first, DtSrc pred, cudaStream_t s);
 cudaError_t launch_sums(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                         void *const *R, double *partials, int nblocks, double *out,
                         cudaStream_t s);

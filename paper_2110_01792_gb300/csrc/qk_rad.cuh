@@ -1,0 +1,306 @@
+// qk_rad.cuh -- fused radiation RK2-SSP stage (Sec. 2.2.2 of arXiv:2110.01792)
+// for sm_103a: PPM reconstruction of E_r and f = F/(c E_r), first-order
+// fallback at faces where a state has |f| > 1, the M1 closure
+// (eq. M1_closure; Levermore, Minerbo or Eddington, a template parameter), HLL flux with wavespeeds from the cell-average Eddington
+// factors, optical-depth correction, RSLA fluxes (eqs. rad_energy, rad_flux),
+// divergence and RK combination.  Same tile scheme as the hydro stage.
+#pragma once
+#include "qk_device.cuh"
+
+namespace qk {
+
+// FP64 keeps the cell-average closure coefficients (a, b) of every slot next
+// to a face (computed once per cell, shared by the three directions); FP32
+// recomputes sqrt(T_DD) per line position instead, which is cheap on the FP32
+// pipe and keeps three CTAs per SM.
+template <typename T> struct RadSmem {
+  static constexpr bool kAB = sizeof(T) == 8;
+  T prim[4][NCROSS];               // E_r, f_x, f_y, f_z of the tile and its cross halo
+  T rk[NCROSS];                    // rho kappa_R of the cell
+  T ab[2][kAB ? NCROSS : 1];       // FP64: Levermore a, b of the cell-average state
+  T rec[8][NREC];                  // qL, qR of each reconstructed variable
+  T sq[kAB ? 1 : NREC];            // FP32: sqrt(T_DD) of the cell average per position
+  T flux[4][NFLUX];
+};
+
+template <typename T> __device__ __forceinline__ T kappa_of(const qk_params &p, double k, T rho) {
+  return p.kappa_mode == QK_KAPPA_RHO ? (T)k * rho : (T)k;
+}
+
+// Stage one cross slot: E_r, f = F / (c E_r) (one reciprocal), rho kappa_R,
+// and in FP64 the closure coefficients of the cell average when the slot is
+// adjacent to a face of the tile (within one cell of the valid region).
+template <typename T, int CL>
+__device__ __forceinline__ void load_slot(RadSmem<T> &sm, int s, const T u[4], T c, T r,
+                                          const qk_params &p, int i, int j, int k,
+                                          const int v[3]) {
+  const T inv = qrcp(c * u[0]);
+  const T fx = u[1] * inv, fy = u[2] * inv, fz = u[3] * inv;
+  sm.prim[0][s] = u[0];
+  sm.prim[1][s] = fx;
+  sm.prim[2][s] = fy;
+  sm.prim[3][s] = fz;
+  sm.rk[s] = r * kappa_of<T>(p, p.kappa_R, r);
+  if constexpr (RadSmem<T>::kAB) {
+    const bool near = i >= -1 && j >= -1 && k >= -1 && i <= v[0] && j <= v[1] && k <= v[2];
+    if (near) {
+      T a, b;
+      closure_ab<T, CL>(fx, fy, fz, a, b);
+      sm.ab[0][s] = a;
+      sm.ab[1][s] = b;
+    }
+  }
+}
+
+// State vector (E, F) and flux along D of a radiation state (E_r, f) with
+// |f|^2 = f2 already known: flux_D = ((chat/c) F_D, c chat E T_xD, c chat E
+// T_yD, c chat E T_zD) (eqs. rad_energy, rad_flux; T from the closure CL).
+template <typename T, int D, int CL>
+__device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T f2, T c, T chat_c, T ccc,
+                                            T U[4], T F[4]) {
+  T a, b;
+  closure_ab_f2<T, CL>(f2, a, b);
+  const T fD = D == 0 ? fx : (D == 1 ? fy : fz);
+  const T cE = c * E;
+  U[0] = E;
+  U[1] = cE * fx;
+  U[2] = cE * fy;
+  U[3] = cE * fz;
+  F[0] = chat_c * U[1 + D];
+  const T cEb = ccc * E;                 // c chat E
+  const T bfD = b * fD;
+  F[1] = cEb * (bfD * fx + (D == 0 ? a : T(0)));
+  F[2] = cEb * (bfD * fy + (D == 1 ? a : T(0)));
+  F[3] = cEb * (bfD * fz + (D == 2 ? a : T(0)));
+}
+
+template <typename T, int D, int NT, int NOWN, int CL>
+__device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx, T dx, T c,
+                                        T chat, int tau_corr, int rk, T (&acc)[NOWN][4]) {
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  const T ccc = c * chat;
+  const T chat_c = chat / c;
+  for (int it = threadIdx.x; it < NREC; it += NT) {
+    int pos, cc[3];
+    item_cell<D>(it, NPOS, pos, cc[0], cc[1], cc[2]);
+    if (cc[A] >= v[A] || cc[B] >= v[B] || cc[D] > v[D]) continue;
+    int s[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+      int x[3] = {cc[0], cc[1], cc[2]};
+      x[D] += o - 2;
+      s[o] = cross_slot(x[0], x[1], x[2]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      T qL, qR;
+      recon<T>(rk, sm.prim[q][s[0]], sm.prim[q][s[1]], sm.prim[q][s[2]], sm.prim[q][s[3]],
+               sm.prim[q][s[4]], qL, qR);
+      sm.rec[2 * q][it] = qL;
+      sm.rec[2 * q + 1][it] = qR;
+    }
+    if constexpr (!RadSmem<T>::kAB)
+      sm.sq[it] = qsqrt(eddington_diag<T, D, CL>(sm.prim[1][s[2]], sm.prim[2][s[2]], sm.prim[3][s[2]]));
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < NFLUX; it += NT) {
+    int f, cc[3];
+    item_cell<D>(it, NFACE, f, cc[0], cc[1], cc[2]);
+    if (cc[A] >= v[A] || cc[B] >= v[B] || f > v[D]) continue;
+    const int il = item_index<D>(f, cc[0], cc[1], cc[2], NPOS);
+    const int ir = item_index<D>(f + 1, cc[0], cc[1], cc[2], NPOS);
+    T wL[4], wR[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      wL[q] = sm.rec[2 * q + 1][il];
+      wR[q] = sm.rec[2 * q][ir];
+    }
+    T fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
+    T fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
+    int xa[3] = {cc[0], cc[1], cc[2]}, xb[3] = {cc[0], cc[1], cc[2]};
+    xa[D] = f - 1;
+    xb[D] = f;
+    const int sa = cross_slot(xa[0], xa[1], xa[2]);
+    const int sb = cross_slot(xb[0], xb[1], xb[2]);
+    if (nn_gt(fL2, T(1)) || nn_gt(fR2, T(1))) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        wL[q] = sm.prim[q][sa];
+        wR[q] = sm.prim[q][sb];
+      }
+      fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
+      fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
+    }
+    T UL[4], FL[4], UR[4], FR[4];
+    rad_flux_of<T, D, CL>(wL[0], wL[1], wL[2], wL[3], fL2, c, chat_c, ccc, UL, FL);
+    rad_flux_of<T, D, CL>(wR[0], wR[1], wR[2], wR[3], fR2, c, chat_c, ccc, UR, FR);
+    T S;
+    if constexpr (RadSmem<T>::kAB) {
+      // sqrt is monotone and correctly rounded: sqrt(max) == max(sqrt)
+      const T fa = sm.prim[1 + D][sa], fb = sm.prim[1 + D][sb];
+      const T Ta = sm.ab[0][sa] + sm.ab[1][sa] * fa * fa;
+      const T Tb = sm.ab[0][sb] + sm.ab[1][sb] * fb * fb;
+      S = chat * qsqrt(nn_max(Ta, Tb));
+    } else {
+      S = chat * max(sm.sq[il], sm.sq[ir]);
+    }
+    T eps = T(1);
+    if (tau_corr) {
+      const T tau = dx * T(0.5) * (sm.rk[sa] + sm.rk[sb]);
+      if (nn_gt(tau, T(1))) eps = qrcp(tau);
+    }
+    T out[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = T(0.5) * (FL[q] + FR[q]) - T(0.5) * S * eps * (UR[q] - UL[q]);
+    if (nn_gt(T(1), eps) && nn_gt(fabs(out[0]), chat * nn_max(UL[0], UR[0]))) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) out[q] = T(0.5) * (FL[q] + FR[q]) - T(0.5) * S * (UR[q] - UL[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sm.flux[q][it] = out[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < NOWN; ++m) {
+    int s = threadIdx.x + m * NT;
+    int cc[3] = {s % TS, (s / TS) % TS, s / (TS * TS)};
+    if (cc[0] >= v[0] || cc[1] >= v[1] || cc[2] >= v[2]) continue;
+    int lo = item_index<D>(cc[D], cc[0], cc[1], cc[2], NFACE);
+    int hi = item_index<D>(cc[D] + 1, cc[0], cc[1], cc[2], NFACE);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      T dv = (sm.flux[q][hi] - sm.flux[q][lo]) * inv_dx;
+      acc[m][q] = (D == 0) ? dv : acc[m][q] + dv;
+    }
+  }
+}
+
+template <typename T, int STAGE, int NT, int CL>
+__global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, F4<T> R0,
+                                                       F4<T> R1, F4<T> Ro, const T *rho,
+                                                       DtSrc dts, int sched) {
+  if (skip_substep(dts)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RadSmem<T> &sm = *reinterpret_cast<RadSmem<T> *>(smem_raw);
+  constexpr int NOWN = NCORE / NT;
+  const T dt = (T)dt_of(dts);
+  const T c = (T)p.c, chat = (T)p.chat;
+  const T inv_dx[3] = {(T)(1.0 / p.dx[0]), (T)(1.0 / p.dx[1]), (T)(1.0 / p.dx[2])};
+  const T dx[3] = {(T)p.dx[0], (T)p.dx[1], (T)p.dx[2]};
+  const F4<T> src = STAGE == 1 ? R0 : R1;
+
+  // tile schedule: strided over the grid (0) or one contiguous run of tiles
+  // per CTA (1, neighbouring tiles in sequence on one SM)
+  int t0 = blockIdx.x, t1 = g.ntiles, tstep = gridDim.x;
+  if (sched) {
+    const int per = (g.ntiles + gridDim.x - 1) / gridDim.x;
+    t0 = blockIdx.x * per;
+    t1 = min(g.ntiles, t0 + per);
+    tstep = 1;
+  }
+  for (int t = t0; t < t1; t += tstep) {
+    const Tile tl = g.tiles[t];
+    const DevBox b = g.boxes[tl.box];
+    const int v[3] = {min(TS, b.n[0] - tl.x0), min(TS, b.n[1] - tl.y0), min(TS, b.n[2] - tl.z0)};
+    T own[NOWN][4];
+#pragma unroll
+    for (int m = 0; m < NOWN; ++m) {
+      int s = threadIdx.x + m * NT;
+      int i = s % TS, j = (s / TS) % TS, k = s / (TS * TS);
+      if (!slot_needed(i, j, k, v)) continue;
+      long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
+      T u[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) u[q] = src.f[q][e];
+      load_slot<T, CL>(sm, s, u, c, rho[e], p, i, j, k, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) own[m][q] = u[q];
+    }
+    for (int s = NCORE + threadIdx.x; s < NCROSS; s += NT) {
+      int i, j, k;
+      slot_cell(s, i, j, k);
+      if (!slot_needed(i, j, k, v)) continue;
+      long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
+      T u[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) u[q] = src.f[q][e];
+      load_slot<T, CL>(sm, s, u, c, rho[e], p, i, j, k, v);
+    }
+    __syncthreads();
+    T acc[NOWN][4];
+    rad_dir<T, 0, NT, NOWN, CL>(sm, v, inv_dx[0], dx[0], c, chat, p.tau_correction, p.recon, acc);
+    rad_dir<T, 1, NT, NOWN, CL>(sm, v, inv_dx[1], dx[1], c, chat, p.tau_correction, p.recon, acc);
+    rad_dir<T, 2, NT, NOWN, CL>(sm, v, inv_dx[2], dx[2], c, chat, p.tau_correction, p.recon, acc);
+#pragma unroll
+    for (int m = 0; m < NOWN; ++m) {
+      int s = threadIdx.x + m * NT;
+      int i = s % TS, j = (s / TS) % TS, k = s / (TS * TS);
+      if (i >= v[0] || j >= v[1] || k >= v[2]) continue;
+      long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        T L = -acc[m][q];
+        if (STAGE == 1) {
+          Ro.f[q][e] = own[m][q] + dt * L;
+        } else {
+          T u0 = R0.f[q][e];
+          Ro.f[q][e] = T(0.5) * u0 + T(0.5) * (own[m][q] + dt * L);
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int STAGE, int NT, int CL>
+static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const *R0,
+                              void *const *R1, void *const *Ro, const void *rho, DtSrc dt,
+                              int grid, int sched, cudaStream_t s) {
+  F4<T> a, b, c;
+  for (int q = 0; q < 4; ++q) {
+    a.f[q] = (T *)R0[q];
+    b.f[q] = R1 ? (T *)R1[q] : nullptr;
+    c.f[q] = (T *)Ro[q];
+  }
+  int smem = (int)sizeof(RadSmem<T>);
+  auto kern = rad_stage_kernel<T, STAGE, NT, CL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (grid <= 0) {
+    int per_sm = 0, nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    grid = nsm * (per_sm > 0 ? per_sm : 1);
+  }
+  if (grid > g.ntiles) grid = g.ntiles;
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, (const T *)rho, dt, sched);
+  return cudaGetLastError();
+}
+
+template <typename T, int STAGE, int CL>
+static cudaError_t launch_nt(const Geometry &g, const qk_params &p, void *const *R0,
+                             void *const *R1, void *const *Ro, const void *rho, DtSrc dt,
+                             int grid, int cfg, cudaStream_t s) {
+  const int sched = cfg_sched(cfg);
+  switch (cfg_threads(cfg)) {
+    case 128: return launch_one<T, STAGE, 128, CL>(g, p, R0, R1, Ro, rho, dt, grid, sched, s);
+    case 512: return launch_one<T, STAGE, 512, CL>(g, p, R0, R1, Ro, rho, dt, grid, sched, s);
+    default: return launch_one<T, STAGE, 256, CL>(g, p, R0, R1, Ro, rho, dt, grid, sched, s);
+  }
+}
+
+// All stage kernels of one closure (instantiated in qk_rad.cu and
+// qk_rad_closures.cu, which nvcc compiles in parallel).
+template <int CL>
+cudaError_t launch_rad_closure(int fp32, int stage, const Geometry &g, const qk_params &p,
+                               void *const *R0, void *const *R1, void *const *Rout,
+                               const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s) {
+  if (fp32)
+    return stage == 1 ? launch_nt<float, 1, CL>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s)
+                      : launch_nt<float, 2, CL>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s);
+  return stage == 1 ? launch_nt<double, 1, CL>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s)
+                    : launch_nt<double, 2, CL>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s);
+}
+
+}  // namespace qk

@@ -37,8 +37,13 @@ class Params(C.Structure):
         ("eps_newton", C.c_double), ("dx", C.c_double * 3),
         ("kappa_mode", C.c_int32), ("eos", C.c_int32), ("max_iter", C.c_int32),
         ("nsub_max", C.c_int32), ("tau_correction", C.c_int32), ("hydro_only", C.c_int32),
-        ("recon", C.c_int32), ("flattening", C.c_int32),
+        ("recon", C.c_int32), ("flattening", C.c_int32), ("closure", C.c_int32),
+        ("bc_lo", C.c_int32 * 3), ("bc_hi", C.c_int32 * 3),
     ]
+
+
+CLOSURE_LEVERMORE, CLOSURE_MINERBO, CLOSURE_EDDINGTON = 0, 1, 2
+BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_DIRICHLET = 0, 1, 2, 3
 
 
 class Box(C.Structure):
@@ -81,11 +86,16 @@ def lib():
     L.qk_status.argtypes = [vp, P(C.c_uint32), P(i64), P(i32), i32, vp]
     L.qk_init_shard.argtypes = [P(vp), P(Params), P(Box), i32, P(i32), i32, i32, P(i32), i32, i32]
     L.qk_halo_info.argtypes = [vp, i32, P(i64), P(i64), P(i32)]
-    L.qk_halo_pack.argtypes = [vp, i32, P(vp), i32, vp, vp]
-    L.qk_halo_unpack.argtypes = [vp, i32, P(vp), i32, vp, vp]
+    L.qk_halo_pack.argtypes = [vp, i32, P(vp), i32, i32, vp, vp]
+    L.qk_halo_unpack.argtypes = [vp, i32, P(vp), i32, i32, vp, vp]
+    L.qk_fill_ghosts_range.argtypes = [vp, P(vp), i32, i32, vp]
+    L.qk_fill_plan.argtypes = [P(Params), P(Box), i32, P(i32), i32, P(i64), i64, P(i64), P(i64)]
+    L.qk_set_dirichlet.argtypes = [vp, P(vp), P(vp), vp]
+    L.qk_set_source.argtypes = [vp, vp]
     L.qk_signal_speed.argtypes = [vp, P(vp), P(dbl), vp]
     L.qk_set_timestep.argtypes = [vp, dbl, P(dbl), vp]
-    for f in ("qk_init_shard", "qk_halo_info", "qk_halo_pack", "qk_halo_unpack",
+    for f in ("qk_fill_plan", "qk_fill_ghosts_range", "qk_set_dirichlet", "qk_set_source",
+              "qk_init_shard", "qk_halo_info", "qk_halo_pack", "qk_halo_unpack",
               "qk_signal_speed", "qk_set_timestep", "qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_autotune",
               "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
               "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
@@ -120,6 +130,12 @@ def make_params(**kw) -> Params:
     p.hydro_only = int(kw.get("hydro_only", 0))
     p.recon = int(kw.get("recon", 0))
     p.flattening = int(kw.get("flattening", 0))
+    p.closure = int(kw.get("closure", 0))
+    lo = kw.get("bc_lo", (0, 0, 0))
+    hi = kw.get("bc_hi", (0, 0, 0))
+    for i in range(3):
+        p.bc_lo[i] = int(lo[i])
+        p.bc_hi[i] = int(hi[i])
     return p
 
 
@@ -137,6 +153,39 @@ def _ptrs(fields, n):
     return (C.c_void_p * n)(*[int(f.data_ptr()) for f in fields])
 
 
+def _boxes(layout):
+    nb = layout.nbox
+    boxes = (Box * nb)()
+    for b in range(nb):
+        for d in range(3):
+            boxes[b].lo[d] = int(layout.lo[b][d])
+            boxes[b].n[d] = int(layout.n[b][d])
+        boxes[b].offset = int(layout.off[b])
+    return boxes
+
+
+def fill_plan(layout, params: dict):
+    """The ghost-fill descriptors of a patch set (host only, no GPU): an
+    (ncopies, 11) int64 array of copies (dst, src, ex, ey, ez, dsx, dsy, flip,
+    sx, sy, sz) and an (nregions, 7) array of Dirichlet regions (dst, -, ex,
+    ey, ez, dsx, dsy)."""
+    L = lib()
+    prm = make_params(**params)
+    dom = (C.c_int32 * 3)(*[int(v) for v in layout.dom_n])
+    nc, nd = C.c_int64(), C.c_int64()
+    rc = L.qk_fill_plan(C.byref(prm), _boxes(layout), layout.nbox, dom, int(layout.ng), None, 0,
+                        C.byref(nc), C.byref(nd))
+    if rc != OK:
+        raise QKError(rc, L.qk_last_error(None).decode())
+    out = np.zeros((nc.value + nd.value, 12), dtype=np.int64)
+    rc = L.qk_fill_plan(C.byref(prm), _boxes(layout), layout.nbox, dom, int(layout.ng),
+                        out.ctypes.data_as(C.POINTER(C.c_int64)), len(out), C.byref(nc),
+                        C.byref(nd))
+    if rc != OK:
+        raise QKError(rc, L.qk_last_error(None).decode())
+    return out[out[:, 11] == 0, :11], out[out[:, 11] == 1, :7]
+
+
 class Context:
     """A patch set on the current CUDA device (wraps qk_init_patches).
 
@@ -148,12 +197,7 @@ class Context:
     def __init__(self, layout, params: dict, precision: int = FP64, owner=None, rank: int = 0):
         self._L = lib()
         nb = layout.nbox
-        boxes = (Box * nb)()
-        for b in range(nb):
-            for d in range(3):
-                boxes[b].lo[d] = int(layout.lo[b][d])
-                boxes[b].n[d] = int(layout.n[b][d])
-            boxes[b].offset = int(layout.off[b])
+        boxes = _boxes(layout)
         dom = (C.c_int32 * 3)(*[int(v) for v in layout.dom_n])
         self.params = make_params(**params)
         self.precision = precision
@@ -219,9 +263,23 @@ class Context:
     def set_graph(self, enable: bool):
         self._check(self._L.qk_set_graph(self._h, 1 if enable else 0))
 
-    def fill_ghosts(self, fields, stream=None):
-        self._check(self._L.qk_fill_ghosts(self._h, _ptrs(fields, len(fields)), len(fields),
-                                           _stream(stream)))
+    def fill_ghosts(self, fields, first=0, stream=None):
+        """Ghost fill of fields holding state fields first, first+1, ... of
+        (rho, m_x, m_y, m_z, E, E_r, F_x, F_y, F_z)."""
+        self._check(self._L.qk_fill_ghosts_range(self._h, _ptrs(fields, len(fields)), int(first),
+                                                 len(fields), _stream(stream)))
+
+    def set_dirichlet(self, U, R=None, stream=None):
+        """Record the states the ghost cells beyond Dirichlet faces hold now."""
+        self._check(self._L.qk_set_dirichlet(self._h, _ptrs(U, 5),
+                                             _ptrs(R, 4) if R is not None else None,
+                                             _stream(stream)))
+
+    def set_source(self, j):
+        """Emissivity field of the exchange (a tensor kept alive by the caller), or None."""
+        self._source = j
+        self._check(self._L.qk_set_source(self._h, C.c_void_p(int(j.data_ptr())) if j is not None
+                                          else None))
 
     def hydro_stage(self, stage, U0, U1, Uout, dt, stream=None):
         self._check(self._L.qk_hydro_stage(self._h, stage, _ptrs(U0, 5), _ptrs(U1, 5),
@@ -277,15 +335,15 @@ class Context:
         self._check(self._L.qk_halo_info(self._h, int(peer), C.byref(s), C.byref(r), None))
         return int(s.value), int(r.value)
 
-    def halo_pack(self, peer, fields, buf, stream=None):
+    def halo_pack(self, peer, fields, buf, first=0, stream=None):
         self._check(self._L.qk_halo_pack(self._h, int(peer), _ptrs(fields, len(fields)),
-                                         len(fields), C.c_void_p(int(buf.data_ptr())),
-                                         _stream(stream)))
+                                         int(first), len(fields),
+                                         C.c_void_p(int(buf.data_ptr())), _stream(stream)))
 
-    def halo_unpack(self, peer, fields, buf, stream=None):
+    def halo_unpack(self, peer, fields, buf, first=0, stream=None):
         self._check(self._L.qk_halo_unpack(self._h, int(peer), _ptrs(fields, len(fields)),
-                                           len(fields), C.c_void_p(int(buf.data_ptr())),
-                                           _stream(stream)))
+                                           int(first), len(fields),
+                                           C.c_void_p(int(buf.data_ptr())), _stream(stream)))
 
     def signal_speed(self, U, stream=None):
         """max(|v| + c_s) over this context's cells."""

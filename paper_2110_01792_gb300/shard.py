@@ -229,36 +229,37 @@ class RankStepper:
         self.sbuf = {p: torch.empty(nf * max(1, s), dtype=dt, device=dev) for p, (s, _) in self.cells.items()}
         self.rbuf = {p: torch.empty(nf * max(1, r), dtype=dt, device=dev) for p, (_, r) in self.cells.items()}
 
-    def _fill(self, fields):
-        """Full ghost fill of ``fields``: rank-local copies, then the halo."""
-        self.ctx.fill_ghosts(fields)
+    def _fill(self, fields, first):
+        """Full ghost fill of ``fields`` (state fields first, first+1, ...):
+        rank-local copies and boundary values, then the halo."""
+        self.ctx.fill_ghosts(fields, first)
         nf = len(fields)
         sends, recvs = {}, {}
         for p in self.peers:
             s, r = self.cells[p]
             if s:
                 sends[p] = self.sbuf[p][:nf * s]
-                self.ctx.halo_pack(p, fields, sends[p])
+                self.ctx.halo_pack(p, fields, sends[p], first)
             if r:
                 recvs[p] = self.rbuf[p][:nf * r]
         yield ("halo", sends, recvs)
         for p, buf in recvs.items():
-            self.ctx.halo_unpack(p, fields, buf)
+            self.ctx.halo_unpack(p, fields, buf, first)
 
     def step(self):
         ctx, U, R = self.ctx, self.U, self.R
         smax = yield ("max", ctx.signal_speed(U))
         dt, nsub, dtr, _ = ctx.set_timestep(smax)
-        yield from self._fill(U)
+        yield from self._fill(U, 0)
         ctx.hydro_stage(1, U, None, self.U1, dt)
-        yield from self._fill(self.U1)
+        yield from self._fill(self.U1, 0)
         ctx.hydro_stage(2, U, self.U1, U, dt)
         if R is not None and not ctx.params.hydro_only:
-            yield from self._fill(U[:1])
+            yield from self._fill(U[:1], 0)
             for _ in range(nsub):
-                yield from self._fill(R)
+                yield from self._fill(R, 5)
                 ctx.rad_stage(1, R, None, self.R1, U[0], dtr)
-                yield from self._fill(self.R1)
+                yield from self._fill(self.R1, 5)
                 ctx.rad_stage(2, R, self.R1, R, U[0], dtr)
                 ctx.exchange(U, R, dtr)
         return dt, nsub

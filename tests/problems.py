@@ -136,3 +136,79 @@ def radiation_pressure_tube(spec, N=None, ng=4):
                   chat=spec["chat_over_cs0"] * cs0, c_v=cv, kappa_P=kappa, kappa_R=kappa,
                   dx=dx, bc_lo=(3, 0, 0), bc_hi=(3, 0, 0), nsub_max=10, tau_correction=1)
     return lay, U, R, params, T[ng:N + ng], L / cs0
+
+
+# --------------------------------------------- dense whole-domain states ---
+VEC_AXIS = {1: 0, 2: 1, 3: 2, 6: 0, 7: 1, 8: 2}  # state field id -> vector axis
+
+
+def scatter(lay, dense):
+    """Dense [z, y, x] arrays of the whole domain -> field arrays of a layout."""
+    out = I.zeros(lay, len(dense))
+    for f, d in zip(out, dense):
+        for b in range(lay.nbox):
+            lo, n = lay.lo[b], lay.n[b]
+            lay.interior(f, b)[...] = d[lo[2]:lo[2] + n[2], lo[1]:lo[1] + n[1], lo[0]:lo[0] + n[0]]
+    return out
+
+
+def gather(lay, fields):
+    out = []
+    for f in fields:
+        d = np.zeros(tuple(lay.dom_n[::-1]))
+        for b in range(lay.nbox):
+            lo, n = lay.lo[b], lay.n[b]
+            d[lo[2]:lo[2] + n[2], lo[1]:lo[1] + n[1], lo[0]:lo[0] + n[0]] = lay.interior(f, b)
+        out.append(d)
+    return out
+
+
+def two_patches(n, ng=4):
+    """The domain n split into two patches along x (non-equal widths)."""
+    a = n[0] // 2 + 1
+    return I.make_layout([[0, 0, 0], [a, 0, 0]], [[a, n[1], n[2]], [n[0] - a, n[1], n[2]]],
+                         tuple(n), ng)
+
+
+def random_state(n, seed, rad=True):
+    """Dense random RHD state (rho, m, E, E_r, F) on a domain n = (nx, ny, nz)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    shp = (n[2], n[1], n[0])
+    rho = np.exp(0.4 * rng.standard_normal(shp))
+    v = 0.5 * rng.standard_normal((3,) + shp)
+    P = np.exp(0.3 * rng.standard_normal(shp))
+    gamma = 5.0 / 3.0
+    U = [rho, rho * v[0], rho * v[1], rho * v[2], P / (gamma - 1) + 0.5 * rho * (v ** 2).sum(0)]
+    if not rad:
+        return U
+    Er = np.exp(0.3 * rng.standard_normal(shp))
+    f = rng.standard_normal((3,) + shp)
+    f *= 0.7 * rng.random(shp) / np.sqrt((f ** 2).sum(0))
+    c = 20.0
+    return U + [Er, c * Er * f[0], c * Er * f[1], c * Er * f[2]]
+
+
+def mirror_double(dense, axes):
+    """Append the mirror image along each axis in ``axes`` (0 = x); vector
+    components along that axis change sign in the image."""
+    out = list(dense)
+    for ax in axes:
+        npax = 2 - ax
+        out = [np.concatenate([d, (-1.0 if VEC_AXIS.get(fid) == ax else 1.0) * np.flip(d, npax)],
+                              axis=npax) for fid, d in enumerate(out)]
+    return out
+
+
+def blob_in_ambient(n, pad, margin, seed):
+    """A random blob inside a uniform ambient state: ``margin`` ambient cells
+    between the blob and each non-periodic wall, ``pad`` more ambient cells
+    beyond the walls (the padded periodic twin)."""
+    ambient = [1.0, 0.3, -0.2, 0.1, 2.0, 1.0, 2.0, -1.0, 0.5]
+    shp = (n[2] + 2 * pad[2], n[1] + 2 * pad[1], n[0] + 2 * pad[0])
+    dense = [np.full(shp, v) for v in ambient]
+    m = [margin if p else 0 for p in pad]
+    blob = random_state(tuple(n[d] - 2 * m[d] for d in range(3)), seed)
+    sl = tuple(slice(pad[d] + m[d], pad[d] + n[d] - m[d]) for d in (2, 1, 0))
+    for d, b in zip(dense, blob):
+        d[sl] = b
+    return dense

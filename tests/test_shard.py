@@ -130,13 +130,13 @@ class FakeShardCtx:
         vol = lambda regs: sum(r[4][0] * r[4][1] * r[4][2] for r in regs)
         return vol(self.plan["send"].get(p, [])), vol(self.plan["recv"].get(p, []))
 
-    def fill_ghosts(self, fields):
+    def fill_ghosts(self, fields, first=0):
         S.apply_local(self.lay, self._np(fields), self.plan["local"])
 
-    def halo_pack(self, p, fields, buf):
+    def halo_pack(self, p, fields, buf, first=0):
         buf.numpy()[...] = S.pack(self.lay, self._np(fields), self.plan["send"][p])
 
-    def halo_unpack(self, p, fields, buf):
+    def halo_unpack(self, p, fields, buf, first=0):
         S.unpack(self.lay, self._np(fields), self.plan["recv"][p], buf.numpy())
 
     def signal_speed(self, U):
