@@ -75,7 +75,7 @@ __device__ __forceinline__ int newton_exchange(const qk_params &p, R_ Eg0, R_ Er
     const R_ dRdEg = k * a_r * dT4;
     const R_ G = R_(1) + cr * dRdEg;
     const R_ D1 = dFR_dEr * G + dRdEg * dFG_dEr;
-    const R_ inv = R_(1) / (D1 * G);
+    const R_ inv = qrcp(D1 * G);
     const R_ dEr = -(FR * G + dRdEg * FG) * (G * inv);
     const R_ dEg = -(FG + dEr * dFG_dEr) * (D1 * inv);
     Er += dEr;
@@ -251,12 +251,12 @@ __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, 
     const double m2 = (m[0] * m[0] + m[1] * m[1]) + m[2] * m[2];
     // one reciprocal serves 1/rho and the flux damping 1/(1 + rho kF chat dt)
     const double Dm = 1.0 + rho * kF * chat * dt;
-    const double inv_rho_Dm = 1.0 / (rho * Dm);
+    const double inv_rho_Dm = frcp(rho * Dm);
     const double inv_rho = Dm * inv_rho_Dm;
     const double damp = rho * inv_rho_Dm;
     const double Ekin0 = 0.5 * m2 * inv_rho;
     const double Eg0 = E - Ekin0;
-    const double inv_Etot = 1.0 / (Eg0 + cr * Er0);
+    const double inv_Etot = frcp(Eg0 + cr * Er0);
     const double k = dt * rho * kP * chat;
     const double inv_rcv = inv_rho * inv_cv;
     // radiation source S = dt (chat/c) j, carried in the residual's E_r0

@@ -8,6 +8,39 @@
 
 namespace qk {
 
+// FP64 reciprocal: the hardware's approximate reciprocal (PTX
+// rcp.approx.ftz.f64, about 20 correct bits) refined by two Newton-Raphson
+// steps for 1/b, r <- r + r (1 - b r), each doubling the correct bits (about
+// 80 > 53 after two): within an ulp of 1/b for normal b with a normal
+// reciprocal (b = 0 or an infinite b give NaN).  Four FP64 slots against the
+// ~7.5 of an IEEE division on this part.
+__device__ __forceinline__ double frcp(double b) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+  double e = fma(-b, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-b, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ double qdiv(double a, double b) { return a * frcp(b); }
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qrcp(double b) { return frcp(b); }
+// Division that must be exact in FP64 (the HLLC ratio of a stationary contact
+// has to come out as exactly 1).
+__device__ __forceinline__ double xdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float xdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float qrcp(float b) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+  return r;
+}
+__device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float qsqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Conserved -> primitive (Sec. 2.2.1): v = m / rho, E_g = E - rho v^2 / 2,
 // P = (gamma - 1) E_g.  In mixed precision the internal energy is recovered
 // with ~48-bit error-free arithmetic (cancellation of E against the kinetic
@@ -18,7 +51,8 @@ __device__ __forceinline__ void con2prim(const T u[5], double gamma, T w[5]);
 template <>
 __device__ __forceinline__ void con2prim<double>(const double u[5], double gamma, double w[5]) {
   double rho = u[0];
-  double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+  const double inv = frcp(rho);
+  double vx = u[1] * inv, vy = u[2] * inv, vz = u[3] * inv;
   double v2 = (vx * vx + vy * vy) + vz * vz;
   double Eg = u[4] - 0.5 * rho * v2;
   w[0] = rho;
@@ -39,21 +73,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // Division, reciprocal and square root: IEEE in FP64; in FP32 the hardware
 // approximations (a few ulp), which the FP32 path's error budget absorbs and
 // which avoid the ~60-instruction IEEE FP32 division sequence.
-__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
-__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double qrcp(double b) { return 1.0 / b; }
-__device__ __forceinline__ float qrcp(float b) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
-  return r;
-}
-__device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float qsqrt(float x) {
-  float r;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
 // Mixed precision: the internal energy E_g = E - |m|^2/(2 rho) is recovered
 // with error-free transformations on the FP32 pipe (|m|^2 by FMA TwoProduct
 // and TwoSum, the division and the subtraction in hi + lo form), which is as
@@ -239,7 +258,7 @@ __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm
   const T mK = rK * uK;
   // physical fluxes of K
   const T FK0 = mK, FKn = mK * uK + pK, FKa = mK * aK, FKb = mK * bK, FKe = uK * (EK + pK);
-  const T ratio = qdiv(SK - uK, SK - Ss);
+  const T ratio = xdiv(SK - uK, SK - Ss);
   const T fac = rK * ratio;
   const T Ue = ratio * (EK + rK * (Ss - uK) * (Ss + qdiv(pK, rK * (SK - uK))));
   T Fs0 = FK0 + SK * (fac - rK);
@@ -262,27 +281,24 @@ __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm
   F[4] = Fse;
 }
 
-// Levermore closure (eq. M1_closure) as the two coefficients of the Eddington
-// tensor T = P_r / E_r = a I + b f f for the reduced flux f, with |f| rescaled
-// to 1 for the closure when |f| > 1 and the n n term dropped when f = 0
-// (Sec. 2.2.2).  With fc^2 = min(|f|^2, 1), s = sqrt(4 - 3 fc^2),
-// D = 5 + 2 s, chi = (3 + 4 fc^2)/D:
-//   a = (1 - chi)/2 = (1 + s - 2 fc^2)/D,
-//   b = (3 chi - 1)/(2 |f|^2) = (2 + 6 fc^2 - s)/(D |f|^2),
-// so n_i n_j = f_i f_j / |f|^2 needs no |f| and one division serves both.
+// Levermore (1984) closure coefficients of T = a I + b f f (so that the
+// n n = f f / |f|^2 term needs no |f|): with s = sqrt(4 - 3 fc^2) and
+// (5 + 2 s)(5 - 2 s) = 3 (3 + 4 fc^2), chi = (3 + 4 fc^2)/(5 + 2 s) = (5 - 2 s)/3,
+// hence
+//   a = (1 - chi)/2 = (s - 1)/3,
+//   b = (3 chi - 1)/(2 |f|^2) = (2 - s)/|f|^2 = 3/(2 + s)   for |f| <= 1
+// (2 - s = 3 |f|^2/(2 + s)), and a = 0, b = 1/|f|^2 beyond (fc = 1, chi = 1).
+// One square root and one reciprocal, free of cancellation at small |f|.
 template <typename T>
 __device__ __forceinline__ void levermore_ab_f2(T f2, T &a, T &b) {
-  const T fc2 = nn_min(f2, T(1));
-  const T s = qsqrt(T(4) - T(3) * fc2);
-  const T D = T(5) + T(2) * s;
-  if (nn_gt(f2, T(0))) {
-    const T r = qrcp(D * f2);
-    a = (T(1) + s - T(2) * fc2) * (f2 * r);
-    b = (T(2) + T(6) * fc2 - s) * r;
-  } else {
-    a = qdiv(T(1) + s, D);
-    b = T(0);
+  if (nn_gt(f2, T(1))) {
+    a = T(0);
+    b = qrcp(f2);
+    return;
   }
+  const T s = qsqrt(T(4) - T(3) * f2);
+  a = (s - T(1)) * T(1.0 / 3.0);
+  b = T(3) * qrcp(T(2) + s);
 }
 
 // The same coefficients for every closure of Sec. 2.2.2, selected at compile

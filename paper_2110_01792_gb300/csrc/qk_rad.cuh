@@ -52,12 +52,14 @@ __device__ __forceinline__ void load_slot(RadSmem<T> &sm, int s, const T u[4], T
   }
 }
 
-// State vector (E, F) and flux along D of a radiation state (E_r, f) with
-// |f|^2 = f2 already known: flux_D = ((chat/c) F_D, c chat E T_xD, c chat E
-// T_yD, c chat E T_zD) (eqs. rad_energy, rad_flux; T from the closure CL).
+// State vector (E, F) and half the flux along D of a radiation state (E_r, f)
+// with |f|^2 = f2 already known: flux_D = ((chat/c) F_D, c chat E T_xD,
+// c chat E T_yD, c chat E T_zD) (eqs. rad_energy, rad_flux; T from the
+// closure CL), scaled by 1/2 through the constants hchat_c = chat/(2c) and
+// hccc = c chat / 2 (the HLL average of two states then needs no multiply).
 template <typename T, int D, int CL>
-__device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T f2, T c, T chat_c, T ccc,
-                                            T U[4], T F[4]) {
+__device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T f2, T c, T hchat_c,
+                                            T hccc, T U[4], T F[4]) {
   T a, b;
   closure_ab_f2<T, CL>(f2, a, b);
   const T fD = D == 0 ? fx : (D == 1 ? fy : fz);
@@ -66,8 +68,8 @@ __device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T f2, T c, T 
   U[1] = cE * fx;
   U[2] = cE * fy;
   U[3] = cE * fz;
-  F[0] = chat_c * U[1 + D];
-  const T cEb = ccc * E;                 // c chat E
+  F[0] = hchat_c * U[1 + D];
+  const T cEb = hccc * E;                // c chat E / 2
   const T bfD = b * fD;
   F[1] = cEb * (bfD * fx + (D == 0 ? a : T(0)));
   F[2] = cEb * (bfD * fy + (D == 1 ? a : T(0)));
@@ -78,8 +80,8 @@ template <typename T, int D, int NT, int NOWN, int CL>
 __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx, T dx, T c,
                                         T chat, int tau_corr, int rk, T (&acc)[NOWN][4]) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
-  const T ccc = c * chat;
-  const T chat_c = chat / c;
+  const T hccc = T(0.5) * c * chat;
+  const T hchat_c = T(0.5) * chat / c;
   for (int it = threadIdx.x; it < NREC; it += NT) {
     int pos, cc[3];
     item_cell<D>(it, NPOS, pos, cc[0], cc[1], cc[2]);
@@ -132,8 +134,8 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
       fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
     }
     T UL[4], FL[4], UR[4], FR[4];
-    rad_flux_of<T, D, CL>(wL[0], wL[1], wL[2], wL[3], fL2, c, chat_c, ccc, UL, FL);
-    rad_flux_of<T, D, CL>(wR[0], wR[1], wR[2], wR[3], fR2, c, chat_c, ccc, UR, FR);
+    rad_flux_of<T, D, CL>(wL[0], wL[1], wL[2], wL[3], fL2, c, hchat_c, hccc, UL, FL);
+    rad_flux_of<T, D, CL>(wR[0], wR[1], wR[2], wR[3], fR2, c, hchat_c, hccc, UR, FR);
     T S;
     if constexpr (RadSmem<T>::kAB) {
       // sqrt is monotone and correctly rounded: sqrt(max) == max(sqrt)
@@ -149,12 +151,15 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
       const T tau = dx * T(0.5) * (sm.rk[sa] + sm.rk[sb]);
       if (nn_gt(tau, T(1))) eps = qrcp(tau);
     }
+    // HLL with S_L = -S, S_R = S: (F_L + F_R)/2 - (S eps / 2)(U_R - U_L)
+    const T hS = T(0.5) * S;
+    const T hSe = hS * eps;
     T out[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) out[q] = T(0.5) * (FL[q] + FR[q]) - T(0.5) * S * eps * (UR[q] - UL[q]);
+    for (int q = 0; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hSe * (UR[q] - UL[q]);
     if (nn_gt(T(1), eps) && nn_gt(fabs(out[0]), chat * nn_max(UL[0], UR[0]))) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) out[q] = T(0.5) * (FL[q] + FR[q]) - T(0.5) * S * (UR[q] - UL[q]);
+      for (int q = 0; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hS * (UR[q] - UL[q]);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) sm.flux[q][it] = out[q];
