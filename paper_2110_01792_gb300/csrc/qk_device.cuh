@@ -35,11 +35,28 @@ __device__ __forceinline__ float qrcp(float b) {
   return r;
 }
 __device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
+// Square root of a positive normal double (no zero, no infinity): the
+// hardware's approximate reciprocal square root y (PTX rsqrt.approx.ftz.f64,
+// about 20 correct bits) gives s = x y, and two Heron corrections
+// s <- s + (y/2)(x - s^2) each square the relative error (measured: within
+// an ulp over [1/3, 4] and wide exponent ranges).  About 5.7 FP64 slots
+// against 7.6 for the IEEE square root on this part.
+__device__ __forceinline__ double psqrt(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double hy = 0.5 * y;
+  double s = x * y;
+  double d = fma(-s, s, x);
+  s = fma(hy, d, s);
+  d = fma(-s, s, x);
+  return fma(hy, d, s);
+}
 __device__ __forceinline__ float qsqrt(float x) {
   float r;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+__device__ __forceinline__ float psqrt(float x) { return qsqrt(x); }
 
 // Conserved -> primitive (Sec. 2.2.1): v = m / rho, E_g = E - rho v^2 / 2,
 // P = (gamma - 1) E_g.  In mixed precision the internal energy is recovered
@@ -245,8 +262,9 @@ __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm
   const T abar = T(0.5) * (cL + cR), rbar = T(0.5) * (rL + rR);
   const T ppvrs = T(0.5) * (pL + pR) - T(0.5) * (uR - uL) * rbar * abar;
   const T ps = max(T(0), ppvrs);
-  const T qL = ps <= pL ? T(1) : qsqrt(T(1) + g1 * (qdiv(ps, pL) - T(1)));
-  const T qR = ps <= pR ? T(1) : qsqrt(T(1) + g1 * (qdiv(ps, pR) - T(1)));
+  // shock branch: the argument exceeds 1
+  const T qL = ps <= pL ? T(1) : psqrt(T(1) + g1 * (qdiv(ps, pL) - T(1)));
+  const T qR = ps <= pR ? T(1) : psqrt(T(1) + g1 * (qdiv(ps, pR) - T(1)));
   const T SL = uL - cL * qL, SR = uR + cR * qR;
   const T mL = rL * (SL - uL), mR = rR * (SR - uR);
   const T Ss = qdiv(pR - pL + uL * mL - uR * mR, mL - mR);
@@ -296,7 +314,7 @@ __device__ __forceinline__ void levermore_ab_f2(T f2, T &a, T &b) {
     b = qrcp(f2);
     return;
   }
-  const T s = qsqrt(T(4) - T(3) * f2);
+  const T s = psqrt(T(4) - T(3) * f2);  // argument in [1, 4]
   a = (s - T(1)) * T(1.0 / 3.0);
   b = T(3) * qrcp(T(2) + s);
 }

@@ -142,7 +142,9 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
       const T fa = sm.prim[1 + D][sa], fb = sm.prim[1 + D][sb];
       const T Ta = sm.ab[0][sa] + sm.ab[1][sa] * fa * fa;
       const T Tb = sm.ab[0][sb] + sm.ab[1][sb] * fb * fb;
-      S = chat * qsqrt(nn_max(Ta, Tb));
+      // T_DD lies in [0, 1]; it is 0 only for a superluminal state with no flux along D
+      const T Tm = nn_max(Ta, Tb);
+      S = nn_gt(Tm, T(0)) ? chat * psqrt(Tm) : T(0);
     } else {
       S = chat * max(sm.sq[il], sm.sq[ir]);
     }
