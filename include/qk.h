@@ -362,6 +362,25 @@ int qk_halo_pack(qk_ctx *ctx, int32_t peer, void *const *fields, int32_t first, 
 int qk_halo_unpack(qk_ctx *ctx, int32_t peer, void *const *fields, int32_t first,
                    int32_t nfields, const void *buf, void *stream);
 
+/* Overlap of the halo exchange with the stage work (Sec. 4: the boundary
+ * fill dominated the paper's multi-GPU runs).  In a sharded context the tiles
+ * are split at creation into interior tiles, whose stencils (reach 4 cells,
+ * flattening included) touch no ghost cell that another rank fills, and
+ * boundary tiles.  qk_set_tile_part selects the tiles that later
+ * qk_hydro_stage / qk_rad_stage calls process (with their flattening
+ * pre-pass): QK_PART_ALL (default), QK_PART_INTERIOR or QK_PART_BOUNDARY.
+ * A stage may therefore run on the interior tiles as soon as the rank-local
+ * ghosts are filled and the halo is packed, and on the boundary tiles after
+ * the halo is unpacked; the two launches write disjoint cells and together
+ * give exactly the full stage.  qk_tile_counts reports the split (a context
+ * from qk_init_patches has no boundary tiles).  Per-patch launches
+ * (qk_set_launch_mode) apply only to QK_PART_ALL. */
+#define QK_PART_ALL 0
+#define QK_PART_INTERIOR 1
+#define QK_PART_BOUNDARY 2
+int qk_set_tile_part(qk_ctx *ctx, int32_t part);
+int qk_tile_counts(const qk_ctx *ctx, int32_t *n_interior, int32_t *n_boundary);
+
 /* Global timestep of a sharded step, in two halves around the caller's
  * max-reduction over ranks (Sec. 2.2: one dt from the CFL condition on the
  * whole domain).  qk_signal_speed writes the maximum of |v| + c_s over this

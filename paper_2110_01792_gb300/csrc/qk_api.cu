@@ -29,6 +29,12 @@ struct qk_ctx {
   int ntiles = 0;
   int nbox_dev = 0;            // patches in the device table (the owned ones)
   std::vector<int> tile_start;  // first tile of each owned patch (tiles grouped by patch)
+  // sharded contexts: the same tiles reordered, interior tiles (no ghost cell
+  // filled from another rank within their stencil reach) first, then the
+  // boundary tiles; `part` selects which ones the stage launches process
+  Tile *d_tiles_ib = nullptr;
+  int n_interior = 0;
+  int part = QK_PART_ALL;
   // sharded contexts: owner rank of every patch, this rank, and the halo
   // descriptors exchanged with each peer (send: owned source -> buffer;
   // recv: buffer -> owned ghost region), in one global order on every rank
@@ -98,6 +104,13 @@ static Geometry geom(const qk_ctx *c) {
   g.boxes = c->d_boxes;
   g.tiles = c->d_tiles;
   g.ntiles = c->ntiles;
+  if (c->part == QK_PART_INTERIOR) {
+    g.tiles = c->d_tiles_ib;
+    g.ntiles = c->n_interior;
+  } else if (c->part == QK_PART_BOUNDARY) {
+    g.tiles = c->d_tiles_ib + c->n_interior;
+    g.ntiles = c->ntiles - c->n_interior;
+  }
   g.nbox = c->nbox_dev;
   g.ng = c->ng;
   g.ncells = c->ncells;
@@ -386,6 +399,7 @@ static void release(qk_ctx *c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->d_boxes);
   cudaFree(c->d_tiles);
+  cudaFree(c->d_tiles_ib);
   cudaFree(c->d_cell0);
   cudaFree(c->d_copies);
   cudaFree(c->d_chunks);
@@ -567,6 +581,78 @@ static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, in
 
   if ((rc = upload(c, &c->d_boxes, db))) return bail(rc);
   if ((rc = upload(c, &c->d_tiles, tiles))) return bail(rc);
+  {
+    // Interior / boundary split of the tiles.  A tile is a boundary tile when
+    // a ghost cell that another rank fills lies within STENCIL_REACH cells of
+    // it (the stage stencils reach 3 cells, the flattening coefficient of the
+    // ring around a tile 4).  Remote ghost cells are marked per owned patch
+    // from the receive descriptors and counted with a summed-volume table.
+    const int R = 4;
+    std::vector<int> order(nown);
+    for (int l = 0; l < nown; ++l) order[l] = l;
+    std::sort(order.begin(), order.end(),
+              [&](int x, int y) { return boxes[c->own[x]].offset < boxes[c->own[y]].offset; });
+    std::vector<std::vector<int>> sat(nown);
+    for (const Copy &cp : rv) {
+      // owning patch of the destination by offset
+      int lo = 0, hi = nown - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (boxes[c->own[order[mid]]].offset <= cp.dst) lo = mid; else hi = mid - 1;
+      }
+      const int l = order[lo];
+      const qk_box &q = boxes[c->own[l]];
+      const int sx = q.n[0] + 2 * nghost, sy = q.n[1] + 2 * nghost, sz = q.n[2] + 2 * nghost;
+      std::vector<int> &m = sat[l];
+      if (m.empty()) m.assign((size_t)(sx + 1) * (sy + 1) * (sz + 1), 0);
+      const long long r0 = cp.dst - q.offset;
+      const int x0 = (int)(r0 % sx), y0 = (int)((r0 / sx) % sy), z0 = (int)(r0 / ((long long)sx * sy));
+      for (int z = 0; z < cp.ez; ++z)
+        for (int y = 0; y < cp.ey; ++y)
+          for (int x = 0; x < cp.ex; ++x)
+            m[((size_t)(z0 + z + 1) * (sy + 1) + (y0 + y + 1)) * (sx + 1) + (x0 + x + 1)] = 1;
+    }
+    for (int l = 0; l < nown; ++l) {
+      std::vector<int> &m = sat[l];
+      if (m.empty()) continue;
+      const qk_box &q = boxes[c->own[l]];
+      const int sx = q.n[0] + 2 * nghost + 1, sy = q.n[1] + 2 * nghost + 1, sz = q.n[2] + 2 * nghost + 1;
+      for (int z = 1; z < sz; ++z)
+        for (int y = 1; y < sy; ++y)
+          for (int x = 1; x < sx; ++x) {
+            auto at = [&](int zz, int yy, int xx) { return m[((size_t)zz * sy + yy) * sx + xx]; };
+            m[((size_t)z * sy + y) * sx + x] += at(z - 1, y, x) + at(z, y - 1, x) + at(z, y, x - 1) -
+                                                at(z - 1, y - 1, x) - at(z - 1, y, x - 1) -
+                                                at(z, y - 1, x - 1) + at(z - 1, y - 1, x - 1);
+          }
+    }
+    std::vector<Tile> inner, outer;
+    for (const Tile &t : tiles) {
+      const std::vector<int> &m = sat[t.box];
+      bool remote = false;
+      if (!m.empty()) {
+        const qk_box &q = boxes[c->own[t.box]];
+        const int full[3] = {q.n[0] + 2 * nghost, q.n[1] + 2 * nghost, q.n[2] + 2 * nghost};
+        const int t0[3] = {t.x0, t.y0, t.z0};
+        int lo3[3], hi3[3];
+        for (int d = 0; d < 3; ++d) {
+          lo3[d] = std::max(0, t0[d] + nghost - R);
+          hi3[d] = std::min(full[d], t0[d] + nghost + std::min(TS, q.n[d] - t0[d]) + R);
+        }
+        const int sx = full[0] + 1, sy = full[1] + 1;
+        auto at = [&](int zz, int yy, int xx) { return m[((size_t)zz * sy + yy) * sx + xx]; };
+        const int cnt = at(hi3[2], hi3[1], hi3[0]) - at(lo3[2], hi3[1], hi3[0]) -
+                        at(hi3[2], lo3[1], hi3[0]) - at(hi3[2], hi3[1], lo3[0]) +
+                        at(lo3[2], lo3[1], hi3[0]) + at(lo3[2], hi3[1], lo3[0]) +
+                        at(hi3[2], lo3[1], lo3[0]) - at(lo3[2], lo3[1], lo3[0]);
+        remote = cnt > 0;
+      }
+      (remote ? outer : inner).push_back(t);
+    }
+    c->n_interior = (int)inner.size();
+    inner.insert(inner.end(), outer.begin(), outer.end());
+    if ((rc = upload(c, &c->d_tiles_ib, inner))) return bail(rc);
+  }
   if ((rc = upload(c, &c->d_cell0, cell0))) return bail(rc);
   if ((rc = upload(c, &c->d_copies, copies))) return bail(rc);
   if ((rc = upload(c, &c->d_chunks, chunks))) return bail(rc);
@@ -818,6 +904,21 @@ int qk_set_source(qk_ctx *c, const void *j) {
   return QK_OK;
 }
 
+int qk_set_tile_part(qk_ctx *c, int32_t part) {
+  if (!c) return QK_EINVAL;
+  if (part != QK_PART_ALL && part != QK_PART_INTERIOR && part != QK_PART_BOUNDARY)
+    return fail(c, QK_EINVAL, "unknown tile part %d", part);
+  c->part = part;
+  return QK_OK;
+}
+
+int qk_tile_counts(const qk_ctx *c, int32_t *n_interior, int32_t *n_boundary) {
+  if (!c) return QK_EINVAL;
+  if (n_interior) *n_interior = c->n_interior;
+  if (n_boundary) *n_boundary = c->ntiles - c->n_interior;
+  return QK_OK;
+}
+
 int qk_set_graph(qk_ctx *c, int32_t enable) {
   if (!c) return QK_EINVAL;
   c->use_graph = enable ? 1 : 0;
@@ -956,7 +1057,7 @@ static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *c
     cudaError_t e = launch_flatten(c->fp32, g, c->p, stage == 1 ? U0 : U1, c->chi, s);
     if (e != cudaSuccess) return e;
   }
-  if (c->launch_mode == QK_LAUNCH_BATCHED)
+  if (c->launch_mode == QK_LAUNCH_BATCHED || c->part != QK_PART_ALL)
     return launch_hydro_stage(c->fp32, stage, g, c->p, U0, U1, Uo, dt, 0, c->cfg[stage - 1], chi,
                               s);
   for (int b = 0; b < c->nbox_dev; ++b) {
@@ -973,7 +1074,7 @@ static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *c
 static cudaError_t rad_launches(qk_ctx *c, int stage, void *const *R0, void *const *R1,
                                 void *const *Ro, const void *rho, DtSrc dt, cudaStream_t s) {
   const Geometry g = geom(c);
-  if (c->launch_mode == QK_LAUNCH_BATCHED)
+  if (c->launch_mode == QK_LAUNCH_BATCHED || c->part != QK_PART_ALL)
     return launch_rad_stage(c->fp32, stage, g, c->p, R0, R1, Ro, rho, dt, 0, c->cfg[1 + stage], s);
   for (int b = 0; b < c->nbox_dev; ++b) {
     Geometry gb = g;

@@ -43,6 +43,7 @@ class Params(C.Structure):
 
 
 CLOSURE_LEVERMORE, CLOSURE_MINERBO, CLOSURE_EDDINGTON = 0, 1, 2
+PART_ALL, PART_INTERIOR, PART_BOUNDARY = 0, 1, 2
 BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_DIRICHLET = 0, 1, 2, 3
 
 
@@ -92,9 +93,11 @@ def lib():
     L.qk_fill_plan.argtypes = [P(Params), P(Box), i32, P(i32), i32, P(i64), i64, P(i64), P(i64)]
     L.qk_set_dirichlet.argtypes = [vp, P(vp), P(vp), vp]
     L.qk_set_source.argtypes = [vp, vp]
+    L.qk_set_tile_part.argtypes = [vp, i32]
+    L.qk_tile_counts.argtypes = [vp, P(i32), P(i32)]
     L.qk_signal_speed.argtypes = [vp, P(vp), P(dbl), vp]
     L.qk_set_timestep.argtypes = [vp, dbl, P(dbl), vp]
-    for f in ("qk_fill_plan", "qk_fill_ghosts_range", "qk_set_dirichlet", "qk_set_source",
+    for f in ("qk_set_tile_part", "qk_tile_counts", "qk_fill_plan", "qk_fill_ghosts_range", "qk_set_dirichlet", "qk_set_source",
               "qk_init_shard", "qk_halo_info", "qk_halo_pack", "qk_halo_unpack",
               "qk_signal_speed", "qk_set_timestep", "qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_autotune",
               "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
@@ -356,3 +359,13 @@ class Context:
         out = (C.c_double * 4)()
         self._check(self._L.qk_set_timestep(self._h, float(smax), out, _stream(stream)))
         return out[0], int(out[1]), out[2], out[3]
+
+    def set_tile_part(self, part):
+        """Tiles processed by later stage calls: PART_ALL, PART_INTERIOR or PART_BOUNDARY."""
+        self._check(self._L.qk_set_tile_part(self._h, int(part)))
+
+    def tile_counts(self):
+        """(interior tiles, boundary tiles) of this context."""
+        i, b = C.c_int32(), C.c_int32()
+        self._check(self._L.qk_tile_counts(self._h, C.byref(i), C.byref(b)))
+        return int(i.value), int(b.value)

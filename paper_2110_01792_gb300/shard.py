@@ -213,11 +213,17 @@ class RankStepper:
     conserved hydro and radiation fields (torch CUDA tensors in the rank's
     layout).  ``step`` is a generator: it yields ("max", value) and expects the
     global max back, and yields ("halo", {peer: send buffer}, {peer: receive
-    buffer}) after packing, expecting the receive buffers filled on resume."""
+    buffer}, event) after packing (event: recorded after the pack on the
+    compute stream, or None), expecting the receive buffers filled on resume.
 
-    def __init__(self, ctx, U, R=None):
+    With ``overlap``, each stage runs on the interior tiles right after the
+    pack, before the yield (so that the transfer can proceed while they run),
+    and on the boundary tiles after the unpack."""
+
+    def __init__(self, ctx, U, R=None, overlap=False):
         import torch
         self.ctx, self.U, self.R = ctx, list(U), (list(R) if R is not None else None)
+        self.overlap = overlap
         dt = U[0].dtype
         self.U1 = [torch.empty_like(u) for u in U]
         self.R1 = [torch.empty_like(r) for r in R] if R is not None else None
@@ -229,9 +235,11 @@ class RankStepper:
         self.sbuf = {p: torch.empty(nf * max(1, s), dtype=dt, device=dev) for p, (s, _) in self.cells.items()}
         self.rbuf = {p: torch.empty(nf * max(1, r), dtype=dt, device=dev) for p, (_, r) in self.cells.items()}
 
-    def _fill(self, fields, first):
+    def _fill(self, fields, first, launch=None):
         """Full ghost fill of ``fields`` (state fields first, first+1, ...):
-        rank-local copies and boundary values, then the halo."""
+        rank-local copies and boundary values, then the halo; then the stage
+        ``launch`` (split around the transfer when overlapping)."""
+        import torch
         self.ctx.fill_ghosts(fields, first)
         nf = len(fields)
         sends, recvs = {}, {}
@@ -242,25 +250,36 @@ class RankStepper:
                 self.ctx.halo_pack(p, fields, sends[p], first)
             if r:
                 recvs[p] = self.rbuf[p][:nf * r]
-        yield ("halo", sends, recvs)
+        event = None
+        if fields[0].is_cuda:
+            event = torch.cuda.Event()
+            event.record()
+        split = self.overlap and launch is not None
+        if split:
+            self.ctx.set_tile_part(1)
+            launch()
+        yield ("halo", sends, recvs, event)
         for p, buf in recvs.items():
             self.ctx.halo_unpack(p, fields, buf, first)
+        if split:
+            self.ctx.set_tile_part(2)
+            launch()
+            self.ctx.set_tile_part(0)
+        elif launch is not None:
+            launch()
 
     def step(self):
         ctx, U, R = self.ctx, self.U, self.R
         smax = yield ("max", ctx.signal_speed(U))
         dt, nsub, dtr, _ = ctx.set_timestep(smax)
-        yield from self._fill(U, 0)
-        ctx.hydro_stage(1, U, None, self.U1, dt)
-        yield from self._fill(self.U1, 0)
-        ctx.hydro_stage(2, U, self.U1, U, dt)
+        U1, R1 = self.U1, self.R1
+        yield from self._fill(U, 0, lambda: ctx.hydro_stage(1, U, None, U1, dt))
+        yield from self._fill(U1, 0, lambda: ctx.hydro_stage(2, U, U1, U, dt))
         if R is not None and not ctx.params.hydro_only:
             yield from self._fill(U[:1], 0)
             for _ in range(nsub):
-                yield from self._fill(R, 5)
-                ctx.rad_stage(1, R, None, self.R1, U[0], dtr)
-                yield from self._fill(self.R1, 5)
-                ctx.rad_stage(2, R, self.R1, R, U[0], dtr)
+                yield from self._fill(R, 5, lambda: ctx.rad_stage(1, R, None, R1, U[0], dtr))
+                yield from self._fill(R1, 5, lambda: ctx.rad_stage(2, R, R1, R, U[0], dtr))
                 ctx.exchange(U, R, dtr)
         return dt, nsub
 
@@ -294,22 +313,39 @@ def run_local(steppers):
                 msgs[r] = None
 
 
-def run_distributed(stepper):
+def run_distributed(stepper, comm_stream=None):
     """Advance this process's rank by one step with torch.distributed: an
     all-reduce (MAX) for the signal speed and one isend / irecv pair per peer
-    for every ghost exchange (device buffers: NCCL; host buffers: gloo)."""
+    for every ghost exchange (device buffers: NCCL; host buffers: gloo).  On
+    the GPU the transfers are issued from ``comm_stream`` (created if None),
+    which waits only for the pack, so that they run while the interior tiles
+    of an overlapping stepper compute; waiting on the requests then orders the
+    unpack on the compute stream after them."""
     import torch
     import torch.distributed as dist
     g = stepper.step()
     msg = next(g)
+    cuda = stepper.U[0].is_cuda
+    if cuda and comm_stream is None:
+        comm_stream = torch.cuda.Stream()
     while True:
         if msg[0] == "max":
             t = torch.tensor([msg[1]], dtype=torch.float64, device=stepper.U[0].device)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             reply = float(t.item())
         else:
-            reqs = [dist.isend(buf, p) for p, buf in sorted(msg[1].items())]
-            reqs += [dist.irecv(buf, p) for p, buf in sorted(msg[2].items())]
+            _, sends, recvs, event = msg
+
+            def issue():
+                r = [dist.isend(buf, p) for p, buf in sorted(sends.items())]
+                return r + [dist.irecv(buf, p) for p, buf in sorted(recvs.items())]
+
+            if cuda:
+                with torch.cuda.stream(comm_stream):
+                    comm_stream.wait_event(event)
+                    reqs = issue()
+            else:
+                reqs = issue()
             for q in reqs:
                 q.wait()
             reply = None

@@ -136,3 +136,91 @@ def test_sharded_context_refuses_whole_step(torch_cuda):
     dU = G.dev(prob.U)
     ctx.step(dU)
     ctx.close()
+
+
+@pytest.mark.parametrize("nranks,flat,bcs", [(2, 1, None), (3, 0, "mixed")])
+def test_overlapped_sharded_step_bit_identical(torch_cuda, nranks, flat, bcs):
+    """Overlap of the halo transfer with the stage work: every stage runs on
+    the interior tiles (no remotely filled ghost cell within 4 cells) before
+    the halo moves and on the boundary tiles after; the result is bit for bit
+    the single-context qk_step, with flattening and with non-periodic faces.
+    Every rank has both kinds of tiles."""
+    torch = torch_cuda
+    from paper_2110_01792_gb300 import qk
+    lay, prob, prm = _overlap_problem(flat)
+    U, R = prob.U, prob.R
+    if bcs:
+        # outflow / Dirichlet on x, Dirichlet / reflecting on y, reflecting z;
+        # the Dirichlet states are whatever the ghost cells hold (zeros are
+        # not physical, so the interior state is copied outward first)
+        prm = dict(prm, bc_lo=(2, 3, 1), bc_hi=(3, 1, 1))
+        U, R = _frozen_ghosts(lay, U, R)
+    ref, href = _single_bc(lay, U, R, prm, 3)
+    owner = (lay.lo[:, 0] // 32 * nranks // 4).astype(np.int32)
+    ranks = []
+    for r in range(nranks):
+        rlay = S.rank_layout(lay, owner, r)
+        ctx = qk.Context(rlay, prm, 0, owner=owner, rank=r)
+        ni, nb = ctx.tile_counts()
+        assert ni > 0 and nb > 0, (r, ni, nb)
+        dU = _to_rank(lay, rlay, owner, r, U, torch.float64)
+        dR = _to_rank(lay, rlay, owner, r, R, torch.float64)
+        if bcs:
+            ctx.set_dirichlet(dU, dR)
+        ranks.append((rlay, ctx, S.RankStepper(ctx, dU, dR, overlap=True)))
+    hist = [S.run_local([st for _, _, st in ranks])[0] for _ in range(3)]
+    assert [(a, int(b)) for a, b in hist] == [(a, int(b)) for a, b in href]
+    for r, (rlay, ctx, st) in enumerate(ranks):
+        got = G.host(st.U) + G.host(st.R)
+        for f in range(9):
+            for b in np.nonzero(owner == r)[0]:
+                assert np.array_equal(rlay.interior(got[f], b), lay.interior(ref[f], b))
+        ctx.close()
+
+
+def _overlap_problem(flattening):
+    """Eight 32^3 patches over 128 x 64 x 32: patches wide enough that tiles
+    more than 4 cells from a rank border exist (interior tiles)."""
+    lo = [[x, y, 0] for y in (0, 32) for x in range(0, 128, 32)]
+    lay = I.make_layout(lo, [[32, 32, 32]] * len(lo), (128, 64, 32), 4)
+    prob = I.rhd_lognormal(layout=lay, seed=23)
+    rng = np.random.Generator(np.random.Philox(78))
+    for b in range(lay.nbox):
+        rho = lay.interior(prob.U[0], b)
+        v = 0.3 * rng.standard_normal((3,) + rho.shape)
+        for d in range(3):
+            lay.interior(prob.U[1 + d], b)[...] = rho * v[d]
+        lay.interior(prob.U[4], b)[...] += 0.5 * rho * (v ** 2).sum(0)
+    prm = dict(prob.params, dx=1.0 / 128, flattening=flattening)
+    return lay, prob, prm
+
+
+def _frozen_ghosts(lay, U, R):
+    """Every ghost cell takes the value of the nearest interior cell of its
+    patch: a physical state for the ghost cells beyond Dirichlet faces (which
+    each patch records for itself)."""
+    out = []
+    g = lay.ng
+    for f in U + R:
+        a = f.copy()
+        for b in range(lay.nbox):
+            full = lay.full(a, b)
+            n = lay.n[b]
+            iz = np.clip(np.arange(n[2] + 2 * g) - g, 0, n[2] - 1) + g
+            iy = np.clip(np.arange(n[1] + 2 * g) - g, 0, n[1] - 1) + g
+            ix = np.clip(np.arange(n[0] + 2 * g) - g, 0, n[0] - 1) + g
+            full[...] = full[np.ix_(iz, iy, ix)]
+        out.append(a)
+    return out[:5], out[5:]
+
+
+def _single_bc(lay, U, R, prm, steps):
+    from paper_2110_01792_gb300 import qk
+    ctx = qk.Context(lay, prm, 0)
+    dU, dR = G.dev(U), G.dev(R)
+    if 3 in tuple(prm.get("bc_lo", ())) + tuple(prm.get("bc_hi", ())):
+        ctx.set_dirichlet(dU, dR)
+    hist = [ctx.step(dU, dR, want_dt=True) for _ in range(steps)]
+    out = G.host(dU) + G.host(dR)
+    ctx.close()
+    return out, hist

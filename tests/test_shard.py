@@ -121,6 +121,15 @@ class FakeShardCtx:
         self.plan = S.exchange_plan(lay, owner)[rank]
         self.own = np.nonzero(owner == rank)[0]
         self.params = _Params()
+        # patch-level stand-in for the interior / boundary tile split: a patch
+        # is "boundary" when any of its ghost regions comes from another rank
+        remote = {r[0] for regs in self.plan["recv"].values() for r in regs}
+        self.parts = {0: self.own, 1: np.array([b for b in self.own if b not in remote]),
+                      2: np.array([b for b in self.own if b in remote])}
+        self.part = 0
+
+    def set_tile_part(self, part):
+        self.part = part
 
     @staticmethod
     def _np(fields):
@@ -160,7 +169,7 @@ class FakeShardCtx:
         src = A0 if stage == 1 else A1
         for f in range(len(A0)):
             a0, s, o = A0[f].numpy(), src[f].numpy(), Aout[f].numpy()
-            for b in self.own:
+            for b in self.parts[self.part]:
                 upd = self.lay.interior(s, b) + dt * self._lap(s, b, rho)
                 self.lay.interior(o, b)[...] = upd if stage == 1 else 0.5 * self.lay.interior(a0, b) + 0.5 * upd
 
@@ -179,7 +188,15 @@ class FakeShardCtx:
 
 
 def _composer_layout():
-    return I.patch_tiling(dom_n=(32, 24, 16), seed=8, ng=3, edges=(8, 16))
+    """Regular 8^3 patches over 48 x 16 x 16 (periodic), split into x-slabs
+    of 24 cells per rank: each rank has patches with and without remote
+    neighbours."""
+    lo = [[x, y, z] for z in (0, 8) for y in (0, 8) for x in range(0, 48, 8)]
+    return I.make_layout(lo, [[8, 8, 8]] * len(lo), (48, 16, 16), 3)
+
+
+def _composer_owner(lay, world):
+    return (lay.lo[:, 0] * world // 48).astype(np.int32)
 
 
 def _composer_fields(lay, owner, rank):
@@ -196,9 +213,9 @@ def _composer_fields(lay, owner, rank):
     return rlay, out[:5], out[5:]
 
 
-def _composer_run(lay, owner, rank, steps, driver):
+def _composer_run(lay, owner, rank, steps, driver, overlap=False):
     rlay, U, R = _composer_fields(lay, owner, rank)
-    st = S.RankStepper(FakeShardCtx(rlay, owner, rank), U, R)
+    st = S.RankStepper(FakeShardCtx(rlay, owner, rank), U, R, overlap=overlap)
     hist = [driver(st) for _ in range(steps)]
     res = {}
     for b in np.nonzero(owner == rank)[0]:
@@ -206,26 +223,32 @@ def _composer_run(lay, owner, rank, steps, driver):
     return res, hist
 
 
-def _composer_worker(rank, world, port, results):
+def _composer_worker(rank, world, port, results, overlap):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         lay = _composer_layout()
-        owner = S.partition(lay, world)
-        res, hist = _composer_run(lay, owner, rank, 2, S.run_distributed)
+        owner = _composer_owner(lay, world)
+        ctx = FakeShardCtx(S.rank_layout(lay, owner, rank), owner, rank)
+        assert len(ctx.parts[1]) > 0 and len(ctx.parts[2]) > 0
+        res, hist = _composer_run(lay, owner, rank, 2, S.run_distributed, overlap)
         results[rank] = (res, hist)
     finally:
         dist.destroy_process_group()
 
 
-def test_step_composer_over_gloo_matches_one_rank():
+@pytest.mark.parametrize("overlap", [False, True])
+def test_step_composer_over_gloo_matches_one_rank(overlap):
     """The per-rank step generator driven by ``run_distributed`` on 2 gloo ranks
     (all-reduce for the speed, isend / irecv of packed halos, ghosts NaN
     until filled) gives bit-for-bit the one-rank result of ``run_local`` with
     the same stencil stages: every ghost fill of every stage and substep saw
-    the right neighbour data and the global timestep."""
+    the right neighbour data and the global timestep.  With overlap, each
+    stage runs on the patches without remote ghosts before the transfer and on
+    the others after it (NaN ghosts would leak into any early launch that
+    needed the halo)."""
     import torch.multiprocessing as mp
     lay = _composer_layout()
     one = np.zeros(lay.nbox, dtype=np.int32)
@@ -235,7 +258,8 @@ def test_step_composer_over_gloo_matches_one_rank():
     results = mgr.dict()
     world = 2
     port = _free_port()
-    procs = [ctx.Process(target=_composer_worker, args=(r, world, port, results)) for r in range(world)]
+    procs = [ctx.Process(target=_composer_worker, args=(r, world, port, results, overlap))
+             for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
