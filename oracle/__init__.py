@@ -137,6 +137,10 @@ def lib():
             L.or_exchange_energy_src.argtypes = [P(Params), C.c_double, C.c_double, C.c_double,
                                                  C.c_double, C.c_double, P(C.c_double),
                                                  P(C.c_double)]
+            L.or_hydro_face_flux.argtypes = [vp, P(Params), vp, C.c_int32, P(C.c_int32),
+                                             C.c_int32, P(C.c_double)]
+            L.or_rad_face_flux.argtypes = [vp, P(Params), vp, vp, C.c_int32, P(C.c_int32),
+                                           C.c_int32, P(C.c_double)]
             L.or_set_dirichlet.restype = C.c_int
             L.or_set_dirichlet.argtypes = [vp, P(Params), vp]
             L.or_fill_ghosts_bc.restype = C.c_int
@@ -234,6 +238,23 @@ def eddington_tensor(f, closure=0):
 
 def eddington_factor(f, closure=0):
     return lib().or_eddington_factor(int(closure), float(f))
+
+
+def hydro_face_flux(grid, p, U, b, c, d):
+    """Hydro flux through the low face of patch b's cell c along axis d."""
+    out = (C.c_double * NHYD)()
+    cc = (C.c_int32 * 3)(*[int(v) for v in c])
+    lib().or_hydro_face_flux(grid.handle, C.byref(p), _ptr_array(U), int(b), cc, int(d), out)
+    return np.array(out[:])
+
+
+def rad_face_flux(grid, p, R, rho, b, c, d):
+    """Radiation flux through the low face of patch b's cell c along axis d."""
+    out = (C.c_double * NRAD)()
+    cc = (C.c_int32 * 3)(*[int(v) for v in c])
+    lib().or_rad_face_flux(grid.handle, C.byref(p), _ptr_array(R), _dptr(rho), int(b), cc,
+                           int(d), out)
+    return np.array(out[:])
 
 
 def set_dirichlet(grid, p, U, R):

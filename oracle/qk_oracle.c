@@ -219,6 +219,13 @@ static or_src resolve(const or_grid *g, const or_params *p, int b, const int c[3
     return r;
   }
   int q = g->owner[(x[2] * g->dom_n[1] + x[1]) * g->dom_n[0] + x[0]];
+  if (q < 0) {
+    /* a refined level that does not cover this cell: the value is the one
+     * patch b's own ghost cell holds (interpolated from the coarser level) */
+    r.e = cell_index(g, b, c[0], c[1], c[2]);
+    r.outside = 1;
+    return r;
+  }
   r.e = cell_index(g, q, (int)(x[0] - g->lo[3 * q]), (int)(x[1] - g->lo[3 * q + 1]),
                    (int)(x[2] - g->lo[3 * q + 2]));
   return r;
@@ -571,20 +578,30 @@ static void hydro_face_flux(const or_grid *g, const or_params *p, double *const 
     recon_cell(p, &w[v][0], &dummy, &wL[v]); /* right face of the left cell  */
     recon_cell(p, &w[v][1], &wR[v], &dummy); /* left face of the right cell  */
   }
-  if (chi) {
+  if (p->flattening) {
     /* reading: the face states are blended with the cell average after the
-     * limiter, q <- chi q + (1 - chi) q_cell */
+     * limiter, q <- chi q + (1 - chi) q_cell; the coefficients come from the
+     * stage's table, or are computed here when there is none */
     int cA[3] = {c[0], c[1], c[2]}, cB[3] = {c[0], c[1], c[2]};
     cA[d] += first + 2;
     cB[d] += first + 3;
-    double chiA = chi_at(g, p, U, chi, b, cA);
-    double chiB = chi_at(g, p, U, chi, b, cB);
+    double chiA = chi ? chi_at(g, p, U, chi, b, cA) : flat_chi(g, p, U, b, cA);
+    double chiB = chi ? chi_at(g, p, U, chi, b, cB) : flat_chi(g, p, U, b, cB);
     for (int v = 0; v < NHYD; ++v) {
       wL[v] = chiA * wL[v] + (1.0 - chiA) * w[v][2];
       wR[v] = chiB * wR[v] + (1.0 - chiB) * w[v][3];
     }
   }
   or_hllc(wL, wR, d, p->gamma, F);
+}
+
+/* The hydro flux through the low face of patch b's cell c along d (between
+ * c - e_d and c), from the state U: the flux the stage uses at that face.
+ * For the flux registers of mesh refinement (Berger & Colella 1989). */
+void or_hydro_face_flux(const or_grid *g, const or_params *p, double *const *U, int32_t b,
+                        const int32_t c[3], int32_t d, double F[NHYD]) {
+  const int cc[3] = {c[0], c[1], c[2]};
+  hydro_face_flux(g, p, U, NULL, b, cc, d, -3, F);
 }
 
 /* L(U) at interior cell (b,i,j,k): minus the divergence of the face fluxes,
@@ -868,6 +885,16 @@ static void rad_face_flux(const or_grid *g, const or_params *p, double *const *R
   if (eps < 1.0 && fabs(Fout[0]) > p->chat * dmax(UL[0], UR[0])) {
     for (int v = 0; v < NRAD; ++v) Fout[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * S * (UR[v] - UL[v]);
   }
+}
+
+/* The radiation flux through the low face of patch b's cell c along d. */
+static void rad_face_flux(const or_grid *g, const or_params *p, double *const *R,
+                          const double *rho, int b, const int c[3], int d, int first,
+                          double Fout[NRAD]);
+void or_rad_face_flux(const or_grid *g, const or_params *p, double *const *R, const double *rho,
+                      int32_t b, const int32_t c[3], int32_t d, double F[NRAD]) {
+  const int cc[3] = {c[0], c[1], c[2]};
+  rad_face_flux(g, p, R, rho, b, cc, d, -3, F);
 }
 
 static void rad_rhs_cell(const or_grid *g, const or_params *p, double *const *R,

@@ -212,3 +212,58 @@ def blob_in_ambient(n, pad, margin, seed):
     for d, b in zip(dense, blob):
         d[sl] = b
     return dense
+
+
+def random_state_smooth(lay, seed, amp=0.3, c=20.0):
+    """Smooth periodic RHD state on a layout: a few random low-order Fourier
+    modes (Philox-seeded) per field, evaluated at cell centres of the domain
+    [0, 1)^3 scaled by dom_n; positive rho, P, E_r and |f| <= 0.6."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    dom = np.array(lay.dom_n, dtype=float)
+    modes = []
+    for _ in range(9):
+        k = rng.integers(-2, 3, size=(3, 3))
+        ph = rng.uniform(0, 2 * np.pi, size=3)
+        a = rng.uniform(0.3, 1.0, size=3)
+        modes.append((k, ph, a))
+
+    def field(v, X, Y, Z):
+        k, ph, a = modes[v]
+        s = np.zeros_like(X)
+        for m in range(3):
+            s += a[m] * np.sin(2 * np.pi * (k[m, 0] * X + k[m, 1] * Y + k[m, 2] * Z) + ph[m])
+        return s / 3.0
+
+    gamma = 5.0 / 3.0
+    U = I.zeros(lay, 5)
+    R = I.zeros(lay, 4)
+    for b in range(lay.nbox):
+        lo, n = lay.lo[b], lay.n[b]
+        Z, Y, X = np.meshgrid(*[(lo[d] + np.arange(n[d]) + 0.5) / dom[d] for d in (2, 1, 0)],
+                              indexing="ij")
+        rho = np.exp(amp * field(0, X, Y, Z))
+        v = [amp * field(1 + d, X, Y, Z) for d in range(3)]
+        P_ = np.exp(amp * field(4, X, Y, Z))
+        Er = np.exp(amp * field(5, X, Y, Z))
+        f = [0.2 * field(6 + d, X, Y, Z) for d in range(3)]
+        lay.interior(U[0], b)[...] = rho
+        for d in range(3):
+            lay.interior(U[1 + d], b)[...] = rho * v[d]
+        lay.interior(U[4], b)[...] = P_ / (gamma - 1) + 0.5 * rho * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
+        lay.interior(R[0], b)[...] = Er
+        for d in range(3):
+            lay.interior(R[1 + d], b)[...] = c * Er * f[d]
+    return U, R
+
+
+def refine_state(coarse, fine, fields):
+    """Fine fields from coarse ones by injection: every fine cell takes its
+    coarse parent's value (a newly refined level before its first step)."""
+    dense = gather(coarse, fields)
+    out = [np.zeros(fine.field_len) for _ in fields]
+    for f, d in zip(out, dense):
+        for b in range(fine.nbox):
+            lo, n = fine.lo[b], fine.n[b]
+            idx = [((lo[a] + np.arange(n[a])) // 2) % coarse.dom_n[a] for a in range(3)]
+            fine.interior(f, b)[...] = d[np.ix_(idx[2], idx[1], idx[0])]
+    return out[:5], out[5:]
