@@ -392,6 +392,59 @@ int qk_tile_counts(const qk_ctx *ctx, int32_t *n_interior, int32_t *n_boundary);
 int qk_signal_speed(qk_ctx *ctx, void *const hydro[5], double *smax, void *stream);
 int qk_set_timestep(qk_ctx *ctx, double smax, double out[4], void *stream);
 
+/* ---- Mesh refinement (two levels; Sec. 2.2, Berger & Colella 1989) ----
+ * A refinement level is a patch set that need not cover its domain.  Its
+ * ghost cells that no patch of the level covers are left to qk_amr_interp;
+ * the rest is as qk_init_patches.  Refinement levels are periodic. */
+int qk_init_level(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
+                  const int32_t domain_n[3], int32_t nghost, int32_t precision);
+
+/* A coarse level (covering its periodic domain) and a fine level with cells
+ * a factor 2 smaller (domain twice as many cells, dx half, patches aligned to
+ * coarse cells, same precision and ghost width).  qk_amr_init builds, on the
+ * host, the lists of: fine ghost cells outside the fine region (with their
+ * coarse parents), coarse-fine faces (each with its four fine faces and the
+ * uncovered coarse cell beside it), and coarse cells under the fine region;
+ * and zeroes the flux registers.  Both contexts must outlive the handle. */
+typedef struct qk_amr qk_amr;
+int qk_amr_init(qk_amr **out, qk_ctx *coarse, qk_ctx *fine);
+void qk_amr_destroy(qk_amr *amr);
+/* Message of the last failing call on `amr` (or of the last failed
+ * qk_amr_init on this thread when amr is NULL). */
+const char *qk_amr_last_error(const qk_amr *amr);
+/* Sizes of the lists: fine ghost cells filled by interpolation, coarse-fine
+ * faces, coarse cells under the fine region (pointers may be NULL). */
+int qk_amr_info(const qk_amr *amr, int64_t *n_cf_ghosts, int64_t *n_faces, int64_t *n_covered);
+
+/* Fill the fine ghost cells outside the fine region of `nfields` fine arrays
+ * holding state fields first .. first+nfields-1 (as qk_fill_ghosts_range)
+ * from the coarse state (1 - alpha) c_old + alpha c_new (arrays of all nine
+ * state fields; only the requested ones are read; their ghost cells filled):
+ * per axis, a quarter of the monotonized-central slope of the coarse
+ * conserved variable toward the fine cell (conservative linear
+ * interpolation; the paper uses linear interpolation for robustness). */
+int qk_amr_interp(qk_amr *amr, void *const c_old[9], void *const c_new[9], double alpha,
+                  void *const *fine_fields, int32_t first, int32_t nfields, void *stream);
+
+/* Flux register: accumulate `weight` times the flux through every
+ * coarse-fine face (level 0: the coarse face; level 1: each of its four fine
+ * faces with a quarter of the weight) computed from the given state with the
+ * stage's arithmetic.  kind 0: hydro, fields = the 5 hydro arrays; kind 1:
+ * radiation, fields = the 4 radiation arrays and rho.  Ghost cells must be
+ * filled; with flattening, call it right after the stage on the same state
+ * (its coefficients are reused).  For one RK2-SSP step of duration dt the
+ * weights are dt/2 for the stage-1 and the stage-2 input states. */
+int qk_amr_register(qk_amr *amr, int32_t level, int32_t kind, void *const *fields,
+                    const void *rho, double weight, void *stream);
+
+/* Level synchronisation: every uncovered coarse cell beside the fine region
+ * gets -side (fine - coarse flux integral) / dx through each of its
+ * coarse-fine faces (side +1 when the cell is on the face's low side), then
+ * every coarse cell under the fine region becomes the mean of its eight fine
+ * cells; the registers are zeroed.  cR and fR are both NULL for hydro only. */
+int qk_amr_sync(qk_amr *amr, void *const cU[5], void *const cR[4], void *const fU[5],
+                void *const fR[4], void *stream);
+
 /* Read the accumulated exchange status (synchronises `stream`):
  * *flags = bit (1 << QK_ENOCONV) | bit (1 << QK_ENEGATIVE); *first_bad = the
  * smallest element index of a failing cell (-1 if none); *max_iter = the

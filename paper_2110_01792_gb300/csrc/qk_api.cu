@@ -9,73 +9,10 @@
 #include <string>
 #include <vector>
 
-#include "qk_internal.cuh"
+#include "qk_ctx.cuh"
 
 using namespace qk;
 
-struct qk_ctx {
-  qk_params p{};
-  int fp32 = 0;
-  int ng = 0;
-  int nbox = 0;
-  int dom[3] = {0, 0, 0};
-  std::vector<qk_box> boxes;
-  int64_t field_len = 0;
-  int64_t ncells = 0;
-  // device tables
-  DevBox *d_boxes = nullptr;
-  Tile *d_tiles = nullptr;
-  long long *d_cell0 = nullptr;
-  int ntiles = 0;
-  int nbox_dev = 0;            // patches in the device table (the owned ones)
-  std::vector<int> tile_start;  // first tile of each owned patch (tiles grouped by patch)
-  // sharded contexts: the same tiles reordered, interior tiles (no ghost cell
-  // filled from another rank within their stencil reach) first, then the
-  // boundary tiles; `part` selects which ones the stage launches process
-  Tile *d_tiles_ib = nullptr;
-  int n_interior = 0;
-  int part = QK_PART_ALL;
-  // sharded contexts: owner rank of every patch, this rank, and the halo
-  // descriptors exchanged with each peer (send: owned source -> buffer;
-  // recv: buffer -> owned ghost region), in one global order on every rank
-  std::vector<int> owner;
-  int rank = 0, nranks = 1;
-  std::vector<int> own;          // owned patch indices (global numbering)
-  Copy *d_send = nullptr, *d_recv = nullptr;
-  Chunk *d_send_chunks = nullptr, *d_recv_chunks = nullptr;
-  std::vector<int> send_chunk0, recv_chunk0;  // per peer: chunk range [p], [p+1)
-  std::vector<long long> send_cells, recv_cells;
-  int launch_mode = QK_LAUNCH_BATCHED;
-  int cfg[4] = {kDefaultCfg, kDefaultCfg, kDefaultCfg, kDefaultCfg};  // hydro1/2, rad1/2
-  Copy *d_copies = nullptr;
-  Chunk *d_chunks = nullptr;
-  int ncopies = 0, nchunks = 0;
-  // Dirichlet boundary store: 9 fields x ndir cells, recorded by
-  // qk_set_dirichlet from the caller's ghost cells, restored by every fill
-  Copy *d_dpack = nullptr, *d_dunpack = nullptr;
-  Chunk *d_dchunks = nullptr;
-  int ndchunks = 0;
-  long long ndir = 0;
-  void *dstore = nullptr;
-  int dir_set = 0;
-  StepInfo *d_si = nullptr;
-  Status *d_status = nullptr;
-  double *d_partials = nullptr;
-  double *d_sums = nullptr;
-  int sum_blocks = 0;
-  void *scratch[9] = {};
-  void *chi = nullptr;   // shock-flattening coefficient (one field)
-  const void *src = nullptr;  // caller's emissivity field j of the exchange, or none
-  size_t elem = 8;
-  // pinned host staging
-  double *h_buf = nullptr;
-  // step graph
-  int use_graph = 1;
-  cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  void *gkey[10] = {};
-  std::string err;
-};
 
 static thread_local std::string g_init_err = "qk: null context";
 
@@ -350,7 +287,7 @@ static int validate_boxes(qk_ctx *c) {
     if (q.offset < 0) return fail(c, QK_EINVAL, "box %d: negative offset", b);
     tot += (int64_t)q.n[0] * q.n[1] * q.n[2];
   }
-  if (tot != dvol)
+  if (!c->partial && tot != dvol)
     return fail(c, QK_EINVAL, "boxes cover %lld cells, the domain has %lld", (long long)tot,
                 (long long)dvol);
   // pairwise overlap (sweep on x)
@@ -424,10 +361,11 @@ extern "C" {
 
 static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
                        const int32_t domain_n[3], int32_t nghost, int32_t precision,
-                       const int32_t *owner, int32_t nranks, int32_t rank) {
+                       const int32_t *owner, int32_t nranks, int32_t rank, int partial = 0) {
   if (!out) return QK_EINVAL;
   *out = nullptr;
   qk_ctx *c = new qk_ctx();
+  c->partial = partial;
   auto bail = [&](int rc) {
     g_init_err = c->err.empty() ? std::string("qk_init_patches failed") : c->err;
     release(c);
@@ -738,6 +676,16 @@ int qk_fill_plan(const qk_params *p, const qk_box *boxes, int32_t nbox,
 int qk_init_patches(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
                     const int32_t domain_n[3], int32_t nghost, int32_t precision) {
   return init_common(out, p, boxes, nbox, domain_n, nghost, precision, nullptr, 1, 0);
+}
+
+int qk_init_level(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,
+                  const int32_t domain_n[3], int32_t nghost, int32_t precision) {
+  for (int d = 0; d < 3; ++d)
+    if (p && (p->bc_lo[d] != QK_BC_PERIODIC || p->bc_hi[d] != QK_BC_PERIODIC)) {
+      g_init_err = "qk_init_level: refinement levels are periodic";
+      return QK_EINVAL;
+    }
+  return init_common(out, p, boxes, nbox, domain_n, nghost, precision, nullptr, 1, 0, 1);
 }
 
 int qk_init_shard(qk_ctx **out, const qk_params *p, const qk_box *boxes, int32_t nbox,

@@ -76,6 +76,53 @@ __device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T f2, T c, T 
   F[3] = cEb * (bfD * fz + (D == 2 ? a : T(0)));
 }
 
+// HLL wavespeed from the diagonal Eddington-tensor elements T_DD of the two
+// cell averages (Sec. 2.2.2): S = chat sqrt(max(Ta, Tb)); sqrt is monotone
+// and correctly rounded, so sqrt(max) == max(sqrt).  T_DD lies in [0, 1]; it
+// is 0 only for a superluminal state with no flux along D.
+template <typename T>
+__device__ __forceinline__ T rad_speed(T Ta, T Tb, T chat) {
+  const T Tm = nn_max(Ta, Tb);
+  return nn_gt(Tm, T(0)) ? chat * psqrt(Tm) : T(0);
+}
+
+// The radiation flux through one face (Sec. 2.2.2): the face states wL, wR
+// (reconstructed E_r and f; `fallback` replaces both by the two cell
+// averages when either has |f| > 1), the wavespeed S, the cells' rho kappa_R
+// for the optical-depth correction, HLL with S_L = -S, S_R = S, and the
+// correction switched off where it would make the energy flux exceed
+// chat max(E_L, E_R).  Shared by the stage kernel and the flux registers of
+// mesh refinement, so both use the same arithmetic.
+template <typename T, int D, int CL, class Fallback>
+__device__ __forceinline__ void rad_face_hll(T wL[4], T wR[4], Fallback fallback, T S, T rka,
+                                             T rkb, T dx, T c, T chat, T hchat_c, T hccc,
+                                             int tau_corr, T out[4]) {
+  T fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
+  T fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
+  if (nn_gt(fL2, T(1)) || nn_gt(fR2, T(1))) {
+    fallback(wL, wR);
+    fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
+    fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
+  }
+  T UL[4], FL[4], UR[4], FR[4];
+  rad_flux_of<T, D, CL>(wL[0], wL[1], wL[2], wL[3], fL2, c, hchat_c, hccc, UL, FL);
+  rad_flux_of<T, D, CL>(wR[0], wR[1], wR[2], wR[3], fR2, c, hchat_c, hccc, UR, FR);
+  T eps = T(1);
+  if (tau_corr) {
+    const T tau = dx * T(0.5) * (rka + rkb);
+    if (nn_gt(tau, T(1))) eps = qrcp(tau);
+  }
+  // HLL with S_L = -S, S_R = S: (F_L + F_R)/2 - (S eps / 2)(U_R - U_L)
+  const T hS = T(0.5) * S;
+  const T hSe = hS * eps;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hSe * (UR[q] - UL[q]);
+  if (nn_gt(T(1), eps) && nn_gt(fabs(out[0]), chat * nn_max(UL[0], UR[0]))) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hS * (UR[q] - UL[q]);
+  }
+}
+
 template <typename T, int D, int NT, int NOWN, int CL>
 __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx, T dx, T c,
                                         T chat, int tau_corr, int rk, T (&acc)[NOWN][4]) {
@@ -117,52 +164,30 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
       wL[q] = sm.rec[2 * q + 1][il];
       wR[q] = sm.rec[2 * q][ir];
     }
-    T fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
-    T fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
     int xa[3] = {cc[0], cc[1], cc[2]}, xb[3] = {cc[0], cc[1], cc[2]};
     xa[D] = f - 1;
     xb[D] = f;
     const int sa = cross_slot(xa[0], xa[1], xa[2]);
     const int sb = cross_slot(xb[0], xb[1], xb[2]);
-    if (nn_gt(fL2, T(1)) || nn_gt(fR2, T(1))) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        wL[q] = sm.prim[q][sa];
-        wR[q] = sm.prim[q][sb];
-      }
-      fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
-      fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
-    }
-    T UL[4], FL[4], UR[4], FR[4];
-    rad_flux_of<T, D, CL>(wL[0], wL[1], wL[2], wL[3], fL2, c, hchat_c, hccc, UL, FL);
-    rad_flux_of<T, D, CL>(wR[0], wR[1], wR[2], wR[3], fR2, c, hchat_c, hccc, UR, FR);
     T S;
     if constexpr (RadSmem<T>::kAB) {
-      // sqrt is monotone and correctly rounded: sqrt(max) == max(sqrt)
       const T fa = sm.prim[1 + D][sa], fb = sm.prim[1 + D][sb];
-      const T Ta = sm.ab[0][sa] + sm.ab[1][sa] * fa * fa;
-      const T Tb = sm.ab[0][sb] + sm.ab[1][sb] * fb * fb;
-      // T_DD lies in [0, 1]; it is 0 only for a superluminal state with no flux along D
-      const T Tm = nn_max(Ta, Tb);
-      S = nn_gt(Tm, T(0)) ? chat * psqrt(Tm) : T(0);
+      S = rad_speed<T>(sm.ab[0][sa] + sm.ab[1][sa] * fa * fa, sm.ab[0][sb] + sm.ab[1][sb] * fb * fb,
+                       chat);
     } else {
       S = chat * max(sm.sq[il], sm.sq[ir]);
     }
-    T eps = T(1);
-    if (tau_corr) {
-      const T tau = dx * T(0.5) * (sm.rk[sa] + sm.rk[sb]);
-      if (nn_gt(tau, T(1))) eps = qrcp(tau);
-    }
-    // HLL with S_L = -S, S_R = S: (F_L + F_R)/2 - (S eps / 2)(U_R - U_L)
-    const T hS = T(0.5) * S;
-    const T hSe = hS * eps;
     T out[4];
+    rad_face_hll<T, D, CL>(
+        wL, wR,
+        [&](T *l, T *r) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hSe * (UR[q] - UL[q]);
-    if (nn_gt(T(1), eps) && nn_gt(fabs(out[0]), chat * nn_max(UL[0], UR[0]))) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hS * (UR[q] - UL[q]);
-    }
+          for (int q = 0; q < 4; ++q) {
+            l[q] = sm.prim[q][sa];
+            r[q] = sm.prim[q][sb];
+          }
+        },
+        S, sm.rk[sa], sm.rk[sb], dx, c, chat, hchat_c, hccc, tau_corr, out);
 #pragma unroll
     for (int q = 0; q < 4; ++q) sm.flux[q][it] = out[q];
   }

@@ -94,10 +94,21 @@ def lib():
     L.qk_set_dirichlet.argtypes = [vp, P(vp), P(vp), vp]
     L.qk_set_source.argtypes = [vp, vp]
     L.qk_set_tile_part.argtypes = [vp, i32]
+    L.qk_init_level.argtypes = [P(vp), P(Params), P(Box), i32, P(i32), i32, i32]
+    L.qk_amr_init.argtypes = [P(vp), vp, vp]
+    L.qk_amr_destroy.argtypes = [vp]
+    L.qk_amr_destroy.restype = None
+    L.qk_amr_last_error.argtypes = [vp]
+    L.qk_amr_last_error.restype = C.c_char_p
+    L.qk_amr_info.argtypes = [vp, P(i64), P(i64), P(i64)]
+    L.qk_amr_interp.argtypes = [vp, P(vp), P(vp), dbl, P(vp), i32, i32, vp]
+    L.qk_amr_register.argtypes = [vp, i32, i32, P(vp), vp, dbl, vp]
+    L.qk_amr_sync.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), vp]
     L.qk_tile_counts.argtypes = [vp, P(i32), P(i32)]
     L.qk_signal_speed.argtypes = [vp, P(vp), P(dbl), vp]
     L.qk_set_timestep.argtypes = [vp, dbl, P(dbl), vp]
-    for f in ("qk_set_tile_part", "qk_tile_counts", "qk_fill_plan", "qk_fill_ghosts_range", "qk_set_dirichlet", "qk_set_source",
+    for f in ("qk_init_level", "qk_amr_init", "qk_amr_info", "qk_amr_interp", "qk_amr_register",
+              "qk_amr_sync", "qk_set_tile_part", "qk_tile_counts", "qk_fill_plan", "qk_fill_ghosts_range", "qk_set_dirichlet", "qk_set_source",
               "qk_init_shard", "qk_halo_info", "qk_halo_pack", "qk_halo_unpack",
               "qk_signal_speed", "qk_set_timestep", "qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_autotune",
               "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
@@ -197,7 +208,8 @@ class Context:
     the whole patch set with this rank's patches placed in its own field
     arrays (see ``shard.rank_layout``)."""
 
-    def __init__(self, layout, params: dict, precision: int = FP64, owner=None, rank: int = 0):
+    def __init__(self, layout, params: dict, precision: int = FP64, owner=None, rank: int = 0,
+                 level: bool = False):
         self._L = lib()
         nb = layout.nbox
         boxes = _boxes(layout)
@@ -207,7 +219,10 @@ class Context:
         self.layout = layout
         h = C.c_void_p()
         self.rank, self.nranks = 0, 1
-        if owner is None:
+        if level:
+            rc = self._L.qk_init_level(C.byref(h), C.byref(self.params), boxes, nb, dom,
+                                       int(layout.ng), int(precision))
+        elif owner is None:
             rc = self._L.qk_init_patches(C.byref(h), C.byref(self.params), boxes, nb, dom,
                                          int(layout.ng), int(precision))
         else:
@@ -369,3 +384,62 @@ class Context:
         i, b = C.c_int32(), C.c_int32()
         self._check(self._L.qk_tile_counts(self._h, C.byref(i), C.byref(b)))
         return int(i.value), int(b.value)
+
+
+def _ptrs9(fields):
+    arr = (C.c_void_p * 9)()
+    for i, f in enumerate(fields):
+        arr[i] = int(f.data_ptr()) if f is not None else None
+    return arr
+
+
+class Amr:
+    """Two refinement levels (wraps qk_amr_init): `coarse` covers the domain,
+    `fine` (a Context made with level=True) refines part of it by 2."""
+
+    def __init__(self, coarse: Context, fine: Context):
+        self._L = lib()
+        self.coarse, self.fine = coarse, fine
+        h = C.c_void_p()
+        rc = self._L.qk_amr_init(C.byref(h), coarse._h, fine._h)
+        if rc != OK:
+            raise QKError(rc, self._L.qk_amr_last_error(None).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.qk_amr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise QKError(rc, self._L.qk_amr_last_error(self._h).decode())
+
+    def info(self):
+        """(fine ghost cells interpolated, coarse-fine faces, coarse cells under the fine region)."""
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self._L.qk_amr_info(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return int(a.value), int(b.value), int(c.value)
+
+    def interp(self, c_old, c_new, alpha, fine_fields, first, stream=None):
+        self._check(self._L.qk_amr_interp(self._h, _ptrs9(c_old), _ptrs9(c_new), float(alpha),
+                                          _ptrs(fine_fields, len(fine_fields)), int(first),
+                                          len(fine_fields), _stream(stream)))
+
+    def register(self, level, kind, fields, rho, weight, stream=None):
+        self._check(self._L.qk_amr_register(self._h, int(level), int(kind),
+                                            _ptrs(fields, len(fields)),
+                                            C.c_void_p(int(rho.data_ptr())) if rho is not None
+                                            else None, float(weight), _stream(stream)))
+
+    def sync(self, cU, cR, fU, fR, stream=None):
+        self._check(self._L.qk_amr_sync(self._h, _ptrs(cU, 5), _ptrs(cR, 4) if cR is not None
+                                        else None, _ptrs(fU, 5),
+                                        _ptrs(fR, 4) if fR is not None else None,
+                                        _stream(stream)))
