@@ -341,6 +341,97 @@ def run_variants(args, steps=5, warmup=3):
     return out
 
 
+def run_precision_report(steps_hydro=10, steps_rhd=20):
+    """Per-field error and conservation drift of the reduced-precision forms at
+    256^3: the hydro and RHD workloads advanced from the same initial state in
+    FP64, FP32-mixed and compensated FP32 (hi + lo per conserved field).  The
+    error of each field is the relative L1 distance to the FP64 result (the
+    FP64 path matches the oracle to 1e-10 per cell; the oracle itself would
+    take hours at this size).  Drift: max over the steps of |total(t) -
+    total(0)| / sum of |terms| for sum rho, sum (E + (c/chat) E_r) and each
+    component of sum (m + F/(c chat)).  Also the cell-updates/s of each form."""
+    import numpy as np
+    import torch
+    from paper_2110_01792_gb300 import qk
+
+    def interior(lay, a):
+        g = lay.ng
+        out = []
+        for b in range(lay.nbox):
+            n = lay.n[b]
+            blk = a[lay.off[b]:lay.off[b] + int(np.prod(n + 2 * g))].reshape(
+                n[2] + 2 * g, n[1] + 2 * g, n[0] + 2 * g)
+            out.append(blk[g:g + n[2], g:g + n[1], g:g + n[0]].ravel())
+        return np.concatenate(out)
+
+    report = {}
+    for name, steps in (("hydro256", steps_hydro), ("rhd256", steps_rhd)):
+        prob = workload(name)
+        lay = prob.layout
+        cr = prob.params["c"] / prob.params["chat"] if prob.R is not None else 0.0
+        icc = 1.0 / (prob.params["c"] * prob.params["chat"]) if prob.R is not None else 0.0
+        init = prob.U + (prob.R or [])
+        mag = {}
+        absint = [np.abs(interior(lay, a)).sum() for a in init]
+        mag["rho"] = absint[0]
+        mag["E_total"] = absint[4] + (cr * absint[5] if prob.R is not None else 0.0)
+        mag["momentum"] = [absint[1 + d] + (icc * absint[6 + d] if prob.R is not None else 0.0)
+                           for d in range(3)]
+        results, entry = {}, {}
+        for form in ("fp64", "fp32", "fp32_compensated"):
+            prec = qk.FP64 if form == "fp64" else qk.FP32_MIXED
+            tdt = torch.float64 if prec == qk.FP64 else torch.float32
+            ctx = qk.Context(lay, prob.params, prec)
+            U = [torch.from_numpy(a).cuda().to(tdt) for a in prob.U]
+            R = None if prob.R is None else [torch.from_numpy(a).cuda().to(tdt) for a in prob.R]
+            lo = None
+            if form == "fp32_compensated":
+                lo = ([torch.from_numpy(a - a.astype(np.float32)).float().cuda() for a in prob.U],
+                      None if R is None else
+                      [torch.from_numpy(a - a.astype(np.float32)).float().cuda() for a in prob.R])
+            sums = [ctx.conserved_sums(U, R, lo=lo)]
+            times = []
+            for _ in range(steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.step(U, R, lo=lo)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+                sums.append(ctx.conserved_sums(U, R, lo=lo))
+            ok = ctx.status()[0] == qk.OK
+            ctx.close()
+            fields = [u.double().cpu().numpy() for u in U + (R or [])]
+            if lo is not None:
+                fields = [a + b.double().cpu().numpy() for a, b in zip(fields, lo[0] + (lo[1] or []))]
+            results[form] = [interior(lay, a) for a in fields]
+            del U, R, lo, fields
+            torch.cuda.empty_cache()
+            S = np.array(sums)
+            d = np.abs(S - S[0]).max(axis=0)
+            entry[form] = {
+                # the first step captures the step graph: timed from the second
+                "cell_updates_per_s": lay.ncells * (steps - 1) / sum(times[1:])
+                if steps > 1 else None,
+                "drift": {"rho": float(d[0] / mag["rho"]),
+                          "E_total": float(d[9] / mag["E_total"]),
+                          "momentum": float(max(d[10 + a] / mag["momentum"][a]
+                                                for a in range(3)))},
+                "status_ok": ok}
+        names = ["rho", "m_x", "m_y", "m_z", "E", "E_r", "F_x", "F_y", "F_z"]
+        ref = results["fp64"]
+        for form in ("fp32", "fp32_compensated"):
+            entry[form]["rel_l1_vs_fp64"] = {
+                names[q]: float(np.abs(results[form][q] - ref[q]).sum() / np.abs(ref[q]).sum())
+                for q in range(len(ref))}
+        entry["steps"] = steps
+        entry["cells"] = lay.ncells
+        report[name] = entry
+        del results, ref
+    return report
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -493,6 +584,7 @@ def run_ours(args):
         return
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(args.precision)
     variants = None if args.no_variants or world > 1 else run_variants(args)
+    precision = None if args.no_variants or world > 1 else run_precision_report()
     nl = launches_per_step(hydro_only, int(prob.params.get("nsub_max", 10)))
     line = {
         "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
@@ -511,6 +603,7 @@ def run_ours(args):
         "nsub_mean": nsub_mean,
         "clocks": clk,
         "variants": variants,
+        "precision_report": precision,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -272,6 +272,25 @@ int qk_timestep(qk_ctx *ctx, void *const hydro[5], double out[4], void *stream);
 int qk_step(qk_ctx *ctx, void *const hydro[5], void *const rad[4], double *dt_out,
             int32_t *nsub_out, void *stream);
 
+/* One full update of a compensated FP32 state (QK_FP32_MIXED contexts only):
+ * every conserved field is held as the unevaluated sum hi + lo of two float
+ * arrays, hydro/rad the hi parts (what the stencils read, exactly as in
+ * qk_step) and hydro_lo/rad_lo the low parts (caller-owned, same layout;
+ * zero for a state that starts as plain floats).  The update is qk_step's,
+ * with the RK combinations accumulated in double-float (every face term dt F/dx
+ * rounded once, identically in both cells sharing the face) and the exchange's
+ * invariants E + (c/chat) E_r and m + F/(c chat) carried to ~2^-48, so that the
+ * periodic conserved totals (qk_conserved_sums_compensated) drift by rounding
+ * at the 1e-14 level instead of the ~1e-11 per step of FP32 storage
+ * (Sec. 2.2's conservative update; not a passage of the paper, a storage
+ * choice).  The first call allocates nine fields of library scratch for the
+ * low parts of the stage-1 results; the launch sequence is captured into its
+ * own CUDA graph per pointer set.  QK_EINVAL for an FP64 or sharded context
+ * or a NULL field. */
+int qk_step_compensated(qk_ctx *ctx, void *const hydro[5], void *const rad[4],
+                        void *const hydro_lo[5], void *const rad_lo[4], double *dt_out,
+                        int32_t *nsub_out, void *stream);
+
 /* The device step record (synchronises `stream`): out[0] = dt, out[1] = N_sub,
  * out[2] = dt_rad, out[3] = max(|v| + c_s) of the last timestep computed;
  * out[4] = radiation substeps and out[5] = timesteps summed since the context
@@ -310,6 +329,12 @@ int qk_set_graph(qk_ctx *ctx, int32_t enable);
  * Synchronises `stream`. */
 int qk_conserved_sums(qk_ctx *ctx, void *const hydro[5], void *const rad[4],
                       double out[QK_NSUMS], void *stream);
+
+/* qk_conserved_sums of a compensated FP32 state (see qk_step_compensated):
+ * each cell contributes hi + lo of every field.  Same output layout. */
+int qk_conserved_sums_compensated(qk_ctx *ctx, void *const hydro[5], void *const rad[4],
+                                  void *const hydro_lo[5], void *const rad_lo[4],
+                                  double out[QK_NSUMS], void *stream);
 
 /* Conservation sums without any GPU allocation.  There is no counterpart in the
  * paper: this serves callers that cannot call cudaMalloc where they need the
@@ -452,6 +477,18 @@ int qk_amr_sync(qk_amr *amr, void *const cU[5], void *const cR[4], void *const f
  * Returns QK_ENOCONV / QK_ENEGATIVE when those bits are set, else QK_OK. */
 int qk_status(qk_ctx *ctx, uint32_t *flags, int64_t *first_bad, int32_t *max_iter,
               int32_t reset, void *stream);
+
+/* The library's FP64 reciprocal and square root, element-wise over n device
+ * doubles x: rcp[i] = 1/x[i] (hardware approximate reciprocal with one
+ * third-order correction) and sqrt_out[i] = sqrt(x[i]) (hardware approximate
+ * reciprocal square root with a second-order correction), the forms the FP64
+ * stage kernels use for the divisions and square roots of Sec. 2.2.1-2.2.2
+ * (HLLC sound speeds, Levermore closure, HLL wavespeed).  Either output may be
+ * NULL.  Valid for positive normal x with a normal reciprocal (and x = 0 for
+ * the square root); each result is meant to lie within one ulp of the IEEE
+ * value.  Asynchronous on `stream`; QK_EINVAL if n < 0 or x is NULL with
+ * n > 0, QK_ECUDA if the launch fails. */
+int qk_eval_math(const double *x, int64_t n, double *rcp, double *sqrt_out, void *stream);
 
 #ifdef __cplusplus
 }

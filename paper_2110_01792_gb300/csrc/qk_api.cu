@@ -333,6 +333,8 @@ template <typename T> static int upload(qk_ctx *c, T **dst, const std::vector<T>
 
 static void release(qk_ctx *c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gexec_c) cudaGraphExecDestroy(c->gexec_c);
+  for (void *s : c->scratch_lo) cudaFree(s);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->d_boxes);
   cudaFree(c->d_tiles);
@@ -355,6 +357,15 @@ static void release(qk_ctx *c) {
   for (void *s : c->scratch) cudaFree(s);
   cudaFree(c->chi);
   if (c->h_buf) cudaFreeHost(c->h_buf);
+}
+
+// Forget the captured step graphs (parameters, launch configurations or
+// modes changed).
+static void drop_graphs(qk_ctx *c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gexec_c) cudaGraphExecDestroy(c->gexec_c);
+  c->gexec = nullptr;
+  c->gexec_c = nullptr;
 }
 
 extern "C" {
@@ -720,10 +731,7 @@ int qk_set_params(qk_ctx *c, const qk_params *p) {
       memcmp(p->bc_hi, c->p.bc_hi, sizeof(p->bc_hi)) != 0)
     return fail(c, QK_EINVAL, "boundary types are fixed when the context is created");
   c->p = *p;
-  if (c->gexec) {
-    cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
-  }
+  drop_graphs(c);
   return QK_OK;
 }
 
@@ -821,10 +829,7 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
   cudaEventDestroy(e1);
   for (void *t : tmp) cudaFree(t);
   if (err != cudaSuccess) return cuda_fail(c, err, "autotune launch");
-  if (c->gexec) {
-    cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
-  }
+  drop_graphs(c);
   if (out_cfg)
     for (int w = 0; w < 4; ++w) out_cfg[w] = c->cfg[w];
   return QK_OK;
@@ -835,20 +840,14 @@ int qk_set_launch_mode(qk_ctx *c, int32_t mode) {
   if (mode != QK_LAUNCH_BATCHED && mode != QK_LAUNCH_PER_PATCH)
     return fail(c, QK_EINVAL, "unknown launch mode %d", mode);
   c->launch_mode = mode;
-  if (c->gexec) {
-    cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
-  }
+  drop_graphs(c);
   return QK_OK;
 }
 
 int qk_set_source(qk_ctx *c, const void *j) {
   if (!c) return QK_EINVAL;
   c->src = j;
-  if (c->gexec) {
-    cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
-  }
+  drop_graphs(c);
   return QK_OK;
 }
 
@@ -998,7 +997,8 @@ int qk_timestep(qk_ctx *c, void *const hydro[5], double out[4], void *stream) {
 // (QK_LAUNCH_BATCHED), or one launch per patch over its own tiles
 // (QK_LAUNCH_PER_PATCH, kept for comparison).
 static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *const *U1,
-                                  void *const *Uo, DtSrc dt, cudaStream_t s) {
+                                  void *const *Uo, DtSrc dt, cudaStream_t s,
+                                  const LoPtrs *lo = nullptr) {
   const Geometry g = geom(c);
   const void *chi = c->p.flattening ? c->chi : nullptr;
   if (chi) {
@@ -1007,57 +1007,67 @@ static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *c
   }
   if (c->launch_mode == QK_LAUNCH_BATCHED || c->part != QK_PART_ALL)
     return launch_hydro_stage(c->fp32, stage, g, c->p, U0, U1, Uo, dt, 0, c->cfg[stage - 1], chi,
-                              s);
+                              s, lo);
   for (int b = 0; b < c->nbox_dev; ++b) {
     Geometry gb = g;
     gb.tiles = c->d_tiles + c->tile_start[b];
     gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
     cudaError_t e = launch_hydro_stage(c->fp32, stage, gb, c->p, U0, U1, Uo, dt, 0,
-                                       c->cfg[stage - 1], chi, s);
+                                       c->cfg[stage - 1], chi, s, lo);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
 static cudaError_t rad_launches(qk_ctx *c, int stage, void *const *R0, void *const *R1,
-                                void *const *Ro, const void *rho, DtSrc dt, cudaStream_t s) {
+                                void *const *Ro, const void *rho, DtSrc dt, cudaStream_t s,
+                                const LoPtrs *lo = nullptr) {
   const Geometry g = geom(c);
   if (c->launch_mode == QK_LAUNCH_BATCHED || c->part != QK_PART_ALL)
-    return launch_rad_stage(c->fp32, stage, g, c->p, R0, R1, Ro, rho, dt, 0, c->cfg[1 + stage], s);
+    return launch_rad_stage(c->fp32, stage, g, c->p, R0, R1, Ro, rho, dt, 0, c->cfg[1 + stage], s,
+                            lo);
   for (int b = 0; b < c->nbox_dev; ++b) {
     Geometry gb = g;
     gb.tiles = c->d_tiles + c->tile_start[b];
     gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
-    cudaError_t e =
-        launch_rad_stage(c->fp32, stage, gb, c->p, R0, R1, Ro, rho, dt, 0, c->cfg[1 + stage], s);
+    cudaError_t e = launch_rad_stage(c->fp32, stage, gb, c->p, R0, R1, Ro, rho, dt, 0,
+                                     c->cfg[1 + stage], s, lo);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-// The launch sequence of one full update (Sec. 2.2 operator split).
-static int enqueue_step(qk_ctx *c, void *const hydro[5], void *const rad[4], cudaStream_t s) {
+// The launch sequence of one full update (Sec. 2.2 operator split).  With
+// hlo (and rlo) the state is compensated: hi + lo per conserved field, the
+// stage-1 results keeping their low parts in the library's scratch_lo.
+static int enqueue_step(qk_ctx *c, void *const hydro[5], void *const rad[4], cudaStream_t s,
+                        void *const *hlo = nullptr, void *const *rlo = nullptr) {
   const Geometry g = geom(c);
-  void *U1[5], *R1[4];
+  void *U1[5], *R1[4], *U1l[5], *R1l[4];
   for (int q = 0; q < 5; ++q) U1[q] = c->scratch[q];
   for (int q = 0; q < 4; ++q) R1[q] = c->scratch[5 + q];
+  for (int q = 0; q < 5; ++q) U1l[q] = c->scratch_lo[q];
+  for (int q = 0; q < 4; ++q) R1l[q] = c->scratch_lo[5 + q];
+  const LoPtrs h1{hlo, nullptr, U1l}, h2{hlo, U1l, hlo};
+  const LoPtrs r1{rlo, nullptr, R1l}, r2{rlo, R1l, rlo};
   const DtSrc dth{c->d_si, 0.0, 0, -1};
   const DtSrc none{nullptr, 0.0, 0, -1};
   QK_CUDA(c, launch_max_speed(c->fp32, g, c->p, hydro, c->d_si, s));
   QK_CUDA(c, launch_timestep(c->p, c->d_si, s));
   QK_CUDA(c, fill(c, hydro, 5, 0, none, s));
-  QK_CUDA(c, hydro_launches(c, 1, hydro, nullptr, U1, dth, s));
+  QK_CUDA(c, hydro_launches(c, 1, hydro, nullptr, U1, dth, s, hlo ? &h1 : nullptr));
   QK_CUDA(c, fill(c, U1, 5, 0, none, s));
-  QK_CUDA(c, hydro_launches(c, 2, hydro, U1, hydro, dth, s));
+  QK_CUDA(c, hydro_launches(c, 2, hydro, U1, hydro, dth, s, hlo ? &h2 : nullptr));
   if (rad && !c->p.hydro_only) {
     QK_CUDA(c, fill(c, hydro, 1, 0, none, s));
     for (int sub = 0; sub < c->p.nsub_max; ++sub) {
       const DtSrc dr{c->d_si, 0.0, 2, sub};
       QK_CUDA(c, fill(c, rad, 4, 5, dr, s));
-      QK_CUDA(c, rad_launches(c, 1, rad, nullptr, R1, hydro[0], dr, s));
+      QK_CUDA(c, rad_launches(c, 1, rad, nullptr, R1, hydro[0], dr, s, rlo ? &r1 : nullptr));
       QK_CUDA(c, fill(c, R1, 4, 5, dr, s));
-      QK_CUDA(c, rad_launches(c, 2, rad, R1, rad, hydro[0], dr, s));
-      QK_CUDA(c, launch_exchange(c->fp32, g, c->p, hydro, rad, c->src, dr, c->d_status, s));
+      QK_CUDA(c, rad_launches(c, 2, rad, R1, rad, hydro[0], dr, s, rlo ? &r2 : nullptr));
+      QK_CUDA(c, launch_exchange(c->fp32, g, c->p, hydro, rad, c->src, dr, c->d_status, s, hlo,
+                                 rlo));
     }
   }
   return QK_OK;
@@ -1111,6 +1121,84 @@ int qk_step(qk_ctx *c, void *const hydro[5], void *const rad[4], double *dt_out,
     QK_CUDA(c, cudaStreamSynchronize(s));
     *nsub_out = (int32_t)c->h_buf[8];
   }
+  return QK_OK;
+}
+
+int qk_step_compensated(qk_ctx *c, void *const hydro[5], void *const rad[4],
+                        void *const hydro_lo[5], void *const rad_lo[4], double *dt_out,
+                        int32_t *nsub_out, void *stream) {
+  if (!c) return QK_EINVAL;
+  if (!c->fp32) return fail(c, QK_EINVAL, "compensated steps need a QK_FP32_MIXED context");
+  int rc = check_fields(c, hydro, 5, "hydro");
+  if (rc) return rc;
+  if ((rc = check_fields(c, hydro_lo, 5, "hydro_lo"))) return rc;
+  if (rad && (rc = check_fields(c, rad, 4, "rad"))) return rc;
+  if (rad && (rc = check_fields(c, rad_lo, 4, "rad_lo"))) return rc;
+  if (c->nranks > 1)
+    return fail(c, QK_EINVAL, "sharded context: compose the step from the stage entry points");
+  if ((rc = need_dirichlet(c))) return rc;
+  for (int f = 0; f < 9; ++f)
+    if (!c->scratch_lo[f]) {
+      cudaError_t e = cudaMalloc(&c->scratch_lo[f], (size_t)c->field_len * c->elem);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(compensation scratch)");
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->use_graph) {
+    void *key[19];
+    for (int q = 0; q < 5; ++q) key[q] = hydro[q];
+    for (int q = 0; q < 4; ++q) key[5 + q] = rad ? rad[q] : nullptr;
+    for (int q = 0; q < 5; ++q) key[9 + q] = hydro_lo[q];
+    for (int q = 0; q < 4; ++q) key[14 + q] = rad ? rad_lo[q] : nullptr;
+    key[18] = (void *)(intptr_t)(rad ? 1 : 0);
+    if (!c->gexec_c || memcmp(key, c->gkey_c, sizeof(key)) != 0) {
+      if (c->gexec_c) {
+        cudaGraphExecDestroy(c->gexec_c);
+        c->gexec_c = nullptr;
+      }
+      QK_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue_step(c, hydro, rad, c->cap_stream, hydro_lo, rad ? rad_lo : nullptr);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+      if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&c->gexec_c, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+      memcpy(c->gkey_c, key, sizeof(key));
+    }
+    QK_CUDA(c, cudaGraphLaunch(c->gexec_c, s));
+  } else {
+    if ((rc = enqueue_step(c, hydro, rad, s, hydro_lo, rad ? rad_lo : nullptr))) return rc;
+  }
+  if (dt_out) QK_CUDA(c, cudaMemcpyAsync(dt_out, &c->d_si->dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (nsub_out) {
+    QK_CUDA(c, cudaMemcpyAsync(c->h_buf + 8, &c->d_si->nsub, sizeof(double), cudaMemcpyDeviceToHost, s));
+    QK_CUDA(c, cudaStreamSynchronize(s));
+    *nsub_out = (int32_t)c->h_buf[8];
+  }
+  return QK_OK;
+}
+
+int qk_conserved_sums_compensated(qk_ctx *c, void *const hydro[5], void *const rad[4],
+                                  void *const hydro_lo[5], void *const rad_lo[4],
+                                  double out[QK_NSUMS], void *stream) {
+  if (!c) return QK_EINVAL;
+  if (!c->fp32) return fail(c, QK_EINVAL, "compensated sums need a QK_FP32_MIXED context");
+  int rc = check_fields(c, hydro, 5, "hydro");
+  if (rc) return rc;
+  if ((rc = check_fields(c, hydro_lo, 5, "hydro_lo"))) return rc;
+  if (rad && (rc = check_fields(c, rad, 4, "rad"))) return rc;
+  if (rad && (rc = check_fields(c, rad_lo, 4, "rad_lo"))) return rc;
+  if (!out) return fail(c, QK_EINVAL, "out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  QK_CUDA(c, launch_sums(c->fp32, geom(c), c->p, hydro, rad, c->d_partials, c->sum_blocks,
+                         c->d_sums, s, hydro_lo, rad ? rad_lo : nullptr));
+  QK_CUDA(c, cudaMemcpyAsync(c->h_buf, c->d_sums, QK_NSUMS * sizeof(double), cudaMemcpyDeviceToHost, s));
+  QK_CUDA(c, cudaStreamSynchronize(s));
+  memcpy(out, c->h_buf, QK_NSUMS * sizeof(double));
   return QK_OK;
 }
 

@@ -154,14 +154,23 @@ __device__ __forceinline__ int newton_refine(const qk_params &p, double Eg0, dou
 // and convergence test (FP32 warm start, then newton_refine); the flux
 // source, momentum and kinetic-energy work in FP32, the new total energy
 // accumulated in FP64 before the final rounding.
+// CP: compensated state (every conserved field hi + lo; UL, RL the lo
+// arrays): E, E_r, m and F are read as hi + lo, the new E and E_r are formed
+// in FP64 from the invariant E + (c/chat) E_r (the kinetic-energy change
+// taken from the FP64 difference of the same two values), and the momentum
+// exchange m + F/(c chat) = const is carried in double-float with a
+// double-float 1/(c chat), so that both invariants hold to ~2^-48.
+template <bool CP>
 __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_params p,
                                                               F5<float> U, F4<float> R,
                                                               const float *src, DtSrc dts,
-                                                              Status *st) {
+                                                              Status *st, F5<float> UL,
+                                                              F4<float> RL) {
   if (skip_substep(dts)) return;
   const double dt = dt_of(dts);
   const double cr = p.c / p.chat;
   const float icc = (float)(1.0 / (p.chat * p.c)), rc = (float)(p.chat / p.c);
+  const float icc_lo = (float)(1.0 / (p.chat * p.c) - (double)icc);
   const double inv_cv = p.eos == QK_EOS_ALPHA_T3 ? 0.0 : 1.0 / p.c_v;
   int my_max = 0;
   unsigned my_flags = 0;
@@ -169,18 +178,26 @@ __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_para
   for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < g.ncells;
        cidx += (long long)gridDim.x * blockDim.x) {
     const long long e = cell_to_elem(g, cidx);
-    float u[5], w[5];
+    float u[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
-    con2prim<float>(u, p.gamma, w);  // w[4] = (gamma-1) E_g with ~48-bit E_g
     const float rho = u[0];
+    float rinv = qrcp(rho);
+    rinv = rinv * fmaf(-rho, rinv, 2.0f);  // one Newton step: ~1 ulp
+    float eg_hi, eg_lo;
+    internal_energy_f32(u, rho, rinv, eg_hi, eg_lo);  // ~48-bit E_g, no EOS round trip
     const float Er0f = R.f[0][e];
     const double rho_d = (double)rho;
-    const double Eg0 = (double)w[4] * (1.0 / (p.gamma - 1.0));
-    const double Er0 = (double)Er0f;
+    double Eg0 = (double)eg_hi + (double)eg_lo;
+    double Er0 = (double)Er0f;
+    float E_lo = 0.0f;
+    if constexpr (CP) {
+      E_lo = UL.f[4][e];
+      Eg0 += (double)E_lo;
+      Er0 += (double)RL.f[0][e];
+    }
     const double kP = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_P * rho_d : p.kappa_P;
     const double k = dt * rho_d * kP * p.chat;
-    const float rinv = qrcp(rho);
     const double inv_rcv = (double)(rinv * (float)inv_cv);
     const double inv_Etot = (double)qrcp((float)(Eg0 + cr * Er0));
     // radiation source S = dt (chat/c) j, carried in the residual's E_r0
@@ -208,18 +225,52 @@ __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_para
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const float F0 = R.f[1 + a][e];
-      const float Fn = F0 * damp;
-      mn[a] = u[1 + a] - (Fn - F0) * icc;
+      if constexpr (CP) {
+        // dF = F0 (damp - 1); F += dF and m -= dF/(c chat), both in double-float
+        float Fl = RL.f[1 + a][e];
+        const float dF = (F0 + Fl) * (damp - 1.0f);
+        float Fh = F0;
+        df_add(Fh, Fl, dF);
+        df_norm(Fh, Fl);
+        R.f[1 + a][e] = Fh;
+        RL.f[1 + a][e] = Fl;
+        const float p1 = __fmul_rn(dF, icc);
+        const float e1 = fmaf(dF, icc, -p1) + dF * icc_lo;
+        float mh = u[1 + a], ml = UL.f[1 + a][e];
+        df_add(mh, ml, -p1);
+        ml = __fsub_rn(ml, e1);
+        df_norm(mh, ml);
+        U.f[1 + a][e] = mh;
+        UL.f[1 + a][e] = ml;
+        mn[a] = mh;
+      } else {
+        const float Fn = F0 * damp;
+        mn[a] = u[1 + a] - (Fn - F0) * icc;
+        R.f[1 + a][e] = Fn;
+        U.f[1 + a][e] = mn[a];
+      }
       ke0 = fmaf(u[1 + a], u[1 + a], ke0);
       ke1 = fmaf(mn[a], mn[a], ke1);
-      R.f[1 + a][e] = Fn;
-      U.f[1 + a][e] = mn[a];
     }
     const float Ekin1 = 0.5f * ke1 * rinv;
-    const float dEkin = 0.5f * (ke1 - ke0) * rinv;
-    U.f[4][e] = (float)(Eg + (double)Ekin1);
-    const double Er_new = Er - (double)(rc * dEkin);
-    R.f[0][e] = (float)Er_new;
+    double Er_new;
+    if constexpr (CP) {
+      // E_new = E_g + E_kin,1; E_r,new = E_r - (chat/c)(E_kin,1 - E_kin,0) with
+      // E_kin,0 = E - E_g0 (the same FP64 values), split into hi + lo
+      const double Ekin0 = ((double)u[4] + (double)E_lo) - Eg0;
+      const double Enew = Eg + (double)Ekin1;
+      Er_new = Er - (p.chat / p.c) * ((double)Ekin1 - Ekin0);
+      const float Eh = (float)Enew, Rh = (float)Er_new;
+      U.f[4][e] = Eh;
+      UL.f[4][e] = (float)(Enew - (double)Eh);
+      R.f[0][e] = Rh;
+      RL.f[0][e] = (float)(Er_new - (double)Rh);
+    } else {
+      const float dEkin = 0.5f * (ke1 - ke0) * rinv;
+      U.f[4][e] = (float)(Eg + (double)Ekin1);
+      Er_new = Er - (double)(rc * dEkin);
+      R.f[0][e] = (float)Er_new;
+    }
     if (!(Eg > 0.0) || !(Er_new > 0.0)) {
       my_flags |= 1u << QK_ENEGATIVE;
       my_bad = min(my_bad, (unsigned long long)e);
@@ -297,7 +348,7 @@ __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, 
 
 cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                             void *const *R, const void *src, DtSrc dt, Status *st,
-                            cudaStream_t s) {
+                            cudaStream_t s, void *const *Ulo, void *const *Rlo) {
   int nsm = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -305,10 +356,18 @@ cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, voi
   int grid = (int)std::min<long long>(want, (long long)nsm * 8);
   if (grid < 1) return cudaSuccess;
   if (fp32) {
-    F5<float> u; F4<float> r;
+    F5<float> u, ul{}; F4<float> r, rl{};
     for (int q = 0; q < 5; ++q) u.f[q] = (float *)U[q];
     for (int q = 0; q < 4; ++q) r.f[q] = (float *)R[q];
-    exchange_kernel_mixed<<<grid, 256, 0, s>>>(g, p, u, r, (const float *)src, dt, st);
+    if (Ulo) {
+      for (int q = 0; q < 5; ++q) ul.f[q] = (float *)Ulo[q];
+      for (int q = 0; q < 4; ++q) rl.f[q] = (float *)Rlo[q];
+      exchange_kernel_mixed<true><<<grid, 256, 0, s>>>(g, p, u, r, (const float *)src, dt, st,
+                                                       ul, rl);
+    } else {
+      exchange_kernel_mixed<false><<<grid, 256, 0, s>>>(g, p, u, r, (const float *)src, dt, st,
+                                                        ul, rl);
+    }
   } else {
     F5<double> u; F4<double> r;
     for (int q = 0; q < 5; ++q) u.f[q] = (double *)U[q];
@@ -565,7 +624,8 @@ constexpr int SUM_NT = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(SUM_NT) sums_kernel(Geometry g, double cr, double icc, F5<T> U,
-                                                      F4<T> R, int has_rad, double *partials) {
+                                                      F4<T> R, int has_rad, double *partials,
+                                                      F5<T> UL, F4<T> RL) {
   DD acc[QK_NSUMS];
 #pragma unroll
   for (int q = 0; q < QK_NSUMS; ++q) acc[q] = DD{0.0, 0.0};
@@ -577,6 +637,15 @@ __global__ void __launch_bounds__(SUM_NT) sums_kernel(Geometry g, double cr, dou
     for (int q = 0; q < 5; ++q) x[q] = (double)U.f[q][e];
 #pragma unroll
     for (int q = 0; q < 4; ++q) x[5 + q] = has_rad ? (double)R.f[q][e] : 0.0;
+    // compensated FP32 state: the value is hi + lo (exact in double)
+    if (UL.f[0]) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) x[q] += (double)UL.f[q][e];
+      if (has_rad) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[5 + q] += (double)RL.f[q][e];
+      }
+    }
     x[9] = x[4] + cr * x[5];
 #pragma unroll
     for (int a = 0; a < 3; ++a) x[10 + a] = x[1 + a] + x[6 + a] * icc;
@@ -610,20 +679,24 @@ __global__ void sums_final_kernel(const double *partials, int nblocks, double vo
 
 cudaError_t launch_sums(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                         void *const *R, double *partials, int nblocks, double *out,
-                        cudaStream_t s) {
+                        cudaStream_t s, void *const *Ulo, void *const *Rlo) {
   const double cr = p.c / p.chat, icc = 1.0 / (p.c * p.chat);
   const double vol = p.dx[0] * p.dx[1] * p.dx[2];
   const int has_rad = R != nullptr;
   if (fp32) {
-    F5<float> u; F4<float> r{};
+    F5<float> u, ul{}; F4<float> r{}, rl{};
     for (int q = 0; q < 5; ++q) u.f[q] = (float *)U[q];
     if (has_rad) for (int q = 0; q < 4; ++q) r.f[q] = (float *)R[q];
-    sums_kernel<float><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials);
+    if (Ulo) {
+      for (int q = 0; q < 5; ++q) ul.f[q] = (float *)Ulo[q];
+      if (has_rad) for (int q = 0; q < 4; ++q) rl.f[q] = (float *)Rlo[q];
+    }
+    sums_kernel<float><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials, ul, rl);
   } else {
-    F5<double> u; F4<double> r{};
+    F5<double> u, ul{}; F4<double> r{}, rl{};
     for (int q = 0; q < 5; ++q) u.f[q] = (double *)U[q];
     if (has_rad) for (int q = 0; q < 4; ++q) r.f[q] = (double *)R[q];
-    sums_kernel<double><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials);
+    sums_kernel<double><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials, ul, rl);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -631,4 +704,27 @@ cudaError_t launch_sums(int fp32, const Geometry &g, const qk_params &p, void *c
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------ arithmetic check ---
+// The FP64 reciprocal and square root that the stage kernels use, applied
+// element-wise, so that callers and tests can compare them with the IEEE
+// operations.
+__global__ void eval_math_kernel(const double *x, long long n, double *rcp, double *sq) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    if (rcp) rcp[i] = frcp(v);
+    if (sq) sq[i] = psqrt(v);
+  }
+}
+
 }  // namespace qk
+
+extern "C" int qk_eval_math(const double *x, int64_t n, double *rcp, double *sqrt_out,
+                            void *stream) {
+  if (n < 0 || (n > 0 && !x)) return QK_EINVAL;
+  if (n == 0) return QK_OK;
+  const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
+  qk::eval_math_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(x, n, rcp, sqrt_out);
+  return cudaGetLastError() == cudaSuccess ? QK_OK : QK_ECUDA;
+}
+

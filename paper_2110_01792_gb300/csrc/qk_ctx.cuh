@@ -62,6 +62,7 @@ struct qk_ctx {
   double *d_sums = nullptr;
   int sum_blocks = 0;
   void *scratch[9] = {};
+  void *scratch_lo[9] = {};  // low parts of the stage-1 results (compensated steps)
   void *chi = nullptr;   // shock-flattening coefficient (one field)
   const void *src = nullptr;  // caller's emissivity field j of the exchange, or none
   size_t elem = 8;
@@ -72,5 +73,7 @@ struct qk_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   void *gkey[10] = {};
+  cudaGraphExec_t gexec_c = nullptr;  // compensated step graph
+  void *gkey_c[19] = {};
   std::string err;
 };

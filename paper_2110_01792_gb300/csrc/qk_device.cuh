@@ -8,19 +8,18 @@
 
 namespace qk {
 
-// FP64 reciprocal: the hardware's approximate reciprocal (PTX
-// rcp.approx.ftz.f64, about 20 correct bits) refined by two Newton-Raphson
-// steps for 1/b, r <- r + r (1 - b r), each doubling the correct bits (about
-// 80 > 53 after two): within an ulp of 1/b for normal b with a normal
-// reciprocal (b = 0 or an infinite b give NaN).  Four FP64 slots against the
-// ~7.5 of an IEEE division on this part.
+// FP64 reciprocal: the hardware's approximate reciprocal r (PTX
+// rcp.approx.ftz.f64, about 20 correct bits, r = (1 - eps)/b) and one
+// third-order correction: with e = 1 - b r = eps (one FMA, exact to rounding),
+// r (1 + e + e^2) = (1 - eps^3)/b, so the relative error drops to ~2^-60 and
+// the result is within an ulp of 1/b after the single rounding of the last FMA
+// (normal b with a normal reciprocal; b = 0 or an infinite b give NaN).
+// Three FP64 slots against the ~7.5 of an IEEE division on this part.
 __device__ __forceinline__ double frcp(double b) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
-  double e = fma(-b, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-b, r, 1.0);
-  return fma(r, e, r);
+  const double e = fma(-b, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 __device__ __forceinline__ double qdiv(double a, double b) { return a * frcp(b); }
 __device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
@@ -35,21 +34,21 @@ __device__ __forceinline__ float qrcp(float b) {
   return r;
 }
 __device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
-// Square root of a positive normal double (no zero, no infinity): the
-// hardware's approximate reciprocal square root y (PTX rsqrt.approx.ftz.f64,
-// about 20 correct bits) gives s = x y, and two Heron corrections
-// s <- s + (y/2)(x - s^2) each square the relative error (measured: within
-// an ulp over [1/3, 4] and wide exponent ranges).  About 5.7 FP64 slots
+// Square root of a positive normal double (no infinity): the hardware's
+// approximate reciprocal square root y (PTX rsqrt.approx.ftz.f64, about 20
+// correct bits) gives s = x y; with e = 1 - s y (one FMA) the exact root is
+// s / sqrt(1 - e) up to the rounding of s, and the binomial series
+// (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + O(e^3) truncated after e^2 leaves a
+// relative error ~(5/16) e^3 ~ 2^-58: within an ulp of sqrt(x).  A zero
+// argument returns itself (the series would give 0 * inf).  Five FP64 slots
 // against 7.6 for the IEEE square root on this part.
 __device__ __forceinline__ double psqrt(double x) {
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  const double hy = 0.5 * y;
-  double s = x * y;
-  double d = fma(-s, s, x);
-  s = fma(hy, d, s);
-  d = fma(-s, s, x);
-  return fma(hy, d, s);
+  const double s = x * y;
+  const double e = fma(-s, y, 1.0);
+  const double r = fma(s, e * fma(e, 0.375, 0.5), s);
+  return (__double_as_longlong(x) << 1) == 0 ? x : r;
 }
 __device__ __forceinline__ float qsqrt(float x) {
   float r;
@@ -81,20 +80,58 @@ __device__ __forceinline__ void con2prim<double>(const double u[5], double gamma
 
 // Error-free transformations (Knuth's TwoSum, FMA TwoProduct) for the FP32
 // path: a value carried as hi + lo holds about 48 significant bits.
+// The operations are the round-to-nearest intrinsics, which the compiler never
+// fuses into an FMA with a neighbouring product (a fused operand would break
+// the identity s + e = a + b that the transform relies on).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = a + b;
-  float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Division, reciprocal and square root: IEEE in FP64; in FP32 the hardware
-// approximations (a few ulp), which the FP32 path's error budget absorbs and
-// which avoid the ~60-instruction IEEE FP32 division sequence.
 // Mixed precision: the internal energy E_g = E - |m|^2/(2 rho) is recovered
 // with error-free transformations on the FP32 pipe (|m|^2 by FMA TwoProduct
 // and TwoSum, the division and the subtraction in hi + lo form), which is as
 // accurate as an FP64 recovery relative to the FP32-stored E and costs no FP64
 // instruction (one FP64 instruction occupies ~64 FP32 issue slots on GB300).
+// Double-float (hi + lo FP32 pair) accumulation for the compensated FP32
+// state: (h, l) += x with the rounding error of h + x kept in l by TwoSum.
+__device__ __forceinline__ void df_add(float &h, float &l, float x) {
+  float s, t;
+  two_sum(h, x, s, t);
+  h = s;
+  l = __fadd_rn(l, t);
+}
+// Renormalise (h, l) so that h is the FP32 rounding of h + l.
+__device__ __forceinline__ void df_norm(float &h, float &l) {
+  float s, t;
+  two_sum(h, l, s, t);
+  h = s;
+  l = t;
+}
+
+// Internal energy E_g = E - |m|^2/(2 rho) of an FP32 state as an unevaluated
+// sum hi + lo (about 48 significant bits), from the velocity reciprocal `inv`
+// (~1 ulp of 1/rho).
+__device__ __forceinline__ void internal_energy_f32(const float u[5], float rho, float inv,
+                                                    float &hi, float &lo) {
+  const float px = __fmul_rn(u[1], u[1]), py = __fmul_rn(u[2], u[2]), pz = __fmul_rn(u[3], u[3]);
+  float ex = fmaf(u[1], u[1], -px), ey = fmaf(u[2], u[2], -py), ez = fmaf(u[3], u[3], -pz);
+  float s1, t1, s2, t2;
+  two_sum(px, py, s1, t1);
+  two_sum(s1, pz, s2, t2);
+  const float l2 = ((t1 + t2) + (ex + ey)) + ez;
+  // q = (s2 + l2) / rho as qh + ql
+  const float qh = __fmul_rn(s2, inv);
+  const float r = fmaf(-qh, rho, s2) + l2;
+  const float ql = r * inv;
+  // E_g = E - (qh + ql)/2
+  float d, dl;
+  two_sum(u[4], __fmul_rn(-0.5f, qh), d, dl);
+  hi = d;
+  lo = dl - 0.5f * ql;
+}
+
 template <>
 __device__ __forceinline__ void con2prim<float>(const float u[5], double gamma, float w[5]) {
   const float rho = u[0];
@@ -104,21 +141,9 @@ __device__ __forceinline__ void con2prim<float>(const float u[5], double gamma, 
   w[1] = u[1] * inv;
   w[2] = u[2] * inv;
   w[3] = u[3] * inv;
-  float px = u[1] * u[1], py = u[2] * u[2], pz = u[3] * u[3];
-  float ex = fmaf(u[1], u[1], -px), ey = fmaf(u[2], u[2], -py), ez = fmaf(u[3], u[3], -pz);
-  float s1, t1, s2, t2;
-  two_sum(px, py, s1, t1);
-  two_sum(s1, pz, s2, t2);
-  const float lo = ((t1 + t2) + (ex + ey)) + ez;
-  // q = (s2 + lo) / rho as qh + ql
-  const float qh = s2 * inv;
-  const float r = fmaf(-qh, rho, s2) + lo;
-  const float ql = r * inv;
-  // E_g = E - (qh + ql)/2
-  float d, dl;
-  two_sum(u[4], -0.5f * qh, d, dl);
-  const float Eg = d + (dl - 0.5f * ql);
-  w[4] = (float)(gamma - 1.0) * Eg;
+  float hi, lo;
+  internal_energy_f32(u, rho, inv, hi, lo);
+  w[4] = (float)(gamma - 1.0) * (hi + lo);
 }
 
 // PPM reconstruction of one cell from the stencil s0..s4 = q_{i-2..i+2}
@@ -182,8 +207,25 @@ __device__ __forceinline__ float nn_max(float a, float b) { return fmaxf(a, b); 
 __device__ __forceinline__ double nn_min(double a, double b) { return nn_gt(a, b) ? b : a; }
 __device__ __forceinline__ float nn_min(float a, float b) { return fminf(a, b); }
 
-// FP64 PPM with the limiter's min/max and order tests on the integer pipe:
-// the same values as ppm<double> except possibly the sign of a zero.
+// Product sign tests of finite doubles on the integer pipe: a b > 0 exactly
+// when both are nonzero with equal sign bits (a product that underflows to
+// zero, |a b| < 2^-1074, counts here as positive).
+__device__ __forceinline__ bool dsame_nz(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return (x ^ y) >= 0 && (x << 1) != 0 && (y << 1) != 0;
+}
+
+// FP64 PPM with the limiter's min/max and every order test on the integer
+// pipe, and the tests rewritten to need fewer FP64 operations:
+// - extremum, (qR - q)(q - qL) <= 0: a sign test of the two differences;
+// - MC slope: half of sign * min(2|dm|, 2|dp|, |dm + dp|/2) is
+//   sign * min(|dm|, |dp|, |dm + dp|/4) exactly (scaling by 2 is exact);
+// - CW84 overshoot, with d = qR - qL and q6 = 6 (q - (qL + qR)/2):
+//   d q6 > d^2  <=>  d (l' - qL) > 0  with l' = 3 q - 2 qR, and
+//   -d^2 > d q6 <=>  d (qR - r') > 0  with r' = 3 q - 2 qL
+//   (expand d q6 -+ d^2); at the tie l' = qL (r' = qR), so a decision that
+//   rounding flips moves the result only by rounding.
+// The values equal ppm<double>'s bit for bit except at such ties.
 template <>
 __device__ __forceinline__ void ppm<double>(double s0, double s1, double s2, double s3,
                                             double s4, double &qL, double &qR) {
@@ -194,28 +236,29 @@ __device__ __forceinline__ void ppm<double>(double s0, double s1, double s2, dou
   const long long klo = min(k1, min(k2, k3)), khi = max(k1, max(k2, k3));
   double l = dunkey(min(max(dkey(fL), klo), khi));
   double r = dunkey(min(max(dkey(fR), klo), khi));
-  if (dle0((r - s2) * (s2 - l))) {
+  if (!dsame_nz(r - s2, s2 - l)) {
     const double dm = s2 - s1, dp = s3 - s2;
-    double slope = 0.0;
-    if (dgt0(dm * dp)) {
+    double h = 0.0;  // half the MC slope
+    if (dsame_nz(dm, dp)) {
       // positive doubles order like their bit patterns
-      const long long a = __double_as_longlong(2.0 * fabs(dm));
-      const long long b = __double_as_longlong(2.0 * fabs(dp));
-      const long long c = __double_as_longlong(0.5 * fabs(dm + dp));
+      const long long a = __double_as_longlong(fabs(dm));
+      const long long b = __double_as_longlong(fabs(dp));
+      const long long c = __double_as_longlong(0.25 * fabs(dm + dp));
       const long long m = min(a, min(b, c));
       const long long sign = __double_as_longlong(dp) & (long long)0x8000000000000000ULL;
-      slope = __longlong_as_double(m | sign);
+      h = __longlong_as_double(m | sign);
     }
-    l = s2 - 0.5 * slope;
-    r = s2 + 0.5 * slope;
+    l = s2 - h;
+    r = s2 + h;
   } else {
+    const double t3 = 3.0 * s2;
     const double d = r - l;
-    const double q6 = 6.0 * (s2 - 0.5 * (l + r));
-    const long long kdq = dkey(d * q6), kdd = dkey(d * d);
-    if (kdq > kdd) {
-      l = 3.0 * s2 - 2.0 * r;
-    } else if (dkey(-(d * d)) > kdq) {
-      r = 3.0 * s2 - 2.0 * l;
+    const double ln = fma(-2.0, r, t3);
+    if (dsame_nz(d, ln - l)) {
+      l = ln;
+    } else {
+      const double rn = fma(-2.0, l, t3);
+      if (dsame_nz(d, r - rn)) r = rn;
     }
   }
   qL = l;
@@ -258,7 +301,7 @@ __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm
   const T rR = wR[0], uR = wR[1 + D], aR_ = wR[1 + A], bR = wR[1 + B], pR = wR[4];
   const T EL = pL * gm1inv + T(0.5) * rL * (uL * uL + (aL_ * aL_ + bL * bL));
   const T ER = pR * gm1inv + T(0.5) * rR * (uR * uR + (aR_ * aR_ + bR * bR));
-  const T cL = qsqrt(qdiv(gamma * pL, rL)), cR = qsqrt(qdiv(gamma * pR, rR));
+  const T cL = psqrt(qdiv(gamma * pL, rL)), cR = psqrt(qdiv(gamma * pR, rR));
   const T abar = T(0.5) * (cL + cR), rbar = T(0.5) * (rL + rR);
   const T ppvrs = T(0.5) * (pL + pR) - T(0.5) * (uR - uL) * rbar * abar;
   const T ps = max(T(0), ppvrs);
@@ -304,7 +347,7 @@ __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm
 // (5 + 2 s)(5 - 2 s) = 3 (3 + 4 fc^2), chi = (3 + 4 fc^2)/(5 + 2 s) = (5 - 2 s)/3,
 // hence
 //   a = (1 - chi)/2 = (s - 1)/3,
-//   b = (3 chi - 1)/(2 |f|^2) = (2 - s)/|f|^2 = 3/(2 + s)   for |f| <= 1
+//   b = (3 chi - 1)/(2 |f|^2) = (2 - s)/|f|^2 = 3/(2 + s) = 1/(a + 1)   for |f| <= 1
 // (2 - s = 3 |f|^2/(2 + s)), and a = 0, b = 1/|f|^2 beyond (fc = 1, chi = 1).
 // One square root and one reciprocal, free of cancellation at small |f|.
 template <typename T>
@@ -315,8 +358,8 @@ __device__ __forceinline__ void levermore_ab_f2(T f2, T &a, T &b) {
     return;
   }
   const T s = psqrt(T(4) - T(3) * f2);  // argument in [1, 4]
-  a = (s - T(1)) * T(1.0 / 3.0);
-  b = T(3) * qrcp(T(2) + s);
+  a = fma(s, T(1.0 / 3.0), T(-1.0 / 3.0));
+  b = qrcp(a + T(1));                    // 3/(2 + s) = 1/(a + 1)
 }
 
 // The same coefficients for every closure of Sec. 2.2.2, selected at compile

@@ -15,11 +15,11 @@ template <typename T> struct HydroSmem {
   T flux[5][NFLUX];    // per face: mass, momentum x/y/z, energy
 };
 
-template <typename T, int D, int NT, int NOWN>
+template <typename T, int D, int NT, int NOWN, bool CP>
 __device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T inv_dx, T gamma,
                                           T gm1inv, T g1, int rk, const T *chi,
                                           const DevBox &bx, int ng, int x0, int y0, int z0,
-                                          T (&acc)[NOWN][5]) {
+                                          T (&acc)[NOWN][5], T (&accl)[NOWN][5], T cdt) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
   // Phase A: reconstruction of every needed position of every line along D.
   for (int it = threadIdx.x; it < NREC; it += NT) {
@@ -80,16 +80,28 @@ __device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T in
     // item_index for faces takes the face number as the position
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      T dv = (sm.flux[q][hi] - sm.flux[q][lo]) * inv_dx;
-      acc[m][q] = (D == 0) ? dv : acc[m][q] + dv;
+      if constexpr (CP) {
+        // compensated state: (acc, accl) -= dt (F_hi - F_lo) / dx exactly,
+        // each face term dt F / dx rounded once, identically in both cells
+        // that share the face, so that the face terms cancel in the sum
+        df_add(acc[m][q], accl[m][q], -__fmul_rn(cdt, sm.flux[q][hi]));
+        df_add(acc[m][q], accl[m][q], __fmul_rn(cdt, sm.flux[q][lo]));
+      } else {
+        T dv = (sm.flux[q][hi] - sm.flux[q][lo]) * inv_dx;
+        acc[m][q] = (D == 0) ? dv : acc[m][q] + dv;
+      }
     }
   }
 }
 
-template <typename T, int STAGE, int NT>
+// CP (FP32 only): compensated state, every conserved field held as hi + lo
+// (L0, L1, Lo the lo arrays of U0, U1, Uo); the stencil reads hi only, the
+// update is accumulated in double-float so that the face terms telescope.
+template <typename T, int STAGE, int NT, bool CP>
 __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p, F5<T> U0,
                                                          F5<T> U1, F5<T> Uo, DtSrc dts, int sched,
-                                                         const T *chi) {
+                                                         const T *chi, F5<T> L0, F5<T> L1,
+                                                         F5<T> Lo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   HydroSmem<T> &sm = *reinterpret_cast<HydroSmem<T> *>(smem_raw);
   constexpr int NOWN = NCORE / NT;
@@ -115,7 +127,7 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
     const DevBox b = g.boxes[tl.box];
     const int v[3] = {min(TS, b.n[0] - tl.x0), min(TS, b.n[1] - tl.y0), min(TS, b.n[2] - tl.z0)};
     // ---- load: conserved -> primitive into shared memory ----
-    T own[NOWN][5];
+    T own[NOWN][5], ownl[NOWN][5];
 #pragma unroll
     for (int m = 0; m < NOWN; ++m) {
       int s = threadIdx.x + m * NT;
@@ -131,6 +143,12 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
         own[m][q] = u[q];
         sm.prim[q][s] = w[q];
       }
+      if constexpr (CP) {
+        if (i < v[0] && j < v[1] && k < v[2]) {
+#pragma unroll
+          for (int q = 0; q < 5; ++q) ownl[m][q] = (STAGE == 1 ? L0 : L1).f[q][e];
+        }
+      }
     }
     for (int s = NCORE + threadIdx.x; s < NCROSS; s += NT) {
       int i, j, k;
@@ -145,13 +163,22 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
       for (int q = 0; q < 5; ++q) sm.prim[q][s] = w[q];
     }
     __syncthreads();
-    T acc[NOWN][5];
-    hydro_dir<T, 0, NT, NOWN>(sm, v, inv_dx[0], gamma, gm1inv, g1, p.recon, chi, b, g.ng,
-                                tl.x0, tl.y0, tl.z0, acc);
-    hydro_dir<T, 1, NT, NOWN>(sm, v, inv_dx[1], gamma, gm1inv, g1, p.recon, chi, b, g.ng,
-                                tl.x0, tl.y0, tl.z0, acc);
-    hydro_dir<T, 2, NT, NOWN>(sm, v, inv_dx[2], gamma, gm1inv, g1, p.recon, chi, b, g.ng,
-                                tl.x0, tl.y0, tl.z0, acc);
+    T acc[NOWN][5], accl[NOWN][5];
+    if constexpr (CP) {
+#pragma unroll
+      for (int m = 0; m < NOWN; ++m)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          acc[m][q] = own[m][q];
+          accl[m][q] = ownl[m][q];
+        }
+    }
+    hydro_dir<T, 0, NT, NOWN, CP>(sm, v, inv_dx[0], gamma, gm1inv, g1, p.recon, chi, b, g.ng,
+                                  tl.x0, tl.y0, tl.z0, acc, accl, dt * inv_dx[0]);
+    hydro_dir<T, 1, NT, NOWN, CP>(sm, v, inv_dx[1], gamma, gm1inv, g1, p.recon, chi, b, g.ng,
+                                  tl.x0, tl.y0, tl.z0, acc, accl, dt * inv_dx[1]);
+    hydro_dir<T, 2, NT, NOWN, CP>(sm, v, inv_dx[2], gamma, gm1inv, g1, p.recon, chi, b, g.ng,
+                                  tl.x0, tl.y0, tl.z0, acc, accl, dt * inv_dx[2]);
     // ---- RK2-SSP combination for the owned cells ----
 #pragma unroll
     for (int m = 0; m < NOWN; ++m) {
@@ -161,12 +188,28 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
       long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
-        T L = -acc[m][q];
-        if (STAGE == 1) {
-          Uo.f[q][e] = own[m][q] + dt * L;
+        if constexpr (CP) {
+          // (acc, accl) = U^s - dt div F; stage 2 averages it with U^0
+          T h = acc[m][q], l = accl[m][q];
+          if (STAGE == 2) {
+            df_add(h, l, U0.f[q][e]);
+            l = __fadd_rn(l, L0.f[q][e]);
+          }
+          df_norm(h, l);
+          if (STAGE == 2) {
+            h *= T(0.5);
+            l *= T(0.5);
+          }
+          Uo.f[q][e] = h;
+          Lo.f[q][e] = l;
         } else {
-          T u0 = U0.f[q][e];
-          Uo.f[q][e] = T(0.5) * u0 + T(0.5) * (own[m][q] + dt * L);
+          T L = -acc[m][q];
+          if (STAGE == 1) {
+            Uo.f[q][e] = own[m][q] + dt * L;
+          } else {
+            T u0 = U0.f[q][e];
+            Uo.f[q][e] = T(0.5) * u0 + T(0.5) * (own[m][q] + dt * L);
+          }
         }
       }
     }
@@ -174,18 +217,23 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
   }
 }
 
-template <typename T, int STAGE, int NT>
+template <typename T, int STAGE, int NT, bool CP>
 static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const *U0,
                               void *const *U1, void *const *Uo, DtSrc dt, int grid, int sched,
-                              const void *chi, cudaStream_t s) {
-  F5<T> a, b, c;
+                              const void *chi, const LoPtrs &lo, cudaStream_t s) {
+  F5<T> a, b, c, l0{}, l1{}, lo_{};
   for (int q = 0; q < 5; ++q) {
     a.f[q] = (T *)U0[q];
     b.f[q] = U1 ? (T *)U1[q] : nullptr;
     c.f[q] = (T *)Uo[q];
+    if (CP) {
+      l0.f[q] = (T *)lo.l0[q];
+      l1.f[q] = lo.l1 ? (T *)lo.l1[q] : nullptr;
+      lo_.f[q] = (T *)lo.lo[q];
+    }
   }
   int smem = (int)sizeof(HydroSmem<T>);
-  auto kern = hydro_stage_kernel<T, STAGE, NT>;
+  auto kern = hydro_stage_kernel<T, STAGE, NT, CP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   if (grid <= 0) {
@@ -197,30 +245,35 @@ static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const
   }
   if (grid > g.ntiles) grid = g.ntiles;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, dt, sched, (const T *)chi);
+  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, dt, sched, (const T *)chi, l0, l1, lo_);
   return cudaGetLastError();
 }
 
-template <typename T, int STAGE>
+template <typename T, int STAGE, bool CP>
 static cudaError_t launch_nt(const Geometry &g, const qk_params &p, void *const *U0,
                              void *const *U1, void *const *Uo, DtSrc dt, int grid, int cfg,
-                             const void *chi, cudaStream_t s) {
+                             const void *chi, const LoPtrs &lo, cudaStream_t s) {
   const int sched = cfg_sched(cfg);
   switch (cfg_threads(cfg)) {
-    case 128: return launch_one<T, STAGE, 128>(g, p, U0, U1, Uo, dt, grid, sched, chi, s);
-    case 512: return launch_one<T, STAGE, 512>(g, p, U0, U1, Uo, dt, grid, sched, chi, s);
-    default: return launch_one<T, STAGE, 256>(g, p, U0, U1, Uo, dt, grid, sched, chi, s);
+    case 128: return launch_one<T, STAGE, 128, CP>(g, p, U0, U1, Uo, dt, grid, sched, chi, lo, s);
+    case 512: return launch_one<T, STAGE, 512, CP>(g, p, U0, U1, Uo, dt, grid, sched, chi, lo, s);
+    default: return launch_one<T, STAGE, 256, CP>(g, p, U0, U1, Uo, dt, grid, sched, chi, lo, s);
   }
 }
 
 cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                                void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
-                               int grid, int cfg, const void *chi, cudaStream_t s) {
+                               int grid, int cfg, const void *chi, cudaStream_t s,
+                               const LoPtrs *lo) {
+  if (fp32 && lo)
+    return stage == 1 ? launch_nt<float, 1, true>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s)
+                      : launch_nt<float, 2, true>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s);
+  const LoPtrs none{};
   if (fp32)
-    return stage == 1 ? launch_nt<float, 1>(g, p, U0, U1, Uout, dt, grid, cfg, chi, s)
-                      : launch_nt<float, 2>(g, p, U0, U1, Uout, dt, grid, cfg, chi, s);
-  return stage == 1 ? launch_nt<double, 1>(g, p, U0, U1, Uout, dt, grid, cfg, chi, s)
-                    : launch_nt<double, 2>(g, p, U0, U1, Uout, dt, grid, cfg, chi, s);
+    return stage == 1 ? launch_nt<float, 1, false>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s)
+                      : launch_nt<float, 2, false>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s);
+  return stage == 1 ? launch_nt<double, 1, false>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s)
+                    : launch_nt<double, 2, false>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s);
 }
 
 // ------------------------------------------------------------- flattening ---

@@ -210,17 +210,29 @@ constexpr int cfg_threads(int cfg) { return cfg & 0xffff; }
 constexpr int cfg_sched(int cfg) { return (cfg >> 16) & 1; }
 constexpr int kDefaultCfg = cfg_make(256, 0);
 
+// Low parts of a compensated FP32 state (hi + lo per conserved field): those
+// of the stage input U0 (R0), of the stage-1 result U1 (R1, stage 2 only) and
+// of the output.  A null LoPtrs* selects the plain kernels.
+struct LoPtrs {
+  void *const *l0;
+  void *const *l1;
+  void *const *lo;
+};
+
 cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                                void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
-                               int grid, int cfg, const void *chi, cudaStream_t s);
+                               int grid, int cfg, const void *chi, cudaStream_t s,
+                               const LoPtrs *lo = nullptr);
 cudaError_t launch_flatten(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                            void *chi, cudaStream_t s);
 cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                              void *const *R0, void *const *R1, void *const *Rout,
-                             const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s);
+                             const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s,
+                             const LoPtrs *lo = nullptr);
 cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                             void *const *R, const void *src, DtSrc dt, Status *st,
-                            cudaStream_t s);
+                            cudaStream_t s, void *const *Ulo = nullptr,
+                            void *const *Rlo = nullptr);
 cudaError_t launch_max_speed(int fp32, const Geometry &g, const qk_params &p,
                              void *const *U, StepInfo *si, cudaStream_t s);
 cudaError_t launch_halo(int fp32, int pack, const Copy *copies, const Chunk *chunks, int nchunks,
@@ -231,7 +243,7 @@ cudaError_t launch_ghost_fill(int fp32, const Copy *copies, const Chunk *chunks,
                               void *const *fields, int nf, int first, DtSrc pred, cudaStream_t s);
 cudaError_t launch_sums(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                         void *const *R, double *partials, int nblocks, double *out,
-                        cudaStream_t s);
+                        cudaStream_t s, void *const *Ulo = nullptr, void *const *Rlo = nullptr);
 int hydro_smem_bytes(int fp32);
 int rad_smem_bytes(int fp32);
 cudaError_t stage_kernel_setup(int fp32);

@@ -7,28 +7,29 @@ namespace qk {
 
 extern template cudaError_t launch_rad_closure<QK_CLOSURE_MINERBO>(
     int, int, const Geometry &, const qk_params &, void *const *, void *const *, void *const *,
-    const void *, DtSrc, int, int, cudaStream_t);
+    const void *, DtSrc, int, int, cudaStream_t, const LoPtrs *);
 extern template cudaError_t launch_rad_closure<QK_CLOSURE_EDDINGTON>(
     int, int, const Geometry &, const qk_params &, void *const *, void *const *, void *const *,
-    const void *, DtSrc, int, int, cudaStream_t);
+    const void *, DtSrc, int, int, cudaStream_t, const LoPtrs *);
 
 template cudaError_t launch_rad_closure<QK_CLOSURE_LEVERMORE>(
     int, int, const Geometry &, const qk_params &, void *const *, void *const *, void *const *,
-    const void *, DtSrc, int, int, cudaStream_t);
+    const void *, DtSrc, int, int, cudaStream_t, const LoPtrs *);
 
 cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                              void *const *R0, void *const *R1, void *const *Rout,
-                             const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s) {
+                             const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s,
+                             const LoPtrs *lo) {
   switch (p.closure) {
     case QK_CLOSURE_MINERBO:
       return launch_rad_closure<QK_CLOSURE_MINERBO>(fp32, stage, g, p, R0, R1, Rout, rho, dt, grid,
-                                                    cfg, s);
+                                                    cfg, s, lo);
     case QK_CLOSURE_EDDINGTON:
       return launch_rad_closure<QK_CLOSURE_EDDINGTON>(fp32, stage, g, p, R0, R1, Rout, rho, dt,
-                                                      grid, cfg, s);
+                                                      grid, cfg, s, lo);
     default:
       return launch_rad_closure<QK_CLOSURE_LEVERMORE>(fp32, stage, g, p, R0, R1, Rout, rho, dt,
-                                                      grid, cfg, s);
+                                                      grid, cfg, s, lo);
   }
 }
 

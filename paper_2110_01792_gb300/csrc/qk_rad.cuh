@@ -77,9 +77,10 @@ __device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T f2, T c, T 
 }
 
 // HLL wavespeed from the diagonal Eddington-tensor elements T_DD of the two
-// cell averages (Sec. 2.2.2): S = chat sqrt(max(Ta, Tb)); sqrt is monotone
-// and correctly rounded, so sqrt(max) == max(sqrt).  T_DD lies in [0, 1]; it
-// is 0 only for a superluminal state with no flux along D.
+// cell averages (Sec. 2.2.2): S = chat sqrt(max(Ta, Tb)), equal to chat
+// max(sqrt(Ta), sqrt(Tb)) since the square root is monotone (within an ulp:
+// psqrt).  T_DD lies in [0, 1]; it is 0 only for a superluminal state with no
+// flux along D.
 template <typename T>
 __device__ __forceinline__ T rad_speed(T Ta, T Tb, T chat) {
   const T Tm = nn_max(Ta, Tb);
@@ -123,9 +124,10 @@ __device__ __forceinline__ void rad_face_hll(T wL[4], T wR[4], Fallback fallback
   }
 }
 
-template <typename T, int D, int NT, int NOWN, int CL>
+template <typename T, int D, int NT, int NOWN, int CL, bool CP>
 __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx, T dx, T c,
-                                        T chat, int tau_corr, int rk, T (&acc)[NOWN][4]) {
+                                        T chat, int tau_corr, int rk, T (&acc)[NOWN][4],
+                                        T (&accl)[NOWN][4], T cdt) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
   const T hccc = T(0.5) * c * chat;
   const T hchat_c = T(0.5) * chat / c;
@@ -201,16 +203,25 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
     int hi = item_index<D>(cc[D] + 1, cc[0], cc[1], cc[2], NFACE);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      T dv = (sm.flux[q][hi] - sm.flux[q][lo]) * inv_dx;
-      acc[m][q] = (D == 0) ? dv : acc[m][q] + dv;
+      if constexpr (CP) {
+        // compensated state: face terms dt F / dx rounded once per face
+        df_add(acc[m][q], accl[m][q], -__fmul_rn(cdt, sm.flux[q][hi]));
+        df_add(acc[m][q], accl[m][q], __fmul_rn(cdt, sm.flux[q][lo]));
+      } else {
+        T dv = (sm.flux[q][hi] - sm.flux[q][lo]) * inv_dx;
+        acc[m][q] = (D == 0) ? dv : acc[m][q] + dv;
+      }
     }
   }
 }
 
-template <typename T, int STAGE, int NT, int CL>
+// CP (FP32 only): compensated state hi + lo (L0, L1, Lo the lo arrays of R0,
+// R1, Ro), as in the hydro stage.
+template <typename T, int STAGE, int NT, int CL, bool CP>
 __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, F4<T> R0,
                                                        F4<T> R1, F4<T> Ro, const T *rho,
-                                                       DtSrc dts, int sched) {
+                                                       DtSrc dts, int sched, F4<T> L0, F4<T> L1,
+                                                       F4<T> Lo) {
   if (skip_substep(dts)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RadSmem<T> &sm = *reinterpret_cast<RadSmem<T> *>(smem_raw);
@@ -234,7 +245,7 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
     const Tile tl = g.tiles[t];
     const DevBox b = g.boxes[tl.box];
     const int v[3] = {min(TS, b.n[0] - tl.x0), min(TS, b.n[1] - tl.y0), min(TS, b.n[2] - tl.z0)};
-    T own[NOWN][4];
+    T own[NOWN][4], ownl[NOWN][4];
 #pragma unroll
     for (int m = 0; m < NOWN; ++m) {
       int s = threadIdx.x + m * NT;
@@ -247,6 +258,12 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
       load_slot<T, CL>(sm, s, u, c, rho[e], p, i, j, k, v);
 #pragma unroll
       for (int q = 0; q < 4; ++q) own[m][q] = u[q];
+      if constexpr (CP) {
+        if (i < v[0] && j < v[1] && k < v[2]) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ownl[m][q] = (STAGE == 1 ? L0 : L1).f[q][e];
+        }
+      }
     }
     for (int s = NCORE + threadIdx.x; s < NCROSS; s += NT) {
       int i, j, k;
@@ -259,10 +276,22 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
       load_slot<T, CL>(sm, s, u, c, rho[e], p, i, j, k, v);
     }
     __syncthreads();
-    T acc[NOWN][4];
-    rad_dir<T, 0, NT, NOWN, CL>(sm, v, inv_dx[0], dx[0], c, chat, p.tau_correction, p.recon, acc);
-    rad_dir<T, 1, NT, NOWN, CL>(sm, v, inv_dx[1], dx[1], c, chat, p.tau_correction, p.recon, acc);
-    rad_dir<T, 2, NT, NOWN, CL>(sm, v, inv_dx[2], dx[2], c, chat, p.tau_correction, p.recon, acc);
+    T acc[NOWN][4], accl[NOWN][4];
+    if constexpr (CP) {
+#pragma unroll
+      for (int m = 0; m < NOWN; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[m][q] = own[m][q];
+          accl[m][q] = ownl[m][q];
+        }
+    }
+    rad_dir<T, 0, NT, NOWN, CL, CP>(sm, v, inv_dx[0], dx[0], c, chat, p.tau_correction, p.recon,
+                                    acc, accl, dt * inv_dx[0]);
+    rad_dir<T, 1, NT, NOWN, CL, CP>(sm, v, inv_dx[1], dx[1], c, chat, p.tau_correction, p.recon,
+                                    acc, accl, dt * inv_dx[1]);
+    rad_dir<T, 2, NT, NOWN, CL, CP>(sm, v, inv_dx[2], dx[2], c, chat, p.tau_correction, p.recon,
+                                    acc, accl, dt * inv_dx[2]);
 #pragma unroll
     for (int m = 0; m < NOWN; ++m) {
       int s = threadIdx.x + m * NT;
@@ -271,30 +300,50 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
       long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        T L = -acc[m][q];
-        if (STAGE == 1) {
-          Ro.f[q][e] = own[m][q] + dt * L;
+        if constexpr (CP) {
+          T h = acc[m][q], l = accl[m][q];
+          if (STAGE == 2) {
+            df_add(h, l, R0.f[q][e]);
+            l = __fadd_rn(l, L0.f[q][e]);
+          }
+          df_norm(h, l);
+          if (STAGE == 2) {
+            h *= T(0.5);
+            l *= T(0.5);
+          }
+          Ro.f[q][e] = h;
+          Lo.f[q][e] = l;
         } else {
-          T u0 = R0.f[q][e];
-          Ro.f[q][e] = T(0.5) * u0 + T(0.5) * (own[m][q] + dt * L);
+          T L = -acc[m][q];
+          if (STAGE == 1) {
+            Ro.f[q][e] = own[m][q] + dt * L;
+          } else {
+            T u0 = R0.f[q][e];
+            Ro.f[q][e] = T(0.5) * u0 + T(0.5) * (own[m][q] + dt * L);
+          }
         }
       }
     }
   }
 }
 
-template <typename T, int STAGE, int NT, int CL>
+template <typename T, int STAGE, int NT, int CL, bool CP>
 static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const *R0,
                               void *const *R1, void *const *Ro, const void *rho, DtSrc dt,
-                              int grid, int sched, cudaStream_t s) {
-  F4<T> a, b, c;
+                              int grid, int sched, const LoPtrs &lo, cudaStream_t s) {
+  F4<T> a, b, c, l0{}, l1{}, lo_{};
   for (int q = 0; q < 4; ++q) {
     a.f[q] = (T *)R0[q];
     b.f[q] = R1 ? (T *)R1[q] : nullptr;
     c.f[q] = (T *)Ro[q];
+    if (CP) {
+      l0.f[q] = (T *)lo.l0[q];
+      l1.f[q] = lo.l1 ? (T *)lo.l1[q] : nullptr;
+      lo_.f[q] = (T *)lo.lo[q];
+    }
   }
   int smem = (int)sizeof(RadSmem<T>);
-  auto kern = rad_stage_kernel<T, STAGE, NT, CL>;
+  auto kern = rad_stage_kernel<T, STAGE, NT, CL, CP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   if (grid <= 0) {
@@ -306,33 +355,42 @@ static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const
   }
   if (grid > g.ntiles) grid = g.ntiles;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, (const T *)rho, dt, sched);
+  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, (const T *)rho, dt, sched, l0, l1, lo_);
   return cudaGetLastError();
 }
 
-template <typename T, int STAGE, int CL>
+template <typename T, int STAGE, int CL, bool CP>
 static cudaError_t launch_nt(const Geometry &g, const qk_params &p, void *const *R0,
                              void *const *R1, void *const *Ro, const void *rho, DtSrc dt,
-                             int grid, int cfg, cudaStream_t s) {
+                             int grid, int cfg, const LoPtrs &lo, cudaStream_t s) {
   const int sched = cfg_sched(cfg);
   switch (cfg_threads(cfg)) {
-    case 128: return launch_one<T, STAGE, 128, CL>(g, p, R0, R1, Ro, rho, dt, grid, sched, s);
-    case 512: return launch_one<T, STAGE, 512, CL>(g, p, R0, R1, Ro, rho, dt, grid, sched, s);
-    default: return launch_one<T, STAGE, 256, CL>(g, p, R0, R1, Ro, rho, dt, grid, sched, s);
+    case 128: return launch_one<T, STAGE, 128, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, s);
+    case 512: return launch_one<T, STAGE, 512, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, s);
+    default: return launch_one<T, STAGE, 256, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, s);
   }
 }
 
 // All stage kernels of one closure (instantiated in qk_rad.cu and
-// qk_rad_closures.cu, which nvcc compiles in parallel).
+// qk_rad_closures.cu, which nvcc compiles in parallel).  `lo` non-null selects
+// the compensated FP32 kernels.
 template <int CL>
 cudaError_t launch_rad_closure(int fp32, int stage, const Geometry &g, const qk_params &p,
                                void *const *R0, void *const *R1, void *const *Rout,
-                               const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s) {
+                               const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s,
+                               const LoPtrs *lo) {
+  if (fp32 && lo)
+    return stage == 1
+               ? launch_nt<float, 1, CL, true>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, s)
+               : launch_nt<float, 2, CL, true>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, s);
+  const LoPtrs none{};
   if (fp32)
-    return stage == 1 ? launch_nt<float, 1, CL>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s)
-                      : launch_nt<float, 2, CL>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s);
-  return stage == 1 ? launch_nt<double, 1, CL>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s)
-                    : launch_nt<double, 2, CL>(g, p, R0, R1, Rout, rho, dt, grid, cfg, s);
+    return stage == 1
+               ? launch_nt<float, 1, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, s)
+               : launch_nt<float, 2, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, s);
+  return stage == 1
+             ? launch_nt<double, 1, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, s)
+             : launch_nt<double, 2, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, s);
 }
 
 }  // namespace qk

@@ -107,16 +107,31 @@ def lib():
     L.qk_tile_counts.argtypes = [vp, P(i32), P(i32)]
     L.qk_signal_speed.argtypes = [vp, P(vp), P(dbl), vp]
     L.qk_set_timestep.argtypes = [vp, dbl, P(dbl), vp]
+    L.qk_eval_math.argtypes = [vp, i64, vp, vp, vp]
+    L.qk_step_compensated.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), P(dbl), P(i32), vp]
+    L.qk_conserved_sums_compensated.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), P(dbl), vp]
     for f in ("qk_init_level", "qk_amr_init", "qk_amr_info", "qk_amr_interp", "qk_amr_register",
               "qk_amr_sync", "qk_set_tile_part", "qk_tile_counts", "qk_fill_plan", "qk_fill_ghosts_range", "qk_set_dirichlet", "qk_set_source",
               "qk_init_shard", "qk_halo_info", "qk_halo_pack", "qk_halo_unpack",
               "qk_signal_speed", "qk_set_timestep", "qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_autotune",
               "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
               "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
-              "qk_status", "qk_step_info"):
+              "qk_status", "qk_step_info", "qk_eval_math", "qk_step_compensated",
+              "qk_conserved_sums_compensated"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
+
+
+def eval_math(x, rcp=None, sqrt_out=None, stream=None):
+    """The library's FP64 reciprocal and square root of the device doubles `x`
+    into the device arrays `rcp` / `sqrt_out` (either may be None)."""
+    rc = lib().qk_eval_math(C.c_void_p(int(x.data_ptr())), int(x.numel()),
+                            C.c_void_p(int(rcp.data_ptr())) if rcp is not None else None,
+                            C.c_void_p(int(sqrt_out.data_ptr())) if sqrt_out is not None else None,
+                            _stream(stream))
+    if rc != OK:
+        raise QKError(rc, "qk_eval_math failed")
 
 
 def make_params(**kw) -> Params:
@@ -317,12 +332,22 @@ class Context:
         self._check(self._L.qk_timestep(self._h, _ptrs(U, 5), out, _stream(stream)))
         return out[0], int(out[1]), out[2], out[3]
 
-    def step(self, U, R=None, want_dt=False, stream=None):
+    def step(self, U, R=None, want_dt=False, stream=None, lo=None):
+        """One full update.  `lo` = (U_lo, R_lo) selects the compensated FP32
+        step (qk_step_compensated): the state is U + U_lo, R + R_lo."""
         dt = C.c_double(0.0)
         ns = C.c_int32(0)
-        self._check(self._L.qk_step(self._h, _ptrs(U, 5), _ptrs(R, 4) if R is not None else None,
-                                    C.byref(dt) if want_dt else None,
-                                    C.byref(ns) if want_dt else None, _stream(stream)))
+        rp = _ptrs(R, 4) if R is not None else None
+        if lo is None:
+            rc = self._L.qk_step(self._h, _ptrs(U, 5), rp, C.byref(dt) if want_dt else None,
+                                 C.byref(ns) if want_dt else None, _stream(stream))
+        else:
+            Ul, Rl = lo
+            rc = self._L.qk_step_compensated(
+                self._h, _ptrs(U, 5), rp, _ptrs(Ul, 5), _ptrs(Rl, 4) if R is not None else None,
+                C.byref(dt) if want_dt else None, C.byref(ns) if want_dt else None,
+                _stream(stream))
+        self._check(rc)
         return (dt.value, ns.value) if want_dt else None
 
     def step_info(self, stream=None):
@@ -331,11 +356,18 @@ class Context:
         self._check(self._L.qk_step_info(self._h, out, _stream(stream)))
         return tuple(out[:])
 
-    def conserved_sums(self, U, R=None, stream=None):
+    def conserved_sums(self, U, R=None, stream=None, lo=None):
+        """qk_conserved_sums; `lo` = (U_lo, R_lo) sums a compensated state."""
         out = (C.c_double * NSUMS)()
-        self._check(self._L.qk_conserved_sums(self._h, _ptrs(U, 5),
-                                              _ptrs(R, 4) if R is not None else None, out,
-                                              _stream(stream)))
+        rp = _ptrs(R, 4) if R is not None else None
+        if lo is None:
+            rc = self._L.qk_conserved_sums(self._h, _ptrs(U, 5), rp, out, _stream(stream))
+        else:
+            Ul, Rl = lo
+            rc = self._L.qk_conserved_sums_compensated(
+                self._h, _ptrs(U, 5), rp, _ptrs(Ul, 5), _ptrs(Rl, 4) if R is not None else None,
+                out, _stream(stream))
+        self._check(rc)
         return np.array(out[:])
 
     def status(self, reset=False, stream=None):

@@ -1,0 +1,62 @@
+"""The FP64 reciprocal and square root of the stage kernels against IEEE
+results (numpy's correctly rounded division and square root): every result
+within one ulp, on the argument ranges the kernels see (the Levermore
+closure's [1, 4], the HLL wavespeed's (0, 1], densities and pressures over
+many decades) and across the exponent range."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+def _args():
+    rng = np.random.Generator(np.random.Philox(97))
+    parts = [
+        rng.uniform(1.0, 4.0, 200_000),                    # 4 - 3 |f|^2
+        rng.uniform(0.0, 1.0, 200_000) + 1e-300,           # T_DD
+        10.0 ** rng.uniform(-300, 300, 400_000),           # any magnitude
+        np.nextafter(np.array([1.0, 2.0, 4.0, 0.25]), 0.0),
+        np.array([1.0, 2.0, 3.0, 4.0, 0.5, 1e-300, 1e300, 1.0 / 3.0]),
+    ]
+    return np.concatenate(parts)
+
+
+def _ulp_err(got, ref):
+    return np.abs(got - ref) / np.spacing(np.abs(ref))
+
+
+def test_reciprocal_and_sqrt_within_one_ulp(torch_cuda):
+    torch = torch_cuda
+    from paper_2110_01792_gb300 import qk
+    x = _args()
+    dx = torch.from_numpy(x).cuda()
+    r = torch.empty_like(dx)
+    s = torch.empty_like(dx)
+    qk.eval_math(dx, r, s)
+    torch.cuda.synchronize()
+    er = _ulp_err(r.cpu().numpy(), 1.0 / x)
+    es = _ulp_err(s.cpu().numpy(), np.sqrt(x))
+    assert er.max() <= 1.0, (er.max(), x[np.argmax(er)])
+    assert es.max() <= 1.0, (es.max(), x[np.argmax(es)])
+    # mostly correctly rounded (the square root carries the rounding of its
+    # first product x y, up to half an ulp, on top of the final rounding)
+    assert np.mean(er <= 0.5) > 0.99 and np.mean(es <= 0.5) > 0.8
+
+
+def test_sqrt_of_zero_is_zero(torch_cuda):
+    torch = torch_cuda
+    from paper_2110_01792_gb300 import qk
+    dx = torch.tensor([0.0, 4.0], dtype=torch.float64, device="cuda")
+    s = torch.empty_like(dx)
+    qk.eval_math(dx, None, s)
+    assert s.cpu().tolist() == [0.0, 2.0]
