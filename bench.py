@@ -48,13 +48,17 @@ ALGO_FLOPS = {
     "rad2": 6 + 3 * (4 * 21.1 + 283.4) + 24 + 8 + 20,
     "exchange": 256.4,
 }
+# radiation stage 2 with the exchange in its epilogue (what qk_step launches)
+ALGO_FLOPS["rad2x"] = ALGO_FLOPS["rad2"] + ALGO_FLOPS["exchange"]
 
 # kernels launched per step (captured in one CUDA graph; substeps beyond N_sub
 # are predicated off but still launched)
-def launches_per_step(hydro_only: bool, nsub_max: int) -> int:
+def launches_per_step(hydro_only: bool, nsub_max: int, fused: bool = True) -> int:
     n = 2 + 2 + 2  # max-speed + timestep, 2 ghost fills, 2 hydro stages
     if not hydro_only:
-        n += 1 + nsub_max * 5  # rho ghost fill; per substep: 2 fills, 2 rad stages, exchange
+        # rho ghost fill; per substep: 2 fills, 2 rad stages (+ the exchange
+        # unless it runs in the epilogue of stage 2)
+        n += 1 + nsub_max * (4 if fused else 5)
     return n
 
 
@@ -155,8 +159,11 @@ def algorithmic_bytes_per_cell(kernel: str, elem: int) -> float:
     """Minimum HBM traffic per interior cell of one launch (values x elem size):
     hydro stage 1 reads 5, writes 5; stage 2 reads 10, writes 5; radiation
     stage 1 reads 4 + rho, writes 4; stage 2 reads 8 + rho, writes 4;
-    exchange reads 9, writes 8."""
-    vals = {"hydro1": 10, "hydro2": 15, "rad1": 9, "rad2": 13, "exchange": 17}[kernel]
+    exchange reads 9, writes 8; stage 2 with the exchange fused reads 8 + rho
+    + m, E (12 + 1), writes 4 + m, E (8)."""
+    vals = {"hydro1": 10, "hydro2": 15, "rad1": 9, "rad2": 13, "exchange": 17,
+            # fused: the exchange's E_r, F come from the stage, rho is read once
+            "rad2x": 21}[kernel]
     return vals * elem
 
 
@@ -247,7 +254,8 @@ NCU_TRAFFIC = {
 def _src_hash(kind: str) -> str:
     import hashlib
     cs = os.path.join(ROOT, "paper_2110_01792_gb300", "csrc")
-    files = {"rad": ["qk_rad.cu", "qk_rad.cuh"], "hydro": ["qk_hydro.cu"], "cell": ["qk_cell.cu"]}[kind]
+    files = {"rad": ["qk_rad.cu", "qk_rad.cuh", "qk_exchange.cuh"], "hydro": ["qk_hydro.cu"],
+             "cell": ["qk_cell.cu", "qk_exchange.cuh"]}[kind]
     h = hashlib.sha1()
     for f in files + ["qk_device.cuh", "qk_internal.cuh"]:
         with open(os.path.join(cs, f), "rb") as fh:
@@ -283,6 +291,9 @@ def run_kernel_only(args):
             ctx.hydro_stage(1, U, None, [torch.empty_like(a) for a in U], dt)
         elif args.kernel_only == "rad1":
             ctx.rad_stage(1, R, None, [torch.empty_like(a) for a in R], U[0], dtr)
+        elif args.kernel_only == "rad2x":
+            R1 = [a.clone() for a in R]
+            ctx.rad_stage2_exchange(R, R1, [torch.empty_like(a) for a in R], U, dtr)
         else:
             ctx.exchange(U, R, dtr)
     torch.cuda.synchronize()
@@ -348,8 +359,10 @@ def run_precision_report(steps_hydro=10, steps_rhd=20):
     error of each field is the relative L1 distance to the FP64 result (the
     FP64 path matches the oracle to 1e-10 per cell; the oracle itself would
     take hours at this size).  Drift: max over the steps of |total(t) -
-    total(0)| / sum of |terms| for sum rho, sum (E + (c/chat) E_r) and each
-    component of sum (m + F/(c chat)).  Also the cell-updates/s of each form."""
+    total(0)|, relative to |total(0)| for sum rho and sum (E + (c/chat) E_r),
+    and to the L1 norm of the final momenta (sum |m| + |F|/(c chat)) for each
+    component of sum (m + F/(c chat)), a total near zero.  Also the
+    cell-updates/s of each form."""
     import numpy as np
     import torch
     from paper_2110_01792_gb300 import qk
@@ -370,14 +383,7 @@ def run_precision_report(steps_hydro=10, steps_rhd=20):
         lay = prob.layout
         cr = prob.params["c"] / prob.params["chat"] if prob.R is not None else 0.0
         icc = 1.0 / (prob.params["c"] * prob.params["chat"]) if prob.R is not None else 0.0
-        init = prob.U + (prob.R or [])
-        mag = {}
-        absint = [np.abs(interior(lay, a)).sum() for a in init]
-        mag["rho"] = absint[0]
-        mag["E_total"] = absint[4] + (cr * absint[5] if prob.R is not None else 0.0)
-        mag["momentum"] = [absint[1 + d] + (icc * absint[6 + d] if prob.R is not None else 0.0)
-                           for d in range(3)]
-        results, entry = {}, {}
+        results, entry, sums_by = {}, {}, {}
         for form in ("fp64", "fp32", "fp32_compensated"):
             prec = qk.FP64 if form == "fp64" else qk.FP32_MIXED
             tdt = torch.float64 if prec == qk.FP64 else torch.float32
@@ -408,19 +414,27 @@ def run_precision_report(steps_hydro=10, steps_rhd=20):
             results[form] = [interior(lay, a) for a in fields]
             del U, R, lo, fields
             torch.cuda.empty_cache()
-            S = np.array(sums)
-            d = np.abs(S - S[0]).max(axis=0)
+            sums_by[form] = np.array(sums)
             entry[form] = {
                 # the first step captures the step graph: timed from the second
                 "cell_updates_per_s": lay.ncells * (steps - 1) / sum(times[1:])
                 if steps > 1 else None,
-                "drift": {"rho": float(d[0] / mag["rho"]),
-                          "E_total": float(d[9] / mag["E_total"]),
-                          "momentum": float(max(d[10 + a] / mag["momentum"][a]
-                                                for a in range(3)))},
                 "status_ok": ok}
-        names = ["rho", "m_x", "m_y", "m_z", "E", "E_r", "F_x", "F_y", "F_z"]
+        # drift scales: |total(0)| for rho and E + (c/chat) E_r; for the
+        # momentum totals (near zero) the L1 norm sum |m| + |F|/(c chat) of
+        # the final FP64 state, times the cell volume as in the sums
         ref = results["fp64"]
+        vol = 1.0 / lay.ncells
+        mom = [vol * (np.abs(ref[1 + a]).sum() +
+                      (icc * np.abs(ref[6 + a]).sum() if prob.R is not None else 0.0))
+               for a in range(3)]
+        for form, S in sums_by.items():
+            d = np.abs(S - S[0]).max(axis=0)
+            entry[form]["drift"] = {
+                "rho": float(d[0] / abs(S[0, 0])),
+                "E_total": float(d[9] / abs(S[0, 9])),
+                "momentum": float(max(d[10 + a] / mom[a] for a in range(3)))}
+        names = ["rho", "m_x", "m_y", "m_z", "E", "E_r", "F_x", "F_y", "F_z"]
         for form in ("fp32", "fp32_compensated"):
             entry[form]["rel_l1_vs_fp64"] = {
                 names[q]: float(np.abs(results[form][q] - ref[q]).sum() / np.abs(ref[q]).sum())
@@ -453,6 +467,7 @@ def run_ours(args):
     prob = workload(args.workload)
     lay = prob.layout
     ctx = qk.Context(lay, prob.params, prec)
+    ctx.set_fused_exchange(not args.no_fused_exchange)
     hydro_only = prob.R is None
     dev = torch.device("cuda", local)
     U = [torch.from_numpy(a).to(dev, tdt) for a in prob.U]
@@ -528,41 +543,57 @@ def run_ours(args):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = cells * args.steps * world / float(te.item())
 
-    # ---- dominant kernel: each stage kernel timed alone through its entry
-    # point (CUDA events on the launching stream), weighted by its launches
-    # per update; the largest share is reported against its roofline ----
+    # ---- dominant kernel: each kernel of the step timed alone through its
+    # entry point (CUDA events on the launching stream), weighted by its
+    # launches per update; the largest share is reported against the peak of
+    # the unit its arithmetic runs on (FP64 for the FP64 path; FP32 for the
+    # FP32-mixed kernels, whose exchange part is FP64 by design) ----
     pk, pk_kind = peaks()
     reps = 10
+    fused = not args.no_fused_exchange
     times = {}
     U1 = [torch.empty_like(a) for a in U]
+    U2 = [torch.empty_like(a) for a in U]
     ctx.fill_ghosts(U)
     dt, _, dtr, _ = ctx.timestep(U)
     times["hydro1"] = (time_kernel(torch, lambda: ctx.hydro_stage(1, U, None, U1, dt), reps,
                                    stream), 1.0)
-    del U1
+    ctx.fill_ghosts(U1)
+    times["hydro2"] = (time_kernel(torch, lambda: ctx.hydro_stage(2, U, U1, U2, dt), reps,
+                                   stream), 1.0)
+    del U1, U2
     if not hydro_only:
         R1 = [torch.empty_like(a) for a in R]
+        R2 = [torch.empty_like(a) for a in R]
         ctx.fill_ghosts(R + [U[0]])
         times["rad1"] = (time_kernel(torch, lambda: ctx.rad_stage(1, R, None, R1, U[0], dtr),
                                      reps, stream), nsub_mean)
-        del R1
+        ctx.fill_ghosts(R1)
         Uc = [a.clone() for a in U]
-        Rc = [a.clone() for a in R]
-        times["exchange"] = (time_kernel(torch, lambda: ctx.exchange(Uc, Rc, dtr), reps, stream),
-                             nsub_mean)
+        if fused:
+            times["rad2x"] = (time_kernel(
+                torch, lambda: ctx.rad_stage2_exchange(R, R1, R2, Uc, dtr), reps, stream),
+                nsub_mean)
+        else:
+            times["rad2"] = (time_kernel(torch, lambda: ctx.rad_stage(2, R, R1, R2, U[0], dtr),
+                                         reps, stream), nsub_mean)
+            times["exchange"] = (time_kernel(torch, lambda: ctx.exchange(Uc, R2, dtr), reps,
+                                             stream), nsub_mean)
         ctx.status(reset=True)
-        del Uc, Rc
+        del R1, R2, Uc
     kname = max(times, key=lambda k: times[k][0] * times[k][1])
     t_k = times[kname][0]
     tname = "double" if prec == qk.FP64 else "float"
-    kern = {"hydro1": f"hydro_stage_kernel<{tname},1>", "rad1": f"rad_stage_kernel<{tname},1>",
+    kern = {"hydro1": f"hydro_stage_kernel<{tname},1>", "hydro2": f"hydro_stage_kernel<{tname},2>",
+            "rad1": f"rad_stage_kernel<{tname},1>", "rad2": f"rad_stage_kernel<{tname},2>",
+            "rad2x": f"rad_stage_ex_kernel<{tname}>",
             "exchange": "exchange_kernel<double>" if prec == qk.FP64
                         else "exchange_kernel_mixed"}[kname]
     bytes_launch = algorithmic_bytes_per_cell(kname, elem) * cells
     flops_launch = ALGO_FLOPS[kname] * cells
     hbm_ach = bytes_launch / t_k / 1e9
     hbm_peak = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
-    fp64_unit = prec == qk.FP64 or kname == "exchange"  # the exchange is FP64 in both modes
+    fp64_unit = prec == qk.FP64
     alu_peak = FP64_PEAK_TFLOPS if fp64_unit else FP32_PEAK_TFLOPS
     alu_ach = flops_launch / t_k / 1e12
     hbm = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
@@ -585,7 +616,8 @@ def run_ours(args):
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(args.precision)
     variants = None if args.no_variants or world > 1 else run_variants(args)
     precision = None if args.no_variants or world > 1 else run_precision_report()
-    nl = launches_per_step(hydro_only, int(prob.params.get("nsub_max", 10)))
+    nl = launches_per_step(hydro_only, int(prob.params.get("nsub_max", 10)),
+                           not args.no_fused_exchange)
     line = {
         "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
@@ -621,7 +653,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--kernel-only", choices=["hydro1", "rad1", "exchange"], default=None,
+    ap.add_argument("--no-fused-exchange", action="store_true",
+                    help="run the exchange as its own launch after radiation stage 2")
+    ap.add_argument("--kernel-only", choices=["hydro1", "rad1", "rad2x", "exchange"], default=None,
                     help="launch one stage kernel 3 times and exit (for ncu captures)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -242,6 +242,16 @@ int qk_hydro_stage(qk_ctx *ctx, int32_t stage, void *const U0[5], void *const U1
 int qk_rad_stage(qk_ctx *ctx, int32_t stage, void *const R0[4], void *const R1[4],
                  void *const Rout[4], const void *rho, double dt_rad, void *stream);
 
+/* Radiation stage 2 with the matter-radiation exchange of every cell in its
+ * epilogue (Sec. 2.2.2 then Sec. 2.2.3, per cell): the same result as
+ * qk_rad_stage(stage 2) followed by qk_rad_matter_exchange on Rout, in one
+ * launch (the form qk_step uses).  hydro is read and its momenta and energy
+ * are updated; its density (ghosts filled) sets the optical depth.  Rout may
+ * alias R0, not R1.  Newton failures go to the context status (qk_status). */
+int qk_rad_stage2_exchange(qk_ctx *ctx, void *const R0[4], void *const R1[4],
+                           void *const Rout[4], void *const hydro[5], double dt_rad,
+                           void *stream);
+
 /* Per-cell implicit matter-radiation exchange over dt_rad (Sec. 2.2.3), in
  * FP64 for both precisions: Newton-Raphson on (E_g, E_r) with the residuals
  * F_G, F_R and eqs. delta_er / delta_eg, the backward-Euler flux source
@@ -316,6 +326,14 @@ int qk_autotune(qk_ctx *ctx, void *const hydro[5], void *const rad[4], int32_t o
  * default is QK_LAUNCH_BATCHED).  Results are identical; captured step graphs
  * are dropped. */
 int qk_set_launch_mode(qk_ctx *ctx, int32_t mode);
+
+/* qk_step (and qk_step_compensated): run the matter-radiation exchange of
+ * every substep in the epilogue of radiation stage 2 (1, default), or as its
+ * own launch after it (0).  The exchange is pointwise (Sec. 2.2.3) and reads
+ * exactly the state stage 2 produces, so both give identical results; fusing
+ * saves re-reading the state and lets the exchange's FP64 work overlap the
+ * stage's FP32 work on the same SMs. */
+int qk_set_fused_exchange(qk_ctx *ctx, int32_t enable);
 
 /* Enable (1, default) or disable (0) CUDA-graph capture in qk_step. */
 int qk_set_graph(qk_ctx *ctx, int32_t enable);

@@ -866,6 +866,13 @@ int qk_tile_counts(const qk_ctx *c, int32_t *n_interior, int32_t *n_boundary) {
   return QK_OK;
 }
 
+int qk_set_fused_exchange(qk_ctx *c, int32_t enable) {
+  if (!c) return QK_EINVAL;
+  c->fuse_exchange = enable ? 1 : 0;
+  drop_graphs(c);
+  return QK_OK;
+}
+
 int qk_set_graph(qk_ctx *c, int32_t enable) {
   if (!c) return QK_EINVAL;
   c->use_graph = enable ? 1 : 0;
@@ -962,6 +969,23 @@ int qk_rad_stage(qk_ctx *c, int32_t stage, void *const R0[4], void *const R1[4],
   return QK_OK;
 }
 
+int qk_rad_stage2_exchange(qk_ctx *c, void *const R0[4], void *const R1[4], void *const Rout[4],
+                           void *const hydro[5], double dt_rad, void *stream) {
+  if (!c) return QK_EINVAL;
+  int rc = check_fields(c, R0, 4, "R0");
+  if (!rc) rc = check_fields(c, R1, 4, "R1");
+  if (!rc) rc = check_fields(c, Rout, 4, "Rout");
+  if (!rc) rc = check_fields(c, hydro, 5, "hydro");
+  if (rc) return rc;
+  for (int q = 0; q < 4; ++q)
+    if (Rout[q] == R1[q]) return fail(c, QK_EINVAL, "Rout must not alias R1");
+  DtSrc d{nullptr, dt_rad, 2, -1};
+  const FuseArgs fx{hydro, nullptr, c->src, c->d_status};
+  QK_CUDA(c, launch_rad_stage(c->fp32, 2, geom(c), c->p, R0, R1, Rout, hydro[0], d, 0, c->cfg[3],
+                              (cudaStream_t)stream, nullptr, &fx));
+  return QK_OK;
+}
+
 int qk_rad_matter_exchange(qk_ctx *c, void *const hydro[5], void *const rad[4], double dt_rad,
                            void *stream) {
   if (!c) return QK_EINVAL;
@@ -1021,17 +1045,17 @@ static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *c
 
 static cudaError_t rad_launches(qk_ctx *c, int stage, void *const *R0, void *const *R1,
                                 void *const *Ro, const void *rho, DtSrc dt, cudaStream_t s,
-                                const LoPtrs *lo = nullptr) {
+                                const LoPtrs *lo = nullptr, const FuseArgs *fx = nullptr) {
   const Geometry g = geom(c);
   if (c->launch_mode == QK_LAUNCH_BATCHED || c->part != QK_PART_ALL)
     return launch_rad_stage(c->fp32, stage, g, c->p, R0, R1, Ro, rho, dt, 0, c->cfg[1 + stage], s,
-                            lo);
+                            lo, fx);
   for (int b = 0; b < c->nbox_dev; ++b) {
     Geometry gb = g;
     gb.tiles = c->d_tiles + c->tile_start[b];
     gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
     cudaError_t e = launch_rad_stage(c->fp32, stage, gb, c->p, R0, R1, Ro, rho, dt, 0,
-                                     c->cfg[1 + stage], s, lo);
+                                     c->cfg[1 + stage], s, lo, fx);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1065,9 +1089,15 @@ static int enqueue_step(qk_ctx *c, void *const hydro[5], void *const rad[4], cud
       QK_CUDA(c, fill(c, rad, 4, 5, dr, s));
       QK_CUDA(c, rad_launches(c, 1, rad, nullptr, R1, hydro[0], dr, s, rlo ? &r1 : nullptr));
       QK_CUDA(c, fill(c, R1, 4, 5, dr, s));
-      QK_CUDA(c, rad_launches(c, 2, rad, R1, rad, hydro[0], dr, s, rlo ? &r2 : nullptr));
-      QK_CUDA(c, launch_exchange(c->fp32, g, c->p, hydro, rad, c->src, dr, c->d_status, s, hlo,
-                                 rlo));
+      if (c->fuse_exchange) {
+        // stage 2 with the exchange of every cell in its epilogue
+        const FuseArgs fx{hydro, hlo, c->src, c->d_status};
+        QK_CUDA(c, rad_launches(c, 2, rad, R1, rad, hydro[0], dr, s, rlo ? &r2 : nullptr, &fx));
+      } else {
+        QK_CUDA(c, rad_launches(c, 2, rad, R1, rad, hydro[0], dr, s, rlo ? &r2 : nullptr));
+        QK_CUDA(c, launch_exchange(c->fp32, g, c->p, hydro, rad, c->src, dr, c->d_status, s, hlo,
+                                   rlo));
+      }
     }
   }
   return QK_OK;

@@ -4,7 +4,7 @@
 // compensated conservation sums.
 #include <algorithm>
 
-#include "qk_device.cuh"
+#include "qk_exchange.cuh"
 
 namespace qk {
 
@@ -28,138 +28,8 @@ __device__ __forceinline__ long long cell_to_elem(const Geometry &g, long long c
 }
 
 // -------------------------------------------------------------- exchange ---
-template <typename T>
-__device__ __forceinline__ double load_d(const T *p, long long e) { return (double)p[e]; }
-
-// Newton-Raphson on (E_g, E_r) for one cell (Sec. 2.2.3, eqs. delta_er and
-// delta_eg).  R = dt rho kappa_P chat (a_r T^4 - E_r) (the '4 pi B' of the
-// paper read as chat a_r T^4), F_G = (E_g - E_g0) + (c/chat) R,
-// F_R = (E_r - E_r0) - R; with a radiation source S the callers pass
-// E_r0 + S for E_r0 (F_R = (E_r - E_r0) - (R + S); the Jacobian does not
-// change); convergence |F_G/E_tot| < eps and
-// |(c/chat) F_R / E_tot| < eps, E_tot = E_g0 + (c/chat) E_r0; the update of
-// the iterate that passes is applied, then the loop stops.  The 2x2
-// elimination of eqs. delta_er / delta_eg is evaluated with one division:
-// with G = dF_G/dE_g, eta = (dR/dE_g)/G,
-//   dE_r = -(F_R G + R' F_G) / D1,  D1 = (dF_R/dE_r) G + R' (dF_G/dE_r),
-//   dE_g = -(F_G + dE_r dF_G/dE_r) / G,
-// and 1/D1, 1/G taken from the single reciprocal of D1 G.  Starts from
-// (Eg, Er) (the cell state, or a warm start); returns the iteration count,
-// or -1 after max_iter iterations.
-template <typename R_>
-__device__ __forceinline__ int newton_exchange(const qk_params &p, R_ Eg0, R_ Er0, R_ k, R_ cr,
-                                               R_ inv_Etot, R_ inv_rcv, R_ eps, int max_iter,
-                                               R_ &Eg, R_ &Er) {
-  const R_ a_r = (R_)p.a_r;
-  const R_ dFG_dEr = -cr * k;     // -c dt rho kappa_P
-  const R_ dFR_dEr = R_(1) + k;
-  const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
-  const R_ dT4_alpha = alpha_eos ? (R_)(4.0 / p.alpha_eos) : R_(0);
-  bool conv = false;
-  int it = 0;
-  for (it = 0; it < max_iter; ++it) {
-    R_ T4, dT4;
-    if (alpha_eos) {
-      T4 = dT4_alpha * Eg;
-      dT4 = dT4_alpha;
-    } else {
-      const R_ Tg = Eg * inv_rcv;
-      const R_ T2 = Tg * Tg;
-      T4 = T2 * T2;
-      dT4 = R_(4) * T2 * Tg * inv_rcv;
-    }
-    const R_ Rr = k * (a_r * T4 - Er);
-    const R_ FG = (Eg - Eg0) + cr * Rr;
-    const R_ FR = (Er - Er0) - Rr;
-    conv = fabs(FG * inv_Etot) < eps && fabs(cr * FR * inv_Etot) < eps;
-    const R_ dRdEg = k * a_r * dT4;
-    const R_ G = R_(1) + cr * dRdEg;
-    const R_ D1 = dFR_dEr * G + dRdEg * dFG_dEr;
-    const R_ inv = qrcp(D1 * G);
-    const R_ dEr = -(FR * G + dRdEg * FG) * (G * inv);
-    const R_ dEg = -(FG + dEr * dFG_dEr) * (D1 * inv);
-    Er += dEr;
-    Eg += dEg;
-    if (conv) break;
-  }
-  return conv ? it + 1 : -1;
-}
-
-// Warp-aggregated status update of the exchange kernels.
-__device__ __forceinline__ void exchange_status(Status *st, int my_max, unsigned my_flags,
-                                                unsigned long long my_bad) {
-  const unsigned full = 0xffffffffu;
-  int wmax = __reduce_max_sync(full, my_max);
-  unsigned wflags = __reduce_or_sync(full, my_flags);
-  unsigned long long wbad = my_bad;
-  for (int o = 16; o > 0; o >>= 1) wbad = min(wbad, __shfl_xor_sync(full, wbad, o));
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&st->max_iter, wmax);
-    if (wflags) {
-      atomicOr(&st->flags, wflags);
-      atomicMin(&st->first_bad, wbad);
-    }
-  }
-}
-
-// Mixed-precision Newton for one cell: the residuals F_G, F_R and the
-// convergence test of Sec. 2.2.3 are evaluated in FP64 at the FP64 iterate,
-// the 2x2 correction (the same elimination as newton_exchange) is solved in
-// FP32 (iterative refinement: each iteration gains ~7 digits, so two
-// iterations from an FP32 warm start reach the 1e-10 tolerance).  Returns
-// the iteration count or -1.
-__device__ __forceinline__ int newton_refine(const qk_params &p, double Eg0, double Er0,
-                                             double k, double cr, double inv_Etot,
-                                             double inv_rcv, double &Eg, double &Er) {
-  const double a_r = p.a_r;
-  const float kf = (float)k, crf = (float)cr, arf = (float)p.a_r;
-  const float dFG_dEr = -crf * kf, dFR_dEr = 1.0f + kf;
-  const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
-  const double dT4_alpha = alpha_eos ? 4.0 / p.alpha_eos : 0.0;
-  bool conv = false;
-  int it = 0;
-  for (it = 0; it < p.max_iter; ++it) {
-    double T4;
-    float dT4;
-    if (alpha_eos) {
-      T4 = dT4_alpha * Eg;
-      dT4 = (float)dT4_alpha;
-    } else {
-      const double Tg = Eg * inv_rcv;
-      const double T2 = Tg * Tg;
-      T4 = T2 * T2;
-      const float Tf = (float)Tg;
-      dT4 = 4.0f * Tf * Tf * Tf * (float)inv_rcv;
-    }
-    const double Rr = k * (a_r * T4 - Er);
-    const double FG = (Eg - Eg0) + cr * Rr;
-    const double FR = (Er - Er0) - Rr;
-    conv = fabs(FG * inv_Etot) < p.eps_newton && fabs(cr * FR * inv_Etot) < p.eps_newton;
-    const float fg = (float)FG, fr = (float)FR;
-    const float dRdEg = kf * arf * dT4;
-    const float G = 1.0f + crf * dRdEg;
-    const float D1 = dFR_dEr * G + dRdEg * dFG_dEr;
-    const float inv = qrcp(D1 * G);
-    const float dEr = -(fr * G + dRdEg * fg) * (G * inv);
-    const float dEg = -(fg + dEr * dFG_dEr) * (D1 * inv);
-    Er += (double)dEr;
-    Eg += (double)dEg;
-    if (conv) break;
-  }
-  return conv ? it + 1 : -1;
-}
-
-// FP32-mixed exchange: FP32 state; the internal energy recovered with the
-// error-free FP32 transforms of con2prim; the Newton solve with FP64 residuals
-// and convergence test (FP32 warm start, then newton_refine); the flux
-// source, momentum and kinetic-energy work in FP32, the new total energy
-// accumulated in FP64 before the final rounding.
-// CP: compensated state (every conserved field hi + lo; UL, RL the lo
-// arrays): E, E_r, m and F are read as hi + lo, the new E and E_r are formed
-// in FP64 from the invariant E + (c/chat) E_r (the kinetic-energy change
-// taken from the FP64 difference of the same two values), and the momentum
-// exchange m + F/(c chat) = const is carried in double-float with a
-// double-float 1/(c chat), so that both invariants hold to ~2^-48.
+// One thread per interior cell (grid-stride over the flat cell index); the
+// per-cell arithmetic is in qk_exchange.cuh.
 template <bool CP>
 __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_params p,
                                                               F5<float> U, F4<float> R,
@@ -167,183 +37,39 @@ __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_para
                                                               Status *st, F5<float> UL,
                                                               F4<float> RL) {
   if (skip_substep(dts)) return;
+  const ExK K = make_exk(p);
   const double dt = dt_of(dts);
-  const double cr = p.c / p.chat;
-  const float icc = (float)(1.0 / (p.chat * p.c)), rc = (float)(p.chat / p.c);
-  const float icc_lo = (float)(1.0 / (p.chat * p.c) - (double)icc);
-  const double inv_cv = p.eos == QK_EOS_ALPHA_T3 ? 0.0 : 1.0 / p.c_v;
-  int my_max = 0;
-  unsigned my_flags = 0;
-  unsigned long long my_bad = ~0ull;
+  ExStat xs;
   for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < g.ncells;
        cidx += (long long)gridDim.x * blockDim.x) {
     const long long e = cell_to_elem(g, cidx);
-    float u[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
-    const float rho = u[0];
-    float rinv = qrcp(rho);
-    rinv = rinv * fmaf(-rho, rinv, 2.0f);  // one Newton step: ~1 ulp
-    float eg_hi, eg_lo;
-    internal_energy_f32(u, rho, rinv, eg_hi, eg_lo);  // ~48-bit E_g, no EOS round trip
-    const float Er0f = R.f[0][e];
-    const double rho_d = (double)rho;
-    double Eg0 = (double)eg_hi + (double)eg_lo;
-    double Er0 = (double)Er0f;
-    float E_lo = 0.0f;
+    const float fr[3] = {R.f[1][e], R.f[2][e], R.f[3][e]};
+    float fl[3] = {0.0f, 0.0f, 0.0f}, el = 0.0f;
     if constexpr (CP) {
-      E_lo = UL.f[4][e];
-      Eg0 += (double)E_lo;
-      Er0 += (double)RL.f[0][e];
+      el = RL.f[0][e];
+      fl[0] = RL.f[1][e];
+      fl[1] = RL.f[2][e];
+      fl[2] = RL.f[3][e];
     }
-    const double kP = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_P * rho_d : p.kappa_P;
-    const double k = dt * rho_d * kP * p.chat;
-    const double inv_rcv = (double)(rinv * (float)inv_cv);
-    const double inv_Etot = (double)qrcp((float)(Eg0 + cr * Er0));
-    // radiation source S = dt (chat/c) j, carried in the residual's E_r0
-    const double Er0S = src ? Er0 + dt * (p.chat / p.c) * (double)src[e] : Er0;
-    // FP32 warm start
-    float Egf = (float)Eg0, Erf = (float)Er0S;
-    const int itf = newton_exchange<float>(p, (float)Eg0, (float)Er0S, (float)k, (float)cr,
-                                           (float)inv_Etot, (float)inv_rcv, 1e-6f, 12, Egf, Erf);
-    double Eg = Eg0, Er = Er0;
-    if (itf > 0 && Egf > 0.0f && Erf > 0.0f && isfinite(Egf) && isfinite(Erf)) {
-      Eg = Egf;
-      Er = Erf;
-    }
-    const int it = newton_refine(p, Eg0, Er0S, k, cr, inv_Etot, inv_rcv, Eg, Er);
-    if (it < 0) {
-      my_flags |= 1u << QK_ENOCONV;
-      my_bad = min(my_bad, (unsigned long long)e);
-    } else {
-      my_max = max(my_max, it);
-    }
-    const float kF = p.kappa_mode == QK_KAPPA_RHO ? (float)p.kappa_R * rho : (float)p.kappa_R;
-    const float damp = qrcp(1.0f + rho * kF * (float)(p.chat * dt));
-    float mn[3];
-    float ke0 = 0.0f, ke1 = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float F0 = R.f[1 + a][e];
-      if constexpr (CP) {
-        // dF = F0 (damp - 1); F += dF and m -= dF/(c chat), both in double-float
-        float Fl = RL.f[1 + a][e];
-        const float dF = (F0 + Fl) * (damp - 1.0f);
-        float Fh = F0;
-        df_add(Fh, Fl, dF);
-        df_norm(Fh, Fl);
-        R.f[1 + a][e] = Fh;
-        RL.f[1 + a][e] = Fl;
-        const float p1 = __fmul_rn(dF, icc);
-        const float e1 = fmaf(dF, icc, -p1) + dF * icc_lo;
-        float mh = u[1 + a], ml = UL.f[1 + a][e];
-        df_add(mh, ml, -p1);
-        ml = __fsub_rn(ml, e1);
-        df_norm(mh, ml);
-        U.f[1 + a][e] = mh;
-        UL.f[1 + a][e] = ml;
-        mn[a] = mh;
-      } else {
-        const float Fn = F0 * damp;
-        mn[a] = u[1 + a] - (Fn - F0) * icc;
-        R.f[1 + a][e] = Fn;
-        U.f[1 + a][e] = mn[a];
-      }
-      ke0 = fmaf(u[1 + a], u[1 + a], ke0);
-      ke1 = fmaf(mn[a], mn[a], ke1);
-    }
-    const float Ekin1 = 0.5f * ke1 * rinv;
-    double Er_new;
-    if constexpr (CP) {
-      // E_new = E_g + E_kin,1; E_r,new = E_r - (chat/c)(E_kin,1 - E_kin,0) with
-      // E_kin,0 = E - E_g0 (the same FP64 values), split into hi + lo
-      const double Ekin0 = ((double)u[4] + (double)E_lo) - Eg0;
-      const double Enew = Eg + (double)Ekin1;
-      Er_new = Er - (p.chat / p.c) * ((double)Ekin1 - Ekin0);
-      const float Eh = (float)Enew, Rh = (float)Er_new;
-      U.f[4][e] = Eh;
-      UL.f[4][e] = (float)(Enew - (double)Eh);
-      R.f[0][e] = Rh;
-      RL.f[0][e] = (float)(Er_new - (double)Rh);
-    } else {
-      const float dEkin = 0.5f * (ke1 - ke0) * rinv;
-      U.f[4][e] = (float)(Eg + (double)Ekin1);
-      Er_new = Er - (double)(rc * dEkin);
-      R.f[0][e] = (float)Er_new;
-    }
-    if (!(Eg > 0.0) || !(Er_new > 0.0)) {
-      my_flags |= 1u << QK_ENEGATIVE;
-      my_bad = min(my_bad, (unsigned long long)e);
-    }
+    exchange_cell_mixed<CP>(p, K, dt, U, R, UL, RL, src, e, R.f[0][e], el, fr, fl, xs);
   }
-  exchange_status(st, my_max, my_flags, my_bad);
+  exchange_status(st, xs.max, xs.flags, xs.bad);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, F5<T> U, F4<T> R,
                                                         const T *src, DtSrc dts, Status *st) {
   if (skip_substep(dts)) return;
+  const ExK K = make_exk(p);
   const double dt = dt_of(dts);
-  const double chat = p.chat, c = p.c;
-  const double cr = c / chat, icc = 1.0 / (chat * c), rc = chat / c;
-  const double inv_cv = p.eos == QK_EOS_ALPHA_T3 ? 0.0 : 1.0 / p.c_v;
-  int my_max = 0;
-  unsigned my_flags = 0;
-  unsigned long long my_bad = ~0ull;
+  ExStat xs;
   for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < g.ncells;
        cidx += (long long)gridDim.x * blockDim.x) {
     const long long e = cell_to_elem(g, cidx);
-    const double rho = load_d(U.f[0], e);
-    double m[3] = {load_d(U.f[1], e), load_d(U.f[2], e), load_d(U.f[3], e)};
-    const double E = load_d(U.f[4], e);
-    const double Er0 = load_d(R.f[0], e);
-    const double kP = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_P * rho : p.kappa_P;
-    const double kF = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_R * rho : p.kappa_R;
-    const double m2 = (m[0] * m[0] + m[1] * m[1]) + m[2] * m[2];
-    // one reciprocal serves 1/rho and the flux damping 1/(1 + rho kF chat dt)
-    const double Dm = 1.0 + rho * kF * chat * dt;
-    const double inv_rho_Dm = frcp(rho * Dm);
-    const double inv_rho = Dm * inv_rho_Dm;
-    const double damp = rho * inv_rho_Dm;
-    const double Ekin0 = 0.5 * m2 * inv_rho;
-    const double Eg0 = E - Ekin0;
-    const double inv_Etot = frcp(Eg0 + cr * Er0);
-    const double k = dt * rho * kP * chat;
-    const double inv_rcv = inv_rho * inv_cv;
-    // radiation source S = dt (chat/c) j, carried in the residual's E_r0
-    const double Er0S = src ? Er0 + dt * rc * load_d(src, e) : Er0;
-    double Eg = Eg0, Er = Er0;
-    int it;
-    it = newton_exchange<double>(p, Eg0, Er0S, k, cr, inv_Etot, inv_rcv, p.eps_newton,
-                                 p.max_iter, Eg, Er);
-    if (it < 0) {
-      my_flags |= 1u << QK_ENOCONV;
-      my_bad = min(my_bad, (unsigned long long)e);
-    } else {
-      my_max = max(my_max, it);
-    }
-    // flux source (backward Euler) and the equal and opposite momentum change
-    double mn[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double F0 = load_d(R.f[1 + a], e);
-      const double Fn = F0 * damp;
-      mn[a] = m[a] - (Fn - F0) * icc;
-      R.f[1 + a][e] = (T)Fn;
-      U.f[1 + a][e] = (T)mn[a];
-    }
-    // work of the radiation force through the kinetic-energy change
-    const double Ekin1 = 0.5 * ((mn[0] * mn[0] + mn[1] * mn[1]) + mn[2] * mn[2]) * inv_rho;
-    const double dEkin = Ekin1 - Ekin0;
-    U.f[4][e] = (T)(Eg + (Ekin0 + dEkin));
-    const double Er_new = Er - rc * dEkin;
-    R.f[0][e] = (T)Er_new;
-    if (!(Eg > 0.0) || !(Er_new > 0.0)) {
-      my_flags |= 1u << QK_ENEGATIVE;
-      my_bad = min(my_bad, (unsigned long long)e);
-    }
+    const double fr[3] = {load_d(R.f[1], e), load_d(R.f[2], e), load_d(R.f[3], e)};
+    exchange_cell<T>(p, K, dt, U, R, src, e, load_d(R.f[0], e), fr, xs);
   }
-  exchange_status(st, my_max, my_flags, my_bad);
+  exchange_status(st, xs.max, xs.flags, xs.bad);
 }
 
 cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, void *const *U,

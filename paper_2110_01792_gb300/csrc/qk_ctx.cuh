@@ -44,6 +44,7 @@ struct qk_ctx {
   std::vector<int> send_chunk0, recv_chunk0;  // per peer: chunk range [p], [p+1)
   std::vector<long long> send_cells, recv_cells;
   int launch_mode = QK_LAUNCH_BATCHED;
+  int fuse_exchange = 1;  // qk_step: exchange in the epilogue of radiation stage 2
   int cfg[4] = {kDefaultCfg, kDefaultCfg, kDefaultCfg, kDefaultCfg};  // hydro1/2, rad1/2
   Copy *d_copies = nullptr;
   Chunk *d_chunks = nullptr;

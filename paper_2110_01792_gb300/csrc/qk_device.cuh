@@ -215,8 +215,18 @@ __device__ __forceinline__ bool dsame_nz(double a, double b) {
   return (x ^ y) >= 0 && (x << 1) != 0 && (y << 1) != 0;
 }
 
-// FP64 PPM with the limiter's min/max and every order test on the integer
-// pipe, and the tests rewritten to need fewer FP64 operations:
+// FP64 PPM interface value between q_j = b and q_{j+1} = c (a = q_{j-1},
+// d = q_{j+2}): (7/12)(b + c) - (1/12)(a + d), with the FMA written out so that
+// every caller (the stage kernels' shared interface pass, the flux registers
+// of mesh refinement) rounds it the same way.
+__device__ __forceinline__ double ppm_face(double a, double b, double c, double d) {
+  return fma(7.0 / 12.0, b + c, -((1.0 / 12.0) * (a + d)));
+}
+
+// The limiter of FP64 PPM for one cell from its two raw interface values fL,
+// fR and the cell averages s1, s2, s3 = q_{i-1}, q_i, q_{i+1}, with the
+// min/max and every order test on the integer pipe, and the tests rewritten
+// to need fewer FP64 operations:
 // - extremum, (qR - q)(q - qL) <= 0: a sign test of the two differences;
 // - MC slope: half of sign * min(2|dm|, 2|dp|, |dm + dp|/2) is
 //   sign * min(|dm|, |dp|, |dm + dp|/4) exactly (scaling by 2 is exact);
@@ -225,13 +235,9 @@ __device__ __forceinline__ bool dsame_nz(double a, double b) {
 //   -d^2 > d q6 <=>  d (qR - r') > 0  with r' = 3 q - 2 qL
 //   (expand d q6 -+ d^2); at the tie l' = qL (r' = qR), so a decision that
 //   rounding flips moves the result only by rounding.
-// The values equal ppm<double>'s bit for bit except at such ties.
-template <>
-__device__ __forceinline__ void ppm<double>(double s0, double s1, double s2, double s3,
-                                            double s4, double &qL, double &qR) {
-  const double c7 = 7.0 / 12.0, c1 = 1.0 / 12.0;
-  const double fL = c7 * (s1 + s2) - c1 * (s0 + s3);
-  const double fR = c7 * (s2 + s3) - c1 * (s1 + s4);
+// The values equal the direct evaluation bit for bit except at such ties.
+__device__ __forceinline__ void ppm_limit(double fL, double fR, double s1, double s2, double s3,
+                                          double &qL, double &qR) {
   const long long k1 = dkey(s1), k2 = dkey(s2), k3 = dkey(s3);
   const long long klo = min(k1, min(k2, k3)), khi = max(k1, max(k2, k3));
   double l = dunkey(min(max(dkey(fL), klo), khi));
@@ -263,6 +269,42 @@ __device__ __forceinline__ void ppm<double>(double s0, double s1, double s2, dou
   }
   qL = l;
   qR = r;
+}
+
+// FP64 PPM of one cell from its stencil s0..s4 (interface values, then the
+// limiter); the stage kernels compute the interface values once per face
+// instead and call ppm_limit.
+template <>
+__device__ __forceinline__ void ppm<double>(double s0, double s1, double s2, double s3,
+                                            double s4, double &qL, double &qR) {
+  ppm_limit(ppm_face(s0, s1, s2, s3), ppm_face(s1, s2, s3, s4), s1, s2, s3, qL, qR);
+}
+
+// FP64 PPM with shared interface values, first pass of one direction D: the
+// interface value at the left face of every cell -1 .. v[D]+1 of every line
+// along D of the tile (NIFP per line, indexed like the line positions with
+// item_index<D>(.., NIFP)), from the cross-slot primitives prim[q], into
+// iface[q].  Position p of a line (cell p-1) then reads its raw face values
+// at p and p+1: each interface value is computed once instead of twice.
+template <int D, int NT, int NV>
+__device__ __forceinline__ void ppm_faces_pass(const double (*prim)[NCROSS],
+                                               double (*iface)[NIF], const int v[3]) {
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  for (int it = threadIdx.x; it < NIF; it += NT) {
+    int k, cc[3];
+    item_cell<D>(it, NIFP, k, cc[0], cc[1], cc[2]);
+    if (cc[A] >= v[A] || cc[B] >= v[B] || cc[D] > v[D] + 1) continue;
+    int s[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      int x[3] = {cc[0], cc[1], cc[2]};
+      x[D] += o - 2;
+      s[o] = cross_slot(x[0], x[1], x[2]);
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      iface[q][it] = ppm_face(prim[q][s[0]], prim[q][s[1]], prim[q][s[2]], prim[q][s[3]]);
+  }
 }
 
 // PLM with the monotonized-central limiter (van Leer 1977), the paper's

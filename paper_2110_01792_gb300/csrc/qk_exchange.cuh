@@ -1,0 +1,359 @@
+// qk_exchange.cuh -- the implicit matter-radiation exchange of one cell
+// (Sec. 2.2.3 of arXiv:2110.01792), shared by the exchange kernels and the
+// epilogue of the radiation stage 2 that fuses it (the exchange is pointwise
+// and follows the transport of every substep).
+#pragma once
+#include "qk_device.cuh"
+
+namespace qk {
+
+template <typename T>
+__device__ __forceinline__ double load_d(const T *p, long long e) { return (double)p[e]; }
+
+// |x| < t for a finite positive threshold t: doubles compare as bit
+// patterns on the integer pipe (NaN fails); floats use the FP32 compare.
+__device__ __forceinline__ bool abs_below(double x, double t) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < __double_as_longlong(t);
+}
+__device__ __forceinline__ bool abs_below(float x, float t) { return fabsf(x) < t; }
+// x > 0 and finite, on the integer pipe.
+__device__ __forceinline__ bool pos_finite(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b < 0x7ff0000000000000LL;
+}
+
+// Newton-Raphson on (E_g, E_r) for one cell (Sec. 2.2.3, eqs. delta_er and
+// delta_eg).  R = dt rho kappa_P chat (a_r T^4 - E_r) (the '4 pi B' of the
+// paper read as chat a_r T^4), F_G = (E_g - E_g0) + (c/chat) R,
+// F_R = (E_r - E_r0) - R; with a radiation source S the callers pass
+// E_r0 + S for E_r0 (F_R = (E_r - E_r0) - (R + S); the Jacobian does not
+// change).  Convergence |F_G/E_tot| < eps and |(c/chat) F_R / E_tot| < eps,
+// E_tot = E_g0 + (c/chat) E_r0, tested as |F_G| < thr_g = eps E_tot and
+// |F_R| < thr_r = thr_g chat/c; the update of the iterate that passes is
+// applied, then the loop stops.  With k = dt rho kappa_P chat and
+// T = E_g/(rho c_v), R = A E_g^4 - k E_r with A = k a_r/(rho c_v)^4 (for the
+// alpha T^3 heat capacity, T^4 = 4 E_g/alpha: R = A E_g - k E_r with
+// A = 4 k a_r/alpha; `alpha_eos`).  The 2x2 elimination of eqs.
+// delta_er / delta_eg is evaluated with one division: with G = dF_G/dE_g,
+//   dE_r = -(F_R G + R' F_G) / D1,  D1 = (dF_R/dE_r) G + R' (dF_G/dE_r),
+//   dE_g = -(F_G + dE_r dF_G/dE_r) / G,
+// and 1/D1, 1/G taken from the single reciprocal of D1 G.  Starts from
+// (Eg, Er) (the cell state, or a warm start); returns the iteration count,
+// or -1 after max_iter iterations.
+template <typename R_>
+__device__ __forceinline__ int newton_exchange(bool alpha_eos, R_ A, R_ k, R_ cr, R_ Eg0, R_ Er0,
+                                               R_ thr_g, R_ thr_r, int max_iter, R_ &Eg,
+                                               R_ &Er) {
+  const R_ dFG_dEr = -cr * k;     // -c dt rho kappa_P
+  const R_ dFR_dEr = R_(1) + k;
+  const R_ A4 = R_(4) * A;
+  bool conv = false;
+  int it = 0;
+  for (it = 0; it < max_iter; ++it) {
+    R_ Rr, dRdEg;
+    if (alpha_eos) {
+      Rr = fma(A, Eg, -(k * Er));
+      dRdEg = A;
+    } else {
+      const R_ E2 = Eg * Eg;
+      Rr = fma(A, E2 * E2, -(k * Er));
+      dRdEg = A4 * E2 * Eg;
+    }
+    const R_ FG = (Eg - Eg0) + cr * Rr;
+    const R_ FR = (Er - Er0) - Rr;
+    conv = abs_below(FG, thr_g) && abs_below(FR, thr_r);
+    const R_ G = R_(1) + cr * dRdEg;
+    const R_ D1 = dFR_dEr * G + dRdEg * dFG_dEr;
+    const R_ inv = qrcp(D1 * G);
+    const R_ dEr = -(FR * G + dRdEg * FG) * (G * inv);
+    const R_ dEg = -(FG + dEr * dFG_dEr) * (D1 * inv);
+    Er += dEr;
+    Eg += dEg;
+    if (conv) break;
+  }
+  return conv ? it + 1 : -1;
+}
+
+// Warp-aggregated status update of the exchange kernels.
+__device__ __forceinline__ void exchange_status(Status *st, int my_max, unsigned my_flags,
+                                                unsigned long long my_bad) {
+  const unsigned full = 0xffffffffu;
+  int wmax = __reduce_max_sync(full, my_max);
+  unsigned wflags = __reduce_or_sync(full, my_flags);
+  unsigned long long wbad = my_bad;
+  for (int o = 16; o > 0; o >>= 1) wbad = min(wbad, __shfl_xor_sync(full, wbad, o));
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&st->max_iter, wmax);
+    if (wflags) {
+      atomicOr(&st->flags, wflags);
+      atomicMin(&st->first_bad, wbad);
+    }
+  }
+}
+
+// Mixed-precision Newton for one cell: the residuals F_G, F_R are evaluated
+// in FP64 at the FP64 iterate (R = A E_g^4 - k E_r as in newton_exchange,
+// with the coefficients A, k given to FP32 accuracy), the convergence test on
+// their FP32 roundings against the FP32 thresholds, and the 2x2 correction
+// (the same elimination as newton_exchange) is solved in FP32 (iterative
+// refinement: each iteration gains ~7 digits, so two iterations from an FP32
+// warm start reach the 1e-10 tolerance).  Returns the iteration count or -1.
+__device__ __forceinline__ int newton_refine(bool alpha_eos, int max_iter, double A, double k,
+                                             double cr, double Eg0, double Er0, float Af,
+                                             float kf, float crf, float thr_g, float thr_r,
+                                             double &Eg, double &Er) {
+  const float dFG_dEr = -crf * kf, dFR_dEr = 1.0f + kf;
+  const float A4 = 4.0f * Af;
+  bool conv = false;
+  int it = 0;
+  for (it = 0; it < max_iter; ++it) {
+    double Rr;
+    float dRdEg;
+    if (alpha_eos) {
+      Rr = fma(A, Eg, -(k * Er));
+      dRdEg = Af;
+    } else {
+      const double E2 = Eg * Eg;
+      Rr = fma(A, E2 * E2, -(k * Er));
+      const float Ef = (float)Eg;
+      dRdEg = A4 * Ef * Ef * Ef;
+    }
+    const float fg = (float)((Eg - Eg0) + cr * Rr);
+    const float fr = (float)((Er - Er0) - Rr);
+    conv = fabsf(fg) < thr_g && fabsf(fr) < thr_r;
+    const float G = 1.0f + crf * dRdEg;
+    const float D1 = dFR_dEr * G + dRdEg * dFG_dEr;
+    const float inv = qrcp(D1 * G);
+    const float dEr = -(fr * G + dRdEg * fg) * (G * inv);
+    const float dEg = -(fg + dEr * dFG_dEr) * (D1 * inv);
+    Er += (double)dEr;
+    Eg += (double)dEg;
+    if (conv) break;
+  }
+  return conv ? it + 1 : -1;
+}
+
+// Constants of the exchange (host or device; the substep dt is passed apart,
+// since inside a captured step it is read from device memory).
+struct ExK {
+  double cr, icc_d, rc_d, inv_cv;
+  double a_e;             // a_r, or 4 a_r/alpha for the alpha T^3 heat capacity
+  float icc, rc, icc_lo;  // FP32 forms; icc_lo: 1/(c chat) - icc
+  float crf, a_ef, inv_cvf, kchat;  // kchat: kappa_P chat (or kappa0 chat)
+};
+__host__ __device__ __forceinline__ ExK make_exk(const qk_params &p) {
+  ExK K;
+  K.cr = p.c / p.chat;
+  K.icc_d = 1.0 / (p.chat * p.c);
+  K.rc_d = p.chat / p.c;
+  K.inv_cv = p.eos == QK_EOS_ALPHA_T3 ? 0.0 : 1.0 / p.c_v;
+  K.a_e = p.eos == QK_EOS_ALPHA_T3 ? 4.0 * p.a_r / p.alpha_eos : p.a_r;
+  K.icc = (float)K.icc_d;
+  K.rc = (float)K.rc_d;
+  K.icc_lo = (float)(K.icc_d - (double)K.icc);
+  K.crf = (float)K.cr;
+  K.a_ef = (float)K.a_e;
+  K.inv_cvf = (float)K.inv_cv;
+  K.kchat = (float)(p.kappa_P * p.chat);
+  return K;
+}
+
+// Per-thread status of the exchange cells it processed.
+struct ExStat {
+  int max = 0;
+  unsigned flags = 0;
+  unsigned long long bad = ~0ull;
+};
+
+// FP64 exchange of cell e: (er, fr) is the radiation state after the
+// transport (read from R by the exchange kernel, or the stage-2 result in
+// registers); reads the gas state from U, writes U and R.
+template <typename T>
+__device__ __forceinline__ void exchange_cell(const qk_params &p, const ExK &K, double dt, F5<T> U,
+                                              F4<T> R, const T *src, long long e, double er,
+                                              const double fr[3], ExStat &xs) {
+  const double rho = load_d(U.f[0], e);
+  double m[3] = {load_d(U.f[1], e), load_d(U.f[2], e), load_d(U.f[3], e)};
+  const double E = load_d(U.f[4], e);
+  const double Er0 = er;
+  const double kP = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_P * rho : p.kappa_P;
+  const double kF = p.kappa_mode == QK_KAPPA_RHO ? p.kappa_R * rho : p.kappa_R;
+  const double m2 = (m[0] * m[0] + m[1] * m[1]) + m[2] * m[2];
+  // one reciprocal serves 1/rho and the flux damping 1/(1 + rho kF chat dt)
+  const double Dm = 1.0 + rho * kF * p.chat * dt;
+  const double inv_rho_Dm = frcp(rho * Dm);
+  const double inv_rho = Dm * inv_rho_Dm;
+  const double damp = rho * inv_rho_Dm;
+  const double Ekin0 = 0.5 * m2 * inv_rho;
+  const double Eg0 = E - Ekin0;
+  const double thr_g = p.eps_newton * (Eg0 + K.cr * Er0);
+  const double thr_r = thr_g * K.rc_d;
+  const double k = dt * rho * kP * p.chat;
+  double A = k * K.a_e;
+  if (p.eos != QK_EOS_ALPHA_T3) {
+    const double i2 = (inv_rho * K.inv_cv) * (inv_rho * K.inv_cv);
+    A *= i2 * i2;
+  }
+  // radiation source S = dt (chat/c) j, carried in the residual's E_r0
+  const double Er0S = src ? Er0 + dt * K.rc_d * load_d(src, e) : Er0;
+  double Eg = Eg0, Er = Er0;
+  int it;
+  it = newton_exchange<double>(p.eos == QK_EOS_ALPHA_T3, A, k, K.cr, Eg0, Er0S, thr_g, thr_r,
+                               p.max_iter, Eg, Er);
+  if (it < 0) {
+    xs.flags |= 1u << QK_ENOCONV;
+    xs.bad = min(xs.bad, (unsigned long long)e);
+  } else {
+    xs.max = max(xs.max, it);
+  }
+  // flux source (backward Euler) and the equal and opposite momentum change
+  double mn[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double F0 = fr[a];
+    const double Fn = F0 * damp;
+    mn[a] = m[a] - (Fn - F0) * K.icc_d;
+    R.f[1 + a][e] = (T)Fn;
+    U.f[1 + a][e] = (T)mn[a];
+  }
+  // work of the radiation force through the kinetic-energy change
+  const double Ekin1 = 0.5 * ((mn[0] * mn[0] + mn[1] * mn[1]) + mn[2] * mn[2]) * inv_rho;
+  const double dEkin = Ekin1 - Ekin0;
+  U.f[4][e] = (T)(Eg + (Ekin0 + dEkin));
+  const double Er_new = Er - K.rc_d * dEkin;
+  R.f[0][e] = (T)Er_new;
+  if (!pos_finite(Eg) || !pos_finite(Er_new)) {
+    xs.flags |= 1u << QK_ENEGATIVE;
+    xs.bad = min(xs.bad, (unsigned long long)e);
+  }
+}
+
+// FP32-mixed exchange of cell e (see exchange_kernel_mixed): (er, fr) the
+// radiation state after the transport, (er_lo, fr_lo) its low parts (CP).
+// FP32 state; the internal energy recovered with the error-free FP32
+// transforms of con2prim; the Newton solve with FP64 residuals and
+// convergence test (FP32 warm start, then newton_refine); the flux source,
+// momentum and kinetic-energy work in FP32, the new total energy accumulated
+// in FP64 before the final rounding.
+// CP: compensated state (every conserved field hi + lo; UL, RL the lo
+// arrays): E, E_r, m and F are read as hi + lo, the new E and E_r are formed
+// in FP64 from the invariant E + (c/chat) E_r (the kinetic-energy change
+// taken from the FP64 difference of the same two values), and the momentum
+// exchange m + F/(c chat) = const is carried in double-float with a
+// double-float 1/(c chat), so that both invariants hold to ~2^-48.
+template <bool CP>
+__device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const ExK &K, double dt,
+                                                    F5<float> U, F4<float> R, F5<float> UL,
+                                                    F4<float> RL, const float *src, long long e,
+                                                    float er, float er_lo, const float fr[3],
+                                                    const float fr_lo[3], ExStat &xs) {
+  float u[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
+  const float rho = u[0];
+  float rinv = qrcp(rho);
+  rinv = rinv * fmaf(-rho, rinv, 2.0f);  // one Newton step: ~1 ulp
+  float eg_hi, eg_lo;
+  internal_energy_f32(u, rho, rinv, eg_hi, eg_lo);  // ~48-bit E_g, no EOS round trip
+  const float Er0f = er;
+  double Eg0 = (double)eg_hi + (double)eg_lo;
+  double Er0 = (double)Er0f;
+  float E_lo = 0.0f;
+  if constexpr (CP) {
+    E_lo = UL.f[4][e];
+    Eg0 += (double)E_lo;
+    Er0 += (double)er_lo;
+  }
+  // the coefficients in FP32: k = dt rho kappa_P chat, A = k a_r/(rho c_v)^4
+  // (or 4 k a_r/alpha), and the convergence thresholds eps E_tot,
+  // eps E_tot chat/c (E_tot = E_g0 + (c/chat) E_r0)
+  const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
+  const float kf = (float)dt * K.kchat * (p.kappa_mode == QK_KAPPA_RHO ? rho * rho : rho);
+  float Af = kf * K.a_ef;
+  if (!alpha_eos) {
+    const float i1 = rinv * K.inv_cvf, i2 = i1 * i1;
+    Af *= i2 * i2;
+  }
+  const double k = (double)kf, A = (double)Af;
+  const float Eg0f = eg_hi + (eg_lo + E_lo);
+  const float Etotf = Eg0f + K.crf * (Er0f + er_lo);
+  const float thr_g = (float)p.eps_newton * Etotf, thr_r = thr_g * K.rc;
+  // radiation source S = dt (chat/c) j, carried in the residual's E_r0
+  const double Er0S = src ? Er0 + dt * K.rc_d * (double)src[e] : Er0;
+  // FP32 warm start to 1e-6
+  float Egf = Eg0f, Erf = src ? (float)Er0S : Er0f;
+  const int itf = newton_exchange<float>(alpha_eos, Af, kf, K.crf, Eg0f, Erf, 1e-6f * Etotf,
+                                         1e-6f * Etotf * K.rc, 12, Egf, Erf);
+  double Eg = Eg0, Er = Er0;
+  if (itf > 0 && Egf > 0.0f && Erf > 0.0f && isfinite(Egf) && isfinite(Erf)) {
+    Eg = Egf;
+    Er = Erf;
+  }
+  const int it = newton_refine(alpha_eos, p.max_iter, A, k, K.cr, Eg0, Er0S, Af, kf, K.crf,
+                               thr_g, thr_r, Eg, Er);
+  if (it < 0) {
+    xs.flags |= 1u << QK_ENOCONV;
+    xs.bad = min(xs.bad, (unsigned long long)e);
+  } else {
+    xs.max = max(xs.max, it);
+  }
+  const float kF = p.kappa_mode == QK_KAPPA_RHO ? (float)p.kappa_R * rho : (float)p.kappa_R;
+  const float damp = qrcp(1.0f + rho * kF * (float)(p.chat * dt));
+  float mn[3];
+  float ke0 = 0.0f, ke1 = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float F0 = fr[a];
+    if constexpr (CP) {
+      // dF = F0 (damp - 1); F += dF and m -= dF/(c chat), both in double-float
+      float Fl = fr_lo[a];
+      const float dF = (F0 + Fl) * (damp - 1.0f);
+      float Fh = F0;
+      df_add(Fh, Fl, dF);
+      df_norm(Fh, Fl);
+      R.f[1 + a][e] = Fh;
+      RL.f[1 + a][e] = Fl;
+      const float p1 = __fmul_rn(dF, K.icc);
+      const float e1 = fmaf(dF, K.icc, -p1) + dF * K.icc_lo;
+      float mh = u[1 + a], ml = UL.f[1 + a][e];
+      df_add(mh, ml, -p1);
+      ml = __fsub_rn(ml, e1);
+      df_norm(mh, ml);
+      U.f[1 + a][e] = mh;
+      UL.f[1 + a][e] = ml;
+      mn[a] = mh;
+    } else {
+      const float Fn = F0 * damp;
+      mn[a] = u[1 + a] - (Fn - F0) * K.icc;
+      R.f[1 + a][e] = Fn;
+      U.f[1 + a][e] = mn[a];
+    }
+    ke0 = fmaf(u[1 + a], u[1 + a], ke0);
+    ke1 = fmaf(mn[a], mn[a], ke1);
+  }
+  const float Ekin1 = 0.5f * ke1 * rinv;
+  double Er_new;
+  if constexpr (CP) {
+    // E_new = E_g + E_kin,1; E_r,new = E_r - (chat/c)(E_kin,1 - E_kin,0) with
+    // E_kin,0 = E - E_g0 (the same FP64 values), split into hi + lo
+    const double Ekin0 = ((double)u[4] + (double)E_lo) - Eg0;
+    const double Enew = Eg + (double)Ekin1;
+    Er_new = Er - (K.rc_d) * ((double)Ekin1 - Ekin0);
+    const float Eh = (float)Enew, Rh = (float)Er_new;
+    U.f[4][e] = Eh;
+    UL.f[4][e] = (float)(Enew - (double)Eh);
+    R.f[0][e] = Rh;
+    RL.f[0][e] = (float)(Er_new - (double)Rh);
+  } else {
+    const float dEkin = 0.5f * (ke1 - ke0) * rinv;
+    U.f[4][e] = (float)(Eg + (double)Ekin1);
+    Er_new = Er - (double)(K.rc * dEkin);
+    R.f[0][e] = (float)Er_new;
+  }
+  if (!pos_finite(Eg) || !pos_finite(Er_new)) {
+    xs.flags |= 1u << QK_ENEGATIVE;
+    xs.bad = min(xs.bad, (unsigned long long)e);
+  }
+}
+
+}  // namespace qk

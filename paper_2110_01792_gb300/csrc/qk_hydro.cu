@@ -10,9 +10,11 @@
 namespace qk {
 
 template <typename T> struct HydroSmem {
+  static constexpr bool kF = sizeof(T) == 8;
   T prim[5][NCROSS];   // rho, vx, vy, vz, P of the tile and its cross halo
   T rec[10][NREC];     // per line position: qL, qR of each primitive
   T flux[5][NFLUX];    // per face: mass, momentum x/y/z, energy
+  T iface[kF ? 5 : 1][kF ? NIF : 1];  // FP64 PPM: interface values, once per face
 };
 
 template <typename T, int D, int NT, int NOWN, bool CP>
@@ -21,6 +23,15 @@ __device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T in
                                           const DevBox &bx, int ng, int x0, int y0, int z0,
                                           T (&acc)[NOWN][5], T (&accl)[NOWN][5], T cdt) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  // FP64 PPM: the interface values first, once per face
+  bool shared_faces = false;
+  if constexpr (HydroSmem<T>::kF) {
+    if (rk != QK_RECON_PLM) {
+      ppm_faces_pass<D, NT, 5>(sm.prim, sm.iface, v);
+      shared_faces = true;
+      __syncthreads();
+    }
+  }
   // Phase A: reconstruction of every needed position of every line along D.
   for (int it = threadIdx.x; it < NREC; it += NT) {
     int pos, c[3];
@@ -36,11 +47,25 @@ __device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T in
     // shock flattening: blend the face states with the cell average,
     // q <- chi q + (1 - chi) q_cell (chi from the flattening pre-pass)
     const T ch = chi ? chi[cell_elem(bx, ng, x0 + c[0], y0 + c[1], z0 + c[2])] : T(1);
+    int fl = 0, fr = 0;
+    if (shared_faces) {
+      fl = item_index<D>(pos, c[0], c[1], c[2], NIFP);
+      fr = item_index<D>(pos + 1, c[0], c[1], c[2], NIFP);
+    }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       T qL, qR;
-      recon<T>(rk, sm.prim[q][s[0]], sm.prim[q][s[1]], sm.prim[q][s[2]], sm.prim[q][s[3]],
-               sm.prim[q][s[4]], qL, qR);
+      if constexpr (HydroSmem<T>::kF) {
+        if (shared_faces)
+          ppm_limit(sm.iface[q][fl], sm.iface[q][fr], sm.prim[q][s[1]], sm.prim[q][s[2]],
+                    sm.prim[q][s[3]], qL, qR);
+        else
+          recon<T>(rk, sm.prim[q][s[0]], sm.prim[q][s[1]], sm.prim[q][s[2]], sm.prim[q][s[3]],
+                   sm.prim[q][s[4]], qL, qR);
+      } else {
+        recon<T>(rk, sm.prim[q][s[0]], sm.prim[q][s[1]], sm.prim[q][s[2]], sm.prim[q][s[3]],
+                 sm.prim[q][s[4]], qL, qR);
+      }
       if (chi) {
         const T qc = sm.prim[q][s[2]];
         qL = ch * qL + (T(1) - ch) * qc;

@@ -29,6 +29,8 @@ constexpr int NCROSS = NCORE + 3 * NHD;
 constexpr int NPOS = TS + 2;
 constexpr int NFACE = TS + 1;
 constexpr int NREC = NPOS * TS * TS;
+constexpr int NIFP = TS + 3;            // PPM interface values per line (FP64)
+constexpr int NIF = NIFP * TS * TS;
 constexpr int NFLUX = NFACE * TS * TS;
 
 struct DevBox {
@@ -225,10 +227,19 @@ cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_
                                const LoPtrs *lo = nullptr);
 cudaError_t launch_flatten(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                            void *chi, cudaStream_t s);
+// The exchange fused into radiation stage 2: gas fields (and their low parts
+// for a compensated state, else NULL), emissivity field or NULL, status word.
+struct FuseArgs {
+  void *const *U;
+  void *const *Ulo;
+  const void *src;
+  Status *st;
+};
+
 cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                              void *const *R0, void *const *R1, void *const *Rout,
                              const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s,
-                             const LoPtrs *lo = nullptr);
+                             const LoPtrs *lo = nullptr, const FuseArgs *fx = nullptr);
 cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                             void *const *R, const void *src, DtSrc dt, Status *st,
                             cudaStream_t s, void *const *Ulo = nullptr,

@@ -5,7 +5,7 @@
 // factors, optical-depth correction, RSLA fluxes (eqs. rad_energy, rad_flux),
 // divergence and RK combination.  Same tile scheme as the hydro stage.
 #pragma once
-#include "qk_device.cuh"
+#include "qk_exchange.cuh"
 
 namespace qk {
 
@@ -19,8 +19,20 @@ template <typename T> struct RadSmem {
   T rk[NCROSS];                    // rho kappa_R of the cell
   T ab[2][kAB ? NCROSS : 1];       // FP64: Levermore a, b of the cell-average state
   T rec[8][NREC];                  // qL, qR of each reconstructed variable
+  T iface[kAB ? 4 : 1][kAB ? NIF : 1];  // FP64 PPM: interface values, once per face
   T sq[kAB ? 1 : NREC];            // FP32: sqrt(T_DD) of the cell average per position
   T flux[4][NFLUX];
+};
+
+// The matter-radiation exchange fused into the epilogue of stage 2 (qk_step):
+// the gas fields U (and their low parts UL for a compensated state), the
+// emissivity field or NULL, and the status word.  on = 0: plain stage.
+template <typename T> struct ExFuse {
+  F5<T> U, UL;
+  const T *src;
+  Status *st;
+  ExK K;
+  int on;
 };
 
 template <typename T> __device__ __forceinline__ T kappa_of(const qk_params &p, double k, T rho) {
@@ -131,6 +143,15 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
   const T hccc = T(0.5) * c * chat;
   const T hchat_c = T(0.5) * chat / c;
+  // FP64 PPM: the interface values first, once per face
+  bool shared_faces = false;
+  if constexpr (RadSmem<T>::kAB) {
+    if (rk != QK_RECON_PLM) {
+      ppm_faces_pass<D, NT, 4>(sm.prim, sm.iface, v);
+      shared_faces = true;
+      __syncthreads();
+    }
+  }
   for (int it = threadIdx.x; it < NREC; it += NT) {
     int pos, cc[3];
     item_cell<D>(it, NPOS, pos, cc[0], cc[1], cc[2]);
@@ -141,6 +162,21 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
       int x[3] = {cc[0], cc[1], cc[2]};
       x[D] += o - 2;
       s[o] = cross_slot(x[0], x[1], x[2]);
+    }
+    if constexpr (RadSmem<T>::kAB) {
+      if (shared_faces) {
+        const int fl = item_index<D>(pos, cc[0], cc[1], cc[2], NIFP);
+        const int fr = item_index<D>(pos + 1, cc[0], cc[1], cc[2], NIFP);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          T qL, qR;
+          ppm_limit(sm.iface[q][fl], sm.iface[q][fr], sm.prim[q][s[1]], sm.prim[q][s[2]],
+                    sm.prim[q][s[3]], qL, qR);
+          sm.rec[2 * q][it] = qL;
+          sm.rec[2 * q + 1][it] = qR;
+        }
+        continue;
+      }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -216,13 +252,23 @@ __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx
 }
 
 // CP (FP32 only): compensated state hi + lo (L0, L1, Lo the lo arrays of R0,
-// R1, Ro), as in the hydro stage.
-template <typename T, int STAGE, int NT, int CL, bool CP>
-__global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, F4<T> R0,
-                                                       F4<T> R1, F4<T> Ro, const T *rho,
-                                                       DtSrc dts, int sched, F4<T> L0, F4<T> L1,
-                                                       F4<T> Lo) {
+// R1, Ro), as in the hydro stage.  EX (stage 2 only): the matter-radiation
+// exchange of every owned cell after its update (xf: the gas fields, the
+// emissivity and the status word).
+// FP32 kernels with the fused exchange are held to the registers of three
+// CTAs per SM (as many as their shared memory allows), the exchange's FP64
+// temporaries spilling to L1 rather than halving the resident warps.
+template <typename T, int NT, bool EX> struct RadMinBlocks {
+  static constexpr int value = (EX && sizeof(T) == 4) ? (NT == 128 ? 6 : (NT == 256 ? 3 : 1)) : 1;
+};
+
+template <typename T, int STAGE, int NT, int CL, bool CP, bool EX>
+__device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_params &p, F4<T> R0,
+                                               F4<T> R1, F4<T> Ro, const T *rho, DtSrc dts,
+                                               int sched, F4<T> L0, F4<T> L1, F4<T> Lo,
+                                               const ExFuse<T> &xf) {
   if (skip_substep(dts)) return;
+  ExStat xs;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RadSmem<T> &sm = *reinterpret_cast<RadSmem<T> *>(smem_raw);
   constexpr int NOWN = NCORE / NT;
@@ -298,6 +344,7 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
       int i = s % TS, j = (s / TS) % TS, k = s / (TS * TS);
       if (i >= v[0] || j >= v[1] || k >= v[2]) continue;
       long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
+      T rv[4], rl[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if constexpr (CP) {
@@ -311,26 +358,77 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
             h *= T(0.5);
             l *= T(0.5);
           }
-          Ro.f[q][e] = h;
-          Lo.f[q][e] = l;
+          rv[q] = h;
+          rl[q] = l;
         } else {
           T L = -acc[m][q];
           if (STAGE == 1) {
-            Ro.f[q][e] = own[m][q] + dt * L;
+            rv[q] = own[m][q] + dt * L;
           } else {
             T u0 = R0.f[q][e];
-            Ro.f[q][e] = T(0.5) * u0 + T(0.5) * (own[m][q] + dt * L);
+            rv[q] = T(0.5) * u0 + T(0.5) * (own[m][q] + dt * L);
           }
+          rl[q] = T(0);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        Ro.f[q][e] = rv[q];
+        if constexpr (CP) Lo.f[q][e] = rl[q];
+      }
+    }
+    if constexpr (EX) {
+      // the exchange of the owned cells on the state just stored (read back
+      // by the same thread, from L1/L2); one cell at a time keeps the
+      // exchange's registers apart from the sweeps'
+#pragma unroll 1
+      for (int m = 0; m < NOWN; ++m) {
+        int s = threadIdx.x + m * NT;
+        int i = s % TS, j = (s / TS) % TS, k = s / (TS * TS);
+        if (i >= v[0] || j >= v[1] || k >= v[2]) continue;
+        long long e = cell_elem(b, g.ng, tl.x0 + i, tl.y0 + j, tl.z0 + k);
+        if constexpr (sizeof(T) == 8) {
+          const double fr[3] = {(double)Ro.f[1][e], (double)Ro.f[2][e], (double)Ro.f[3][e]};
+          exchange_cell<T>(p, xf.K, dt_of(dts), xf.U, Ro, xf.src, e, (double)Ro.f[0][e], fr,
+                           xs);
+        } else {
+          const float fr[3] = {Ro.f[1][e], Ro.f[2][e], Ro.f[3][e]};
+          float fl[3] = {0.0f, 0.0f, 0.0f}, el = 0.0f;
+          if constexpr (CP) {
+            el = Lo.f[0][e];
+            fl[0] = Lo.f[1][e];
+            fl[1] = Lo.f[2][e];
+            fl[2] = Lo.f[3][e];
+          }
+          exchange_cell_mixed<CP>(p, xf.K, dt_of(dts), xf.U, Ro, xf.UL, Lo, xf.src, e,
+                                  Ro.f[0][e], el, fr, fl, xs);
         }
       }
     }
   }
+  if constexpr (EX) exchange_status(xf.st, xs.max, xs.flags, xs.bad);
+}
+
+template <typename T, int STAGE, int NT, int CL, bool CP>
+__global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, F4<T> R0,
+                                                       F4<T> R1, F4<T> Ro, const T *rho,
+                                                       DtSrc dts, int sched, F4<T> L0, F4<T> L1,
+                                                       F4<T> Lo, ExFuse<T> xf) {
+  rad_stage_body<T, STAGE, NT, CL, CP, false>(g, p, R0, R1, Ro, rho, dts, sched, L0, L1, Lo, xf);
+}
+
+template <typename T, int NT, int CL, bool CP>
+__global__ void __launch_bounds__(NT, (RadMinBlocks<T, NT, true>::value))
+    rad_stage_ex_kernel(Geometry g, qk_params p, F4<T> R0, F4<T> R1, F4<T> Ro, const T *rho,
+                        DtSrc dts, int sched, F4<T> L0, F4<T> L1, F4<T> Lo, ExFuse<T> xf) {
+  rad_stage_body<T, 2, NT, CL, CP, true>(g, p, R0, R1, Ro, rho, dts, sched, L0, L1, Lo, xf);
 }
 
 template <typename T, int STAGE, int NT, int CL, bool CP>
 static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const *R0,
                               void *const *R1, void *const *Ro, const void *rho, DtSrc dt,
-                              int grid, int sched, const LoPtrs &lo, cudaStream_t s) {
+                              int grid, int sched, const LoPtrs &lo, const FuseArgs *fx,
+                              cudaStream_t s) {
   F4<T> a, b, c, l0{}, l1{}, lo_{};
   for (int q = 0; q < 4; ++q) {
     a.f[q] = (T *)R0[q];
@@ -342,8 +440,21 @@ static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const
       lo_.f[q] = (T *)lo.lo[q];
     }
   }
+  ExFuse<T> xf{};
+  if (fx && STAGE == 2) {
+    for (int q = 0; q < 5; ++q) {
+      xf.U.f[q] = (T *)fx->U[q];
+      xf.UL.f[q] = fx->Ulo ? (T *)fx->Ulo[q] : nullptr;
+    }
+    xf.src = (const T *)fx->src;
+    xf.st = fx->st;
+    xf.K = make_exk(p);
+    xf.on = 1;
+  }
   int smem = (int)sizeof(RadSmem<T>);
   auto kern = rad_stage_kernel<T, STAGE, NT, CL, CP>;
+  if constexpr (STAGE == 2)
+    if (xf.on) kern = rad_stage_ex_kernel<T, NT, CL, CP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   if (grid <= 0) {
@@ -355,42 +466,46 @@ static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const
   }
   if (grid > g.ntiles) grid = g.ntiles;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, (const T *)rho, dt, sched, l0, l1, lo_);
+  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, (const T *)rho, dt, sched, l0, l1, lo_, xf);
   return cudaGetLastError();
 }
 
 template <typename T, int STAGE, int CL, bool CP>
 static cudaError_t launch_nt(const Geometry &g, const qk_params &p, void *const *R0,
                              void *const *R1, void *const *Ro, const void *rho, DtSrc dt,
-                             int grid, int cfg, const LoPtrs &lo, cudaStream_t s) {
+                             int grid, int cfg, const LoPtrs &lo, const FuseArgs *fx,
+                             cudaStream_t s) {
   const int sched = cfg_sched(cfg);
   switch (cfg_threads(cfg)) {
-    case 128: return launch_one<T, STAGE, 128, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, s);
-    case 512: return launch_one<T, STAGE, 512, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, s);
-    default: return launch_one<T, STAGE, 256, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, s);
+    case 128:
+      return launch_one<T, STAGE, 128, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, fx, s);
+    case 512:
+      return launch_one<T, STAGE, 512, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, fx, s);
+    default:
+      return launch_one<T, STAGE, 256, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, fx, s);
   }
 }
 
 // All stage kernels of one closure (instantiated in qk_rad.cu and
 // qk_rad_closures.cu, which nvcc compiles in parallel).  `lo` non-null selects
-// the compensated FP32 kernels.
+// the compensated FP32 kernels; `fx` non-null fuses the exchange into stage 2.
 template <int CL>
 cudaError_t launch_rad_closure(int fp32, int stage, const Geometry &g, const qk_params &p,
                                void *const *R0, void *const *R1, void *const *Rout,
                                const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s,
-                               const LoPtrs *lo) {
+                               const LoPtrs *lo, const FuseArgs *fx) {
   if (fp32 && lo)
     return stage == 1
-               ? launch_nt<float, 1, CL, true>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, s)
-               : launch_nt<float, 2, CL, true>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, s);
+               ? launch_nt<float, 1, CL, true>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, fx, s)
+               : launch_nt<float, 2, CL, true>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, fx, s);
   const LoPtrs none{};
   if (fp32)
     return stage == 1
-               ? launch_nt<float, 1, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, s)
-               : launch_nt<float, 2, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, s);
+               ? launch_nt<float, 1, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s)
+               : launch_nt<float, 2, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s);
   return stage == 1
-             ? launch_nt<double, 1, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, s)
-             : launch_nt<double, 2, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, s);
+             ? launch_nt<double, 1, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s)
+             : launch_nt<double, 2, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s);
 }
 
 }  // namespace qk

@@ -6,9 +6,9 @@ namespace qk {
 
 template cudaError_t launch_rad_closure<QK_CLOSURE_MINERBO>(
     int, int, const Geometry &, const qk_params &, void *const *, void *const *, void *const *,
-    const void *, DtSrc, int, int, cudaStream_t, const LoPtrs *);
+    const void *, DtSrc, int, int, cudaStream_t, const LoPtrs *, const FuseArgs *);
 template cudaError_t launch_rad_closure<QK_CLOSURE_EDDINGTON>(
     int, int, const Geometry &, const qk_params &, void *const *, void *const *, void *const *,
-    const void *, DtSrc, int, int, cudaStream_t, const LoPtrs *);
+    const void *, DtSrc, int, int, cudaStream_t, const LoPtrs *, const FuseArgs *);
 
 }  // namespace qk

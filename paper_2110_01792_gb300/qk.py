@@ -75,6 +75,8 @@ def lib():
     L.qk_set_params.argtypes = [vp, P(Params)]
     L.qk_set_graph.argtypes = [vp, i32]
     L.qk_set_launch_mode.argtypes = [vp, i32]
+    L.qk_set_fused_exchange.argtypes = [vp, i32]
+    L.qk_rad_stage2_exchange.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), dbl, vp]
     L.qk_autotune.argtypes = [vp, P(vp), P(vp), P(i32), vp]
     L.qk_fill_ghosts.argtypes = [vp, P(vp), i32, vp]
     L.qk_hydro_stage.argtypes = [vp, i32, P(vp), P(vp), P(vp), dbl, vp]
@@ -113,7 +115,7 @@ def lib():
     for f in ("qk_init_level", "qk_amr_init", "qk_amr_info", "qk_amr_interp", "qk_amr_register",
               "qk_amr_sync", "qk_set_tile_part", "qk_tile_counts", "qk_fill_plan", "qk_fill_ghosts_range", "qk_set_dirichlet", "qk_set_source",
               "qk_init_shard", "qk_halo_info", "qk_halo_pack", "qk_halo_unpack",
-              "qk_signal_speed", "qk_set_timestep", "qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_autotune",
+              "qk_signal_speed", "qk_set_timestep", "qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_set_fused_exchange", "qk_rad_stage2_exchange", "qk_autotune",
               "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
               "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
               "qk_status", "qk_step_info", "qk_eval_math", "qk_step_compensated",
@@ -293,6 +295,9 @@ class Context:
         return {n: (int(v) & 0xffff, "contiguous" if (int(v) >> 16) & 1 else "strided")
                 for n, v in zip(names, out[:])}
 
+    def set_fused_exchange(self, enable: bool):
+        self._check(self._L.qk_set_fused_exchange(self._h, 1 if enable else 0))
+
     def set_graph(self, enable: bool):
         self._check(self._L.qk_set_graph(self._h, 1 if enable else 0))
 
@@ -322,6 +327,12 @@ class Context:
         self._check(self._L.qk_rad_stage(self._h, stage, _ptrs(R0, 4), _ptrs(R1, 4),
                                          _ptrs(Rout, 4), C.c_void_p(int(rho.data_ptr())),
                                          float(dt), _stream(stream)))
+
+    def rad_stage2_exchange(self, R0, R1, Rout, U, dt, stream=None):
+        """Radiation stage 2 with the exchange fused into its epilogue."""
+        self._check(self._L.qk_rad_stage2_exchange(self._h, _ptrs(R0, 4), _ptrs(R1, 4),
+                                                   _ptrs(Rout, 4), _ptrs(U, 5), float(dt),
+                                                   _stream(stream)))
 
     def exchange(self, U, R, dt, stream=None):
         self._check(self._L.qk_rad_matter_exchange(self._h, _ptrs(U, 5), _ptrs(R, 4), float(dt),

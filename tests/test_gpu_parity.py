@@ -390,6 +390,40 @@ def test_per_patch_launches_match_batched(torch_cuda):
         assert np.array_equal(G.interior(lay, a), G.interior(lay, b))
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fused_exchange_matches_separate_launch(torch_cuda, prec):
+    """The exchange fused into the epilogue of radiation stage 2 gives the same
+    bits as its own launch after the stage (it reads the same values), with a
+    radiation source, in FP64 and FP32-mixed, and for a compensated state."""
+    torch = torch_cuda
+    lay, prob, prm = _small_rhd()
+    tdt = torch.float64 if prec == 0 else torch.float32
+    rng = np.random.Generator(np.random.Philox(5))
+    src = rng.uniform(0.0, 2.0, lay.field_len)
+    outs = []
+    for fused in (True, False):
+        for comp in ((False, True) if prec == 1 else (False,)):
+            ctx = _ctx(lay, prm, prec)
+            ctx.set_fused_exchange(fused)
+            j = torch.from_numpy(src).to(tdt).cuda()
+            ctx.set_source(j)
+            dU, dR = G.dev(prob.U, tdt), G.dev(prob.R, tdt)
+            lo = None
+            if comp:
+                lo = ([torch.zeros_like(a) for a in dU], [torch.zeros_like(a) for a in dR])
+            for _ in range(3):
+                ctx.step(dU, dR, lo=lo)
+            st = ctx.status()
+            ctx.close()
+            assert st[0] == 0, st
+            res = G.host(dU) + G.host(dR) + (G.host(lo[0]) + G.host(lo[1]) if comp else [])
+            outs.append([G.interior(lay, a) for a in res])
+    half = len(outs) // 2
+    for a, b in zip(outs[:half], outs[half:]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
 def test_autotune_keeps_state_and_results(torch_cuda):
     """qk_autotune leaves the interior state untouched, returns one of the
     candidate configurations per stage kernel, and updates computed with the
