@@ -244,10 +244,9 @@ def time_kernel(torch, fn, reps, stream):
 # (profiles/ncu_*_128.md), valid only while the kernel's sources hash to the
 # value recorded at capture time.
 NCU_TRAFFIC = {
-    ("rhd128", "rad_stage_kernel<double,1>"): (136.33e6, "rad", "a4001c8e823b"),
-    ("rhd128", "hydro_stage_kernel<double,1>"): (152.35e6, "hydro", "735146949d70"),
-    ("rhd128", "hydro_stage_kernel<float,1>"): (105.66e6, "hydro", "735146949d70"),
-    ("rhd128", "exchange_kernel_mixed"): (95.45e6, "cell", "071a2ba2f58e"),
+    ("rhd128", "rad_stage_ex_kernel<double>"): (344.13e6, "rad", "d0a5a6cf9b03"),
+    ("rhd128", "rad_stage_ex_kernel<float>"): (418.56e6, "rad", "d0a5a6cf9b03"),
+    ("rhd128", "hydro_stage_kernel<float,1>"): (105.54e6, "hydro", "e8b211bfaf7f"),
 }
 
 

@@ -48,6 +48,9 @@ static Geometry geom(const qk_ctx *c) {
     g.tiles = c->d_tiles_ib + c->n_interior;
     g.ntiles = c->ntiles - c->n_interior;
   }
+  // columns cover every owned cell: only for the whole tile set
+  g.cols = c->part == QK_PART_ALL ? c->d_cols : nullptr;
+  g.ncols = c->part == QK_PART_ALL ? c->ncols : 0;
   g.nbox = c->nbox_dev;
   g.ng = c->ng;
   g.ncells = c->ncells;
@@ -339,6 +342,7 @@ static void release(qk_ctx *c) {
   cudaFree(c->d_boxes);
   cudaFree(c->d_tiles);
   cudaFree(c->d_tiles_ib);
+  cudaFree(c->d_cols);
   cudaFree(c->d_cell0);
   cudaFree(c->d_copies);
   cudaFree(c->d_chunks);
@@ -445,6 +449,21 @@ static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, in
   }
   c->tile_start[nown] = (int)tiles.size();
   c->ntiles = (int)tiles.size();
+  // column work list: CW x CW footprints, z split into chunks of CZ planes
+  // (halved while there are fewer than four items per SM of a GB300)
+  std::vector<Column> cols;
+  for (int cz = CZ; cz >= 4; cz /= 2) {
+    cols.clear();
+    for (int l = 0; l < nown; ++l) {
+      const qk_box &q = boxes[c->own[l]];
+      for (int y = 0; y < q.n[1]; y += CW)
+        for (int x = 0; x < q.n[0]; x += CW)
+          for (int z = 0; z < q.n[2]; z += cz)
+            cols.push_back(Column{l, x, y, z, std::min(z + cz, (int)q.n[2])});
+    }
+    if (cols.size() >= 4 * 152) break;
+  }
+  c->ncols = (int)cols.size();
   std::vector<Copy> copies;
   std::vector<std::vector<Copy>> send(c->nranks), recv(c->nranks);
   std::vector<DirRegion> dir;
@@ -530,6 +549,7 @@ static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, in
 
   if ((rc = upload(c, &c->d_boxes, db))) return bail(rc);
   if ((rc = upload(c, &c->d_tiles, tiles))) return bail(rc);
+  if ((rc = upload(c, &c->d_cols, cols))) return bail(rc);
   {
     // Interior / boundary split of the tiles.  A tile is a boundary tile when
     // a ghost cell that another rank fills lies within STENCIL_REACH cells of
@@ -799,9 +819,10 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
     const int stage = which % 2 + 1;
     float best = 1e30f;
     int best_cfg = c->cfg[which];
-    for (int ti = 0; ti < 3 && err == cudaSuccess; ++ti)
-      for (int sched = 0; sched < 2 && err == cudaSuccess; ++sched) {
-        const int cfg = cfg_make(threads[ti], sched);
+    // candidates: threads x schedule on TS^3 tiles, and (hydro) the columns
+    const int ncand = 6 + (is_rad ? 0 : 1);
+    for (int ci = 0; ci < ncand && err == cudaSuccess; ++ci) {
+        const int cfg = ci < 6 ? cfg_make(threads[ci / 2], ci % 2) : cfg_make(CNT, 0, 1);
         auto launch = [&]() {
           if (!is_rad)
             return launch_hydro_stage(c->fp32, stage, g, c->p, hydro, stage == 2 ? U1 : nullptr,
@@ -832,6 +853,21 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
   drop_graphs(c);
   if (out_cfg)
     for (int w = 0; w < 4; ++w) out_cfg[w] = c->cfg[w];
+  return QK_OK;
+}
+
+int qk_set_launch_config(qk_ctx *c, const int32_t cfg[4]) {
+  if (!c) return QK_EINVAL;
+  if (!cfg) return fail(c, QK_EINVAL, "cfg is NULL");
+  for (int w = 0; w < 4; ++w) {
+    const int v = cfg[w], th = cfg_threads(v), shape = cfg_shape(v);
+    const bool ok = (v >> 18) == 0 &&
+                    (shape == 0 ? (th == 128 || th == 256 || th == 512)
+                                : (w < 2 && th == CNT && cfg_sched(v) == 0));
+    if (!ok) return fail(c, QK_EINVAL, "invalid launch configuration %d for stage kernel %d", v, w);
+  }
+  for (int w = 0; w < 4; ++w) c->cfg[w] = cfg[w];
+  drop_graphs(c);
   return QK_OK;
 }
 

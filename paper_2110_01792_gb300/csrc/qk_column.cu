@@ -1,0 +1,296 @@
+// qk_column.cu -- plane-marching form of the fused hydro RK2-SSP stage
+// (Sec. 2.2.1 of arXiv:2110.01792) for sm_103a: the same arithmetic per cell
+// and per face as qk_hydro.cu (con2prim, PPM/PLM with flattening, HLLC, the
+// divergence summed ((x + y) + z), the RK combination), organised for fewer
+// instructions per cell.  A CTA of CW x CW threads owns a CW x CW footprint of
+// one patch and walks its planes along z:
+//   - z: every thread keeps the primitives of planes z-1 .. z+3 of its own
+//     cell in registers, reconstructs cell z+1 and computes the flux through
+//     face z+1/2 once; the flux through z-1/2 is carried from the previous
+//     plane, so each z face is solved once per column;
+//   - x and y: the plane z with a HALO-deep ring sits in shared memory;
+//     reconstruction (CW+2 positions per row) and faces (CW+1 per row) of both
+//     directions are computed in one pass each;
+//   - the item -> shared-memory index maps are fixed for the whole column.
+// Three barriers per plane.  Used through launch configurations of shape 1
+// (cfg_shape); results equal the TS^3 tile kernels' up to the rounding of
+// the identical formulas (the same device functions).
+#include "qk_device.cuh"
+
+namespace qk {
+
+template <typename T> struct ColSmem {
+  T prim[5][CNPL];                 // rho, vx, vy, vz, P of plane z and its ring
+  T rec[2][10][CXPOS * CW];        // x and y: qL, qR of each primitive per position
+  T flux[2][5][CXFACE * CW];       // x and y face fluxes
+};
+
+__device__ __forceinline__ int pslot(int i, int j) { return (j + HALO) * CPW + (i + HALO); }
+
+// HLLC along axis D from the face states, as the tile kernel's phase B.
+template <typename T, int D>
+__device__ __forceinline__ void col_face(const T wL[5], const T wR[5], T gamma, T gm1inv, T g1,
+                                         T F[5]) {
+  hllc<T, D>(wL, wR, gamma, gm1inv, g1, F);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_prim(const F5<T> &U, long long e, double gamma, T w[5]) {
+  T u[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
+  con2prim<T>(u, gamma, w);
+}
+
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(CNT) hydro_column_kernel(Geometry g, qk_params p, F5<T> U0,
+                                                          F5<T> U1, F5<T> Uo, DtSrc dts,
+                                                          const T *chi) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ColSmem<T> &sm = *reinterpret_cast<ColSmem<T> *>(smem_raw);
+  const T dt = (T)dt_of(dts);
+  const double gamma_d = p.gamma;
+  const T gamma = (T)p.gamma;
+  const T gm1inv = (T)(1.0 / (p.gamma - 1.0));
+  const T g1 = (T)((p.gamma + 1.0) / (2.0 * p.gamma));
+  const T inv_dx[3] = {(T)(1.0 / p.dx[0]), (T)(1.0 / p.dx[1]), (T)(1.0 / p.dx[2])};
+  const F5<T> src = STAGE == 1 ? U0 : U1;
+  const int rk = p.recon;
+  const int t = threadIdx.x;
+  const int ti = t % CW, tj = t / CW;  // own cell in the footprint
+
+  for (int w = blockIdx.x; w < g.ncols; w += gridDim.x) {
+    const Column col = g.cols[w];
+    const DevBox b = g.boxes[col.box];
+    const int vx = min(CW, b.n[0] - col.x0), vy = min(CW, b.n[1] - col.y0);
+    const long long plane = (long long)b.sx * b.sy;
+    // own cell: its primitives feed the ring of valid neighbours up to HALO
+    // cells beyond the valid footprint (the patch's ghost cells)
+    const bool own_load = ti < vx + HALO && tj < vy + HALO;
+    const bool own_valid = ti < vx && tj < vy;
+    const long long own0 = cell_elem(b, g.ng, col.x0 + ti, col.y0 + tj, 0);
+    // ring cell of this thread (x sides first, then y sides), if any
+    int ri = 0, rj = 0;
+    bool ring = false;
+    if (t < CNRING) {
+      const int side = t / (HALO * CW), r = t % (HALO * CW);
+      const int h = r % HALO, along = r / HALO;
+      if (side == 0) { ri = h - HALO; rj = along; }
+      else if (side == 1) { ri = CW + h; rj = along; }
+      else if (side == 2) { ri = along; rj = h - HALO; }
+      else { ri = along; rj = CW + h; }
+      // needed where a valid stencil reaches it: rows (columns) of the valid
+      // footprint, and on the far sides only the cells within HALO of the
+      // valid extent (the rest lies beyond the patch ghosts; for a partial
+      // footprint the own cells past the valid extent supply the near ones)
+      ring = (side == 0 && rj < vy) || (side == 1 && ri < vx + HALO && rj < vy) ||
+             (side == 2 && ri < vx) || (side == 3 && rj < vy + HALO && ri < vx);
+    }
+    const long long ring0 = ring ? cell_elem(b, g.ng, col.x0 + ri, col.y0 + rj, 0) : 0;
+
+    // z window: primitives of planes z-1 .. z+3 of the own cell
+    T win[5][5];
+    auto load_plane = [&](int z, T out[5]) {
+      if (own_load) {
+        load_prim<T>(src, own0 + (long long)z * plane, gamma_d, out);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) out[q] = (q == 0 || q == 4) ? T(1) : T(0);
+      }
+    };
+    auto chi_at = [&](int z) -> T {
+      return (chi && own_load) ? chi[own0 + (long long)z * plane] : T(1);
+    };
+    // reconstruct the own cell at plane z from the five planes st[0..4]
+    auto recon_z = [&](const T st[5][5], T ch, T qL[5], T qR[5]) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        recon<T>(rk, st[0][q], st[1][q], st[2][q], st[3][q], st[4][q], qL[q], qR[q]);
+        if (chi) {
+          qL[q] = ch * qL[q] + (T(1) - ch) * st[2][q];
+          qR[q] = ch * qR[q] + (T(1) - ch) * st[2][q];
+        }
+      }
+    };
+    // start-up: face z0 - 1/2 from the reconstructions of cells z0-1 and z0
+    T carryR[5], Fz[5];
+    {
+      T st[5][5];
+#pragma unroll
+      for (int o = 0; o < 5; ++o) load_plane(col.z0 - 3 + o, st[o]);
+      T qL[5], qR[5];
+      recon_z(st, chi_at(col.z0 - 1), qL, qR);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) carryR[q] = qR[q];
+#pragma unroll
+      for (int o = 0; o < 4; ++o)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) st[o][q] = st[o + 1][q];
+      load_plane(col.z0 + 2, st[4]);
+      recon_z(st, chi_at(col.z0), qL, qR);
+      col_face<T, 2>(carryR, qL, gamma, gm1inv, g1, Fz);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) carryR[q] = qR[q];
+#pragma unroll
+      for (int o = 0; o < 4; ++o)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) win[o][q] = st[o + 1][q];  // planes z0-1 .. z0+2
+    }
+
+    for (int z = col.z0; z < col.z1; ++z) {
+      // ---- load: plane z+3 into the window, plane z (own + ring) into smem
+      load_plane(z + 3, win[4]);
+      if (own_load) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) sm.prim[q][pslot(ti, tj)] = win[1][q];
+      }
+      if (ring) {
+        T wr[5];
+        load_prim<T>(src, ring0 + (long long)z * plane, gamma_d, wr);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) sm.prim[q][pslot(ri, rj)] = wr[q];
+      }
+      __syncthreads();
+      // ---- x and y reconstruction (items t, t + CNT, ...), and z in registers
+      for (int it = t; it < 2 * CXPOS * CW; it += CNT) {
+        const int dir = it >= CXPOS * CW;
+        const int r = it - dir * CXPOS * CW;
+        int ci, cj, base, stride;
+        if (!dir) {
+          const int pos = r % CXPOS;
+          cj = r / CXPOS;
+          ci = pos - 1;
+          if (cj >= vy || ci > vx) continue;
+          base = pslot(ci - 2, cj);
+          stride = 1;
+        } else {
+          ci = r % CW;
+          const int pos = r / CW;
+          cj = pos - 1;
+          if (ci >= vx || cj > vy) continue;
+          base = pslot(ci, cj - 2);
+          stride = CPW;
+        }
+        const T ch = chi ? chi[cell_elem(b, g.ng, col.x0 + ci, col.y0 + cj, z)] : T(1);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const T *pq = sm.prim[q] + base;
+          T qL, qR;
+          recon<T>(rk, pq[0], pq[stride], pq[2 * stride], pq[3 * stride], pq[4 * stride], qL,
+                   qR);
+          if (chi) {
+            const T qc = pq[2 * stride];
+            qL = ch * qL + (T(1) - ch) * qc;
+            qR = ch * qR + (T(1) - ch) * qc;
+          }
+          sm.rec[dir][2 * q][r] = qL;
+          sm.rec[dir][2 * q + 1][r] = qR;
+        }
+      }
+      T Fzn[5];
+      {
+        T qL[5], qR[5];
+        recon_z(win, chi_at(z + 1), qL, qR);
+        col_face<T, 2>(carryR, qL, gamma, gm1inv, g1, Fzn);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) carryR[q] = qR[q];
+      }
+      __syncthreads();
+      // ---- x and y faces
+      for (int it = t; it < 2 * CXFACE * CW; it += CNT) {
+        const int dir = it >= CXFACE * CW;
+        const int r = it - dir * CXFACE * CW;
+        int il, ir;
+        if (!dir) {
+          const int f = r % CXFACE, cj = r / CXFACE;
+          if (cj >= vy || f > vx) continue;
+          il = cj * CXPOS + f;
+          ir = il + 1;
+        } else {
+          const int ci = r % CW, f = r / CW;
+          if (ci >= vx || f > vy) continue;
+          il = f * CW + ci;
+          ir = il + CW;
+        }
+        T wL[5], wR[5], F[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          wL[q] = sm.rec[dir][2 * q + 1][il];
+          wR[q] = sm.rec[dir][2 * q][ir];
+        }
+        if (!dir)
+          col_face<T, 0>(wL, wR, gamma, gm1inv, g1, F);
+        else
+          col_face<T, 1>(wL, wR, gamma, gm1inv, g1, F);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) sm.flux[dir][q][r] = F[q];
+      }
+      __syncthreads();
+      // ---- divergence ((x + y) + z) and the RK combination of the own cell
+      if (own_valid) {
+        const long long e = own0 + (long long)z * plane;
+        const int fx = tj * CXFACE + ti, fy = tj * CW + ti;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          T acc = (sm.flux[0][q][fx + 1] - sm.flux[0][q][fx]) * inv_dx[0];
+          acc = acc + (sm.flux[1][q][fy + CW] - sm.flux[1][q][fy]) * inv_dx[1];
+          acc = acc + (Fzn[q] - Fz[q]) * inv_dx[2];
+          const T L = -acc;
+          const T own = src.f[q][e];
+          if (STAGE == 1) {
+            Uo.f[q][e] = own + dt * L;
+          } else {
+            const T u0 = U0.f[q][e];
+            Uo.f[q][e] = T(0.5) * u0 + T(0.5) * (own + dt * L);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q) Fz[q] = Fzn[q];
+#pragma unroll
+      for (int o = 0; o < 4; ++o)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) win[o][q] = win[o + 1][q];
+      // the next plane's load overwrites prim after the two barriers above;
+      // rec and flux are rewritten only after the next load barrier
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int STAGE>
+static cudaError_t launch_col(const Geometry &g, const qk_params &p, void *const *U0,
+                              void *const *U1, void *const *Uo, DtSrc dt, const void *chi,
+                              cudaStream_t s) {
+  F5<T> a, b, c;
+  for (int q = 0; q < 5; ++q) {
+    a.f[q] = (T *)U0[q];
+    b.f[q] = U1 ? (T *)U1[q] : nullptr;
+    c.f[q] = (T *)Uo[q];
+  }
+  const int smem = (int)sizeof(ColSmem<T>);
+  auto kern = hydro_column_kernel<T, STAGE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CNT, smem);
+  int grid = nsm * (per_sm > 0 ? per_sm : 1);
+  if (grid > g.ncols) grid = g.ncols;
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, CNT, smem, s>>>(g, p, a, b, c, dt, (const T *)chi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hydro_column(int fp32, int stage, const Geometry &g, const qk_params &p,
+                                void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
+                                const void *chi, cudaStream_t s) {
+  if (fp32)
+    return stage == 1 ? launch_col<float, 1>(g, p, U0, U1, Uout, dt, chi, s)
+                      : launch_col<float, 2>(g, p, U0, U1, Uout, dt, chi, s);
+  return stage == 1 ? launch_col<double, 1>(g, p, U0, U1, Uout, dt, chi, s)
+                    : launch_col<double, 2>(g, p, U0, U1, Uout, dt, chi, s);
+}
+
+}  // namespace qk

@@ -31,6 +31,8 @@ struct qk_ctx {
   // filled from another rank within their stencil reach) first, then the
   // boundary tiles; `part` selects which ones the stage launches process
   Tile *d_tiles_ib = nullptr;
+  Column *d_cols = nullptr;    // column work list of the plane-marching kernels
+  int ncols = 0;
   int n_interior = 0;
   int part = QK_PART_ALL;
   // sharded contexts: owner rank of every patch, this rank, and the halo

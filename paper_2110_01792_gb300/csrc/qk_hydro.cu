@@ -290,6 +290,9 @@ cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_
                                void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
                                int grid, int cfg, const void *chi, cudaStream_t s,
                                const LoPtrs *lo) {
+  // columns (shape 1) when the geometry has them; compensated states use tiles
+  if (cfg_shape(cfg) == 1 && g.cols && g.ncols > 0 && !lo)
+    return launch_hydro_column(fp32, stage, g, p, U0, U1, Uout, dt, chi, s);
   if (fp32 && lo)
     return stage == 1 ? launch_nt<float, 1, true>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s)
                       : launch_nt<float, 2, true>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s);

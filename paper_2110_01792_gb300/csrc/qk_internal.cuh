@@ -33,6 +33,25 @@ constexpr int NIFP = TS + 3;            // PPM interface values per line (FP64)
 constexpr int NIF = NIFP * TS * TS;
 constexpr int NFLUX = NFACE * TS * TS;
 
+// Column geometry (the plane-marching stage kernels).  A CTA of CW x CW
+// threads owns a CW x CW footprint of one patch and marches along z through
+// planes [z0, z1): the z stencil lives in a per-thread register window, the
+// x and y stencils of the current plane in shared memory (the plane and a
+// HALO-deep ring, corners unused).
+constexpr int CW = 16;
+constexpr int CPW = CW + 2 * HALO;     // plane row length with the ring
+constexpr int CNPL = CPW * CPW;        // plane slots
+constexpr int CXPOS = CW + 2;          // reconstruction positions per row (cells -1..CW)
+constexpr int CXFACE = CW + 1;         // faces per row
+constexpr int CNT = CW * CW;           // threads per column CTA
+constexpr int CNRING = 4 * HALO * CW;  // ring cells of a plane (x and y sides)
+constexpr int CZ = 32;                 // planes per column work item
+
+struct Column {
+  int box;
+  int x0, y0, z0, z1;
+};
+
 struct DevBox {
   int lo[3];
   int n[3];
@@ -198,6 +217,8 @@ struct Geometry {
   const DevBox *boxes;
   const Tile *tiles;
   int ntiles;
+  const Column *cols;  // column work list (plane-marching kernels)
+  int ncols;
   int nbox;
   int ng;
   long long ncells;
@@ -207,9 +228,13 @@ struct Geometry {
 // Launch configuration of a stage kernel: threads per CTA (128, 256 or 512 on
 // the same shared-memory tile) and the tile schedule (0: strided over the
 // grid, 1: one contiguous run of tiles per CTA), packed as threads | sched<<16.
-constexpr int cfg_make(int threads, int sched) { return threads | (sched << 16); }
+constexpr int cfg_make(int threads, int sched, int shape = 0) {
+  return threads | (sched << 16) | (shape << 17);
+}
 constexpr int cfg_threads(int cfg) { return cfg & 0xffff; }
 constexpr int cfg_sched(int cfg) { return (cfg >> 16) & 1; }
+// tile shape: 0 = TS^3 cross tiles, 1 = CW x CW columns marching along z
+constexpr int cfg_shape(int cfg) { return (cfg >> 17) & 1; }
 constexpr int kDefaultCfg = cfg_make(256, 0);
 
 // Low parts of a compensated FP32 state (hi + lo per conserved field): those
@@ -225,6 +250,9 @@ cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_
                                void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
                                int grid, int cfg, const void *chi, cudaStream_t s,
                                const LoPtrs *lo = nullptr);
+cudaError_t launch_hydro_column(int fp32, int stage, const Geometry &g, const qk_params &p,
+                                void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
+                                const void *chi, cudaStream_t s);
 cudaError_t launch_flatten(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                            void *chi, cudaStream_t s);
 // The exchange fused into radiation stage 2: gas fields (and their low parts

@@ -76,6 +76,7 @@ def lib():
     L.qk_set_graph.argtypes = [vp, i32]
     L.qk_set_launch_mode.argtypes = [vp, i32]
     L.qk_set_fused_exchange.argtypes = [vp, i32]
+    L.qk_set_launch_config.argtypes = [vp, P(i32)]
     L.qk_rad_stage2_exchange.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), dbl, vp]
     L.qk_autotune.argtypes = [vp, P(vp), P(vp), P(i32), vp]
     L.qk_fill_ghosts.argtypes = [vp, P(vp), i32, vp]
@@ -115,7 +116,7 @@ def lib():
     for f in ("qk_init_level", "qk_amr_init", "qk_amr_info", "qk_amr_interp", "qk_amr_register",
               "qk_amr_sync", "qk_set_tile_part", "qk_tile_counts", "qk_fill_plan", "qk_fill_ghosts_range", "qk_set_dirichlet", "qk_set_source",
               "qk_init_shard", "qk_halo_info", "qk_halo_pack", "qk_halo_unpack",
-              "qk_signal_speed", "qk_set_timestep", "qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_set_fused_exchange", "qk_rad_stage2_exchange", "qk_autotune",
+              "qk_signal_speed", "qk_set_timestep", "qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_set_fused_exchange", "qk_rad_stage2_exchange", "qk_set_launch_config", "qk_autotune",
               "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
               "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
               "qk_status", "qk_step_info", "qk_eval_math", "qk_step_compensated",
@@ -134,6 +135,25 @@ def eval_math(x, rcp=None, sqrt_out=None, stream=None):
                             _stream(stream))
     if rc != OK:
         raise QKError(rc, "qk_eval_math failed")
+
+
+_CFG_NAMES = ("hydro1", "hydro2", "rad1", "rad2")
+
+
+def _decode_cfg(vals):
+    """threads | schedule << 16 | shape << 17 -> {kernel: (threads, schedule)},
+    schedule "strided" / "contiguous" on 8^3 tiles, or "columns"."""
+    out = {}
+    for n, v in zip(_CFG_NAMES, vals):
+        v = int(v)
+        sched = "columns" if (v >> 17) & 1 else ("contiguous" if (v >> 16) & 1 else "strided")
+        out[n] = (v & 0xffff, sched)
+    return out
+
+
+def _encode_cfg(c):
+    th, sched = c
+    return int(th) | ({"strided": 0, "contiguous": 1 << 16, "columns": 1 << 17}[sched])
 
 
 def make_params(**kw) -> Params:
@@ -291,9 +311,13 @@ class Context:
         out = (C.c_int32 * 4)()
         self._check(self._L.qk_autotune(self._h, _ptrs(U, 5), _ptrs(R, 4) if R is not None else None,
                                         out, _stream(stream)))
-        names = ("hydro1", "hydro2", "rad1", "rad2")
-        return {n: (int(v) & 0xffff, "contiguous" if (int(v) >> 16) & 1 else "strided")
-                for n, v in zip(names, out[:])}
+        return _decode_cfg(out[:])
+
+    def set_launch_config(self, cfg):
+        """Set the four stage kernels' launch configurations, given as
+        {kernel: (threads, schedule)} like autotune's result."""
+        arr = (C.c_int32 * 4)(*[_encode_cfg(cfg[n]) for n in _CFG_NAMES])
+        self._check(self._L.qk_set_launch_config(self._h, arr))
 
     def set_fused_exchange(self, enable: bool):
         self._check(self._L.qk_set_fused_exchange(self._h, 1 if enable else 0))

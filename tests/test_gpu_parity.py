@@ -128,6 +128,70 @@ def test_hydro_stages_match_oracle(torch_cuda, lay):
     assert max(e2) <= TOL_STAGE, e2
 
 
+COLS = {"hydro1": (256, "columns"), "hydro2": (256, "columns"), "rad1": (256, "strided"),
+        "rad2": (256, "strided")}
+
+
+@pytest.mark.parametrize("recon,flat", [(0, 0), (1, 0), (0, 1)], ids=["ppm", "plm", "ppm_flat"])
+@pytest.mark.parametrize("lay", [RAGGED, I.single_box(40, ng=4)], ids=["ragged", "box40"])
+def test_column_hydro_stages_match_oracle(torch_cuda, lay, recon, flat):
+    """The plane-marching form of the hydro stage (16 x 16 columns walking
+    along z, partial footprints, z chunks): FP64 agrees with the oracle to
+    1e-12 per stage; FP32 agrees with the 8^3-tile FP32 kernel to FP32
+    rounding (the same formulas in another order of work)."""
+    torch = torch_cuda
+    prob, prm = _random_rhd(lay, 4)
+    prm["hydro_only"] = 1
+    prm["recon"] = recon
+    prm["flattening"] = flat
+    U0 = prob.U
+    p = O.make_params(**prm)
+    g = _grid(lay)
+    dt = 0.2 * O.timestep(g, p, U0)[0]
+    U1r = [np.zeros_like(a) for a in U0]
+    O.hydro_stage(g, p, 1, U0, None, U1r, dt)
+    U2r = [a.copy() for a in U0]
+    O.hydro_stage(g, p, 2, U2r, U1r, U2r, dt)
+    for prec in (0, 1):
+        tdt = torch.float64 if prec == 0 else torch.float32
+        res = []
+        for cfg in (COLS, None):
+            ctx = _ctx(lay, prm, prec)
+            if cfg is not None:
+                ctx.set_launch_config(cfg)
+            dU0 = G.dev(U0, tdt)
+            dU1 = G.dev([np.zeros_like(a) for a in U0], tdt)
+            ctx.fill_ghosts(dU0)
+            ctx.hydro_stage(1, dU0, None, dU1, dt)
+            s1 = G.host(dU1)
+            dU1 = G.dev(U1r, tdt)
+            ctx.fill_ghosts(dU1)
+            ctx.hydro_stage(2, dU0, dU1, dU0, dt)
+            torch.cuda.synchronize()
+            res.append((s1, G.host(dU0)))
+            ctx.close()
+        (c1, c2), (t1, t2) = res
+        if prec == 0:
+            e1 = G.max_rel_err(lay, c1, U1r)
+            e2 = G.max_rel_err(lay, c2, U2r)
+            assert max(e1) <= TOL_STAGE and max(e2) <= TOL_STAGE, (e1, e2)
+        else:
+            e1 = G.max_rel_err(lay, c1, t1)
+            e2 = G.max_rel_err(lay, c2, t2)
+            assert max(e1) <= 1e-5 and max(e2) <= 1e-5, (e1, e2)
+
+
+def test_column_hydro_ten_steps_fp64(torch_cuda):
+    """10 FP64 hydro steps of the seeded 32^3 workload with the column kernels
+    agree with the oracle to 1e-10 per cell."""
+    prob = I.config("hydro32")
+    Ug, _, hg, st = _run_gpu_steps(prob.layout, prob, prob.params, 10, launch=COLS)
+    Ur, _, hr = _run_oracle_steps(prob.layout, prob, prob.params, 10)
+    _check_dt(hg, hr)
+    e = G.max_rel_err(prob.layout, Ug, Ur)
+    assert max(e) <= TOL_STEPS, e
+
+
 # ------------------------------------------------------------- rad stage --
 
 @pytest.mark.parametrize("kappa0", [None, 60.0], ids=["thin", "thick_kappa_rho"])
@@ -239,10 +303,12 @@ def test_conserved_sums_match_oracle(torch_cuda):
 
 # --------------------------------------------------------- whole steps ----
 
-def _run_gpu_steps(lay, prob, prm, nsteps, prec=0, graph=True):
+def _run_gpu_steps(lay, prob, prm, nsteps, prec=0, graph=True, launch=None):
     torch = pytest.importorskip("torch")
     ctx = _ctx(lay, prm, prec)
     ctx.set_graph(graph)
+    if launch is not None:
+        ctx.set_launch_config(launch)
     dt_ = torch.float64 if prec == 0 else torch.float32
     dU = G.dev(prob.U, dt_)
     dR = G.dev(prob.R, dt_) if prob.R is not None else None
@@ -438,7 +504,7 @@ def test_autotune_keeps_state_and_results(torch_cuda):
             cfg = ctx.autotune(dU, dR)
             assert set(cfg) == {"hydro1", "hydro2", "rad1", "rad2"}
             for th, sch in cfg.values():
-                assert th in (128, 256, 512) and sch in ("strided", "contiguous")
+                assert th in (128, 256, 512) and sch in ("strided", "contiguous", "columns")
             for a, b in zip(G.host(dU) + G.host(dR), before):
                 assert np.array_equal(G.interior(lay, a), G.interior(lay, b))
         for _ in range(2):
