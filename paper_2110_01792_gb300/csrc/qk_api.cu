@@ -449,19 +449,40 @@ static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, in
   }
   c->tile_start[nown] = (int)tiles.size();
   c->ntiles = (int)tiles.size();
-  // column work list: CW x CW footprints, z split into chunks of CZ planes
-  // (halved while there are fewer than four items per SM of a GB300)
+  // column work list: CW x CW footprints, z split into chunks of cz planes.
+  // A column costs ~ (cz + 2.5) plane times (the start-up reconstructs two
+  // planes ahead); the persistent grid holds `slots` columns at once, so cz
+  // minimises waves x (cz + 2.5), waves = ceil(columns / slots).
   std::vector<Column> cols;
-  for (int cz = CZ; cz >= 4; cz /= 2) {
-    cols.clear();
+  {
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long slots = (long long)std::max(nsm, 1) * (c->fp32 ? 3 : 2);
+    int max_nz = 1;
+    for (int l = 0; l < nown; ++l) max_nz = std::max(max_nz, (int)boxes[c->own[l]].n[2]);
+    int best_cz = max_nz;
+    double best_cost = 1e300;
+    for (int cz = std::min(8, max_nz); cz <= max_nz; ++cz) {
+      long long items = 0;
+      for (int l = 0; l < nown; ++l) {
+        const qk_box &q = boxes[c->own[l]];
+        items += (long long)((q.n[0] + CW - 1) / CW) * ((q.n[1] + CW - 1) / CW) *
+                 ((q.n[2] + cz - 1) / cz);
+      }
+      const double cost = (double)((items + slots - 1) / slots) * (std::min(cz, max_nz) + 2.5);
+      if (cost < best_cost) {
+        best_cost = cost;
+        best_cz = cz;
+      }
+    }
     for (int l = 0; l < nown; ++l) {
       const qk_box &q = boxes[c->own[l]];
       for (int y = 0; y < q.n[1]; y += CW)
         for (int x = 0; x < q.n[0]; x += CW)
-          for (int z = 0; z < q.n[2]; z += cz)
-            cols.push_back(Column{l, x, y, z, std::min(z + cz, (int)q.n[2])});
+          for (int z = 0; z < q.n[2]; z += best_cz)
+            cols.push_back(Column{l, x, y, z, std::min(z + best_cz, (int)q.n[2])});
     }
-    if (cols.size() >= 4 * 152) break;
   }
   c->ncols = (int)cols.size();
   std::vector<Copy> copies;

@@ -42,8 +42,14 @@ __device__ __forceinline__ void load_prim(const F5<T> &U, long long e, double ga
   con2prim<T>(u, gamma, w);
 }
 
+// Resident CTAs per SM the registers are held to (FP32: three, as many as
+// fit beside each other's shared memory; FP64: two).
+template <typename T> struct ColMinBlocks {
+  static constexpr int value = sizeof(T) == 4 ? 3 : 2;
+};
+
 template <typename T, int STAGE>
-__global__ void __launch_bounds__(CNT) hydro_column_kernel(Geometry g, qk_params p, F5<T> U0,
+__global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kernel(Geometry g, qk_params p, F5<T> U0,
                                                           F5<T> U1, F5<T> Uo, DtSrc dts,
                                                           const T *chi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -137,19 +143,35 @@ __global__ void __launch_bounds__(CNT) hydro_column_kernel(Geometry g, qk_params
         for (int q = 0; q < 5; ++q) win[o][q] = st[o + 1][q];  // planes z0-1 .. z0+2
     }
 
+    // the conserved values of the next plane to enter (own: z+3, ring: z),
+    // loaded one plane ahead so that their latency overlaps the work on the
+    // current plane
+    T nown[5], nring[5];
+    auto fetch = [&](int z) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        nown[q] = own_load ? src.f[q][own0 + (long long)(z + 3) * plane] : T(1);
+        nring[q] = ring ? src.f[q][ring0 + (long long)z * plane] : T(1);
+      }
+    };
+    fetch(col.z0);
     for (int z = col.z0; z < col.z1; ++z) {
-      // ---- load: plane z+3 into the window, plane z (own + ring) into smem
-      load_plane(z + 3, win[4]);
+      // ---- plane z+3 into the window, plane z (own + ring) into smem
       if (own_load) {
+        con2prim<T>(nown, gamma_d, win[4]);
 #pragma unroll
         for (int q = 0; q < 5; ++q) sm.prim[q][pslot(ti, tj)] = win[1][q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) win[4][q] = (q == 0 || q == 4) ? T(1) : T(0);
       }
       if (ring) {
         T wr[5];
-        load_prim<T>(src, ring0 + (long long)z * plane, gamma_d, wr);
+        con2prim<T>(nring, gamma_d, wr);
 #pragma unroll
         for (int q = 0; q < 5; ++q) sm.prim[q][pslot(ri, rj)] = wr[q];
       }
+      if (z + 1 < col.z1) fetch(z + 1);
       __syncthreads();
       // ---- x and y reconstruction (items t, t + CNT, ...), and z in registers
       for (int it = t; it < 2 * CXPOS * CW; it += CNT) {

@@ -45,7 +45,6 @@ constexpr int CXPOS = CW + 2;          // reconstruction positions per row (cell
 constexpr int CXFACE = CW + 1;         // faces per row
 constexpr int CNT = CW * CW;           // threads per column CTA
 constexpr int CNRING = 4 * HALO * CW;  // ring cells of a plane (x and y sides)
-constexpr int CZ = 32;                 // planes per column work item
 
 struct Column {
   int box;
