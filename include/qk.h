@@ -310,12 +310,14 @@ int qk_step_info(qk_ctx *ctx, double out[6], void *stream);
 /* Autotune the launch configuration of the four stage kernels (hydro stage
  * 1/2, radiation stage 1/2): the tile shape and schedule -- 8^3 tiles with
  * 128, 256 or 512 threads per CTA (the same shared-memory tile), strided over
- * the grid or one contiguous run of tiles per CTA; for the hydro stages also
- * 16 x 16 columns of 256 threads marching along z -- each timed with CUDA
+ * the grid or one contiguous run of tiles per CTA, or 16 x 16 columns of 256
+ * threads marching along z -- each timed with CUDA
  * events on the caller's state; the fastest is kept for qk_step and the stage
  * entry points of this context.  rad may be NULL (hydro only).  The state is
- * not changed except that its ghost cells are refilled; allocates and frees
- * one temporary copy of five fields; synchronises `stream`.  out_cfg (may be
+ * not changed except that its ghost cells are refilled; radiation stage 2 is
+ * timed with the exchange fused when qk_step fuses it (on a copy of the gas
+ * state); allocates and frees temporary copies of five (ten with the fused
+ * exchange) fields; synchronises `stream`.  out_cfg (may be
  * NULL) receives the choices as threads | schedule << 16 | shape << 17
  * (shape 1: columns).  Results do not depend on the configuration beyond the
  * rounding of identical formulas. */
@@ -325,8 +327,9 @@ int qk_autotune(qk_ctx *ctx, void *const hydro[5], void *const rad[4], int32_t o
 /* Set the launch configuration of the four stage kernels (hydro stage 1/2,
  * radiation stage 1/2) directly, in qk_autotune's encoding: threads (128,
  * 256, 512) | schedule (0 strided, 1 contiguous) << 16 | shape << 17, shape 1
- * (16 x 16 columns, 256 threads) for the hydro stages only.  QK_EINVAL for any
- * other value. */
+ * being 16 x 16 columns of 256 threads (schedule 0).  Compensated steps
+ * (qk_step_compensated) and the tile parts of sharded contexts always use the
+ * 8^3 tiles.  QK_EINVAL for any other value. */
 int qk_set_launch_config(qk_ctx *ctx, const int32_t cfg[4]);
 
 #define QK_LAUNCH_BATCHED 0   /* one persistent launch per stage over all patches */

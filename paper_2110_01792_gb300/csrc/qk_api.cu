@@ -810,14 +810,32 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
   cudaStream_t s = (cudaStream_t)stream;
   const Geometry g = geom(c);
   const int threads[3] = {128, 256, 512};
-  void *tmp[5] = {};
-  for (int q = 0; q < 5; ++q) {
+  // scratch: five fields for the stage outputs and, when qk_step fuses the
+  // exchange into radiation stage 2, a copy of the gas state for the
+  // exchange to update, and a status word of its own
+  const bool fused = rad && c->fuse_exchange;
+  void *tmp[10] = {};
+  Status *tst = nullptr;
+  auto release = [&]() {
+    for (void *t : tmp) cudaFree(t);
+    cudaFree(tst);
+  };
+  for (int q = 0; q < (fused ? 10 : 5); ++q) {
     cudaError_t e = cudaMalloc(&tmp[q], (size_t)c->field_len * c->elem);
     if (e != cudaSuccess) {
-      for (void *t : tmp) cudaFree(t);
+      release();
       return cuda_fail(c, e, "cudaMalloc(autotune scratch)");
     }
   }
+  if (fused) {
+    cudaError_t e = cudaMalloc((void **)&tst, sizeof(Status));
+    if (e != cudaSuccess) {
+      release();
+      return cuda_fail(c, e, "cudaMalloc(autotune status)");
+    }
+  }
+  void *Uc[5];
+  for (int q = 0; q < 5; ++q) Uc[q] = tmp[5 + q];
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -834,23 +852,35 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
   if (err == cudaSuccess && rad) err = fill(c, rad, 4, 5, DtSrc{nullptr, 0.0, 0, -1}, s);
   if (err == cudaSuccess && c->p.flattening) err = launch_flatten(c->fp32, g, c->p, hydro, c->chi, s);
   const DtSrc dth{c->d_si, 0.0, 0, -1}, dtr{c->d_si, 0.0, 2, -1};
+  const FuseArgs fx{Uc, nullptr, c->src, tst};
   for (int which = 0; which < 4 && err == cudaSuccess; ++which) {
     const bool is_rad = which >= 2;
     if (is_rad && !rad) continue;
     const int stage = which % 2 + 1;
     float best = 1e30f;
     int best_cfg = c->cfg[which];
-    // candidates: threads x schedule on TS^3 tiles, and (hydro) the columns
-    const int ncand = 6 + (is_rad ? 0 : 1);
+    // stage 2 reads the stage-1 result with its ghosts filled
+    if (which == 1) err = fill(c, U1, 5, 0, DtSrc{nullptr, 0.0, 0, -1}, s);
+    if (which == 3) err = fill(c, R1, 4, 5, DtSrc{nullptr, 0.0, 0, -1}, s);
+    // candidates: threads x schedule on TS^3 tiles, and the columns
+    const int ncand = 7;
     for (int ci = 0; ci < ncand && err == cudaSuccess; ++ci) {
         const int cfg = ci < 6 ? cfg_make(threads[ci / 2], ci % 2) : cfg_make(CNT, 0, 1);
+        // radiation stage 2 is timed as qk_step runs it: with the exchange
+        // fused when it is, on a fresh copy of the gas state
+        if (which == 3 && fused)
+          for (int q = 0; q < 5 && err == cudaSuccess; ++q)
+            err = cudaMemcpyAsync(Uc[q], hydro[q], (size_t)c->field_len * c->elem,
+                                  cudaMemcpyDeviceToDevice, s);
+        if (err != cudaSuccess) break;
         auto launch = [&]() {
           if (!is_rad)
             return launch_hydro_stage(c->fp32, stage, g, c->p, hydro, stage == 2 ? U1 : nullptr,
                                       stage == 1 ? U1 : tmp, dth, 0, cfg,
                                       c->p.flattening ? c->chi : nullptr, s);
           return launch_rad_stage(c->fp32, stage, g, c->p, rad, stage == 2 ? R1 : nullptr,
-                                  stage == 1 ? R1 : Rt, hydro[0], dtr, 0, cfg, s);
+                                  stage == 1 ? R1 : Rt, hydro[0], dtr, 0, cfg, s, nullptr,
+                                  which == 3 && fused ? &fx : nullptr);
         };
         err = launch();
         if (err != cudaSuccess) break;
@@ -869,7 +899,8 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  for (void *t : tmp) cudaFree(t);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  release();
   if (err != cudaSuccess) return cuda_fail(c, err, "autotune launch");
   drop_graphs(c);
   if (out_cfg)
@@ -884,7 +915,7 @@ int qk_set_launch_config(qk_ctx *c, const int32_t cfg[4]) {
     const int v = cfg[w], th = cfg_threads(v), shape = cfg_shape(v);
     const bool ok = (v >> 18) == 0 &&
                     (shape == 0 ? (th == 128 || th == 256 || th == 512)
-                                : (w < 2 && th == CNT && cfg_sched(v) == 0));
+                                : (th == CNT && cfg_sched(v) == 0));
     if (!ok) return fail(c, QK_EINVAL, "invalid launch configuration %d for stage kernel %d", v, w);
   }
   for (int w = 0; w < 4; ++w) c->cfg[w] = cfg[w];

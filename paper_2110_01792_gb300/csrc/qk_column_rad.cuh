@@ -1,0 +1,427 @@
+// qk_column_rad.cuh -- plane-marching form of the fused radiation RK2-SSP stage
+// (Sec. 2.2.2 of arXiv:2110.01792), with the matter-radiation exchange
+// optionally fused per cell (Sec. 2.2.3, stage 2): the same per-cell and
+// per-face arithmetic as qk_rad.cuh (f = F/(c E_r), the closure, PPM/PLM, the
+// |f| > 1 fallback, the HLL wavespeed from the cell-average Eddington factors,
+// the optical-depth correction, the divergence ((x + y) + z), the RK
+// combination), organised as the hydro column kernel (qk_column.cu): a CTA of
+// CW x CW threads walks the planes of a CW x CW footprint along z, the z
+// stencil in a per-thread register window, x and y on one shared-memory plane
+// with a HALO-deep ring.
+#pragma once
+#include "qk_rad.cuh"
+
+namespace qk {
+
+template <typename T> struct ColRadSmem {
+  static constexpr bool kAB = sizeof(T) == 8;
+  T prim[4][CNPL];                   // E_r, f_x, f_y, f_z of plane z and its ring
+  T rk[CNPL];                        // rho kappa_R
+  T ab[2][kAB ? CNPL : 1];           // FP64: closure a, b of the cell average
+  T rec[2][8][CXPOS * CW];           // x and y: qL, qR per position
+  T sq[2][kAB ? 1 : CXPOS * CW];     // FP32: sqrt(T_DD) of the cell average per position
+  T flux[2][4][CXFACE * CW];
+};
+
+__device__ __forceinline__ int cslot(int i, int j) { return (j + HALO) * CPW + (i + HALO); }
+
+// E_r, f = F/(c E_r) and rho kappa_R of one cell from its conserved values.
+template <typename T>
+__device__ __forceinline__ void rad_prim(const T u[4], T c, T r, const qk_params &p, T w[4],
+                                         T &rk) {
+  const T inv = qrcp(c * u[0]);
+  w[0] = u[0];
+  w[1] = u[1] * inv;
+  w[2] = u[2] * inv;
+  w[3] = u[3] * inv;
+  rk = r * kappa_of<T>(p, p.kappa_R, r);
+}
+
+template <typename T> struct ColMinBlocksRad {
+  static constexpr int value = sizeof(T) == 4 ? 3 : 2;
+};
+
+template <typename T, int STAGE, int CL, bool EX>
+__global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
+    rad_column_kernel(Geometry g, qk_params p, F4<T> R0, F4<T> R1, F4<T> Ro, const T *rho,
+                      DtSrc dts, ExFuse<T> xf) {
+  if (skip_substep(dts)) return;
+  constexpr bool kAB = ColRadSmem<T>::kAB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ColRadSmem<T> &sm = *reinterpret_cast<ColRadSmem<T> *>(smem_raw);
+  const T dt = (T)dt_of(dts);
+  const T c = (T)p.c, chat = (T)p.chat;
+  const T inv_dx[3] = {(T)(1.0 / p.dx[0]), (T)(1.0 / p.dx[1]), (T)(1.0 / p.dx[2])};
+  const T dx[3] = {(T)p.dx[0], (T)p.dx[1], (T)p.dx[2]};
+  const T hccc = T(0.5) * c * chat;
+  const T hchat_c = T(0.5) * chat / c;
+  const F4<T> src = STAGE == 1 ? R0 : R1;
+  const int rk = p.recon;
+  const int t = threadIdx.x;
+  const int ti = t % CW, tj = t / CW;
+  ExStat xs;
+
+  for (int w = blockIdx.x; w < g.ncols; w += gridDim.x) {
+    const Column col = g.cols[w];
+    const DevBox b = g.boxes[col.box];
+    const int vx = min(CW, b.n[0] - col.x0), vy = min(CW, b.n[1] - col.y0);
+    const long long plane = (long long)b.sx * b.sy;
+    const bool own_load = ti < vx + HALO && tj < vy + HALO;
+    const bool own_valid = ti < vx && tj < vy;
+    // the cell-average closure of the own cell is read by faces of valid cells
+    const bool own_near = ti <= vx && tj <= vy;
+    const long long own0 = cell_elem(b, g.ng, col.x0 + ti, col.y0 + tj, 0);
+    int ri = 0, rj = 0, rside = 0;
+    bool ring = false;
+    if (t < CNRING) {
+      rside = t / (HALO * CW);
+      const int r = t % (HALO * CW), h = r % HALO, along = r / HALO;
+      if (rside == 0) { ri = h - HALO; rj = along; }
+      else if (rside == 1) { ri = CW + h; rj = along; }
+      else if (rside == 2) { ri = along; rj = h - HALO; }
+      else { ri = along; rj = CW + h; }
+      ring = (rside == 0 && rj < vy) || (rside == 1 && ri < vx + HALO && rj < vy) ||
+             (rside == 2 && ri < vx) || (rside == 3 && rj < vy + HALO && ri < vx);
+    }
+    // ring cells adjacent to the footprint need the cell-average closure
+    const bool ring_near = ring && (ri == -1 || rj == -1 || ri == vx || rj == vy);
+    const long long ring0 = ring ? cell_elem(b, g.ng, col.x0 + ri, col.y0 + rj, 0) : 0;
+
+    // z window: E_r, f and rho kappa_R of planes z-1 .. z+3 (own cell)
+    T win[5][4], rkw[5];
+    T az0 = T(0), bz0 = T(0);     // FP64: closure of plane z (carried)
+    T sqz0 = T(0);                // FP32: sqrt(T_zz) of plane z (carried)
+    auto load_plane = [&](int z, T out[4], T &rko) {
+      if (own_load) {
+        const long long e = own0 + (long long)z * plane;
+        T u[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) u[q] = src.f[q][e];
+        rad_prim<T>(u, c, rho[e], p, out, rko);
+      } else {
+        out[0] = T(1);
+        out[1] = out[2] = out[3] = T(0);
+        rko = T(0);
+      }
+    };
+    // the z-face quantities of the cell in window slot s: closure (FP64) or
+    // sqrt(T_zz) (FP32)
+    auto zclosure = [&](const T wq[4], T &a, T &bb, T &sq) {
+      if constexpr (kAB) {
+        closure_ab<T, CL>(wq[1], wq[2], wq[3], a, bb);
+      } else {
+        sq = qsqrt(eddington_diag<T, 2, CL>(wq[1], wq[2], wq[3]));
+      }
+    };
+    auto zface = [&](const T wL[4], const T wR[4], const T cL[4], const T cR[4], T aL, T bL,
+                     T sqL, T aR, T bR, T sqR, T rka, T rkb, T out[4]) {
+      T S;
+      if constexpr (kAB) {
+        S = rad_speed<T>(aL + bL * cL[3] * cL[3], aR + bR * cR[3] * cR[3], chat);
+      } else {
+        S = chat * max(sqL, sqR);
+      }
+      T l[4], r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        l[q] = wL[q];
+        r[q] = wR[q];
+      }
+      rad_face_hll<T, 2, CL>(
+          l, r,
+          [&](T *ll, T *rr) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              ll[q] = cL[q];
+              rr[q] = cR[q];
+            }
+          },
+          S, rka, rkb, dx[2], c, chat, hchat_c, hccc, p.tau_correction, out);
+    };
+    auto recon_z = [&](const T st[5][4], T qL[4], T qR[4]) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        recon<T>(rk, st[0][q], st[1][q], st[2][q], st[3][q], st[4][q], qL[q], qR[q]);
+    };
+
+    // start-up: face z0 - 1/2 from cells z0-1 and z0
+    T carryR[4], Fz[4];
+    {
+      T st[5][4], rks[5];
+#pragma unroll
+      for (int o = 0; o < 5; ++o) load_plane(col.z0 - 3 + o, st[o], rks[o]);
+      T qL[4], qR[4];
+      recon_z(st, qL, qR);  // cell z0-1
+#pragma unroll
+      for (int q = 0; q < 4; ++q) carryR[q] = qR[q];
+      T am = T(0), bm = T(0), sqm = T(0);
+      zclosure(st[2], am, bm, sqm);  // cell z0-1
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        rks[o] = rks[o + 1];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) st[o][q] = st[o + 1][q];
+      }
+      load_plane(col.z0 + 2, st[4], rks[4]);
+      recon_z(st, qL, qR);  // cell z0
+      zclosure(st[2], az0, bz0, sqz0);
+      zface(carryR, qL, st[1], st[2], am, bm, sqm, az0, bz0, sqz0, rks[1], rks[2], Fz);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) carryR[q] = qR[q];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        rkw[o] = rks[o + 1];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) win[o][q] = st[o + 1][q];  // planes z0-1 .. z0+2
+      }
+    }
+
+    // next plane's inputs, fetched one plane ahead
+    T nown[4], nring[4], nrho_own = T(1), nrho_ring = T(1);
+    auto fetch = [&](int z) {
+      const long long eo = own0 + (long long)(z + 3) * plane;
+      const long long er = ring0 + (long long)z * plane;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        nown[q] = own_load ? src.f[q][eo] : T(1);
+        nring[q] = ring ? src.f[q][er] : T(1);
+      }
+      nrho_own = own_load ? rho[eo] : T(1);
+      nrho_ring = ring ? rho[er] : T(1);
+    };
+    fetch(col.z0);
+    for (int z = col.z0; z < col.z1; ++z) {
+      // ---- plane z+3 into the window; plane z (own + ring) into smem
+      if (own_load) {
+        rad_prim<T>(nown, c, nrho_own, p, win[4], rkw[4]);
+        const int s = cslot(ti, tj);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sm.prim[q][s] = win[1][q];
+        sm.rk[s] = rkw[1];
+        if constexpr (kAB) {
+          if (own_near) {
+            sm.ab[0][s] = az0;
+            sm.ab[1][s] = bz0;
+          }
+        }
+      } else {
+        win[4][0] = T(1);
+        win[4][1] = win[4][2] = win[4][3] = T(0);
+        rkw[4] = T(0);
+      }
+      if (ring) {
+        T wr[4], rkr;
+        rad_prim<T>(nring, c, nrho_ring, p, wr, rkr);
+        const int s = cslot(ri, rj);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sm.prim[q][s] = wr[q];
+        sm.rk[s] = rkr;
+        if constexpr (kAB) {
+          if (ring_near) {
+            T a, bb;
+            closure_ab<T, CL>(wr[1], wr[2], wr[3], a, bb);
+            sm.ab[0][s] = a;
+            sm.ab[1][s] = bb;
+          }
+        }
+      }
+      if (z + 1 < col.z1) fetch(z + 1);
+      __syncthreads();
+      // ---- x and y reconstruction; z in registers
+      for (int it = t; it < 2 * CXPOS * CW; it += CNT) {
+        const int dir = it >= CXPOS * CW;
+        const int r = it - dir * CXPOS * CW;
+        int ci, cj, base, stride;
+        if (!dir) {
+          const int pos = r % CXPOS;
+          cj = r / CXPOS;
+          ci = pos - 1;
+          if (cj >= vy || ci > vx) continue;
+          base = cslot(ci - 2, cj);
+          stride = 1;
+        } else {
+          ci = r % CW;
+          const int pos = r / CW;
+          cj = pos - 1;
+          if (ci >= vx || cj > vy) continue;
+          base = cslot(ci, cj - 2);
+          stride = CPW;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const T *pq = sm.prim[q] + base;
+          T qL, qR;
+          recon<T>(rk, pq[0], pq[stride], pq[2 * stride], pq[3 * stride], pq[4 * stride], qL,
+                   qR);
+          sm.rec[dir][2 * q][r] = qL;
+          sm.rec[dir][2 * q + 1][r] = qR;
+        }
+        if constexpr (!kAB) {
+          const int s2 = base + 2 * stride;
+          sm.sq[dir][r] =
+              dir ? qsqrt(eddington_diag<T, 1, CL>(sm.prim[1][s2], sm.prim[2][s2], sm.prim[3][s2]))
+                  : qsqrt(eddington_diag<T, 0, CL>(sm.prim[1][s2], sm.prim[2][s2], sm.prim[3][s2]));
+        }
+      }
+      T Fzn[4];
+      T az1 = T(0), bz1 = T(0), sqz1 = T(0);
+      {
+        T qL[4], qR[4];
+        recon_z(win, qL, qR);  // cell z+1
+        zclosure(win[2], az1, bz1, sqz1);
+        zface(carryR, qL, win[1], win[2], az0, bz0, sqz0, az1, bz1, sqz1, rkw[1], rkw[2], Fzn);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) carryR[q] = qR[q];
+      }
+      __syncthreads();
+      // ---- x and y faces
+      for (int it = t; it < 2 * CXFACE * CW; it += CNT) {
+        const int dir = it >= CXFACE * CW;
+        const int r = it - dir * CXFACE * CW;
+        int il, ir, sa, sb;
+        if (!dir) {
+          const int f = r % CXFACE, cj = r / CXFACE;
+          if (cj >= vy || f > vx) continue;
+          il = cj * CXPOS + f;
+          ir = il + 1;
+          sa = cslot(f - 1, cj);
+          sb = sa + 1;
+        } else {
+          const int ci = r % CW, f = r / CW;
+          if (ci >= vx || f > vy) continue;
+          il = f * CW + ci;
+          ir = il + CW;
+          sa = cslot(ci, f - 1);
+          sb = sa + CPW;
+        }
+        T wL[4], wR[4], out[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          wL[q] = sm.rec[dir][2 * q + 1][il];
+          wR[q] = sm.rec[dir][2 * q][ir];
+        }
+        auto fallback = [&](T *l, T *r2) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            l[q] = sm.prim[q][sa];
+            r2[q] = sm.prim[q][sb];
+          }
+        };
+        T S;
+        if constexpr (kAB) {
+          const T fa = sm.prim[1 + dir][sa], fb = sm.prim[1 + dir][sb];
+          S = rad_speed<T>(sm.ab[0][sa] + sm.ab[1][sa] * fa * fa,
+                           sm.ab[0][sb] + sm.ab[1][sb] * fb * fb, chat);
+        } else {
+          S = chat * max(sm.sq[dir][il], sm.sq[dir][ir]);
+        }
+        if (!dir)
+          rad_face_hll<T, 0, CL>(wL, wR, fallback, S, sm.rk[sa], sm.rk[sb], dx[0], c, chat,
+                                 hchat_c, hccc, p.tau_correction, out);
+        else
+          rad_face_hll<T, 1, CL>(wL, wR, fallback, S, sm.rk[sa], sm.rk[sb], dx[1], c, chat,
+                                 hchat_c, hccc, p.tau_correction, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sm.flux[dir][q][r] = out[q];
+      }
+      __syncthreads();
+      // ---- divergence ((x + y) + z), RK combination, optional exchange
+      if (own_valid) {
+        const long long e = own0 + (long long)z * plane;
+        const int fx = tj * CXFACE + ti, fy = tj * CW + ti;
+        T rv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          T acc = (sm.flux[0][q][fx + 1] - sm.flux[0][q][fx]) * inv_dx[0];
+          acc = acc + (sm.flux[1][q][fy + CW] - sm.flux[1][q][fy]) * inv_dx[1];
+          acc = acc + (Fzn[q] - Fz[q]) * inv_dx[2];
+          const T L = -acc;
+          const T own = src.f[q][e];
+          if (STAGE == 1) {
+            rv[q] = own + dt * L;
+          } else {
+            const T u0 = R0.f[q][e];
+            rv[q] = T(0.5) * u0 + T(0.5) * (own + dt * L);
+          }
+          Ro.f[q][e] = rv[q];
+        }
+        if constexpr (EX) {
+          if constexpr (kAB) {
+            const double fr[3] = {(double)rv[1], (double)rv[2], (double)rv[3]};
+            exchange_cell<T>(p, xf.K, dt_of(dts), xf.U, Ro, xf.src, e, (double)rv[0], fr, xs);
+          } else {
+            const float fl[3] = {0.0f, 0.0f, 0.0f};
+            F4<float> none{};
+            exchange_cell_mixed<false>(p, xf.K, dt_of(dts), xf.U, Ro, xf.UL, none, xf.src, e,
+                                       rv[0], 0.0f, rv + 1, fl, xs);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Fz[q] = Fzn[q];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        rkw[o] = rkw[o + 1];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) win[o][q] = win[o + 1][q];
+      }
+      az0 = az1;
+      bz0 = bz1;
+      sqz0 = sqz1;
+    }
+    __syncthreads();
+  }
+  if constexpr (EX) exchange_status(xf.st, xs.max, xs.flags, xs.bad);
+}
+
+template <typename T, int STAGE, int CL, bool EX>
+static cudaError_t launch_rad_col_one(const Geometry &g, const qk_params &p, void *const *R0,
+                                      void *const *R1, void *const *Ro, const void *rho,
+                                      DtSrc dt, const FuseArgs *fx, cudaStream_t s) {
+  F4<T> a, b, c;
+  for (int q = 0; q < 4; ++q) {
+    a.f[q] = (T *)R0[q];
+    b.f[q] = R1 ? (T *)R1[q] : nullptr;
+    c.f[q] = (T *)Ro[q];
+  }
+  ExFuse<T> xf{};
+  if (EX) {
+    for (int q = 0; q < 5; ++q) xf.U.f[q] = (T *)fx->U[q];
+    xf.src = (const T *)fx->src;
+    xf.st = fx->st;
+    xf.K = make_exk(p);
+    xf.on = 1;
+  }
+  const int smem = (int)sizeof(ColRadSmem<T>);
+  auto kern = rad_column_kernel<T, STAGE, CL, EX>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CNT, smem);
+  int grid = nsm * (per_sm > 0 ? per_sm : 1);
+  if (grid > g.ncols) grid = g.ncols;
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, CNT, smem, s>>>(g, p, a, b, c, (const T *)rho, dt, xf);
+  return cudaGetLastError();
+}
+
+// Column launches of one closure (instantiated per closure in
+// qk_column_rad.cu); fx non-null fuses the exchange into stage 2.
+template <int CL>
+cudaError_t launch_rad_column_closure(int fp32, int stage, const Geometry &g, const qk_params &p,
+                                      void *const *R0, void *const *R1, void *const *Ro,
+                                      const void *rho, DtSrc dt, const FuseArgs *fx,
+                                      cudaStream_t s) {
+  if (fp32) {
+    if (stage == 1) return launch_rad_col_one<float, 1, CL, false>(g, p, R0, R1, Ro, rho, dt, fx, s);
+    if (fx) return launch_rad_col_one<float, 2, CL, true>(g, p, R0, R1, Ro, rho, dt, fx, s);
+    return launch_rad_col_one<float, 2, CL, false>(g, p, R0, R1, Ro, rho, dt, fx, s);
+  }
+  if (stage == 1) return launch_rad_col_one<double, 1, CL, false>(g, p, R0, R1, Ro, rho, dt, fx, s);
+  if (fx) return launch_rad_col_one<double, 2, CL, true>(g, p, R0, R1, Ro, rho, dt, fx, s);
+  return launch_rad_col_one<double, 2, CL, false>(g, p, R0, R1, Ro, rho, dt, fx, s);
+}
+
+}  // namespace qk

@@ -263,6 +263,9 @@ struct FuseArgs {
   Status *st;
 };
 
+cudaError_t launch_rad_column(int fp32, int stage, const Geometry &g, const qk_params &p,
+                              void *const *R0, void *const *R1, void *const *Rout,
+                              const void *rho, DtSrc dt, const FuseArgs *fx, cudaStream_t s);
 cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                              void *const *R0, void *const *R1, void *const *Rout,
                              const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s,

@@ -20,6 +20,9 @@ cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_pa
                              void *const *R0, void *const *R1, void *const *Rout,
                              const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s,
                              const LoPtrs *lo, const FuseArgs *fx) {
+  // columns (shape 1) when the geometry has them; compensated states use tiles
+  if (cfg_shape(cfg) == 1 && g.cols && g.ncols > 0 && !lo)
+    return launch_rad_column(fp32, stage, g, p, R0, R1, Rout, rho, dt, fx, s);
   switch (p.closure) {
     case QK_CLOSURE_MINERBO:
       return launch_rad_closure<QK_CLOSURE_MINERBO>(fp32, stage, g, p, R0, R1, Rout, rho, dt, grid,
