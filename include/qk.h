@@ -521,6 +521,17 @@ int qk_status(qk_ctx *ctx, uint32_t *flags, int64_t *first_bad, int32_t *max_ite
  * n > 0, QK_ECUDA if the launch fails. */
 int qk_eval_math(const double *x, int64_t n, double *rcp, double *sqrt_out, void *stream);
 
+/* The library's integer-pipe conversions, element-wise over n device values
+ * (either pair may be NULL): d_out[i] = f_in[i] widened to double (exact, for
+ * every float), f_out[i] = d_in[i] narrowed to float by truncation toward
+ * zero (within one FP32 ulp; magnitudes below the normal float range give a
+ * signed zero, above it the largest finite float).  The mixed-precision
+ * exchange (Sec. 2.2.3) uses them in place of conversion instructions, which
+ * occupy the FP64 pipe on this part.  Asynchronous on `stream`; QK_EINVAL if
+ * n < 0, QK_ECUDA if the launch fails. */
+int qk_eval_convert(const float *f_in, double *d_out, const double *d_in, float *f_out, int64_t n,
+                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

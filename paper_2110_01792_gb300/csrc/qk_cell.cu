@@ -443,7 +443,25 @@ __global__ void eval_math_kernel(const double *x, long long n, double *rcp, doub
   }
 }
 
+__global__ void eval_convert_kernel(const float *fi, double *dout, const double *di, float *fout,
+                                    long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (fi && dout) dout[i] = f2d(fi[i]);
+    if (di && fout) fout[i] = d2f_trunc(di[i]);
+  }
+}
+
 }  // namespace qk
+
+extern "C" int qk_eval_convert(const float *f_in, double *d_out, const double *d_in, float *f_out,
+                               int64_t n, void *stream) {
+  if (n < 0) return QK_EINVAL;
+  if (n == 0) return QK_OK;
+  const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
+  qk::eval_convert_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(f_in, d_out, d_in, f_out, n);
+  return cudaGetLastError() == cudaSuccess ? QK_OK : QK_ECUDA;
+}
 
 extern "C" int qk_eval_math(const double *x, int64_t n, double *rcp, double *sqrt_out,
                             void *stream) {

@@ -57,6 +57,39 @@ __device__ __forceinline__ float qsqrt(float x) {
 }
 __device__ __forceinline__ float psqrt(float x) { return qsqrt(x); }
 
+// float <-> double conversions on the integer pipe.  On GB300 every F2F
+// conversion occupies a slot of the 1/64-rate FP64 pipe; these do the same
+// with integer operations on the bit patterns.
+// f2d: exact widening (normal, subnormal, zero, infinite and NaN floats).
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  if (e == 0u) {
+    if (m == 0u) return __hiloint2double((int)sign, 0);
+    const int sh = __clz(m) - 8;  // normalise the subnormal: leading 1 to bit 23
+    m = (m << sh) & 0x7fffffu;
+    e = 1u - (unsigned)sh;        // wraps; the rebias below brings it back in range
+  }
+  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;  // rebias 127 -> 1023
+  return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+// d2f_trunc: narrowing by truncation of the mantissa (within one FP32 ulp,
+// toward zero); magnitudes below the normal FP32 range give a signed zero,
+// above it the largest finite float (infinities and NaNs map to infinities
+// and NaNs).
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u));
+  const int fe = e - 896;
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7f7fffffu);
+  return __uint_as_float(sign | ((unsigned)fe << 23) | m);
+}
+
 // Conserved -> primitive (Sec. 2.2.1): v = m / rho, E_g = E - rho v^2 / 2,
 // P = (gamma - 1) E_g.  In mixed precision the internal energy is recovered
 // with ~48-bit error-free arithmetic (cancellation of E against the kinetic

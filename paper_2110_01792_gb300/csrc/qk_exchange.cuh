@@ -115,19 +115,21 @@ __device__ __forceinline__ int newton_refine(bool alpha_eos, int max_iter, doubl
     } else {
       const double E2 = Eg * Eg;
       Rr = fma(A, E2 * E2, -(k * Er));
-      const float Ef = (float)Eg;
+      const float Ef = d2f_trunc(Eg);
       dRdEg = A4 * Ef * Ef * Ef;
     }
-    const float fg = (float)((Eg - Eg0) + cr * Rr);
-    const float fr = (float)((Er - Er0) - Rr);
+    // the FP32 correction needs the residuals to FP32 accuracy only: narrowed
+    // on the integer pipe
+    const float fg = d2f_trunc((Eg - Eg0) + cr * Rr);
+    const float fr = d2f_trunc((Er - Er0) - Rr);
     conv = fabsf(fg) < thr_g && fabsf(fr) < thr_r;
     const float G = 1.0f + crf * dRdEg;
     const float D1 = dFR_dEr * G + dRdEg * dFG_dEr;
     const float inv = qrcp(D1 * G);
     const float dEr = -(fr * G + dRdEg * fg) * (G * inv);
     const float dEg = -(fg + dEr * dFG_dEr) * (D1 * inv);
-    Er += (double)dEr;
-    Eg += (double)dEg;
+    Er += f2d(dEr);
+    Eg += f2d(dEg);
     if (conv) break;
   }
   return conv ? it + 1 : -1;
@@ -256,13 +258,14 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
   float eg_hi, eg_lo;
   internal_energy_f32(u, rho, rinv, eg_hi, eg_lo);  // ~48-bit E_g, no EOS round trip
   const float Er0f = er;
-  double Eg0 = (double)eg_hi + (double)eg_lo;
-  double Er0 = (double)Er0f;
+  // widenings on the integer pipe (exact)
+  double Eg0 = f2d(eg_hi) + f2d(eg_lo);
+  double Er0 = f2d(Er0f);
   float E_lo = 0.0f;
   if constexpr (CP) {
     E_lo = UL.f[4][e];
-    Eg0 += (double)E_lo;
-    Er0 += (double)er_lo;
+    Eg0 += f2d(E_lo);
+    Er0 += f2d(er_lo);
   }
   // the coefficients in FP32: k = dt rho kappa_P chat, A = k a_r/(rho c_v)^4
   // (or 4 k a_r/alpha), and the convergence thresholds eps E_tot,
@@ -274,20 +277,20 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
     const float i1 = rinv * K.inv_cvf, i2 = i1 * i1;
     Af *= i2 * i2;
   }
-  const double k = (double)kf, A = (double)Af;
+  const double k = f2d(kf), A = f2d(Af);
   const float Eg0f = eg_hi + (eg_lo + E_lo);
   const float Etotf = Eg0f + K.crf * (Er0f + er_lo);
   const float thr_g = (float)p.eps_newton * Etotf, thr_r = thr_g * K.rc;
   // radiation source S = dt (chat/c) j, carried in the residual's E_r0
-  const double Er0S = src ? Er0 + dt * K.rc_d * (double)src[e] : Er0;
+  const double Er0S = src ? Er0 + dt * K.rc_d * f2d(src[e]) : Er0;
   // FP32 warm start to 1e-6
   float Egf = Eg0f, Erf = src ? (float)Er0S : Er0f;
   const int itf = newton_exchange<float>(alpha_eos, Af, kf, K.crf, Eg0f, Erf, 1e-6f * Etotf,
                                          1e-6f * Etotf * K.rc, 12, Egf, Erf);
   double Eg = Eg0, Er = Er0;
   if (itf > 0 && Egf > 0.0f && Erf > 0.0f && isfinite(Egf) && isfinite(Erf)) {
-    Eg = Egf;
-    Er = Erf;
+    Eg = f2d(Egf);
+    Er = f2d(Erf);
   }
   const int it = newton_refine(alpha_eos, p.max_iter, A, k, K.cr, Eg0, Er0S, Af, kf, K.crf,
                                thr_g, thr_r, Eg, Er);
@@ -336,18 +339,19 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
   if constexpr (CP) {
     // E_new = E_g + E_kin,1; E_r,new = E_r - (chat/c)(E_kin,1 - E_kin,0) with
     // E_kin,0 = E - E_g0 (the same FP64 values), split into hi + lo
-    const double Ekin0 = ((double)u[4] + (double)E_lo) - Eg0;
-    const double Enew = Eg + (double)Ekin1;
-    Er_new = Er - (K.rc_d) * ((double)Ekin1 - Ekin0);
+    const double Ekin0 = (f2d(u[4]) + f2d(E_lo)) - Eg0;
+    const double Ek1 = f2d(Ekin1);
+    const double Enew = Eg + Ek1;
+    Er_new = Er - (K.rc_d) * (Ek1 - Ekin0);
     const float Eh = (float)Enew, Rh = (float)Er_new;
     U.f[4][e] = Eh;
-    UL.f[4][e] = (float)(Enew - (double)Eh);
+    UL.f[4][e] = (float)(Enew - f2d(Eh));
     R.f[0][e] = Rh;
-    RL.f[0][e] = (float)(Er_new - (double)Rh);
+    RL.f[0][e] = (float)(Er_new - f2d(Rh));
   } else {
     const float dEkin = 0.5f * (ke1 - ke0) * rinv;
-    U.f[4][e] = (float)(Eg + (double)Ekin1);
-    Er_new = Er - (double)(K.rc * dEkin);
+    U.f[4][e] = (float)(Eg + f2d(Ekin1));
+    Er_new = Er - f2d(K.rc * dEkin);
     R.f[0][e] = (float)Er_new;
   }
   if (!pos_finite(Eg) || !pos_finite(Er_new)) {

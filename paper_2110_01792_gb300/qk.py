@@ -111,6 +111,7 @@ def lib():
     L.qk_signal_speed.argtypes = [vp, P(vp), P(dbl), vp]
     L.qk_set_timestep.argtypes = [vp, dbl, P(dbl), vp]
     L.qk_eval_math.argtypes = [vp, i64, vp, vp, vp]
+    L.qk_eval_convert.argtypes = [vp, vp, vp, vp, i64, vp]
     L.qk_step_compensated.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), P(dbl), P(i32), vp]
     L.qk_conserved_sums_compensated.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), P(dbl), vp]
     for f in ("qk_init_level", "qk_amr_init", "qk_amr_info", "qk_amr_interp", "qk_amr_register",
@@ -119,7 +120,7 @@ def lib():
               "qk_signal_speed", "qk_set_timestep", "qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_set_fused_exchange", "qk_rad_stage2_exchange", "qk_set_launch_config", "qk_autotune",
               "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
               "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
-              "qk_status", "qk_step_info", "qk_eval_math", "qk_step_compensated",
+              "qk_status", "qk_step_info", "qk_eval_math", "qk_eval_convert", "qk_step_compensated",
               "qk_conserved_sums_compensated"):
         getattr(L, f).restype = C.c_int
     _lib = L
@@ -154,6 +155,16 @@ def _decode_cfg(vals):
 def _encode_cfg(c):
     th, sched = c
     return int(th) | ({"strided": 0, "contiguous": 1 << 16, "columns": 1 << 17}[sched])
+
+
+def eval_convert(f_in=None, d_out=None, d_in=None, f_out=None, stream=None):
+    """The library's float -> double widening of `f_in` into `d_out` and
+    double -> float truncation of `d_in` into `f_out` (device tensors)."""
+    n = int((f_in if f_in is not None else d_in).numel())
+    ptr = lambda t: C.c_void_p(int(t.data_ptr())) if t is not None else None
+    rc = lib().qk_eval_convert(ptr(f_in), ptr(d_out), ptr(d_in), ptr(f_out), n, _stream(stream))
+    if rc != OK:
+        raise QKError(rc, "qk_eval_convert failed")
 
 
 def make_params(**kw) -> Params:

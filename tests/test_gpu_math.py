@@ -60,3 +60,41 @@ def test_sqrt_of_zero_is_zero(torch_cuda):
     s = torch.empty_like(dx)
     qk.eval_math(dx, None, s)
     assert s.cpu().tolist() == [0.0, 2.0]
+
+
+def test_integer_pipe_conversions(torch_cuda):
+    """float -> double widening equals numpy's exact conversion for every
+    class of float (normal, subnormal, zero, infinite, NaN); double -> float
+    truncation lies within one FP32 ulp toward zero, flushes magnitudes below
+    the normal float range to signed zeros and clamps above it."""
+    torch = torch_cuda
+    from paper_2110_01792_gb300 import qk
+    rng = np.random.Generator(np.random.Philox(11))
+    bits = rng.integers(0, 2 ** 32, 400_000, dtype=np.uint64).astype(np.uint32)
+    extra = np.array([0.0, -0.0, np.inf, -np.inf, 1e-45, -1e-45, 1.17e-38, 3.4e38],
+                     dtype=np.float32)
+    f = np.concatenate([bits.view(np.float32), extra])
+    d = torch.empty(f.size, dtype=torch.float64, device="cuda")
+    qk.eval_convert(f_in=torch.from_numpy(f).cuda(), d_out=d)
+    got = d.cpu().numpy()
+    with np.errstate(invalid="ignore"):  # signalling NaN bit patterns
+        ref = f.astype(np.float64)
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].view(np.uint64), ref[~nan].view(np.uint64))
+    x = np.concatenate([rng.standard_normal(200_000) * 10.0 ** rng.uniform(-45, 45, 200_000),
+                        np.array([0.0, -0.0, 1e300, -1e300, 1e-300, np.inf])])
+    fo = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    qk.eval_convert(d_in=torch.from_numpy(x).cuda(), f_out=fo)
+    y = fo.cpu().numpy().astype(np.float64)
+    fmax, fmin = float(np.finfo(np.float32).max), float(np.finfo(np.float32).tiny)
+    ax = np.abs(x)
+    normal = (ax >= fmin) & (ax <= fmax)
+    assert np.all(np.abs(y[normal]) <= ax[normal])
+    up = np.nextafter(np.abs(y[normal]).astype(np.float32), np.float32(np.inf)).astype(np.float64)
+    assert np.all(ax[normal] < up)
+    assert np.all(np.sign(y[normal]) == np.sign(x[normal]))
+    assert np.all(y[ax < fmin] == 0.0)
+    big = np.isfinite(x) & (ax > fmax)
+    assert np.all(np.abs(y[big]) == fmax)
+    assert np.isinf(y[-1])
