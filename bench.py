@@ -282,7 +282,13 @@ def run_kernel_only(args):
     ctx = qk.Context(prob.layout, prob.params, prec)
     U = [torch.from_numpy(a).cuda().to(tdt) for a in prob.U]
     R = None if prob.R is None else [torch.from_numpy(a).cuda().to(tdt) for a in prob.R]
-    tuned = None if args.no_autotune else ctx.autotune(U, R)
+    if args.tile_shape == "auto":
+        tuned = None if args.no_autotune else ctx.autotune(U, R)
+    else:
+        # pinned launch configuration (deterministic captures)
+        cfg = (256, "columns") if args.tile_shape == "columns" else (256, "strided")
+        tuned = {k: cfg for k in ("hydro1", "hydro2", "rad1", "rad2")}
+        ctx.set_launch_config(tuned)
     ctx.fill_ghosts(U + (R or []))
     dt, _, dtr, _ = ctx.timestep(U)
     for _ in range(3):
@@ -654,6 +660,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-fused-exchange", action="store_true",
                     help="run the exchange as its own launch after radiation stage 2")
+    ap.add_argument("--tile-shape", choices=["auto", "tiles", "columns"], default="auto",
+                    help="with --kernel-only: autotune, or pin 8^3 tiles / 16x16 columns")
     ap.add_argument("--kernel-only", choices=["hydro1", "rad1", "rad2x", "exchange"], default=None,
                     help="launch one stage kernel 3 times and exit (for ncu captures)")
     args = ap.parse_args()

@@ -92,7 +92,7 @@ __device__ __forceinline__ void hydro_face_at(const F5<const T> &U, const T *chi
     T u[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = U.f[v][c];
-    con2prim<T>(u, p.gamma, q[o]);
+    con2prim<T>(u, (T)(p.gamma - 1.0), q[o]);
   }
   T wL[5], wR[5], dummy;
 #pragma unroll

@@ -476,13 +476,16 @@ static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, in
         best_cz = cz;
       }
     }
+    c->col_start.assign(nown + 1, 0);
     for (int l = 0; l < nown; ++l) {
       const qk_box &q = boxes[c->own[l]];
+      c->col_start[l] = (int)cols.size();
       for (int y = 0; y < q.n[1]; y += CW)
         for (int x = 0; x < q.n[0]; x += CW)
           for (int z = 0; z < q.n[2]; z += best_cz)
             cols.push_back(Column{l, x, y, z, std::min(z + best_cz, (int)q.n[2])});
     }
+    c->col_start[nown] = (int)cols.size();
   }
   c->ncols = (int)cols.size();
   std::vector<Copy> copies;
@@ -1105,6 +1108,17 @@ int qk_timestep(qk_ctx *c, void *const hydro[5], double out[4], void *stream) {
   return QK_OK;
 }
 
+// The work lists of patch b alone (tiles and columns are grouped by patch).
+static Geometry patch_geom(const qk_ctx *c, Geometry g, int b) {
+  g.tiles = c->d_tiles + c->tile_start[b];
+  g.ntiles = c->tile_start[b + 1] - c->tile_start[b];
+  if (g.cols) {
+    g.cols = c->d_cols + c->col_start[b];
+    g.ncols = c->col_start[b + 1] - c->col_start[b];
+  }
+  return g;
+}
+
 // Stage launches: one persistent launch over the tiles of every patch
 // (QK_LAUNCH_BATCHED), or one launch per patch over its own tiles
 // (QK_LAUNCH_PER_PATCH, kept for comparison).
@@ -1121,9 +1135,7 @@ static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *c
     return launch_hydro_stage(c->fp32, stage, g, c->p, U0, U1, Uo, dt, 0, c->cfg[stage - 1], chi,
                               s, lo);
   for (int b = 0; b < c->nbox_dev; ++b) {
-    Geometry gb = g;
-    gb.tiles = c->d_tiles + c->tile_start[b];
-    gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
+    const Geometry gb = patch_geom(c, g, b);
     cudaError_t e = launch_hydro_stage(c->fp32, stage, gb, c->p, U0, U1, Uo, dt, 0,
                                        c->cfg[stage - 1], chi, s, lo);
     if (e != cudaSuccess) return e;
@@ -1139,9 +1151,7 @@ static cudaError_t rad_launches(qk_ctx *c, int stage, void *const *R0, void *con
     return launch_rad_stage(c->fp32, stage, g, c->p, R0, R1, Ro, rho, dt, 0, c->cfg[1 + stage], s,
                             lo, fx);
   for (int b = 0; b < c->nbox_dev; ++b) {
-    Geometry gb = g;
-    gb.tiles = c->d_tiles + c->tile_start[b];
-    gb.ntiles = c->tile_start[b + 1] - c->tile_start[b];
+    const Geometry gb = patch_geom(c, g, b);
     cudaError_t e = launch_rad_stage(c->fp32, stage, gb, c->p, R0, R1, Ro, rho, dt, 0,
                                      c->cfg[1 + stage], s, lo, fx);
     if (e != cudaSuccess) return e;

@@ -125,7 +125,7 @@ __device__ __forceinline__ double cell_speed<float>(const F5<float> &U, long lon
   float u[5], w[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
-  con2prim<float>(u, gamma, w);
+  con2prim<float>(u, (float)(gamma - 1.0), w);
   const float v2 = (w[1] * w[1] + w[2] * w[2]) + w[3] * w[3];
   return (double)(qsqrt(v2) + qsqrt((float)gamma * w[4] * qrcp(w[0])));
 }

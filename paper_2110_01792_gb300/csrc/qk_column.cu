@@ -35,11 +35,11 @@ __device__ __forceinline__ void col_face(const T wL[5], const T wR[5], T gamma, 
 }
 
 template <typename T>
-__device__ __forceinline__ void load_prim(const F5<T> &U, long long e, double gamma, T w[5]) {
+__device__ __forceinline__ void load_prim(const F5<T> &U, long long e, T gm1, T w[5]) {
   T u[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
-  con2prim<T>(u, gamma, w);
+  con2prim<T>(u, gm1, w);
 }
 
 // Resident CTAs per SM the registers are held to (FP32: three, as many as
@@ -49,17 +49,18 @@ template <typename T> struct ColMinBlocks {
 };
 
 template <typename T, int STAGE>
-__global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kernel(Geometry g, qk_params p, F5<T> U0,
-                                                          F5<T> U1, F5<T> Uo, DtSrc dts,
+__global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kernel(Geometry g, qk_params p, SC<T> K,
+                                                          F5<T> U0, F5<T> U1, F5<T> Uo, DtSrc dts,
                                                           const T *chi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ColSmem<T> &sm = *reinterpret_cast<ColSmem<T> *>(smem_raw);
-  const T dt = (T)dt_of(dts);
-  const double gamma_d = p.gamma;
-  const T gamma = (T)p.gamma;
-  const T gm1inv = (T)(1.0 / (p.gamma - 1.0));
-  const T g1 = (T)((p.gamma + 1.0) / (2.0 * p.gamma));
-  const T inv_dx[3] = {(T)(1.0 / p.dx[0]), (T)(1.0 / p.dx[1]), (T)(1.0 / p.dx[2])};
+  // the timestep, converted once per CTA
+  __shared__ T s_dt;
+  if (threadIdx.x == 0) s_dt = (T)dt_of(dts);
+  __syncthreads();
+  const T dt = s_dt;
+  const T gm1 = K.gm1, gamma = K.gamma, gm1inv = K.gm1inv, g1 = K.g1;
+  const T *inv_dx = K.inv_dx;
   const F5<T> src = STAGE == 1 ? U0 : U1;
   const int rk = p.recon;
   const int t = threadIdx.x;
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
     T win[5][5];
     auto load_plane = [&](int z, T out[5]) {
       if (own_load) {
-        load_prim<T>(src, own0 + (long long)z * plane, gamma_d, out);
+        load_prim<T>(src, own0 + (long long)z * plane, gm1, out);
       } else {
 #pragma unroll
         for (int q = 0; q < 5; ++q) out[q] = (q == 0 || q == 4) ? T(1) : T(0);
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
     for (int z = col.z0; z < col.z1; ++z) {
       // ---- plane z+3 into the window, plane z (own + ring) into smem
       if (own_load) {
-        con2prim<T>(nown, gamma_d, win[4]);
+        con2prim<T>(nown, gm1, win[4]);
 #pragma unroll
         for (int q = 0; q < 5; ++q) sm.prim[q][pslot(ti, tj)] = win[1][q];
       } else {
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
       }
       if (ring) {
         T wr[5];
-        con2prim<T>(nring, gamma_d, wr);
+        con2prim<T>(nring, gm1, wr);
 #pragma unroll
         for (int q = 0; q < 5; ++q) sm.prim[q][pslot(ri, rj)] = wr[q];
       }
@@ -301,7 +302,7 @@ static cudaError_t launch_col(const Geometry &g, const qk_params &p, void *const
   int grid = nsm * (per_sm > 0 ? per_sm : 1);
   if (grid > g.ncols) grid = g.ncols;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, CNT, smem, s>>>(g, p, a, b, c, dt, (const T *)chi);
+  kern<<<grid, CNT, smem, s>>>(g, p, make_sc<T>(p), a, b, c, dt, (const T *)chi);
   return cudaGetLastError();
 }
 

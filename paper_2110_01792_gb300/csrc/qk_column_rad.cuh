@@ -27,14 +27,13 @@ __device__ __forceinline__ int cslot(int i, int j) { return (j + HALO) * CPW + (
 
 // E_r, f = F/(c E_r) and rho kappa_R of one cell from its conserved values.
 template <typename T>
-__device__ __forceinline__ void rad_prim(const T u[4], T c, T r, const qk_params &p, T w[4],
-                                         T &rk) {
+__device__ __forceinline__ void rad_prim(const T u[4], T c, T r, const SC<T> &K, T w[4], T &rk) {
   const T inv = qrcp(c * u[0]);
   w[0] = u[0];
   w[1] = u[1] * inv;
   w[2] = u[2] * inv;
   w[3] = u[3] * inv;
-  rk = r * kappa_of<T>(p, p.kappa_R, r);
+  rk = rho_kappa<T>(K, r);
 }
 
 template <typename T> struct ColMinBlocksRad {
@@ -43,16 +42,19 @@ template <typename T> struct ColMinBlocksRad {
 
 template <typename T, int STAGE, int CL, bool EX>
 __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
-    rad_column_kernel(Geometry g, qk_params p, F4<T> R0, F4<T> R1, F4<T> Ro, const T *rho,
-                      DtSrc dts, ExFuse<T> xf) {
+    rad_column_kernel(Geometry g, qk_params p, SC<T> K, F4<T> R0, F4<T> R1, F4<T> Ro,
+                      const T *rho, DtSrc dts, ExFuse<T> xf) {
   if (skip_substep(dts)) return;
   constexpr bool kAB = ColRadSmem<T>::kAB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ColRadSmem<T> &sm = *reinterpret_cast<ColRadSmem<T> *>(smem_raw);
-  const T dt = (T)dt_of(dts);
-  const T c = (T)p.c, chat = (T)p.chat;
-  const T inv_dx[3] = {(T)(1.0 / p.dx[0]), (T)(1.0 / p.dx[1]), (T)(1.0 / p.dx[2])};
-  const T dx[3] = {(T)p.dx[0], (T)p.dx[1], (T)p.dx[2]};
+  // the timestep, converted once per CTA
+  __shared__ T s_dt;
+  if (threadIdx.x == 0) s_dt = (T)dt_of(dts);
+  __syncthreads();
+  const T dt = s_dt;
+  const T c = K.c, chat = K.chat;
+  const T *inv_dx = K.inv_dx, *dx = K.dx;
   const T hccc = T(0.5) * c * chat;
   const T hchat_c = T(0.5) * chat / c;
   const F4<T> src = STAGE == 1 ? R0 : R1;
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
         T u[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) u[q] = src.f[q][e];
-        rad_prim<T>(u, c, rho[e], p, out, rko);
+        rad_prim<T>(u, c, rho[e], K, out, rko);
       } else {
         out[0] = T(1);
         out[1] = out[2] = out[3] = T(0);
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
     for (int z = col.z0; z < col.z1; ++z) {
       // ---- plane z+3 into the window; plane z (own + ring) into smem
       if (own_load) {
-        rad_prim<T>(nown, c, nrho_own, p, win[4], rkw[4]);
+        rad_prim<T>(nown, c, nrho_own, K, win[4], rkw[4]);
         const int s = cslot(ti, tj);
 #pragma unroll
         for (int q = 0; q < 4; ++q) sm.prim[q][s] = win[1][q];
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
       }
       if (ring) {
         T wr[4], rkr;
-        rad_prim<T>(nring, c, nrho_ring, p, wr, rkr);
+        rad_prim<T>(nring, c, nrho_ring, K, wr, rkr);
         const int s = cslot(ri, rj);
 #pragma unroll
         for (int q = 0; q < 4; ++q) sm.prim[q][s] = wr[q];
@@ -403,7 +405,7 @@ static cudaError_t launch_rad_col_one(const Geometry &g, const qk_params &p, voi
   int grid = nsm * (per_sm > 0 ? per_sm : 1);
   if (grid > g.ncols) grid = g.ncols;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, CNT, smem, s>>>(g, p, a, b, c, (const T *)rho, dt, xf);
+  kern<<<grid, CNT, smem, s>>>(g, p, make_sc<T>(p), a, b, c, (const T *)rho, dt, xf);
   return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@ struct qk_ctx {
   Tile *d_tiles_ib = nullptr;
   Column *d_cols = nullptr;    // column work list of the plane-marching kernels
   int ncols = 0;
+  std::vector<int> col_start;  // first column of each owned patch (grouped by patch)
   int n_interior = 0;
   int part = QK_PART_ALL;
   // sharded contexts: owner rank of every patch, this rank, and the halo

@@ -91,14 +91,15 @@ __device__ __forceinline__ float d2f_trunc(double x) {
 }
 
 // Conserved -> primitive (Sec. 2.2.1): v = m / rho, E_g = E - rho v^2 / 2,
-// P = (gamma - 1) E_g.  In mixed precision the internal energy is recovered
+// P = (gamma - 1) E_g, with gm1 = gamma - 1 given in the stencil precision
+// (formed once per kernel: a conversion per cell would occupy the FP64 pipe).  In mixed precision the internal energy is recovered
 // with ~48-bit error-free arithmetic (cancellation of E against the kinetic
 // energy), the rest in FP32.
 template <typename T>
-__device__ __forceinline__ void con2prim(const T u[5], double gamma, T w[5]);
+__device__ __forceinline__ void con2prim(const T u[5], T gm1, T w[5]);
 
 template <>
-__device__ __forceinline__ void con2prim<double>(const double u[5], double gamma, double w[5]) {
+__device__ __forceinline__ void con2prim<double>(const double u[5], double gm1, double w[5]) {
   double rho = u[0];
   const double inv = frcp(rho);
   double vx = u[1] * inv, vy = u[2] * inv, vz = u[3] * inv;
@@ -108,7 +109,7 @@ __device__ __forceinline__ void con2prim<double>(const double u[5], double gamma
   w[1] = vx;
   w[2] = vy;
   w[3] = vz;
-  w[4] = (gamma - 1.0) * Eg;
+  w[4] = gm1 * Eg;
 }
 
 // Error-free transformations (Knuth's TwoSum, FMA TwoProduct) for the FP32
@@ -166,7 +167,7 @@ __device__ __forceinline__ void internal_energy_f32(const float u[5], float rho,
 }
 
 template <>
-__device__ __forceinline__ void con2prim<float>(const float u[5], double gamma, float w[5]) {
+__device__ __forceinline__ void con2prim<float>(const float u[5], float gm1, float w[5]) {
   const float rho = u[0];
   float inv = qrcp(rho);
   inv = inv * fmaf(-rho, inv, 2.0f);  // one Newton step: ~1 ulp
@@ -176,7 +177,7 @@ __device__ __forceinline__ void con2prim<float>(const float u[5], double gamma, 
   w[3] = u[3] * inv;
   float hi, lo;
   internal_energy_f32(u, rho, inv, hi, lo);
-  w[4] = (float)(gamma - 1.0) * (hi + lo);
+  w[4] = gm1 * (hi + lo);
 }
 
 // PPM reconstruction of one cell from the stencil s0..s4 = q_{i-2..i+2}

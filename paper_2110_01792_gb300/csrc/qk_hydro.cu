@@ -123,19 +123,20 @@ __device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T in
 // (L0, L1, Lo the lo arrays of U0, U1, Uo); the stencil reads hi only, the
 // update is accumulated in double-float so that the face terms telescope.
 template <typename T, int STAGE, int NT, bool CP>
-__global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p, F5<T> U0,
-                                                         F5<T> U1, F5<T> Uo, DtSrc dts, int sched,
-                                                         const T *chi, F5<T> L0, F5<T> L1,
-                                                         F5<T> Lo) {
+__global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p, SC<T> K,
+                                                         F5<T> U0, F5<T> U1, F5<T> Uo, DtSrc dts,
+                                                         int sched, const T *chi, F5<T> L0,
+                                                         F5<T> L1, F5<T> Lo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   HydroSmem<T> &sm = *reinterpret_cast<HydroSmem<T> *>(smem_raw);
   constexpr int NOWN = NCORE / NT;
-  const T dt = (T)dt_of(dts);
-  const double gamma_d = p.gamma;
-  const T gamma = (T)p.gamma;
-  const T gm1inv = (T)(1.0 / (p.gamma - 1.0));
-  const T g1 = (T)((p.gamma + 1.0) / (2.0 * p.gamma));
-  const T inv_dx[3] = {(T)(1.0 / p.dx[0]), (T)(1.0 / p.dx[1]), (T)(1.0 / p.dx[2])};
+  // the timestep, converted once per CTA
+  __shared__ T s_dt;
+  if (threadIdx.x == 0) s_dt = (T)dt_of(dts);
+  __syncthreads();
+  const T dt = s_dt;
+  const T gm1 = K.gm1, gamma = K.gamma, gm1inv = K.gm1inv, g1 = K.g1;
+  const T *inv_dx = K.inv_dx;
   const F5<T> src = STAGE == 1 ? U0 : U1;
 
   // tile schedule: strided over the grid (0) or one contiguous run of tiles
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
       T u[5], w[5];
 #pragma unroll
       for (int q = 0; q < 5; ++q) u[q] = src.f[q][e];
-      con2prim<T>(u, gamma_d, w);
+      con2prim<T>(u, gm1, w);
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         own[m][q] = u[q];
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
       T u[5], w[5];
 #pragma unroll
       for (int q = 0; q < 5; ++q) u[q] = src.f[q][e];
-      con2prim<T>(u, gamma_d, w);
+      con2prim<T>(u, gm1, w);
 #pragma unroll
       for (int q = 0; q < 5; ++q) sm.prim[q][s] = w[q];
     }
@@ -270,7 +271,8 @@ static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const
   }
   if (grid > g.ntiles) grid = g.ntiles;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, dt, sched, (const T *)chi, l0, l1, lo_);
+  kern<<<grid, NT, smem, s>>>(g, p, make_sc<T>(p), a, b, c, dt, sched, (const T *)chi, l0, l1,
+                              lo_);
   return cudaGetLastError();
 }
 
@@ -313,12 +315,12 @@ cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_
 // p_{c-1})), else 0, with dp1 = p_{c+1} - p_{c-1}, dp2 = p_{c+2} - p_{c-2};
 // f_d = max(ftilde(c), ftilde(c - sign(dp1))); chi = min_d (1 - f_d).
 template <typename T>
-__device__ __forceinline__ void flat_prim(const F5<T> &U, long long e, double gamma, int d,
+__device__ __forceinline__ void flat_prim(const F5<T> &U, long long e, T gm1, int d,
                                           T &pr, T &un) {
   T u[5], w[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
-  con2prim<T>(u, gamma, w);
+  con2prim<T>(u, gm1, w);
   pr = w[4];
   un = w[1 + d];
 }
@@ -335,6 +337,7 @@ __device__ __forceinline__ T flat_ftilde(const T pr[7], const T un[7], int c) {
 
 template <typename T>
 __global__ void __launch_bounds__(512) flatten_kernel(Geometry g, double gamma, F5<T> U, T *chi) {
+  const T gm1 = (T)(gamma - 1.0);
   for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
     const Tile tl = g.tiles[t];
     const DevBox b = g.boxes[tl.box];
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(512) flatten_kernel(Geometry g, double gamma, 
         for (int o = -3; o <= 3; ++o) {
           int cc[3] = {tl.x0 + c[0], tl.y0 + c[1], tl.z0 + c[2]};
           cc[d] += o;
-          flat_prim<T>(U, cell_elem(b, g.ng, cc[0], cc[1], cc[2]), gamma, d, pr[o + 3], un[o + 3]);
+          flat_prim<T>(U, cell_elem(b, g.ng, cc[0], cc[1], cc[2]), gm1, d, pr[o + 3], un[o + 3]);
         }
         T f = flat_ftilde<T>(pr, un, 3);
         const T dp1 = pr[4] - pr[2];

@@ -105,6 +105,32 @@ struct Status {
   unsigned long long total_iter;
 };
 
+// Constants of a stage kernel in its stencil precision, formed on the host:
+// device-side conversions and divisions of the FP64 parameters occupy the
+// FP64 pipe, and a register-bound kernel may repeat them at every use.
+template <typename T> struct SC {
+  T gamma, gm1, gm1inv, g1;  // gamma, gamma - 1, 1/(gamma - 1), (gamma + 1)/(2 gamma)
+  T inv_dx[3], dx[3];
+  T c, chat, kR;             // speed of light, reduced speed, kappa_R (or kappa0)
+  int kmode;                 // QK_KAPPA_*
+};
+template <typename T> inline SC<T> make_sc(const qk_params &p) {
+  SC<T> k;
+  k.gamma = (T)p.gamma;
+  k.gm1 = (T)(p.gamma - 1.0);
+  k.gm1inv = (T)(1.0 / (p.gamma - 1.0));
+  k.g1 = (T)((p.gamma + 1.0) / (2.0 * p.gamma));
+  for (int d = 0; d < 3; ++d) {
+    k.inv_dx[d] = (T)(1.0 / p.dx[d]);
+    k.dx[d] = (T)p.dx[d];
+  }
+  k.c = (T)p.c;
+  k.chat = (T)p.chat;
+  k.kR = (T)p.kappa_R;
+  k.kmode = p.kappa_mode;
+  return k;
+}
+
 // Where a stage takes its timestep: a device StepInfo field when `p` is set,
 // else the host value `v`.  `nsub`/`sub` predicate radiation substeps.
 struct DtSrc {

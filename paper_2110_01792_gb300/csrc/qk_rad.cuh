@@ -38,13 +38,17 @@ template <typename T> struct ExFuse {
 template <typename T> __device__ __forceinline__ T kappa_of(const qk_params &p, double k, T rho) {
   return p.kappa_mode == QK_KAPPA_RHO ? (T)k * rho : (T)k;
 }
+// rho kappa_R of a cell from the host-formed constant (no conversion)
+template <typename T> __device__ __forceinline__ T rho_kappa(const SC<T> &K, T rho) {
+  return rho * (K.kmode == QK_KAPPA_RHO ? K.kR * rho : K.kR);
+}
 
 // Stage one cross slot: E_r, f = F / (c E_r) (one reciprocal), rho kappa_R,
 // and in FP64 the closure coefficients of the cell average when the slot is
 // adjacent to a face of the tile (within one cell of the valid region).
 template <typename T, int CL>
 __device__ __forceinline__ void load_slot(RadSmem<T> &sm, int s, const T u[4], T c, T r,
-                                          const qk_params &p, int i, int j, int k,
+                                          const SC<T> &K, int i, int j, int k,
                                           const int v[3]) {
   const T inv = qrcp(c * u[0]);
   const T fx = u[1] * inv, fy = u[2] * inv, fz = u[3] * inv;
@@ -52,7 +56,7 @@ __device__ __forceinline__ void load_slot(RadSmem<T> &sm, int s, const T u[4], T
   sm.prim[1][s] = fx;
   sm.prim[2][s] = fy;
   sm.prim[3][s] = fz;
-  sm.rk[s] = r * kappa_of<T>(p, p.kappa_R, r);
+  sm.rk[s] = rho_kappa<T>(K, r);
   if constexpr (RadSmem<T>::kAB) {
     const bool near = i >= -1 && j >= -1 && k >= -1 && i <= v[0] && j <= v[1] && k <= v[2];
     if (near) {
@@ -263,19 +267,22 @@ template <typename T, int NT, bool EX> struct RadMinBlocks {
 };
 
 template <typename T, int STAGE, int NT, int CL, bool CP, bool EX>
-__device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_params &p, F4<T> R0,
-                                               F4<T> R1, F4<T> Ro, const T *rho, DtSrc dts,
-                                               int sched, F4<T> L0, F4<T> L1, F4<T> Lo,
-                                               const ExFuse<T> &xf) {
+__device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_params &p,
+                                               const SC<T> &K, F4<T> R0, F4<T> R1, F4<T> Ro,
+                                               const T *rho, DtSrc dts, int sched, F4<T> L0,
+                                               F4<T> L1, F4<T> Lo, const ExFuse<T> &xf) {
   if (skip_substep(dts)) return;
   ExStat xs;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RadSmem<T> &sm = *reinterpret_cast<RadSmem<T> *>(smem_raw);
   constexpr int NOWN = NCORE / NT;
-  const T dt = (T)dt_of(dts);
-  const T c = (T)p.c, chat = (T)p.chat;
-  const T inv_dx[3] = {(T)(1.0 / p.dx[0]), (T)(1.0 / p.dx[1]), (T)(1.0 / p.dx[2])};
-  const T dx[3] = {(T)p.dx[0], (T)p.dx[1], (T)p.dx[2]};
+  // the timestep, converted once per CTA
+  __shared__ T s_dt;
+  if (threadIdx.x == 0) s_dt = (T)dt_of(dts);
+  __syncthreads();
+  const T dt = s_dt;
+  const T c = K.c, chat = K.chat;
+  const T *inv_dx = K.inv_dx, *dx = K.dx;
   const F4<T> src = STAGE == 1 ? R0 : R1;
 
   // tile schedule: strided over the grid (0) or one contiguous run of tiles
@@ -301,7 +308,7 @@ __device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_param
       T u[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) u[q] = src.f[q][e];
-      load_slot<T, CL>(sm, s, u, c, rho[e], p, i, j, k, v);
+      load_slot<T, CL>(sm, s, u, c, rho[e], K, i, j, k, v);
 #pragma unroll
       for (int q = 0; q < 4; ++q) own[m][q] = u[q];
       if constexpr (CP) {
@@ -319,7 +326,7 @@ __device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_param
       T u[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) u[q] = src.f[q][e];
-      load_slot<T, CL>(sm, s, u, c, rho[e], p, i, j, k, v);
+      load_slot<T, CL>(sm, s, u, c, rho[e], K, i, j, k, v);
     }
     __syncthreads();
     T acc[NOWN][4], accl[NOWN][4];
@@ -410,18 +417,20 @@ __device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_param
 }
 
 template <typename T, int STAGE, int NT, int CL, bool CP>
-__global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, F4<T> R0,
-                                                       F4<T> R1, F4<T> Ro, const T *rho,
+__global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, SC<T> K,
+                                                       F4<T> R0, F4<T> R1, F4<T> Ro, const T *rho,
                                                        DtSrc dts, int sched, F4<T> L0, F4<T> L1,
                                                        F4<T> Lo, ExFuse<T> xf) {
-  rad_stage_body<T, STAGE, NT, CL, CP, false>(g, p, R0, R1, Ro, rho, dts, sched, L0, L1, Lo, xf);
+  rad_stage_body<T, STAGE, NT, CL, CP, false>(g, p, K, R0, R1, Ro, rho, dts, sched, L0, L1, Lo,
+                                              xf);
 }
 
 template <typename T, int NT, int CL, bool CP>
 __global__ void __launch_bounds__(NT, (RadMinBlocks<T, NT, true>::value))
-    rad_stage_ex_kernel(Geometry g, qk_params p, F4<T> R0, F4<T> R1, F4<T> Ro, const T *rho,
-                        DtSrc dts, int sched, F4<T> L0, F4<T> L1, F4<T> Lo, ExFuse<T> xf) {
-  rad_stage_body<T, 2, NT, CL, CP, true>(g, p, R0, R1, Ro, rho, dts, sched, L0, L1, Lo, xf);
+    rad_stage_ex_kernel(Geometry g, qk_params p, SC<T> K, F4<T> R0, F4<T> R1, F4<T> Ro,
+                        const T *rho, DtSrc dts, int sched, F4<T> L0, F4<T> L1, F4<T> Lo,
+                        ExFuse<T> xf) {
+  rad_stage_body<T, 2, NT, CL, CP, true>(g, p, K, R0, R1, Ro, rho, dts, sched, L0, L1, Lo, xf);
 }
 
 template <typename T, int STAGE, int NT, int CL, bool CP>
@@ -466,7 +475,8 @@ static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const
   }
   if (grid > g.ntiles) grid = g.ntiles;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, NT, smem, s>>>(g, p, a, b, c, (const T *)rho, dt, sched, l0, l1, lo_, xf);
+  kern<<<grid, NT, smem, s>>>(g, p, make_sc<T>(p), a, b, c, (const T *)rho, dt, sched, l0, l1,
+                              lo_, xf);
   return cudaGetLastError();
 }
 

@@ -515,14 +515,17 @@ def test_step_conserves_on_gpu(torch_cuda):
         assert abs(s1[10 + d] - s0[10 + d]) <= 1e-13 * abs(s0[9]) / 100.0
 
 
-def test_per_patch_launches_match_batched(torch_cuda):
+@pytest.mark.parametrize("shape", ["tiles", "columns"])
+def test_per_patch_launches_match_batched(torch_cuda, shape):
     """One launch per patch and stage gives bit-identical results to the
-    batched persistent launch over all patches (each tile's arithmetic does not
-    depend on which CTA runs it)."""
+    batched persistent launch over all patches (each tile's or column's
+    arithmetic does not depend on which CTA runs it), with either tile shape."""
     lay, prob, prm = _small_rhd()
     outs = []
     for per_patch in (False, True):
         ctx = _ctx(lay, prm)
+        if shape == "columns":
+            ctx.set_launch_config(ALLCOLS)
         ctx.set_launch_mode(per_patch)
         dU, dR = G.dev(prob.U), G.dev(prob.R)
         for _ in range(3):
