@@ -198,7 +198,26 @@ __device__ __forceinline__ void exchange_cell(const qk_params &p, const ExK &K, 
   }
   // radiation source S = dt (chat/c) j, carried in the residual's E_r0
   const double Er0S = src ? Er0 + dt * K.rc_d * load_d(src, e) : Er0;
+  // Start the FP64 iteration from an FP32 Newton solve to 1e-6 (the same
+  // equations on FP32 pipes, inputs narrowed on the integer pipe): the FP64
+  // iteration then needs about two steps, one correction and one confirming
+  // the tolerance, instead of ~4 from the cell state.  It converges to the
+  // same root (the last correction is applied, so the result is accurate far
+  // below the tolerance whichever start is taken); a failed FP32 solve leaves
+  // the start at the cell state.
   double Eg = Eg0, Er = Er0;
+  {
+    const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
+    const float Ef0 = d2f_trunc(Eg0), Rf0 = d2f_trunc(Er0S);
+    const float Af = d2f_trunc(A), kf = d2f_trunc(k), tf = d2f_trunc(thr_g);
+    float Egf = Ef0, Erf = Rf0;
+    const int itf = newton_exchange<float>(alpha_eos, Af, kf, K.crf, Ef0, Rf0, 1e4f * tf,
+                                           1e4f * tf * K.rc, 12, Egf, Erf);
+    if (itf > 0 && Egf > 0.0f && Erf > 0.0f && isfinite(Egf) && isfinite(Erf)) {
+      Eg = f2d(Egf);
+      Er = f2d(Erf);
+    }
+  }
   int it;
   it = newton_exchange<double>(p.eos == QK_EOS_ALPHA_T3, A, k, K.cr, Eg0, Er0S, thr_g, thr_r,
                                p.max_iter, Eg, Er);

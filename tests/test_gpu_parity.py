@@ -320,7 +320,10 @@ def test_exchange_matches_oracle(torch_cuda, kappa0):
     ctx.exchange(dU, dR, dtr)
     torch.cuda.synchronize()
     rc, flags, bad, maxit = ctx.status()
-    assert rc == 0 and flags == 0 and bad == -1 and abs(maxit - info[2]) <= 1
+    # the FP64 iteration starts from an FP32 Newton solve, so it takes at most
+    # as many steps as the oracle's from the cell state (and at least the
+    # correction plus the confirming step)
+    assert rc == 0 and flags == 0 and bad == -1 and 2 <= maxit <= info[2] + 1, (maxit, info)
     e = G.max_rel_err(lay, G.host(dU) + G.host(dR), Ur + Rr)
     ctx.close()
     assert max(e) <= TOL_STAGE, e
