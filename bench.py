@@ -587,13 +587,24 @@ def run_ours(args):
         ctx.status(reset=True)
         del R1, R2, Uc
     kname = max(times, key=lambda k: times[k][0] * times[k][1])
+    tot_k = sum(v[0] * v[1] for v in times.values())
     t_k = times[kname][0]
     tname = "double" if prec == qk.FP64 else "float"
-    kern = {"hydro1": f"hydro_stage_kernel<{tname},1>", "hydro2": f"hydro_stage_kernel<{tname},2>",
-            "rad1": f"rad_stage_kernel<{tname},1>", "rad2": f"rad_stage_kernel<{tname},2>",
-            "rad2x": f"rad_stage_ex_kernel<{tname}>",
-            "exchange": "exchange_kernel<double>" if prec == qk.FP64
-                        else "exchange_kernel_mixed"}[kname]
+    stage_of = {"hydro1": "hydro1", "hydro2": "hydro2", "rad1": "rad1", "rad2": "rad2",
+                "rad2x": "rad2"}
+    cols = bool(tuned) and kname in stage_of and tuned[stage_of[kname]][1] == "columns"
+    if cols:
+        kern = {"hydro1": f"hydro_column_kernel<{tname},1>",
+                "hydro2": f"hydro_column_kernel<{tname},2>",
+                "rad1": f"rad_column_kernel<{tname},1>", "rad2": f"rad_column_kernel<{tname},2>",
+                "rad2x": f"rad_column_kernel<{tname},2,EX>"}[kname]
+    else:
+        kern = {"hydro1": f"hydro_stage_kernel<{tname},1>",
+                "hydro2": f"hydro_stage_kernel<{tname},2>",
+                "rad1": f"rad_stage_kernel<{tname},1>", "rad2": f"rad_stage_kernel<{tname},2>",
+                "rad2x": f"rad_stage_ex_kernel<{tname}>",
+                "exchange": "exchange_kernel<double>" if prec == qk.FP64
+                            else "exchange_kernel_mixed"}[kname]
     bytes_launch = algorithmic_bytes_per_cell(kname, elem) * cells
     flops_launch = ALGO_FLOPS[kname] * cells
     hbm_ach = bytes_launch / t_k / 1e9
@@ -611,7 +622,8 @@ def run_ours(args):
     roofline = dict(main_, kernel=kern, traffic=ncu_traffic(args.workload, kern),
                     launch_s=t_k, algorithmic_bytes_per_launch=bytes_launch,
                     algorithmic_flops_per_launch=flops_launch, other=other,
-                    kernel_shares={k: v[0] * v[1] for k, v in times.items()})
+                    kernel_s_per_update={k: v[0] * v[1] for k, v in times.items()},
+                    kernel_shares={k: v[0] * v[1] / tot_k for k, v in times.items()})
 
     ctx.close()
     if rank != 0:

@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_para
   if (skip_substep(dts)) return;
   const ExK K = make_exk(p);
   const double dt = dt_of(dts);
+  const float dtf = (float)dt;
   ExStat xs;
   for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < g.ncells;
        cidx += (long long)gridDim.x * blockDim.x) {
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_para
       fl[1] = RL.f[2][e];
       fl[2] = RL.f[3][e];
     }
-    exchange_cell_mixed<CP>(p, K, dt, U, R, UL, RL, src, e, R.f[0][e], el, fr, fl, xs);
+    exchange_cell_mixed<CP>(p, K, dt, dtf, U, R, UL, RL, src, e, R.f[0][e], el, fr, fl, xs);
   }
   exchange_status(st, xs.max, xs.flags, xs.bad);
 }

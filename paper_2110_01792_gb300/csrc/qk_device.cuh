@@ -144,6 +144,48 @@ __device__ __forceinline__ void df_norm(float &h, float &l) {
   l = t;
 }
 
+// Double-float values (h + l, |l| <= ulp(h)/2, ~48 significant bits) for
+// arithmetic that needs more than FP32 without the FP64 pipe (Dekker 1971;
+// Knuth's TwoSum; FMA TwoProduct), on round-to-nearest intrinsics so that no
+// product is fused into the transforms.  Sums and products end with the fast
+// renormalisation (Dekker's FastTwoSum), whose error under cancellation is
+// bounded in absolute terms (~2^-48 of the operands), the measure the
+// callers need.
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_fast(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_of(float a, float b) {  // any a, b
+  float s, e;
+  two_sum(a, b, s, e);
+  return DF{s, e};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  float s, e;
+  two_sum(x.h, y.h, s, e);
+  return df_fast(s, __fadd_rn(e, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ DF df_neg(DF x) { return DF{-x.h, -x.l}; }
+__device__ __forceinline__ DF df_sub(DF x, DF y) { return df_add(x, df_neg(y)); }
+__device__ __forceinline__ DF df_add_f(DF x, float b) {
+  float s, e;
+  two_sum(x.h, b, s, e);
+  return df_fast(s, __fadd_rn(e, x.l));
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float p = __fmul_rn(x.h, y.h);
+  const float e = fmaf(x.h, y.h, -p);
+  return df_fast(p, __fadd_rn(e, __fadd_rn(__fmul_rn(x.h, y.l), __fmul_rn(x.l, y.h))));
+}
+__device__ __forceinline__ DF df_mul_f(DF x, float b) {
+  const float p = __fmul_rn(x.h, b);
+  const float e = fmaf(x.h, b, -p);
+  return df_fast(p, __fadd_rn(e, __fmul_rn(x.l, b)));
+}
+
 // Internal energy E_g = E - |m|^2/(2 rho) of an FP32 state as an unevaluated
 // sum hi + lo (about 48 significant bits), from the velocity reciprocal `inv`
 // (~1 ulp of 1/rho).

@@ -135,6 +135,46 @@ __device__ __forceinline__ int newton_refine(bool alpha_eos, int max_iter, doubl
   return conv ? it + 1 : -1;
 }
 
+// The same refinement with double-float residuals and iterates (~48
+// significant bits, on the FP32 pipes): the residual of a cell is evaluated
+// to ~2^-46 k (c/chat) E_tot, well inside the 1e-10 tolerance while
+// k (c/chat) <= 1e3 (the callers use newton_refine beyond).  A, k are FP32
+// numbers (the coefficients of the equations being solved), cr = c/chat is a
+// double-float constant.
+__device__ __forceinline__ int newton_refine_df(bool alpha_eos, int max_iter, float Af, float kf,
+                                                DF cr, float crf, DF Eg0, DF Er0, float thr_g,
+                                                float thr_r, DF &Eg, DF &Er) {
+  const float dFG_dEr = -crf * kf, dFR_dEr = 1.0f + kf;
+  const float A4 = 4.0f * Af;
+  bool conv = false;
+  int it = 0;
+  for (it = 0; it < max_iter; ++it) {
+    DF Rr;
+    float dRdEg;
+    if (alpha_eos) {
+      Rr = df_sub(df_mul_f(Eg, Af), df_mul_f(Er, kf));
+      dRdEg = Af;
+    } else {
+      const DF E2 = df_mul(Eg, Eg);
+      Rr = df_sub(df_mul_f(df_mul(E2, E2), Af), df_mul_f(Er, kf));
+      dRdEg = A4 * Eg.h * Eg.h * Eg.h;
+    }
+    const DF FG = df_add(df_sub(Eg, Eg0), df_mul(cr, Rr));
+    const DF FR = df_sub(df_sub(Er, Er0), Rr);
+    const float fg = FG.h, fr = FR.h;
+    conv = fabsf(fg) < thr_g && fabsf(fr) < thr_r;
+    const float G = 1.0f + crf * dRdEg;
+    const float D1 = dFR_dEr * G + dRdEg * dFG_dEr;
+    const float inv = qrcp(D1 * G);
+    const float dEr = -(fr * G + dRdEg * fg) * (G * inv);
+    const float dEg = -(fg + dEr * dFG_dEr) * (D1 * inv);
+    Er = df_add_f(Er, dEr);
+    Eg = df_add_f(Eg, dEg);
+    if (conv) break;
+  }
+  return conv ? it + 1 : -1;
+}
+
 // Constants of the exchange (host or device; the substep dt is passed apart,
 // since inside a captured step it is read from device memory).
 struct ExK {
@@ -142,6 +182,8 @@ struct ExK {
   double a_e;             // a_r, or 4 a_r/alpha for the alpha T^3 heat capacity
   float icc, rc, icc_lo;  // FP32 forms; icc_lo: 1/(c chat) - icc
   float crf, a_ef, inv_cvf, kchat;  // kchat: kappa_P chat (or kappa0 chat)
+  float kRf, chatf, epsf;          // kappa_R (or kappa0), chat, the Newton tolerance
+  DF cr_df, rc_df;                 // c/chat and chat/c as double-float
 };
 __host__ __device__ __forceinline__ ExK make_exk(const qk_params &p) {
   ExK K;
@@ -157,6 +199,13 @@ __host__ __device__ __forceinline__ ExK make_exk(const qk_params &p) {
   K.a_ef = (float)K.a_e;
   K.inv_cvf = (float)K.inv_cv;
   K.kchat = (float)(p.kappa_P * p.chat);
+  K.kRf = (float)p.kappa_R;
+  K.chatf = (float)p.chat;
+  K.epsf = (float)p.eps_newton;
+  K.cr_df.h = (float)K.cr;
+  K.cr_df.l = (float)(K.cr - (double)K.cr_df.h);
+  K.rc_df.h = (float)K.rc_d;
+  K.rc_df.l = (float)(K.rc_d - (double)K.rc_df.h);
   return K;
 }
 
@@ -250,24 +299,34 @@ __device__ __forceinline__ void exchange_cell(const qk_params &p, const ExK &K, 
 }
 
 // FP32-mixed exchange of cell e (see exchange_kernel_mixed): (er, fr) the
-// radiation state after the transport, (er_lo, fr_lo) its low parts (CP).
+// radiation state after the transport, (er_lo, fr_lo) its low parts (CP);
+// dt the substep and dtf its FP32 rounding (formed once by the caller).
 // FP32 state; the internal energy recovered with the error-free FP32
-// transforms of con2prim; the Newton solve with FP64 residuals and
-// convergence test (FP32 warm start, then newton_refine); the flux source,
-// momentum and kinetic-energy work in FP32, the new total energy accumulated
-// in FP64 before the final rounding.
+// transforms of con2prim; the Newton solve on the FP32 coefficients A, k with
+// ~48-bit residuals: an FP32 warm start, then newton_refine_df in
+// double-float where its rounding (~2^-43 (1 + k c/chat) E_tot) stays below
+// the tolerance eps E_tot, else newton_refine in FP64; the flux source and
+// the momentum and kinetic-energy work in FP32, the new total energy and
+// radiation energy formed in double-float before the final rounding.
 // CP: compensated state (every conserved field hi + lo; UL, RL the lo
 // arrays): E, E_r, m and F are read as hi + lo, the new E and E_r are formed
-// in FP64 from the invariant E + (c/chat) E_r (the kinetic-energy change
-// taken from the FP64 difference of the same two values), and the momentum
-// exchange m + F/(c chat) = const is carried in double-float with a
-// double-float 1/(c chat), so that both invariants hold to ~2^-48.
+// from the invariant E + (c/chat) E_r (the kinetic-energy change taken from
+// the double-float difference of the same two values) and stored hi + lo,
+// and the momentum exchange m + F/(c chat) = const is carried in double-float
+// with a double-float 1/(c chat), so that both invariants hold to ~2^-47.
+__device__ __forceinline__ bool pos_finite(float x) { return x > 0.0f && x <= 3.402823466e38f; }
+__device__ __forceinline__ DF df_of_double(double x) {
+  const float h = (float)x;
+  return DF{h, (float)(x - (double)h)};
+}
+
 template <bool CP>
 __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const ExK &K, double dt,
-                                                    F5<float> U, F4<float> R, F5<float> UL,
-                                                    F4<float> RL, const float *src, long long e,
-                                                    float er, float er_lo, const float fr[3],
-                                                    const float fr_lo[3], ExStat &xs) {
+                                                    float dtf, F5<float> U, F4<float> R,
+                                                    F5<float> UL, F4<float> RL, const float *src,
+                                                    long long e, float er, float er_lo,
+                                                    const float fr[3], const float fr_lo[3],
+                                                    ExStat &xs) {
   float u[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
@@ -276,51 +335,56 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
   rinv = rinv * fmaf(-rho, rinv, 2.0f);  // one Newton step: ~1 ulp
   float eg_hi, eg_lo;
   internal_energy_f32(u, rho, rinv, eg_hi, eg_lo);  // ~48-bit E_g, no EOS round trip
-  const float Er0f = er;
-  // widenings on the integer pipe (exact)
-  double Eg0 = f2d(eg_hi) + f2d(eg_lo);
-  double Er0 = f2d(Er0f);
+  DF Eg0 = df_of(eg_hi, eg_lo);
+  DF Er0{er, 0.0f};
   float E_lo = 0.0f;
   if constexpr (CP) {
     E_lo = UL.f[4][e];
-    Eg0 += f2d(E_lo);
-    Er0 += f2d(er_lo);
+    Eg0 = df_add_f(Eg0, E_lo);
+    Er0 = df_of(er, er_lo);
   }
   // the coefficients in FP32: k = dt rho kappa_P chat, A = k a_r/(rho c_v)^4
   // (or 4 k a_r/alpha), and the convergence thresholds eps E_tot,
   // eps E_tot chat/c (E_tot = E_g0 + (c/chat) E_r0)
   const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
-  const float kf = (float)dt * K.kchat * (p.kappa_mode == QK_KAPPA_RHO ? rho * rho : rho);
+  const float kf = dtf * K.kchat * (p.kappa_mode == QK_KAPPA_RHO ? rho * rho : rho);
   float Af = kf * K.a_ef;
   if (!alpha_eos) {
     const float i1 = rinv * K.inv_cvf, i2 = i1 * i1;
     Af *= i2 * i2;
   }
-  const double k = f2d(kf), A = f2d(Af);
-  const float Eg0f = eg_hi + (eg_lo + E_lo);
-  const float Etotf = Eg0f + K.crf * (Er0f + er_lo);
-  const float thr_g = (float)p.eps_newton * Etotf, thr_r = thr_g * K.rc;
+  const float Etotf = Eg0.h + K.crf * Er0.h;
+  const float thr_g = K.epsf * Etotf, thr_r = thr_g * K.rc;
   // radiation source S = dt (chat/c) j, carried in the residual's E_r0
-  const double Er0S = src ? Er0 + dt * K.rc_d * f2d(src[e]) : Er0;
+  const DF Er0S = src ? df_add_f(Er0, (dtf * K.rc) * src[e]) : Er0;
   // FP32 warm start to 1e-6
-  float Egf = Eg0f, Erf = src ? (float)Er0S : Er0f;
-  const int itf = newton_exchange<float>(alpha_eos, Af, kf, K.crf, Eg0f, Erf, 1e-6f * Etotf,
+  float Egf = Eg0.h, Erf = Er0S.h;
+  const int itf = newton_exchange<float>(alpha_eos, Af, kf, K.crf, Eg0.h, Erf, 1e-6f * Etotf,
                                          1e-6f * Etotf * K.rc, 12, Egf, Erf);
-  double Eg = Eg0, Er = Er0;
-  if (itf > 0 && Egf > 0.0f && Erf > 0.0f && isfinite(Egf) && isfinite(Erf)) {
-    Eg = f2d(Egf);
-    Er = f2d(Erf);
+  DF Eg = Eg0, Er = Er0S;
+  if (itf > 0 && pos_finite(Egf) && pos_finite(Erf)) {
+    Eg = DF{Egf, 0.0f};
+    Er = DF{Erf, 0.0f};
   }
-  const int it = newton_refine(alpha_eos, p.max_iter, A, k, K.cr, Eg0, Er0S, Af, kf, K.crf,
-                               thr_g, thr_r, Eg, Er);
+  int it;
+  if ((1.0f + kf * K.crf) * 0x1p-43f < K.epsf) {  // false for a NaN k
+    it = newton_refine_df(alpha_eos, p.max_iter, Af, kf, K.cr_df, K.crf, Eg0, Er0S, thr_g, thr_r,
+                          Eg, Er);
+  } else {
+    double Egd = f2d(Eg.h), Erd = f2d(Er.h);
+    it = newton_refine(alpha_eos, p.max_iter, f2d(Af), f2d(kf), K.cr, f2d(Eg0.h) + f2d(Eg0.l),
+                       f2d(Er0S.h) + f2d(Er0S.l), Af, kf, K.crf, thr_g, thr_r, Egd, Erd);
+    Eg = df_of_double(Egd);
+    Er = df_of_double(Erd);
+  }
   if (it < 0) {
     xs.flags |= 1u << QK_ENOCONV;
     xs.bad = min(xs.bad, (unsigned long long)e);
   } else {
     xs.max = max(xs.max, it);
   }
-  const float kF = p.kappa_mode == QK_KAPPA_RHO ? (float)p.kappa_R * rho : (float)p.kappa_R;
-  const float damp = qrcp(1.0f + rho * kF * (float)(p.chat * dt));
+  const float kF = p.kappa_mode == QK_KAPPA_RHO ? K.kRf * rho : K.kRf;
+  const float damp = qrcp(1.0f + rho * kF * (K.chatf * dtf));
   float mn[3];
   float ke0 = 0.0f, ke1 = 0.0f;
 #pragma unroll
@@ -354,26 +418,24 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
     ke1 = fmaf(mn[a], mn[a], ke1);
   }
   const float Ekin1 = 0.5f * ke1 * rinv;
-  double Er_new;
+  const DF Enew = df_add_f(Eg, Ekin1);
+  DF Er_new;
   if constexpr (CP) {
     // E_new = E_g + E_kin,1; E_r,new = E_r - (chat/c)(E_kin,1 - E_kin,0) with
-    // E_kin,0 = E - E_g0 (the same FP64 values), split into hi + lo
-    const double Ekin0 = (f2d(u[4]) + f2d(E_lo)) - Eg0;
-    const double Ek1 = f2d(Ekin1);
-    const double Enew = Eg + Ek1;
-    Er_new = Er - (K.rc_d) * (Ek1 - Ekin0);
-    const float Eh = (float)Enew, Rh = (float)Er_new;
-    U.f[4][e] = Eh;
-    UL.f[4][e] = (float)(Enew - f2d(Eh));
-    R.f[0][e] = Rh;
-    RL.f[0][e] = (float)(Er_new - f2d(Rh));
+    // E_kin,0 = E - E_g0 (the same double-float values)
+    const DF Ekin0 = df_sub(df_of(u[4], E_lo), Eg0);
+    Er_new = df_sub(Er, df_mul(K.rc_df, df_add_f(df_neg(Ekin0), Ekin1)));
+    U.f[4][e] = Enew.h;
+    UL.f[4][e] = Enew.l;
+    R.f[0][e] = Er_new.h;
+    RL.f[0][e] = Er_new.l;
   } else {
     const float dEkin = 0.5f * (ke1 - ke0) * rinv;
-    U.f[4][e] = (float)(Eg + f2d(Ekin1));
-    Er_new = Er - f2d(K.rc * dEkin);
-    R.f[0][e] = (float)Er_new;
+    Er_new = df_add_f(Er, -K.rc * dEkin);
+    U.f[4][e] = Enew.h;
+    R.f[0][e] = Er_new.h;
   }
-  if (!pos_finite(Eg) || !pos_finite(Er_new)) {
+  if (!pos_finite(Eg.h) || !pos_finite(Er_new.h)) {
     xs.flags |= 1u << QK_ENEGATIVE;
     xs.bad = min(xs.bad, (unsigned long long)e);
   }

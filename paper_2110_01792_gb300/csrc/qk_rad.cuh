@@ -407,7 +407,7 @@ __device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_param
             fl[1] = Lo.f[2][e];
             fl[2] = Lo.f[3][e];
           }
-          exchange_cell_mixed<CP>(p, xf.K, dt_of(dts), xf.U, Ro, xf.UL, Lo, xf.src, e,
+          exchange_cell_mixed<CP>(p, xf.K, dt_of(dts), dt, xf.U, Ro, xf.UL, Lo, xf.src, e,
                                   Ro.f[0][e], el, fr, fl, xs);
         }
       }
