@@ -244,9 +244,10 @@ def time_kernel(torch, fn, reps, stream):
 # (profiles/ncu_*_128.md), valid only while the kernel's sources hash to the
 # value recorded at capture time.
 NCU_TRAFFIC = {
-    ("rhd128", "rad_stage_ex_kernel<double>"): (344.13e6, "rad", "d0a5a6cf9b03"),
-    ("rhd128", "rad_stage_ex_kernel<float>"): (418.56e6, "rad", "d0a5a6cf9b03"),
-    ("rhd128", "hydro_stage_kernel<float,1>"): (105.54e6, "hydro", "e8b211bfaf7f"),
+    ("rhd128", "rad_stage_ex_kernel<double>"): (343.16e6, "rad", "36644bed4b8c"),
+    ("rhd128", "rad_column_kernel<float,2,EX>"): (165.34e6, "radcol", "3e27ab1294bf"),
+    ("rhd128", "rad_column_kernel<float,1>"): (54.70e6, "radcol", "3e27ab1294bf"),
+    ("rhd128", "hydro_column_kernel<float,1>"): (59.63e6, "hydrocol", "ab1a8b3a89bd"),
 }
 
 
@@ -254,6 +255,9 @@ def _src_hash(kind: str) -> str:
     import hashlib
     cs = os.path.join(ROOT, "paper_2110_01792_gb300", "csrc")
     files = {"rad": ["qk_rad.cu", "qk_rad.cuh", "qk_exchange.cuh"], "hydro": ["qk_hydro.cu"],
+             "radcol": ["qk_column_rad.cu", "qk_column_rad.cuh", "qk_rad.cuh",
+                        "qk_exchange.cuh"],
+             "hydrocol": ["qk_column.cu"],
              "cell": ["qk_cell.cu", "qk_exchange.cuh"]}[kind]
     h = hashlib.sha1()
     for f in files + ["qk_device.cuh", "qk_internal.cuh"]:

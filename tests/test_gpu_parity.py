@@ -329,6 +329,42 @@ def test_exchange_matches_oracle(torch_cuda, kappa0):
     assert max(e) <= TOL_STAGE, e
 
 
+@pytest.mark.parametrize("kappa_mode", [0, 1], ids=["kconst", "krho"])
+def test_mixed_exchange_matches_oracle(torch_cuda, kappa_mode):
+    """FP32-mixed exchange against the FP64 oracle on the same FP32-rounded
+    state, with the opacity set so that k c/chat = dt rho kappa_P c (times rho
+    for kappa = kappa0 rho) straddles the bound below which the refinement
+    runs in double-float (k c/chat < eps 2^43 - 1, ~878 at eps = 1e-10):
+    both the double-float and the FP64 refinement are exercised.  The FP32
+    coefficients A, k and the FP32 storage bound the per-cell error
+    (~1e-6 relative)."""
+    torch = torch_cuda
+    lay = RAGGED
+    prob, prm = _random_rhd(lay, 7)
+    rho = G.interior(lay, prob.U[0])
+    dtr = 0.3 * (1.0 / 19) / prm["chat"]
+    w = rho if kappa_mode == 0 else rho * rho
+    prm["kappa_mode"] = kappa_mode
+    prm["kappa_P"] = prm["kappa_R"] = 878.0 / (dtr * float(np.median(w)) * prm["c"])
+    kcr = dtr * w * prm["kappa_P"] * prm["c"]
+    assert 0.3 < np.mean(kcr < 850.0) < 0.7 and np.mean(kcr > 900.0) > 0.3
+    U32 = [a.astype(np.float32).astype(np.float64) for a in prob.U]
+    R32 = [a.astype(np.float32).astype(np.float64) for a in prob.R]
+    Ur = [a.copy() for a in U32]
+    Rr = [a.copy() for a in R32]
+    rc, info = O.exchange(_grid(lay), O.make_params(**prm), Ur, Rr, dtr)
+    assert rc == 0
+    ctx = _ctx(lay, prm, 1)
+    dU, dR = G.dev(U32, torch.float32), G.dev(R32, torch.float32)
+    ctx.exchange(dU, dR, dtr)
+    torch.cuda.synchronize()
+    rc, flags, bad, maxit = ctx.status()
+    ctx.close()
+    assert rc == 0 and flags == 0 and bad == -1 and maxit <= info[2] + 1, (maxit, info)
+    e = G.max_rel_err(lay, G.host(dU) + G.host(dR), Ur + Rr)
+    assert max(e) <= 4e-6, e
+
+
 def test_exchange_nonconvergence_reported(torch_cuda):
     torch = torch_cuda
     lay = I.single_box(3, 2, 2)
