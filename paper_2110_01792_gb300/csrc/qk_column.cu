@@ -23,6 +23,10 @@ template <typename T> struct ColSmem {
   T prim[5][CNPL];                 // rho, vx, vy, vz, P of plane z and its ring
   T rec[2][10][CXPOS * CW];        // x and y: qL, qR of each primitive per position
   T flux[2][5][CXFACE * CW];       // x and y face fluxes
+  // FP32: the own cell's U_src (5) and U_0 (5, stage 2) read by the epilogue,
+  // staged one phase ahead (cp.async)
+  static constexpr bool kPre = sizeof(T) == 4;
+  T pre[kPre ? 10 : 1][kPre ? CNT : 1];
 };
 
 __device__ __forceinline__ int pslot(int i, int j) { return (j + HALO) * CPW + (i + HALO); }
@@ -174,6 +178,19 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
       }
       if (z + 1 < col.z1) fetch(z + 1);
       __syncthreads();
+      if constexpr (ColSmem<T>::kPre) {
+        // the epilogue's own-cell inputs, in flight during the two phases
+        if (own_valid) {
+          const long long e = own0 + (long long)z * plane;
+#pragma unroll
+          for (int q = 0; q < 5; ++q) cp_async_elem(&sm.pre[q][t], src.f[q] + e);
+          if constexpr (STAGE == 2) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) cp_async_elem(&sm.pre[5 + q][t], U0.f[q] + e);
+          }
+        }
+        cp_async_commit();
+      }
       // ---- x and y reconstruction (items t, t + CNT, ...), and z in registers
       for (int it = t; it < 2 * CXPOS * CW; it += CNT) {
         const int dir = it >= CXPOS * CW;
@@ -253,17 +270,19 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
       if (own_valid) {
         const long long e = own0 + (long long)z * plane;
         const int fx = tj * CXFACE + ti, fy = tj * CW + ti;
+        constexpr bool kPre = ColSmem<T>::kPre;
+        if constexpr (kPre) cp_async_wait_all();
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           T acc = (sm.flux[0][q][fx + 1] - sm.flux[0][q][fx]) * inv_dx[0];
           acc = acc + (sm.flux[1][q][fy + CW] - sm.flux[1][q][fy]) * inv_dx[1];
           acc = acc + (Fzn[q] - Fz[q]) * inv_dx[2];
           const T L = -acc;
-          const T own = src.f[q][e];
+          const T own = kPre ? sm.pre[kPre ? q : 0][kPre ? t : 0] : src.f[q][e];
           if (STAGE == 1) {
             Uo.f[q][e] = own + dt * L;
           } else {
-            const T u0 = U0.f[q][e];
+            const T u0 = kPre ? sm.pre[kPre ? 5 + q : 0][kPre ? t : 0] : U0.f[q][e];
             Uo.f[q][e] = T(0.5) * u0 + T(0.5) * (own + dt * L);
           }
         }

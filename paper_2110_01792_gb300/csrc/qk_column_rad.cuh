@@ -21,6 +21,10 @@ template <typename T> struct ColRadSmem {
   T rec[2][8][CXPOS * CW];           // x and y: qL, qR per position
   T sq[2][kAB ? 1 : CXPOS * CW];     // FP32: sqrt(T_DD) of the cell average per position
   T flux[2][4][CXFACE * CW];
+  // FP32: the own cell's values read by the epilogue, staged one phase ahead
+  // (cp.async): R_src (4), R_0 (4, stage 2), the gas state U (5, exchange)
+  static constexpr int kPre = kAB ? 1 : 13;
+  T pre[kPre][kAB ? 1 : CNT];
 };
 
 __device__ __forceinline__ int cslot(int i, int j) { return (j + HALO) * CPW + (i + HALO); }
@@ -229,6 +233,23 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
       }
       if (z + 1 < col.z1) fetch(z + 1);
       __syncthreads();
+      if constexpr (!kAB) {
+        // the epilogue's own-cell inputs, in flight during the two phases
+        if (own_valid) {
+          const long long e = own0 + (long long)z * plane;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cp_async_elem(&sm.pre[q][t], src.f[q] + e);
+          if constexpr (STAGE == 2) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cp_async_elem(&sm.pre[4 + q][t], R0.f[q] + e);
+          }
+          if constexpr (EX) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) cp_async_elem(&sm.pre[8 + q][t], xf.U.f[q] + e);
+          }
+        }
+        cp_async_commit();
+      }
       // ---- x and y reconstruction; z in registers
       for (int it = t; it < 2 * CXPOS * CW; it += CNT) {
         const int dir = it >= CXPOS * CW;
@@ -331,6 +352,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
       if (own_valid) {
         const long long e = own0 + (long long)z * plane;
         const int fx = tj * CXFACE + ti, fy = tj * CW + ti;
+        if constexpr (!kAB) cp_async_wait_all();
         T rv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -338,11 +360,11 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
           acc = acc + (sm.flux[1][q][fy + CW] - sm.flux[1][q][fy]) * inv_dx[1];
           acc = acc + (Fzn[q] - Fz[q]) * inv_dx[2];
           const T L = -acc;
-          const T own = src.f[q][e];
+          const T own = kAB ? src.f[q][e] : sm.pre[kAB ? 0 : q][kAB ? 0 : t];
           if (STAGE == 1) {
             rv[q] = own + dt * L;
           } else {
-            const T u0 = R0.f[q][e];
+            const T u0 = kAB ? R0.f[q][e] : sm.pre[kAB ? 0 : 4 + q][kAB ? 0 : t];
             rv[q] = T(0.5) * u0 + T(0.5) * (own + dt * L);
           }
           Ro.f[q][e] = rv[q];
@@ -355,7 +377,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
             const float fl[3] = {0.0f, 0.0f, 0.0f};
             F4<float> none{};
             exchange_cell_mixed<false>(p, xf.K, dt_of(dts), dt, xf.U, Ro, xf.UL, none, xf.src, e,
-                                       rv[0], 0.0f, rv + 1, fl, xs);
+                                       rv[0], 0.0f, rv + 1, fl, xs, &sm.pre[8][t], CNT);
           }
         }
       }

@@ -144,6 +144,26 @@ __device__ __forceinline__ void df_norm(float &h, float &l) {
   l = t;
 }
 
+// Per-thread asynchronous copy of one 4- or 8-byte element from global to
+// shared memory (cp.async, the L1-allocating form); the copies of a thread are
+// committed as a group and waited for by the same thread, which is the only
+// reader of what it staged (no barrier needed).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst_smem, const T *src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Double-float values (h + l, |l| <= ulp(h)/2, ~48 significant bits) for
 // arithmetic that needs more than FP32 without the FP64 pipe (Dekker 1971;
 // Knuth's TwoSum; FMA TwoProduct), on round-to-nearest intrinsics so that no

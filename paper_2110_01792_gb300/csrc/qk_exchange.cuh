@@ -300,7 +300,9 @@ __device__ __forceinline__ void exchange_cell(const qk_params &p, const ExK &K, 
 
 // FP32-mixed exchange of cell e (see exchange_kernel_mixed): (er, fr) the
 // radiation state after the transport, (er_lo, fr_lo) its low parts (CP);
-// dt the substep and dtf its FP32 rounding (formed once by the caller).
+// dt the substep and dtf its FP32 rounding (formed once by the caller);
+// u_pre: the gas state of the cell already staged by the caller (field q at
+// u_pre[q u_stride]), else it is read from U.
 // FP32 state; the internal energy recovered with the error-free FP32
 // transforms of con2prim; the Newton solve on the FP32 coefficients A, k with
 // ~48-bit residuals: an FP32 warm start, then newton_refine_df in
@@ -326,10 +328,11 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
                                                     F5<float> UL, F4<float> RL, const float *src,
                                                     long long e, float er, float er_lo,
                                                     const float fr[3], const float fr_lo[3],
-                                                    ExStat &xs) {
+                                                    ExStat &xs, const float *u_pre = nullptr,
+                                                    int u_stride = 0) {
   float u[5];
 #pragma unroll
-  for (int q = 0; q < 5; ++q) u[q] = U.f[q][e];
+  for (int q = 0; q < 5; ++q) u[q] = u_pre ? u_pre[q * u_stride] : U.f[q][e];
   const float rho = u[0];
   float rinv = qrcp(rho);
   rinv = rinv * fmaf(-rho, rinv, 2.0f);  // one Newton step: ~1 ulp
