@@ -226,6 +226,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_alu_peak(torch, qk, fp64: bool, stream) -> float:
+    """FMA throughput of this GPU in TFLOP/s from the library's probe
+    (qk_fma_probe: 8 independent FMA chains per thread, 64 warps per SM),
+    best of three launches timed with CUDA events on `stream`."""
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    sink = torch.empty(8 * 256 * nsm, dtype=torch.float64 if fp64 else torch.float32,
+                       device="cuda")
+    iters = 2000 if fp64 else 100000      # ~10 ms per launch
+    h = stream.cuda_stream
+    qk.fma_probe(fp64, iters, sink, h)
+    best = 0.0
+    for _ in range(3):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        fl = qk.fma_probe(fp64, iters, sink, h)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, fl / (ev0.elapsed_time(ev1) / 1e3) / 1e12)
+    return best
+
+
 def time_kernel(torch, fn, reps, stream):
     """Average device duration of one launch of fn() (CUDA events on `stream`)."""
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -556,7 +579,8 @@ def run_ours(args):
     # entry point (CUDA events on the launching stream), weighted by its
     # launches per update; the largest share is reported against the peak of
     # the unit its arithmetic runs on (FP64 for the FP64 path; FP32 for the
-    # FP32-mixed kernels, whose exchange part is FP64 by design) ----
+    # FP32-mixed kernels), from the unit counts and clocks and, beside it,
+    # from the FMA throughput measured by the library's probe ----
     pk, pk_kind = peaks()
     reps = 10
     fused = not args.no_fused_exchange
@@ -618,10 +642,14 @@ def run_ours(args):
     alu_ach = flops_launch / t_k / 1e12
     hbm = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
            "frac": hbm_ach / hbm_peak, "peak_source": f"{pk_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    alu_meas = measure_alu_peak(torch, qk, fp64_unit, stream)
     alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
            "frac": alu_ach / alu_peak,
            "peak_source": ("FP64" if fp64_unit else "FP32") +
-                          " unit counts x 2.07 GHz (no measured FP64/FP32 peak in MEASURED_PEAKS.json)"}
+                          " unit counts x 2.07 GHz (no measured FP64/FP32 peak in MEASURED_PEAKS.json)",
+           "measured_peak": alu_meas, "frac_of_measured": alu_ach / alu_meas,
+           "measured_peak_source": "qk_fma_probe in this run (independent FMA chains, "
+                                   "64 warps per SM, best of 3)"}
     main_, other = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
     roofline = dict(main_, kernel=kern, traffic=ncu_traffic(args.workload, kern),
                     launch_s=t_k, algorithmic_bytes_per_launch=bytes_launch,

@@ -532,6 +532,19 @@ int qk_eval_math(const double *x, int64_t n, double *rcp, double *sqrt_out, void
 int qk_eval_convert(const float *f_in, double *d_out, const double *d_in, float *f_out, int64_t n,
                     void *stream);
 
+/* FMA throughput probe (not part of the method): the ALU peak against which
+ * the stage kernels' arithmetic is measured.  Launches min(8 x SMs,
+ * sink_len / 256) blocks of 256 threads; each thread runs 8 independent
+ * chains a <- a (1 - 2^-20) + 2^-10 for `iters` steps, starting from
+ * a = (thread index mod 32) + chain index, in FP64 (fp64 != 0) or FP32, and
+ * stores the sum of its chains in sink[thread] (device array of sink_len
+ * doubles or floats, owned by the caller).  *flops (may be NULL) receives the
+ * flop count of the launch (2 per step and chain); the caller times the
+ * launch on `stream`.  QK_EINVAL if iters < 1, sink is NULL or sink_len < 256,
+ * QK_ECUDA if the launch fails. */
+int qk_fma_probe(int32_t fp64, int64_t iters, void *sink, int64_t sink_len, double *flops,
+                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -453,7 +453,49 @@ __global__ void eval_convert_kernel(const float *fi, double *dout, const double 
   }
 }
 
+// -------------------------------------------------------- ALU probe ---
+// FMA throughput probe: every thread runs QK_FMA_CHAINS independent chains
+// a <- a m + c for `iters` steps (2 flops per step and chain) and stores the
+// sum of its chains, so that nothing is dead code.  With m = 1 - 2^-20 and
+// c = 2^-10 the chains approach c / (1 - m) = 1024 from their start values
+// and stay finite and normal.
+constexpr int QK_FMA_CHAINS = 8;
+template <typename T>
+__global__ void __launch_bounds__(256) fma_probe_kernel(long long iters, T *sink) {
+  const T m = T(1) - T(1.0 / 1048576.0), c = T(1.0 / 1024.0);
+  T a[QK_FMA_CHAINS];
+#pragma unroll
+  for (int i = 0; i < QK_FMA_CHAINS; ++i) a[i] = T(threadIdx.x % 32 + i);
+  for (long long k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int i = 0; i < QK_FMA_CHAINS; ++i) a[i] = fma(a[i], m, c);
+  }
+  T sum = T(0);
+#pragma unroll
+  for (int i = 0; i < QK_FMA_CHAINS; ++i) sum += a[i];
+  sink[(long long)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 }  // namespace qk
+
+extern "C" int qk_fma_probe(int32_t fp64, int64_t iters, void *sink, int64_t sink_len,
+                            double *flops, void *stream) {
+  if (iters < 1 || !sink || sink_len < 1) return QK_EINVAL;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return QK_ECUDA;
+  // 8 blocks of 256 threads per SM (64 warps), fewer if the sink is smaller
+  long long blocks = std::min<long long>(8LL * nsm, sink_len / 256);
+  if (blocks < 1) return QK_EINVAL;
+  if (fp64)
+    qk::fma_probe_kernel<double><<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(iters, (double *)sink);
+  else
+    qk::fma_probe_kernel<float><<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(iters, (float *)sink);
+  if (cudaGetLastError() != cudaSuccess) return QK_ECUDA;
+  if (flops) *flops = 2.0 * qk::QK_FMA_CHAINS * (double)iters * (double)(blocks * 256);
+  return QK_OK;
+}
 
 extern "C" int qk_eval_convert(const float *f_in, double *d_out, const double *d_in, float *f_out,
                                int64_t n, void *stream) {

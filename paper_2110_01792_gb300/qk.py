@@ -112,6 +112,7 @@ def lib():
     L.qk_set_timestep.argtypes = [vp, dbl, P(dbl), vp]
     L.qk_eval_math.argtypes = [vp, i64, vp, vp, vp]
     L.qk_eval_convert.argtypes = [vp, vp, vp, vp, i64, vp]
+    L.qk_fma_probe.argtypes = [i32, i64, vp, i64, P(dbl), vp]
     L.qk_step_compensated.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), P(dbl), P(i32), vp]
     L.qk_conserved_sums_compensated.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), P(dbl), vp]
     for f in ("qk_init_level", "qk_amr_init", "qk_amr_info", "qk_amr_interp", "qk_amr_register",
@@ -120,7 +121,8 @@ def lib():
               "qk_signal_speed", "qk_set_timestep", "qk_set_params", "qk_set_graph", "qk_set_launch_mode", "qk_set_fused_exchange", "qk_rad_stage2_exchange", "qk_set_launch_config", "qk_autotune",
               "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
               "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
-              "qk_status", "qk_step_info", "qk_eval_math", "qk_eval_convert", "qk_step_compensated",
+              "qk_status", "qk_step_info", "qk_eval_math", "qk_eval_convert", "qk_fma_probe",
+              "qk_step_compensated",
               "qk_conserved_sums_compensated"):
         getattr(L, f).restype = C.c_int
     _lib = L
@@ -165,6 +167,18 @@ def eval_convert(f_in=None, d_out=None, d_in=None, f_out=None, stream=None):
     rc = lib().qk_eval_convert(ptr(f_in), ptr(d_out), ptr(d_in), ptr(f_out), n, _stream(stream))
     if rc != OK:
         raise QKError(rc, "qk_eval_convert failed")
+
+
+def fma_probe(fp64: bool, iters: int, sink, stream=None) -> float:
+    """Launch the library's FMA throughput probe on `stream` (the caller times
+    it); `sink` is a device tensor of at least 256 doubles / floats.  Returns
+    the launch's flop count."""
+    fl = C.c_double(0.0)
+    rc = lib().qk_fma_probe(1 if fp64 else 0, int(iters), C.c_void_p(int(sink.data_ptr())),
+                            int(sink.numel()), C.byref(fl), _stream(stream))
+    if rc != OK:
+        raise QKError(rc, "qk_fma_probe failed")
+    return fl.value
 
 
 def make_params(**kw) -> Params:

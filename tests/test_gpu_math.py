@@ -98,3 +98,31 @@ def test_integer_pipe_conversions(torch_cuda):
     big = np.isfinite(x) & (ax > fmax)
     assert np.all(np.abs(y[big]) == fmax)
     assert np.isinf(y[-1])
+
+
+@pytest.mark.parametrize("fp64", [True, False], ids=["fp64", "fp32"])
+def test_fma_probe_values_and_flop_count(torch_cuda, fp64):
+    """The ALU probe computes what it counts: every thread's 8 chains
+    a <- a (1 - 2^-20) + 2^-10 from a0 = (thread mod 32) + chain follow the
+    closed form a_n = L + m^n (a0 - L), L = 2^-10 / 2^-20 = 1024 (rounding
+    accumulates to ~n ulp(1024) at most), and the flop count is
+    2 x 8 x iters x threads."""
+    torch = torch_cuda
+    from paper_2110_01792_gb300 import qk
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    n_threads = 8 * 256 * nsm
+    sink = torch.full((n_threads + 100,), -1.0, dtype=torch.float64 if fp64 else torch.float32,
+                      device="cuda")
+    iters = 1000
+    fl = qk.fma_probe(fp64, iters, sink)
+    torch.cuda.synchronize()
+    assert fl == 2.0 * 8 * iters * n_threads
+    got = sink.double().cpu().numpy()
+    m, L = 1.0 - 2.0 ** -20, 1024.0
+    t = np.arange(n_threads) % 32
+    exp = sum(L + m ** iters * ((t + i) - L) for i in range(8))
+    ulp = np.spacing(np.float64(L) if fp64 else np.float32(L))
+    assert np.max(np.abs(got[:n_threads] - exp)) <= 8 * iters * float(ulp)
+    assert np.all(got[n_threads:] == -1.0)  # nothing beyond the launched threads
+    with pytest.raises(qk.QKError):
+        qk.fma_probe(fp64, 0, sink)
