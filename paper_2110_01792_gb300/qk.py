@@ -13,7 +13,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libqk.so")
+# QK_FMAD=0 selects the diagnostic build without FMA contraction
+# (build.build(fmad=False)); the default is the production library.
+LIB_PATH = os.path.join(_HERE, "_build" if os.environ.get("QK_FMAD", "1") != "0"
+                        else "_build_nofmad", "libqk.so")
 
 OK, EINVAL, ECUDA, ENOCONV, ENEGATIVE = 0, 1, 2, 3, 4
 FP64, FP32_MIXED = 0, 1
