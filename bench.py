@@ -313,7 +313,7 @@ def run_kernel_only(args):
         tuned = None if args.no_autotune else ctx.autotune(U, R)
     else:
         # pinned launch configuration (deterministic captures)
-        cfg = (256, "columns") if args.tile_shape == "columns" else (256, "strided")
+        cfg = (256, "columns") if args.tile_shape == "columns" else (args.threads, "strided")
         tuned = {k: cfg for k in ("hydro1", "hydro2", "rad1", "rad2")}
         ctx.set_launch_config(tuned)
     ctx.fill_ghosts(U + (R or []))
@@ -706,6 +706,8 @@ def main():
                     help="run the exchange as its own launch after radiation stage 2")
     ap.add_argument("--tile-shape", choices=["auto", "tiles", "columns"], default="auto",
                     help="with --kernel-only: autotune, or pin 8^3 tiles / 16x16 columns")
+    ap.add_argument("--threads", type=int, default=256, choices=[128, 256, 512],
+                    help="with --kernel-only --tile-shape tiles: threads per 8^3 tile CTA")
     ap.add_argument("--kernel-only", choices=["hydro1", "rad1", "rad2x", "exchange"], default=None,
                     help="launch one stage kernel 3 times and exit (for ncu captures)")
     args = ap.parse_args()

@@ -56,6 +56,21 @@ __device__ __forceinline__ float qsqrt(float x) {
   return r;
 }
 __device__ __forceinline__ float psqrt(float x) { return qsqrt(x); }
+// sqrt(n / d) for a positive normal d and n >= 0 with a normal product n d:
+// y ~ 1/sqrt(n d) (rsqrt.approx.ftz.f64) gives s = n y ~ sqrt(n/d), and the
+// series of psqrt on e = 1 - (n d) y^2 corrects it to within about an ulp
+// (the rounding of n d adds at most 2^-54).  Seven FP64 slots against the
+// nine of a reciprocal, a product and psqrt.  A zero n returns zero.
+__device__ __forceinline__ double psqrt_div(double n, double d) {
+  const double P = n * d;
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(P));
+  const double s = n * y;
+  const double e = fma(-(P * y), y, 1.0);
+  const double r = fma(s, e * fma(e, 0.375, 0.5), s);
+  return (__double_as_longlong(n) << 1) == 0 ? n : r;
+}
+__device__ __forceinline__ float psqrt_div(float n, float d) { return qsqrt(__fdividef(n, d)); }
 
 // float <-> double conversions on the integer pipe.  On GB300 every F2F
 // conversion occupies a slot of the 1/64-rate FP64 pipe; these do the same
@@ -303,6 +318,34 @@ __device__ __forceinline__ float nn_max(float a, float b) { return fmaxf(a, b); 
 __device__ __forceinline__ double nn_min(double a, double b) { return nn_gt(a, b) ? b : a; }
 __device__ __forceinline__ float nn_min(float a, float b) { return fminf(a, b); }
 
+// Sign tests and max(0, x) of doubles on the integer pipe (x >= 0 and x <= 0
+// hold for both zeros, as IEEE comparisons do); floats use FP32 operations.
+__device__ __forceinline__ bool is_ge0(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 || (b << 1) == 0;
+}
+__device__ __forceinline__ bool is_le0(double x) { return __double_as_longlong(x) <= 0; }
+__device__ __forceinline__ double pos_part(double x) { return __double_as_longlong(x) > 0 ? x : 0.0; }
+__device__ __forceinline__ bool is_ge0(float x) { return x >= 0.0f; }
+__device__ __forceinline__ bool is_le0(float x) { return x <= 0.0f; }
+__device__ __forceinline__ float pos_part(float x) { return fmaxf(x, 0.0f); }
+// The same number (bit patterns for doubles; an FP32 compare for floats).
+__device__ __forceinline__ bool same_value(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
+__device__ __forceinline__ bool same_value(float a, float b) { return a == b; }
+
+// Signs of differences of finite doubles from their keys: kzero identifies the
+// two zeros (dkey(-0) = -1, dkey(+0) = 0), after which a - b > 0, = 0, < 0
+// exactly when kzero(dkey(a)) >, =, < kzero(dkey(b)) (the difference of two
+// doubles rounds to zero only when they are equal).  kdiff_same: a - b and
+// c - d are nonzero with the same sign, i.e. (a - b)(c - d) > 0.
+__device__ __forceinline__ long long kzero(long long k) { return k == -1 ? 0 : k; }
+__device__ __forceinline__ bool kdiff_same(long long za, long long zb, long long zc,
+                                           long long zd) {
+  return (za > zb && zc > zd) || (za < zb && zc < zd);
+}
+
 // Product sign tests of finite doubles on the integer pipe: a b > 0 exactly
 // when both are nonzero with equal sign bits (a product that underflows to
 // zero, |a b| < 2^-1074, counts here as positive).
@@ -331,14 +374,18 @@ __device__ __forceinline__ double ppm_face(double a, double b, double c, double 
 //   -d^2 > d q6 <=>  d (qR - r') > 0  with r' = 3 q - 2 qL
 //   (expand d q6 -+ d^2); at the tie l' = qL (r' = qR), so a decision that
 //   rounding flips moves the result only by rounding.
+// The sign tests compare integer keys instead of forming the differences.
 // The values equal the direct evaluation bit for bit except at such ties.
 __device__ __forceinline__ void ppm_limit(double fL, double fR, double s1, double s2, double s3,
                                           double &qL, double &qR) {
   const long long k1 = dkey(s1), k2 = dkey(s2), k3 = dkey(s3);
   const long long klo = min(k1, min(k2, k3)), khi = max(k1, max(k2, k3));
-  double l = dunkey(min(max(dkey(fL), klo), khi));
-  double r = dunkey(min(max(dkey(fR), klo), khi));
-  if (!dsame_nz(r - s2, s2 - l)) {
+  const long long kl = min(max(dkey(fL), klo), khi), kr = min(max(dkey(fR), klo), khi);
+  double l = dunkey(kl);
+  double r = dunkey(kr);
+  // the signs of the differences from the keys (no FP64 subtraction)
+  const long long zl = kzero(kl), zr = kzero(kr), z2 = kzero(k2);
+  if (!kdiff_same(zr, z2, z2, zl)) {  // (r - q)(q - l) <= 0
     const double dm = s2 - s1, dp = s3 - s2;
     double h = 0.0;  // half the MC slope
     if (dsame_nz(dm, dp)) {
@@ -353,14 +400,14 @@ __device__ __forceinline__ void ppm_limit(double fL, double fR, double s1, doubl
     l = s2 - h;
     r = s2 + h;
   } else {
+    // d = r - l has the sign of zr - zl (nonzero: r > q > l or r < q < l)
     const double t3 = 3.0 * s2;
-    const double d = r - l;
     const double ln = fma(-2.0, r, t3);
-    if (dsame_nz(d, ln - l)) {
+    if (kdiff_same(zr, zl, kzero(dkey(ln)), zl)) {  // d (l' - l) > 0
       l = ln;
     } else {
       const double rn = fma(-2.0, l, t3);
-      if (dsame_nz(d, r - rn)) r = rn;
+      if (kdiff_same(zr, zl, zr, kzero(dkey(rn)))) r = rn;  // d (r - r') > 0
     }
   }
   qL = l;
@@ -430,54 +477,58 @@ __device__ __forceinline__ void recon(int kind, T s0, T s1, T s2, T s3, T s4, T 
 // states wL, wR = (rho, vx, vy, vz, P): PVRS pressure estimate for the
 // wavespeeds S_L, S_R, contact speed S*, and the HLLC star state written with
 // the ratio (S_K - u_K)/(S_K - S*) first so that a stationary contact keeps
-// U*_K = U_K exactly.  The region is chosen by selects, not branches.
+// U*_K = U_K exactly (the ratio is taken as exactly 1 when numerator and
+// denominator are the same number).  Only one side K enters the flux: the
+// supersonic side (S_L >= 0: left, else S_R <= 0: right), else the upwind
+// side of the star region (tie S* = 0 -> left); its total energy alone is
+// formed.  The transverse momentum fluxes are the mass flux times the
+// transverse velocity of K (for the star state,
+// m_K a_K + S_K (rho*_K a_K - rho_K a_K) = a_K F_rho).  The region is chosen
+// by selects, not branches; in FP64 the sign and order tests run on the
+// integer pipe.  sqrt(gamma p / rho) and sqrt(1 + g1 (p*/p_K - 1)) =
+// sqrt((p_K + g1 (p* - p_K)) / p_K) are square roots of quotients
+// (psqrt_div: one approximate reciprocal square root, no division).
 template <typename T, int D>
 __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm1inv, T g1,
                                      T F[5]) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
-  const T rL = wL[0], uL = wL[1 + D], aL_ = wL[1 + A], bL = wL[1 + B], pL = wL[4];
-  const T rR = wR[0], uR = wR[1 + D], aR_ = wR[1 + A], bR = wR[1 + B], pR = wR[4];
-  const T EL = pL * gm1inv + T(0.5) * rL * (uL * uL + (aL_ * aL_ + bL * bL));
-  const T ER = pR * gm1inv + T(0.5) * rR * (uR * uR + (aR_ * aR_ + bR * bR));
-  const T cL = psqrt(qdiv(gamma * pL, rL)), cR = psqrt(qdiv(gamma * pR, rR));
-  const T abar = T(0.5) * (cL + cR), rbar = T(0.5) * (rL + rR);
-  const T ppvrs = T(0.5) * (pL + pR) - T(0.5) * (uR - uL) * rbar * abar;
-  const T ps = max(T(0), ppvrs);
+  const T rL = wL[0], uL = wL[1 + D], pL = wL[4];
+  const T rR = wR[0], uR = wR[1 + D], pR = wR[4];
+  const T cL = psqrt_div(gamma * pL, rL), cR = psqrt_div(gamma * pR, rR);
+  // p_pvrs = (pL + pR)/2 - (uR - uL) rbar abar / 2, rbar abar = (rL + rR)(cL + cR)/4
+  const T ppvrs =
+      T(0.5) * fma(T(-0.25) * (uR - uL), (rL + rR) * (cL + cR), pL + pR);
+  const T ps = pos_part(ppvrs);
   // shock branch: the argument exceeds 1
-  const T qL = ps <= pL ? T(1) : psqrt(T(1) + g1 * (qdiv(ps, pL) - T(1)));
-  const T qR = ps <= pR ? T(1) : psqrt(T(1) + g1 * (qdiv(ps, pR) - T(1)));
+  const T qL = nn_gt(ps, pL) ? psqrt_div(fma(g1, ps - pL, pL), pL) : T(1);
+  const T qR = nn_gt(ps, pR) ? psqrt_div(fma(g1, ps - pR, pR), pR) : T(1);
   const T SL = uL - cL * qL, SR = uR + cR * qR;
   const T mL = rL * (SL - uL), mR = rR * (SR - uR);
   const T Ss = qdiv(pR - pL + uL * mL - uR * mR, mL - mR);
-  // upwind side K of the star region (tie S* = 0 -> left)
-  const bool left = Ss >= T(0);
-  const T rK = left ? rL : rR, uK = left ? uL : uR, aK = left ? aL_ : aR_;
-  const T bK = left ? bL : bR, pK = left ? pL : pR, EK = left ? EL : ER;
+  const bool supL = is_ge0(SL), supR = !supL && is_le0(SR);
+  const bool left = supL || (!supR && is_ge0(Ss));
+  const T rK = left ? rL : rR, uK = left ? uL : uR, pK = left ? pL : pR;
+  const T aK = left ? wL[1 + A] : wR[1 + A], bK = left ? wL[1 + B] : wR[1 + B];
   const T SK = left ? SL : SR;
-  const T mK = rK * uK;
+  const T EK = pK * gm1inv + T(0.5) * rK * (uK * uK + (aK * aK + bK * bK));
   // physical fluxes of K
-  const T FK0 = mK, FKn = mK * uK + pK, FKa = mK * aK, FKb = mK * bK, FKe = uK * (EK + pK);
-  const T ratio = xdiv(SK - uK, SK - Ss);
+  const T mK = rK * uK;
+  const T FKn = mK * uK + pK, FKe = uK * (EK + pK);
+  // star-state fluxes of K
+  const T num = SK - uK, den = SK - Ss;
+  const T ratio = same_value(num, den) ? T(1) : qdiv(num, den);
   const T fac = rK * ratio;
-  const T Ue = ratio * (EK + rK * (Ss - uK) * (Ss + qdiv(pK, rK * (SK - uK))));
-  T Fs0 = FK0 + SK * (fac - rK);
-  T Fsn = FKn + SK * (fac * Ss - mK);
-  T Fsa = FKa + SK * (fac * aK - rK * aK);
-  T Fsb = FKb + SK * (fac * bK - rK * bK);
-  T Fse = FKe + SK * (Ue - EK);
-  // supersonic cases take the upwind physical flux
-  if (SL >= T(0)) {
-    const T m = rL * uL;
-    Fs0 = m; Fsn = m * uL + pL; Fsa = m * aL_; Fsb = m * bL; Fse = uL * (EL + pL);
-  } else if (SR <= T(0)) {
-    const T m = rR * uR;
-    Fs0 = m; Fsn = m * uR + pR; Fsa = m * aR_; Fsb = m * bR; Fse = uR * (ER + pR);
-  }
-  F[0] = Fs0;
-  F[1 + D] = Fsn;
-  F[1 + A] = Fsa;
-  F[1 + B] = Fsb;
-  F[4] = Fse;
+  const T Ue = ratio * (EK + rK * (Ss - uK) * (Ss + qdiv(pK, rK * num)));
+  const T Fs0 = mK + SK * (fac - rK);
+  const T Fsn = FKn + SK * (fac * Ss - mK);
+  const T Fse = FKe + SK * (Ue - EK);
+  const bool sup = supL || supR;
+  const T F0 = sup ? mK : Fs0;
+  F[0] = F0;
+  F[1 + D] = sup ? FKn : Fsn;
+  F[1 + A] = aK * F0;
+  F[1 + B] = bK * F0;
+  F[4] = sup ? FKe : Fse;
 }
 
 // Levermore (1984) closure coefficients of T = a I + b f f (so that the
