@@ -499,9 +499,14 @@ __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm
   const T ppvrs =
       T(0.5) * fma(T(-0.25) * (uR - uL), (rL + rR) * (cL + cR), pL + pR);
   const T ps = pos_part(ppvrs);
-  // shock branch: the argument exceeds 1
-  const T qL = nn_gt(ps, pL) ? psqrt_div(fma(g1, ps - pL, pL), pL) : T(1);
-  const T qR = nn_gt(ps, pR) ? psqrt_div(fma(g1, ps - pR, pR), pR) : T(1);
+  // shock branch (the argument exceeds 1): one square root for the first
+  // shocked side (left if both), the second only where both sides are
+  const bool shL = nn_gt(ps, pL), shR = nn_gt(ps, pR);
+  const T p1 = shL ? pL : pR;
+  const T q1 = psqrt_div(fma(g1, ps - p1, p1), p1);
+  const T qL = shL ? q1 : T(1);
+  T qR = shR ? q1 : T(1);
+  if (shL && shR) qR = psqrt_div(fma(g1, ps - pR, pR), pR);
   const T SL = uL - cL * qL, SR = uR + cR * qR;
   const T mL = rL * (SL - uL), mR = rR * (SR - uR);
   const T Ss = qdiv(pR - pL + uL * mL - uR * mR, mL - mR);
@@ -518,7 +523,8 @@ __device__ __forceinline__ void hllc(const T wL[5], const T wR[5], T gamma, T gm
   const T num = SK - uK, den = SK - Ss;
   const T ratio = same_value(num, den) ? T(1) : qdiv(num, den);
   const T fac = rK * ratio;
-  const T Ue = ratio * (EK + rK * (Ss - uK) * (Ss + qdiv(pK, rK * num)));
+  // E*_K = ratio (E_K + (S* - u_K)(rho_K S* + p_K / (S_K - u_K)))
+  const T Ue = ratio * fma(Ss - uK, fma(rK, Ss, qdiv(pK, num)), EK);
   const T Fs0 = mK + SK * (fac - rK);
   const T Fsn = FKn + SK * (fac * Ss - mK);
   const T Fse = FKe + SK * (Ue - EK);

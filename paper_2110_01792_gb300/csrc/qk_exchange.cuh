@@ -16,10 +16,15 @@ __device__ __forceinline__ bool abs_below(double x, double t) {
   return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < __double_as_longlong(t);
 }
 __device__ __forceinline__ bool abs_below(float x, float t) { return fabsf(x) < t; }
-// x > 0 and finite, on the integer pipe.
+// x > 0 and finite, on the integer pipe; floats by FP32 compares.
 __device__ __forceinline__ bool pos_finite(double x) {
   const long long b = __double_as_longlong(x);
   return b > 0 && b < 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool pos_finite(float x) { return x > 0.0f && x <= 3.402823466e38f; }
+// a positive normal float
+__device__ __forceinline__ bool pos_normal(float x) {
+  return x >= 1.175494351e-38f && x <= 3.402823466e38f;
 }
 
 // Newton-Raphson on (E_g, E_r) for one cell (Sec. 2.2.3, eqs. delta_er and
@@ -254,22 +259,37 @@ __device__ __forceinline__ void exchange_cell(const qk_params &p, const ExK &K, 
   // same root (the last correction is applied, so the result is accurate far
   // below the tolerance whichever start is taken); a failed FP32 solve leaves
   // the start at the cell state.
+  // Where the FP32 solve succeeded and its coefficients and the thresholds
+  // are normal floats, the FP64 iteration is newton_refine: FP64 residuals
+  // and convergence test (the same equations and tolerance), the 2x2
+  // correction from the FP32 Jacobian (a Jacobian accurate to ~1e-7 still
+  // gains ~7 digits per step, so the two steps from the warm start remain);
+  // otherwise, or if that does not converge, the full FP64 Newton iteration.
+  const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
   double Eg = Eg0, Er = Er0;
+  int it = -1;
   {
-    const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
     const float Ef0 = d2f_trunc(Eg0), Rf0 = d2f_trunc(Er0S);
     const float Af = d2f_trunc(A), kf = d2f_trunc(k), tf = d2f_trunc(thr_g);
     float Egf = Ef0, Erf = Rf0;
     const int itf = newton_exchange<float>(alpha_eos, Af, kf, K.crf, Ef0, Rf0, 1e4f * tf,
                                            1e4f * tf * K.rc, 12, Egf, Erf);
-    if (itf > 0 && Egf > 0.0f && Erf > 0.0f && isfinite(Egf) && isfinite(Erf)) {
+    const bool warm = itf > 0 && pos_finite(Egf) && pos_finite(Erf);
+    if (warm) {
       Eg = f2d(Egf);
       Er = f2d(Erf);
     }
+    const float trf = d2f_trunc(thr_r);
+    if (warm && pos_normal(Af) && pos_normal(kf) && pos_normal(tf) && pos_normal(trf))
+      it = newton_refine(alpha_eos, p.max_iter, A, k, K.cr, Eg0, Er0S, Af, kf, K.crf, tf, trf,
+                         Eg, Er);
   }
-  int it;
-  it = newton_exchange<double>(p.eos == QK_EOS_ALPHA_T3, A, k, K.cr, Eg0, Er0S, thr_g, thr_r,
-                               p.max_iter, Eg, Er);
+  if (it < 0) {
+    Eg = Eg0;
+    Er = Er0;
+    it = newton_exchange<double>(alpha_eos, A, k, K.cr, Eg0, Er0S, thr_g, thr_r, p.max_iter, Eg,
+                                 Er);
+  }
   if (it < 0) {
     xs.flags |= 1u << QK_ENOCONV;
     xs.bad = min(xs.bad, (unsigned long long)e);
@@ -316,7 +336,6 @@ __device__ __forceinline__ void exchange_cell(const qk_params &p, const ExK &K, 
 // the double-float difference of the same two values) and stored hi + lo,
 // and the momentum exchange m + F/(c chat) = const is carried in double-float
 // with a double-float 1/(c chat), so that both invariants hold to ~2^-47.
-__device__ __forceinline__ bool pos_finite(float x) { return x > 0.0f && x <= 3.402823466e38f; }
 __device__ __forceinline__ DF df_of_double(double x) {
   const float h = (float)x;
   return DF{h, (float)(x - (double)h)};

@@ -68,28 +68,29 @@ __device__ __forceinline__ void load_slot(RadSmem<T> &sm, int s, const T u[4], T
   }
 }
 
-// State vector (E, F) and half the flux along D of a radiation state (E_r, f)
-// with |f|^2 = f2 already known: flux_D = ((chat/c) F_D, c chat E T_xD,
-// c chat E T_yD, c chat E T_zD) (eqs. rad_energy, rad_flux; T from the
-// closure CL), scaled by 1/2 through the constants hchat_c = chat/(2c) and
-// hccc = c chat / 2 (the HLL average of two states then needs no multiply).
+// E_r, E_r f (the state vector (E, F) with F = c E_r f, the factor c left to
+// the caller) and half the flux along D of a radiation state (E_r, f) with
+// |f|^2 = f2 already known: flux_D = ((chat/c) F_D, c chat E T_xD,
+// c chat E T_yD, c chat E T_zD) (eqs. rad_energy, rad_flux; T = a I + b f f
+// from the closure CL), scaled by 1/2 through the constants hchat = chat/2
+// and hccc = c chat / 2 (the HLL average of two states then needs no
+// multiply).
 template <typename T, int D, int CL>
-__device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T f2, T c, T hchat_c,
-                                            T hccc, T U[4], T F[4]) {
+__device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T f2, T hchat, T hccc,
+                                            T U[4], T F[4]) {
   T a, b;
   closure_ab_f2<T, CL>(f2, a, b);
   const T fD = D == 0 ? fx : (D == 1 ? fy : fz);
-  const T cE = c * E;
   U[0] = E;
-  U[1] = cE * fx;
-  U[2] = cE * fy;
-  U[3] = cE * fz;
-  F[0] = hchat_c * U[1 + D];
-  const T cEb = hccc * E;                // c chat E / 2
-  const T bfD = b * fD;
-  F[1] = cEb * (bfD * fx + (D == 0 ? a : T(0)));
-  F[2] = cEb * (bfD * fy + (D == 1 ? a : T(0)));
-  F[3] = cEb * (bfD * fz + (D == 2 ? a : T(0)));
+  U[1] = E * fx;
+  U[2] = E * fy;
+  U[3] = E * fz;
+  F[0] = hchat * U[1 + D];
+  const T cEb = hccc * E;  // c chat E / 2
+  const T g = cEb * (b * fD);
+  F[1] = D == 0 ? fma(g, fx, cEb * a) : g * fx;
+  F[2] = D == 1 ? fma(g, fy, cEb * a) : g * fy;
+  F[3] = D == 2 ? fma(g, fz, cEb * a) : g * fz;
 }
 
 // HLL wavespeed from the diagonal Eddington-tensor elements T_DD of the two
@@ -122,21 +123,28 @@ __device__ __forceinline__ void rad_face_hll(T wL[4], T wR[4], Fallback fallback
     fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
   }
   T UL[4], FL[4], UR[4], FR[4];
-  rad_flux_of<T, D, CL>(wL[0], wL[1], wL[2], wL[3], fL2, c, hchat_c, hccc, UL, FL);
-  rad_flux_of<T, D, CL>(wR[0], wR[1], wR[2], wR[3], fR2, c, hchat_c, hccc, UR, FR);
+  const T hchat = hchat_c * c;
+  rad_flux_of<T, D, CL>(wL[0], wL[1], wL[2], wL[3], fL2, hchat, hccc, UL, FL);
+  rad_flux_of<T, D, CL>(wR[0], wR[1], wR[2], wR[3], fR2, hchat, hccc, UR, FR);
   T eps = T(1);
   if (tau_corr) {
     const T tau = dx * T(0.5) * (rka + rkb);
     if (nn_gt(tau, T(1))) eps = qrcp(tau);
   }
-  // HLL with S_L = -S, S_R = S: (F_L + F_R)/2 - (S eps / 2)(U_R - U_L)
+  // HLL with S_L = -S, S_R = S: (F_L + F_R)/2 - (S eps / 2)(U_R - U_L), the
+  // flux components of U carrying their factor c in the coefficient
   const T hS = T(0.5) * S;
-  const T hSe = hS * eps;
+  T hSe = hS * eps;
+  T hSec = hSe * c;
+  out[0] = (FL[0] + FR[0]) - hSe * (UR[0] - UL[0]);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hSe * (UR[q] - UL[q]);
+  for (int q = 1; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hSec * (UR[q] - UL[q]);
   if (nn_gt(T(1), eps) && nn_gt(fabs(out[0]), chat * nn_max(UL[0], UR[0]))) {
+    hSe = hS;
+    hSec = hS * c;
+    out[0] = (FL[0] + FR[0]) - hSe * (UR[0] - UL[0]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hS * (UR[q] - UL[q]);
+    for (int q = 1; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hSec * (UR[q] - UL[q]);
   }
 }
 
