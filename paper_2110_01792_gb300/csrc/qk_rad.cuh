@@ -68,31 +68,6 @@ __device__ __forceinline__ void load_slot(RadSmem<T> &sm, int s, const T u[4], T
   }
 }
 
-// E_r, E_r f (the state vector (E, F) with F = c E_r f, the factor c left to
-// the caller) and half the flux along D of a radiation state (E_r, f) with
-// |f|^2 = f2 already known: flux_D = ((chat/c) F_D, c chat E T_xD,
-// c chat E T_yD, c chat E T_zD) (eqs. rad_energy, rad_flux; T = a I + b f f
-// from the closure CL), scaled by 1/2 through the constants hchat = chat/2
-// and hccc = c chat / 2 (the HLL average of two states then needs no
-// multiply).
-template <typename T, int D, int CL>
-__device__ __forceinline__ void rad_flux_of(T E, T fx, T fy, T fz, T f2, T hchat, T hccc,
-                                            T U[4], T F[4]) {
-  T a, b;
-  closure_ab_f2<T, CL>(f2, a, b);
-  const T fD = D == 0 ? fx : (D == 1 ? fy : fz);
-  U[0] = E;
-  U[1] = E * fx;
-  U[2] = E * fy;
-  U[3] = E * fz;
-  F[0] = hchat * U[1 + D];
-  const T cEb = hccc * E;  // c chat E / 2
-  const T g = cEb * (b * fD);
-  F[1] = D == 0 ? fma(g, fx, cEb * a) : g * fx;
-  F[2] = D == 1 ? fma(g, fy, cEb * a) : g * fy;
-  F[3] = D == 2 ? fma(g, fz, cEb * a) : g * fz;
-}
-
 // HLL wavespeed from the diagonal Eddington-tensor elements T_DD of the two
 // cell averages (Sec. 2.2.2): S = chat sqrt(max(Ta, Tb)), equal to chat
 // max(sqrt(Ta), sqrt(Tb)) since the square root is monotone (within an ulp:
@@ -111,10 +86,20 @@ __device__ __forceinline__ T rad_speed(T Ta, T Tb, T chat) {
 // correction switched off where it would make the energy flux exceed
 // chat max(E_L, E_R).  Shared by the stage kernel and the flux registers of
 // mesh refinement, so both use the same arithmetic.
+//
+// With flux_D = ((chat/c) F_D, c chat E T_qD) (eqs. rad_energy, rad_flux),
+// F = c E f and T = a I + b f f (closure CL), the HLL flux
+// (flux_L + flux_R)/2 - (S eps/2)(U_R - U_L) is evaluated as
+//   energy: (chat/2)(E_L f_L,D + E_R f_R,D) - (S eps/2)(E_R - E_L),
+//   F_q:    al_L f_L,q + al_R f_R,q (+ (c chat/2)(E_L a_L + E_R a_R) for q = D),
+// al_L = (c chat/2) E_L b_L f_L,D + (S eps c/2) E_L and
+// al_R = (c chat/2) E_R b_R f_R,D - (S eps c/2) E_R: the terms of each side
+// that multiply the same f_q are gathered before the product.
 template <typename T, int D, int CL, class Fallback>
 __device__ __forceinline__ void rad_face_hll(T wL[4], T wR[4], Fallback fallback, T S, T rka,
                                              T rkb, T dx, T c, T chat, T hchat_c, T hccc,
                                              int tau_corr, T out[4]) {
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
   T fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
   T fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
   if (nn_gt(fL2, T(1)) || nn_gt(fR2, T(1))) {
@@ -122,30 +107,32 @@ __device__ __forceinline__ void rad_face_hll(T wL[4], T wR[4], Fallback fallback
     fL2 = (wL[1] * wL[1] + wL[2] * wL[2]) + wL[3] * wL[3];
     fR2 = (wR[1] * wR[1] + wR[2] * wR[2]) + wR[3] * wR[3];
   }
-  T UL[4], FL[4], UR[4], FR[4];
-  const T hchat = hchat_c * c;
-  rad_flux_of<T, D, CL>(wL[0], wL[1], wL[2], wL[3], fL2, hchat, hccc, UL, FL);
-  rad_flux_of<T, D, CL>(wR[0], wR[1], wR[2], wR[3], fR2, hchat, hccc, UR, FR);
+  T aL, bL, aR, bR;
+  closure_ab_f2<T, CL>(fL2, aL, bL);
+  closure_ab_f2<T, CL>(fR2, aR, bR);
+  const T EL = wL[0], ER = wR[0], fLD = wL[1 + D], fRD = wR[1 + D];
   T eps = T(1);
   if (tau_corr) {
     const T tau = dx * T(0.5) * (rka + rkb);
     if (nn_gt(tau, T(1))) eps = qrcp(tau);
   }
-  // HLL with S_L = -S, S_R = S: (F_L + F_R)/2 - (S eps / 2)(U_R - U_L), the
-  // flux components of U carrying their factor c in the coefficient
   const T hS = T(0.5) * S;
   T hSe = hS * eps;
-  T hSec = hSe * c;
-  out[0] = (FL[0] + FR[0]) - hSe * (UR[0] - UL[0]);
-#pragma unroll
-  for (int q = 1; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hSec * (UR[q] - UL[q]);
-  if (nn_gt(T(1), eps) && nn_gt(fabs(out[0]), chat * nn_max(UL[0], UR[0]))) {
+  const T FE = (hchat_c * c) * fma(EL, fLD, ER * fRD);
+  const T dE = ER - EL;
+  T o0 = fma(-hSe, dE, FE);
+  if (nn_gt(T(1), eps) && nn_gt(fabs(o0), chat * nn_max(EL, ER))) {
     hSe = hS;
-    hSec = hS * c;
-    out[0] = (FL[0] + FR[0]) - hSe * (UR[0] - UL[0]);
-#pragma unroll
-    for (int q = 1; q < 4; ++q) out[q] = (FL[q] + FR[q]) - hSec * (UR[q] - UL[q]);
+    o0 = fma(-hSe, dE, FE);
   }
+  out[0] = o0;
+  const T hSec = hSe * c;
+  const T cEbL = hccc * EL, cEbR = hccc * ER;
+  const T alL = fma(cEbL * bL, fLD, hSec * EL);
+  const T alR = fma(cEbR * bR, fRD, -(hSec * ER));
+  out[1 + A] = fma(alL, wL[1 + A], alR * wR[1 + A]);
+  out[1 + B] = fma(alL, wL[1 + B], alR * wR[1 + B]);
+  out[1 + D] = fma(alL, fLD, fma(alR, fRD, fma(cEbL, aL, cEbR * aR)));
 }
 
 template <typename T, int D, int NT, int NOWN, int CL, bool CP>
