@@ -458,7 +458,7 @@ static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, in
     int nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long long slots = (long long)std::max(nsm, 1) * (c->fp32 ? 3 : 2);
+    const long long slots = (long long)std::max(nsm, 1) * (c->fp32 ? COL_CTAS_FP32 : COL_CTAS_FP64);
     int max_nz = 1;
     for (int l = 0; l < nown; ++l) max_nz = std::max(max_nz, (int)boxes[c->own[l]].n[2]);
     int best_cz = max_nz;

@@ -46,10 +46,9 @@ __device__ __forceinline__ void load_prim(const F5<T> &U, long long e, T gm1, T 
   con2prim<T>(u, gm1, w);
 }
 
-// Resident CTAs per SM the registers are held to (FP32: three, as many as
-// fit beside each other's shared memory; FP64: two).
+// Resident CTAs per SM the registers are held to (COL_CTAS_*).
 template <typename T> struct ColMinBlocks {
-  static constexpr int value = sizeof(T) == 4 ? 3 : 2;
+  static constexpr int value = sizeof(T) == 4 ? COL_CTAS_FP32 : COL_CTAS_FP64;
 };
 
 template <typename T, int STAGE>

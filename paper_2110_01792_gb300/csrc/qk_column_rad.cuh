@@ -41,7 +41,7 @@ __device__ __forceinline__ void rad_prim(const T u[4], T c, T r, const SC<T> &K,
 }
 
 template <typename T> struct ColMinBlocksRad {
-  static constexpr int value = sizeof(T) == 4 ? 3 : 2;
+  static constexpr int value = sizeof(T) == 4 ? COL_CTAS_FP32 : COL_CTAS_FP64;
 };
 
 template <typename T, int STAGE, int CL, bool EX>

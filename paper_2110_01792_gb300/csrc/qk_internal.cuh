@@ -44,6 +44,10 @@ constexpr int CNPL = CPW * CPW;        // plane slots
 constexpr int CXPOS = CW + 2;          // reconstruction positions per row (cells -1..CW)
 constexpr int CXFACE = CW + 1;         // faces per row
 constexpr int CNT = CW * CW;           // threads per column CTA
+// resident column CTAs per SM the kernels' registers are held to (FP32:
+// three, as many as fit beside each other's shared memory; FP64: two), also
+// the slots of the host's z-chunk cost model
+constexpr int COL_CTAS_FP32 = 3, COL_CTAS_FP64 = 2;
 constexpr int CNRING = 4 * HALO * CW;  // ring cells of a plane (x and y sides)
 
 struct Column {
