@@ -179,6 +179,25 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Binary exponent and mantissa of a positive normal float (x = fmant(x)
+// 2^fexpo(x), fmant in [1, 2)), 2^ex for |ex| <= 126, and m 2^ex for a
+// positive normal m (0 below the normal range, infinity above it), on the
+// integer pipe.
+__device__ __forceinline__ int fexpo(float x) {
+  return (int)((__float_as_uint(x) >> 23) & 0xffu) - 127;
+}
+__device__ __forceinline__ float fmant(float x) {
+  return __uint_as_float((__float_as_uint(x) & 0x007fffffu) | 0x3f800000u);
+}
+__device__ __forceinline__ float pow2f(int ex) { return __uint_as_float((unsigned)(ex + 127) << 23); }
+__device__ __forceinline__ float fscale(float m, int ex) {
+  const unsigned u = __float_as_uint(m);
+  const int be = (int)((u >> 23) & 0xffu) + ex;
+  if (be <= 0) return 0.0f;
+  if (be >= 255) return __uint_as_float(0x7f800000u);
+  return __uint_as_float((u & 0x807fffffu) | ((unsigned)be << 23));
+}
+
 // Double-float values (h + l, |l| <= ulp(h)/2, ~48 significant bits) for
 // arithmetic that needs more than FP32 without the FP64 pipe (Dekker 1971;
 // Knuth's TwoSum; FMA TwoProduct), on round-to-nearest intrinsics so that no

@@ -189,6 +189,8 @@ struct ExK {
   float crf, a_ef, inv_cvf, kchat;  // kchat: kappa_P chat (or kappa0 chat)
   float kRf, chatf, epsf;          // kappa_R (or kappa0), chat, the Newton tolerance
   DF cr_df, rc_df;                 // c/chat and chat/c as double-float
+  float a_m, cv_m;                 // a_e = a_m 2^a_e2, 1/c_v = cv_m 2^cv_e, mantissas in [1, 2)
+  int a_e2, cv_e;
 };
 __host__ __device__ __forceinline__ ExK make_exk(const qk_params &p) {
   ExK K;
@@ -211,6 +213,13 @@ __host__ __device__ __forceinline__ ExK make_exk(const qk_params &p) {
   K.cr_df.l = (float)(K.cr - (double)K.cr_df.h);
   K.rc_df.h = (float)K.rc_d;
   K.rc_df.l = (float)(K.rc_d - (double)K.rc_df.h);
+  int ex = 0;
+  double m = frexp(K.a_e, &ex);  // m in [0.5, 1)
+  K.a_m = (float)(2.0 * m);
+  K.a_e2 = ex - 1;
+  m = frexp(K.inv_cv, &ex);
+  K.cv_m = (float)(2.0 * m);
+  K.cv_e = ex - 1;
   return K;
 }
 
@@ -327,7 +336,8 @@ __device__ __forceinline__ void exchange_cell(const qk_params &p, const ExK &K, 
 // transforms of con2prim; the Newton solve on the FP32 coefficients A, k with
 // ~48-bit residuals: an FP32 warm start, then newton_refine_df in
 // double-float where its rounding (~2^-43 (1 + k c/chat) E_tot) stays below
-// the tolerance eps E_tot, else newton_refine in FP64; the flux source and
+// the tolerance eps E_tot, else newton_refine in FP64, both on the energies
+// scaled by a power of two to O(1); the flux source and
 // the momentum and kinetic-energy work in FP32, the new total energy and
 // radiation energy formed in double-float before the final rounding.
 // CP: compensated state (every conserved field hi + lo; UL, RL the lo
@@ -365,40 +375,57 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
     Eg0 = df_add_f(Eg0, E_lo);
     Er0 = df_of(er, er_lo);
   }
-  // the coefficients in FP32: k = dt rho kappa_P chat, A = k a_r/(rho c_v)^4
-  // (or 4 k a_r/alpha), and the convergence thresholds eps E_tot,
-  // eps E_tot chat/c (E_tot = E_g0 + (c/chat) E_r0)
+  // The solve runs on the energies divided by 2^eE (exact), eE the binary
+  // exponent of E_tot = E_g0 + (c/chat) E_r0, so that its FP32 and
+  // double-float numbers are O(1) in any units (in cgs E_g^4 would overflow
+  // FP32): with E = E' 2^eE the equations keep their form with k unchanged and
+  // A' = A 2^(3 eE) (A for the alpha T^3 heat capacity, where R is linear in
+  // E_g).  Coefficients in FP32: k = dt rho kappa_P chat and
+  // A' = k a_r (rho c_v)^-4 2^(3 eE) as a product of mantissas and a sum of
+  // exponents (the factors alone may leave the FP32 range); the thresholds
+  // eps E_tot', eps E_tot' chat/c.  (Scaling every cell, rather than only
+  // those outside the FP32 range, measured faster: no divergent branch.)
   const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
   const float kf = dtf * K.kchat * (p.kappa_mode == QK_KAPPA_RHO ? rho * rho : rho);
-  float Af = kf * K.a_ef;
-  if (!alpha_eos) {
-    const float i1 = rinv * K.inv_cvf, i2 = i1 * i1;
-    Af *= i2 * i2;
+  const float Etot_u = Eg0.h + K.crf * Er0.h;
+  const int eE = pos_normal(Etot_u) ? min(max(fexpo(Etot_u), -100), 100) : 0;
+  const float sc = pow2f(-eE), isc = pow2f(eE);
+  float Af;
+  if (alpha_eos) {
+    Af = kf * K.a_ef;
+  } else {
+    const float mq = fmant(rinv) * K.cv_m, mq2 = mq * mq;  // (rho c_v)^-1 = mq 2^eq
+    const int eq = fexpo(rinv) + K.cv_e;
+    Af = fscale(kf * K.a_m * (mq2 * mq2), K.a_e2 + 4 * eq + 3 * eE);
   }
-  const float Etotf = Eg0.h + K.crf * Er0.h;
+  const DF Eg0s{Eg0.h * sc, Eg0.l * sc};
+  const DF Er0s{Er0.h * sc, Er0.l * sc};
+  const float Etotf = Etot_u * sc;
   const float thr_g = K.epsf * Etotf, thr_r = thr_g * K.rc;
   // radiation source S = dt (chat/c) j, carried in the residual's E_r0
-  const DF Er0S = src ? df_add_f(Er0, (dtf * K.rc) * src[e]) : Er0;
+  const DF Er0S = src ? df_add_f(Er0s, ((dtf * K.rc) * src[e]) * sc) : Er0s;
   // FP32 warm start to 1e-6
-  float Egf = Eg0.h, Erf = Er0S.h;
-  const int itf = newton_exchange<float>(alpha_eos, Af, kf, K.crf, Eg0.h, Erf, 1e-6f * Etotf,
+  float Egf = Eg0s.h, Erf = Er0S.h;
+  const int itf = newton_exchange<float>(alpha_eos, Af, kf, K.crf, Eg0s.h, Erf, 1e-6f * Etotf,
                                          1e-6f * Etotf * K.rc, 12, Egf, Erf);
-  DF Eg = Eg0, Er = Er0S;
+  DF Eg = Eg0s, Er = Er0S;
   if (itf > 0 && pos_finite(Egf) && pos_finite(Erf)) {
     Eg = DF{Egf, 0.0f};
     Er = DF{Erf, 0.0f};
   }
   int it;
   if ((1.0f + kf * K.crf) * 0x1p-43f < K.epsf) {  // false for a NaN k
-    it = newton_refine_df(alpha_eos, p.max_iter, Af, kf, K.cr_df, K.crf, Eg0, Er0S, thr_g, thr_r,
+    it = newton_refine_df(alpha_eos, p.max_iter, Af, kf, K.cr_df, K.crf, Eg0s, Er0S, thr_g, thr_r,
                           Eg, Er);
   } else {
     double Egd = f2d(Eg.h), Erd = f2d(Er.h);
-    it = newton_refine(alpha_eos, p.max_iter, f2d(Af), f2d(kf), K.cr, f2d(Eg0.h) + f2d(Eg0.l),
+    it = newton_refine(alpha_eos, p.max_iter, f2d(Af), f2d(kf), K.cr, f2d(Eg0s.h) + f2d(Eg0s.l),
                        f2d(Er0S.h) + f2d(Er0S.l), Af, kf, K.crf, thr_g, thr_r, Egd, Erd);
     Eg = df_of_double(Egd);
     Er = df_of_double(Erd);
   }
+  Eg = DF{Eg.h * isc, Eg.l * isc};
+  Er = DF{Er.h * isc, Er.l * isc};
   if (it < 0) {
     xs.flags |= 1u << QK_ENOCONV;
     xs.bad = min(xs.bad, (unsigned long long)e);

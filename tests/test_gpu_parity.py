@@ -329,6 +329,66 @@ def test_exchange_matches_oracle(torch_cuda, kappa0):
     assert max(e) <= TOL_STAGE, e
 
 
+def _cgs_state(lay, seed):
+    """The random RHD state rescaled to cgs magnitudes (rho ~ 1e-2 g/cm^3,
+    T ~ 1e7 K, c_v = 1.24e8, a_r = 7.56e-15, c = 3e10 cm/s, chat = 10 c_s:
+    E_g ~ 1e13 and E_r ~ 1e14 erg/cm^3), with its parameters."""
+    prob, prm = _random_rhd(lay, seed)
+    gamma, c_v, T0, a_r, c = prm["gamma"], 1.24e8, 1e7, 7.56e-15, 3e10
+    cs0 = math.sqrt(gamma * (gamma - 1.0) * c_v * T0)
+    U = [a.copy() for a in prob.U]
+    R = [a.copy() for a in prob.R]
+    for b in range(lay.nbox):
+        rho = lay.interior(prob.U[0], b)
+        v = [lay.interior(prob.U[1 + d], b) / rho for d in range(3)]
+        Er = lay.interior(prob.R[0], b)
+        f = [lay.interior(prob.R[1 + d], b) / (prm["c"] * Er) for d in range(3)]
+        rho2 = 1e-2 * rho
+        v2 = [cs0 * x for x in v]
+        lay.interior(U[0], b)[...] = rho2
+        for d in range(3):
+            lay.interior(U[1 + d], b)[...] = rho2 * v2[d]
+        lay.interior(U[4], b)[...] = rho2 * c_v * T0 + 0.5 * rho2 * sum(x * x for x in v2)
+        Er2 = a_r * T0 ** 4 * Er  # E_r = T_r^4 in the code-unit state
+        lay.interior(R[0], b)[...] = Er2
+        for d in range(3):
+            lay.interior(R[1 + d], b)[...] = c * Er2 * f[d]
+    prm = dict(prm, c_v=c_v, a_r=a_r, c=c, chat=10.0 * cs0, kappa_P=1.0, kappa_R=1.0,
+               kappa_mode=0)
+    return U, R, prm
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_exchange_cgs_scales_matches_oracle(torch_cuda, prec):
+    """The exchange on cgs-scaled states: E_g^4 overflows FP32 and
+    A = k a_r/(rho c_v)^4 is not a normal float, so the FP32 warm start, the
+    FP32-Jacobian and the double-float refinements stand aside and the full
+    FP64 Newton iteration runs.  FP64 agrees with the oracle to 1e-12 per
+    cell; FP32-mixed (FP32 state, oracle on the same rounded inputs) to the
+    FP32 storage (4e-6) with no failure status."""
+    torch = torch_cuda
+    lay = RAGGED
+    U, R, prm = _cgs_state(lay, 8)
+    if prec == 1:
+        U = [a.astype(np.float32).astype(np.float64) for a in U]
+        R = [a.astype(np.float32).astype(np.float64) for a in R]
+    dtr = 0.3 * (1.0 / 19) / prm["chat"]
+    Ur = [a.copy() for a in U]
+    Rr = [a.copy() for a in R]
+    rc, info = O.exchange(_grid(lay), O.make_params(**prm), Ur, Rr, dtr)
+    assert rc == 0
+    ctx = _ctx(lay, prm, prec)
+    tdt = torch.float64 if prec == 0 else torch.float32
+    dU, dR = G.dev(U, tdt), G.dev(R, tdt)
+    ctx.exchange(dU, dR, dtr)
+    torch.cuda.synchronize()
+    rc, flags, bad, maxit = ctx.status()
+    ctx.close()
+    assert rc == 0 and flags == 0 and bad == -1 and 1 <= maxit <= info[2] + 1, (maxit, info)
+    e = G.max_rel_err(lay, G.host(dU) + G.host(dR), Ur + Rr)
+    assert max(e) <= (TOL_STAGE if prec == 0 else 4e-6), e
+
+
 @pytest.mark.parametrize("kappa_mode", [0, 1], ids=["kconst", "krho"])
 def test_mixed_exchange_matches_oracle(torch_cuda, kappa_mode):
     """FP32-mixed exchange against the FP64 oracle on the same FP32-rounded
