@@ -267,10 +267,12 @@ def time_kernel(torch, fn, reps, stream):
 # (profiles/ncu_*_128.md), valid only while the kernel's sources hash to the
 # value recorded at capture time.
 NCU_TRAFFIC = {
-    ("rhd128", "rad_stage_ex_kernel<double>"): (343.16e6, "rad", "36644bed4b8c"),
-    ("rhd128", "rad_column_kernel<float,2,EX>"): (165.34e6, "radcol", "3e27ab1294bf"),
-    ("rhd128", "rad_column_kernel<float,1>"): (54.70e6, "radcol", "3e27ab1294bf"),
-    ("rhd128", "hydro_column_kernel<float,1>"): (59.63e6, "hydrocol", "ab1a8b3a89bd"),
+    ("rhd128", "rad_stage_ex_kernel<double>"): (342.76e6, "rad", "8d7d55bb2947"),
+    ("rhd128", "rad_stage_kernel<double,1>"): (135.02e6, "rad", "8d7d55bb2947"),
+    ("rhd128", "hydro_stage_kernel<double,1>"): (150.91e6, "hydro", "89f91359c44a"),
+    ("rhd128", "rad_column_kernel<float,2,EX>"): (164.92e6, "radcol", "715cee76a212"),
+    ("rhd128", "rad_column_kernel<float,1>"): (54.69e6, "radcol", "715cee76a212"),
+    ("rhd128", "hydro_column_kernel<float,1>"): (58.73e6, "hydrocol", "f2e0909c7b7a"),
 }
 
 
