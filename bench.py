@@ -550,19 +550,20 @@ def run_ours(args):
 
     # ---- end to end through the public API with a host-resident state ----
     # the state lives in pinned host memory (from the start of the timed
-    # steps); every step copies it to the device, runs qk_step, and copies
-    # the updated state back (in place)
-    dfields = U + (R or [])
+    # steps); every step is one qk_step_host call, which copies it to the
+    # device, runs the update and copies it back (in place)
     h2d = sum(h.numel() * h.element_size() for h in host)
     d2h = h2d
+    hU, hR = host[:5], (host[5:] if R is not None else None)
 
     def e2e_step():
-        for d, h in zip(dfields, host):
-            d.copy_(h, non_blocking=True)
-        ctx.step(U, R)
-        for h, d in zip(host, dfields):
-            h.copy_(d, non_blocking=True)
+        ctx.step_host(hU, hR, stream=stream.cuda_stream)
 
+    snap = [h.clone() for h in host]
+    e2e_step()  # allocates the context's device copy of the state
+    for h, h0 in zip(host, snap):
+        h.copy_(h0)  # back to the start of the timed steps
+    del snap
     torch.cuda.synchronize()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)

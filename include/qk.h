@@ -532,6 +532,21 @@ int qk_eval_math(const double *x, int64_t n, double *rcp, double *sqrt_out, void
 int qk_eval_convert(const float *f_in, double *d_out, const double *d_in, float *f_out, int64_t n,
                     void *stream);
 
+/* qk_step on a state held in host memory (the end-to-end form of the
+ * update): copies the 5 hydro (and 4 radiation) fields of all patches,
+ * field_len elements each in the context's precision, from the caller's host
+ * arrays (pinned or pageable; pinned ones move by DMA at full rate) into
+ * device copies owned by the context (allocated on the first call), runs
+ * qk_step on them and copies the updated fields back into the same host
+ * arrays.  The copies are spread over three internal streams (one field per
+ * copy engine at a time) and ordered after the work already on `stream`;
+ * the call returns when the host arrays hold the result.  dt_out and
+ * nsub_out as in qk_step (dt_out must then be host memory that stays valid
+ * until the call returns).  QK_EINVAL for a NULL field; QK_ECUDA if an
+ * allocation, copy or launch fails. */
+int qk_step_host(qk_ctx *ctx, void *const hydro[5], void *const rad[4], double *dt_out,
+                 int32_t *nsub_out, void *stream);
+
 /* FMA throughput probe (not part of the method): the ALU peak against which
  * the stage kernels' arithmetic is measured.  Launches min(8 x SMs,
  * sink_len / 256) blocks of 256 threads; each thread runs 8 independent

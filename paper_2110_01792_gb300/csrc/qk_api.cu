@@ -361,6 +361,11 @@ static void release(qk_ctx *c) {
   for (void *s : c->scratch) cudaFree(s);
   cudaFree(c->chi);
   if (c->h_buf) cudaFreeHost(c->h_buf);
+  for (void *h : c->hstate) cudaFree(h);
+  for (cudaStream_t h : c->hcopy)
+    if (h) cudaStreamDestroy(h);
+  for (cudaEvent_t e : c->hcopy_ev)
+    if (e) cudaEventDestroy(e);
 }
 
 // Forget the captured step graphs (parameters, launch configurations or
@@ -1249,6 +1254,87 @@ int qk_step(qk_ctx *c, void *const hydro[5], void *const rad[4], double *dt_out,
     QK_CUDA(c, cudaStreamSynchronize(s));
     *nsub_out = (int32_t)c->h_buf[8];
   }
+  return QK_OK;
+}
+
+// Copies of `nf` whole fields between the caller's arrays and the context's
+// device copies.  Pinned, 16-byte aligned host arrays (all of them) are copied
+// by the SMs through their device mapping, on `s`, in one launch per
+// direction; otherwise one cudaMemcpyAsync per field, spread over the copy
+// streams (field q on stream q mod 3) and ordered after the work already on
+// `s`, which waits for all of them.
+static int host_copies(qk_ctx *c, void *const *host, int nf, bool to_device, cudaStream_t s) {
+  const size_t bytes = (size_t)c->field_len * c->elem;
+  FieldCopies fc{};
+  bool mapped = true;
+  for (int q = 0; q < nf && mapped; ++q) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host[q]) != cudaSuccess) {
+      cudaGetLastError();  // clear: an unknown pointer is pageable memory
+      mapped = false;
+      break;
+    }
+    void *dp = a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+    if (!dp || ((uintptr_t)dp & 15) != 0) {
+      mapped = false;
+      break;
+    }
+    fc.src[q] = to_device ? (const void *)dp : (const void *)c->hstate[q];
+    fc.dst[q] = to_device ? c->hstate[q] : dp;
+  }
+  if (mapped) {
+    QK_CUDA(c, launch_field_copies(fc, nf, bytes, s));
+    return QK_OK;
+  }
+  QK_CUDA(c, cudaEventRecord(c->hcopy_ev[3], s));
+  for (int i = 0; i < 3; ++i) QK_CUDA(c, cudaStreamWaitEvent(c->hcopy[i], c->hcopy_ev[3], 0));
+  for (int q = 0; q < nf; ++q) {
+    void *dst = to_device ? c->hstate[q] : host[q];
+    const void *src = to_device ? (const void *)host[q] : (const void *)c->hstate[q];
+    QK_CUDA(c, cudaMemcpyAsync(dst, src, bytes,
+                               to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost,
+                               c->hcopy[q % 3]));
+  }
+  for (int i = 0; i < 3; ++i) {
+    QK_CUDA(c, cudaEventRecord(c->hcopy_ev[i], c->hcopy[i]));
+    QK_CUDA(c, cudaStreamWaitEvent(s, c->hcopy_ev[i], 0));
+  }
+  return QK_OK;
+}
+
+int qk_step_host(qk_ctx *c, void *const hydro[5], void *const rad[4], double *dt_out,
+                 int32_t *nsub_out, void *stream) {
+  if (!c) return QK_EINVAL;
+  if (!hydro) return fail(c, QK_EINVAL, "hydro fields missing");
+  for (int q = 0; q < 5; ++q)
+    if (!hydro[q]) return fail(c, QK_EINVAL, "hydro field %d is NULL", q);
+  if (rad)
+    for (int q = 0; q < 4; ++q)
+      if (!rad[q]) return fail(c, QK_EINVAL, "rad field %d is NULL", q);
+  const int nf = rad ? 9 : 5;
+  const size_t bytes = (size_t)c->field_len * c->elem;
+  for (int q = 0; q < nf; ++q)
+    if (!c->hstate[q]) QK_CUDA(c, cudaMalloc(&c->hstate[q], bytes));
+  if (!c->hcopy[0]) {
+    for (int i = 0; i < 3; ++i)
+      QK_CUDA(c, cudaStreamCreateWithFlags(&c->hcopy[i], cudaStreamNonBlocking));
+    for (int i = 0; i < 4; ++i)
+      QK_CUDA(c, cudaEventCreateWithFlags(&c->hcopy_ev[i], cudaEventDisableTiming));
+  }
+  void *host[9];
+  for (int q = 0; q < 5; ++q) host[q] = hydro[q];
+  for (int q = 5; q < nf; ++q) host[q] = rad[q - 5];
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = host_copies(c, host, nf, true, s);
+  if (rc) return rc;
+  void *const *dev = c->hstate;
+  if ((rc = qk_step(c, dev, rad ? dev + 5 : nullptr, dt_out, nullptr, stream))) return rc;
+  if ((rc = host_copies(c, host, nf, false, s))) return rc;
+  if (nsub_out)
+    QK_CUDA(c, cudaMemcpyAsync(c->h_buf + 8, &c->d_si->nsub, sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+  QK_CUDA(c, cudaStreamSynchronize(s));
+  if (nsub_out) *nsub_out = (int32_t)c->h_buf[8];
   return QK_OK;
 }
 

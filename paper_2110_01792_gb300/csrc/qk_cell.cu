@@ -260,6 +260,37 @@ cudaError_t launch_ghost_fill(int fp32, const Copy *copies, const Chunk *chunks,
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------- field copies ---
+// Host <-> device copies of whole fields by the SMs (loads or stores through
+// the host mapping of pinned memory cross the CPU-GPU link in parallel from
+// every SM): blockIdx.y is the field, 16-byte words grid-strided over x, the
+// tail (bytes mod 16) by the first threads.
+__global__ void __launch_bounds__(256) field_copy_kernel(FieldCopies fc, long long n16,
+                                                         int tail) {
+  const uint4 *src = (const uint4 *)fc.src[blockIdx.y];
+  uint4 *dst = (uint4 *)fc.dst[blockIdx.y];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+  if (blockIdx.x == 0 && threadIdx.x < tail)
+    ((unsigned char *)(dst + n16))[threadIdx.x] = ((const unsigned char *)(src + n16))[threadIdx.x];
+}
+
+cudaError_t launch_field_copies(const FieldCopies &fc, int nf, size_t bytes, cudaStream_t s) {
+  if (nf < 1 || nf > 9 || bytes == 0) return cudaSuccess;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long n16 = (long long)(bytes / 16);
+  const int tail = (int)(bytes % 16);
+  long long bx = (n16 + 255) / 256;
+  const long long cap = (long long)std::max(nsm, 1) * 8 / nf + 1;  // ~8 CTAs per SM in all
+  if (bx > cap) bx = cap;
+  if (bx < 1) bx = 1;
+  field_copy_kernel<<<dim3((unsigned)bx, (unsigned)nf), 256, 0, s>>>(fc, n16, tail);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------- halo pack ---
 // Cross-rank part of the ghost fill, and the Dirichlet boundary store.  The
 // packing side gathers, for each region, the source cells (the descriptor's

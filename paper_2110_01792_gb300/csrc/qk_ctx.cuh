@@ -72,6 +72,11 @@ struct qk_ctx {
   size_t elem = 8;
   // pinned host staging
   double *h_buf = nullptr;
+  // qk_step_host: device copy of a host-resident state, and the streams and
+  // events that spread its copies over the copy engines
+  void *hstate[9] = {};
+  cudaStream_t hcopy[3] = {};
+  cudaEvent_t hcopy_ev[4] = {};
   // step graph
   int use_graph = 1;
   cudaStream_t cap_stream = nullptr;

@@ -117,6 +117,7 @@ def lib():
     L.qk_eval_convert.argtypes = [vp, vp, vp, vp, i64, vp]
     L.qk_fma_probe.argtypes = [i32, i64, vp, i64, P(dbl), vp]
     L.qk_step_compensated.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), P(dbl), P(i32), vp]
+    L.qk_step_host.argtypes = [vp, P(vp), P(vp), P(dbl), P(i32), vp]
     L.qk_conserved_sums_compensated.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), P(dbl), vp]
     for f in ("qk_init_level", "qk_amr_init", "qk_amr_info", "qk_amr_interp", "qk_amr_register",
               "qk_amr_sync", "qk_set_tile_part", "qk_tile_counts", "qk_fill_plan", "qk_fill_ghosts_range", "qk_set_dirichlet", "qk_set_source",
@@ -125,7 +126,7 @@ def lib():
               "qk_fill_ghosts", "qk_hydro_stage", "qk_rad_stage",
               "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
               "qk_status", "qk_step_info", "qk_eval_math", "qk_eval_convert", "qk_fma_probe",
-              "qk_step_compensated",
+              "qk_step_compensated", "qk_step_host",
               "qk_conserved_sums_compensated"):
         getattr(L, f).restype = C.c_int
     _lib = L
@@ -410,6 +411,24 @@ class Context:
                 self._h, _ptrs(U, 5), rp, _ptrs(Ul, 5), _ptrs(Rl, 4) if R is not None else None,
                 C.byref(dt) if want_dt else None, C.byref(ns) if want_dt else None,
                 _stream(stream))
+        self._check(rc)
+        return (dt.value, ns.value) if want_dt else None
+
+    def step_host(self, U, R=None, want_dt=False, stream=None):
+        """One full update of a state held in host memory (qk_step_host): U,
+        R are CPU tensors (pinned for full copy speed) or numpy arrays of the
+        context's precision, updated in place; returns after the copy back."""
+        def hp(fields, n):
+            assert len(fields) == n, f"expected {n} fields"
+            out = (C.c_void_p * n)()
+            for i, f in enumerate(fields):
+                out[i] = f.ctypes.data if isinstance(f, np.ndarray) else int(f.data_ptr())
+            return out
+        dt = C.c_double(0.0)
+        ns = C.c_int32(0)
+        rc = self._L.qk_step_host(self._h, hp(U, 5), hp(R, 4) if R is not None else None,
+                                  C.byref(dt) if want_dt else None,
+                                  C.byref(ns) if want_dt else None, _stream(stream))
         self._check(rc)
         return (dt.value, ns.value) if want_dt else None
 

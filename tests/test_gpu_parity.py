@@ -822,3 +822,31 @@ def test_shock_tube_with_flattening_ten_steps_gpu(torch_cuda):
     _check_dt(hg, hr)
     e = G.max_rel_err(lay, Ug, Ur)
     assert max(e) <= TOL_STEPS, e
+
+
+def test_step_host_matches_device_step(torch_cuda):
+    """qk_step_host (state in host memory: pinned tensors and pageable numpy
+    arrays) gives bit for bit the device qk_step of the same state, FP64 and
+    FP32-mixed, with the step size and N_sub reported alike."""
+    torch = torch_cuda
+    lay, prob, prm = _small_rhd()
+    for prec in (0, 1):
+        tdt = torch.float64 if prec == 0 else torch.float32
+        ndt = np.float64 if prec == 0 else np.float32
+        ctx = _ctx(lay, prm, prec)
+        dU, dR = G.dev(prob.U, tdt), G.dev(prob.R, tdt)
+        pU = [torch.from_numpy(a).to(tdt).pin_memory() for a in prob.U]
+        pR = [torch.from_numpy(a).to(tdt).pin_memory() for a in prob.R]
+        nU = [np.ascontiguousarray(a, dtype=ndt) for a in prob.U]
+        nR = [np.ascontiguousarray(a, dtype=ndt) for a in prob.R]
+        for _ in range(3):
+            a = ctx.step(dU, dR, want_dt=True)
+            b = ctx.step_host(pU, pR, want_dt=True)
+            c = ctx.step_host(nU, nR, want_dt=True)
+            assert a == b == c, (a, b, c)
+        torch.cuda.synchronize()
+        assert ctx.status()[0] == 0
+        ctx.close()
+        for d, p_, n_ in zip(G.host(dU) + G.host(dR), pU + pR, nU + nR):
+            assert np.array_equal(G.interior(lay, d), G.interior(lay, p_.double().numpy()))
+            assert np.array_equal(G.interior(lay, d), G.interior(lay, n_.astype(np.float64)))
