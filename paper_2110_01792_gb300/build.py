@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libqk.so")
 SOURCES = ["qk_api.cu", "qk_hydro.cu", "qk_column.cu", "qk_rad.cu", "qk_rad_closures.cu",
            "qk_column_rad.cu", "qk_cell.cu", "qk_noalloc.cu", "qk_amr.cu"]
 HEADERS = ["qk_internal.cuh", "qk_device.cuh", "qk_rad.cuh", "qk_ctx.cuh", "qk_exchange.cuh",
-           "qk_column_rad.cuh"]
+           "qk_column_rad.cuh", "qk_copy.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "qk_copy.cuh"
 #include "qk_ctx.cuh"
 
 using namespace qk;

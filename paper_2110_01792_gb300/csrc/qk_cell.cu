@@ -4,6 +4,7 @@
 // compensated conservation sums.
 #include <algorithm>
 
+#include "qk_copy.cuh"
 #include "qk_exchange.cuh"
 
 namespace qk {

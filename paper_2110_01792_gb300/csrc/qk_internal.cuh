@@ -310,14 +310,6 @@ cudaError_t launch_halo(int fp32, int pack, const Copy *copies, const Chunk *chu
                         void *const *fields, int nf, int first, void *buf, long long nbuf,
                         DtSrc pred, cudaStream_t s);
 cudaError_t launch_timestep(const qk_params &p, StepInfo *si, cudaStream_t s);
-// Whole-field copies by the SMs between device arrays and pinned host arrays
-// mapped into the device address space (16-byte aligned, `bytes` each, up to
-// 9 fields in one launch).
-struct FieldCopies {
-  const void *src[9];
-  void *dst[9];
-};
-cudaError_t launch_field_copies(const FieldCopies &fc, int nf, size_t bytes, cudaStream_t s);
 cudaError_t launch_ghost_fill(int fp32, const Copy *copies, const Chunk *chunks, int nchunks,
                               void *const *fields, int nf, int first, DtSrc pred, cudaStream_t s);
 cudaError_t launch_sums(int fp32, const Geometry &g, const qk_params &p, void *const *U,
