@@ -195,3 +195,51 @@ def test_radiation_uniform_state_unchanged():
     O.rad_stage(g, p, 2, R, R1, R, rho, 1e-3)
     for a, b in zip(R, R0):
         assert np.array_equal(lay.interior(a, 0), lay.interior(b, 0))
+
+
+@pytest.mark.parametrize("tau_cell", [0.0, 4.0])
+def test_single_step_at_an_energy_jump_closed_form(tau_cell):
+    """One forward stage of the radiation update at a jump of E_r (1 | 2)
+    with a uniform reduced flux f = (0.3, 0, 0), by hand: PLM keeps the face
+    states at the cell averages there (the MC slopes vanish beside a step),
+    so the HLL flux at the jump face is
+      energy: (chat/2) f (E_L + E_R) - (S eps / 2)(E_R - E_L),
+      F_x:    (c chat/2) chi (E_L + E_R) - (S eps c f / 2)(E_R - E_L),
+    with S = chat sqrt(T_xx) = chat sqrt(chi) of the cell averages (Levermore
+    chi(0.3), the same on both sides) and eps = min(1, 1/tau), tau = dx (rho
+    kappa_R) (Sec. 2.2.2; the optical-depth factor as read), and the faces
+    inside the two plateaus carry the upwind-free flux of the uniform state.
+    A dropped 1/2, chat/c, square root or eps changes the cells beside the
+    jump at O(dt/dx)."""
+    N = 16
+    lay = I.single_box(N, 4, 4)
+    c, chat, f0, dt = 100.0, 10.0, 0.3, 1e-3
+    dx = 1.0 / N
+    R = I.zeros(lay, 4)
+    E = np.where(np.arange(N) < N // 2, 1.0, 2.0)
+    lay.interior(R[0], 0)[...] = E[None, None, :]
+    lay.interior(R[1], 0)[...] = c * f0 * E[None, None, :]
+    kap = tau_cell / dx
+    rho = np.ones(lay.field_len)
+    p = O.make_params(c=c, chat=chat, kappa_P=kap, kappa_R=kap, dx=dx, recon=1,
+                      tau_correction=1)
+    g = _grid(lay)
+    R1 = [np.zeros_like(a) for a in R]
+    O.rad_stage(g, p, 1, R, None, R1, rho, dt)
+    chi = (3.0 + 4.0 * f0 ** 2) / (5.0 + 2.0 * math.sqrt(4.0 - 3.0 * f0 ** 2))
+    S = chat * math.sqrt(chi)
+    eps = 1.0 if tau_cell <= 1.0 else 1.0 / tau_cell
+    EL, ER = 1.0, 2.0
+    FE = 0.5 * chat * f0 * (EL + ER) - 0.5 * S * eps * (ER - EL)
+    FF = 0.5 * c * chat * chi * (EL + ER) - 0.5 * S * eps * c * f0 * (ER - EL)
+    k = dt / dx
+    want = {  # cell: (E, F_x) after the stage
+        N // 2 - 1: (EL - k * (FE - chat * f0 * EL), c * f0 * EL - k * (FF - c * chat * chi * EL)),
+        N // 2: (ER - k * (chat * f0 * ER - FE), c * f0 * ER - k * (c * chat * chi * ER - FF)),
+        N // 4: (EL, c * f0 * EL),
+    }
+    Eo, Fo = lay.interior(R1[0], 0), lay.interior(R1[1], 0)
+    for i, (we, wf) in want.items():
+        assert np.allclose(Eo[:, :, i], we, rtol=1e-13, atol=0), (i, Eo[0, 0, i], we)
+        assert np.allclose(Fo[:, :, i], wf, rtol=1e-13, atol=0), (i, Fo[0, 0, i], wf)
+        assert np.all(lay.interior(R1[2], 0)[:, :, i] == 0.0)
