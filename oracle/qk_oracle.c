@@ -961,7 +961,7 @@ static void eos_T4(const or_params *p, double rho, double Eg, double *T4, double
  * eqs. delta_er and delta_eg with eta = -(dF_R/dE_g)/(dF_G/dE_g); kappa does
  * not depend on T here, so dkappa/dT = 0.  The convergence test
  * |F_G/E_tot| < eps and |(c/chat) F_R/E_tot| < eps with E_tot = E_g0 +
- * (c/chat) E_r0 is made on the residuals of each iterate; reading: the Newton
+ * (c/chat)(E_r0 + S) is made on the residuals of each iterate; reading: the Newton
  * update computed from the iterate whose residuals pass is still applied,
  * and the iteration then stops.  S is the optional source of the radiation
  * energy residual, F_R = (E_r - E_r0) - (R + S); it does not depend on the
@@ -971,7 +971,8 @@ int or_exchange_energy_src(const or_params *p, double rho, double Eg0, double Er
                            double S, double *Eg_out, double *Er_out) {
   double kP = kappa_of(p, p->kappa_P, rho);
   double cr = p->c / p->chat;
-  double Etot = Eg0 + cr * Er0;
+  /* E_tot = E_g^(t) + (c/chat)(E_r^(t) + S), the paper's definition */
+  double Etot = Eg0 + cr * (Er0 + S);
   double Eg = Eg0, Er = Er0;
   int it = 0, converged = 0;
   for (it = 0; it < p->max_iter; ++it) {

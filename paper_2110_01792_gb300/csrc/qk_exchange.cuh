@@ -33,7 +33,7 @@ __device__ __forceinline__ bool pos_normal(float x) {
 // F_R = (E_r - E_r0) - R; with a radiation source S the callers pass
 // E_r0 + S for E_r0 (F_R = (E_r - E_r0) - (R + S); the Jacobian does not
 // change).  Convergence |F_G/E_tot| < eps and |(c/chat) F_R / E_tot| < eps,
-// E_tot = E_g0 + (c/chat) E_r0, tested as |F_G| < thr_g = eps E_tot and
+// E_tot = E_g0 + (c/chat)(E_r0 + S), tested as |F_G| < thr_g = eps E_tot and
 // |F_R| < thr_r = thr_g chat/c; the update of the iterate that passes is
 // applied, then the loop stops.  With k = dt rho kappa_P chat and
 // T = E_g/(rho c_v), R = A E_g^4 - k E_r with A = k a_r/(rho c_v)^4 (for the
@@ -251,7 +251,10 @@ __device__ __forceinline__ void exchange_cell(const qk_params &p, const ExK &K, 
   const double damp = rho * inv_rho_Dm;
   const double Ekin0 = 0.5 * m2 * inv_rho;
   const double Eg0 = E - Ekin0;
-  const double thr_g = p.eps_newton * (Eg0 + K.cr * Er0);
+  // radiation source S = dt (chat/c) j, carried in the residual's E_r0
+  const double Er0S = src ? Er0 + dt * K.rc_d * load_d(src, e) : Er0;
+  // tolerance against E_tot = E_g0 + (c/chat)(E_r0 + S)
+  const double thr_g = p.eps_newton * (Eg0 + K.cr * Er0S);
   const double thr_r = thr_g * K.rc_d;
   const double k = dt * rho * kP * p.chat;
   double A = k * K.a_e;
@@ -259,8 +262,6 @@ __device__ __forceinline__ void exchange_cell(const qk_params &p, const ExK &K, 
     const double i2 = (inv_rho * K.inv_cv) * (inv_rho * K.inv_cv);
     A *= i2 * i2;
   }
-  // radiation source S = dt (chat/c) j, carried in the residual's E_r0
-  const double Er0S = src ? Er0 + dt * K.rc_d * load_d(src, e) : Er0;
   // Start the FP64 iteration from an FP32 Newton solve to 1e-6 (the same
   // equations on FP32 pipes, inputs narrowed on the integer pipe): the FP64
   // iteration then needs about two steps, one correction and one confirming
@@ -376,7 +377,7 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
     Er0 = df_of(er, er_lo);
   }
   // The solve runs on the energies divided by 2^eE (exact), eE the binary
-  // exponent of E_tot = E_g0 + (c/chat) E_r0, so that its FP32 and
+  // exponent of E_tot = E_g0 + (c/chat)(E_r0 + S), so that its FP32 and
   // double-float numbers are O(1) in any units (in cgs E_g^4 would overflow
   // FP32): with E = E' 2^eE the equations keep their form with k unchanged and
   // A' = A 2^(3 eE) (A for the alpha T^3 heat capacity, where R is linear in
@@ -387,7 +388,9 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
   // those outside the FP32 range, measured faster: no divergent branch.)
   const bool alpha_eos = p.eos == QK_EOS_ALPHA_T3;
   const float kf = dtf * K.kchat * (p.kappa_mode == QK_KAPPA_RHO ? rho * rho : rho);
-  const float Etot_u = Eg0.h + K.crf * Er0.h;
+  // radiation source S = dt (chat/c) j, carried in the residual's E_r0
+  const float S_u = src ? (dtf * K.rc) * src[e] : 0.0f;
+  const float Etot_u = Eg0.h + K.crf * (Er0.h + S_u);
   const int eE = pos_normal(Etot_u) ? min(max(fexpo(Etot_u), -100), 100) : 0;
   const float sc = pow2f(-eE), isc = pow2f(eE);
   float Af;
@@ -402,8 +405,7 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
   const DF Er0s{Er0.h * sc, Er0.l * sc};
   const float Etotf = Etot_u * sc;
   const float thr_g = K.epsf * Etotf, thr_r = thr_g * K.rc;
-  // radiation source S = dt (chat/c) j, carried in the residual's E_r0
-  const DF Er0S = src ? df_add_f(Er0s, ((dtf * K.rc) * src[e]) * sc) : Er0s;
+  const DF Er0S = src ? df_add_f(Er0s, S_u * sc) : Er0s;
   // FP32 warm start to 1e-6
   float Egf = Eg0s.h, Erf = Er0S.h;
   const int itf = newton_exchange<float>(alpha_eos, Af, kf, K.crf, Eg0s.h, Erf, 1e-6f * Etotf,

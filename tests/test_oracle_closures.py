@@ -186,3 +186,45 @@ def test_source_field_in_the_cell_exchange():
     np.testing.assert_array_equal(lay.interior(U[4], 0), E0)
     np.testing.assert_allclose(lay.interior(R[0], 0), Er0 + dt * (p.chat / p.c) * lay.interior(j, 0),
                                rtol=1e-15, atol=0)
+
+
+def test_newton_tolerance_is_relative_to_E_tot_with_the_source():
+    """Sec. 2.2.3 defines the convergence test against
+    E_tot = E_g + (c/chat)(E_r + S), the source included.  With kappa_P = 0
+    the first iterate (E_g0, E_r0) has the residuals F_G = 0 and F_R = -S
+    exactly, so it passes the paper's test iff (c/chat) S / E_tot < eps.
+    Here (c/chat) S / E_tot = 30/38.5 = 0.779; without S in E_tot the ratio
+    would be 30/8.5 = 3.53.  A tolerance between 0.779 and 3.53 therefore
+    stops at the first iterate (count 1) only under the paper's definition;
+    below 0.779 the second iterate (the exact solution, residual at
+    round-off) stops it (count 2).  The update of the passing iterate is
+    applied either way (E_r = E_r0 + S)."""
+    Eg0, Er0, S = 1.5, 0.7, 3.0
+    for eps, count in ((0.80, 1), (0.95, 1), (0.75, 2), (0.5, 2)):
+        p = O.make_params(kappa_P=0.0, kappa_R=0.0, c=30.0, chat=3.0, c_v=1.0, a_r=1.0,
+                          eps_newton=eps)
+        Eg, Er, it = O.exchange_energy(p, 2.0, Eg0, Er0, 0.1, S)
+        assert it == count, (eps, it)
+        assert Eg == Eg0 and Er == Er0 + S
+
+
+def test_newton_converges_with_a_source_far_above_the_state():
+    """A source 1e9 times the cell's own E_g0 + (c/chat) E_r0, strongly coupled
+    (k (c/chat) = 150): the paper's tolerance eps (E_g0 + (c/chat)(E_r0 + S))
+    is reached in a few iterations and the energy budget
+    E_g + (c/chat) E_r = E_g0 + (c/chat)(E_r0 + S) holds to that tolerance.
+    Against E_g0 + (c/chat) E_r0 alone the tolerance would sit 1e7 times
+    below it, under the round-off of the residuals (~1e-16 of their terms)."""
+    p = O.make_params(kappa_P=50.0, kappa_R=1.0, c=30.0, chat=3.0, c_v=1.5, a_r=1.0)
+    cr = p.c / p.chat
+    rho, Eg0, Er0, dt = 1.0, 0.5, 0.02, 0.1
+    S = 1e7 * (Eg0 + cr * Er0)
+    Eg, Er, it = O.exchange_energy(p, rho, Eg0, Er0, dt, S)
+    Etot = Eg0 + cr * (Er0 + S)
+    assert 0 < it <= 100, it
+    assert abs((Eg + cr * Er) - Etot) <= 1e-10 * Etot
+    # the gas equation of the backward-Euler system holds at the result:
+    # F_G = (E_g - E_g0) + (c/chat) k (a_r T^4 - E_r) = 0 to eps E_tot
+    T = Eg / (rho * p.c_v)
+    k = dt * rho * p.kappa_P * p.chat
+    assert abs((Eg - Eg0) + cr * k * (p.a_r * T ** 4 - Er)) <= 1e-10 * Etot
