@@ -369,28 +369,37 @@ int qk_conserved_sums_compensated(qk_ctx *ctx, void *const hydro[5], void *const
 
 /* Conservation sums without any GPU allocation.  There is no counterpart in the
  * paper: this serves callers that cannot call cudaMalloc where they need the
- * totals (a host callback or diagnostics hook, a process whose device memory
- * is owned by an external allocator, or code that never creates a qk_ctx).
+ * totals (a diagnostics hook that runs between steps under a fixed memory
+ * budget, a process whose device memory is owned by an external allocator, or
+ * code that never creates a qk_ctx).  It launches kernels and synchronises
+ * `stream`, so it must not be called from a CUDA stream host callback (CUDA
+ * API calls are not allowed there).
  * It computes exactly what qk_conserved_sums computes (same kernels, same
- * fixed reduction order, same output layout and units) for the patch set
- * `boxes` (the layout of the field arrays, as given to qk_init_patches), and
- * copies the QK_NSUMS results to the host array `out`.  All working memory
- * (patch table, partial sums, result) lives in one static device array of
- * QK_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads
- * the library until the process exits; at most QK_NOALLOC_MAX_BOXES patches
- * (QK_EINVAL beyond that).  On failure a message is written to `err` (a
- * caller-owned buffer of `errlen` bytes; may be NULL).  The call
- * allocates nothing and synchronises `stream`.  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call outside any stream capture.  Every call
- * overwrites the whole array, so nothing carries over between calls, but calls
- * that overlap on the GPU (other streams, other host threads) race on it. */
+ * fixed reduction order, same output layout and units, bit-identical
+ * results) for the patch set `boxes` (the layout of the field arrays, as given
+ * to qk_init_patches, patches disjoint), and copies the QK_NSUMS results to
+ * the host array `out`.  field_len: elements of every field array; a patch
+ * whose padded extent (n + 2 nghost per axis, from its offset) ends beyond it
+ * is rejected with QK_EINVAL, so no kernel reads past the arrays.  All
+ * working memory (patch table, partial sums, result) lives in one static
+ * device array of QK_NOALLOC_SCRATCH_BYTES inside the library, held by every
+ * GPU that loads the library until the process exits; at most
+ * QK_NOALLOC_MAX_BOXES patches (QK_EINVAL beyond that).  On failure a message
+ * is written to `err` (a caller-owned buffer of `errlen` bytes; may be NULL).
+ * The call allocates nothing and synchronises `stream`.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current and keeps it for the life of the process; make that
+ * first call outside any stream capture, and make none after a
+ * cudaDeviceReset (which unloads the array; the kept address would be stale).
+ * Every call overwrites the whole array, so nothing carries over between
+ * calls, but calls that overlap on the GPU (other streams, other host
+ * threads) race on it. */
 #define QK_NOALLOC_MAX_BOXES 4096
 #define QK_NOALLOC_SCRATCH_BYTES (576 * 1024)
 int qk_conserved_sums_noalloc(const qk_params *p, const qk_box *boxes, int32_t nbox,
-                              int32_t nghost, int32_t precision, void *const hydro[5],
-                              void *const rad[4], double out[QK_NSUMS], void *stream,
-                              char *err, int32_t errlen);
+                              int32_t nghost, int32_t precision, int64_t field_len,
+                              void *const hydro[5], void *const rad[4], double out[QK_NSUMS],
+                              void *stream, char *err, int32_t errlen);
 
 /* Halo sizes of a sharded context: *send_cells = cells per field this rank
  * sends to `peer`, *recv_cells = cells per field it receives from `peer`,

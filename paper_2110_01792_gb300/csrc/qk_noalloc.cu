@@ -2,10 +2,12 @@
 // memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need the
-// conservation totals: code running inside a host callback or a tight
-// diagnostics hook, code under an external memory manager that owns every
+// conservation totals: a diagnostics hook that runs between steps under a
+// strict memory budget, code under an external memory manager that owns every
 // device allocation of the process, or a caller that has not (and will not)
-// create a qk context.  qk_conserved_sums_noalloc serves them.  It takes the
+// create a qk context.  qk_conserved_sums_noalloc serves them.  (It launches
+// kernels and synchronises its stream, so it must not be called from a CUDA
+// stream host callback, where CUDA API calls are not allowed.)  It takes the
 // patch table and the fields directly and keeps all of its working memory in
 // one fixed-size array in the library's device memory (a file-scope
 // __device__ array, so every GPU that loads the library holds it until the
@@ -61,7 +63,10 @@ __global__ void noalloc_table_kernel(unsigned char *base, int nbox, int ng) {
   cell0[nbox] = acc;
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device (with that
+// device current) and kept for the life of the process.  A cudaDeviceReset
+// unloads the module, so the kept address does not survive it (documented in
+// the header).
 static unsigned char *scratch_address(int dev, cudaError_t *err) {
   static std::mutex mu;
   static unsigned char *addr[64] = {};
@@ -90,7 +95,7 @@ static void report(char *err, int32_t errlen, const char *fmt, int a = 0, int b 
 }
 
 extern "C" int qk_conserved_sums_noalloc(const qk_params *p, const qk_box *boxes, int32_t nbox,
-                                         int32_t nghost, int32_t precision,
+                                         int32_t nghost, int32_t precision, int64_t field_len,
                                          void *const hydro[5], void *const rad[4],
                                          double out[QK_NSUMS], void *stream, char *err,
                                          int32_t errlen) {
@@ -124,12 +129,22 @@ extern "C" int qk_conserved_sums_noalloc(const qk_params *p, const qk_box *boxes
       }
   long long ncells = 0;
   for (int b = 0; b < nbox; ++b) {
-    if (boxes[b].n[0] < 1 || boxes[b].n[1] < 1 || boxes[b].n[2] < 1 || boxes[b].offset < 0) {
+    const qk_box &q = boxes[b];
+    if (q.n[0] < 1 || q.n[1] < 1 || q.n[2] < 1 || q.offset < 0) {
       report(err, errlen, "qk_conserved_sums_noalloc: patch %d has an empty extent or a "
                           "negative offset", b);
       return QK_EINVAL;
     }
-    ncells += (long long)boxes[b].n[0] * boxes[b].n[1] * boxes[b].n[2];
+    // the padded patch must lie inside every field array (no read past them)
+    const long long sx = (long long)q.n[0] + 2 * nghost, sy = (long long)q.n[1] + 2 * nghost,
+                    sz = (long long)q.n[2] + 2 * nghost;
+    if (q.n[0] > (1 << 20) || q.n[1] > (1 << 20) || q.n[2] > (1 << 20) ||
+        q.offset > field_len || sx * sy * sz > field_len - q.offset) {
+      report(err, errlen, "qk_conserved_sums_noalloc: patch %d with its ghost cells ends "
+                          "beyond field_len", b);
+      return QK_EINVAL;
+    }
+    ncells += (long long)q.n[0] * q.n[1] * q.n[2];
   }
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -146,7 +161,7 @@ extern "C" int qk_conserved_sums_noalloc(const qk_params *p, const qk_box *boxes
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    Geometry g;
+    Geometry g{};
     g.boxes = reinterpret_cast<const DevBox *>(base + kOffDevBox);
     g.tiles = nullptr;
     g.ntiles = 0;

@@ -1,13 +1,16 @@
 """The allocation-free conservation sums (qk_conserved_sums_noalloc).
 
 That entry point exists for callers that cannot call cudaMalloc where they
-need the conservation totals (host callbacks, code under an external device
-allocator, code without a qk context).  It keeps its working memory in a fixed
-static device array of the library.  Here it is called through the C ABI twice
-in a row, on two different patch sets and precisions, and each result is
-compared with qk_conserved_sums of a regular context on the same fields, to
-the tolerance of the other sum tests (4e-16 relative).  This file is collected
-last so that a failure here does not hide the rest of the suite.
+need the conservation totals (a diagnostics hook under a fixed device-memory
+budget, code under an external device allocator, code without a qk context).
+It keeps its working memory in a fixed static device array of the library.
+Here it is called through the C ABI twice in a row, on two different patch
+sets and precisions, and each result must equal qk_conserved_sums of a
+regular context on the same fields bit for bit (same kernels, same reduction
+order).  A warm call must leave the device's free memory and the caching
+allocator's counters unchanged.  One more case fills the static patch table to
+its limit (exactly 4096 patches).  This file is collected last so that a
+failure here does not hide the rest of the suite.
 """
 import ctypes as C
 
@@ -30,8 +33,8 @@ def env():
     L = qk.lib()
     fn = L.qk_conserved_sums_noalloc
     fn.argtypes = [C.POINTER(qk.Params), C.POINTER(qk.Box), C.c_int32, C.c_int32, C.c_int32,
-                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_double),
-                   C.c_void_p, C.c_char_p, C.c_int32]
+                   C.c_int64, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                   C.POINTER(C.c_double), C.c_void_p, C.c_char_p, C.c_int32]
     fn.restype = C.c_int
     return torch, qk, fn
 
@@ -62,6 +65,23 @@ def _ptrs(ts):
     return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
 
 
+def _noalloc(qk, fn, lay, prm, prec, dU, dR, stream):
+    out = (C.c_double * qk.NSUMS)()
+    err = C.create_string_buffer(256)
+    params = qk.make_params(**prm)
+    rc = fn(C.byref(params), _boxes(qk, lay), lay.nbox, lay.ng, prec, lay.field_len, _ptrs(dU),
+            _ptrs(dR) if dR is not None else None, out, C.c_void_p(stream), err, 256)
+    assert rc == qk.OK, err.value.decode()
+    return np.array(out[:])
+
+
+def _memory(torch):
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    st = torch.cuda.memory_stats()
+    return free, st.get("allocation.all.allocated", 0), st.get("reserved_bytes.all.current", 0)
+
+
 def test_noalloc_sums_match_context_sums_on_two_calls(env):
     torch, qk, fn = env
     cases = [
@@ -80,14 +100,34 @@ def test_noalloc_sums_match_context_sums_on_two_calls(env):
         ctx = qk.Context(lay, prm, prec)
         ref = ctx.conserved_sums(dU, dR)
         ctx.close()
-        out = (C.c_double * qk.NSUMS)()
-        err = C.create_string_buffer(256)
-        params = qk.make_params(**prm)
-        rc = fn(C.byref(params), _boxes(qk, lay), lay.nbox, lay.ng, prec, _ptrs(dU),
-                _ptrs(dR) if dR is not None else None, out, C.c_void_p(stream), err, 256)
-        assert rc == qk.OK, err.value.decode()
-        got = np.array(out[:])
-        assert np.all(np.abs(got - ref) <= 4e-16 * np.abs(ref) + 1e-300), (got, ref)
+        got = _noalloc(qk, fn, lay, prm, prec, dU, dR, stream)
+        np.testing.assert_array_equal(got, ref)
+        # a warm call allocates nothing: free device memory and the caching
+        # allocator's counters stay where they were
+        before = _memory(torch)
+        again = _noalloc(qk, fn, lay, prm, prec, dU, dR, stream)
+        after = _memory(torch)
+        assert after == before, (before, after)
+        np.testing.assert_array_equal(again, ref)
+
+
+def test_noalloc_sums_at_the_patch_limit(env):
+    """Exactly QK_NOALLOC_MAX_BOXES = 4096 patches (16^3 boxes of 4^3 cells in a
+    64^3 periodic domain): the largest patch-table copy, table build and
+    prefix the static layout holds."""
+    torch, qk, fn = env
+    lo = [[4 * i, 4 * j, 4 * k] for k in range(16) for j in range(16) for i in range(16)]
+    lay = I.make_layout(lo, [[4, 4, 4]] * 4096, (64, 64, 64), 3)
+    assert lay.nbox == 4096
+    U, R, prm = _state(lay, 31, True)
+    dU = [torch.from_numpy(a).cuda() for a in U]
+    dR = [torch.from_numpy(a).cuda() for a in R]
+    ctx = qk.Context(lay, prm, qk.FP64)
+    ref = ctx.conserved_sums(dU, dR)
+    ctx.close()
+    stream = torch.cuda.current_stream().cuda_stream
+    got = _noalloc(qk, fn, lay, prm, qk.FP64, dU, dR, stream)
+    np.testing.assert_array_equal(got, ref)
 
 
 def test_noalloc_rejects_too_many_patches(env):
@@ -102,5 +142,25 @@ def test_noalloc_rejects_too_many_patches(env):
     out = (C.c_double * qk.NSUMS)()
     err = C.create_string_buffer(256)
     params = qk.make_params(hydro_only=1, dx=0.25)
-    rc = fn(C.byref(params), boxes, n, 4, qk.FP64, _ptrs(dU), None, out, None, err, 256)
+    rc = fn(C.byref(params), boxes, n, 4, qk.FP64, lay.field_len, _ptrs(dU), None, out, None,
+            err, 256)
     assert rc == qk.EINVAL and b"4096" in err.value
+
+
+def test_noalloc_rejects_a_patch_beyond_the_field_length(env):
+    """A patch table that does not fit the field arrays is refused before any
+    launch (the sums kernel would read past the caller's arrays)."""
+    torch, qk, fn = env
+    lay = I.single_box(4, 4, 4)
+    dU = [torch.zeros(lay.field_len, dtype=torch.float64, device="cuda") for _ in range(5)]
+    boxes = _boxes(qk, lay)
+    out = (C.c_double * qk.NSUMS)()
+    err = C.create_string_buffer(256)
+    params = qk.make_params(hydro_only=1, dx=0.25)
+    rc = fn(C.byref(params), boxes, 1, 4, qk.FP64, lay.field_len - 1, _ptrs(dU), None, out,
+            None, err, 256)
+    assert rc == qk.EINVAL and b"field_len" in err.value
+    boxes[0].offset = 1
+    rc = fn(C.byref(params), boxes, 1, 4, qk.FP64, lay.field_len, _ptrs(dU), None, out, None,
+            err, 256)
+    assert rc == qk.EINVAL
