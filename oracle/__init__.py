@@ -43,15 +43,25 @@ OK, EINVAL, ENOCONV, ENEGATIVE = 0, 1, 3, 4
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liboracle.so``."""
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (with OpenMP for
+    the host-thread cell loops where the compiler has it, else serial)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.run(base, check=True)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's cell loops (z-planes over OpenMP threads;
+    results are bit-identical to one thread).  Returns the number in effect:
+    1 when the oracle was built without OpenMP."""
+    return int(lib().or_set_threads(int(n)))
 
 
 class Params(C.Structure):
@@ -154,6 +164,8 @@ def lib():
                                         C.c_double, C.c_int64, vp, vp]
             L.or_step.argtypes = [vp, P(Params), vp, vp, vp, vp, P(C.c_double), P(C.c_int64)]
             L.or_conserved_sums.argtypes = [vp, P(Params), vp, vp, P(C.c_double)]
+            L.or_set_threads.restype = C.c_int
+            L.or_set_threads.argtypes = [C.c_int]
             _lib = L
     return _lib
 

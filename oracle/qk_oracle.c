@@ -41,6 +41,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_OK 0
 #define OR_EINVAL 1
@@ -287,37 +290,97 @@ int or_set_dirichlet(or_grid *g, const or_params *p, double *const *fields) {
 
 /* Fill every ghost cell of nf fields (field ids fid0 .. fid0+nf-1) under the
  * boundary conditions: the value a stencil read of that cell sees. */
+/* ------------------------------------------------------------------------ */
+/* host threads                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Cell loops run over z-planes (patch b, index k), distributed over host
+ * threads with OpenMP when the oracle is compiled with it.  Every cell is
+ * computed by the same code from the same inputs whichever thread takes its
+ * plane, and every reduction whose result depends on the order (the exchange
+ * status, the conservation sums) is combined in the serial plane order, so
+ * the results are bit-identical to one thread. */
+static int or_nthreads = 1;
+
+/* Set the number of host threads of the cell loops; returns the number in
+ * effect (1 when the oracle was compiled without OpenMP). */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  or_nthreads = n < 1 ? 1 : n;
+#else
+  (void)n;
+  or_nthreads = 1;
+#endif
+  return or_nthreads;
+}
+
+typedef struct {
+  int b, k;
+} or_plane;
+
+/* the z-planes k in [k0, n_z + k1) of every patch, in serial order
+ * (interior planes: k0 = k1 = 0; with ghost layers: k0 = -ng, k1 = ng) */
+static or_plane *grid_planes(const or_grid *g, int k0, int k1, int64_t *np) {
+  int64_t n = 0;
+  for (int b = 0; b < g->nbox; ++b) n += g->n[3 * b + 2] + k1 - k0;
+  or_plane *pl = (or_plane *)malloc((size_t)(n > 0 ? n : 1) * sizeof(or_plane));
+  int64_t t = 0;
+  for (int b = 0; b < g->nbox; ++b)
+    for (int k = k0; k < g->n[3 * b + 2] + k1; ++k) {
+      pl[t].b = b;
+      pl[t].k = k;
+      ++t;
+    }
+  *np = n;
+  return pl;
+}
+
 int or_fill_ghosts_bc(const or_grid *g, const or_params *p, double *const *f, int nf, int fid0) {
   int ng = g->ng;
-  for (int b = 0; b < g->nbox; ++b) {
+  int bad = 0;
+  int64_t np;
+  or_plane *pl = grid_planes(g, -ng, ng, &np);
+  /* ghost cells are written from interior cells (or the boundary store)
+   * only, so the planes are independent */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(or_nthreads) if (or_nthreads > 1)
+  for (int64_t t = 0; t < np; ++t) {
+    const int b = pl[t].b, k = pl[t].k;
     const int32_t *n = g->n + 3 * b;
-    for (int k = -ng; k < n[2] + ng; ++k)
-      for (int j = -ng; j < n[1] + ng; ++j)
-        for (int i = -ng; i < n[0] + ng; ++i) {
-          int inside = i >= 0 && j >= 0 && k >= 0 && i < n[0] && j < n[1] && k < n[2];
-          if (inside) continue;
-          int c[3] = {i, j, k};
-          or_src r = resolve(g, p, b, c);
-          if (r.e < 0 && !g->dstore) return OR_EINVAL;
-          for (int v = 0; v < nf; ++v) f[v][cell_index(g, b, i, j, k)] = src_value(g, f[v], fid0 + v, &r);
+    for (int j = -ng; j < n[1] + ng; ++j)
+      for (int i = -ng; i < n[0] + ng; ++i) {
+        int inside = i >= 0 && j >= 0 && k >= 0 && i < n[0] && j < n[1] && k < n[2];
+        if (inside) continue;
+        int c[3] = {i, j, k};
+        or_src r = resolve(g, p, b, c);
+        if (r.e < 0 && !g->dstore) {
+#pragma omp atomic write
+          bad = 1;
+          continue;
         }
+        for (int v = 0; v < nf; ++v) f[v][cell_index(g, b, i, j, k)] = src_value(g, f[v], fid0 + v, &r);
+      }
   }
-  return OR_OK;
+  free(pl);
+  return bad ? OR_EINVAL : OR_OK;
 }
 
 /* fill every ghost cell of every patch from the owner of its periodic image */
 void or_fill_ghosts(const or_grid *g, double *f) {
   int ng = g->ng;
-  for (int b = 0; b < g->nbox; ++b) {
+  int64_t np;
+  or_plane *pl = grid_planes(g, -ng, ng, &np);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(or_nthreads) if (or_nthreads > 1)
+  for (int64_t t = 0; t < np; ++t) {
+    const int b = pl[t].b, k = pl[t].k;
     const int32_t *n = g->n + 3 * b;
-    for (int k = -ng; k < n[2] + ng; ++k)
-      for (int j = -ng; j < n[1] + ng; ++j)
-        for (int i = -ng; i < n[0] + ng; ++i) {
-          int inside = i >= 0 && j >= 0 && k >= 0 && i < n[0] && j < n[1] && k < n[2];
-          if (inside) continue;
-          f[cell_index(g, b, i, j, k)] = f[owner_index(g, b, i, j, k)];
-        }
+    for (int j = -ng; j < n[1] + ng; ++j)
+      for (int i = -ng; i < n[0] + ng; ++i) {
+        int inside = i >= 0 && j >= 0 && k >= 0 && i < n[0] && j < n[1] && k < n[2];
+        if (inside) continue;
+        f[cell_index(g, b, i, j, k)] = f[owner_index(g, b, i, j, k)];
+      }
   }
+  free(pl);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -619,9 +682,21 @@ static void hydro_rhs_cell(const or_grid *g, const or_params *p, double *const *
 }
 
 /* iterate over a list of interior cells (b,i,j,k quadruples) or, when
- * cells == NULL, over every interior cell of every patch */
+ * cells == NULL, over every interior cell of every patch (z-planes over the
+ * host threads; fn writes only its own cell of its outputs and reads no
+ * output of another cell, as every stage here does) */
 typedef void (*cell_fn)(const or_grid *g, const or_params *p, int b, const int c[3],
                         void *ctx);
+static void for_plane(const or_grid *g, const or_params *p, int b, int k, cell_fn fn,
+                      void *ctx) {
+  const int32_t *n = g->n + 3 * b;
+  for (int j = 0; j < n[1]; ++j)
+    for (int i = 0; i < n[0]; ++i) {
+      int c[3] = {i, j, k};
+      fn(g, p, b, c, ctx);
+    }
+}
+
 static void for_cells(const or_grid *g, const or_params *p, int64_t ncell,
                       const int32_t *cells, cell_fn fn, void *ctx) {
   if (cells) {
@@ -631,15 +706,11 @@ static void for_cells(const or_grid *g, const or_params *p, int64_t ncell,
     }
     return;
   }
-  for (int b = 0; b < g->nbox; ++b) {
-    const int32_t *n = g->n + 3 * b;
-    for (int k = 0; k < n[2]; ++k)
-      for (int j = 0; j < n[1]; ++j)
-        for (int i = 0; i < n[0]; ++i) {
-          int c[3] = {i, j, k};
-          fn(g, p, b, c, ctx);
-        }
-  }
+  int64_t np;
+  or_plane *pl = grid_planes(g, 0, 0, &np);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(or_nthreads) if (or_nthreads > 1)
+  for (int64_t t = 0; t < np; ++t) for_plane(g, p, pl[t].b, pl[t].k, fn, ctx);
+  free(pl);
 }
 
 typedef struct {
@@ -691,15 +762,19 @@ int or_hydro_stage(const or_grid *g, const or_params *p, int stage, double *cons
       if (end > len) len = end;
     }
     chi = (double *)calloc((size_t)len, sizeof(double));
-    for (int b = 0; b < g->nbox; ++b) {
+    int64_t np;
+    or_plane *pl = grid_planes(g, 0, 0, &np);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(or_nthreads) if (or_nthreads > 1)
+    for (int64_t t = 0; t < np; ++t) {
+      const int b = pl[t].b, k = pl[t].k;
       const int32_t *n = g->n + 3 * b;
-      for (int k = 0; k < n[2]; ++k)
-        for (int j = 0; j < n[1]; ++j)
-          for (int i = 0; i < n[0]; ++i) {
-            int c[3] = {i, j, k};
-            chi[cell_index(g, b, i, j, k)] = flat_chi(g, p, src, b, c);
-          }
+      for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+          int c[3] = {i, j, k};
+          chi[cell_index(g, b, i, j, k)] = flat_chi(g, p, src, b, c);
+        }
     }
+    free(pl);
     s.chi = chi;
   }
   for_cells(g, p, ncell, cells, hydro_stage_cell, &s);
@@ -713,21 +788,31 @@ int or_hydro_stage(const or_grid *g, const or_params *p, int stage, double *cons
 
 /* max(|v| + c_s) over all interior cells, |v| = sqrt((vx^2+vy^2)+vz^2) */
 double or_max_signal_speed(const or_grid *g, const or_params *p, double *const *U) {
-  double smax = 0.0;
-  for (int b = 0; b < g->nbox; ++b) {
+  int64_t np;
+  or_plane *pl = grid_planes(g, 0, 0, &np);
+  double *pmax = (double *)malloc((size_t)(np > 0 ? np : 1) * sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1) num_threads(or_nthreads) if (or_nthreads > 1)
+  for (int64_t t = 0; t < np; ++t) {
+    const int b = pl[t].b, k = pl[t].k;
     const int32_t *n = g->n + 3 * b;
-    for (int k = 0; k < n[2]; ++k)
-      for (int j = 0; j < n[1]; ++j)
-        for (int i = 0; i < n[0]; ++i) {
-          int64_t e = cell_index(g, b, i, j, k);
-          double Uc[NHYD], q[NHYD];
-          for (int v = 0; v < NHYD; ++v) Uc[v] = U[v][e];
-          con2prim(Uc, p->gamma, q);
-          double vmag = sqrt((q[1] * q[1] + q[2] * q[2]) + q[3] * q[3]);
-          double cs = sqrt(p->gamma * q[4] / q[0]);
-          smax = dmax(smax, vmag + cs);
-        }
+    double m = 0.0;
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        int64_t e = cell_index(g, b, i, j, k);
+        double Uc[NHYD], q[NHYD];
+        for (int v = 0; v < NHYD; ++v) Uc[v] = U[v][e];
+        con2prim(Uc, p->gamma, q);
+        double vmag = sqrt((q[1] * q[1] + q[2] * q[2]) + q[3] * q[3]);
+        double cs = sqrt(p->gamma * q[4] / q[0]);
+        m = dmax(m, vmag + cs);
+      }
+    pmax[t] = m;
   }
+  /* the maximum of the plane maxima (exact in any order) */
+  double smax = 0.0;
+  for (int64_t t = 0; t < np; ++t) smax = dmax(smax, pmax[t]);
+  free(pmax);
+  free(pl);
   return smax;
 }
 
@@ -1070,7 +1155,28 @@ int or_exchange(const or_grid *g, const or_params *p, double *const *U, double *
                 double dt, int64_t ncell, const int32_t *cells, const double *src,
                 int64_t out_info[4]) {
   exch_ctx x = {U, R, dt, src, 0, -1, 0, 0};
-  for_cells(g, p, ncell, cells, exchange_cell, &x);
+  if (cells) {
+    for_cells(g, p, ncell, cells, exchange_cell, &x);
+  } else {
+    /* one status record per z-plane, combined in the serial plane order (the
+     * first failing element is the one a serial sweep meets first) */
+    int64_t np;
+    or_plane *pl = grid_planes(g, 0, 0, &np);
+    exch_ctx *px = (exch_ctx *)malloc((size_t)(np > 0 ? np : 1) * sizeof(exch_ctx));
+#pragma omp parallel for schedule(dynamic, 1) num_threads(or_nthreads) if (or_nthreads > 1)
+    for (int64_t t = 0; t < np; ++t) {
+      px[t] = x;
+      for_plane(g, p, pl[t].b, pl[t].k, exchange_cell, &px[t]);
+    }
+    for (int64_t t = 0; t < np; ++t) {
+      x.status |= px[t].status;
+      if (x.first_bad < 0) x.first_bad = px[t].first_bad;
+      if (px[t].max_it > x.max_it) x.max_it = px[t].max_it;
+      x.total_it += px[t].total_it;
+    }
+    free(px);
+    free(pl);
+  }
   if (out_info) {
     out_info[0] = x.status;
     out_info[1] = x.first_bad;

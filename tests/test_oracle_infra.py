@@ -125,3 +125,32 @@ def test_planted_sign_error_is_caught():
     good = [0.3, 0.09 + 1.0, 0.0, 0.0, 0.3 * (E + 1.0)]
     np.testing.assert_allclose(F, good, rtol=1e-14)
     assert not np.allclose(bad, good)
+
+
+@pytest.mark.parametrize("flat,bc", [(0, "periodic"), (1, "walls")])
+def test_threaded_oracle_is_bit_identical(flat, bc):
+    """The oracle's host-thread cell loops (z-planes over OpenMP threads)
+    change no arithmetic: three RHD steps of a ragged patch set on 1 and on
+    several threads give the same bits in every field, the same timestep and
+    the same exchange record (status, first failing cell, iterations)."""
+    lay = I.patch_tiling(dom_n=(24, 16, 16), seed=7, ng=4, edges=(8, 16))
+    prob = I.rhd_lognormal(layout=lay, seed=9, kappa_mode=1, sigma=1.5)
+    prm = dict(prob.params, dx=1.0 / 24, flattening=flat)
+    if bc == "walls":
+        prm.update(bc_lo=(O.BC_REFLECT, 0, 0), bc_hi=(O.BC_OUTFLOW, 0, 0))
+    g = _grid(lay)
+    p = O.make_params(**prm)
+    results = []
+    try:
+        for nt in (1, 4):
+            O.set_threads(nt)
+            U = [a.copy() for a in prob.U]
+            R = [a.copy() for a in prob.R]
+            recs = [O.step(g, p, U, R) for _ in range(3)]
+            results.append((U + R, recs))
+    finally:
+        O.set_threads(1)
+    (f1, r1), (f4, r4) = results
+    assert r1 == r4
+    for a, b in zip(f1, f4):
+        np.testing.assert_array_equal(a, b)
