@@ -279,8 +279,10 @@ class RankStepper:
             yield from self._fill(U[:1], 0)
             for _ in range(nsub):
                 yield from self._fill(R, 5, lambda: ctx.rad_stage(1, R, None, R1, U[0], dtr))
-                yield from self._fill(R1, 5, lambda: ctx.rad_stage(2, R, R1, R, U[0], dtr))
-                ctx.exchange(U, R, dtr)
+                # stage 2 with the exchange in its epilogue (as qk_step runs it);
+                # the exchange is per cell, so it follows each tile part
+                yield from self._fill(R1, 5,
+                                      lambda: ctx.rad_stage2_exchange(R, R1, R, U, dtr))
         return dt, nsub
 
 

@@ -179,12 +179,17 @@ class FakeShardCtx:
     def rad_stage(self, stage, R0, R1, Rout, rho, dt):
         self._stage(stage, R0, R1, Rout, dt, rho.numpy())
 
-    def exchange(self, U, R, dt):
-        for b in self.own:
+    def exchange(self, U, R, dt, patches=None):
+        for b in self.own if patches is None else patches:
             e, er = self.lay.interior(U[4].numpy(), b), self.lay.interior(R[0].numpy(), b)
             d = dt * (er - e)
             e += d
             er -= d
+
+    def rad_stage2_exchange(self, R0, R1, Rout, U, dt):
+        # stage 2, then the per-cell exchange on the same tile part
+        self._stage(2, R0, R1, Rout, dt, U[0].numpy())
+        self.exchange(U, Rout, dt, self.parts[self.part])
 
 
 def _composer_layout():
