@@ -17,6 +17,10 @@ pytestmark = pytest.mark.gpu
 TOL_STAGE = 1e-12
 TOL_STEPS = 1e-10
 TOL_MIXED_L1 = 1e-5
+# FP32 stage against the FP64 oracle, per field (see _check_fp32_stage):
+# 8 and 168 FP32 ulps (2^-24)
+TOL_FP32_L1 = 8 * 2.0 ** -24
+TOL_FP32_MAX = 168 * 2.0 ** -24
 
 
 @pytest.fixture(scope="module")
@@ -182,6 +186,25 @@ def test_hydro_stages_supersonic_match_oracle(torch_cuda, shape):
     assert max(e2) <= TOL_STAGE, e2
 
 
+def _check_fp32_stage(lay, got, ref, tag):
+    """One FP32 stage against the FP64 oracle's stage from the same inputs,
+    per field: relative L1 and max relative error (RMS floor).  The FP32
+    result carries the rounding of its FP32 inputs and output (half an ulp,
+    2^-25, each), the approximate reciprocal / square root / quotient of the
+    FP32 arithmetic (a few ulp) and their propagation through the stencil
+    (the stage adds dt L, a fraction of the value, whose own relative error
+    is that of a difference of face fluxes): a few ulps on average, relative
+    L1 <= 8 ulp (4.8e-7; measured 0.7-1.7 ulp), and tens of ulps in the
+    worst cell, max relative <= 168 ulp (1e-5; measured up to 18 ulp).  The
+    max bound keeps room for a limiter decision of PPM or of the HLLC region
+    taken at a near-tie, which FP32 may decide the other way than FP64."""
+    l1 = G.rel_l1(lay, got, ref)
+    mx = G.max_rel_err(lay, got, ref)
+    print(f"fp32 vs oracle {tag}: rel_l1 max {max(l1):.3e} max_rel max {max(mx):.3e}")
+    assert max(l1) <= TOL_FP32_L1, (tag, l1)
+    assert max(mx) <= TOL_FP32_MAX, (tag, mx)
+
+
 COLS = {"hydro1": (256, "columns"), "hydro2": (256, "columns"), "rad1": (256, "strided"),
         "rad2": (256, "strided")}
 
@@ -191,8 +214,8 @@ COLS = {"hydro1": (256, "columns"), "hydro2": (256, "columns"), "rad1": (256, "s
 def test_column_hydro_stages_match_oracle(torch_cuda, lay, recon, flat):
     """The plane-marching form of the hydro stage (16 x 16 columns walking
     along z, partial footprints, z chunks): FP64 agrees with the oracle to
-    1e-12 per stage; FP32 agrees with the 8^3-tile FP32 kernel to FP32
-    rounding (the same formulas in another order of work)."""
+    1e-12 per stage; FP32 (columns and 8^3 tiles) agrees with the FP64
+    oracle within the FP32 bounds of _check_fp32_stage."""
     torch = torch_cuda
     prob, prm = _random_rhd(lay, 4)
     prm["hydro_only"] = 1
@@ -230,9 +253,9 @@ def test_column_hydro_stages_match_oracle(torch_cuda, lay, recon, flat):
             e2 = G.max_rel_err(lay, c2, U2r)
             assert max(e1) <= TOL_STAGE and max(e2) <= TOL_STAGE, (e1, e2)
         else:
-            e1 = G.max_rel_err(lay, c1, t1)
-            e2 = G.max_rel_err(lay, c2, t2)
-            assert max(e1) <= 1e-5 and max(e2) <= 1e-5, (e1, e2)
+            for tag, a, ref in (("col1", c1, U1r), ("col2", c2, U2r), ("tile1", t1, U1r),
+                                ("tile2", t2, U2r)):
+                _check_fp32_stage(lay, a, ref, tag)
 
 
 def test_column_hydro_ten_steps_fp64(torch_cuda):
@@ -288,7 +311,8 @@ def test_column_rad_stages_match_oracle(torch_cuda, lay, kappa0, closure):
     """The plane-marching form of the radiation stage (16 x 16 columns along
     z; partial footprints, z chunks, superluminal fallbacks, the optical-depth
     correction, the three closures): FP64 agrees with the oracle to 1e-12 per
-    stage; FP32 agrees with the 8^3-tile FP32 kernel to FP32 rounding."""
+    stage; FP32 (columns and 8^3 tiles) agrees with the FP64 oracle within
+    the FP32 bounds of _check_fp32_stage."""
     torch = torch_cuda
     prob, prm = _random_rhd(lay, 4, kappa0)
     prm["closure"] = closure
@@ -325,9 +349,9 @@ def test_column_rad_stages_match_oracle(torch_cuda, lay, kappa0, closure):
             e2 = G.max_rel_err(lay, c2, R2r)
             assert max(e1) <= TOL_STAGE and max(e2) <= TOL_STAGE, (e1, e2)
         else:
-            e1 = G.max_rel_err(lay, c1, t1)
-            e2 = G.max_rel_err(lay, c2, t2)
-            assert max(e1) <= 1e-5 and max(e2) <= 1e-5, (e1, e2)
+            for tag, a, ref in (("col1", c1, R1r), ("col2", c2, R2r), ("tile1", t1, R1r),
+                                ("tile2", t2, R2r)):
+                _check_fp32_stage(lay, a, ref, tag)
 
 
 @pytest.mark.parametrize("kappa_mode", [0, 1], ids=["kconst", "krho"])
