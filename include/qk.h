@@ -301,6 +301,22 @@ int qk_step_compensated(qk_ctx *ctx, void *const hydro[5], void *const rad[4],
                         void *const hydro_lo[5], void *const rad_lo[4], double *dt_out,
                         int32_t *nsub_out, void *stream);
 
+/* Storage of the low parts of a compensated state (qk_step_compensated,
+ * qk_conserved_sums_compensated).  QK_LO_F32 (the default): float arrays, the
+ * value hi + lo held to ~48 bits in 8 bytes.  QK_LO_I16: int16 arrays (the
+ * caller's hydro_lo / rad_lo then hold 2-byte elements), lo kept as the
+ * integer k = rint(lo 2^(38 - E)), E the binary exponent of hi, i.e. to 2^-15
+ * of an FP32 ulp of hi: ~39 significant bits in 6 bytes per value, three
+ * quarters of FP64's bytes, with the same exact telescoping of the face terms
+ * in the accumulation (every store rounds the value once, at ~2^-40).  Values
+ * below ~2^-100 in magnitude keep hi only.  Not a passage of the paper (a
+ * storage choice of the conservative update, Sec. 2.2).  Changing the format
+ * releases the library's stage-1 low parts and the captured compensated step.
+ * QK_EINVAL for another value. */
+#define QK_LO_F32 1
+#define QK_LO_I16 2
+int qk_set_lo_format(qk_ctx *ctx, int32_t fmt);
+
 /* The device step record (synchronises `stream`): out[0] = dt, out[1] = N_sub,
  * out[2] = dt_rad, out[3] = max(|v| + c_s) of the last timestep computed;
  * out[4] = radiation substeps and out[5] = timesteps summed since the context

@@ -1176,8 +1176,8 @@ static int enqueue_step(qk_ctx *c, void *const hydro[5], void *const rad[4], cud
   for (int q = 0; q < 4; ++q) R1[q] = c->scratch[5 + q];
   for (int q = 0; q < 5; ++q) U1l[q] = c->scratch_lo[q];
   for (int q = 0; q < 4; ++q) R1l[q] = c->scratch_lo[5 + q];
-  const LoPtrs h1{hlo, nullptr, U1l}, h2{hlo, U1l, hlo};
-  const LoPtrs r1{rlo, nullptr, R1l}, r2{rlo, R1l, rlo};
+  const LoPtrs h1{hlo, nullptr, U1l, c->lo_fmt}, h2{hlo, U1l, hlo, c->lo_fmt};
+  const LoPtrs r1{rlo, nullptr, R1l, c->lo_fmt}, r2{rlo, R1l, rlo, c->lo_fmt};
   const DtSrc dth{c->d_si, 0.0, 0, -1};
   const DtSrc none{nullptr, 0.0, 0, -1};
   QK_CUDA(c, launch_max_speed(c->fp32, g, c->p, hydro, c->d_si, s));
@@ -1200,7 +1200,7 @@ static int enqueue_step(qk_ctx *c, void *const hydro[5], void *const rad[4], cud
       } else {
         QK_CUDA(c, rad_launches(c, 2, rad, R1, rad, hydro[0], dr, s, rlo ? &r2 : nullptr));
         QK_CUDA(c, launch_exchange(c->fp32, g, c->p, hydro, rad, c->src, dr, c->d_status, s, hlo,
-                                   rlo));
+                                   rlo, c->lo_fmt));
       }
     }
   }
@@ -1354,7 +1354,8 @@ int qk_step_compensated(qk_ctx *c, void *const hydro[5], void *const rad[4],
   if ((rc = need_dirichlet(c))) return rc;
   for (int f = 0; f < 9; ++f)
     if (!c->scratch_lo[f]) {
-      cudaError_t e = cudaMalloc(&c->scratch_lo[f], (size_t)c->field_len * c->elem);
+      const size_t lo_elem = c->lo_fmt == QK_LO_I16 ? 2 : 4;
+      cudaError_t e = cudaMalloc(&c->scratch_lo[f], (size_t)c->field_len * lo_elem);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(compensation scratch)");
     }
   cudaStream_t s = (cudaStream_t)stream;
@@ -1410,10 +1411,28 @@ int qk_conserved_sums_compensated(qk_ctx *c, void *const hydro[5], void *const r
   if (!out) return fail(c, QK_EINVAL, "out is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   QK_CUDA(c, launch_sums(c->fp32, geom(c), c->p, hydro, rad, c->d_partials, c->sum_blocks,
-                         c->d_sums, s, hydro_lo, rad ? rad_lo : nullptr));
+                         c->d_sums, s, hydro_lo, rad ? rad_lo : nullptr, c->lo_fmt));
   QK_CUDA(c, cudaMemcpyAsync(c->h_buf, c->d_sums, QK_NSUMS * sizeof(double), cudaMemcpyDeviceToHost, s));
   QK_CUDA(c, cudaStreamSynchronize(s));
   memcpy(out, c->h_buf, QK_NSUMS * sizeof(double));
+  return QK_OK;
+}
+
+int qk_set_lo_format(qk_ctx *c, int32_t fmt) {
+  if (!c) return QK_EINVAL;
+  if (fmt != QK_LO_F32 && fmt != QK_LO_I16)
+    return fail(c, QK_EINVAL, "unknown low-part format %d", fmt);
+  if (fmt == c->lo_fmt) return QK_OK;
+  // the stage-1 low parts and the captured step change with the format
+  for (void *&p : c->scratch_lo) {
+    cudaFree(p);
+    p = nullptr;
+  }
+  if (c->gexec_c) {
+    cudaGraphExecDestroy(c->gexec_c);
+    c->gexec_c = nullptr;
+  }
+  c->lo_fmt = fmt;
   return QK_OK;
 }
 

@@ -31,7 +31,7 @@ __device__ __forceinline__ long long cell_to_elem(const Geometry &g, long long c
 // -------------------------------------------------------------- exchange ---
 // One thread per interior cell (grid-stride over the flat cell index); the
 // per-cell arithmetic is in qk_exchange.cuh.
-template <bool CP>
+template <int CP>
 __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_params p,
                                                               F5<float> U, F4<float> R,
                                                               const float *src, DtSrc dts,
@@ -47,13 +47,14 @@ __global__ void __launch_bounds__(256) exchange_kernel_mixed(Geometry g, qk_para
     const long long e = cell_to_elem(g, cidx);
     const float fr[3] = {R.f[1][e], R.f[2][e], R.f[3][e]};
     float fl[3] = {0.0f, 0.0f, 0.0f}, el = 0.0f;
+    const float er = R.f[0][e];
     if constexpr (CP) {
-      el = RL.f[0][e];
-      fl[0] = RL.f[1][e];
-      fl[1] = RL.f[2][e];
-      fl[2] = RL.f[3][e];
+      el = lo_get<CP>(RL.f[0], e, er);
+      fl[0] = lo_get<CP>(RL.f[1], e, fr[0]);
+      fl[1] = lo_get<CP>(RL.f[2], e, fr[1]);
+      fl[2] = lo_get<CP>(RL.f[3], e, fr[2]);
     }
-    exchange_cell_mixed<CP>(p, K, dt, dtf, U, R, UL, RL, src, e, R.f[0][e], el, fr, fl, xs);
+    exchange_cell_mixed<CP>(p, K, dt, dtf, U, R, UL, RL, src, e, er, el, fr, fl, xs);
   }
   exchange_status(st, xs.max, xs.flags, xs.bad);
 }
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(256) exchange_kernel(Geometry g, qk_params p, 
 
 cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                             void *const *R, const void *src, DtSrc dt, Status *st,
-                            cudaStream_t s, void *const *Ulo, void *const *Rlo) {
+                            cudaStream_t s, void *const *Ulo, void *const *Rlo, int lofmt) {
   int nsm = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -90,11 +91,15 @@ cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, voi
     if (Ulo) {
       for (int q = 0; q < 5; ++q) ul.f[q] = (float *)Ulo[q];
       for (int q = 0; q < 4; ++q) rl.f[q] = (float *)Rlo[q];
-      exchange_kernel_mixed<true><<<grid, 256, 0, s>>>(g, p, u, r, (const float *)src, dt, st,
-                                                       ul, rl);
+      if (lofmt == 2)
+        exchange_kernel_mixed<2><<<grid, 256, 0, s>>>(g, p, u, r, (const float *)src, dt, st,
+                                                      ul, rl);
+      else
+        exchange_kernel_mixed<1><<<grid, 256, 0, s>>>(g, p, u, r, (const float *)src, dt, st,
+                                                      ul, rl);
     } else {
-      exchange_kernel_mixed<false><<<grid, 256, 0, s>>>(g, p, u, r, (const float *)src, dt, st,
-                                                        ul, rl);
+      exchange_kernel_mixed<0><<<grid, 256, 0, s>>>(g, p, u, r, (const float *)src, dt, st,
+                                                    ul, rl);
     }
   } else {
     F5<double> u; F4<double> r;
@@ -381,7 +386,7 @@ __device__ __forceinline__ DD dd_add(DD a, DD b) {
 
 constexpr int SUM_NT = 256;
 
-template <typename T>
+template <typename T, int CP>
 __global__ void __launch_bounds__(SUM_NT) sums_kernel(Geometry g, double cr, double icc, F5<T> U,
                                                       F4<T> R, int has_rad, double *partials,
                                                       F5<T> UL, F4<T> RL) {
@@ -397,12 +402,12 @@ __global__ void __launch_bounds__(SUM_NT) sums_kernel(Geometry g, double cr, dou
 #pragma unroll
     for (int q = 0; q < 4; ++q) x[5 + q] = has_rad ? (double)R.f[q][e] : 0.0;
     // compensated FP32 state: the value is hi + lo (exact in double)
-    if (UL.f[0]) {
+    if constexpr (CP != 0) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) x[q] += (double)UL.f[q][e];
+      for (int q = 0; q < 5; ++q) x[q] += (double)lo_get<CP>(UL.f[q], e, U.f[q][e]);
       if (has_rad) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) x[5 + q] += (double)RL.f[q][e];
+        for (int q = 0; q < 4; ++q) x[5 + q] += (double)lo_get<CP>(RL.f[q], e, R.f[q][e]);
       }
     }
     x[9] = x[4] + cr * x[5];
@@ -438,7 +443,7 @@ __global__ void sums_final_kernel(const double *partials, int nblocks, double vo
 
 cudaError_t launch_sums(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                         void *const *R, double *partials, int nblocks, double *out,
-                        cudaStream_t s, void *const *Ulo, void *const *Rlo) {
+                        cudaStream_t s, void *const *Ulo, void *const *Rlo, int lofmt) {
   const double cr = p.c / p.chat, icc = 1.0 / (p.c * p.chat);
   const double vol = p.dx[0] * p.dx[1] * p.dx[2];
   const int has_rad = R != nullptr;
@@ -450,12 +455,21 @@ cudaError_t launch_sums(int fp32, const Geometry &g, const qk_params &p, void *c
       for (int q = 0; q < 5; ++q) ul.f[q] = (float *)Ulo[q];
       if (has_rad) for (int q = 0; q < 4; ++q) rl.f[q] = (float *)Rlo[q];
     }
-    sums_kernel<float><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials, ul, rl);
+    if (!Ulo)
+      sums_kernel<float, 0><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials, ul,
+                                                       rl);
+    else if (lofmt == 2)
+      sums_kernel<float, 2><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials, ul,
+                                                       rl);
+    else
+      sums_kernel<float, 1><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials, ul,
+                                                       rl);
   } else {
     F5<double> u, ul{}; F4<double> r{}, rl{};
     for (int q = 0; q < 5; ++q) u.f[q] = (double *)U[q];
     if (has_rad) for (int q = 0; q < 4; ++q) r.f[q] = (double *)R[q];
-    sums_kernel<double><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials, ul, rl);
+    sums_kernel<double, 0><<<nblocks, SUM_NT, 0, s>>>(g, cr, icc, u, r, has_rad, partials, ul,
+                                                      rl);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

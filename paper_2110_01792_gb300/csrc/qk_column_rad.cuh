@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
           } else {
             const float fl[3] = {0.0f, 0.0f, 0.0f};
             F4<float> none{};
-            exchange_cell_mixed<false>(p, xf.K, dt_of(dts), dt, xf.U, Ro, xf.UL, none, xf.src, e,
+            exchange_cell_mixed<0>(p, xf.K, dt_of(dts), dt, xf.U, Ro, xf.UL, none, xf.src, e,
                                        rv[0], 0.0f, rv + 1, fl, xs, &sm.pre[8][t], CNT);
           }
         }

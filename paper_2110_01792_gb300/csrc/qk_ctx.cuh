@@ -67,6 +67,7 @@ struct qk_ctx {
   int sum_blocks = 0;
   void *scratch[9] = {};
   void *scratch_lo[9] = {};  // low parts of the stage-1 results (compensated steps)
+  int lo_fmt = QK_LO_F32;    // storage of the low parts (QK_LO_F32 or QK_LO_I16)
   void *chi = nullptr;   // shock-flattening coefficient (one field)
   const void *src = nullptr;  // caller's emissivity field j of the exchange, or none
   size_t elem = 8;

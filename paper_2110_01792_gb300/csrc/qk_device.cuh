@@ -198,6 +198,39 @@ __device__ __forceinline__ float fscale(float m, int ex) {
   return __uint_as_float((u & 0x807fffffu) | ((unsigned)be << 23));
 }
 
+// Storage of the low parts of a compensated FP32 state (hi + lo per conserved
+// value).  CP = 1: lo as an FP32 value (8 bytes per value in all).  CP = 2: lo
+// in 16 bits as the integer k = rint(lo 2^(38 - E)), E the binary exponent of
+// hi: after renormalisation |lo| <= ulp(hi)/2 = 2^(E - 24), so |k| <= 2^14, and
+// lo is kept to 2^-15 ulp(hi): a 39-bit significand in 6 bytes per value.  A
+// CP = 2 array travels as float* and is read and written as int16.  lo is
+// dropped (k = 0) where it is zero or below the normal FP32 range (|hi| below
+// ~2^-100), and decodes to zero below 2^(E - 38) = 2^-126.
+template <int CP>
+__device__ __forceinline__ float lo_get(const float *p, long long e, float hi) {
+  if constexpr (CP == 2) {
+    const int k = reinterpret_cast<const short *>(p)[e];
+    if (k == 0) return 0.0f;
+    const int E = (int)((__float_as_uint(hi) >> 23) & 0xffu) - 127;
+    return fscale((float)k, E - 38);
+  } else {
+    return p[e];
+  }
+}
+template <int CP>
+__device__ __forceinline__ void lo_put(float *p, long long e, float hi, float lo) {
+  if constexpr (CP == 2) {
+    int k = 0;
+    if ((__float_as_uint(lo) & 0x7f800000u) != 0u) {
+      const int E = (int)((__float_as_uint(hi) >> 23) & 0xffu) - 127;
+      k = min(max(__float2int_rn(fscale(lo, 38 - E)), -32767), 32767);
+    }
+    reinterpret_cast<short *>(p)[e] = (short)k;
+  } else {
+    p[e] = lo;
+  }
+}
+
 // Double-float values (h + l, |l| <= ulp(h)/2, ~48 significant bits) for
 // arithmetic that needs more than FP32 without the FP64 pipe (Dekker 1971;
 // Knuth's TwoSum; FMA TwoProduct), on round-to-nearest intrinsics so that no

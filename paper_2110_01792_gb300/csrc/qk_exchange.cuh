@@ -352,7 +352,7 @@ __device__ __forceinline__ DF df_of_double(double x) {
   return DF{h, (float)(x - (double)h)};
 }
 
-template <bool CP>
+template <int CP>
 __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const ExK &K, double dt,
                                                     float dtf, F5<float> U, F4<float> R,
                                                     F5<float> UL, F4<float> RL, const float *src,
@@ -372,7 +372,7 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
   DF Er0{er, 0.0f};
   float E_lo = 0.0f;
   if constexpr (CP) {
-    E_lo = UL.f[4][e];
+    E_lo = lo_get<CP>(UL.f[4], e, u[4]);
     Eg0 = df_add_f(Eg0, E_lo);
     Er0 = df_of(er, er_lo);
   }
@@ -449,15 +449,15 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
       df_add(Fh, Fl, dF);
       df_norm(Fh, Fl);
       R.f[1 + a][e] = Fh;
-      RL.f[1 + a][e] = Fl;
+      lo_put<CP>(RL.f[1 + a], e, Fh, Fl);
       const float p1 = __fmul_rn(dF, K.icc);
       const float e1 = fmaf(dF, K.icc, -p1) + dF * K.icc_lo;
-      float mh = u[1 + a], ml = UL.f[1 + a][e];
+      float mh = u[1 + a], ml = lo_get<CP>(UL.f[1 + a], e, u[1 + a]);
       df_add(mh, ml, -p1);
       ml = __fsub_rn(ml, e1);
       df_norm(mh, ml);
       U.f[1 + a][e] = mh;
-      UL.f[1 + a][e] = ml;
+      lo_put<CP>(UL.f[1 + a], e, mh, ml);
       mn[a] = mh;
     } else {
       const float Fn = F0 * damp;
@@ -477,9 +477,9 @@ __device__ __forceinline__ void exchange_cell_mixed(const qk_params &p, const Ex
     const DF Ekin0 = df_sub(df_of(u[4], E_lo), Eg0);
     Er_new = df_sub(Er, df_mul(K.rc_df, df_add_f(df_neg(Ekin0), Ekin1)));
     U.f[4][e] = Enew.h;
-    UL.f[4][e] = Enew.l;
+    lo_put<CP>(UL.f[4], e, Enew.h, Enew.l);
     R.f[0][e] = Er_new.h;
-    RL.f[0][e] = Er_new.l;
+    lo_put<CP>(RL.f[0], e, Er_new.h, Er_new.l);
   } else {
     const float dEkin = 0.5f * (ke1 - ke0) * rinv;
     Er_new = df_add_f(Er, -K.rc * dEkin);

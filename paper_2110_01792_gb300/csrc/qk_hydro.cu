@@ -17,7 +17,7 @@ template <typename T> struct HydroSmem {
   T iface[kF ? 5 : 1][kF ? NIF : 1];  // FP64 PPM: interface values, once per face
 };
 
-template <typename T, int D, int NT, int NOWN, bool CP>
+template <typename T, int D, int NT, int NOWN, int CP>
 __device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T inv_dx, T gamma,
                                           T gm1inv, T g1, int rk, const T *chi,
                                           const DevBox &bx, int ng, int x0, int y0, int z0,
@@ -120,9 +120,10 @@ __device__ __forceinline__ void hydro_dir(HydroSmem<T> &sm, const int v[3], T in
 }
 
 // CP (FP32 only): compensated state, every conserved field held as hi + lo
-// (L0, L1, Lo the lo arrays of U0, U1, Uo); the stencil reads hi only, the
+// (L0, L1, Lo the lo arrays of U0, U1, Uo, stored as lo_get / lo_put read and
+// write them: CP = 1 FP32, CP = 2 16 bits); the stencil reads hi only, the
 // update is accumulated in double-float so that the face terms telescope.
-template <typename T, int STAGE, int NT, bool CP>
+template <typename T, int STAGE, int NT, int CP>
 __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p, SC<T> K,
                                                          F5<T> U0, F5<T> U1, F5<T> Uo, DtSrc dts,
                                                          int sched, const T *chi, F5<T> L0,
@@ -172,7 +173,8 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
       if constexpr (CP) {
         if (i < v[0] && j < v[1] && k < v[2]) {
 #pragma unroll
-          for (int q = 0; q < 5; ++q) ownl[m][q] = (STAGE == 1 ? L0 : L1).f[q][e];
+          for (int q = 0; q < 5; ++q)
+            ownl[m][q] = lo_get<CP>((STAGE == 1 ? L0 : L1).f[q], e, own[m][q]);
         }
       }
     }
@@ -218,8 +220,9 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
           // (acc, accl) = U^s - dt div F; stage 2 averages it with U^0
           T h = acc[m][q], l = accl[m][q];
           if (STAGE == 2) {
-            df_add(h, l, U0.f[q][e]);
-            l = __fadd_rn(l, L0.f[q][e]);
+            const T u0h = U0.f[q][e];
+            df_add(h, l, u0h);
+            l = __fadd_rn(l, lo_get<CP>(L0.f[q], e, u0h));
           }
           df_norm(h, l);
           if (STAGE == 2) {
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
             l *= T(0.5);
           }
           Uo.f[q][e] = h;
-          Lo.f[q][e] = l;
+          lo_put<CP>(Lo.f[q], e, h, l);
         } else {
           T L = -acc[m][q];
           if (STAGE == 1) {
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(NT) hydro_stage_kernel(Geometry g, qk_params p
   }
 }
 
-template <typename T, int STAGE, int NT, bool CP>
+template <typename T, int STAGE, int NT, int CP>
 static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const *U0,
                               void *const *U1, void *const *Uo, DtSrc dt, int grid, int sched,
                               const void *chi, const LoPtrs &lo, cudaStream_t s) {
@@ -276,15 +279,23 @@ static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const
   return cudaGetLastError();
 }
 
-template <typename T, int STAGE, bool CP>
+template <typename T, int STAGE, int CP>
 static cudaError_t launch_nt(const Geometry &g, const qk_params &p, void *const *U0,
                              void *const *U1, void *const *Uo, DtSrc dt, int grid, int cfg,
                              const void *chi, const LoPtrs &lo, cudaStream_t s) {
   const int sched = cfg_sched(cfg);
-  switch (cfg_threads(cfg)) {
-    case 128: return launch_one<T, STAGE, 128, CP>(g, p, U0, U1, Uo, dt, grid, sched, chi, lo, s);
-    case 512: return launch_one<T, STAGE, 512, CP>(g, p, U0, U1, Uo, dt, grid, sched, chi, lo, s);
-    default: return launch_one<T, STAGE, 256, CP>(g, p, U0, U1, Uo, dt, grid, sched, chi, lo, s);
+  // the 16-bit compensated form exists for 256 threads per tile only
+  if constexpr (CP == 2) {
+    return launch_one<T, STAGE, 256, CP>(g, p, U0, U1, Uo, dt, grid, sched, chi, lo, s);
+  } else {
+    switch (cfg_threads(cfg)) {
+      case 128:
+        return launch_one<T, STAGE, 128, CP>(g, p, U0, U1, Uo, dt, grid, sched, chi, lo, s);
+      case 512:
+        return launch_one<T, STAGE, 512, CP>(g, p, U0, U1, Uo, dt, grid, sched, chi, lo, s);
+      default:
+        return launch_one<T, STAGE, 256, CP>(g, p, U0, U1, Uo, dt, grid, sched, chi, lo, s);
+    }
   }
 }
 
@@ -295,15 +306,18 @@ cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_
   // columns (shape 1) when the geometry has them; compensated states use tiles
   if (cfg_shape(cfg) == 1 && g.cols && g.ncols > 0 && !lo)
     return launch_hydro_column(fp32, stage, g, p, U0, U1, Uout, dt, chi, s);
+  if (fp32 && lo && lo->fmt == 2)
+    return stage == 1 ? launch_nt<float, 1, 2>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s)
+                      : launch_nt<float, 2, 2>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s);
   if (fp32 && lo)
-    return stage == 1 ? launch_nt<float, 1, true>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s)
-                      : launch_nt<float, 2, true>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s);
+    return stage == 1 ? launch_nt<float, 1, 1>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s)
+                      : launch_nt<float, 2, 1>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s);
   const LoPtrs none{};
   if (fp32)
-    return stage == 1 ? launch_nt<float, 1, false>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s)
-                      : launch_nt<float, 2, false>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s);
-  return stage == 1 ? launch_nt<double, 1, false>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s)
-                    : launch_nt<double, 2, false>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s);
+    return stage == 1 ? launch_nt<float, 1, 0>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s)
+                      : launch_nt<float, 2, 0>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s);
+  return stage == 1 ? launch_nt<double, 1, 0>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s)
+                    : launch_nt<double, 2, 0>(g, p, U0, U1, Uout, dt, grid, cfg, chi, none, s);
 }
 
 // ------------------------------------------------------------- flattening ---

@@ -273,6 +273,7 @@ struct LoPtrs {
   void *const *l0;
   void *const *l1;
   void *const *lo;
+  int fmt = 1;  // storage of the low parts: 1 FP32, 2 16-bit (see lo_get / lo_put)
 };
 
 cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
@@ -303,7 +304,7 @@ cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_pa
 cudaError_t launch_exchange(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                             void *const *R, const void *src, DtSrc dt, Status *st,
                             cudaStream_t s, void *const *Ulo = nullptr,
-                            void *const *Rlo = nullptr);
+                            void *const *Rlo = nullptr, int lofmt = 1);
 cudaError_t launch_max_speed(int fp32, const Geometry &g, const qk_params &p,
                              void *const *U, StepInfo *si, cudaStream_t s);
 cudaError_t launch_halo(int fp32, int pack, const Copy *copies, const Chunk *chunks, int nchunks,
@@ -314,7 +315,8 @@ cudaError_t launch_ghost_fill(int fp32, const Copy *copies, const Chunk *chunks,
                               void *const *fields, int nf, int first, DtSrc pred, cudaStream_t s);
 cudaError_t launch_sums(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                         void *const *R, double *partials, int nblocks, double *out,
-                        cudaStream_t s, void *const *Ulo = nullptr, void *const *Rlo = nullptr);
+                        cudaStream_t s, void *const *Ulo = nullptr, void *const *Rlo = nullptr,
+                        int lofmt = 1);
 int hydro_smem_bytes(int fp32);
 int rad_smem_bytes(int fp32);
 cudaError_t stage_kernel_setup(int fp32);

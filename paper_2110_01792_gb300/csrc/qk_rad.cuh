@@ -135,7 +135,7 @@ __device__ __forceinline__ void rad_face_hll(T wL[4], T wR[4], Fallback fallback
   out[1 + D] = fma(alL, fLD, fma(alR, fRD, fma(cEbL, aL, cEbR * aR)));
 }
 
-template <typename T, int D, int NT, int NOWN, int CL, bool CP>
+template <typename T, int D, int NT, int NOWN, int CL, int CP>
 __device__ __forceinline__ void rad_dir(RadSmem<T> &sm, const int v[3], T inv_dx, T dx, T c,
                                         T chat, int tau_corr, int rk, T (&acc)[NOWN][4],
                                         T (&accl)[NOWN][4], T cdt) {
@@ -261,7 +261,7 @@ template <typename T, int NT, bool EX> struct RadMinBlocks {
   static constexpr int value = (EX && sizeof(T) == 4) ? (NT == 128 ? 6 : (NT == 256 ? 3 : 1)) : 1;
 };
 
-template <typename T, int STAGE, int NT, int CL, bool CP, bool EX>
+template <typename T, int STAGE, int NT, int CL, int CP, bool EX>
 __device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_params &p,
                                                const SC<T> &K, F4<T> R0, F4<T> R1, F4<T> Ro,
                                                const T *rho, DtSrc dts, int sched, F4<T> L0,
@@ -309,7 +309,8 @@ __device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_param
       if constexpr (CP) {
         if (i < v[0] && j < v[1] && k < v[2]) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) ownl[m][q] = (STAGE == 1 ? L0 : L1).f[q][e];
+          for (int q = 0; q < 4; ++q)
+            ownl[m][q] = lo_get<CP>((STAGE == 1 ? L0 : L1).f[q], e, own[m][q]);
         }
       }
     }
@@ -352,8 +353,9 @@ __device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_param
         if constexpr (CP) {
           T h = acc[m][q], l = accl[m][q];
           if (STAGE == 2) {
-            df_add(h, l, R0.f[q][e]);
-            l = __fadd_rn(l, L0.f[q][e]);
+            const T r0h = R0.f[q][e];
+            df_add(h, l, r0h);
+            l = __fadd_rn(l, lo_get<CP>(L0.f[q], e, r0h));
           }
           df_norm(h, l);
           if (STAGE == 2) {
@@ -376,7 +378,7 @@ __device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_param
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         Ro.f[q][e] = rv[q];
-        if constexpr (CP) Lo.f[q][e] = rl[q];
+        if constexpr (CP) lo_put<CP>(Lo.f[q], e, rv[q], rl[q]);
       }
     }
     if constexpr (EX) {
@@ -396,14 +398,15 @@ __device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_param
         } else {
           const float fr[3] = {Ro.f[1][e], Ro.f[2][e], Ro.f[3][e]};
           float fl[3] = {0.0f, 0.0f, 0.0f}, el = 0.0f;
+          const float er = Ro.f[0][e];
           if constexpr (CP) {
-            el = Lo.f[0][e];
-            fl[0] = Lo.f[1][e];
-            fl[1] = Lo.f[2][e];
-            fl[2] = Lo.f[3][e];
+            el = lo_get<CP>(Lo.f[0], e, er);
+            fl[0] = lo_get<CP>(Lo.f[1], e, fr[0]);
+            fl[1] = lo_get<CP>(Lo.f[2], e, fr[1]);
+            fl[2] = lo_get<CP>(Lo.f[3], e, fr[2]);
           }
-          exchange_cell_mixed<CP>(p, xf.K, dt_of(dts), dt, xf.U, Ro, xf.UL, Lo, xf.src, e,
-                                  Ro.f[0][e], el, fr, fl, xs);
+          exchange_cell_mixed<CP>(p, xf.K, dt_of(dts), dt, xf.U, Ro, xf.UL, Lo, xf.src, e, er,
+                                  el, fr, fl, xs);
         }
       }
     }
@@ -411,7 +414,7 @@ __device__ __forceinline__ void rad_stage_body(const Geometry &g, const qk_param
   if constexpr (EX) exchange_status(xf.st, xs.max, xs.flags, xs.bad);
 }
 
-template <typename T, int STAGE, int NT, int CL, bool CP>
+template <typename T, int STAGE, int NT, int CL, int CP>
 __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, SC<T> K,
                                                        F4<T> R0, F4<T> R1, F4<T> Ro, const T *rho,
                                                        DtSrc dts, int sched, F4<T> L0, F4<T> L1,
@@ -420,7 +423,7 @@ __global__ void __launch_bounds__(NT) rad_stage_kernel(Geometry g, qk_params p, 
                                               xf);
 }
 
-template <typename T, int NT, int CL, bool CP>
+template <typename T, int NT, int CL, int CP>
 __global__ void __launch_bounds__(NT, (RadMinBlocks<T, NT, true>::value))
     rad_stage_ex_kernel(Geometry g, qk_params p, SC<T> K, F4<T> R0, F4<T> R1, F4<T> Ro,
                         const T *rho, DtSrc dts, int sched, F4<T> L0, F4<T> L1, F4<T> Lo,
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(NT, (RadMinBlocks<T, NT, true>::value))
   rad_stage_body<T, 2, NT, CL, CP, true>(g, p, K, R0, R1, Ro, rho, dts, sched, L0, L1, Lo, xf);
 }
 
-template <typename T, int STAGE, int NT, int CL, bool CP>
+template <typename T, int STAGE, int NT, int CL, int CP>
 static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const *R0,
                               void *const *R1, void *const *Ro, const void *rho, DtSrc dt,
                               int grid, int sched, const LoPtrs &lo, const FuseArgs *fx,
@@ -475,19 +478,27 @@ static cudaError_t launch_one(const Geometry &g, const qk_params &p, void *const
   return cudaGetLastError();
 }
 
-template <typename T, int STAGE, int CL, bool CP>
+template <typename T, int STAGE, int CL, int CP>
 static cudaError_t launch_nt(const Geometry &g, const qk_params &p, void *const *R0,
                              void *const *R1, void *const *Ro, const void *rho, DtSrc dt,
                              int grid, int cfg, const LoPtrs &lo, const FuseArgs *fx,
                              cudaStream_t s) {
   const int sched = cfg_sched(cfg);
-  switch (cfg_threads(cfg)) {
-    case 128:
-      return launch_one<T, STAGE, 128, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, fx, s);
-    case 512:
-      return launch_one<T, STAGE, 512, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, fx, s);
-    default:
-      return launch_one<T, STAGE, 256, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, fx, s);
+  // the 16-bit compensated form exists for 256 threads per tile only
+  if constexpr (CP == 2) {
+    return launch_one<T, STAGE, 256, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, fx, s);
+  } else {
+    switch (cfg_threads(cfg)) {
+      case 128:
+        return launch_one<T, STAGE, 128, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, fx,
+                                                 s);
+      case 512:
+        return launch_one<T, STAGE, 512, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, fx,
+                                                 s);
+      default:
+        return launch_one<T, STAGE, 256, CL, CP>(g, p, R0, R1, Ro, rho, dt, grid, sched, lo, fx,
+                                                 s);
+    }
   }
 }
 
@@ -499,18 +510,22 @@ cudaError_t launch_rad_closure(int fp32, int stage, const Geometry &g, const qk_
                                void *const *R0, void *const *R1, void *const *Rout,
                                const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s,
                                const LoPtrs *lo, const FuseArgs *fx) {
+  if (fp32 && lo && lo->fmt == 2)
+    return stage == 1
+               ? launch_nt<float, 1, CL, 2>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, fx, s)
+               : launch_nt<float, 2, CL, 2>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, fx, s);
   if (fp32 && lo)
     return stage == 1
-               ? launch_nt<float, 1, CL, true>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, fx, s)
-               : launch_nt<float, 2, CL, true>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, fx, s);
+               ? launch_nt<float, 1, CL, 1>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, fx, s)
+               : launch_nt<float, 2, CL, 1>(g, p, R0, R1, Rout, rho, dt, grid, cfg, *lo, fx, s);
   const LoPtrs none{};
   if (fp32)
     return stage == 1
-               ? launch_nt<float, 1, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s)
-               : launch_nt<float, 2, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s);
+               ? launch_nt<float, 1, CL, 0>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s)
+               : launch_nt<float, 2, CL, 0>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s);
   return stage == 1
-             ? launch_nt<double, 1, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s)
-             : launch_nt<double, 2, CL, false>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s);
+             ? launch_nt<double, 1, CL, 0>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s)
+             : launch_nt<double, 2, CL, 0>(g, p, R0, R1, Rout, rho, dt, grid, cfg, none, fx, s);
 }
 
 }  // namespace qk

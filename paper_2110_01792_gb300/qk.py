@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build" if os.environ.get("QK_FMAD", "1") != "0"
 OK, EINVAL, ECUDA, ENOCONV, ENEGATIVE = 0, 1, 2, 3, 4
 FP64, FP32_MIXED = 0, 1
 LAUNCH_BATCHED, LAUNCH_PER_PATCH = 0, 1
+LO_F32, LO_I16 = 1, 2
 NSUMS = 13
 _lib = None
 
@@ -119,6 +120,7 @@ def lib():
     L.qk_step_compensated.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), P(dbl), P(i32), vp]
     L.qk_step_host.argtypes = [vp, P(vp), P(vp), P(dbl), P(i32), vp]
     L.qk_conserved_sums_compensated.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), P(dbl), vp]
+    L.qk_set_lo_format.argtypes = [vp, i32]
     for f in ("qk_init_level", "qk_amr_init", "qk_amr_info", "qk_amr_interp", "qk_amr_register",
               "qk_amr_sync", "qk_set_tile_part", "qk_tile_counts", "qk_fill_plan", "qk_fill_ghosts_range", "qk_set_dirichlet", "qk_set_source",
               "qk_init_shard", "qk_halo_info", "qk_halo_pack", "qk_halo_unpack",
@@ -127,7 +129,7 @@ def lib():
               "qk_rad_matter_exchange", "qk_timestep", "qk_step", "qk_conserved_sums",
               "qk_status", "qk_step_info", "qk_eval_math", "qk_eval_convert", "qk_fma_probe",
               "qk_step_compensated", "qk_step_host",
-              "qk_conserved_sums_compensated"):
+              "qk_conserved_sums_compensated", "qk_set_lo_format"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -142,6 +144,28 @@ def eval_math(x, rcp=None, sqrt_out=None, stream=None):
                             _stream(stream))
     if rc != OK:
         raise QKError(rc, "qk_eval_math failed")
+
+
+def lo16_encode(hi, lo):
+    """Host form of the 16-bit low parts (LO_I16): for float32 hi and the
+    residual lo (|lo| <= ulp(hi)/2), k = rint(lo 2^(38 - E)) as int16, E the
+    binary exponent of hi (zero where lo or hi is zero or below the normal
+    float range)."""
+    hi = np.asarray(hi, dtype=np.float32)
+    lo = np.asarray(lo, dtype=np.float64)
+    _, e = np.frexp(hi)
+    E = e.astype(np.int64) - 1
+    k = np.rint(np.ldexp(lo, (38 - E).astype(np.int32)))
+    k = np.where((np.abs(lo) < 2.0 ** -126) | (hi == 0), 0.0, k)
+    return np.clip(k, -32767, 32767).astype(np.int16)
+
+
+def lo16_decode(hi, k):
+    """The low parts held by LO_I16 arrays: lo = k 2^(E - 38) (float64)."""
+    hi = np.asarray(hi, dtype=np.float32)
+    _, e = np.frexp(hi)
+    E = e.astype(np.int64) - 1
+    return np.ldexp(np.asarray(k, dtype=np.float64), (E - 38).astype(np.int32))
 
 
 _CFG_NAMES = ("hydro1", "hydro2", "rad1", "rad2")
@@ -347,6 +371,11 @@ class Context:
         {kernel: (threads, schedule)} like autotune's result."""
         arr = (C.c_int32 * 4)(*[_encode_cfg(cfg[n]) for n in _CFG_NAMES])
         self._check(self._L.qk_set_launch_config(self._h, arr))
+
+    def set_lo_format(self, fmt: int):
+        """Storage of the low parts of compensated states: LO_F32 (float
+        arrays) or LO_I16 (int16 arrays, ~39-bit values in 6 bytes)."""
+        self._check(self._L.qk_set_lo_format(self._h, int(fmt)))
 
     def set_fused_exchange(self, enable: bool):
         self._check(self._L.qk_set_fused_exchange(self._h, 1 if enable else 0))

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -133,3 +134,17 @@ def test_init_shard_rejects_invalid_ownership():
         rc, msg = init(owner, nranks, rank, offs)
         assert rc == qk.EINVAL, (word, rc, msg)
         assert word in msg.lower(), (word, msg)
+
+
+
+def test_lo16_host_encoding_round_trip():
+    """The host form of the 16-bit low parts keeps hi + lo to ~2^-39 of the
+    value over a wide range of magnitudes and signs, with |k| <= 2^14."""
+    from paper_2110_01792_gb300 import qk
+    rng = np.random.Generator(np.random.Philox(5))
+    x = rng.lognormal(0.0, 8.0, 200000) * rng.choice([-1.0, 1.0], 200000)
+    hi = x.astype(np.float32)
+    k = qk.lo16_encode(hi, x - hi.astype(np.float64))
+    back = hi.astype(np.float64) + qk.lo16_decode(hi, k)
+    assert np.abs(k).max() <= 2 ** 14
+    assert np.max(np.abs(back - x) / np.abs(x)) <= 2.0 ** -38

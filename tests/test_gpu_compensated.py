@@ -1,9 +1,11 @@
 """Compensated FP32 state (qk_step_compensated): every conserved field held as
-hi + lo floats.  Against the FP64 oracle it meets the FP32-mixed bound
-(relative L1 <= 1e-5 in every field), and the periodic conserved totals --
-sum rho, sum m, sum (E + (c/chat) E_r), sum (m + F/(c chat)) -- stay constant
-to 1e-13 of their magnitude over 10 steps, where plain FP32 storage drifts by
-rounding at ~1e-11 per step."""
+hi + lo.  Against the FP64 oracle it meets the FP32-mixed bound (relative L1
+<= 1e-5 in every field), and the periodic conserved totals -- sum rho, sum m,
+sum (E + (c/chat) E_r), sum (m + F/(c chat)) -- stay constant over 10 steps,
+where plain FP32 storage drifts by rounding at ~1e-11 per step: to 1e-13 of
+their magnitude with FP32 low parts (~48-bit values), and to the 1e-12 bound
+of the mixed form with 16-bit low parts (QK_LO_I16, ~39-bit values, 6 bytes
+per value)."""
 import numpy as np
 import pytest
 
@@ -14,7 +16,7 @@ from tests import gpu_util as G
 pytestmark = pytest.mark.gpu
 
 TOL_L1 = 1e-5
-TOL_DRIFT = 1e-13
+TOL_DRIFT = {"f32": 1e-13, "i16": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -68,19 +70,33 @@ def _magnitudes(lay, U, R, cr, icc):
     return s(U[0]), mom, etot
 
 
+def _lo_parts(torch, qk, arrays, fmt):
+    """Device low parts of a state given in FP64: the FP32 rounding residual,
+    as floats (f32) or in the 16-bit encoding (i16)."""
+    out = []
+    for a in arrays:
+        hi = a.astype(np.float32)
+        res = a - hi.astype(np.float64)
+        if fmt == "i16":
+            out.append(torch.from_numpy(qk.lo16_encode(hi, res)).cuda())
+        else:
+            out.append(torch.from_numpy(res).float().cuda())
+    return out
+
+
 def _run(torch, lay, prob, prm, nsteps, compensated):
+    """compensated: False (plain FP32 storage), "f32" or "i16" low parts."""
     from paper_2110_01792_gb300 import qk
     ctx = qk.Context(lay, prm, qk.FP32_MIXED)
+    if compensated == "i16":
+        ctx.set_lo_format(qk.LO_I16)
     U = G.dev(prob.U, torch.float32)
     R = G.dev(prob.R, torch.float32) if prob.R is not None else None
     lo = None
     if compensated:
         # the FP32 rounding residual of the initial state is its low part
-        Ul = [torch.from_numpy(a - a.astype(np.float32).astype(np.float64)).float().cuda()
-              for a in prob.U]
-        Rl = ([torch.from_numpy(a - a.astype(np.float32).astype(np.float64)).float().cuda()
-               for a in prob.R] if R is not None else None)
-        lo = (Ul, Rl)
+        lo = (_lo_parts(torch, qk, prob.U, compensated),
+              _lo_parts(torch, qk, prob.R, compensated) if R is not None else None)
     sums = [ctx.conserved_sums(U, R, lo=lo)]
     for _ in range(nsteps):
         ctx.step(U, R, lo=lo)
@@ -89,7 +105,12 @@ def _run(torch, lay, prob, prm, nsteps, compensated):
     ctx.close()
     out = G.host(U) + (G.host(R) if R is not None else [])
     if compensated:
-        extra = G.host(lo[0]) + (G.host(lo[1]) if R is not None else [])
+        los = lo[0] + (lo[1] if R is not None else [])
+        if compensated == "i16":
+            extra = [qk.lo16_decode(h.astype(np.float32), l.cpu().numpy())
+                     for h, l in zip(out, los)]
+        else:
+            extra = G.host(los)
         out = [a + b for a, b in zip(out, extra)]
     return out, np.array(sums), st
 
@@ -102,10 +123,11 @@ def _drift(sums, mags):
             "momentum": max(d[:, 10 + a].max() / mom_m[a] for a in range(3))}
 
 
-def test_compensated_hydro_accuracy_and_conservation(torch_cuda):
+@pytest.mark.parametrize("fmt", ["f32", "i16"])
+def test_compensated_hydro_accuracy_and_conservation(torch_cuda, fmt):
     prob = I.config("hydro32")
     lay, prm = prob.layout, prob.params
-    got, sums, st = _run(torch_cuda, lay, prob, prm, 10, True)
+    got, sums, st = _run(torch_cuda, lay, prob, prm, 10, fmt)
     ref, _ = _oracle(lay, prob, prm, 10)
     l1 = G.rel_l1(lay, got, ref)
     assert max(l1) <= TOL_L1, l1
@@ -113,14 +135,16 @@ def test_compensated_hydro_accuracy_and_conservation(torch_cuda):
     dc = _drift(sums, mags)
     _, sums_plain, _ = _run(torch_cuda, lay, prob, prm, 10, False)
     dp = _drift(sums_plain, mags)
-    assert dc["rho"] <= TOL_DRIFT and dc["E_total"] <= TOL_DRIFT, (dc, dp)
-    assert dc["momentum"] <= TOL_DRIFT, (dc, dp)
+    tol = TOL_DRIFT[fmt]
+    assert dc["rho"] <= tol and dc["E_total"] <= tol, (dc, dp)
+    assert dc["momentum"] <= tol, (dc, dp)
     assert dc["rho"] < dp["rho"] and dc["E_total"] < dp["E_total"], (dc, dp)
 
 
-def test_compensated_rhd_accuracy_and_conservation(torch_cuda):
+@pytest.mark.parametrize("fmt", ["f32", "i16"])
+def test_compensated_rhd_accuracy_and_conservation(torch_cuda, fmt):
     lay, prob, prm = _small_rhd()
-    got, sums, st = _run(torch_cuda, lay, prob, prm, 10, True)
+    got, sums, st = _run(torch_cuda, lay, prob, prm, 10, fmt)
     assert st[0] == 0, st
     ref_U, ref_R = _oracle(lay, prob, prm, 10)
     l1 = G.rel_l1(lay, got, ref_U + ref_R)
@@ -131,6 +155,8 @@ def test_compensated_rhd_accuracy_and_conservation(torch_cuda):
     dc = _drift(sums, mags)
     _, sums_plain, _ = _run(torch_cuda, lay, prob, prm, 10, False)
     dp = _drift(sums_plain, mags)
-    assert dc["rho"] <= TOL_DRIFT and dc["E_total"] <= TOL_DRIFT, (dc, dp)
-    assert dc["momentum"] <= TOL_DRIFT, (dc, dp)
+    tol = TOL_DRIFT[fmt]
+    assert dc["rho"] <= tol and dc["E_total"] <= tol, (dc, dp)
+    assert dc["momentum"] <= tol, (dc, dp)
     assert dc["E_total"] < dp["E_total"], (dc, dp)
+
