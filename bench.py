@@ -470,7 +470,7 @@ def kernel_name(kname: str, fp64: bool, tuned) -> str:
     tname = "double" if fp64 else "float"
     stage_of = {"hydro1": "hydro1", "hydro2": "hydro2", "rad1": "rad1", "rad2": "rad2",
                 "rad2x": "rad2"}
-    cols = bool(tuned) and kname in stage_of and tuned[stage_of[kname]][1] == "columns"
+    cols = bool(tuned) and kname in stage_of and tuned[stage_of[kname]][1].startswith("columns")
     if cols:
         return {"hydro1": f"hydro_column_kernel<{tname},1>",
                 "hydro2": f"hydro_column_kernel<{tname},2>",
@@ -532,8 +532,9 @@ def run_variant(torch, qk, name, prec_name, steps, warmup, autotune=True, per_pa
     time over `steps` full updates after `warmup`), compact: v (cell-updates/s),
     ms (per step), hbm (algorithmic bytes per update x v / measured HBM peak),
     gbs (that algorithmic rate in GB/s), l2 (1: working set below the L2),
-    nsub (mean substeps), cfg (tuned shape per stage kernel: c columns, t
-    tiles); with stage_hbm the HBM fraction of each hydro stage kernel alone."""
+    nsub (mean substeps), cfg (tuned shape per stage kernel: c columns, C
+    columns of 288 threads, t tiles); with stage_hbm the HBM fraction of each
+    hydro stage kernel alone."""
     prob = workload(name)
     p = qk.FP64 if prec_name == "fp64" else qk.FP32_MIXED
     tdt = torch.float64 if p == qk.FP64 else torch.float32
@@ -571,7 +572,8 @@ def run_variant(torch, qk, name, prec_name, steps, warmup, autotune=True, per_pa
     if lay.nbox > 1:
         out["patches"] = lay.nbox
     if tuned:
-        out["cfg"] = "".join("c" if tuned[k][1] == "columns" else "t"
+        out["cfg"] = "".join(("C" if tuned[k][0] > 256 else "c")
+                             if tuned[k][1].startswith("columns") else "t"
                              for k in ("hydro1", "hydro2", "rad1", "rad2"))
     if not ok:
         out["status"] = "exchange error"

@@ -327,7 +327,8 @@ int qk_step_info(qk_ctx *ctx, double out[6], void *stream);
  * 1/2, radiation stage 1/2): the tile shape and schedule -- 8^3 tiles with
  * 128, 256 or 512 threads per CTA (the same shared-memory tile), strided over
  * the grid or one contiguous run of tiles per CTA, or 16 x 16 columns of 256
- * threads marching along z -- each timed with CUDA
+ * threads marching along z (FP32 hydro: also of 288 threads, whose ninth warp
+ * evens out the per-plane work, at 3 or 2 CTAs per SM) -- each timed with CUDA
  * events on the caller's state; the fastest is kept for qk_step and the stage
  * entry points of this context.  rad may be NULL (hydro only).  The state is
  * not changed except that its ghost cells are refilled; radiation stage 2 is
@@ -343,7 +344,9 @@ int qk_autotune(qk_ctx *ctx, void *const hydro[5], void *const rad[4], int32_t o
 /* Set the launch configuration of the four stage kernels (hydro stage 1/2,
  * radiation stage 1/2) directly, in qk_autotune's encoding: threads (128,
  * 256, 512) | schedule (0 strided, 1 contiguous) << 16 | shape << 17, shape 1
- * being 16 x 16 columns of 256 threads (schedule 0).  Compensated steps
+ * being 16 x 16 columns of 256 threads (schedule 0) or of 288 threads
+ * (schedule 0: registers held to 3 CTAs per SM, 1: to 2; FP32 hydro stages --
+ * elsewhere a 288-thread column configuration runs as 256).  Compensated steps
  * (qk_step_compensated) and the tile parts of sharded contexts always use the
  * 8^3 tiles.  QK_EINVAL for any other value. */
 int qk_set_launch_config(qk_ctx *ctx, const int32_t cfg[4]);

@@ -871,10 +871,13 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
     // stage 2 reads the stage-1 result with its ghosts filled
     if (which == 1) err = fill(c, U1, 5, 0, DtSrc{nullptr, 0.0, 0, -1}, s);
     if (which == 3) err = fill(c, R1, 4, 5, DtSrc{nullptr, 0.0, 0, -1}, s);
-    // candidates: threads x schedule on TS^3 tiles, and the columns
-    const int ncand = 7;
+    // candidates: threads x schedule on TS^3 tiles, and the columns (FP32
+    // hydro: also CNT + 32 threads at 3 or 2 CTAs per SM)
+    const int ncand = (c->fp32 && !is_rad) ? 9 : 7;
     for (int ci = 0; ci < ncand && err == cudaSuccess; ++ci) {
-        const int cfg = ci < 6 ? cfg_make(threads[ci / 2], ci % 2) : cfg_make(CNT, 0, 1);
+        const int cfg = ci < 6    ? cfg_make(threads[ci / 2], ci % 2)
+                        : ci == 6 ? cfg_make(CNT, 0, 1)
+                                  : cfg_make(CNT + 32, ci - 7, 1);
         // radiation stage 2 is timed as qk_step runs it: with the exchange
         // fused when it is, on a fresh copy of the gas state
         if (which == 3 && fused)
@@ -924,7 +927,7 @@ int qk_set_launch_config(qk_ctx *c, const int32_t cfg[4]) {
     const int v = cfg[w], th = cfg_threads(v), shape = cfg_shape(v);
     const bool ok = (v >> 18) == 0 &&
                     (shape == 0 ? (th == 128 || th == 256 || th == 512)
-                                : (th == CNT && cfg_sched(v) == 0));
+                                : ((th == CNT && cfg_sched(v) == 0) || th == CNT + 32));
     if (!ok) return fail(c, QK_EINVAL, "invalid launch configuration %d for stage kernel %d", v, w);
   }
   for (int w = 0; w < 4; ++w) c->cfg[w] = cfg[w];

@@ -15,7 +15,7 @@
 // Three barriers per plane.  Used through launch configurations of shape 1
 // (cfg_shape); results equal the TS^3 tile kernels' up to the rounding of
 // the identical formulas (the same device functions).
-#include "qk_device.cuh"
+#include "qk_pair.cuh"
 
 namespace qk {
 
@@ -27,6 +27,9 @@ template <typename T> struct ColSmem {
   // staged one phase ahead (cp.async)
   static constexpr bool kPre = sizeof(T) == 4;
   T pre[kPre ? 10 : 1][kPre ? CNT : 1];
+  // FP32: the conserved values of the next plane to enter (own cells, then
+  // ring cells), staged one plane ahead (cp.async)
+  T nxt[kPre ? 5 : 1][kPre ? CNT + CNRING : 1];
 };
 
 __device__ __forceinline__ int pslot(int i, int j) { return (j + HALO) * CPW + (i + HALO); }
@@ -46,15 +49,17 @@ __device__ __forceinline__ void load_prim(const F5<T> &U, long long e, T gm1, T 
   con2prim<T>(u, gm1, w);
 }
 
-// Resident CTAs per SM the registers are held to (COL_CTAS_*).
-template <typename T> struct ColMinBlocks {
-  static constexpr int value = sizeof(T) == 4 ? COL_CTAS_FP32 : COL_CTAS_FP64;
-};
-
-template <typename T, int STAGE>
-__global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kernel(Geometry g, qk_params p, SC<T> K,
+// Threads per CTA: CNT (one per footprint cell), or CNT + 32: a ninth warp
+// without an own cell, so that the x and y items of a plane (CW (CW + 2)
+// reconstruction positions and CW (CW + 1) faces per direction) come to at
+// most two per thread instead of three for a quarter of the warps -- the
+// phases between barriers end together.  MINB: resident CTAs per SM the
+// registers are held to.
+template <typename T, int STAGE, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) hydro_column_kernel(Geometry g, qk_params p, SC<T> K,
                                                           F5<T> U0, F5<T> U1, F5<T> Uo, DtSrc dts,
                                                           const T *chi) {
+  static_assert(NT >= CNT && NT >= CNRING, "one own cell per thread, ring cells on the last");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ColSmem<T> &sm = *reinterpret_cast<ColSmem<T> *>(smem_raw);
   // the timestep, converted once per CTA
@@ -67,7 +72,9 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
   const F5<T> src = STAGE == 1 ? U0 : U1;
   const int rk = p.recon;
   const int t = threadIdx.x;
+  const bool has_own = t < CNT;        // threads CNT.. (the ninth warp) own no cell
   const int ti = t % CW, tj = t / CW;  // own cell in the footprint
+  const int rt = t - (NT - CNRING);    // ring cells go to the last CNRING threads
 
   for (int w = blockIdx.x; w < g.ncols; w += gridDim.x) {
     const Column col = g.cols[w];
@@ -76,14 +83,14 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
     const long long plane = (long long)b.sx * b.sy;
     // own cell: its primitives feed the ring of valid neighbours up to HALO
     // cells beyond the valid footprint (the patch's ghost cells)
-    const bool own_load = ti < vx + HALO && tj < vy + HALO;
-    const bool own_valid = ti < vx && tj < vy;
-    const long long own0 = cell_elem(b, g.ng, col.x0 + ti, col.y0 + tj, 0);
+    const bool own_load = has_own && ti < vx + HALO && tj < vy + HALO;
+    const bool own_valid = has_own && ti < vx && tj < vy;
+    const long long own0 = has_own ? cell_elem(b, g.ng, col.x0 + ti, col.y0 + tj, 0) : 0;
     // ring cell of this thread (x sides first, then y sides), if any
     int ri = 0, rj = 0;
     bool ring = false;
-    if (t < CNRING) {
-      const int side = t / (HALO * CW), r = t % (HALO * CW);
+    if (rt >= 0) {
+      const int side = rt / (HALO * CW), r = rt % (HALO * CW);
       const int h = r % HALO, along = r / HALO;
       if (side == 0) { ri = h - HALO; rj = along; }
       else if (side == 1) { ri = CW + h; rj = along; }
@@ -124,7 +131,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
     };
     // start-up: face z0 - 1/2 from the reconstructions of cells z0-1 and z0
     T carryR[5], Fz[5];
-    {
+    if (has_own) {
       T st[5][5];
 #pragma unroll
       for (int o = 0; o < 5; ++o) load_plane(col.z0 - 3 + o, st[o]);
@@ -149,23 +156,48 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
 
     // the conserved values of the next plane to enter (own: z+3, ring: z),
     // loaded one plane ahead so that their latency overlaps the work on the
-    // current plane
+    // current plane: FP32 into shared memory by per-thread cp.async (each
+    // thread reads back only what it staged, after its own wait; no register
+    // is held across the plane), FP64 into registers
+    constexpr bool kStage = ColSmem<T>::kPre;
     T nown[5], nring[5];
     auto fetch = [&](int z) {
+      if constexpr (kStage) {
+        if (own_load) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        nown[q] = own_load ? src.f[q][own0 + (long long)(z + 3) * plane] : T(1);
-        nring[q] = ring ? src.f[q][ring0 + (long long)z * plane] : T(1);
+          for (int q = 0; q < 5; ++q)
+            cp_async_elem(&sm.nxt[q][t], src.f[q] + own0 + (long long)(z + 3) * plane);
+        }
+        if (ring) {
+#pragma unroll
+          for (int q = 0; q < 5; ++q)
+            cp_async_elem(&sm.nxt[q][CNT + rt], src.f[q] + ring0 + (long long)z * plane);
+        }
+        cp_async_commit();
+      } else {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          nown[q] = own_load ? src.f[q][own0 + (long long)(z + 3) * plane] : T(1);
+          nring[q] = ring ? src.f[q][ring0 + (long long)z * plane] : T(1);
+        }
       }
     };
     fetch(col.z0);
     for (int z = col.z0; z < col.z1; ++z) {
+      if constexpr (kStage) {
+        cp_async_wait_all();
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          nown[q] = own_load ? sm.nxt[q][t] : T(1);
+          nring[q] = ring ? sm.nxt[q][CNT + (ring ? rt : 0)] : T(1);
+        }
+      }
       // ---- plane z+3 into the window, plane z (own + ring) into smem
       if (own_load) {
         con2prim<T>(nown, gm1, win[4]);
 #pragma unroll
         for (int q = 0; q < 5; ++q) sm.prim[q][pslot(ti, tj)] = win[1][q];
-      } else {
+      } else if (has_own) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) win[4][q] = (q == 0 || q == 4) ? T(1) : T(0);
       }
@@ -190,44 +222,81 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
         }
         cp_async_commit();
       }
-      // ---- x and y reconstruction (items t, t + CNT, ...), and z in registers
-      for (int it = t; it < 2 * CXPOS * CW; it += CNT) {
-        const int dir = it >= CXPOS * CW;
-        const int r = it - dir * CXPOS * CW;
-        int ci, cj, base, stride;
-        if (!dir) {
-          const int pos = r % CXPOS;
-          cj = r / CXPOS;
-          ci = pos - 1;
-          if (cj >= vy || ci > vx) continue;
-          base = pslot(ci - 2, cj);
-          stride = 1;
-        } else {
-          ci = r % CW;
-          const int pos = r / CW;
-          cj = pos - 1;
-          if (ci >= vx || cj > vy) continue;
-          base = pslot(ci, cj - 2);
-          stride = CPW;
-        }
-        const T ch = chi ? chi[cell_elem(b, g.ng, col.x0 + ci, col.y0 + cj, z)] : T(1);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          const T *pq = sm.prim[q] + base;
-          T qL, qR;
-          recon<T>(rk, pq[0], pq[stride], pq[2 * stride], pq[3 * stride], pq[4 * stride], qL,
-                   qR);
+      // ---- x and y reconstruction (items t, t + NT, ...), and z in registers
+      if constexpr (sizeof(T) == 4) {
+        // FP32: position r of the x rows and position r of the y columns as
+        // the two lanes of packed arithmetic (qk_pair.cuh); both lanes' reads
+        // lie in the plane for every r < CXPOS CW, and a lane whose position
+        // is not needed writes a slot that no face reads
+        for (int r = t; r < CXPOS * CW; r += NT) {
+          const int cjx = r / CXPOS, cix = r % CXPOS - 1;
+          const int ciy = r % CW, cjy = r / CW - 1;
+          const bool okx = cjx < vy && cix <= vx, oky = ciy < vx && cjy <= vy;
+          if (!okx && !oky) continue;
+          const int bx = pslot(cix - 2, cjx), by = pslot(ciy, cjy - 2);
+          f2 ch = p2(1.0f);
           if (chi) {
-            const T qc = pq[2 * stride];
-            qL = ch * qL + (T(1) - ch) * qc;
-            qR = ch * qR + (T(1) - ch) * qc;
+            if (okx) ch.x = chi[cell_elem(b, g.ng, col.x0 + cix, col.y0 + cjx, z)];
+            if (oky) ch.y = chi[cell_elem(b, g.ng, col.x0 + ciy, col.y0 + cjy, z)];
           }
-          sm.rec[dir][2 * q][r] = qL;
-          sm.rec[dir][2 * q + 1][r] = qR;
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            const float *pq = sm.prim[q];
+            f2 st[5];
+#pragma unroll
+            for (int o = 0; o < 5; ++o) st[o] = make_float2(pq[bx + o], pq[by + o * CPW]);
+            f2 qL, qR;
+            recon2(rk, st[0], st[1], st[2], st[3], st[4], qL, qR);
+            if (chi) {
+              const f2 oc = sub2(p2(1.0f), ch);
+              qL = fma2(ch, qL, mul2(oc, st[2]));
+              qR = fma2(ch, qR, mul2(oc, st[2]));
+            }
+            sm.rec[0][2 * q][r] = qL.x;
+            sm.rec[0][2 * q + 1][r] = qR.x;
+            sm.rec[1][2 * q][r] = qL.y;
+            sm.rec[1][2 * q + 1][r] = qR.y;
+          }
+        }
+      } else {
+        for (int it = t; it < 2 * CXPOS * CW; it += NT) {
+          const int dir = it >= CXPOS * CW;
+          const int r = it - dir * CXPOS * CW;
+          int ci, cj, base, stride;
+          if (!dir) {
+            const int pos = r % CXPOS;
+            cj = r / CXPOS;
+            ci = pos - 1;
+            if (cj >= vy || ci > vx) continue;
+            base = pslot(ci - 2, cj);
+            stride = 1;
+          } else {
+            ci = r % CW;
+            const int pos = r / CW;
+            cj = pos - 1;
+            if (ci >= vx || cj > vy) continue;
+            base = pslot(ci, cj - 2);
+            stride = CPW;
+          }
+          const T ch = chi ? chi[cell_elem(b, g.ng, col.x0 + ci, col.y0 + cj, z)] : T(1);
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            const T *pq = sm.prim[q] + base;
+            T qL, qR;
+            recon<T>(rk, pq[0], pq[stride], pq[2 * stride], pq[3 * stride], pq[4 * stride], qL,
+                     qR);
+            if (chi) {
+              const T qc = pq[2 * stride];
+              qL = ch * qL + (T(1) - ch) * qc;
+              qR = ch * qR + (T(1) - ch) * qc;
+            }
+            sm.rec[dir][2 * q][r] = qL;
+            sm.rec[dir][2 * q + 1][r] = qR;
+          }
         }
       }
       T Fzn[5];
-      {
+      if (has_own) {
         T qL[5], qR[5];
         recon_z(win, chi_at(z + 1), qL, qR);
         col_face<T, 2>(carryR, qL, gamma, gm1inv, g1, Fzn);
@@ -236,33 +305,59 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
       }
       __syncthreads();
       // ---- x and y faces
-      for (int it = t; it < 2 * CXFACE * CW; it += CNT) {
-        const int dir = it >= CXFACE * CW;
-        const int r = it - dir * CXFACE * CW;
-        int il, ir;
-        if (!dir) {
-          const int f = r % CXFACE, cj = r / CXFACE;
-          if (cj >= vy || f > vx) continue;
-          il = cj * CXPOS + f;
-          ir = il + 1;
-        } else {
-          const int ci = r % CW, f = r / CW;
-          if (ci >= vx || f > vy) continue;
-          il = f * CW + ci;
-          ir = il + CW;
-        }
-        T wL[5], wR[5], F[5];
+      if constexpr (sizeof(T) == 4) {
+        // FP32: face r of the x rows and face r of the y columns as the two
+        // lanes of hllc2, each in its own frame (rho, u_n, u_t1, u_t2, P):
+        // x (rho, vx, vy, vz, P), y (rho, vy, vz, vx, P)
+        for (int r = t; r < CXFACE * CW; r += NT) {
+          const int fx = r % CXFACE, cjx = r / CXFACE;
+          const int ciy = r % CW, fy = r / CW;
+          const bool okx = cjx < vy && fx <= vx, oky = ciy < vx && fy <= vy;
+          if (!okx && !oky) continue;
+          const int ilx = cjx * CXPOS + fx, ily = fy * CW + ciy;
+          constexpr int qy[5] = {0, 2, 3, 1, 4};
+          f2 wL[5], wR[5], F[5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          wL[q] = sm.rec[dir][2 * q + 1][il];
-          wR[q] = sm.rec[dir][2 * q][ir];
-        }
-        if (!dir)
-          col_face<T, 0>(wL, wR, gamma, gm1inv, g1, F);
-        else
-          col_face<T, 1>(wL, wR, gamma, gm1inv, g1, F);
+          for (int k = 0; k < 5; ++k) {
+            wL[k] = make_float2(sm.rec[0][2 * k + 1][ilx], sm.rec[1][2 * qy[k] + 1][ily]);
+            wR[k] = make_float2(sm.rec[0][2 * k][ilx + 1], sm.rec[1][2 * qy[k]][ily + CW]);
+          }
+          hllc2(wL, wR, gamma, gm1inv, g1, F);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) sm.flux[dir][q][r] = F[q];
+          for (int k = 0; k < 5; ++k) {
+            sm.flux[0][k][r] = F[k].x;
+            sm.flux[1][qy[k]][r] = F[k].y;
+          }
+        }
+      } else {
+        for (int it = t; it < 2 * CXFACE * CW; it += NT) {
+          const int dir = it >= CXFACE * CW;
+          const int r = it - dir * CXFACE * CW;
+          int il, ir;
+          if (!dir) {
+            const int f = r % CXFACE, cj = r / CXFACE;
+            if (cj >= vy || f > vx) continue;
+            il = cj * CXPOS + f;
+            ir = il + 1;
+          } else {
+            const int ci = r % CW, f = r / CW;
+            if (ci >= vx || f > vy) continue;
+            il = f * CW + ci;
+            ir = il + CW;
+          }
+          T wL[5], wR[5], F[5];
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            wL[q] = sm.rec[dir][2 * q + 1][il];
+            wR[q] = sm.rec[dir][2 * q][ir];
+          }
+          if (!dir)
+            col_face<T, 0>(wL, wR, gamma, gm1inv, g1, F);
+          else
+            col_face<T, 1>(wL, wR, gamma, gm1inv, g1, F);
+#pragma unroll
+          for (int q = 0; q < 5; ++q) sm.flux[dir][q][r] = F[q];
+        }
       }
       __syncthreads();
       // ---- divergence ((x + y) + z) and the RK combination of the own cell
@@ -286,12 +381,14 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
           }
         }
       }
+      if (has_own) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) Fz[q] = Fzn[q];
+        for (int q = 0; q < 5; ++q) Fz[q] = Fzn[q];
 #pragma unroll
-      for (int o = 0; o < 4; ++o)
+        for (int o = 0; o < 4; ++o)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) win[o][q] = win[o + 1][q];
+          for (int q = 0; q < 5; ++q) win[o][q] = win[o + 1][q];
+      }
       // the next plane's load overwrites prim after the two barriers above;
       // rec and flux are rewritten only after the next load barrier
     }
@@ -299,7 +396,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocks<T>::value) hydro_column_kern
   }
 }
 
-template <typename T, int STAGE>
+template <typename T, int STAGE, int NT, int MINB>
 static cudaError_t launch_col(const Geometry &g, const qk_params &p, void *const *U0,
                               void *const *U1, void *const *Uo, DtSrc dt, const void *chi,
                               cudaStream_t s) {
@@ -310,28 +407,41 @@ static cudaError_t launch_col(const Geometry &g, const qk_params &p, void *const
     c.f[q] = (T *)Uo[q];
   }
   const int smem = (int)sizeof(ColSmem<T>);
-  auto kern = hydro_column_kernel<T, STAGE>;
+  auto kern = hydro_column_kernel<T, STAGE, NT, MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0, nsm = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CNT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
   int grid = nsm * (per_sm > 0 ? per_sm : 1);
   if (grid > g.ncols) grid = g.ncols;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, CNT, smem, s>>>(g, p, make_sc<T>(p), a, b, c, dt, (const T *)chi);
+  kern<<<grid, NT, smem, s>>>(g, p, make_sc<T>(p), a, b, c, dt, (const T *)chi);
   return cudaGetLastError();
+}
+
+template <int STAGE>
+static cudaError_t launch_col_f32(int cfg, const Geometry &g, const qk_params &p, void *const *U0,
+                                  void *const *U1, void *const *Uo, DtSrc dt, const void *chi,
+                                  cudaStream_t s) {
+  // the column configurations: CNT threads at COL_CTAS_FP32 per SM, or
+  // CNT + 32 threads at 3 (schedule 0) or 2 (schedule 1) per SM
+  if (cfg_threads(cfg) == CNT + 32)
+    return cfg_sched(cfg) ? launch_col<float, STAGE, CNT + 32, 2>(g, p, U0, U1, Uo, dt, chi, s)
+                          : launch_col<float, STAGE, CNT + 32, 3>(g, p, U0, U1, Uo, dt, chi, s);
+  return launch_col<float, STAGE, CNT, COL_CTAS_FP32>(g, p, U0, U1, Uo, dt, chi, s);
 }
 
 cudaError_t launch_hydro_column(int fp32, int stage, const Geometry &g, const qk_params &p,
                                 void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
-                                const void *chi, cudaStream_t s) {
+                                const void *chi, cudaStream_t s, int cfg) {
   if (fp32)
-    return stage == 1 ? launch_col<float, 1>(g, p, U0, U1, Uout, dt, chi, s)
-                      : launch_col<float, 2>(g, p, U0, U1, Uout, dt, chi, s);
-  return stage == 1 ? launch_col<double, 1>(g, p, U0, U1, Uout, dt, chi, s)
-                    : launch_col<double, 2>(g, p, U0, U1, Uout, dt, chi, s);
+    return stage == 1 ? launch_col_f32<1>(cfg, g, p, U0, U1, Uout, dt, chi, s)
+                      : launch_col_f32<2>(cfg, g, p, U0, U1, Uout, dt, chi, s);
+  // FP64: one configuration (CNT threads, COL_CTAS_FP64 per SM)
+  return stage == 1 ? launch_col<double, 1, CNT, COL_CTAS_FP64>(g, p, U0, U1, Uout, dt, chi, s)
+                    : launch_col<double, 2, CNT, COL_CTAS_FP64>(g, p, U0, U1, Uout, dt, chi, s);
 }
 
 }  // namespace qk

@@ -305,7 +305,7 @@ cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_
                                const LoPtrs *lo) {
   // columns (shape 1) when the geometry has them; compensated states use tiles
   if (cfg_shape(cfg) == 1 && g.cols && g.ncols > 0 && !lo)
-    return launch_hydro_column(fp32, stage, g, p, U0, U1, Uout, dt, chi, s);
+    return launch_hydro_column(fp32, stage, g, p, U0, U1, Uout, dt, chi, s, cfg);
   if (fp32 && lo && lo->fmt == 2)
     return stage == 1 ? launch_nt<float, 1, 2>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s)
                       : launch_nt<float, 2, 2>(g, p, U0, U1, Uout, dt, grid, cfg, chi, *lo, s);

@@ -282,7 +282,7 @@ cudaError_t launch_hydro_stage(int fp32, int stage, const Geometry &g, const qk_
                                const LoPtrs *lo = nullptr);
 cudaError_t launch_hydro_column(int fp32, int stage, const Geometry &g, const qk_params &p,
                                 void *const *U0, void *const *U1, void *const *Uout, DtSrc dt,
-                                const void *chi, cudaStream_t s);
+                                const void *chi, cudaStream_t s, int cfg);
 cudaError_t launch_flatten(int fp32, const Geometry &g, const qk_params &p, void *const *U,
                            void *chi, cudaStream_t s);
 // The exchange fused into radiation stage 2: gas fields (and their low parts

@@ -1,0 +1,145 @@
+// qk_pair.cuh -- the FP32 reconstruction and HLLC flux of Sec. 2.2.1 on two
+// independent lanes at once, with Blackwell's packed FP32 arithmetic
+// (add/mul/fma.rn.f32x2: one instruction issues both lanes).  The column
+// kernels pair an x item with a y item of the same plane (two reconstruction
+// positions, or two faces), so that every add, multiply and FMA of the
+// formulas issues once for both; minima, maxima, comparisons, selections and
+// the special-function approximations (reciprocal, square root) stay per lane.
+// The formulas are those of ppm / plm / hllc in qk_device.cuh, lane by lane.
+#pragma once
+#include "qk_device.cuh"
+
+namespace qk {
+
+typedef float2 f2;
+
+__device__ __forceinline__ f2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+// a - b as fma(b, -1, a): one packed instruction, exact like a subtraction
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, p2(-1.0f), a); }
+__device__ __forceinline__ f2 min2(f2 a, f2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
+__device__ __forceinline__ f2 max2(f2 a, f2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+__device__ __forceinline__ f2 rcp2(f2 a) { return make_float2(qrcp(a.x), qrcp(a.y)); }
+__device__ __forceinline__ f2 sqrt2(f2 a) { return make_float2(qsqrt(a.x), qsqrt(a.y)); }
+__device__ __forceinline__ f2 sel2(bool cx, bool cy, f2 a, f2 b) {
+  return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
+}
+
+// PPM of one cell per lane from the stencil s0..s4 (ppm in qk_device.cuh):
+// interface values, clamp to the neighbours' range, linear MC reconstruction
+// at an extremum ((qR - q)(q - qL) <= 0), else the CW84 overshoot resets.
+// The MC half slope is sign(dp) min(|dm|, |dp|, |dm + dp|/4) (half of the
+// slope min(2|dm|, 2|dp|, |dm + dp|/2), scaling by 2 being exact), and the
+// CW84 tests d q6 > d^2 and -d^2 > d q6 are d (l' - qL) > 0 and
+// d (qR - r') > 0 with l' = 3q - 2qR, r' = 3q - 2qL (expand d q6 -+ d^2).
+__device__ __forceinline__ void ppm2(f2 s0, f2 s1, f2 s2, f2 s3, f2 s4, f2 &qL, f2 &qR) {
+  const f2 fL = fma2(p2(7.0f / 12.0f), add2(s1, s2), mul2(p2(-1.0f / 12.0f), add2(s0, s3)));
+  const f2 fR = fma2(p2(7.0f / 12.0f), add2(s2, s3), mul2(p2(-1.0f / 12.0f), add2(s1, s4)));
+  const f2 lo = min2(s1, min2(s2, s3)), hi = max2(s1, max2(s2, s3));
+  const f2 l = min2(max2(fL, lo), hi), r = min2(max2(fR, lo), hi);
+  const f2 dm = sub2(s2, s1), dp = sub2(s3, s2);
+  const f2 pr = mul2(dm, dp);
+  const f2 q4 = mul2(p2(0.25f), add2(dm, dp));
+  f2 h;
+  h.x = pr.x > 0.0f ? copysignf(fminf(fminf(fabsf(dm.x), fabsf(dp.x)), fabsf(q4.x)), dp.x) : 0.0f;
+  h.y = pr.y > 0.0f ? copysignf(fminf(fminf(fabsf(dm.y), fabsf(dp.y)), fabsf(q4.y)), dp.y) : 0.0f;
+  const f2 t3 = mul2(p2(3.0f), s2);
+  const f2 ln = fma2(p2(-2.0f), r, t3), rn = fma2(p2(-2.0f), l, t3);
+  const f2 d = sub2(r, l);
+  const f2 a1 = mul2(d, sub2(ln, l)), a2 = mul2(d, sub2(r, rn));
+  const f2 ex = mul2(sub2(r, s2), sub2(s2, l));
+  const f2 lh = sub2(s2, h), rh = add2(s2, h);
+  const bool ex_x = ex.x <= 0.0f, ex_y = ex.y <= 0.0f;
+  const bool c1x = a1.x > 0.0f, c1y = a1.y > 0.0f;
+  const bool c2x = !c1x && a2.x > 0.0f, c2y = !c1y && a2.y > 0.0f;
+  qL = sel2(ex_x, ex_y, lh, sel2(c1x, c1y, ln, l));
+  qR = sel2(ex_x, ex_y, rh, sel2(c2x, c2y, rn, r));
+}
+
+// PLM with the MC limiter per lane (plm in qk_device.cuh).
+__device__ __forceinline__ void plm2(f2 s1, f2 s2, f2 s3, f2 &qL, f2 &qR) {
+  const f2 dm = sub2(s2, s1), dp = sub2(s3, s2);
+  const f2 pr = mul2(dm, dp);
+  const f2 q4 = mul2(p2(0.25f), add2(dm, dp));
+  f2 h;
+  h.x = pr.x > 0.0f ? copysignf(fminf(fminf(fabsf(dm.x), fabsf(dp.x)), fabsf(q4.x)), dp.x) : 0.0f;
+  h.y = pr.y > 0.0f ? copysignf(fminf(fminf(fabsf(dm.y), fabsf(dp.y)), fabsf(q4.y)), dp.y) : 0.0f;
+  qL = sub2(s2, h);
+  qR = add2(s2, h);
+}
+
+__device__ __forceinline__ void recon2(int kind, f2 s0, f2 s1, f2 s2, f2 s3, f2 s4, f2 &qL,
+                                       f2 &qR) {
+  if (kind == QK_RECON_PLM)
+    plm2(s1, s2, s3, qL, qR);
+  else
+    ppm2(s0, s1, s2, s3, s4, qL, qR);
+}
+
+// HLLC flux per lane (hllc in qk_device.cuh) from face states given in the
+// face's own frame: w = (rho, u_n, u_t1, u_t2, P), u_n the velocity normal to
+// the face; F = (mass, normal momentum, t1 momentum, t2 momentum, energy)
+// fluxes.  Each lane may be a face of another direction; the caller maps the
+// components.  PVRS pressure, shock factors (the second square root only
+// where both sides are shocked), S*, and the flux of the side K that the
+// face's region selects; the star ratio (S_K - u_K)/(S_K - S*) is exactly 1
+// when numerator and denominator are the same number.
+__device__ __forceinline__ void hllc2(const f2 wL[5], const f2 wR[5], float gamma, float gm1inv,
+                                      float g1, f2 F[5]) {
+  const f2 rL = wL[0], uL = wL[1], pL = wL[4];
+  const f2 rR = wR[0], uR = wR[1], pR = wR[4];
+  // c = sqrt(gamma p / rho)
+  const f2 cL = sqrt2(mul2(mul2(p2(gamma), pL), rcp2(rL)));
+  const f2 cR = sqrt2(mul2(mul2(p2(gamma), pR), rcp2(rR)));
+  // p_pvrs = (pL + pR)/2 - (uR - uL)(rL + rR)(cL + cR)/8
+  const f2 ppv = mul2(p2(0.5f), fma2(mul2(p2(-0.25f), sub2(uR, uL)),
+                                     mul2(add2(rL, rR), add2(cL, cR)), add2(pL, pR)));
+  const f2 ps = max2(ppv, p2(0.0f));
+  const bool shLx = ps.x > pL.x, shLy = ps.y > pL.y, shRx = ps.x > pR.x, shRy = ps.y > pR.y;
+  // shock factor sqrt((p_K + g1 (p* - p_K)) / p_K) for the first shocked side
+  // (left if both), and for the right side where both are shocked
+  const f2 p1 = sel2(shLx, shLy, pL, pR);
+  const f2 q1 = sqrt2(mul2(fma2(p2(g1), sub2(ps, p1), p1), rcp2(p1)));
+  f2 qL = sel2(shLx, shLy, q1, p2(1.0f));
+  f2 qR = sel2(shRx, shRy, q1, p2(1.0f));
+  if ((shLx && shRx) || (shLy && shRy)) {
+    const f2 q2 = sqrt2(mul2(fma2(p2(g1), sub2(ps, pR), pR), rcp2(pR)));
+    qR = sel2(shLx && shRx, shLy && shRy, q2, qR);
+  }
+  const f2 SL = sub2(uL, mul2(cL, qL)), SR = fma2(cR, qR, uR);
+  const f2 mL = mul2(rL, sub2(SL, uL)), mR = mul2(rR, sub2(SR, uR));
+  // S* = (pR - pL + uL mL - uR mR) / (mL - mR)
+  const f2 nS = sub2(fma2(uL, mL, sub2(pR, pL)), mul2(uR, mR));
+  const f2 Ss = mul2(nS, rcp2(sub2(mL, mR)));
+  const bool supLx = SL.x >= 0.0f, supLy = SL.y >= 0.0f;
+  const bool supRx = !supLx && SR.x <= 0.0f, supRy = !supLy && SR.y <= 0.0f;
+  const bool lx = supLx || (!supRx && Ss.x >= 0.0f), ly = supLy || (!supRy && Ss.y >= 0.0f);
+  const f2 rK = sel2(lx, ly, rL, rR), uK = sel2(lx, ly, uL, uR), pK = sel2(lx, ly, pL, pR);
+  const f2 aK = sel2(lx, ly, wL[2], wR[2]), bK = sel2(lx, ly, wL[3], wR[3]);
+  const f2 SK = sel2(lx, ly, SL, SR);
+  // E_K = p_K/(gamma - 1) + rho_K (u_K^2 + (a_K^2 + b_K^2)) / 2
+  const f2 v2 = fma2(uK, uK, fma2(aK, aK, mul2(bK, bK)));
+  const f2 EK = fma2(pK, p2(gm1inv), mul2(mul2(p2(0.5f), rK), v2));
+  const f2 mK = mul2(rK, uK);
+  const f2 FKn = fma2(mK, uK, pK), FKe = mul2(uK, add2(EK, pK));
+  const f2 num = sub2(SK, uK), den = sub2(SK, Ss);
+  const f2 rq = mul2(num, rcp2(den));
+  const f2 ratio = sel2(num.x == den.x, num.y == den.y, p2(1.0f), rq);
+  const f2 fac = mul2(rK, ratio);
+  // E*_K = ratio (E_K + (S* - u_K)(rho_K S* + p_K / (S_K - u_K)))
+  const f2 Ue = mul2(ratio, fma2(sub2(Ss, uK), fma2(rK, Ss, mul2(pK, rcp2(num))), EK));
+  const f2 Fs0 = fma2(SK, sub2(fac, rK), mK);
+  const f2 Fsn = fma2(SK, sub2(mul2(fac, Ss), mK), FKn);
+  const f2 Fse = fma2(SK, sub2(Ue, EK), FKe);
+  const bool supx = supLx || supRx, supy = supLy || supRy;
+  const f2 F0 = sel2(supx, supy, mK, Fs0);
+  F[0] = F0;
+  F[1] = sel2(supx, supy, FKn, Fsn);
+  F[2] = mul2(aK, F0);
+  F[3] = mul2(bK, F0);
+  F[4] = sel2(supx, supy, FKe, Fse);
+}
+
+}  // namespace qk

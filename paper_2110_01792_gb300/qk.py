@@ -173,18 +173,23 @@ _CFG_NAMES = ("hydro1", "hydro2", "rad1", "rad2")
 
 def _decode_cfg(vals):
     """threads | schedule << 16 | shape << 17 -> {kernel: (threads, schedule)},
-    schedule "strided" / "contiguous" on 8^3 tiles, or "columns"."""
+    schedule "strided" / "contiguous" on 8^3 tiles, or "columns" / "columns2"
+    (16 x 16 columns; "columns2": registers held to two CTAs per SM)."""
     out = {}
     for n, v in zip(_CFG_NAMES, vals):
         v = int(v)
-        sched = "columns" if (v >> 17) & 1 else ("contiguous" if (v >> 16) & 1 else "strided")
+        if (v >> 17) & 1:
+            sched = "columns2" if (v >> 16) & 1 else "columns"
+        else:
+            sched = "contiguous" if (v >> 16) & 1 else "strided"
         out[n] = (v & 0xffff, sched)
     return out
 
 
 def _encode_cfg(c):
     th, sched = c
-    return int(th) | ({"strided": 0, "contiguous": 1 << 16, "columns": 1 << 17}[sched])
+    return int(th) | ({"strided": 0, "contiguous": 1 << 16, "columns": 1 << 17,
+                       "columns2": 3 << 16}[sched])
 
 
 def eval_convert(f_in=None, d_out=None, d_in=None, f_out=None, stream=None):

@@ -258,6 +258,37 @@ def test_column_hydro_stages_match_oracle(torch_cuda, lay, recon, flat):
                 _check_fp32_stage(lay, a, ref, tag)
 
 
+@pytest.mark.parametrize("lay", [RAGGED, I.single_box(40, ng=4)], ids=["ragged", "box40"])
+def test_column_hydro_fp32_thread_counts_bit_identical(torch_cuda, lay):
+    """The FP32 hydro column kernels with 288 threads per CTA (a ninth warp
+    that owns no cell and takes x/y items and ring cells), registers held to 3
+    or 2 CTAs per SM, compute every cell with the same arithmetic as the
+    256-thread kernel: both stages bit-identical, partial footprints and z
+    chunks included."""
+    torch = torch_cuda
+    prob, prm = _random_rhd(lay, 6)
+    prm["hydro_only"] = 1
+    p = O.make_params(**prm)
+    dt = 0.2 * O.timestep(_grid(lay), p, prob.U)[0]
+    res = []
+    for cfg in ((256, "columns"), (288, "columns"), (288, "columns2")):
+        ctx = _ctx(lay, prm, 1)
+        ctx.set_launch_config({"hydro1": cfg, "hydro2": cfg, "rad1": (256, "strided"),
+                               "rad2": (256, "strided")})
+        dU0 = G.dev(prob.U, torch.float32)
+        dU1 = G.dev([np.zeros_like(a) for a in prob.U], torch.float32)
+        ctx.fill_ghosts(dU0)
+        ctx.hydro_stage(1, dU0, None, dU1, dt)
+        ctx.fill_ghosts(dU1)
+        ctx.hydro_stage(2, dU0, dU1, dU0, dt)
+        torch.cuda.synchronize()
+        res.append(G.host(dU1) + G.host(dU0))
+        ctx.close()
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            assert np.array_equal(G.interior(lay, a), G.interior(lay, b))
+
+
 def test_column_hydro_ten_steps_fp64(torch_cuda):
     """10 FP64 hydro steps of the seeded 32^3 workload with the column kernels
     agree with the oracle to 1e-10 per cell."""
@@ -761,7 +792,8 @@ def test_autotune_keeps_state_and_results(torch_cuda):
             cfg = ctx.autotune(dU, dR)
             assert set(cfg) == {"hydro1", "hydro2", "rad1", "rad2"}
             for th, sch in cfg.values():
-                assert th in (128, 256, 512) and sch in ("strided", "contiguous", "columns")
+                assert th in (128, 256, 288, 512) and sch in ("strided", "contiguous", "columns",
+                                                               "columns2")
             for a, b in zip(G.host(dU) + G.host(dR), before):
                 assert np.array_equal(G.interior(lay, a), G.interior(lay, b))
         for _ in range(2):
