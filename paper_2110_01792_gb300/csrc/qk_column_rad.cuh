@@ -10,6 +10,7 @@
 // with a HALO-deep ring.
 #pragma once
 #include "qk_rad.cuh"
+#include "qk_pair.cuh"
 
 namespace qk {
 
@@ -25,6 +26,9 @@ template <typename T> struct ColRadSmem {
   // (cp.async): R_src (4), R_0 (4, stage 2), the gas state U (5, exchange)
   static constexpr int kPre = kAB ? 1 : 13;
   T pre[kPre][kAB ? 1 : CNT];
+  // FP32: E_r, F and rho of the next plane to enter (own cells, then ring
+  // cells), staged one plane ahead (cp.async)
+  T nxt[kAB ? 1 : 5][kAB ? 1 : CNT + CNRING];
 };
 
 __device__ __forceinline__ int cslot(int i, int j) { return (j + HALO) * CPW + (i + HALO); }
@@ -182,21 +186,48 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
       }
     }
 
-    // next plane's inputs, fetched one plane ahead
+    // next plane's inputs, fetched one plane ahead: FP32 into shared memory
+    // by per-thread cp.async (read back by the same thread after its own
+    // wait), FP64 into registers
+    const int rslot = CNT + (t < CNRING ? t : 0);
     T nown[4], nring[4], nrho_own = T(1), nrho_ring = T(1);
     auto fetch = [&](int z) {
       const long long eo = own0 + (long long)(z + 3) * plane;
       const long long er = ring0 + (long long)z * plane;
+      if constexpr (!kAB) {
+        if (own_load) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        nown[q] = own_load ? src.f[q][eo] : T(1);
-        nring[q] = ring ? src.f[q][er] : T(1);
+          for (int q = 0; q < 4; ++q) cp_async_elem(&sm.nxt[q][t], src.f[q] + eo);
+          cp_async_elem(&sm.nxt[4][t], rho + eo);
+        }
+        if (ring) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cp_async_elem(&sm.nxt[q][rslot], src.f[q] + er);
+          cp_async_elem(&sm.nxt[4][rslot], rho + er);
+        }
+        cp_async_commit();
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          nown[q] = own_load ? src.f[q][eo] : T(1);
+          nring[q] = ring ? src.f[q][er] : T(1);
+        }
+        nrho_own = own_load ? rho[eo] : T(1);
+        nrho_ring = ring ? rho[er] : T(1);
       }
-      nrho_own = own_load ? rho[eo] : T(1);
-      nrho_ring = ring ? rho[er] : T(1);
     };
     fetch(col.z0);
     for (int z = col.z0; z < col.z1; ++z) {
+      if constexpr (!kAB) {
+        cp_async_wait_all();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          nown[q] = own_load ? sm.nxt[q][t] : T(1);
+          nring[q] = ring ? sm.nxt[q][rslot] : T(1);
+        }
+        nrho_own = own_load ? sm.nxt[4][t] : T(1);
+        nrho_ring = ring ? sm.nxt[4][rslot] : T(1);
+      }
       // ---- plane z+3 into the window; plane z (own + ring) into smem
       if (own_load) {
         rad_prim<T>(nown, c, nrho_own, K, win[4], rkw[4]);
@@ -251,39 +282,71 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
         cp_async_commit();
       }
       // ---- x and y reconstruction; z in registers
-      for (int it = t; it < 2 * CXPOS * CW; it += CNT) {
-        const int dir = it >= CXPOS * CW;
-        const int r = it - dir * CXPOS * CW;
-        int ci, cj, base, stride;
-        if (!dir) {
-          const int pos = r % CXPOS;
-          cj = r / CXPOS;
-          ci = pos - 1;
-          if (cj >= vy || ci > vx) continue;
-          base = cslot(ci - 2, cj);
-          stride = 1;
-        } else {
-          ci = r % CW;
-          const int pos = r / CW;
-          cj = pos - 1;
-          if (ci >= vx || cj > vy) continue;
-          base = cslot(ci, cj - 2);
-          stride = CPW;
-        }
+      if constexpr (!kAB) {
+        // FP32: position r of the x rows and position r of the y columns as
+        // the two lanes of packed arithmetic (qk_pair.cuh), with sqrt(T_DD) of
+        // each position's cell average (x: T_xx, y: T_yy); every read lies in
+        // the plane for r < CXPOS CW, and a lane whose position is not needed
+        // writes a slot that no face reads
+        for (int r = t; r < CXPOS * CW; r += CNT) {
+          const int cjx = r / CXPOS, cix = r % CXPOS - 1;
+          const int ciy = r % CW, cjy = r / CW - 1;
+          const bool okx = cjx < vy && cix <= vx, oky = ciy < vx && cjy <= vy;
+          if (!okx && !oky) continue;
+          const int bx = cslot(cix - 2, cjx), by = cslot(ciy, cjy - 2);
+          f2 mid[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const T *pq = sm.prim[q] + base;
-          T qL, qR;
-          recon<T>(rk, pq[0], pq[stride], pq[2 * stride], pq[3 * stride], pq[4 * stride], qL,
-                   qR);
-          sm.rec[dir][2 * q][r] = qL;
-          sm.rec[dir][2 * q + 1][r] = qR;
+          for (int q = 0; q < 4; ++q) {
+            const float *pq = sm.prim[q];
+            f2 st[5];
+#pragma unroll
+            for (int o = 0; o < 5; ++o) st[o] = make_float2(pq[bx + o], pq[by + o * CPW]);
+            mid[q] = st[2];
+            f2 qL, qR;
+            recon2(rk, st[0], st[1], st[2], st[3], st[4], qL, qR);
+            sm.rec[0][2 * q][r] = qL.x;
+            sm.rec[0][2 * q + 1][r] = qR.x;
+            sm.rec[1][2 * q][r] = qL.y;
+            sm.rec[1][2 * q + 1][r] = qR.y;
+          }
+          // T_DD = a + b f_D^2 of the cell average, D = x (lane x), y (lane y)
+          const f2 fsq = fma2(mid[3], mid[3], fma2(mid[1], mid[1], mul2(mid[2], mid[2])));
+          f2 a, bb;
+          closure_ab2<CL>(fsq, a, bb);
+          const f2 fD = make_float2(mid[1].x, mid[2].y);
+          const f2 Tdd = fma2(mul2(bb, fD), fD, a);
+          sm.sq[0][r] = qsqrt(Tdd.x);
+          sm.sq[1][r] = qsqrt(Tdd.y);
         }
-        if constexpr (!kAB) {
-          const int s2 = base + 2 * stride;
-          sm.sq[dir][r] =
-              dir ? qsqrt(eddington_diag<T, 1, CL>(sm.prim[1][s2], sm.prim[2][s2], sm.prim[3][s2]))
-                  : qsqrt(eddington_diag<T, 0, CL>(sm.prim[1][s2], sm.prim[2][s2], sm.prim[3][s2]));
+      } else {
+        for (int it = t; it < 2 * CXPOS * CW; it += CNT) {
+          const int dir = it >= CXPOS * CW;
+          const int r = it - dir * CXPOS * CW;
+          int ci, cj, base, stride;
+          if (!dir) {
+            const int pos = r % CXPOS;
+            cj = r / CXPOS;
+            ci = pos - 1;
+            if (cj >= vy || ci > vx) continue;
+            base = cslot(ci - 2, cj);
+            stride = 1;
+          } else {
+            ci = r % CW;
+            const int pos = r / CW;
+            cj = pos - 1;
+            if (ci >= vx || cj > vy) continue;
+            base = cslot(ci, cj - 2);
+            stride = CPW;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const T *pq = sm.prim[q] + base;
+            T qL, qR;
+            recon<T>(rk, pq[0], pq[stride], pq[2 * stride], pq[3 * stride], pq[4 * stride], qL,
+                     qR);
+            sm.rec[dir][2 * q][r] = qL;
+            sm.rec[dir][2 * q + 1][r] = qR;
+          }
         }
       }
       T Fzn[4];
@@ -298,54 +361,83 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
       }
       __syncthreads();
       // ---- x and y faces
-      for (int it = t; it < 2 * CXFACE * CW; it += CNT) {
-        const int dir = it >= CXFACE * CW;
-        const int r = it - dir * CXFACE * CW;
-        int il, ir, sa, sb;
-        if (!dir) {
-          const int f = r % CXFACE, cj = r / CXFACE;
-          if (cj >= vy || f > vx) continue;
-          il = cj * CXPOS + f;
-          ir = il + 1;
-          sa = cslot(f - 1, cj);
-          sb = sa + 1;
-        } else {
-          const int ci = r % CW, f = r / CW;
-          if (ci >= vx || f > vy) continue;
-          il = f * CW + ci;
-          ir = il + CW;
-          sa = cslot(ci, f - 1);
-          sb = sa + CPW;
-        }
-        T wL[4], wR[4], out[4];
+      if constexpr (!kAB) {
+        // FP32: face r of the x rows and face r of the y columns as the two
+        // lanes of rad_face_hll2, each in its own frame (E_r, f_n, f_t1,
+        // f_t2): x (E_r, f_x, f_y, f_z), y (E_r, f_y, f_z, f_x)
+        for (int r = t; r < CXFACE * CW; r += CNT) {
+          const int fx = r % CXFACE, cjx = r / CXFACE;
+          const int ciy = r % CW, fy = r / CW;
+          const bool okx = cjx < vy && fx <= vx, oky = ciy < vx && fy <= vy;
+          if (!okx && !oky) continue;
+          const int ilx = cjx * CXPOS + fx, ily = fy * CW + ciy;
+          const int sax = cslot(fx - 1, cjx), say = cslot(ciy, fy - 1);
+          constexpr int qy[4] = {0, 2, 3, 1};
+          f2 wL[4], wR[4], avL[4], avR[4], out[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          wL[q] = sm.rec[dir][2 * q + 1][il];
-          wR[q] = sm.rec[dir][2 * q][ir];
+          for (int k = 0; k < 4; ++k) {
+            wL[k] = make_float2(sm.rec[0][2 * k + 1][ilx], sm.rec[1][2 * qy[k] + 1][ily]);
+            wR[k] = make_float2(sm.rec[0][2 * k][ilx + 1], sm.rec[1][2 * qy[k]][ily + CW]);
+            avL[k] = make_float2(sm.prim[k][sax], sm.prim[qy[k]][say]);
+            avR[k] = make_float2(sm.prim[k][sax + 1], sm.prim[qy[k]][say + CPW]);
+          }
+          const f2 S = mul2(p2(chat), make_float2(fmaxf(sm.sq[0][ilx], sm.sq[0][ilx + 1]),
+                                                  fmaxf(sm.sq[1][ily], sm.sq[1][ily + CW])));
+          const f2 rka = make_float2(sm.rk[sax], sm.rk[say]);
+          const f2 rkb = make_float2(sm.rk[sax + 1], sm.rk[say + CPW]);
+          rad_face_hll2<CL>(wL, wR, avL, avR, S, rka, rkb, make_float2(dx[0], dx[1]), c, chat,
+                            hchat_c, hccc, p.tau_correction, out);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            sm.flux[0][k][r] = out[k].x;
+            sm.flux[1][qy[k]][r] = out[k].y;
+          }
         }
-        auto fallback = [&](T *l, T *r2) {
+      } else {
+        for (int it = t; it < 2 * CXFACE * CW; it += CNT) {
+          const int dir = it >= CXFACE * CW;
+          const int r = it - dir * CXFACE * CW;
+          int il, ir, sa, sb;
+          if (!dir) {
+            const int f = r % CXFACE, cj = r / CXFACE;
+            if (cj >= vy || f > vx) continue;
+            il = cj * CXPOS + f;
+            ir = il + 1;
+            sa = cslot(f - 1, cj);
+            sb = sa + 1;
+          } else {
+            const int ci = r % CW, f = r / CW;
+            if (ci >= vx || f > vy) continue;
+            il = f * CW + ci;
+            ir = il + CW;
+            sa = cslot(ci, f - 1);
+            sb = sa + CPW;
+          }
+          T wL[4], wR[4], out[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            l[q] = sm.prim[q][sa];
-            r2[q] = sm.prim[q][sb];
+            wL[q] = sm.rec[dir][2 * q + 1][il];
+            wR[q] = sm.rec[dir][2 * q][ir];
           }
-        };
-        T S;
-        if constexpr (kAB) {
-          const T fa = sm.prim[1 + dir][sa], fb = sm.prim[1 + dir][sb];
-          S = rad_speed<T>(sm.ab[0][sa] + sm.ab[1][sa] * fa * fa,
-                           sm.ab[0][sb] + sm.ab[1][sb] * fb * fb, chat);
-        } else {
-          S = chat * max(sm.sq[dir][il], sm.sq[dir][ir]);
-        }
-        if (!dir)
-          rad_face_hll<T, 0, CL>(wL, wR, fallback, S, sm.rk[sa], sm.rk[sb], dx[0], c, chat,
-                                 hchat_c, hccc, p.tau_correction, out);
-        else
-          rad_face_hll<T, 1, CL>(wL, wR, fallback, S, sm.rk[sa], sm.rk[sb], dx[1], c, chat,
-                                 hchat_c, hccc, p.tau_correction, out);
+          auto fallback = [&](T *l, T *r2) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) sm.flux[dir][q][r] = out[q];
+            for (int q = 0; q < 4; ++q) {
+              l[q] = sm.prim[q][sa];
+              r2[q] = sm.prim[q][sb];
+            }
+          };
+          const T fa = sm.prim[1 + dir][sa], fb = sm.prim[1 + dir][sb];
+          const T S = rad_speed<T>(sm.ab[0][sa] + sm.ab[1][sa] * fa * fa,
+                                   sm.ab[0][sb] + sm.ab[1][sb] * fb * fb, chat);
+          if (!dir)
+            rad_face_hll<T, 0, CL>(wL, wR, fallback, S, sm.rk[sa], sm.rk[sb], dx[0], c, chat,
+                                   hchat_c, hccc, p.tau_correction, out);
+          else
+            rad_face_hll<T, 1, CL>(wL, wR, fallback, S, sm.rk[sa], sm.rk[sb], dx[1], c, chat,
+                                   hchat_c, hccc, p.tau_correction, out);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) sm.flux[dir][q][r] = out[q];
+        }
       }
       __syncthreads();
       // ---- divergence ((x + y) + z), RK combination, optional exchange

@@ -142,4 +142,87 @@ __device__ __forceinline__ void hllc2(const f2 wL[5], const f2 wR[5], float gamm
   F[4] = sel2(supx, supy, FKe, Fse);
 }
 
+// Closure coefficients of T = a I + b f f per lane from |f|^2 (closure_ab_f2
+// in qk_device.cuh, closure CL).
+template <int CL>
+__device__ __forceinline__ void closure_ab2(f2 fsq, f2 &a, f2 &b) {
+  if constexpr (CL == QK_CLOSURE_EDDINGTON) {
+    a = p2(1.0f / 3.0f);
+    b = p2(0.0f);
+  } else {
+    const bool sx = fsq.x > 1.0f, sy = fsq.y > 1.0f;
+    if constexpr (CL == QK_CLOSURE_MINERBO) {
+      const f2 fc = sqrt2(fsq);
+      const f2 h = fma2(p2(3.0f), fsq, sub2(p2(3.0f), fc));
+      a = sub2(p2(1.0f / 3.0f), mul2(mul2(fsq, h), p2(1.0f / 15.0f)));
+      b = mul2(h, p2(0.2f));
+    } else {
+      // Levermore: s = sqrt(4 - 3 |f|^2), a = (s - 1)/3, b = 1/(a + 1)
+      const f2 sq = sqrt2(fma2(p2(-3.0f), fsq, p2(4.0f)));
+      a = fma2(sq, p2(1.0f / 3.0f), p2(-1.0f / 3.0f));
+      b = rcp2(add2(a, p2(1.0f)));
+    }
+    // |f| > 1: chi = 1, a = 0, b = 1/|f|^2
+    if (sx || sy) {
+      const f2 ib = rcp2(fsq);
+      a = sel2(sx, sy, p2(0.0f), a);
+      b = sel2(sx, sy, ib, b);
+    }
+  }
+}
+
+// The radiation HLL face flux per lane (rad_face_hll in qk_rad.cuh), each
+// lane in its face's own frame: w = (E_r, f_n, f_t1, f_t2), out = (energy
+// flux, F_n flux, F_t1 flux, F_t2 flux).  avL / avR: the two cell averages
+// in the same frame, which replace the lane's face states where either of
+// them has |f| > 1; S the lane's wavespeed, rka / rkb the cells' rho kappa_R.
+template <int CL>
+__device__ __forceinline__ void rad_face_hll2(f2 wL[4], f2 wR[4], const f2 avL[4],
+                                              const f2 avR[4], f2 S, f2 rka, f2 rkb, f2 dx,
+                                              float c, float chat, float hchat_c, float hccc,
+                                              int tau_corr, f2 out[4]) {
+  f2 fL2 = fma2(wL[3], wL[3], fma2(wL[1], wL[1], mul2(wL[2], wL[2])));
+  f2 fR2 = fma2(wR[3], wR[3], fma2(wR[1], wR[1], mul2(wR[2], wR[2])));
+  const bool fbx = fL2.x > 1.0f || fR2.x > 1.0f, fby = fL2.y > 1.0f || fR2.y > 1.0f;
+  if (fbx || fby) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      wL[q] = sel2(fbx, fby, avL[q], wL[q]);
+      wR[q] = sel2(fbx, fby, avR[q], wR[q]);
+    }
+    fL2 = fma2(wL[3], wL[3], fma2(wL[1], wL[1], mul2(wL[2], wL[2])));
+    fR2 = fma2(wR[3], wR[3], fma2(wR[1], wR[1], mul2(wR[2], wR[2])));
+  }
+  f2 aL, bL, aR, bR;
+  closure_ab2<CL>(fL2, aL, bL);
+  closure_ab2<CL>(fR2, aR, bR);
+  const f2 EL = wL[0], ER = wR[0], fLD = wL[1], fRD = wR[1];
+  f2 eps = p2(1.0f);
+  if (tau_corr) {
+    const f2 tau = mul2(mul2(dx, p2(0.5f)), add2(rka, rkb));
+    const bool tx = tau.x > 1.0f, ty = tau.y > 1.0f;
+    if (tx || ty) eps = sel2(tx, ty, rcp2(tau), eps);
+  }
+  const f2 hS = mul2(p2(0.5f), S);
+  f2 hSe = mul2(hS, eps);
+  const f2 FE = mul2(p2(hchat_c * c), fma2(EL, fLD, mul2(ER, fRD)));
+  const f2 dE = sub2(ER, EL);
+  f2 o0 = sub2(FE, mul2(hSe, dE));
+  // the correction is dropped where the energy flux would exceed chat max(E_L, E_R)
+  const bool kx = eps.x < 1.0f && fabsf(o0.x) > chat * fmaxf(EL.x, ER.x);
+  const bool ky = eps.y < 1.0f && fabsf(o0.y) > chat * fmaxf(EL.y, ER.y);
+  if (kx || ky) {
+    hSe = sel2(kx, ky, hS, hSe);
+    o0 = sub2(FE, mul2(hSe, dE));
+  }
+  out[0] = o0;
+  const f2 hSec = mul2(hSe, p2(c));
+  const f2 cEbL = mul2(p2(hccc), EL), cEbR = mul2(p2(hccc), ER);
+  const f2 alL = fma2(mul2(cEbL, bL), fLD, mul2(hSec, EL));
+  const f2 alR = sub2(mul2(mul2(cEbR, bR), fRD), mul2(hSec, ER));
+  out[2] = fma2(alL, wL[2], mul2(alR, wR[2]));
+  out[3] = fma2(alL, wL[3], mul2(alR, wR[3]));
+  out[1] = fma2(alL, fLD, fma2(alR, fRD, fma2(cEbL, aL, mul2(cEbR, aR))));
+}
+
 }  // namespace qk
