@@ -119,11 +119,30 @@ __global__ void __launch_bounds__(NT, MINB) hydro_column_kernel(Geometry g, qk_p
       return (chi && own_load) ? chi[own0 + (long long)z * plane] : T(1);
     };
     // reconstruct the own cell at plane z from the five planes st[0..4]
+    // (FP32: the primitives in pairs (rho, v_x), (v_y, v_z) as the lanes of
+    // packed arithmetic, P alone)
     auto recon_z = [&](const T st[5][5], T ch, T qL[5], T qR[5]) {
+      constexpr int q0 = sizeof(T) == 4 ? 4 : 0;
+      if constexpr (sizeof(T) == 4) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
+        for (int q = 0; q < 4; q += 2) {
+          f2 s2[5];
+#pragma unroll
+          for (int o = 0; o < 5; ++o) s2[o] = make_float2(st[o][q], st[o][q + 1]);
+          f2 l2, r2;
+          recon2(rk, s2[0], s2[1], s2[2], s2[3], s2[4], l2, r2);
+          qL[q] = l2.x;
+          qL[q + 1] = l2.y;
+          qR[q] = r2.x;
+          qR[q + 1] = r2.y;
+        }
+      }
+#pragma unroll
+      for (int q = q0; q < 5; ++q)
         recon<T>(rk, st[0][q], st[1][q], st[2][q], st[3][q], st[4][q], qL[q], qR[q]);
-        if (chi) {
+      if (chi) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
           qL[q] = ch * qL[q] + (T(1) - ch) * st[2][q];
           qR[q] = ch * qR[q] + (T(1) - ch) * st[2][q];
         }
@@ -309,7 +328,9 @@ __global__ void __launch_bounds__(NT, MINB) hydro_column_kernel(Geometry g, qk_p
         // FP32: face r of the x rows and face r of the y columns as the two
         // lanes of hllc2, each in its own frame (rho, u_n, u_t1, u_t2, P):
         // x (rho, vx, vy, vz, P), y (rho, vy, vz, vx, P)
-        for (int r = t; r < CXFACE * CW; r += NT) {
+        // (the pairs beyond NT fall to the second warp: the first already
+        // took the extra reconstruction round)
+        for (int r = (t + NT - 32) % NT; r < CXFACE * CW; r += NT) {
           const int fx = r % CXFACE, cjx = r / CXFACE;
           const int ciy = r % CW, fy = r / CW;
           const bool okx = cjx < vy && fx <= vx, oky = ciy < vx && fy <= vy;

@@ -83,9 +83,12 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
     const long long own0 = cell_elem(b, g.ng, col.x0 + ti, col.y0 + tj, 0);
     int ri = 0, rj = 0, rside = 0;
     bool ring = false;
-    if (t < CNRING) {
-      rside = t / (HALO * CW);
-      const int r = t % (HALO * CW), h = r % HALO, along = r / HALO;
+    // ring cells go to the last CNRING threads (the first warp takes the
+    // extra reconstruction round of the plane)
+    const int rt = t - (CNT - CNRING);
+    if (rt >= 0) {
+      rside = rt / (HALO * CW);
+      const int r = rt % (HALO * CW), h = r % HALO, along = r / HALO;
       if (rside == 0) { ri = h - HALO; rj = along; }
       else if (rside == 1) { ri = CW + h; rj = along; }
       else if (rside == 2) { ri = along; rj = h - HALO; }
@@ -148,10 +151,27 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
           },
           S, rka, rkb, dx[2], c, chat, hchat_c, hccc, p.tau_correction, out);
     };
+    // (FP32: the fields in pairs (E_r, f_x), (f_y, f_z) as the lanes of packed
+    // arithmetic)
     auto recon_z = [&](const T st[5][4], T qL[4], T qR[4]) {
+      if constexpr (!kAB) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        recon<T>(rk, st[0][q], st[1][q], st[2][q], st[3][q], st[4][q], qL[q], qR[q]);
+        for (int q = 0; q < 4; q += 2) {
+          f2 s2[5];
+#pragma unroll
+          for (int o = 0; o < 5; ++o) s2[o] = make_float2(st[o][q], st[o][q + 1]);
+          f2 l2, r2;
+          recon2(rk, s2[0], s2[1], s2[2], s2[3], s2[4], l2, r2);
+          qL[q] = l2.x;
+          qL[q + 1] = l2.y;
+          qR[q] = r2.x;
+          qR[q + 1] = r2.y;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          recon<T>(rk, st[0][q], st[1][q], st[2][q], st[3][q], st[4][q], qL[q], qR[q]);
+      }
     };
 
     // start-up: face z0 - 1/2 from cells z0-1 and z0
@@ -189,7 +209,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
     // next plane's inputs, fetched one plane ahead: FP32 into shared memory
     // by per-thread cp.async (read back by the same thread after its own
     // wait), FP64 into registers
-    const int rslot = CNT + (t < CNRING ? t : 0);
+    const int rslot = CNT + (rt >= 0 ? rt : 0);
     T nown[4], nring[4], nrho_own = T(1), nrho_ring = T(1);
     auto fetch = [&](int z) {
       const long long eo = own0 + (long long)(z + 3) * plane;
@@ -365,7 +385,9 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
         // FP32: face r of the x rows and face r of the y columns as the two
         // lanes of rad_face_hll2, each in its own frame (E_r, f_n, f_t1,
         // f_t2): x (E_r, f_x, f_y, f_z), y (E_r, f_y, f_z, f_x)
-        for (int r = t; r < CXFACE * CW; r += CNT) {
+        // (the pairs beyond CNT fall to the second warp: the first already
+        // took the extra reconstruction round)
+        for (int r = (t + CNT - 32) % CNT; r < CXFACE * CW; r += CNT) {
           const int fx = r % CXFACE, cjx = r / CXFACE;
           const int ciy = r % CW, fy = r / CW;
           const bool okx = cjx < vy && fx <= vx, oky = ciy < vx && fy <= vy;
