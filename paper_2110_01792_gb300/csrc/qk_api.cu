@@ -59,6 +59,22 @@ static Geometry geom(const qk_ctx *c) {
   return g;
 }
 
+// The column list a launch configuration runs on: the one chunked for two
+// CTAs per SM for the column configurations held to two (any list covers
+// every cell, so this choice changes only the load balance).
+static bool two_cta_cols(const qk_ctx *c, int cfg) {
+  return c->d_cols2 && cfg_shape(cfg) == 1 && cfg_threads(cfg) == CNT + 32 && cfg_sched(cfg) == 1;
+}
+static Geometry geom_cfg(const qk_ctx *c, int cfg) {
+  Geometry g = geom(c);
+  if (g.cols && two_cta_cols(c, cfg)) {
+    g.cols = c->d_cols2;
+    g.ncols = c->ncols2;
+  }
+  return g;
+}
+
+
 static int check_params(qk_ctx *c, const qk_params *p) {
   if (!p) return fail(c, QK_EINVAL, "params is NULL");
   if (p->closure < QK_CLOSURE_LEVERMORE || p->closure > QK_CLOSURE_EDDINGTON)
@@ -344,6 +360,7 @@ static void release(qk_ctx *c) {
   cudaFree(c->d_tiles);
   cudaFree(c->d_tiles_ib);
   cudaFree(c->d_cols);
+  cudaFree(c->d_cols2);
   cudaFree(c->d_cell0);
   cudaFree(c->d_copies);
   cudaFree(c->d_chunks);
@@ -458,42 +475,49 @@ static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, in
   // column work list: CW x CW footprints, z split into chunks of cz planes.
   // A column costs ~ (cz + 2.5) plane times (the start-up reconstructs two
   // planes ahead); the persistent grid holds `slots` columns at once, so cz
-  // minimises waves x (cz + 2.5), waves = ceil(columns / slots).
-  std::vector<Column> cols;
+  // minimises waves x (cz + 2.5), waves = ceil(columns / slots).  Two lists:
+  // for the column kernels' usual residency (COL_CTAS_* per SM) and, FP32,
+  // for the configurations held to two CTAs per SM.
+  std::vector<Column> cols, cols2;
   {
     int nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long long slots = (long long)std::max(nsm, 1) * (c->fp32 ? COL_CTAS_FP32 : COL_CTAS_FP64);
     int max_nz = 1;
     for (int l = 0; l < nown; ++l) max_nz = std::max(max_nz, (int)boxes[c->own[l]].n[2]);
-    int best_cz = max_nz;
-    double best_cost = 1e300;
-    for (int cz = std::min(8, max_nz); cz <= max_nz; ++cz) {
-      long long items = 0;
+    auto build = [&](long long slots, std::vector<Column> &out, std::vector<int> &start) {
+      int best_cz = max_nz;
+      double best_cost = 1e300;
+      for (int cz = std::min(8, max_nz); cz <= max_nz; ++cz) {
+        long long items = 0;
+        for (int l = 0; l < nown; ++l) {
+          const qk_box &q = boxes[c->own[l]];
+          items += (long long)((q.n[0] + CW - 1) / CW) * ((q.n[1] + CW - 1) / CW) *
+                   ((q.n[2] + cz - 1) / cz);
+        }
+        const double cost = (double)((items + slots - 1) / slots) * (std::min(cz, max_nz) + 2.5);
+        if (cost < best_cost) {
+          best_cost = cost;
+          best_cz = cz;
+        }
+      }
+      start.assign(nown + 1, 0);
       for (int l = 0; l < nown; ++l) {
         const qk_box &q = boxes[c->own[l]];
-        items += (long long)((q.n[0] + CW - 1) / CW) * ((q.n[1] + CW - 1) / CW) *
-                 ((q.n[2] + cz - 1) / cz);
+        start[l] = (int)out.size();
+        for (int y = 0; y < q.n[1]; y += CW)
+          for (int x = 0; x < q.n[0]; x += CW)
+            for (int z = 0; z < q.n[2]; z += best_cz)
+              out.push_back(Column{l, x, y, z, std::min(z + best_cz, (int)q.n[2])});
       }
-      const double cost = (double)((items + slots - 1) / slots) * (std::min(cz, max_nz) + 2.5);
-      if (cost < best_cost) {
-        best_cost = cost;
-        best_cz = cz;
-      }
-    }
-    c->col_start.assign(nown + 1, 0);
-    for (int l = 0; l < nown; ++l) {
-      const qk_box &q = boxes[c->own[l]];
-      c->col_start[l] = (int)cols.size();
-      for (int y = 0; y < q.n[1]; y += CW)
-        for (int x = 0; x < q.n[0]; x += CW)
-          for (int z = 0; z < q.n[2]; z += best_cz)
-            cols.push_back(Column{l, x, y, z, std::min(z + best_cz, (int)q.n[2])});
-    }
-    c->col_start[nown] = (int)cols.size();
+      start[nown] = (int)out.size();
+    };
+    const long long sm = std::max(nsm, 1);
+    build(sm * (c->fp32 ? COL_CTAS_FP32 : COL_CTAS_FP64), cols, c->col_start);
+    if (c->fp32) build(sm * 2, cols2, c->col_start2);
   }
   c->ncols = (int)cols.size();
+  c->ncols2 = (int)cols2.size();
   std::vector<Copy> copies;
   std::vector<std::vector<Copy>> send(c->nranks), recv(c->nranks);
   std::vector<DirRegion> dir;
@@ -580,6 +604,7 @@ static int init_common(qk_ctx **out, const qk_params *p, const qk_box *boxes, in
   if ((rc = upload(c, &c->d_boxes, db))) return bail(rc);
   if ((rc = upload(c, &c->d_tiles, tiles))) return bail(rc);
   if ((rc = upload(c, &c->d_cols, cols))) return bail(rc);
+  if (!cols2.empty() && (rc = upload(c, &c->d_cols2, cols2))) return bail(rc);
   {
     // Interior / boundary split of the tiles.  A tile is a boundary tile when
     // a ghost cell that another rank fills lies within STENCIL_REACH cells of
@@ -872,8 +897,10 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
     if (which == 1) err = fill(c, U1, 5, 0, DtSrc{nullptr, 0.0, 0, -1}, s);
     if (which == 3) err = fill(c, R1, 4, 5, DtSrc{nullptr, 0.0, 0, -1}, s);
     // candidates: threads x schedule on TS^3 tiles, and the columns (FP32
-    // hydro: also CNT + 32 threads at 3 or 2 CTAs per SM)
-    const int ncand = (c->fp32 && !is_rad) ? 9 : 7;
+    // hydro, and radiation with the Levermore closure: also CNT + 32 threads
+    // at 3 or 2 CTAs per SM)
+    const bool wide = c->fp32 && (!is_rad || c->p.closure == QK_CLOSURE_LEVERMORE);
+    const int ncand = wide ? 9 : 7;
     for (int ci = 0; ci < ncand && err == cudaSuccess; ++ci) {
         const int cfg = ci < 6    ? cfg_make(threads[ci / 2], ci % 2)
                         : ci == 6 ? cfg_make(CNT, 0, 1)
@@ -885,12 +912,13 @@ int qk_autotune(qk_ctx *c, void *const hydro[5], void *const rad[4], int32_t out
             err = cudaMemcpyAsync(Uc[q], hydro[q], (size_t)c->field_len * c->elem,
                                   cudaMemcpyDeviceToDevice, s);
         if (err != cudaSuccess) break;
+        const Geometry gc = geom_cfg(c, cfg);
         auto launch = [&]() {
           if (!is_rad)
-            return launch_hydro_stage(c->fp32, stage, g, c->p, hydro, stage == 2 ? U1 : nullptr,
+            return launch_hydro_stage(c->fp32, stage, gc, c->p, hydro, stage == 2 ? U1 : nullptr,
                                       stage == 1 ? U1 : tmp, dth, 0, cfg,
                                       c->p.flattening ? c->chi : nullptr, s);
-          return launch_rad_stage(c->fp32, stage, g, c->p, rad, stage == 2 ? R1 : nullptr,
+          return launch_rad_stage(c->fp32, stage, gc, c->p, rad, stage == 2 ? R1 : nullptr,
                                   stage == 1 ? R1 : Rt, hydro[0], dtr, 0, cfg, s, nullptr,
                                   which == 3 && fused ? &fx : nullptr);
         };
@@ -1042,7 +1070,8 @@ int qk_hydro_stage(qk_ctx *c, int32_t stage, void *const U0[5], void *const U1[5
   if (c->p.flattening)
     QK_CUDA(c, launch_flatten(c->fp32, geom(c), c->p, stage == 1 ? U0 : U1, c->chi,
                               (cudaStream_t)stream));
-  QK_CUDA(c, launch_hydro_stage(c->fp32, stage, geom(c), c->p, U0, stage == 2 ? U1 : nullptr,
+  QK_CUDA(c, launch_hydro_stage(c->fp32, stage, geom_cfg(c, c->cfg[stage - 1]), c->p, U0,
+                                stage == 2 ? U1 : nullptr,
                                 Uout, d, 0, c->cfg[stage - 1], c->p.flattening ? c->chi : nullptr,
                                 (cudaStream_t)stream));
   return QK_OK;
@@ -1064,7 +1093,8 @@ int qk_rad_stage(qk_ctx *c, int32_t stage, void *const R0[4], void *const R1[4],
     for (int q = 0; q < 4; ++q)
       if (Rout[q] == R1[q]) return fail(c, QK_EINVAL, "Rout must not alias R1");
   DtSrc d{nullptr, dt_rad, 2, -1};
-  QK_CUDA(c, launch_rad_stage(c->fp32, stage, geom(c), c->p, R0, stage == 2 ? R1 : nullptr, Rout,
+  QK_CUDA(c, launch_rad_stage(c->fp32, stage, geom_cfg(c, c->cfg[1 + stage]), c->p, R0,
+                              stage == 2 ? R1 : nullptr, Rout,
                               rho, d, 0, c->cfg[2 + stage - 1], (cudaStream_t)stream));
   return QK_OK;
 }
@@ -1081,7 +1111,8 @@ int qk_rad_stage2_exchange(qk_ctx *c, void *const R0[4], void *const R1[4], void
     if (Rout[q] == R1[q]) return fail(c, QK_EINVAL, "Rout must not alias R1");
   DtSrc d{nullptr, dt_rad, 2, -1};
   const FuseArgs fx{hydro, nullptr, c->src, c->d_status};
-  QK_CUDA(c, launch_rad_stage(c->fp32, 2, geom(c), c->p, R0, R1, Rout, hydro[0], d, 0, c->cfg[3],
+  QK_CUDA(c, launch_rad_stage(c->fp32, 2, geom_cfg(c, c->cfg[3]), c->p, R0, R1, Rout, hydro[0], d,
+                              0, c->cfg[3],
                               (cudaStream_t)stream, nullptr, &fx));
   return QK_OK;
 }
@@ -1118,10 +1149,13 @@ int qk_timestep(qk_ctx *c, void *const hydro[5], double out[4], void *stream) {
 }
 
 // The work lists of patch b alone (tiles and columns are grouped by patch).
-static Geometry patch_geom(const qk_ctx *c, Geometry g, int b) {
+static Geometry patch_geom(const qk_ctx *c, Geometry g, int b, int cfg = 0) {
   g.tiles = c->d_tiles + c->tile_start[b];
   g.ntiles = c->tile_start[b + 1] - c->tile_start[b];
-  if (g.cols) {
+  if (g.cols && two_cta_cols(c, cfg)) {
+    g.cols = c->d_cols2 + c->col_start2[b];
+    g.ncols = c->col_start2[b + 1] - c->col_start2[b];
+  } else if (g.cols) {
     g.cols = c->d_cols + c->col_start[b];
     g.ncols = c->col_start[b + 1] - c->col_start[b];
   }
@@ -1134,7 +1168,7 @@ static Geometry patch_geom(const qk_ctx *c, Geometry g, int b) {
 static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *const *U1,
                                   void *const *Uo, DtSrc dt, cudaStream_t s,
                                   const LoPtrs *lo = nullptr) {
-  const Geometry g = geom(c);
+  const Geometry g = geom_cfg(c, c->cfg[stage - 1]);
   const void *chi = c->p.flattening ? c->chi : nullptr;
   if (chi) {
     cudaError_t e = launch_flatten(c->fp32, g, c->p, stage == 1 ? U0 : U1, c->chi, s);
@@ -1144,7 +1178,7 @@ static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *c
     return launch_hydro_stage(c->fp32, stage, g, c->p, U0, U1, Uo, dt, 0, c->cfg[stage - 1], chi,
                               s, lo);
   for (int b = 0; b < c->nbox_dev; ++b) {
-    const Geometry gb = patch_geom(c, g, b);
+    const Geometry gb = patch_geom(c, g, b, c->cfg[stage - 1]);
     cudaError_t e = launch_hydro_stage(c->fp32, stage, gb, c->p, U0, U1, Uo, dt, 0,
                                        c->cfg[stage - 1], chi, s, lo);
     if (e != cudaSuccess) return e;
@@ -1155,12 +1189,12 @@ static cudaError_t hydro_launches(qk_ctx *c, int stage, void *const *U0, void *c
 static cudaError_t rad_launches(qk_ctx *c, int stage, void *const *R0, void *const *R1,
                                 void *const *Ro, const void *rho, DtSrc dt, cudaStream_t s,
                                 const LoPtrs *lo = nullptr, const FuseArgs *fx = nullptr) {
-  const Geometry g = geom(c);
+  const Geometry g = geom_cfg(c, c->cfg[1 + stage]);
   if (c->launch_mode == QK_LAUNCH_BATCHED || c->part != QK_PART_ALL)
     return launch_rad_stage(c->fp32, stage, g, c->p, R0, R1, Ro, rho, dt, 0, c->cfg[1 + stage], s,
                             lo, fx);
   for (int b = 0; b < c->nbox_dev; ++b) {
-    const Geometry gb = patch_geom(c, g, b);
+    const Geometry gb = patch_geom(c, g, b, c->cfg[1 + stage]);
     cudaError_t e = launch_rad_stage(c->fp32, stage, gb, c->p, R0, R1, Ro, rho, dt, 0,
                                      c->cfg[1 + stage], s, lo, fx);
     if (e != cudaSuccess) return e;

@@ -48,10 +48,15 @@ template <typename T> struct ColMinBlocksRad {
   static constexpr int value = sizeof(T) == 4 ? COL_CTAS_FP32 : COL_CTAS_FP64;
 };
 
-template <typename T, int STAGE, int CL, bool EX>
-__global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
+// NT threads per CTA: CNT (one per footprint cell) or, FP32, CNT + 32 (a
+// ninth warp without an own cell, so that a plane's x/y pairs come to one per
+// thread), registers held to MINB CTAs per SM.
+template <typename T, int STAGE, int CL, bool EX, int NT = CNT,
+          int MINB = ColMinBlocksRad<T>::value>
+__global__ void __launch_bounds__(NT, MINB)
     rad_column_kernel(Geometry g, qk_params p, SC<T> K, F4<T> R0, F4<T> R1, F4<T> Ro,
                       const T *rho, DtSrc dts, ExFuse<T> xf) {
+  static_assert(NT >= CNT && NT >= CNRING, "one own cell per thread, ring cells on the last");
   if (skip_substep(dts)) return;
   constexpr bool kAB = ColRadSmem<T>::kAB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -68,6 +73,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
   const F4<T> src = STAGE == 1 ? R0 : R1;
   const int rk = p.recon;
   const int t = threadIdx.x;
+  const bool has_own = t < CNT;  // threads CNT.. (a ninth warp) own no cell
   const int ti = t % CW, tj = t / CW;
   ExStat xs;
 
@@ -76,16 +82,16 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
     const DevBox b = g.boxes[col.box];
     const int vx = min(CW, b.n[0] - col.x0), vy = min(CW, b.n[1] - col.y0);
     const long long plane = (long long)b.sx * b.sy;
-    const bool own_load = ti < vx + HALO && tj < vy + HALO;
-    const bool own_valid = ti < vx && tj < vy;
+    const bool own_load = has_own && ti < vx + HALO && tj < vy + HALO;
+    const bool own_valid = has_own && ti < vx && tj < vy;
     // the cell-average closure of the own cell is read by faces of valid cells
-    const bool own_near = ti <= vx && tj <= vy;
-    const long long own0 = cell_elem(b, g.ng, col.x0 + ti, col.y0 + tj, 0);
+    const bool own_near = has_own && ti <= vx && tj <= vy;
+    const long long own0 = has_own ? cell_elem(b, g.ng, col.x0 + ti, col.y0 + tj, 0) : 0;
     int ri = 0, rj = 0, rside = 0;
     bool ring = false;
     // ring cells go to the last CNRING threads (the first warp takes the
     // extra reconstruction round of the plane)
-    const int rt = t - (CNT - CNRING);
+    const int rt = t - (NT - CNRING);
     if (rt >= 0) {
       rside = rt / (HALO * CW);
       const int r = rt % (HALO * CW), h = r % HALO, along = r / HALO;
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
 
     // start-up: face z0 - 1/2 from cells z0-1 and z0
     T carryR[4], Fz[4];
-    {
+    if (has_own) {
       T st[5][4], rks[5];
 #pragma unroll
       for (int o = 0; o < 5; ++o) load_plane(col.z0 - 3 + o, st[o], rks[o]);
@@ -261,7 +267,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
             sm.ab[1][s] = bz0;
           }
         }
-      } else {
+      } else if (has_own) {
         win[4][0] = T(1);
         win[4][1] = win[4][2] = win[4][3] = T(0);
         rkw[4] = T(0);
@@ -308,7 +314,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
         // each position's cell average (x: T_xx, y: T_yy); every read lies in
         // the plane for r < CXPOS CW, and a lane whose position is not needed
         // writes a slot that no face reads
-        for (int r = t; r < CXPOS * CW; r += CNT) {
+        for (int r = t; r < CXPOS * CW; r += NT) {
           const int cjx = r / CXPOS, cix = r % CXPOS - 1;
           const int ciy = r % CW, cjy = r / CW - 1;
           const bool okx = cjx < vy && cix <= vx, oky = ciy < vx && cjy <= vy;
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
           sm.sq[1][r] = qsqrt(Tdd.y);
         }
       } else {
-        for (int it = t; it < 2 * CXPOS * CW; it += CNT) {
+        for (int it = t; it < 2 * CXPOS * CW; it += NT) {
           const int dir = it >= CXPOS * CW;
           const int r = it - dir * CXPOS * CW;
           int ci, cj, base, stride;
@@ -371,7 +377,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
       }
       T Fzn[4];
       T az1 = T(0), bz1 = T(0), sqz1 = T(0);
-      {
+      if (has_own) {
         T qL[4], qR[4];
         recon_z(win, qL, qR);  // cell z+1
         zclosure(win[2], az1, bz1, sqz1);
@@ -385,9 +391,9 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
         // FP32: face r of the x rows and face r of the y columns as the two
         // lanes of rad_face_hll2, each in its own frame (E_r, f_n, f_t1,
         // f_t2): x (E_r, f_x, f_y, f_z), y (E_r, f_y, f_z, f_x)
-        // (the pairs beyond CNT fall to the second warp: the first already
+        // (the pairs beyond NT fall to the second warp: the first already
         // took the extra reconstruction round)
-        for (int r = (t + CNT - 32) % CNT; r < CXFACE * CW; r += CNT) {
+        for (int r = (t + NT - 32) % NT; r < CXFACE * CW; r += NT) {
           const int fx = r % CXFACE, cjx = r / CXFACE;
           const int ciy = r % CW, fy = r / CW;
           const bool okx = cjx < vy && fx <= vx, oky = ciy < vx && fy <= vy;
@@ -416,7 +422,7 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
           }
         }
       } else {
-        for (int it = t; it < 2 * CXFACE * CW; it += CNT) {
+        for (int it = t; it < 2 * CXFACE * CW; it += NT) {
           const int dir = it >= CXFACE * CW;
           const int r = it - dir * CXFACE * CW;
           int il, ir, sa, sb;
@@ -495,24 +501,27 @@ __global__ void __launch_bounds__(CNT, ColMinBlocksRad<T>::value)
           }
         }
       }
+      if (has_own) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) Fz[q] = Fzn[q];
+        for (int q = 0; q < 4; ++q) Fz[q] = Fzn[q];
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        rkw[o] = rkw[o + 1];
+        for (int o = 0; o < 4; ++o) {
+          rkw[o] = rkw[o + 1];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) win[o][q] = win[o + 1][q];
+          for (int q = 0; q < 4; ++q) win[o][q] = win[o + 1][q];
+        }
+        az0 = az1;
+        bz0 = bz1;
+        sqz0 = sqz1;
       }
-      az0 = az1;
-      bz0 = bz1;
-      sqz0 = sqz1;
     }
     __syncthreads();
   }
   if constexpr (EX) exchange_status(xf.st, xs.max, xs.flags, xs.bad);
 }
 
-template <typename T, int STAGE, int CL, bool EX>
+template <typename T, int STAGE, int CL, bool EX, int NT = CNT,
+          int MINB = ColMinBlocksRad<T>::value>
 static cudaError_t launch_rad_col_one(const Geometry &g, const qk_params &p, void *const *R0,
                                       void *const *R1, void *const *Ro, const void *rho,
                                       DtSrc dt, const FuseArgs *fx, cudaStream_t s) {
@@ -531,18 +540,38 @@ static cudaError_t launch_rad_col_one(const Geometry &g, const qk_params &p, voi
     xf.on = 1;
   }
   const int smem = (int)sizeof(ColRadSmem<T>);
-  auto kern = rad_column_kernel<T, STAGE, CL, EX>;
+  auto kern = rad_column_kernel<T, STAGE, CL, EX, NT, MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0, nsm = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CNT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
   int grid = nsm * (per_sm > 0 ? per_sm : 1);
   if (grid > g.ncols) grid = g.ncols;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, CNT, smem, s>>>(g, p, make_sc<T>(p), a, b, c, (const T *)rho, dt, xf);
+  kern<<<grid, NT, smem, s>>>(g, p, make_sc<T>(p), a, b, c, (const T *)rho, dt, xf);
   return cudaGetLastError();
+}
+
+// FP32 column launches of one stage form (STAGE, EX) in launch configuration
+// `cfg`: CNT threads, or (Levermore closure, the default) CNT + 32 threads at
+// 3 (schedule 0) or 2 (schedule 1) CTAs per SM; other closures run the
+// CNT-thread kernel for every column configuration.
+template <int STAGE, int CL, bool EX>
+static cudaError_t launch_rad_col_f32(int cfg, const Geometry &g, const qk_params &p,
+                                      void *const *R0, void *const *R1, void *const *Ro,
+                                      const void *rho, DtSrc dt, const FuseArgs *fx,
+                                      cudaStream_t s) {
+  if constexpr (CL == QK_CLOSURE_LEVERMORE) {
+    if (cfg_threads(cfg) == CNT + 32)
+      return cfg_sched(cfg)
+                 ? launch_rad_col_one<float, STAGE, CL, EX, CNT + 32, 2>(g, p, R0, R1, Ro, rho,
+                                                                          dt, fx, s)
+                 : launch_rad_col_one<float, STAGE, CL, EX, CNT + 32, 3>(g, p, R0, R1, Ro, rho,
+                                                                          dt, fx, s);
+  }
+  return launch_rad_col_one<float, STAGE, CL, EX>(g, p, R0, R1, Ro, rho, dt, fx, s);
 }
 
 // Column launches of one closure (instantiated per closure in
@@ -551,11 +580,11 @@ template <int CL>
 cudaError_t launch_rad_column_closure(int fp32, int stage, const Geometry &g, const qk_params &p,
                                       void *const *R0, void *const *R1, void *const *Ro,
                                       const void *rho, DtSrc dt, const FuseArgs *fx,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, int cfg) {
   if (fp32) {
-    if (stage == 1) return launch_rad_col_one<float, 1, CL, false>(g, p, R0, R1, Ro, rho, dt, fx, s);
-    if (fx) return launch_rad_col_one<float, 2, CL, true>(g, p, R0, R1, Ro, rho, dt, fx, s);
-    return launch_rad_col_one<float, 2, CL, false>(g, p, R0, R1, Ro, rho, dt, fx, s);
+    if (stage == 1) return launch_rad_col_f32<1, CL, false>(cfg, g, p, R0, R1, Ro, rho, dt, fx, s);
+    if (fx) return launch_rad_col_f32<2, CL, true>(cfg, g, p, R0, R1, Ro, rho, dt, fx, s);
+    return launch_rad_col_f32<2, CL, false>(cfg, g, p, R0, R1, Ro, rho, dt, fx, s);
   }
   if (stage == 1) return launch_rad_col_one<double, 1, CL, false>(g, p, R0, R1, Ro, rho, dt, fx, s);
   if (fx) return launch_rad_col_one<double, 2, CL, true>(g, p, R0, R1, Ro, rho, dt, fx, s);

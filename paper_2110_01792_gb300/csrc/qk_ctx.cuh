@@ -34,6 +34,9 @@ struct qk_ctx {
   Column *d_cols = nullptr;    // column work list of the plane-marching kernels
   int ncols = 0;
   std::vector<int> col_start;  // first column of each owned patch (grouped by patch)
+  Column *d_cols2 = nullptr;   // FP32: the list chunked for two column CTAs per SM
+  int ncols2 = 0;
+  std::vector<int> col_start2;
   int n_interior = 0;
   int part = QK_PART_ALL;
   // sharded contexts: owner rank of every patch, this rank, and the halo

@@ -296,7 +296,8 @@ struct FuseArgs {
 
 cudaError_t launch_rad_column(int fp32, int stage, const Geometry &g, const qk_params &p,
                               void *const *R0, void *const *R1, void *const *Rout,
-                              const void *rho, DtSrc dt, const FuseArgs *fx, cudaStream_t s);
+                              const void *rho, DtSrc dt, const FuseArgs *fx, cudaStream_t s,
+                              int cfg);
 cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_params &p,
                              void *const *R0, void *const *R1, void *const *Rout,
                              const void *rho, DtSrc dt, int grid, int cfg, cudaStream_t s,

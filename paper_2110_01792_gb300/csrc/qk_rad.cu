@@ -22,7 +22,7 @@ cudaError_t launch_rad_stage(int fp32, int stage, const Geometry &g, const qk_pa
                              const LoPtrs *lo, const FuseArgs *fx) {
   // columns (shape 1) when the geometry has them; compensated states use tiles
   if (cfg_shape(cfg) == 1 && g.cols && g.ncols > 0 && !lo)
-    return launch_rad_column(fp32, stage, g, p, R0, R1, Rout, rho, dt, fx, s);
+    return launch_rad_column(fp32, stage, g, p, R0, R1, Rout, rho, dt, fx, s, cfg);
   switch (p.closure) {
     case QK_CLOSURE_MINERBO:
       return launch_rad_closure<QK_CLOSURE_MINERBO>(fp32, stage, g, p, R0, R1, Rout, rho, dt, grid,
