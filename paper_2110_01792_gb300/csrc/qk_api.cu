@@ -278,6 +278,11 @@ static int build_copies(qk_ctx *c, std::vector<Copy> &out,
                         cp.sx = step[0];
                         cp.sy = step[1] * qsx;
                         cp.sz = step[2] * qsx * qsy;
+                        // 16-byte rows (4 floats or 2 doubles) when every row of the
+                        // region starts on a multiple of 4 elements on both sides
+                        cp.vec = cp.sx == 1 && cp.ex % 4 == 0 && cp.dst % 4 == 0 &&
+                                 cp.src % 4 == 0 && cp.dsx % 4 == 0 && cp.sy % 4 == 0 &&
+                                 cp.sz % 4 == 0;
                         if (!sharded) {
                           out.push_back(cp);
                         } else {

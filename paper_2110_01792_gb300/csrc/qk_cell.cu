@@ -222,15 +222,53 @@ __device__ __forceinline__ T *field_ptr(const F5<T> &fa, const F4<T> &fb, int f)
   return f < 5 ? fa.f[f] : fb.f[f - 5];
 }
 
+// 16-byte vector of the field type (4 floats or 2 doubles) and its negation.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  typedef float4 type;
+  static constexpr int n = 4;
+  __device__ static float4 neg(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+};
+template <> struct Vec16<double> {
+  typedef double2 type;
+  static constexpr int n = 2;
+  __device__ static double2 neg(double2 v) { return make_double2(-v.x, -v.y); }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) ghost_fill_kernel(const Copy *copies, const Chunk *chunks,
                                                          F5<T> fa, F4<T> fb, int nf, int first,
-                                                         DtSrc pred) {
+                                                         DtSrc pred, int vec_ok) {
   if (skip_substep(pred)) return;
   const Chunk ch = chunks[blockIdx.x];
   const Copy cp = copies[ch.copy];
   const int ncell = cp.ex * cp.ey * cp.ez;
   const int end = min(ncell, ch.start + CHUNK_CELLS);
+  if (vec_ok && cp.vec) {
+    // rows of 4-element multiples, every row start on a 16-byte boundary (the
+    // field pointers are 16-byte aligned): 16-byte loads and stores; the
+    // chunk starts on a multiple of 4 cells, so no vector crosses a row
+    typedef typename Vec16<T>::type VT;
+    constexpr int V = Vec16<T>::n;
+    for (int l = ch.start + threadIdx.x * V; l < end; l += blockDim.x * V) {
+      const int x = l % cp.ex;
+      const int r = l / cp.ex;
+      const int y = r % cp.ey;
+      const int z = r / cp.ey;
+      const long long d = cp.dst + ((long long)z * cp.dsy + y) * cp.dsx + x;
+      const long long s = cp.src + z * cp.sz + y * cp.sy + x;
+#pragma unroll
+      for (int f = 0; f < 9; ++f) {
+        if (f >= nf) break;
+        T *fld = field_ptr(fa, fb, f);
+        const int ax = field_axis(first + f);
+        const VT v = *reinterpret_cast<const VT *>(fld + s);
+        *reinterpret_cast<VT *>(fld + d) =
+            (ax >= 0 && ((cp.flip >> ax) & 1)) ? Vec16<T>::neg(v) : v;
+      }
+    }
+    return;
+  }
   for (int l = ch.start + threadIdx.x; l < end; l += blockDim.x) {
     const int x = l % cp.ex;
     const int r = l / cp.ex;
@@ -252,16 +290,22 @@ __global__ void __launch_bounds__(256) ghost_fill_kernel(const Copy *copies, con
 cudaError_t launch_ghost_fill(int fp32, const Copy *copies, const Chunk *chunks, int nchunks,
                               void *const *fields, int nf, int first, DtSrc pred, cudaStream_t s) {
   if (nchunks < 1 || nf < 1) return cudaSuccess;
+  // the vector path needs every field pointer on a 16-byte boundary
+  int vec_ok = 1;
+  for (int q = 0; q < nf; ++q)
+    if (reinterpret_cast<uintptr_t>(fields[q]) % 16 != 0) vec_ok = 0;
   if (fp32) {
     F5<float> a{}; F4<float> b{};
     for (int q = 0; q < nf && q < 5; ++q) a.f[q] = (float *)fields[q];
     for (int q = 5; q < nf; ++q) b.f[q - 5] = (float *)fields[q];
-    ghost_fill_kernel<float><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, first, pred);
+    ghost_fill_kernel<float><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, first, pred,
+                                                     vec_ok);
   } else {
     F5<double> a{}; F4<double> b{};
     for (int q = 0; q < nf && q < 5; ++q) a.f[q] = (double *)fields[q];
     for (int q = 5; q < nf; ++q) b.f[q - 5] = (double *)fields[q];
-    ghost_fill_kernel<double><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, first, pred);
+    ghost_fill_kernel<double><<<nchunks, 256, 0, s>>>(copies, chunks, a, b, nf, first, pred,
+                                                      vec_ok);
   }
   return cudaGetLastError();
 }

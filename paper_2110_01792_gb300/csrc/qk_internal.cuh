@@ -75,6 +75,8 @@ struct Copy {
   int ex, ey, ez;      // extents
   int dsx, dsy;        // destination row / plane strides (elements / rows)
   int flip;            // bit d: negate the d-components of vectors (reflecting face)
+  int vec;             // 1: rows move as 16-byte vectors (x step +1; extent, offsets and
+                       // row / plane strides multiples of 4 elements)
   long long sx, sy, sz;  // source element step per x, y, z step: +-1 / +-row / +-plane,
                          // negative across a reflecting face, 0 across an outflow face
 };
