@@ -401,19 +401,24 @@ __global__ void __launch_bounds__(NT, MINB)
           const int ilx = cjx * CXPOS + fx, ily = fy * CW + ciy;
           const int sax = cslot(fx - 1, cjx), say = cslot(ciy, fy - 1);
           constexpr int qy[4] = {0, 2, 3, 1};
-          f2 wL[4], wR[4], avL[4], avR[4], out[4];
+          f2 wL[4], wR[4], out[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             wL[k] = make_float2(sm.rec[0][2 * k + 1][ilx], sm.rec[1][2 * qy[k] + 1][ily]);
             wR[k] = make_float2(sm.rec[0][2 * k][ilx + 1], sm.rec[1][2 * qy[k]][ily + CW]);
-            avL[k] = make_float2(sm.prim[k][sax], sm.prim[qy[k]][say]);
-            avR[k] = make_float2(sm.prim[k][sax + 1], sm.prim[qy[k]][say + CPW]);
           }
+          auto averages = [&](f2 *avL, f2 *avR) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              avL[k] = make_float2(sm.prim[k][sax], sm.prim[qy[k]][say]);
+              avR[k] = make_float2(sm.prim[k][sax + 1], sm.prim[qy[k]][say + CPW]);
+            }
+          };
           const f2 S = mul2(p2(chat), make_float2(fmaxf(sm.sq[0][ilx], sm.sq[0][ilx + 1]),
                                                   fmaxf(sm.sq[1][ily], sm.sq[1][ily + CW])));
           const f2 rka = make_float2(sm.rk[sax], sm.rk[say]);
           const f2 rkb = make_float2(sm.rk[sax + 1], sm.rk[say + CPW]);
-          rad_face_hll2<CL>(wL, wR, avL, avR, S, rka, rkb, make_float2(dx[0], dx[1]), c, chat,
+          rad_face_hll2<CL>(wL, wR, averages, S, rka, rkb, make_float2(dx[0], dx[1]), c, chat,
                             hchat_c, hccc, p.tau_correction, out);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {

@@ -173,18 +173,21 @@ __device__ __forceinline__ void closure_ab2(f2 fsq, f2 &a, f2 &b) {
 
 // The radiation HLL face flux per lane (rad_face_hll in qk_rad.cuh), each
 // lane in its face's own frame: w = (E_r, f_n, f_t1, f_t2), out = (energy
-// flux, F_n flux, F_t1 flux, F_t2 flux).  avL / avR: the two cell averages
-// in the same frame, which replace the lane's face states where either of
-// them has |f| > 1; S the lane's wavespeed, rka / rkb the cells' rho kappa_R.
-template <int CL>
-__device__ __forceinline__ void rad_face_hll2(f2 wL[4], f2 wR[4], const f2 avL[4],
-                                              const f2 avR[4], f2 S, f2 rka, f2 rkb, f2 dx,
-                                              float c, float chat, float hchat_c, float hccc,
-                                              int tau_corr, f2 out[4]) {
+// flux, F_n flux, F_t1 flux, F_t2 flux).  averages(avL, avR) supplies the two
+// cell averages in the same frame (called only when some lane needs them):
+// they replace the lane's face states where either of them has |f| > 1; S
+// the lane's wavespeed, rka / rkb the cells' rho kappa_R.
+template <int CL, class Averages>
+__device__ __forceinline__ void rad_face_hll2(f2 wL[4], f2 wR[4], Averages averages, f2 S,
+                                              f2 rka, f2 rkb, f2 dx, float c, float chat,
+                                              float hchat_c, float hccc, int tau_corr,
+                                              f2 out[4]) {
   f2 fL2 = fma2(wL[3], wL[3], fma2(wL[1], wL[1], mul2(wL[2], wL[2])));
   f2 fR2 = fma2(wR[3], wR[3], fma2(wR[1], wR[1], mul2(wR[2], wR[2])));
   const bool fbx = fL2.x > 1.0f || fR2.x > 1.0f, fby = fL2.y > 1.0f || fR2.y > 1.0f;
   if (fbx || fby) {
+    f2 avL[4], avR[4];
+    averages(avL, avR);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       wL[q] = sel2(fbx, fby, avL[q], wL[q]);
