@@ -19,6 +19,17 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 // a - b as fma(b, -1, a): one packed instruction, exact like a subtraction
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, p2(-1.0f), a); }
+// three-input FP32 minimum / maximum (one instruction on sm_100 and later)
+__device__ __forceinline__ float fmin3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
 __device__ __forceinline__ f2 min2(f2 a, f2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
 __device__ __forceinline__ f2 max2(f2 a, f2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
 __device__ __forceinline__ f2 rcp2(f2 a) { return make_float2(qrcp(a.x), qrcp(a.y)); }
@@ -37,14 +48,15 @@ __device__ __forceinline__ f2 sel2(bool cx, bool cy, f2 a, f2 b) {
 __device__ __forceinline__ void ppm2(f2 s0, f2 s1, f2 s2, f2 s3, f2 s4, f2 &qL, f2 &qR) {
   const f2 fL = fma2(p2(7.0f / 12.0f), add2(s1, s2), mul2(p2(-1.0f / 12.0f), add2(s0, s3)));
   const f2 fR = fma2(p2(7.0f / 12.0f), add2(s2, s3), mul2(p2(-1.0f / 12.0f), add2(s1, s4)));
-  const f2 lo = min2(s1, min2(s2, s3)), hi = max2(s1, max2(s2, s3));
+  const f2 lo = make_float2(fmin3f(s1.x, s2.x, s3.x), fmin3f(s1.y, s2.y, s3.y));
+  const f2 hi = make_float2(fmax3f(s1.x, s2.x, s3.x), fmax3f(s1.y, s2.y, s3.y));
   const f2 l = min2(max2(fL, lo), hi), r = min2(max2(fR, lo), hi);
   const f2 dm = sub2(s2, s1), dp = sub2(s3, s2);
   const f2 pr = mul2(dm, dp);
   const f2 q4 = mul2(p2(0.25f), add2(dm, dp));
   f2 h;
-  h.x = pr.x > 0.0f ? copysignf(fminf(fminf(fabsf(dm.x), fabsf(dp.x)), fabsf(q4.x)), dp.x) : 0.0f;
-  h.y = pr.y > 0.0f ? copysignf(fminf(fminf(fabsf(dm.y), fabsf(dp.y)), fabsf(q4.y)), dp.y) : 0.0f;
+  h.x = pr.x > 0.0f ? copysignf(fmin3f(fabsf(dm.x), fabsf(dp.x), fabsf(q4.x)), dp.x) : 0.0f;
+  h.y = pr.y > 0.0f ? copysignf(fmin3f(fabsf(dm.y), fabsf(dp.y), fabsf(q4.y)), dp.y) : 0.0f;
   const f2 t3 = mul2(p2(3.0f), s2);
   const f2 ln = fma2(p2(-2.0f), r, t3), rn = fma2(p2(-2.0f), l, t3);
   const f2 d = sub2(r, l);
@@ -64,8 +76,8 @@ __device__ __forceinline__ void plm2(f2 s1, f2 s2, f2 s3, f2 &qL, f2 &qR) {
   const f2 pr = mul2(dm, dp);
   const f2 q4 = mul2(p2(0.25f), add2(dm, dp));
   f2 h;
-  h.x = pr.x > 0.0f ? copysignf(fminf(fminf(fabsf(dm.x), fabsf(dp.x)), fabsf(q4.x)), dp.x) : 0.0f;
-  h.y = pr.y > 0.0f ? copysignf(fminf(fminf(fabsf(dm.y), fabsf(dp.y)), fabsf(q4.y)), dp.y) : 0.0f;
+  h.x = pr.x > 0.0f ? copysignf(fmin3f(fabsf(dm.x), fabsf(dp.x), fabsf(q4.x)), dp.x) : 0.0f;
+  h.y = pr.y > 0.0f ? copysignf(fmin3f(fabsf(dm.y), fabsf(dp.y), fabsf(q4.y)), dp.y) : 0.0f;
   qL = sub2(s2, h);
   qR = add2(s2, h);
 }
