@@ -361,8 +361,8 @@ def _src_hash(kind: str) -> str:
     cs = os.path.join(ROOT, "paper_2110_01792_gb300", "csrc")
     files = {"rad": ["qk_rad.cu", "qk_rad.cuh", "qk_exchange.cuh"], "hydro": ["qk_hydro.cu"],
              "radcol": ["qk_column_rad.cu", "qk_column_rad.cuh", "qk_rad.cuh",
-                        "qk_exchange.cuh"],
-             "hydrocol": ["qk_column.cu"],
+                        "qk_exchange.cuh", "qk_pair.cuh"],
+             "hydrocol": ["qk_column.cu", "qk_pair.cuh"],
              "cell": ["qk_cell.cu", "qk_exchange.cuh"]}[kind]
     h = hashlib.sha1()
     for f in files + ["qk_device.cuh", "qk_internal.cuh"]:

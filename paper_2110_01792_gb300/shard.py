@@ -317,8 +317,9 @@ def run_local(steppers):
 
 def run_distributed(stepper, comm_stream=None):
     """Advance this process's rank by one step with torch.distributed: an
-    all-reduce (MAX) for the signal speed and one isend / irecv pair per peer
-    for every ghost exchange (device buffers: NCCL; host buffers: gloo).  On
+    all-reduce (MAX) for the signal speed and, for every ghost exchange, one
+    batch of an isend / irecv pair per peer (device buffers: NCCL, one group;
+    host buffers: gloo).  On
     the GPU the transfers are issued from ``comm_stream`` (created if None),
     which waits only for the pack, so that they run while the interior tiles
     of an overlapping stepper compute; waiting on the requests then orders the
@@ -339,8 +340,11 @@ def run_distributed(stepper, comm_stream=None):
             _, sends, recvs, event = msg
 
             def issue():
-                r = [dist.isend(buf, p) for p, buf in sorted(sends.items())]
-                return r + [dist.irecv(buf, p) for p, buf in sorted(recvs.items())]
+                # one batch (a NCCL group on the GPU): a send and a receive
+                # between the same two ranks must not wait on each other
+                ops = [dist.P2POp(dist.isend, buf, p) for p, buf in sorted(sends.items())]
+                ops += [dist.P2POp(dist.irecv, buf, p) for p, buf in sorted(recvs.items())]
+                return dist.batch_isend_irecv(ops) if ops else []
 
             if cuda:
                 with torch.cuda.stream(comm_stream):
