@@ -344,15 +344,15 @@ def time_kernel(torch, fn, reps, stream):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
-# (profiles/ncu_*_128.md), valid only while the kernel's sources hash to the
-# value recorded at capture time.
+# (profiles/ncu_*.md), valid only while the kernel's sources hash to the value
+# recorded at capture time.
 NCU_TRAFFIC = {
-    ("rhd128", "rad_stage_ex_kernel<double>"): (342.76e6, "rad", "8d7d55bb2947"),
-    ("rhd128", "rad_stage_kernel<double,1>"): (135.02e6, "rad", "8d7d55bb2947"),
-    ("rhd128", "hydro_stage_kernel<double,1>"): (150.91e6, "hydro", "89f91359c44a"),
-    ("rhd128", "rad_column_kernel<float,2,EX>"): (164.92e6, "radcol", "715cee76a212"),
-    ("rhd128", "rad_column_kernel<float,1>"): (54.69e6, "radcol", "715cee76a212"),
-    ("rhd128", "hydro_column_kernel<float,1>"): (58.73e6, "hydrocol", "f2e0909c7b7a"),
+    ("rhd128", "rad_stage_ex_kernel<double>"): (343.60e6, "rad", "d29a954f2328"),
+    ("rhd128", "rad_stage_kernel<double,1>"): (136.05e6, "rad", "d29a954f2328"),
+    ("rhd128", "hydro_stage_kernel<double,1>"): (151.16e6, "hydro", "4381cd0106e6"),
+    ("hydro256", "hydro_column_kernel<float,1>"): (858.49e6, "hydrocol", "283973deb5e2"),
+    ("rhd128", "rad_column_kernel<float,2,EX>"): (169.53e6, "radcol", "024efd58fe0b"),
+    ("rhd128", "rad_column_kernel<float,1>"): (56.33e6, "radcol", "024efd58fe0b"),
 }
 
 
