@@ -1020,8 +1020,9 @@ def run_sharded(args):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = cells * args.steps / float(te.item())
 
+    # a rank's patch is the 128^3 RHD box: the kernel traffic of that workload applies
     roofline = dominant_roofline(torch, qk, ctx, U, R, prec, tuned, nsub_mean, n ** 3,
-                                 "sharded", stream)
+                                 "rhd128", stream)
     peers = len(st.peers)
     # launches per step: signal speed + timestep; per ghost fill the local fill,
     # one pack and one unpack per peer with cells, and the stage (two parts
@@ -1041,8 +1042,9 @@ def run_sharded(args):
         "config": {"workload": f"sharded RHD ({n * world}x{n}x{n} periodic, one {n}^3 patch "
                                f"per rank, {args.precision})",
                    "cells": cells, "ghost": 4, "patches": world, "precision": args.precision,
-                   "l2": l2_note(h2d), "parallelism": f"{world} rank(s), patches sharded, "
-                                                      "NCCL halo exchange overlapped",
+                   "l2": l2_note(h2d),
+                   "parallelism": (f"{world} ranks, patches sharded, NCCL halo exchange overlapped"
+                                   if world > 1 else "1 rank (sharded path, no halo)"),
                    "launch_config": tuned or "default"},
         "roofline": roofline,
         "cpu_baseline": None,
