@@ -180,20 +180,23 @@ __global__ void __launch_bounds__(NT, MINB) hydro_column_kernel(Geometry g, qk_p
     // is held across the plane), FP64 into registers
     constexpr bool kStage = ColSmem<T>::kPre;
     T nown[5], nring[5];
+    // (FP32: every call commits one group, empty past the column's last
+    // plane, so that the waits below can count groups)
     auto fetch = [&](int z) {
+      const bool any = z < col.z1;
       if constexpr (kStage) {
-        if (own_load) {
+        if (any && own_load) {
 #pragma unroll
           for (int q = 0; q < 5; ++q)
             cp_async_elem(&sm.nxt[q][t], src.f[q] + own0 + (long long)(z + 3) * plane);
         }
-        if (ring) {
+        if (any && ring) {
 #pragma unroll
           for (int q = 0; q < 5; ++q)
             cp_async_elem(&sm.nxt[q][CNT + rt], src.f[q] + ring0 + (long long)z * plane);
         }
         cp_async_commit();
-      } else {
+      } else if (any) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           nown[q] = own_load ? src.f[q][own0 + (long long)(z + 3) * plane] : T(1);
@@ -201,17 +204,17 @@ __global__ void __launch_bounds__(NT, MINB) hydro_column_kernel(Geometry g, qk_p
         }
       }
     };
-    fetch(col.z0);
-    for (int z = col.z0; z < col.z1; ++z) {
+    // plane zp enters: zp+3 into the own window (which holds zp-1 .. zp+2),
+    // plane zp of the own cell and of the ring cells into smem (FP32: from the
+    // staged values, after the thread's own wait)
+    auto enter = [&](int zp) {
       if constexpr (kStage) {
-        cp_async_wait_all();
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           nown[q] = own_load ? sm.nxt[q][t] : T(1);
           nring[q] = ring ? sm.nxt[q][CNT + (ring ? rt : 0)] : T(1);
         }
       }
-      // ---- plane z+3 into the window, plane z (own + ring) into smem
       if (own_load) {
         con2prim<T>(nown, gm1, win[4]);
 #pragma unroll
@@ -226,8 +229,16 @@ __global__ void __launch_bounds__(NT, MINB) hydro_column_kernel(Geometry g, qk_p
 #pragma unroll
         for (int q = 0; q < 5; ++q) sm.prim[q][pslot(ri, rj)] = wr[q];
       }
-      if (z + 1 < col.z1) fetch(z + 1);
-      __syncthreads();
+    };
+    // Two barriers per plane: the x/y reconstruction and the z face of
+    // plane z; then the x/y faces of plane z with plane z+1 entering the
+    // primitives (no face reads them); then the epilogue of plane z.
+    fetch(col.z0);
+    if constexpr (kStage) cp_async_wait_all();
+    enter(col.z0);
+    fetch(col.z0 + 1);
+    __syncthreads();
+    for (int z = col.z0; z < col.z1; ++z) {
       if constexpr (ColSmem<T>::kPre) {
         // the epilogue's own-cell inputs, in flight during the two phases
         if (own_valid) {
@@ -380,13 +391,27 @@ __global__ void __launch_bounds__(NT, MINB) hydro_column_kernel(Geometry g, qk_p
           for (int q = 0; q < 5; ++q) sm.flux[dir][q][r] = F[q];
         }
       }
+      // ---- plane z+1 enters (the window first moves on to planes z .. z+3)
+      if (has_own) {
+#pragma unroll
+        for (int o = 0; o < 4; ++o)
+#pragma unroll
+          for (int q = 0; q < 5; ++q) win[o][q] = win[o + 1][q];
+      }
+      if (z + 1 < col.z1) {
+        // its staged values: the group before the most recent one
+        if constexpr (kStage) cp_async_wait_group<1>();
+        enter(z + 1);
+      }
+      fetch(z + 2);
       __syncthreads();
       // ---- divergence ((x + y) + z) and the RK combination of the own cell
       if (own_valid) {
         const long long e = own0 + (long long)z * plane;
         const int fx = tj * CXFACE + ti, fy = tj * CW + ti;
         constexpr bool kPre = ColSmem<T>::kPre;
-        if constexpr (kPre) cp_async_wait_all();
+        // its own-cell inputs: the group before the most recent one
+        if constexpr (kPre) cp_async_wait_group<1>();
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           T acc = (sm.flux[0][q][fx + 1] - sm.flux[0][q][fx]) * inv_dx[0];
@@ -405,14 +430,11 @@ __global__ void __launch_bounds__(NT, MINB) hydro_column_kernel(Geometry g, qk_p
       if (has_own) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) Fz[q] = Fzn[q];
-#pragma unroll
-        for (int o = 0; o < 4; ++o)
-#pragma unroll
-          for (int q = 0; q < 5; ++q) win[o][q] = win[o + 1][q];
       }
-      // the next plane's load overwrites prim after the two barriers above;
-      // rec and flux are rewritten only after the next load barrier
+      // the next plane's reconstruction rewrites rec (last read before the
+      // barrier above); its faces rewrite flux after the next barrier
     }
+    if constexpr (kStage) cp_async_wait_all();
     __syncthreads();
   }
 }

@@ -178,6 +178,11 @@ __device__ __forceinline__ void cp_async_commit() {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
+// Wait until at most N of this thread's most recent groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // Binary exponent and mantissa of a positive normal float (x = fmant(x)
 // 2^fexpo(x), fmant in [1, 2)), 2^ex for |ex| <= 126, and m 2^ex for a
