@@ -350,7 +350,7 @@ NCU_TRAFFIC = {
     ("rhd128", "rad_stage_ex_kernel<double>"): (343.60e6, "rad", "d29a954f2328"),
     ("rhd128", "rad_stage_kernel<double,1>"): (136.05e6, "rad", "d29a954f2328"),
     ("rhd128", "hydro_stage_kernel<double,1>"): (151.16e6, "hydro", "4381cd0106e6"),
-    ("hydro256", "hydro_column_kernel<float,1>"): (858.49e6, "hydrocol", "283973deb5e2"),
+    ("hydro256", "hydro_column_kernel<float,1>"): (854.41e6, "hydrocol", "f852a34270fc"),
     ("rhd128", "rad_column_kernel<float,2,EX>"): (169.53e6, "radcol", "024efd58fe0b"),
     ("rhd128", "rad_column_kernel<float,1>"): (56.33e6, "radcol", "024efd58fe0b"),
 }
