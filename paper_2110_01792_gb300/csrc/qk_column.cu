@@ -12,7 +12,7 @@
 //     reconstruction (CW+2 positions per row) and faces (CW+1 per row) of both
 //     directions are computed in one pass each;
 //   - the item -> shared-memory index maps are fixed for the whole column.
-// Three barriers per plane.  Used through launch configurations of shape 1
+// Two barriers per plane.  Used through launch configurations of shape 1
 // (cfg_shape); results equal the TS^3 tile kernels' up to the rounding of
 // the identical formulas (the same device functions).
 #include "qk_pair.cuh"
@@ -257,36 +257,66 @@ __global__ void __launch_bounds__(NT, MINB) hydro_column_kernel(Geometry g, qk_p
         // FP32: position r of the x rows and position r of the y columns as
         // the two lanes of packed arithmetic (qk_pair.cuh); both lanes' reads
         // lie in the plane for every r < CXPOS CW, and a lane whose position
-        // is not needed writes a slot that no face reads
-        for (int r = t; r < CXPOS * CW; r += NT) {
+        // is not needed writes a slot that no face reads.  Each thread takes
+        // position t with all five primitives; the positions past NT (32 of
+        // them at NT = CNT) go one primitive per warp to the first five warps,
+        // so that no warp reconstructs two whole positions while the others
+        // wait at the barrier.
+        constexpr int NREC = CXPOS * CW;
+        constexpr int NXR = NREC > NT ? NREC - NT : 0;
+        static_assert(NXR <= 32, "the extra positions fit one warp per primitive");
+        // primitive q of pair item r (ch: the flattening coefficients of its
+        // two cells)
+        auto item_ok = [&](int r, bool &okx, bool &oky) {
           const int cjx = r / CXPOS, cix = r % CXPOS - 1;
           const int ciy = r % CW, cjy = r / CW - 1;
-          const bool okx = cjx < vy && cix <= vx, oky = ciy < vx && cjy <= vy;
-          if (!okx && !oky) continue;
-          const int bx = pslot(cix - 2, cjx), by = pslot(ciy, cjy - 2);
+          okx = cjx < vy && cix <= vx;
+          oky = ciy < vx && cjy <= vy;
+          return okx || oky;
+        };
+        auto item_chi = [&](int r, bool okx, bool oky) {
           f2 ch = p2(1.0f);
           if (chi) {
+            const int cjx = r / CXPOS, cix = r % CXPOS - 1;
+            const int ciy = r % CW, cjy = r / CW - 1;
             if (okx) ch.x = chi[cell_elem(b, g.ng, col.x0 + cix, col.y0 + cjx, z)];
             if (oky) ch.y = chi[cell_elem(b, g.ng, col.x0 + ciy, col.y0 + cjy, z)];
           }
+          return ch;
+        };
+        auto recon_xy = [&](int r, int q, f2 ch) {
+          const int cjx = r / CXPOS, cix = r % CXPOS - 1;
+          const int ciy = r % CW, cjy = r / CW - 1;
+          const int bx = pslot(cix - 2, cjx), by = pslot(ciy, cjy - 2);
+          const float *pq = sm.prim[q];
+          f2 st[5];
 #pragma unroll
-          for (int q = 0; q < 5; ++q) {
-            const float *pq = sm.prim[q];
-            f2 st[5];
-#pragma unroll
-            for (int o = 0; o < 5; ++o) st[o] = make_float2(pq[bx + o], pq[by + o * CPW]);
-            f2 qL, qR;
-            recon2(rk, st[0], st[1], st[2], st[3], st[4], qL, qR);
-            if (chi) {
-              const f2 oc = sub2(p2(1.0f), ch);
-              qL = fma2(ch, qL, mul2(oc, st[2]));
-              qR = fma2(ch, qR, mul2(oc, st[2]));
-            }
-            sm.rec[0][2 * q][r] = qL.x;
-            sm.rec[0][2 * q + 1][r] = qR.x;
-            sm.rec[1][2 * q][r] = qL.y;
-            sm.rec[1][2 * q + 1][r] = qR.y;
+          for (int o = 0; o < 5; ++o) st[o] = make_float2(pq[bx + o], pq[by + o * CPW]);
+          f2 qL, qR;
+          recon2(rk, st[0], st[1], st[2], st[3], st[4], qL, qR);
+          if (chi) {
+            const f2 oc = sub2(p2(1.0f), ch);
+            qL = fma2(ch, qL, mul2(oc, st[2]));
+            qR = fma2(ch, qR, mul2(oc, st[2]));
           }
+          sm.rec[0][2 * q][r] = qL.x;
+          sm.rec[0][2 * q + 1][r] = qR.x;
+          sm.rec[1][2 * q][r] = qL.y;
+          sm.rec[1][2 * q + 1][r] = qR.y;
+        };
+        {
+          bool okx, oky;
+          if (t < NREC && item_ok(t, okx, oky)) {
+            const f2 ch = item_chi(t, okx, oky);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) recon_xy(t, q, ch);
+          }
+        }
+        if constexpr (NXR > 0) {
+          const int lane = t & 31, q = t >> 5;
+          bool okx, oky;
+          if (q < 5 && lane < NXR && item_ok(NT + lane, okx, oky))
+            recon_xy(NT + lane, q, item_chi(NT + lane, okx, oky));
         }
       } else {
         for (int it = t; it < 2 * CXPOS * CW; it += NT) {

@@ -313,29 +313,44 @@ __global__ void __launch_bounds__(NT, MINB)
         // the two lanes of packed arithmetic (qk_pair.cuh), with sqrt(T_DD) of
         // each position's cell average (x: T_xx, y: T_yy); every read lies in
         // the plane for r < CXPOS CW, and a lane whose position is not needed
-        // writes a slot that no face reads
-        for (int r = t; r < CXPOS * CW; r += NT) {
+        // writes a slot that no face reads.  Each thread takes position t
+        // (four fields and sqrt(T_DD)); the positions past NT (32 of them at
+        // NT = CNT) go one field per warp to the first four warps and their
+        // sqrt(T_DD) to the fifth, so that no warp takes two whole positions
+        // while the others wait at the barrier.
+        constexpr int NREC = CXPOS * CW;
+        constexpr int NXR = NREC > NT ? NREC - NT : 0;
+        static_assert(NXR <= 32, "the extra positions fit one warp per field");
+        auto item_ok = [&](int r) {
           const int cjx = r / CXPOS, cix = r % CXPOS - 1;
           const int ciy = r % CW, cjy = r / CW - 1;
-          const bool okx = cjx < vy && cix <= vx, oky = ciy < vx && cjy <= vy;
-          if (!okx && !oky) continue;
-          const int bx = cslot(cix - 2, cjx), by = cslot(ciy, cjy - 2);
-          f2 mid[4];
+          return (cjx < vy && cix <= vx) || (ciy < vx && cjy <= vy);
+        };
+        auto item_base = [&](int r, int &bx, int &by) {
+          const int cjx = r / CXPOS, cix = r % CXPOS - 1;
+          const int ciy = r % CW, cjy = r / CW - 1;
+          bx = cslot(cix - 2, cjx);
+          by = cslot(ciy, cjy - 2);
+        };
+        // field q of pair item r; returns its cell-average values
+        auto recon_xy = [&](int r, int q) -> f2 {
+          int bx, by;
+          item_base(r, bx, by);
+          const float *pq = sm.prim[q];
+          f2 st[5];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float *pq = sm.prim[q];
-            f2 st[5];
-#pragma unroll
-            for (int o = 0; o < 5; ++o) st[o] = make_float2(pq[bx + o], pq[by + o * CPW]);
-            mid[q] = st[2];
-            f2 qL, qR;
-            recon2(rk, st[0], st[1], st[2], st[3], st[4], qL, qR);
-            sm.rec[0][2 * q][r] = qL.x;
-            sm.rec[0][2 * q + 1][r] = qR.x;
-            sm.rec[1][2 * q][r] = qL.y;
-            sm.rec[1][2 * q + 1][r] = qR.y;
-          }
-          // T_DD = a + b f_D^2 of the cell average, D = x (lane x), y (lane y)
+          for (int o = 0; o < 5; ++o) st[o] = make_float2(pq[bx + o], pq[by + o * CPW]);
+          f2 qL, qR;
+          recon2(rk, st[0], st[1], st[2], st[3], st[4], qL, qR);
+          sm.rec[0][2 * q][r] = qL.x;
+          sm.rec[0][2 * q + 1][r] = qR.x;
+          sm.rec[1][2 * q][r] = qL.y;
+          sm.rec[1][2 * q + 1][r] = qR.y;
+          return st[2];
+        };
+        // T_DD = a + b f_D^2 of the cell average of item r, D = x (lane x),
+        // y (lane y), from its four fields mid
+        auto sq_xy = [&](int r, const f2 mid[4]) {
           const f2 fsq = fma2(mid[3], mid[3], fma2(mid[1], mid[1], mul2(mid[2], mid[2])));
           f2 a, bb;
           closure_ab2<CL>(fsq, a, bb);
@@ -343,6 +358,28 @@ __global__ void __launch_bounds__(NT, MINB)
           const f2 Tdd = fma2(mul2(bb, fD), fD, a);
           sm.sq[0][r] = qsqrt(Tdd.x);
           sm.sq[1][r] = qsqrt(Tdd.y);
+        };
+        if (t < NREC && item_ok(t)) {
+          f2 mid[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) mid[q] = recon_xy(t, q);
+          sq_xy(t, mid);
+        }
+        if constexpr (NXR > 0) {
+          const int lane = t & 31, q = t >> 5, r = NT + lane;
+          if (q < 5 && lane < NXR && item_ok(r)) {
+            if (q < 4) {
+              recon_xy(r, q);
+            } else {
+              int bx, by;
+              item_base(r, bx, by);
+              f2 mid[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                mid[k] = make_float2(sm.prim[k][bx + 2], sm.prim[k][by + 2 * CPW]);
+              sq_xy(r, mid);
+            }
+          }
         }
       } else {
         for (int it = t; it < 2 * CXPOS * CW; it += NT) {
