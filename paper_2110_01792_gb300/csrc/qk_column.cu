@@ -368,27 +368,64 @@ __global__ void __launch_bounds__(NT, MINB) hydro_column_kernel(Geometry g, qk_p
       if constexpr (sizeof(T) == 4) {
         // FP32: face r of the x rows and face r of the y columns as the two
         // lanes of hllc2, each in its own frame (rho, u_n, u_t1, u_t2, P):
-        // x (rho, vx, vy, vz, P), y (rho, vy, vz, vx, P)
-        // (the pairs beyond NT fall to the second warp: the first already
-        // took the extra reconstruction round)
-        for (int r = (t + NT - 32) % NT; r < CXFACE * CW; r += NT) {
+        // x (rho, vx, vy, vz, P), y (rho, vy, vz, vx, P).  Each thread takes
+        // pair t; the pairs past NT (16 of them at NT = CNT) go as single
+        // faces, x and y on separate lanes, to the first warp (which enters
+        // no ring cell below), so that its extra round costs one face per
+        // lane rather than a pair.
+        constexpr int NFP = CXFACE * CW;
+        constexpr int NXF = NFP > NT ? NFP - NT : 0;
+        static_assert(2 * NXF <= 32, "the extra faces fit one warp");
+        constexpr int qy[5] = {0, 2, 3, 1, 4};
+        if (t < NFP) {
+          const int r = t;
           const int fx = r % CXFACE, cjx = r / CXFACE;
           const int ciy = r % CW, fy = r / CW;
           const bool okx = cjx < vy && fx <= vx, oky = ciy < vx && fy <= vy;
-          if (!okx && !oky) continue;
-          const int ilx = cjx * CXPOS + fx, ily = fy * CW + ciy;
-          constexpr int qy[5] = {0, 2, 3, 1, 4};
-          f2 wL[5], wR[5], F[5];
+          if (okx || oky) {
+            const int ilx = cjx * CXPOS + fx, ily = fy * CW + ciy;
+            f2 wL[5], wR[5], F[5];
 #pragma unroll
-          for (int k = 0; k < 5; ++k) {
-            wL[k] = make_float2(sm.rec[0][2 * k + 1][ilx], sm.rec[1][2 * qy[k] + 1][ily]);
-            wR[k] = make_float2(sm.rec[0][2 * k][ilx + 1], sm.rec[1][2 * qy[k]][ily + CW]);
+            for (int k = 0; k < 5; ++k) {
+              wL[k] = make_float2(sm.rec[0][2 * k + 1][ilx], sm.rec[1][2 * qy[k] + 1][ily]);
+              wR[k] = make_float2(sm.rec[0][2 * k][ilx + 1], sm.rec[1][2 * qy[k]][ily + CW]);
+            }
+            hllc2(wL, wR, gamma, gm1inv, g1, F);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+              sm.flux[0][k][r] = F[k].x;
+              sm.flux[1][qy[k]][r] = F[k].y;
+            }
           }
-          hllc2(wL, wR, gamma, gm1inv, g1, F);
+        }
+        if constexpr (NXF > 0) {
+          if (t < 2 * NXF) {
+            const int dir = t / NXF, r = NT + t % NXF;
+            int il, step;
+            bool ok;
+            if (dir == 0) {
+              const int fx = r % CXFACE, cjx = r / CXFACE;
+              ok = cjx < vy && fx <= vx;
+              il = cjx * CXPOS + fx;
+              step = 1;
+            } else {
+              const int ciy = r % CW, fy = r / CW;
+              ok = ciy < vx && fy <= vy;
+              il = fy * CW + ciy;
+              step = CW;
+            }
+            if (ok) {
+              float wL[5], wR[5], F[5];
 #pragma unroll
-          for (int k = 0; k < 5; ++k) {
-            sm.flux[0][k][r] = F[k].x;
-            sm.flux[1][qy[k]][r] = F[k].y;
+              for (int k = 0; k < 5; ++k) {
+                const int qk = dir ? qy[k] : k;
+                wL[k] = sm.rec[dir][2 * qk + 1][il];
+                wR[k] = sm.rec[dir][2 * qk][il + step];
+              }
+              hllc2(wL, wR, gamma, gm1inv, g1, F);
+#pragma unroll
+              for (int k = 0; k < 5; ++k) sm.flux[dir][dir ? qy[k] : k][r] = F[k];
+            }
           }
         }
       } else {

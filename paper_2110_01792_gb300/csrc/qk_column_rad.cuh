@@ -427,40 +427,92 @@ __global__ void __launch_bounds__(NT, MINB)
       if constexpr (!kAB) {
         // FP32: face r of the x rows and face r of the y columns as the two
         // lanes of rad_face_hll2, each in its own frame (E_r, f_n, f_t1,
-        // f_t2): x (E_r, f_x, f_y, f_z), y (E_r, f_y, f_z, f_x)
-        // (the pairs beyond NT fall to the second warp: the first already
-        // took the extra reconstruction round)
-        for (int r = (t + NT - 32) % NT; r < CXFACE * CW; r += NT) {
+        // f_t2): x (E_r, f_x, f_y, f_z), y (E_r, f_y, f_z, f_x).  Each thread
+        // takes pair t; the pairs past NT (16 of them at NT = CNT) go as
+        // single faces, x and y on separate lanes, to the last warp, so that
+        // its extra round costs one face per lane rather than a pair.
+        constexpr int NFP = CXFACE * CW;
+        constexpr int NXF = NFP > NT ? NFP - NT : 0;
+        static_assert(2 * NXF <= 32, "the extra faces fit one warp");
+        constexpr int qy[4] = {0, 2, 3, 1};
+        if (t < NFP) {
+          const int r = t;
           const int fx = r % CXFACE, cjx = r / CXFACE;
           const int ciy = r % CW, fy = r / CW;
           const bool okx = cjx < vy && fx <= vx, oky = ciy < vx && fy <= vy;
-          if (!okx && !oky) continue;
-          const int ilx = cjx * CXPOS + fx, ily = fy * CW + ciy;
-          const int sax = cslot(fx - 1, cjx), say = cslot(ciy, fy - 1);
-          constexpr int qy[4] = {0, 2, 3, 1};
-          f2 wL[4], wR[4], out[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            wL[k] = make_float2(sm.rec[0][2 * k + 1][ilx], sm.rec[1][2 * qy[k] + 1][ily]);
-            wR[k] = make_float2(sm.rec[0][2 * k][ilx + 1], sm.rec[1][2 * qy[k]][ily + CW]);
-          }
-          auto averages = [&](f2 *avL, f2 *avR) {
+          if (okx || oky) {
+            const int ilx = cjx * CXPOS + fx, ily = fy * CW + ciy;
+            const int sax = cslot(fx - 1, cjx), say = cslot(ciy, fy - 1);
+            f2 wL[4], wR[4], out[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              avL[k] = make_float2(sm.prim[k][sax], sm.prim[qy[k]][say]);
-              avR[k] = make_float2(sm.prim[k][sax + 1], sm.prim[qy[k]][say + CPW]);
+              wL[k] = make_float2(sm.rec[0][2 * k + 1][ilx], sm.rec[1][2 * qy[k] + 1][ily]);
+              wR[k] = make_float2(sm.rec[0][2 * k][ilx + 1], sm.rec[1][2 * qy[k]][ily + CW]);
             }
-          };
-          const f2 S = mul2(p2(chat), make_float2(fmaxf(sm.sq[0][ilx], sm.sq[0][ilx + 1]),
-                                                  fmaxf(sm.sq[1][ily], sm.sq[1][ily + CW])));
-          const f2 rka = make_float2(sm.rk[sax], sm.rk[say]);
-          const f2 rkb = make_float2(sm.rk[sax + 1], sm.rk[say + CPW]);
-          rad_face_hll2<CL>(wL, wR, averages, S, rka, rkb, make_float2(dx[0], dx[1]), c, chat,
-                            hchat_c, hccc, p.tau_correction, out);
+            auto averages = [&](f2 *avL, f2 *avR) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            sm.flux[0][k][r] = out[k].x;
-            sm.flux[1][qy[k]][r] = out[k].y;
+              for (int k = 0; k < 4; ++k) {
+                avL[k] = make_float2(sm.prim[k][sax], sm.prim[qy[k]][say]);
+                avR[k] = make_float2(sm.prim[k][sax + 1], sm.prim[qy[k]][say + CPW]);
+              }
+            };
+            const f2 S = mul2(p2(chat), make_float2(fmaxf(sm.sq[0][ilx], sm.sq[0][ilx + 1]),
+                                                    fmaxf(sm.sq[1][ily], sm.sq[1][ily + CW])));
+            const f2 rka = make_float2(sm.rk[sax], sm.rk[say]);
+            const f2 rkb = make_float2(sm.rk[sax + 1], sm.rk[say + CPW]);
+            rad_face_hll2<CL>(wL, wR, averages, S, rka, rkb, make_float2(dx[0], dx[1]), c, chat,
+                              hchat_c, hccc, p.tau_correction, out);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              sm.flux[0][k][r] = out[k].x;
+              sm.flux[1][qy[k]][r] = out[k].y;
+            }
+          }
+        }
+        if constexpr (NXF > 0) {
+          const int lane = t - (NT - 32);
+          if (lane >= 0 && lane < 2 * NXF) {
+            const int dir = lane / NXF, r = NT + lane % NXF;
+            int il, step, sa, sstep;
+            bool ok;
+            if (dir == 0) {
+              const int fx = r % CXFACE, cjx = r / CXFACE;
+              ok = cjx < vy && fx <= vx;
+              il = cjx * CXPOS + fx;
+              step = 1;
+              sa = cslot(fx - 1, cjx);
+              sstep = 1;
+            } else {
+              const int ciy = r % CW, fy = r / CW;
+              ok = ciy < vx && fy <= vy;
+              il = fy * CW + ciy;
+              step = CW;
+              sa = cslot(ciy, fy - 1);
+              sstep = CPW;
+            }
+            if (ok) {
+              float wL[4], wR[4], out[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const int qk = dir ? qy[k] : k;
+                wL[k] = sm.rec[dir][2 * qk + 1][il];
+                wR[k] = sm.rec[dir][2 * qk][il + step];
+              }
+              auto averages = [&](float *avL, float *avR) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                  const int qk = dir ? qy[k] : k;
+                  avL[k] = sm.prim[qk][sa];
+                  avR[k] = sm.prim[qk][sa + sstep];
+                }
+              };
+              const float S = __fmul_rn(chat, fmaxf(sm.sq[dir][il], sm.sq[dir][il + step]));
+              rad_face_hll2<CL>(wL, wR, averages, S, sm.rk[sa], sm.rk[sa + sstep],
+                                dir ? dx[1] : dx[0], c, chat, hchat_c, hccc, p.tau_correction,
+                                out);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) sm.flux[dir][dir ? qy[k] : k][r] = out[k];
+            }
           }
         }
       } else {
