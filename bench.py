@@ -344,21 +344,37 @@ def time_kernel(torch, fn, reps, stream):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
-# (profiles/ncu_*.md), valid only while the kernel's sources hash to the value
-# recorded at capture time.
+# (profiles/ncu_*.md), valid only while the kernel's code (comments and
+# whitespace removed) hashes to the value recorded at capture time.
 NCU_TRAFFIC = {
-    ("rhd128", "rad_stage_ex_kernel<double>"): (343.05e6, "rad", "883bdf51d812"),
-    ("rhd128", "rad_stage_kernel<double,1>"): (135.91e6, "rad", "883bdf51d812"),
-    ("rhd128", "hydro_stage_kernel<double,1>"): (150.50e6, "hydro", "a8fd1f513130"),
-    ("hydro256", "hydro_column_kernel<float,1>"): (843.54e6, "hydrocol", "ed74fba6a9fd"),
-    ("rhd128", "rad_column_kernel<float,2,EX>"): (170.06e6, "radcol", "611f7b9fb245"),
-    ("rhd128", "rad_column_kernel<float,1>"): (56.11e6, "radcol", "611f7b9fb245"),
+    ("rhd128", "rad_stage_ex_kernel<double>"): (343.05e6, "rad", "5e02440890a4"),
+    ("rhd128", "rad_stage_kernel<double,1>"): (135.91e6, "rad", "5e02440890a4"),
+    ("rhd128", "hydro_stage_kernel<double,1>"): (150.50e6, "hydro", "08c0e4e62ed0"),
+    ("hydro256", "hydro_column_kernel<float,1>"): (843.54e6, "hydrocol", "a98b6816d223"),
+    ("rhd128", "rad_column_kernel<float,2,EX>"): (170.06e6, "radcol", "8bc1abbe78e3"),
+    ("rhd128", "rad_column_kernel<float,1>"): (56.11e6, "radcol", "8bc1abbe78e3"),
 }
 
 
-def _src_hash(kind: str) -> str:
+def _strip_code(text: str) -> str:
+    """C/C++/CUDA source without its comments and whitespace: what the
+    compiler sees of it (the sources quote no comment markers in strings)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return "".join(text.split())
+
+
+def _src_hash(kind: str, read=None) -> str:
+    """sha1 prefix of a kernel's code (its sources plus qk_device.cuh and
+    qk_internal.cuh, comments and whitespace removed); read(name) returns a
+    source's text (default: the working tree)."""
     import hashlib
     cs = os.path.join(ROOT, "paper_2110_01792_gb300", "csrc")
+    if read is None:
+        def read(name):
+            with open(os.path.join(cs, name), encoding="utf-8") as fh:
+                return fh.read()
     files = {"rad": ["qk_rad.cu", "qk_rad.cuh", "qk_exchange.cuh"], "hydro": ["qk_hydro.cu"],
              "radcol": ["qk_column_rad.cu", "qk_column_rad.cuh", "qk_rad.cuh",
                         "qk_exchange.cuh", "qk_pair.cuh"],
@@ -366,8 +382,7 @@ def _src_hash(kind: str) -> str:
              "cell": ["qk_cell.cu", "qk_exchange.cuh"]}[kind]
     h = hashlib.sha1()
     for f in files + ["qk_device.cuh", "qk_internal.cuh"]:
-        with open(os.path.join(cs, f), "rb") as fh:
-            h.update(fh.read())
+        h.update(_strip_code(read(f)).encode())
     return h.hexdigest()[:12]
 
 

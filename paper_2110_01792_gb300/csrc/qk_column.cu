@@ -51,10 +51,10 @@ __device__ __forceinline__ void load_prim(const F5<T> &U, long long e, T gm1, T 
 
 // Threads per CTA: CNT (one per footprint cell), or CNT + 32: a ninth warp
 // without an own cell, so that the x and y items of a plane (CW (CW + 2)
-// reconstruction positions and CW (CW + 1) faces per direction) come to at
-// most two per thread instead of three for a quarter of the warps -- the
-// phases between barriers end together.  MINB: resident CTAs per SM the
-// registers are held to.
+// reconstruction positions and CW (CW + 1) faces per direction; FP32: as
+// x/y pairs) come to one pair per thread (FP32) or at most two items per
+// thread (FP64) -- the phases between barriers end together.  MINB:
+// resident CTAs per SM the registers are held to.
 template <typename T, int STAGE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) hydro_column_kernel(Geometry g, qk_params p, SC<T> K,
                                                           F5<T> U0, F5<T> U1, F5<T> Uo, DtSrc dts,

@@ -89,8 +89,7 @@ __global__ void __launch_bounds__(NT, MINB)
     const long long own0 = has_own ? cell_elem(b, g.ng, col.x0 + ti, col.y0 + tj, 0) : 0;
     int ri = 0, rj = 0, rside = 0;
     bool ring = false;
-    // ring cells go to the last CNRING threads (the first warp takes the
-    // extra reconstruction round of the plane)
+    // ring cells go to the last CNRING threads
     const int rt = t - (NT - CNRING);
     if (rt >= 0) {
       rside = rt / (HALO * CW);
